@@ -1,0 +1,467 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the PDF / alpha_s hot path on GB300.
+
+One step = one pass of the hot path over one batch: x f(x, Q^2) for all 13
+flavours (FP64, log-bicubic with continuation outside the grid) plus
+alpha_s(Q^2), for 1e7 query points on the three-subgrid synthetic grid.
+Metric: evaluations per second (points x flavours, alpha_s counting one per
+point).  Inputs (160 MB) and outputs (1.1 GB) exceed the 129 MB L2, so no
+flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank evaluates its own batch (weak scaling, no
+collective in the data path); the step time is the max over ranks.
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import math
+import os
+import shutil
+import subprocess
+import sys
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "PDF evals/s (points×flavours) FP64 vs FP32 vs surrogate at stated max rel err"
+N_POINTS = 10_000_000
+MC_EVENTS = 1_000_000
+WORKLOAD = ("three Q subgrids (12/15/25 Q knots split at Q = 1.51 and 4.92 GeV, Q in [1, 1e5] GeV), "
+            "196 x knots in [1e-9, 1], 13 flavours; 1e7 queries per rank, x log-uniform in [1e-10, 1], "
+            "Q log-uniform in [1, 2e5] GeV (15% outside the grid); all flavours + alpha_s per point")
+
+# Ceilings.  FP64/FP32 FMA: GB300 has 152 SMs at up to 2070 MHz; FP64 issues
+# 2 DFMA/clk/SM (1.25 TFLOP/s nominal), FP32 128 FFMA/clk/SM.
+SMS, SM_MHZ = 152, 2070.0
+FP64_PEAK = SMS * 2 * 2 * SM_MHZ * 1e6       # flop/s
+FP32_PEAK = SMS * 128 * 2 * SM_MHZ * 1e6
+
+# Algorithmic work per evaluation (flops): the separable 4x4 contraction is
+# 16 multiply-adds (32 flops) per site; each point also costs 2 logs and
+# ~40 flops of Hermite/tangent weights.  Continuation rules: a log-linear
+# pair rule is 5 ops (div, log, mul, exp, mul), the low-Q^2 rule 9.
+FLOP_SITE, FLOP_POINT, FLOP_PAIR, FLOP_LOWQ = 32, 42, 5, 9
+CLASS_EVAL_FLOPS = {  # class -> flops per (point, flavour) beyond the point part
+    "in": 1 * FLOP_SITE,
+    "lowx": 2 * FLOP_SITE + FLOP_PAIR,
+    "highq": 2 * FLOP_SITE + FLOP_PAIR,
+    "lowq": 2 * FLOP_SITE + FLOP_LOWQ,
+    "lowx_highq": 4 * FLOP_SITE + 3 * FLOP_PAIR,
+    "lowx_lowq": 4 * FLOP_SITE + 2 * FLOP_LOWQ + FLOP_PAIR,
+}
+
+
+def classify(g, x, q2):
+    """Class counts of a batch (host-side bookkeeping for the flop count)."""
+    lowx = x < g.x_knots[0]
+    lowq = q2 < g.q2_knots[0]
+    highq = q2 > g.q2_knots[-1]
+    return {
+        "in": int((~lowx & ~lowq & ~highq).sum()),
+        "lowx": int((lowx & ~lowq & ~highq).sum()),
+        "highq": int((~lowx & highq).sum()),
+        "lowq": int((~lowx & lowq).sum()),
+        "lowx_highq": int((lowx & highq).sum()),
+        "lowx_lowq": int((lowx & lowq).sum()),
+    }
+
+
+def algorithmic_flops(counts, nflav):
+    return sum(c * (FLOP_POINT + nflav * CLASS_EVAL_FLOPS[k]) for k, c in counts.items())
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("xfxq2.cu", "pdf_internal.cuh", "grid.cu"):
+        h.update((ROOT / "paper_2009_06635_gb300" / "csrc" / name).read_bytes())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel, n_points):
+    """DRAM bytes per launch from the committed ncu summary, or None if the
+    kernel source changed since the counters were taken."""
+    f = ROOT / "profiles" / "traffic.json"
+    if not f.exists():
+        return None
+    try:
+        rec = json.loads(f.read_text()).get(kernel)
+    except Exception:
+        return None
+    if not rec or rec.get("source_hash") != kernel_source_hash():
+        return None
+    return rec["dram_bytes_per_point"] * n_points
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = ROOT / "gpurun_out" / f"clocks_{os.getpid()}.csv"
+
+    def start(self):
+        if not shutil.which("nvidia-smi"):
+            return
+        self.path.parent.mkdir(exist_ok=True)
+        self.fh = open(self.path, "w")
+        self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                      "--format=csv,noheader,nounits", "-lms", "200"],
+                                     stdout=self.fh, stderr=subprocess.DEVNULL)
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = [r.split(", ") for r in self.path.read_text().strip().splitlines() if r.strip()]
+        rows = [r for r in rows if len(r) >= 9]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].strip() == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((float(r[3]) for r in rows if r[3].replace(".", "").isdigit()), default=None)}
+
+
+def dist_setup():
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(world, v):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_timed(fn, steps, warmup, world, sync):
+    """W untimed steps, then K steps bracketed by barrier + synchronize."""
+    import torch
+
+    for _ in range(warmup):
+        fn()
+    sync()
+    barrier(world)
+    sync()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    sync()
+    barrier(world)
+    sync()
+    return e0.elapsed_time(e1) / steps  # ms per step
+
+
+# --------------------------------------------------------------------------
+# reference arm: the CPU oracle on the host cores
+# --------------------------------------------------------------------------
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2009_06635_gb300 import synthetic as S
+
+    g = S.grid_full()
+    og = oracle.OracleGrid(g)
+    sample = 200_000
+    x, q2 = S.queries_full(sample, 3)
+    for _ in range(max(1, args.warmup)):
+        og.xfxq2(x[:20_000], q2[:20_000])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        og.xfxq2(x, q2)
+        og.alphas(q2)
+    dt = (time.perf_counter() - t0) / args.steps
+    evals = sample * (g.nflav + 1)
+    value = evals / dt
+    cores = oracle.max_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "reference_sample_points_per_step": sample},
+        "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{sample} points of the same query law per step, all flavours + alpha_s"},
+        "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+
+def cpu_baseline_leg(g, x, q2, out_gpu, a_gpu, x32, q32, out32, target_s=10.0):
+    """Time the oracle as it stands on the host cores on a bounded sample of
+    the workload; with the same oracle outputs, state the GPU paths' errors
+    on that sample."""
+    import oracle
+
+    og = oracle.OracleGrid(g)
+    cores = oracle.max_threads()
+    probe = 20_000
+    t0 = time.perf_counter()
+    og.xfxq2(x[:probe], q2[:probe])
+    og.alphas(q2[:probe])
+    per_pt = (time.perf_counter() - t0) / probe
+    m = int(min(len(x), max(probe, target_s / per_pt)))
+    idx = np.random.default_rng(11).choice(len(x), m, replace=False)
+    idx.sort()
+    t0 = time.perf_counter()
+    v, s, fl = og.xfxq2(x[idx], q2[idx])
+    av, asv = og.alphas(q2[idx])
+    dt = time.perf_counter() - t0
+    rate = m * (g.nflav + 1) / dt
+    err64 = np.abs(out_gpu[idx] - v) / np.maximum(np.abs(v), s)
+    err64 = np.where(fl, 0.0, err64)
+    aerr = float((np.abs(a_gpu[idx] - av) / np.maximum(np.abs(av), asv)).max())
+    # FP32 path against the oracle at the float inputs (a sub-sample)
+    k = min(m, 200_000)
+    v3, s3, f3 = og.xfxq2(x32[idx[:k]].astype(np.float64), q32[idx[:k]].astype(np.float64))
+    err32 = np.where(f3, 0.0, np.abs(out32[idx[:k]] - v3) / np.maximum(np.abs(v3), s3))
+    return ({"value": rate, "unit": "evals/s", "cores": cores, "kind": "oracle",
+             "sample": f"{m} of the {len(x)} points (all flavours + alpha_s), {dt:.1f} s on {cores} threads"},
+            {"fp64_max_scaled_err": float(np.nanmax(err64)), "alphas_max_scaled_err": aerr,
+             "fp32_max_scaled_err_per_flavour": [float(e) for e in np.nanmax(err32, axis=0)],
+             "scaled_err": "|gpu - oracle| / max(|oracle|, sum|w f|), on the sampled points",
+             "marginal_excluded": int(fl.sum()), "sample_points": m})
+
+
+def our_arm(args):
+    import torch
+
+    import paper_2009_06635_gb300 as P
+    from paper_2009_06635_gb300 import _native
+    from paper_2009_06635_gb300 import synthetic as S
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sync = torch.cuda.synchronize
+    lib = _native.load(build_if_missing=False)
+
+    g = S.grid_full()
+    G = P.pdf_load_grid(g)
+    n = args.points
+    x, q2 = S.queries_full(n, 3 + 1000 * rank)
+    counts = classify(g, x, q2)
+    nf = g.nflav
+    xd = torch.from_numpy(x).to(dev)
+    qd = torch.from_numpy(q2).to(dev)
+    out = torch.empty((n, nf), dtype=torch.float64, device=dev)
+    aout = torch.empty((n,), dtype=torch.float64, device=dev)
+    evals_step = n * (nf + 1)
+
+    # per-launch duration of the dominant kernel, on the launching stream
+    ev = []
+
+    def step64(record=False):
+        if record:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            P.xfxq2_all_flavours(G, xd, qd, out=out)
+            b.record()
+            ev.append((a, b))
+        else:
+            P.xfxq2_all_flavours(G, xd, qd, out=out)
+        P.alphas_q2(G, qd, out=aout)
+
+    if args.only:
+        xs = (xd, qd, out, aout) if args.only == "fp64" else (xd.float(), qd.float(), out.float(), aout.float())
+        ms = run_timed(lambda: (P.xfxq2_all_flavours(G, xs[0], xs[1], out=xs[2]), P.alphas_q2(G, xs[1], out=xs[3])),
+                       args.steps, args.warmup, world, sync)
+        if rank == 0:
+            print(json.dumps({"only": args.only, "points": n, "ms_per_step": ms, "evals_per_s": evals_step / (ms * 1e-3)}))
+        return 0
+
+    clocks = Clocks(local)
+    clocks.start()
+    ms64 = run_timed(lambda: step64(True), args.steps, args.warmup, world, sync)
+    clk = clocks.stop()
+    kern_ms = [a.elapsed_time(b) for a, b in ev[args.warmup:]]
+    kern_ms = float(np.mean(kern_ms))
+    ms64 = max_over_ranks(world, ms64)
+    value = world * evals_step / (ms64 * 1e-3)
+
+    # FP32 path on the same workload
+    x32, q32 = x.astype(np.float32), q2.astype(np.float32)
+    xd32, qd32 = torch.from_numpy(x32).to(dev), torch.from_numpy(q32).to(dev)
+    out32 = torch.empty((n, nf), dtype=torch.float32, device=dev)
+    aout32 = torch.empty((n,), dtype=torch.float32, device=dev)
+    ev32 = []
+
+    def step32():
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        P.xfxq2_all_flavours(G, xd32, qd32, out=out32)
+        b.record()
+        ev32.append((a, b))
+        P.alphas_q2(G, qd32, out=aout32)
+
+    ms32 = max_over_ranks(world, run_timed(step32, args.steps, args.warmup, world, sync))
+    k32 = float(np.mean([a.elapsed_time(b) for a, b in ev32[args.warmup:]]))
+
+    # single flavour, alpha_s alone, fused MC event batch
+    one = torch.empty((n,), dtype=torch.float64, device=dev)
+    ms_pid = run_timed(lambda: P.xfxq2(G, 21, xd, qd, out=one), args.steps, 2, world, sync)
+    ms_as = run_timed(lambda: P.alphas_q2(G, qd, out=aout), args.steps, 2, world, sync)
+    x1, x2, s2 = S.events_mc(MC_EVENTS, 4 + 1000 * rank)
+    x1d, x2d = torch.from_numpy(x1).to(dev), torch.from_numpy(x2).to(dev)
+    mco = torch.empty((MC_EVENTS, 2 * nf + 1), dtype=torch.float64, device=dev)
+    ms_mc = run_timed(lambda: P.pdf_mc_event(G, x1d, x2d, s2, out=mco), args.steps, 2, world, sync)
+    x1f, x2f = x1d.float(), x2d.float()
+    mco32 = torch.empty((MC_EVENTS, 2 * nf + 1), dtype=torch.float32, device=dev)
+    ms_mc32 = run_timed(lambda: P.pdf_mc_event(G, x1f, x2f, float(np.float32(s2)), out=mco32),
+                        args.steps, 2, world, sync)
+
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    hx = torch.from_numpy(x).pin_memory()
+    hq = torch.from_numpy(q2).pin_memory()
+    hout = torch.empty((n, nf), dtype=torch.float64).pin_memory()
+    hal = torch.empty((n,), dtype=torch.float64).pin_memory()
+    e2e_steps = max(3, min(args.steps, 10))
+    for _ in range(2):
+        P.xfxq2_all_flavours_host(G, hx, hq, out=hout, alphas_out=hal)
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        P.xfxq2_all_flavours_host(G, hx, hq, out=hout, alphas_out=hal)
+    e2e_s = max_over_ranks(world, (time.perf_counter() - t0) / e2e_steps)
+
+    # ceilings measured on this GPU
+    fp64_meas = ctypes.c_double(0.0)
+    fp32_meas = ctypes.c_double(0.0)
+    _native.check(lib.pdf_probe_fma_rate(64, 4096, ctypes.byref(fp64_meas)), "probe fp64")
+    _native.check(lib.pdf_probe_fma_rate(32, 65536, ctypes.byref(fp32_meas)), "probe fp32")
+    peaks = json.loads((ROOT / "MEASURED_PEAKS.json").read_text()) if (ROOT / "MEASURED_PEAKS.json").exists() else {}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+
+    flops = algorithmic_flops(counts, nf)
+    achieved = flops / (kern_ms * 1e-3)
+    traffic = profiled_traffic("k_xf<double,points>", n)
+    bytes32 = n * (8 + 4 * nf)
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "evals/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms64,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic: seeded LHAPDF-shaped grid and log-uniform queries (no real PDF set in the container)",
+        "config": {"workload": WORKLOAD, "points_per_rank": n, "evals_per_step_per_rank": evals_step,
+                   "class_counts": counts, "l2": "inputs + outputs 1.3 GB per step > 129 MB L2, no flush",
+                   "parallelism": f"{world} independent replicas (weak scaling, no collective)"},
+        "roofline": {"bound": "alu", "kernel": "xfxq2_all_flavours FP64 (k_xf<double,points>)",
+                     "achieved": achieved / 1e12, "peak": FP64_PEAK / 1e12, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_PEAK, "traffic": traffic,
+                     "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
+                     "peak_measured_dfma": fp64_meas.value / 1e12,
+                     "kernel_ms": kern_ms, "algorithmic_flops_per_launch": flops,
+                     "hbm_frac": n * (16 + 8 * nf) / (kern_ms * 1e-3) / (hbm * 1e9)},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk,
+        "e2e": {"value": world * evals_step / e2e_s, "unit": "evals/s", "h2d_bytes_per_step": 16 * n,
+                "d2h_bytes_per_step": 8 * n * (nf + 1), "ms_per_step": e2e_s * 1e3,
+                "call": "xfxq2_all_flavours_host (pinned host buffers, alpha_s included)"},
+        "paths": {
+            "fp32": {"value": world * evals_step / (ms32 * 1e-3), "ms_per_step": ms32, "kernel_ms": k32,
+                     "roofline": {"bound": "hbm", "achieved": bytes32 / (k32 * 1e-3) / 1e9, "peak": hbm,
+                                  "unit": "GB/s", "frac": bytes32 / (k32 * 1e-3) / 1e9 / hbm,
+                                  "fp32_fma_peak_derived_tflops": FP32_PEAK / 1e12,
+                                  "fp32_fma_peak_measured_tflops": fp32_meas.value / 1e12}},
+            "single_pid_fp64": {"value": world * n / (ms_pid * 1e-3), "ms_per_step": ms_pid},
+            "alphas_fp64": {"value": world * n / (ms_as * 1e-3), "ms_per_step": ms_as},
+            "mc_event_fp64": {"value": world * MC_EVENTS * (2 * nf + 1) / (ms_mc * 1e-3), "ms_per_step": ms_mc,
+                              "events": MC_EVENTS},
+            "mc_event_fp32": {"value": world * MC_EVENTS * (2 * nf + 1) / (ms_mc32 * 1e-3),
+                              "ms_per_step": ms_mc32, "events": MC_EVENTS},
+        },
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sync()
+        cpu, acc = cpu_baseline_leg(g, x, q2, out.cpu().numpy(), aout.cpu().numpy(), x32, q32,
+                                    out32.cpu().numpy().astype(np.float64))
+        line["cpu_baseline"] = cpu
+        line["accuracy"] = acc
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--points", type=int, default=N_POINTS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", choices=["fp64", "fp32"], default=None,
+                    help="run only that path's step (a small case for profiling); prints its timing")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        return reference_arm(args)
+    return our_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,172 @@
+/*
+ * pdf_gb300.h -- C ABI of the GB300 PDF / alpha_s evaluation library.
+ *
+ * The library evaluates parton distribution functions x f(x, Q^2) and the
+ * strong coupling alpha_s(Q^2) for large batches of query points on one
+ * NVIDIA GB300 (sm_103a), following PDFFlow (arXiv:2009.06635):
+ *   - Sec. 2.1 / Fig. 1: a PDF object is made once from the tabulated set
+ *     (mkPDF) and then queried for one flavour (xfxQ2), all flavours
+ *     (xfxQ2_allpid) or alpha_s (alphas_Q2);
+ *   - Sec. 2.2: log-bicubic interpolation in (ln x, ln Q^2) of the tabulated
+ *     values, Q subgrids split at flavour thresholds interpolated
+ *     independently, finite-difference knot tangents that do not reach past
+ *     the x edges or a subgrid boundary;
+ *   - Fig. 1 (EXTRAPOLATE): continuation outside the grid -- low x and high
+ *     Q^2 continue log-linearly from the two outermost knots (linearly when
+ *     either value is not positive); low Q^2 continues with the anomalous
+ *     dimension gamma = ln(F(1.01 Q2min)/F(Q2min)) / ln 1.01 as
+ *     F(Q2min) rho^(gamma rho + 1 - rho), rho = Q^2/Q2min; corners apply the
+ *     Q rule at the two lowest x knots, then the low-x rule;
+ *   - Sec. 2.3: alpha_s by log-cubic interpolation of (Q^2, alpha_s) nodes,
+ *     subgrids split at repeated nodes, constant outside the node range.
+ *
+ * Conventions for every call:
+ *   - Return value: PDF_OK (0) on success, a negative PDF_ERR_* code
+ *     otherwise; pdf_last_error() then describes the failure (per thread).
+ *   - Query and output pointers of the non-"_host" calls are DEVICE memory
+ *     owned by the caller; the call enqueues its kernels on `stream`
+ *     (0 = the legacy default stream) and returns without waiting.
+ *   - "_host" calls take HOST memory (pinned memory gives the overlapped
+ *     fast path), copy through device buffers the grid owns, and return only
+ *     when the outputs are in host memory.  Two "_host" calls on one grid
+ *     must not run concurrently from different threads.
+ *   - Arrays are dense and row-major; outputs of the all-flavour calls are
+ *     [n][nflav] in the column order the grid was loaded with.
+ *   - A query point with x <= 0, x above the last x knot, Q^2 <= 0,
+ *     Q^2 = +inf or a NaN coordinate is invalid: its outputs are NaN and the
+ *     grid's invalid-point counter is incremented once per point.
+ *     No call traps, spins or aborts on any input values.
+ *   - n == 0 is valid and launches nothing.
+ */
+#ifndef PDF_GB300_H
+#define PDF_GB300_H
+
+#include <stddef.h>
+#include <cuda_runtime_api.h>
+
+#if defined(__GNUC__)
+#define PDF_API __attribute__((visibility("default")))
+#else
+#define PDF_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  PDF_OK = 0,
+  PDF_ERR_NULL = -1,       /* a required pointer is NULL                      */
+  PDF_ERR_GRID = -2,       /* malformed grid descriptor                       */
+  PDF_ERR_PID = -3,        /* flavour id not in the grid                      */
+  PDF_ERR_CUDA = -4,       /* a CUDA runtime call or kernel launch failed     */
+  PDF_ERR_ALLOC = -5,      /* device or host allocation failed                */
+  PDF_ERR_ARG = -6,        /* an argument is out of range                     */
+  PDF_ERR_NO_ALPHAS = -7   /* the grid was loaded without alpha_s nodes       */
+};
+
+/* Size limits of a grid (checked by pdf_load_grid). */
+#define PDF_MAX_NX 2048      /* x knots                                        */
+#define PDF_MAX_ROWS 1024    /* Q^2 knots over all subgrids (duplicates count) */
+#define PDF_MAX_NFLAV 64     /* flavour columns                                */
+#define PDF_MAX_NALPHAS 1024 /* alpha_s nodes                                  */
+
+/* Opaque handle: owns device copies of the knots, the values, the staged
+ * per-cell tables and the invalid-point counter. */
+typedef struct pdf_grid pdf_grid;
+
+/* A PDF set in LHAPDF layout (host memory, read during pdf_load_grid only;
+ * the caller keeps ownership).  PDFFlow Sec. 2.1-2.3.
+ *   nx, x_knots      strictly increasing, 0 < x <= 1, nx >= 2.
+ *   nsub, nq         number of Q subgrids and knots per subgrid (each >= 2).
+ *   q2_knots         sum(nq) values, strictly increasing inside a subgrid; the
+ *                    first knot of subgrid s+1 equals the last of subgrid s
+ *                    (flavour threshold).  Q2max >= 1.01 Q2min is required by
+ *                    the low-Q^2 continuation.
+ *   nflav, pids      flavour ids of the value columns (PDG; 21 = gluon,
+ *                    pid 0 is accepted as an alias of 21 by pdf_xfxq2).
+ *   values           [sum(nq)][nx][nflav] tabulated x f(x, Q^2), finite.
+ *   na, as_q2, as_vals  alpha_s nodes (na = 0: no alpha_s); as_q2 > 0
+ *                    non-decreasing, a repeated value splits subgrids, every
+ *                    subgrid has >= 2 nodes. */
+typedef struct {
+  int nx;
+  const double *x_knots;
+  int nsub;
+  const int *nq;
+  const double *q2_knots;
+  int nflav;
+  const int *pids;
+  const double *values;
+  int na;
+  const double *as_q2;
+  const double *as_vals;
+} pdf_grid_desc;
+
+/* Validate `desc`, copy it to the device and stage the per-cell tables
+ * (logs of the knots, finite-difference tangent weights, bicubic patch
+ * coefficients in FP64 and FP32, alpha_s cubic coefficients).  PDFFlow
+ * Sec. 2.1 (mkPDF) and 2.2 (data loaded once into device tensors).
+ * Synchronous; uses the current CUDA device.  *out receives the handle. */
+PDF_API int pdf_load_grid(const pdf_grid_desc *desc, pdf_grid **out);
+
+/* Free a handle and all its device memory (NULL is a no-op).  Waits for
+ * work the handle's own streams still run. */
+PDF_API int pdf_free_grid(pdf_grid *grid);
+
+/* Number of flavour columns and the column index of a pid (-1 if absent). */
+PDF_API int pdf_grid_nflav(const pdf_grid *grid);
+PDF_API int pdf_grid_pid_column(const pdf_grid *grid, int pid);
+
+/* x f(x, Q^2) of one flavour `pid` at n points: x, q2, out are [n] FP64
+ * device arrays.  PDFFlow Sec. 2.1 (xfxQ2), Sec. 2.2. */
+PDF_API int xfxq2(const pdf_grid *grid, int pid, const double *x, const double *q2, size_t n,
+          double *out, cudaStream_t stream);
+
+/* All flavours at n points: out is [n][nflav] FP64.  PDFFlow (xfxQ2_allpid). */
+PDF_API int xfxq2_all_flavours(const pdf_grid *grid, const double *x, const double *q2, size_t n,
+                       double *out, cudaStream_t stream);
+
+/* alpha_s(Q^2) at n points, FP64 [n].  PDFFlow Sec. 2.3 (alphas_Q2). */
+PDF_API int alphas_q2(const pdf_grid *grid, const double *q2, size_t n, double *out,
+              cudaStream_t stream);
+
+/* FP32 variants: float inputs and outputs, FP32 arithmetic and accumulation
+ * on FP32-rounded patch coefficients; the knot search is exact for the float
+ * inputs (the same cell an FP64 search picks) and ln x, ln Q^2 are taken
+ * relative to the cell's knot so that no absolute-log rounding enters. */
+PDF_API int xfxq2_f32(const pdf_grid *grid, int pid, const float *x, const float *q2, size_t n,
+              float *out, cudaStream_t stream);
+PDF_API int xfxq2_all_flavours_f32(const pdf_grid *grid, const float *x, const float *q2, size_t n,
+                           float *out, cudaStream_t stream);
+PDF_API int alphas_q2_f32(const pdf_grid *grid, const float *q2, size_t n, float *out,
+                  cudaStream_t stream);
+
+/* One Monte Carlo event batch in a single launch (PDFFlow Sec. 4.1: the PDF
+ * load of a hadronic integrand): for event e, Q^2 = x1[e] x2[e] s, and
+ * out[e] = [ xf(x1, Q^2) for all flavours | xf(x2, Q^2) for all flavours |
+ * alpha_s(Q^2) ], i.e. out is [n][2 nflav + 1].  The grid needs alpha_s. */
+PDF_API int pdf_mc_event(const pdf_grid *grid, const double *x1, const double *x2, double s, size_t n,
+                 double *out, cudaStream_t stream);
+PDF_API int pdf_mc_event_f32(const pdf_grid *grid, const float *x1, const float *x2, float s, size_t n,
+                     float *out, cudaStream_t stream);
+
+/* Host-memory variant of xfxq2_all_flavours (end-to-end use: host inputs,
+ * host outputs): out is [n][nflav]; if alphas_out is not NULL it receives
+ * alpha_s(q2) [n] as well (the grid then needs alpha_s nodes).  Synchronous;
+ * see the conventions above. */
+PDF_API int xfxq2_all_flavours_host(const pdf_grid *grid, const double *x, const double *q2, size_t n,
+                                    double *out, double *alphas_out);
+
+/* Invalid-point counter: read (synchronous) and reset. */
+PDF_API int pdf_grid_invalid_count(const pdf_grid *grid, unsigned long long *count);
+PDF_API int pdf_grid_reset_invalid_count(pdf_grid *grid);
+
+/* Description of the last error on the calling thread ("" if none). */
+PDF_API const char *pdf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PDF_GB300_H */

@@ -1,0 +1,29 @@
+/*
+ * pdf_gb300_probe.h -- measurement helpers of the GB300 PDF library.
+ *
+ * Not part of the evaluation path (the paper has no counterpart): they
+ * measure the arithmetic ceilings that bound the evaluation kernels, so the
+ * benchmark can state its roofline fractions against numbers taken on the
+ * same GPU, next to the ceilings derived from unit counts and clocks.
+ */
+#ifndef PDF_GB300_PROBE_H
+#define PDF_GB300_PROBE_H
+
+#include "pdf_gb300.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Sustained fused-multiply-add rate of the current device: every thread of a
+ * grid of (SMs x 8) blocks of 256 threads runs 8 independent FMA chains of
+ * `iters` steps in registers.  precision: 64 (DFMA) or 32 (FFMA).
+ * *flops_per_s receives 2 x FMAs / elapsed seconds (CUDA events).
+ * Synchronous; returns PDF_OK or a PDF_ERR_* code. */
+PDF_API int pdf_probe_fma_rate(int precision, int iters, double *flops_per_s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PDF_GB300_PROBE_H */

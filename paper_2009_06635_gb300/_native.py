@@ -1,0 +1,104 @@
+"""ctypes binding of libpdfgb300.so (the C ABI declared in include/pdf_gb300.h).
+
+Argument marshalling only: every evaluation runs in the library's CUDA
+kernels.  There is no CPU fallback -- if the library cannot be loaded or a
+call fails, a PdfError is raised.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+from pathlib import Path
+
+_PKG = Path(__file__).resolve().parent
+LIB_PATH = _PKG / "_lib" / "libpdfgb300.so"
+HEADERS = sorted((_PKG.parent / "include").glob("*.h"))
+
+PDF_OK = 0
+ERRORS = {
+    -1: "PDF_ERR_NULL", -2: "PDF_ERR_GRID", -3: "PDF_ERR_PID", -4: "PDF_ERR_CUDA",
+    -5: "PDF_ERR_ALLOC", -6: "PDF_ERR_ARG", -7: "PDF_ERR_NO_ALPHAS",
+}
+
+
+class PdfError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("x_knots", ctypes.c_void_p),
+        ("nsub", ctypes.c_int), ("nq", ctypes.c_void_p),
+        ("q2_knots", ctypes.c_void_p),
+        ("nflav", ctypes.c_int), ("pids", ctypes.c_void_p),
+        ("values", ctypes.c_void_p),
+        ("na", ctypes.c_int), ("as_q2", ctypes.c_void_p), ("as_vals", ctypes.c_void_p),
+    ]
+
+
+_lib = None
+_lock = threading.Lock()
+
+P, SZ, I32, F64, F32 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_double, ctypes.c_float
+SIGNATURES = {
+    "pdf_load_grid": (I32, [ctypes.POINTER(GridDesc), ctypes.POINTER(P)]),
+    "pdf_free_grid": (I32, [P]),
+    "pdf_grid_nflav": (I32, [P]),
+    "pdf_grid_pid_column": (I32, [P, I32]),
+    "xfxq2": (I32, [P, I32, P, P, SZ, P, P]),
+    "xfxq2_all_flavours": (I32, [P, P, P, SZ, P, P]),
+    "alphas_q2": (I32, [P, P, SZ, P, P]),
+    "xfxq2_f32": (I32, [P, I32, P, P, SZ, P, P]),
+    "xfxq2_all_flavours_f32": (I32, [P, P, P, SZ, P, P]),
+    "alphas_q2_f32": (I32, [P, P, SZ, P, P]),
+    "pdf_mc_event": (I32, [P, P, P, F64, SZ, P, P]),
+    "pdf_mc_event_f32": (I32, [P, P, P, F32, SZ, P, P]),
+    "xfxq2_all_flavours_host": (I32, [P, P, P, SZ, P, P]),
+    "pdf_grid_invalid_count": (I32, [P, ctypes.POINTER(ctypes.c_ulonglong)]),
+    "pdf_grid_reset_invalid_count": (I32, [P]),
+    "pdf_last_error": (ctypes.c_char_p, []),
+    "pdf_probe_fma_rate": (I32, [I32, I32, ctypes.POINTER(ctypes.c_double)]),
+}
+
+
+def header_functions() -> list[str]:
+    """Names of the functions the headers under include/ declare."""
+    names = []
+    for h in HEADERS:
+        names += re.findall(r"^PDF_API\s+(?:const\s+char\s*\*|int)\s*([A-Za-z_0-9]+)\s*\(", h.read_text(),
+                            flags=re.M)
+    return names
+
+
+def load(build_if_missing: bool = True):
+    """Load the library (building it with nvcc first if it is absent)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not LIB_PATH.exists():
+            if not build_if_missing:
+                raise PdfError(-4, f"CUDA library not built: {LIB_PATH}")
+            from . import build as _build
+
+            _build.build()
+        lib = ctypes.CDLL(str(LIB_PATH), mode=os.RTLD_LOCAL if hasattr(os, "RTLD_LOCAL") else 0)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def last_error() -> str:
+    return load().pdf_last_error().decode()
+
+
+def check(rc: int, what: str):
+    if rc != PDF_OK:
+        raise PdfError(rc, f"{what}: {last_error()}")

@@ -1,0 +1,470 @@
+// grid.cu -- pdf_load_grid: validation, device layout and staging kernels.
+//
+// Staging (PDFFlow Sec. 2.2, the LHAPDF data loaded once into device
+// memory) precomputes everything that depends only on the grid:
+//   - ln of every knot (device log, so a query on a knot gets t = 0 exactly);
+//   - per cell, the tangent-augmented Hermite weights w_a(t) as cubics: the
+//     knot tangent is the mean of the two adjacent secant slopes, one-sided
+//     at the x edges and at the ends of each Q subgrid (Sec. 2.2's special
+//     care at edges and thresholds), times the cell width;
+//   - per cell and flavour, the bicubic patch sum_ab w_a(t) w_b(u) f_ab in
+//     monomial form (16 coefficients), in FP64 and rounded to FP32;
+//   - per alpha_s cell the cubic in u (Sec. 2.3), same tangents per subgrid;
+//   - a degenerate cell on the last x knot and on the top Q knot (t = 0
+//     there; its patch carries only that knot's column or row), so the last
+//     knots are reproduced exactly;
+//   - fixed sites used by the continuation (1.01 Q2min, the top knots) and
+//     float thresholds for the exact FP32 search.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "pdf_internal.cuh"
+
+namespace pdfgb {
+
+static thread_local char g_errbuf[512];
+
+int set_error(int code, const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_errbuf, sizeof g_errbuf, fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int check_launch(const char *what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(PDF_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+  return PDF_OK;
+}
+
+// Hermite basis in monomial form, coefficients of t^0..t^3.
+__device__ __constant__ double kH00[4] = {1.0, 0.0, -3.0, 2.0};
+__device__ __constant__ double kH01[4] = {0.0, 0.0, 3.0, -2.0};
+__device__ __constant__ double kH10[4] = {0.0, 1.0, -2.0, 1.0};
+__device__ __constant__ double kH11[4] = {0.0, 0.0, -1.0, 1.0};
+
+// Knot weights of one cell: tangent at the left knot = aL * right secant +
+// bL * left secant, at the right knot = dR * cell secant + gR * next secant
+// (secants as differences of values over differences of logs); the tangent
+// multiplies the cell width d, so the left-secant term carries d/d_prev and
+// the next-secant term d/d_next.
+__device__ void cell_weights(double aL, double bm, double dR, double gp, double *W) {
+  for (int k = 0; k < 4; k++) {
+    W[0 * 4 + k] = -bm * kH10[k];
+    W[1 * 4 + k] = kH00[k] - (aL - bm) * kH10[k] - dR * kH11[k];
+    W[2 * 4 + k] = kH01[k] + aL * kH10[k] + (dR - gp) * kH11[k];
+    W[3 * 4 + k] = gp * kH11[k];
+  }
+}
+
+struct Stage {
+  // inputs (device copies)
+  const double *xk, *q2k, *vals, *aq2, *aval;
+  const int *first, *nq;
+  int nx, nrows, nf, na, nsub, nxc, nqc;
+  // outputs
+  double *lx, *lq, *alq;
+  double *xcell, *qcell, *xW, *qW, *coef, *acell;
+  float *coef32, *xthr32, *q2thr32, *aq2thr32, *xcell32, *qcell32, *acell32;
+  int *row_qc, *qc_row;
+  double *scal;  // scalar outputs, see k_scalars
+};
+
+__global__ void k_logs(Stage S) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < S.nx) { S.lx[i] = log(S.xk[i]); S.xthr32[i] = __double2float_ru(S.xk[i]); }
+  if (i < S.nrows) { S.lq[i] = log(S.q2k[i]); S.q2thr32[i] = __double2float_ru(S.q2k[i]); }
+  if (i < S.na) { S.alq[i] = log(S.aq2[i]); S.aq2thr32[i] = __double2float_ru(S.aq2[i]); }
+}
+
+// Degenerate cell on a last knot: all weight on the knot itself (a = 1).
+__device__ void knot_weights(double *W) {
+  for (int m = 0; m < 16; m++) W[m] = 0.0;
+  W[1 * 4 + 0] = 1.0;
+}
+
+__global__ void k_xcells(Stage S) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= S.nx) return;
+  if (i == S.nx - 1) {
+    S.xcell[2 * i] = S.lx[i];
+    S.xcell[2 * i + 1] = 0.0;
+    S.xcell32[2 * i] = (float)(1.0 / S.xk[i]);
+    S.xcell32[2 * i + 1] = 0.f;
+    knot_weights(S.xW + 16 * i);
+    return;
+  }
+  double d = S.lx[i + 1] - S.lx[i];
+  S.xcell[2 * i] = S.lx[i];
+  S.xcell[2 * i + 1] = 1.0 / d;
+  S.xcell32[2 * i] = (float)(1.0 / S.xk[i]);
+  S.xcell32[2 * i + 1] = (float)(1.0 / d);
+  double aL = 1.0, bm = 0.0, dR = 1.0, gp = 0.0;
+  if (i > 0) { aL = 0.5; bm = 0.5 * d / (S.lx[i] - S.lx[i - 1]); }
+  if (i + 1 < S.nx - 1) { dR = 0.5; gp = 0.5 * d / (S.lx[i + 2] - S.lx[i + 1]); }
+  cell_weights(aL, bm, dR, gp, S.xW + 16 * i);
+}
+
+__global__ void k_qcells(Stage S) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= S.nrows) return;
+  int s = 0, qc0 = 0;
+  while (s + 1 < S.nsub && j >= S.first[s + 1]) { qc0 += S.nq[s] - 1; s++; }
+  int j0 = S.first[s], j1 = S.first[s] + S.nq[s] - 1;
+  if (j == S.nrows - 1) {  // top knot: degenerate cell nqc
+    S.row_qc[j] = S.nqc;
+    S.qc_row[S.nqc] = j;
+    S.qcell[2 * j] = S.lq[j];
+    S.qcell[2 * j + 1] = 0.0;
+    S.qcell32[2 * j] = (float)(1.0 / S.q2k[j]);
+    S.qcell32[2 * j + 1] = 0.f;
+    knot_weights(S.qW + 16 * S.nqc);
+    return;
+  }
+  if (j >= j1) { S.row_qc[j] = -1; return; }  // last row of a lower subgrid starts no cell
+  int qc = qc0 + (j - j0);
+  S.row_qc[j] = qc;
+  S.qc_row[qc] = j;
+  double d = S.lq[j + 1] - S.lq[j];
+  S.qcell[2 * j] = S.lq[j];
+  S.qcell[2 * j + 1] = 1.0 / d;
+  S.qcell32[2 * j] = (float)(1.0 / S.q2k[j]);
+  S.qcell32[2 * j + 1] = (float)(1.0 / d);
+  double aL = 1.0, bm = 0.0, dR = 1.0, gp = 0.0;
+  if (j > j0) { aL = 0.5; bm = 0.5 * d / (S.lq[j] - S.lq[j - 1]); }
+  if (j + 1 < j1) { dR = 0.5; gp = 0.5 * d / (S.lq[j + 2] - S.lq[j + 1]); }
+  cell_weights(aL, bm, dR, gp, S.qW + 16 * qc);
+}
+
+// One thread per (q cell, x cell, flavour) slot, degenerate ones included:
+// expand sum_ab w_a(t) w_b(u) f_ab into monomials.
+__global__ void k_coef(Stage S) {
+  long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long total = (long long)(S.nqc + 1) * S.nx * S.nf;
+  if (id >= total) return;
+  int f = (int)(id % S.nf);
+  long long cell = id / S.nf;
+  int xc = (int)(cell % S.nx), qc = (int)(cell / S.nx);
+  int j = S.qc_row[qc], i = xc;
+  const double *Wx = S.xW + 16 * xc, *Wq = S.qW + 16 * qc;
+  double c[16];
+  for (int m = 0; m < 16; m++) c[m] = 0.0;
+  for (int b = 0; b < 4; b++) {
+    int row = j - 1 + b;
+    if (row < 0 || row >= S.nrows) continue;
+    for (int a = 0; a < 4; a++) {
+      int col = i - 1 + a;
+      if (col < 0 || col >= S.nx) continue;
+      double fv = S.vals[((size_t)row * S.nx + col) * S.nf + f];
+      for (int l = 0; l < 4; l++) {
+        double wl = Wq[b * 4 + l] * fv;
+        for (int k = 0; k < 4; k++) c[l * 4 + k] = fma(Wx[a * 4 + k], wl, c[l * 4 + k]);
+      }
+    }
+  }
+  double *o = S.coef + (size_t)id * 16;
+  float *o32 = S.coef32 + (size_t)id * 16;
+  for (int m = 0; m < 16; m++) { o[m] = c[m]; o32[m] = (float)c[m]; }
+}
+
+// alpha_s cells: one thread per node; the last node gets a degenerate cell.
+__global__ void k_acells(Stage S) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= S.na) return;
+  double *o = S.acell + 6 * k;
+  float *o32 = S.acell32 + 6 * k;
+  if (k == S.na - 1) {
+    o[0] = S.alq[k]; o[1] = 0.0; o[2] = S.aval[k]; o[3] = o[4] = o[5] = 0.0;
+    o32[0] = (float)(1.0 / S.aq2[k]); o32[1] = 0.f; o32[2] = (float)S.aval[k];
+    o32[3] = o32[4] = o32[5] = 0.f;
+    return;
+  }
+  if (!(S.aq2[k] < S.aq2[k + 1])) {  // zero-width pair at a threshold: not a cell
+    for (int m = 0; m < 6; m++) { o[m] = 0.0; o32[m] = 0.f; }
+    return;
+  }
+  const double *l = S.alq, *f = S.aval;
+  double d = l[k + 1] - l[k];
+  bool left_edge = (k == 0) || (S.aq2[k] == S.aq2[k - 1]);
+  bool right_edge = (k + 1 == S.na - 1) || (S.aq2[k + 2] == S.aq2[k + 1]);
+  double sec = (f[k + 1] - f[k]) / d;
+  double s0 = left_edge ? sec : 0.5 * (sec + (f[k] - f[k - 1]) / (l[k] - l[k - 1]));
+  double s1 = right_edge ? sec : 0.5 * (sec + (f[k + 2] - f[k + 1]) / (l[k + 2] - l[k + 1]));
+  double m0 = d * s0, m1 = d * s1;
+  o[0] = l[k];
+  o[1] = 1.0 / d;
+  o[2] = f[k];
+  o[3] = m0;
+  o[4] = -3.0 * f[k] + 3.0 * f[k + 1] - 2.0 * m0 - m1;
+  o[5] = 2.0 * f[k] - 2.0 * f[k + 1] + m0 + m1;
+  o32[0] = (float)(1.0 / S.aq2[k]);
+  o32[1] = (float)(1.0 / d);
+  for (int m = 2; m < 6; m++) o32[m] = (float)o[m];
+}
+
+// Scalars (single thread).  scal layout:
+//  2 top_qc  3 q101_qc  4 q101_u  5 lx0  6 idx0  7 lq2max  8 idq_top  9 ln101
+__global__ void k_scalars(Stage S) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double *o = S.scal;
+  int top = S.nrows - 2;
+  o[2] = (double)S.row_qc[top];
+  double v = 1.01 * S.q2k[0];
+  int j = 0;  // same rule as the query search: the last row with Q^2_j <= v
+  while (j + 1 < S.nrows && S.q2k[j + 1] <= v) j++;
+  o[3] = (double)S.row_qc[j];
+  o[4] = (log(v) - S.qcell[2 * j]) * S.qcell[2 * j + 1];
+  o[5] = S.xcell[0];
+  o[6] = S.xcell[1];
+  o[7] = S.lq[S.nrows - 1];
+  o[8] = S.qcell[2 * top + 1];
+  o[9] = log(1.01);
+}
+
+static int pow2_floor(int n) {
+  int p = 1;
+  while (p * 2 <= n) p *= 2;
+  return n >= 1 ? p : 0;
+}
+
+static int validate(const pdf_grid_desc *d, int *nrows_out) {
+  if (!d) return set_error(PDF_ERR_NULL, "pdf_load_grid: descriptor is NULL");
+  if (!d->x_knots || !d->nq || !d->q2_knots || !d->pids || !d->values)
+    return set_error(PDF_ERR_NULL, "pdf_load_grid: a descriptor array is NULL");
+  if (d->nx < 2 || d->nx > PDF_MAX_NX)
+    return set_error(PDF_ERR_GRID, "pdf_load_grid: nx = %d outside [2, %d]", d->nx, PDF_MAX_NX);
+  if (d->nflav < 1 || d->nflav > PDF_MAX_NFLAV)
+    return set_error(PDF_ERR_GRID, "pdf_load_grid: nflav = %d outside [1, %d]", d->nflav, PDF_MAX_NFLAV);
+  if (d->nsub < 1) return set_error(PDF_ERR_GRID, "pdf_load_grid: nsub = %d < 1", d->nsub);
+  for (int i = 0; i < d->nx; i++) {
+    double x = d->x_knots[i];
+    if (!(x > 0.0) || !(x <= 1.0))
+      return set_error(PDF_ERR_GRID, "pdf_load_grid: x knot %d = %g outside (0, 1]", i, x);
+    if (i > 0 && !(x > d->x_knots[i - 1]))
+      return set_error(PDF_ERR_GRID, "pdf_load_grid: x knots not strictly increasing at %d", i);
+  }
+  long rows = 0;
+  for (int s = 0; s < d->nsub; s++) {
+    if (d->nq[s] < 2) return set_error(PDF_ERR_GRID, "pdf_load_grid: subgrid %d has %d < 2 knots", s, d->nq[s]);
+    rows += d->nq[s];
+    if (rows > PDF_MAX_ROWS) return set_error(PDF_ERR_GRID, "pdf_load_grid: more than %d Q rows", PDF_MAX_ROWS);
+  }
+  int r0 = 0;
+  for (int s = 0; s < d->nsub; s++) {
+    for (int j = r0; j < r0 + d->nq[s]; j++) {
+      double q = d->q2_knots[j];
+      if (!(q > 0.0) || !std::isfinite(q))
+        return set_error(PDF_ERR_GRID, "pdf_load_grid: Q2 knot %d = %g not positive and finite", j, q);
+      if (j > r0 && !(q > d->q2_knots[j - 1]))
+        return set_error(PDF_ERR_GRID, "pdf_load_grid: Q2 knots of subgrid %d not strictly increasing", s);
+    }
+    if (s > 0 && d->q2_knots[r0] != d->q2_knots[r0 - 1])
+      return set_error(PDF_ERR_GRID, "pdf_load_grid: subgrid %d does not start at the previous one's last knot", s);
+    r0 += d->nq[s];
+  }
+  if (!(d->q2_knots[rows - 1] >= 1.01 * d->q2_knots[0]))
+    return set_error(PDF_ERR_GRID, "pdf_load_grid: Q2 range narrower than a factor 1.01");
+  size_t nv = (size_t)rows * d->nx * d->nflav;
+  for (size_t k = 0; k < nv; k++)
+    if (!std::isfinite(d->values[k])) return set_error(PDF_ERR_GRID, "pdf_load_grid: value %zu not finite", k);
+  for (int f = 0; f < d->nflav; f++)
+    for (int g = 0; g < f; g++)
+      if (d->pids[f] == d->pids[g]) return set_error(PDF_ERR_GRID, "pdf_load_grid: pid %d repeated", d->pids[f]);
+  if (d->na < 0 || d->na == 1 || d->na > PDF_MAX_NALPHAS)
+    return set_error(PDF_ERR_GRID, "pdf_load_grid: na = %d (0, or 2..%d)", d->na, PDF_MAX_NALPHAS);
+  if (d->na > 0) {
+    if (!d->as_q2 || !d->as_vals) return set_error(PDF_ERR_NULL, "pdf_load_grid: alpha_s arrays NULL");
+    int run = 1;
+    for (int k = 0; k < d->na; k++) {
+      if (!(d->as_q2[k] > 0.0) || !std::isfinite(d->as_q2[k]) || !std::isfinite(d->as_vals[k]))
+        return set_error(PDF_ERR_GRID, "pdf_load_grid: alpha_s node %d invalid", k);
+      if (k > 0) {
+        if (d->as_q2[k] < d->as_q2[k - 1])
+          return set_error(PDF_ERR_GRID, "pdf_load_grid: alpha_s nodes decrease at %d", k);
+        if (d->as_q2[k] == d->as_q2[k - 1]) {
+          if (run < 2) return set_error(PDF_ERR_GRID, "pdf_load_grid: alpha_s subgrid with < 2 nodes");
+          run = 1;
+        } else {
+          run++;
+        }
+      }
+    }
+    if (run < 2) return set_error(PDF_ERR_GRID, "pdf_load_grid: alpha_s subgrid with < 2 nodes");
+  }
+  *nrows_out = (int)rows;
+  return PDF_OK;
+}
+
+// Bump allocator over one device allocation.
+struct Arena {
+  char *base = nullptr;
+  size_t off = 0, cap = 0;
+  template <typename T>
+  T *take(size_t count) {
+    size_t bytes = ((count * sizeof(T) + 255) / 256) * 256;
+    T *p = reinterpret_cast<T *>(base + off);
+    off += bytes;
+    return p;
+  }
+};
+
+}  // namespace pdfgb
+
+using namespace pdfgb;
+
+extern "C" const char *pdf_last_error(void) { return g_errbuf; }
+
+extern "C" int pdf_load_grid(const pdf_grid_desc *d, pdf_grid **out) {
+  g_errbuf[0] = 0;
+  if (!out) return set_error(PDF_ERR_NULL, "pdf_load_grid: out is NULL");
+  *out = nullptr;
+  int nrows = 0;
+  int rc = validate(d, &nrows);
+  if (rc) return rc;
+  const int nx = d->nx, nf = d->nflav, na = d->na, nsub = d->nsub;
+  const int nxc = nx - 1, nqc = nrows - nsub;
+
+  // sizes (a dry run of the arena)
+  auto layout = [&](Arena &A, Stage &S, unsigned long long **inv) {
+    S.xk = A.take<double>(nx); S.q2k = A.take<double>(nrows);
+    S.vals = A.take<double>((size_t)nrows * nx * nf);
+    S.aq2 = A.take<double>(na > 0 ? na : 1); S.aval = A.take<double>(na > 0 ? na : 1);
+    S.first = A.take<int>(nsub); S.nq = A.take<int>(nsub);
+    S.lx = A.take<double>(nx); S.lq = A.take<double>(nrows); S.alq = A.take<double>(na > 0 ? na : 1);
+    S.xcell = A.take<double>(2 * nx); S.qcell = A.take<double>(2 * nrows);
+    S.xW = A.take<double>(16 * nx); S.qW = A.take<double>(16 * (nqc + 1));
+    S.coef = A.take<double>((size_t)(nqc + 1) * nx * nf * 16);
+    S.coef32 = A.take<float>((size_t)(nqc + 1) * nx * nf * 16);
+    S.acell = A.take<double>(6 * (na > 0 ? na : 1));
+    S.acell32 = A.take<float>(6 * (na > 0 ? na : 1));
+    S.xthr32 = A.take<float>(nx); S.q2thr32 = A.take<float>(nrows); S.aq2thr32 = A.take<float>(na > 0 ? na : 1);
+    S.xcell32 = A.take<float>(2 * nx); S.qcell32 = A.take<float>(2 * nrows);
+    S.row_qc = A.take<int>(nrows); S.qc_row = A.take<int>(nqc + 1);
+    S.scal = A.take<double>(16);
+    *inv = A.take<unsigned long long>(1);
+  };
+  Arena dry;
+  Stage S{};
+  unsigned long long *inv = nullptr;
+  layout(dry, S, &inv);
+
+  pdf_grid *g = new (std::nothrow) pdf_grid();
+  if (!g) return set_error(PDF_ERR_ALLOC, "pdf_load_grid: host allocation failed");
+  cudaGetDevice(&g->device);
+  void *base = nullptr;
+  cudaError_t e = cudaMalloc(&base, dry.off);
+  if (e != cudaSuccess) {
+    delete g;
+    return set_error(PDF_ERR_ALLOC, "pdf_load_grid: cudaMalloc(%zu): %s", dry.off, cudaGetErrorString(e));
+  }
+  g->blocks[0] = base;
+  g->nblocks = 1;
+  Arena A;
+  A.base = static_cast<char *>(base);
+  A.cap = dry.off;
+  layout(A, S, &inv);
+  S.nx = nx; S.nrows = nrows; S.nf = nf; S.na = na; S.nsub = nsub; S.nxc = nxc; S.nqc = nqc;
+
+  int first[1024];
+  for (int s = 0, r = 0; s < nsub; s++) { first[s] = r; r += d->nq[s]; }
+  auto H2D = [&](const void *dst, const void *src, size_t bytes) {
+    if (e == cudaSuccess && bytes) e = cudaMemcpy(const_cast<void *>(dst), src, bytes, cudaMemcpyHostToDevice);
+  };
+  H2D(S.xk, d->x_knots, sizeof(double) * nx);
+  H2D(S.q2k, d->q2_knots, sizeof(double) * nrows);
+  H2D(S.vals, d->values, sizeof(double) * (size_t)nrows * nx * nf);
+  if (na > 0) { H2D(S.aq2, d->as_q2, sizeof(double) * na); H2D(S.aval, d->as_vals, sizeof(double) * na); }
+  H2D(S.first, first, sizeof(int) * nsub);
+  H2D(S.nq, d->nq, sizeof(int) * nsub);
+  if (e == cudaSuccess) e = cudaMemset(inv, 0, sizeof(unsigned long long));
+  if (e != cudaSuccess) {
+    pdf_free_grid(g);
+    return set_error(PDF_ERR_CUDA, "pdf_load_grid: copy to device: %s", cudaGetErrorString(e));
+  }
+
+  int nmax = nx > nrows ? nx : nrows;
+  if (na > nmax) nmax = na;
+  k_logs<<<(nmax + 127) / 128, 128>>>(S);
+  k_xcells<<<(nx + 127) / 128, 128>>>(S);
+  k_qcells<<<(nrows + 127) / 128, 128>>>(S);
+  long long ncoef = (long long)(nqc + 1) * nx * nf;
+  k_coef<<<(unsigned)((ncoef + 127) / 128), 128>>>(S);
+  if (na > 1) k_acells<<<(na + 127) / 128, 128>>>(S);
+  k_scalars<<<1, 32>>>(S);
+  if ((rc = check_launch("pdf_load_grid staging"))) { pdf_free_grid(g); return rc; }
+  double scal[16];
+  e = cudaMemcpy(scal, S.scal, sizeof scal, cudaMemcpyDeviceToHost);  // synchronises
+  if (e != cudaSuccess) {
+    pdf_free_grid(g);
+    return set_error(PDF_ERR_CUDA, "pdf_load_grid: staging: %s", cudaGetErrorString(e));
+  }
+
+  GridView &v = g->v;
+  v.nx = nx; v.nrows = nrows; v.nf = nf; v.nxc = nxc; v.nqc = nqc; v.na = na; v.nsub = nsub;
+  v.xstep = pow2_floor(nx - 1); v.qstep = pow2_floor(nrows - 1); v.astep = na > 1 ? pow2_floor(na - 1) : 0;
+  v.xk = S.xk; v.q2k = S.q2k; v.xcell = S.xcell; v.qcell = S.qcell; v.row_qc = S.row_qc;
+  v.coef = S.coef; v.coef32 = S.coef32; v.xW = S.xW; v.qW = S.qW;
+  v.xthr32 = S.xthr32; v.q2thr32 = S.q2thr32; v.xcell32 = S.xcell32; v.qcell32 = S.qcell32;
+  v.aq2 = S.aq2; v.acell = S.acell; v.acell32 = S.acell32; v.aq2thr32 = S.aq2thr32;
+  v.as_lo = na > 0 ? d->as_vals[0] : NAN;
+  v.as_hi = na > 0 ? d->as_vals[na - 1] : NAN;
+  v.x0 = d->x_knots[0]; v.xlast = d->x_knots[nx - 1];
+  v.q2min = d->q2_knots[0]; v.q2max = d->q2_knots[nrows - 1];
+  v.aq2lo = na > 0 ? d->as_q2[0] : NAN; v.aq2hi = na > 0 ? d->as_q2[na - 1] : NAN;
+  // float thresholds: x < x0 <=> x < round_up(x0) for a float x, etc.
+  auto ru = [](double a) { float f = (float)a; if ((double)f < a) f = nextafterf(f, INFINITY); return f; };
+  auto rd = [](double a) { float f = (float)a; if ((double)f > a) f = nextafterf(f, -INFINITY); return f; };
+  v.x0_ru = ru(v.x0); v.xlast_rd = rd(v.xlast); v.q2min_ru = ru(v.q2min); v.q2max_rd = rd(v.q2max);
+  v.aq2lo_ru = na > 0 ? ru(v.aq2lo) : NAN; v.aq2hi_rd = na > 0 ? rd(v.aq2hi) : NAN;
+  v.as_lo32 = (float)v.as_lo; v.as_hi32 = (float)v.as_hi;
+  v.top_qc = (int)scal[2]; v.q101_qc = (int)scal[3]; v.q101_u = scal[4];
+  v.lx0 = scal[5]; v.idx0 = scal[6]; v.lq2max = scal[7]; v.idq_top = scal[8]; v.ln101 = scal[9];
+  v.inv_q2min = 1.0 / v.q2min;
+  v.x0inv32 = (float)(1.0 / v.x0); v.idx0_32 = (float)v.idx0;
+  v.q2maxinv32 = (float)(1.0 / v.q2max); v.idq_top32 = (float)v.idq_top;
+  v.q2min32 = (float)v.q2min; v.ln101_32 = (float)v.ln101;
+  v.q101_u32 = (float)v.q101_u;
+  v.invalid = inv;
+  for (int f = 0; f < nf; f++) g->pids[f] = d->pids[f];
+  *out = g;
+  return PDF_OK;
+}
+
+extern "C" int pdf_free_grid(pdf_grid *g) {
+  if (!g) return PDF_OK;
+  for (int k = 0; k < 2; k++) {
+    if (g->io_stream[k]) { cudaStreamSynchronize(g->io_stream[k]); cudaStreamDestroy(g->io_stream[k]); }
+    if (g->io_buf[k]) cudaFree(g->io_buf[k]);
+  }
+  for (int b = 0; b < g->nblocks; b++) cudaFree(g->blocks[b]);
+  delete g;
+  return PDF_OK;
+}
+
+extern "C" int pdf_grid_nflav(const pdf_grid *g) { return g ? g->v.nf : set_error(PDF_ERR_NULL, "grid is NULL"); }
+
+extern "C" int pdf_grid_pid_column(const pdf_grid *g, int pid) {
+  if (!g) return set_error(PDF_ERR_NULL, "grid is NULL");
+  if (pid == 0) pid = 21;
+  for (int f = 0; f < g->v.nf; f++)
+    if (g->pids[f] == pid) return f;
+  return -1;
+}
+
+extern "C" int pdf_grid_invalid_count(const pdf_grid *g, unsigned long long *count) {
+  if (!g || !count) return set_error(PDF_ERR_NULL, "pdf_grid_invalid_count: NULL argument");
+  cudaError_t e = cudaMemcpy(count, g->v.invalid, sizeof *count, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return set_error(PDF_ERR_CUDA, "pdf_grid_invalid_count: %s", cudaGetErrorString(e));
+  return PDF_OK;
+}
+
+extern "C" int pdf_grid_reset_invalid_count(pdf_grid *g) {
+  if (!g) return set_error(PDF_ERR_NULL, "pdf_grid_reset_invalid_count: grid is NULL");
+  cudaError_t e = cudaMemset(g->v.invalid, 0, sizeof(unsigned long long));
+  if (e != cudaSuccess) return set_error(PDF_ERR_CUDA, "pdf_grid_reset_invalid_count: %s", cudaGetErrorString(e));
+  return PDF_OK;
+}

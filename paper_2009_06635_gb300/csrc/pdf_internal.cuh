@@ -1,0 +1,196 @@
+// pdf_internal.cuh -- device-side layout of a staged grid and the helpers
+// shared by the evaluation kernels.
+//
+// Layout in HBM (all staged once by pdf_load_grid, PDFFlow Sec. 2.2):
+//   coef   [nqc+1][nx][nflav][16]  bicubic patch of every cell and flavour in
+//          monomial form, c[l*4 + k] multiplies t^k u^l, t and u the
+//          positions inside the cell in ln x and ln Q^2.  One evaluation
+//          reads one contiguous, 128-byte aligned block (FP64) or 64 bytes
+//          (FP32), instead of gathering 16 knots and forming weights.
+//   xk/q2k raw knots, searched as integer bit patterns (positive doubles
+//          order like their bits), so a cell choice never depends on a log.
+//   xcell  per x cell {ln x_i, 1/(ln x_{i+1} - ln x_i)}; qcell likewise per
+//          cell-start row; row_qc maps a cell-start row to its Q-cell index.
+//          One extra, degenerate cell sits on the last x knot and one on the
+//          top Q knot ({ln knot, 0}: t = 0 there, and its patch holds only
+//          that knot's column or row), so a query exactly on the last knot
+//          returns the tabulated value exactly, like every other knot.
+//   xW/qW  per cell, the 4 knot weights of the tangent-augmented Hermite
+//          segment as cubics in t (u): w_a(t) = sum_k W[a][k] t^k.  The patch
+//          of a cell is sum_ab w_a(t) w_b(u) f_ab; coef is that sum expanded.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "pdf_gb300.h"
+
+namespace pdfgb {
+
+// Class of a query point (decides which sites are evaluated and how the
+// continuation combines them).
+enum : int {
+  C_IN = 0,          // inside the grid
+  C_LOWX = 1,        // x < x0, Q^2 inside
+  C_HIGHQ = 2,       // x inside, Q^2 > Q2max
+  C_LOWQ = 3,        // x inside, Q^2 < Q2min
+  C_LOWX_HIGHQ = 4,  // both
+  C_LOWX_LOWQ = 5,
+  C_INVALID = 6,
+  NCLASS = 7
+};
+
+// A place where the in-grid interpolant is evaluated: patch cell + position.
+template <typename T>
+struct Site {
+  int xc, qc;
+  T t, u;
+};
+
+struct GridView {
+  int nx, nrows, nf, nxc, nqc, na, nsub;  // nxc, nqc: proper cells; slots are nx, nqc + 1
+  int xstep, qstep, astep;  // largest power of two <= n-1 (binary search start)
+
+  const double *xk, *q2k;     // raw knots (bit patterns searched)
+  const double *xcell;        // [nx][2]
+  const double *qcell;        // [nrows][2] (cell-start rows and the top row)
+  const int *row_qc;          // [nrows]
+  const double *coef;         // [nqc + 1][nx][nf][16]
+  const float *coef32;
+  const double *xW, *qW;      // [nx][16], [nqc + 1][16]
+  const float *xthr32, *q2thr32;   // smallest float >= knot
+  const float *xcell32, *qcell32;  // {1/knot, 1/dln}
+
+  // alpha_s
+  const double *aq2;          // [na]
+  const double *acell;        // [na][6] {lq_j, 1/dlq, a0, a1, a2, a3}
+  const float *acell32;       // [na][6] {1/Q^2_j, 1/dlq, a0, a1, a2, a3}
+  const float *aq2thr32;
+  double as_lo, as_hi, aq2lo, aq2hi;
+  float as_lo32, as_hi32;
+
+  // classification (FP64) and float thresholds (FP32)
+  double x0, xlast, q2min, q2max;
+  float x0_ru, xlast_rd, q2min_ru, q2max_rd, aq2lo_ru, aq2hi_rd;
+  // continuation parameters
+  double lx0, idx0;           // p_x = (ln x - lx0) * idx0
+  double lq2max, idq_top;     // p_q = -(ln Q^2 - lq2max) * idq_top
+  double inv_q2min, ln101;    // ln 1.01
+  float x0inv32, idx0_32, q2maxinv32, idq_top32, q2min32, ln101_32;
+  // fixed sites: the second x knot is (cell 1, t = 0), Q2max is the
+  // degenerate top cell at u = 0, the knot below it (top_qc, u = 0), and
+  // 1.01 Q2min is (q101_qc, q101_u)
+  int q101_qc, top_qc;
+  double q101_u;
+  float q101_u32;
+
+  unsigned long long *invalid;
+};
+
+// ---------------------------------------------------------------------------
+// search: largest index j in [0, n-1] with key_j <= key, given key_0 <= key
+// (fixed-step binary search, no data-dependent trip count).  Keys are the bit
+// patterns of positive floating-point numbers (monotone in the value).  With
+// a repeated knot (a threshold) the later copy wins, which puts a query on
+// the threshold into the upper subgrid; j = n-1 only for a query exactly on
+// the last knot (its degenerate cell).
+// ---------------------------------------------------------------------------
+template <typename K>
+__device__ __forceinline__ int search_cell(const K *keys, int n, int step, K key) {
+  int lo = 0;
+  for (int s = step; s > 0; s >>= 1) {
+    int c = lo + s;
+    if (c < n && keys[c] <= key) lo = c;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------
+// patch evaluation: P_l(t) = sum_k c[l][k] t^k, F = sum_l P_l(t) u^l (Horner)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double patch(const double *c, double t, double u) {
+  const double2 *p = reinterpret_cast<const double2 *>(c);
+  double2 a0 = __ldg(p + 0), b0 = __ldg(p + 1), a1 = __ldg(p + 2), b1 = __ldg(p + 3);
+  double2 a2 = __ldg(p + 4), b2 = __ldg(p + 5), a3 = __ldg(p + 6), b3 = __ldg(p + 7);
+  double P0 = fma(fma(fma(b0.y, t, b0.x), t, a0.y), t, a0.x);
+  double P1 = fma(fma(fma(b1.y, t, b1.x), t, a1.y), t, a1.x);
+  double P2 = fma(fma(fma(b2.y, t, b2.x), t, a2.y), t, a2.x);
+  double P3 = fma(fma(fma(b3.y, t, b3.x), t, a3.y), t, a3.x);
+  return fma(fma(fma(P3, u, P2), u, P1), u, P0);
+}
+
+__device__ __forceinline__ float patch(const float *c, float t, float u) {
+  const float4 *p = reinterpret_cast<const float4 *>(c);
+  float4 q0 = __ldg(p + 0), q1 = __ldg(p + 1), q2 = __ldg(p + 2), q3 = __ldg(p + 3);
+  float P0 = fmaf(fmaf(fmaf(q0.w, t, q0.z), t, q0.y), t, q0.x);
+  float P1 = fmaf(fmaf(fmaf(q1.w, t, q1.z), t, q1.y), t, q1.x);
+  float P2 = fmaf(fmaf(fmaf(q2.w, t, q2.z), t, q2.y), t, q2.x);
+  float P3 = fmaf(fmaf(fmaf(q3.w, t, q3.z), t, q3.y), t, q3.x);
+  return fmaf(fmaf(fmaf(P3, u, P2), u, P1), u, P0);
+}
+
+// ---------------------------------------------------------------------------
+// continuation rules (the EXTRAPOLATE box of PDFFlow Fig. 1)
+// ---------------------------------------------------------------------------
+// From g0 at one knot (p = 0) and g1 at the next one inwards (p = 1):
+// log-linear if both are positive, linear otherwise.
+__device__ __forceinline__ double pair_rule(double g0, double g1, double p) {
+  if (g0 > 0.0 && g1 > 0.0) return g0 * exp(p * log(g1 / g0));
+  return g0 + (g1 - g0) * p;
+}
+__device__ __forceinline__ float pair_rule(float g0, float g1, float p) {
+  if (g0 > 0.f && g1 > 0.f) return g0 * expf(p * logf(g1 / g0));
+  return fmaf(g1 - g0, p, g0);
+}
+
+// Low Q^2: f0 = F(Q2min), f1 = F(1.01 Q2min); rho = Q^2/Q2min, lr = ln rho.
+__device__ __forceinline__ double lowq_rule(double f0, double f1, double rho, double lr,
+                                            double ln101) {
+  double gam = (f0 > 0.0 && f1 > 0.0) ? log(f1 / f0) / ln101 : 1.0;
+  double ex = (gam * rho + 1.0) - rho;
+  return f0 * exp(ex * lr);
+}
+__device__ __forceinline__ float lowq_rule(float f0, float f1, float rho, float lr, float ln101) {
+  float gam = (f0 > 0.f && f1 > 0.f) ? logf(f1 / f0) / ln101 : 1.f;
+  float ex = (gam * rho + 1.f) - rho;
+  return f0 * expf(ex * lr);
+}
+
+// Combine the site values of one point and flavour according to its class.
+// F(a, b) is the patch at x-site a (0/1) and q-site b (0/1).
+template <typename T, typename FN>
+__device__ __forceinline__ T combine(int cls, T px, T pq, T lr, T ln101, FN F) {
+  switch (cls) {
+    case C_IN: return F(0, 0);
+    case C_LOWX: return pair_rule(F(0, 0), F(1, 0), px);
+    case C_HIGHQ: return pair_rule(F(0, 0), F(0, 1), pq);
+    case C_LOWQ: return lowq_rule(F(0, 0), F(0, 1), pq, lr, ln101);
+    case C_LOWX_HIGHQ:
+      return pair_rule(pair_rule(F(0, 0), F(0, 1), pq), pair_rule(F(1, 0), F(1, 1), pq), px);
+    case C_LOWX_LOWQ:
+      return pair_rule(lowq_rule(F(0, 0), F(0, 1), pq, lr, ln101),
+                       lowq_rule(F(1, 0), F(1, 1), pq, lr, ln101), px);
+    default: return T(NAN);
+  }
+}
+
+// Host-side helpers shared by the translation units.
+int set_error(int code, const char *fmt, ...);
+int check_launch(const char *what);
+
+}  // namespace pdfgb
+
+// The opaque handle.
+struct pdf_grid {
+  pdfgb::GridView v;
+  int device;
+  int pids[PDF_MAX_NFLAV];
+  // device allocations owned by the handle
+  void *blocks[32];
+  int nblocks;
+  // host-I/O pipeline (lazily created)
+  cudaStream_t io_stream[2];
+  cudaEvent_t io_event[2];
+  void *io_buf[2];
+  size_t io_cap;  // points per buffer
+};

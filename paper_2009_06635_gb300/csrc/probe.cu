@@ -1,0 +1,55 @@
+// probe.cu -- FMA-rate microbenchmark (the ALU ceiling of the FP64 and FP32
+// evaluation kernels).  8 independent chains per thread hide the FMA latency.
+#include "pdf_gb300_probe.h"
+#include "pdf_internal.cuh"
+
+namespace pdfgb {
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma(T a, T b, int iters, T *sink) {
+  T c0 = (T)threadIdx.x, c1 = c0 + T(1), c2 = c0 + T(2), c3 = c0 + T(3);
+  T c4 = c0 + T(4), c5 = c0 + T(5), c6 = c0 + T(6), c7 = c0 + T(7);
+  for (int i = 0; i < iters; i++) {
+    c0 = c0 * a + b; c1 = c1 * a + b; c2 = c2 * a + b; c3 = c3 * a + b;
+    c4 = c4 * a + b; c5 = c5 * a + b; c6 = c6 * a + b; c7 = c7 * a + b;
+  }
+  T r = c0 + c1 + c2 + c3 + c4 + c5 + c6 + c7;
+  if (r == T(-1.2345)) sink[threadIdx.x] = r;  // keeps the chains live
+}
+
+template <typename T>
+static int probe(int iters, double *out) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  T *sink = nullptr;
+  cudaEvent_t e0, e1;
+  if (cudaMalloc(&sink, 256 * sizeof(T)) != cudaSuccess) return set_error(PDF_ERR_ALLOC, "probe: cudaMalloc");
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int blocks = sms * 8;
+  k_fma<T><<<blocks, 256>>>(T(0.999999), T(1e-7), iters / 8 + 1, sink);  // warm-up
+  cudaEventRecord(e0);
+  k_fma<T><<<blocks, 256>>>(T(0.999999), T(1e-7), iters, sink);
+  cudaEventRecord(e1);
+  cudaError_t e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(sink);
+  if (e != cudaSuccess) return set_error(PDF_ERR_CUDA, "probe: %s", cudaGetErrorString(e));
+  *out = 2.0 * 8.0 * (double)iters * blocks * 256 / (ms * 1e-3);
+  return check_launch("probe");
+}
+
+}  // namespace pdfgb
+
+extern "C" int pdf_probe_fma_rate(int precision, int iters, double *flops_per_s) {
+  using namespace pdfgb;
+  if (!flops_per_s) return set_error(PDF_ERR_NULL, "pdf_probe_fma_rate: NULL output");
+  if (iters < 1 || iters > (1 << 24)) return set_error(PDF_ERR_ARG, "pdf_probe_fma_rate: iters out of range");
+  if (precision == 64) return probe<double>(iters, flops_per_s);
+  if (precision == 32) return probe<float>(iters, flops_per_s);
+  return set_error(PDF_ERR_ARG, "pdf_probe_fma_rate: precision must be 32 or 64");
+}

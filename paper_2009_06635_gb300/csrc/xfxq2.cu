@@ -1,0 +1,451 @@
+// xfxq2.cu -- evaluation kernels for x f(x, Q^2) and alpha_s(Q^2).
+//
+// One warp owns a tile of 32 query points (16 events in the Monte Carlo
+// layout).  Phase 1 (lane = point): read x and Q^2 (coalesced), classify
+// against the grid edges, search the cells on the raw bit patterns (knots in
+// shared memory), take ln x and ln Q^2 once, and record the patch sites and
+// continuation parameters of the point; points are then ordered by class so
+// that lanes of one instruction take the same branch.  Phase 2 (lane =
+// (point, flavour) item): evaluate the patch at each site -- 16 coefficients,
+// 15 FMAs -- combine by class, and write the output; consecutive lanes write
+// consecutive outputs, so the [n][nflav] stores are coalesced.
+#include <cmath>
+#include <type_traits>
+
+#include "pdf_internal.cuh"
+
+namespace pdfgb {
+
+constexpr int kWarps = 8;
+constexpr int kThreads = 32 * kWarps;
+
+template <typename T>
+struct Prec;
+template <>
+struct Prec<double> {
+  using K = long long;
+  static __device__ __forceinline__ K key(double v) { return __double_as_longlong(v); }
+  static __device__ __forceinline__ const double *coef(const GridView &g) { return g.coef; }
+};
+template <>
+struct Prec<float> {
+  using K = int;
+  static __device__ __forceinline__ K key(float v) { return __float_as_int(v); }
+  static __device__ __forceinline__ const float *coef(const GridView &g) { return g.coef32; }
+};
+
+// Per-warp record of the points of one tile, indexed by class-sorted slot.
+template <typename T>
+struct WarpRec {
+  int cls[32], orig[32], xc0[32], xc1[32], qc0[32], qc1[32];
+  T t0[32], t1[32], u0[32], u1[32], px[32], pq[32], lr[32], as[32];
+};
+
+// Sites and continuation parameters of one point.
+template <typename T>
+struct PointSites {
+  int cls, xc0, xc1, qc0, qc1;
+  T t0, t1, u0, u1, px, pq, lr;
+};
+
+// ---- FP64 classification and sites ---------------------------------------
+__device__ __forceinline__ PointSites<double> sites(const GridView &g, const long long *xkeys,
+                                                    const long long *qkeys, double x, double q2) {
+  PointSites<double> r;
+  r.xc0 = r.xc1 = r.qc0 = r.qc1 = 0;
+  r.t0 = r.t1 = r.u0 = r.u1 = r.px = r.pq = r.lr = 0.0;
+  bool valid = (x > 0.0) && (x <= g.xlast) && (q2 > 0.0) && (q2 < INFINITY);
+  if (!valid) { r.cls = C_INVALID; return r; }
+  bool lowx = x < g.x0, lowq = q2 < g.q2min, highq = q2 > g.q2max;
+  double lx = log(x);
+  if (!lowx) {
+    int i = search_cell(xkeys, g.nx, g.xstep, __double_as_longlong(x));
+    r.xc0 = i;
+    r.t0 = (lx - g.xcell[2 * i]) * g.xcell[2 * i + 1];
+  } else {
+    r.xc1 = 1;
+    r.px = (lx - g.lx0) * g.idx0;
+  }
+  if (!lowq && !highq) {
+    int j = search_cell(qkeys, g.nrows, g.qstep, __double_as_longlong(q2));
+    r.qc0 = g.row_qc[j];
+    r.u0 = (log(q2) - g.qcell[2 * j]) * g.qcell[2 * j + 1];
+  } else if (highq) {
+    r.qc0 = g.nqc;
+    r.qc1 = g.top_qc;
+    r.pq = -(log(q2) - g.lq2max) * g.idq_top;
+  } else {
+    r.qc1 = g.q101_qc;
+    r.u1 = g.q101_u;
+    r.pq = q2 / g.q2min;
+    r.lr = log(r.pq);
+  }
+  r.cls = lowx ? (highq ? C_LOWX_HIGHQ : lowq ? C_LOWX_LOWQ : C_LOWX)
+               : (highq ? C_HIGHQ : lowq ? C_LOWQ : C_IN);
+  return r;
+}
+
+// ---- FP32 classification and sites -----------------------------------------
+// The comparisons against rounded-up/down float thresholds decide exactly as
+// FP64 comparisons of the float input against the FP64 knots would.  ln x
+// enters only relative to a knot, ln(x / x_i) = log1p(x * (1/x_i) - 1), so no
+// large absolute logarithm is rounded to FP32.
+__device__ __forceinline__ PointSites<float> sites(const GridView &g, const int *xkeys,
+                                                   const int *qkeys, float x, float q2) {
+  PointSites<float> r;
+  r.xc0 = r.xc1 = r.qc0 = r.qc1 = 0;
+  r.t0 = r.t1 = r.u0 = r.u1 = r.px = r.pq = r.lr = 0.f;
+  bool valid = (x > 0.f) && (x <= g.xlast_rd) && (q2 > 0.f) && (q2 < INFINITY);
+  if (!valid) { r.cls = C_INVALID; return r; }
+  bool lowx = x < g.x0_ru, lowq = q2 < g.q2min_ru, highq = q2 > g.q2max_rd;
+  if (!lowx) {
+    int i = search_cell(xkeys, g.nx, g.xstep, __float_as_int(x));
+    r.xc0 = i;
+    r.t0 = log1pf(fmaf(x, g.xcell32[2 * i], -1.f)) * g.xcell32[2 * i + 1];
+  } else {
+    r.xc1 = 1;
+    r.px = logf(x * g.x0inv32) * g.idx0_32;
+  }
+  if (!lowq && !highq) {
+    int j = search_cell(qkeys, g.nrows, g.qstep, __float_as_int(q2));
+    r.qc0 = g.row_qc[j];
+    r.u0 = log1pf(fmaf(q2, g.qcell32[2 * j], -1.f)) * g.qcell32[2 * j + 1];
+  } else if (highq) {
+    r.qc0 = g.nqc;
+    r.qc1 = g.top_qc;
+    r.pq = -logf(q2 * g.q2maxinv32) * g.idq_top32;
+  } else {
+    r.qc1 = g.q101_qc;
+    r.u1 = g.q101_u32;
+    r.pq = q2 / g.q2min32;
+    r.lr = logf(r.pq);
+  }
+  r.cls = lowx ? (highq ? C_LOWX_HIGHQ : lowq ? C_LOWX_LOWQ : C_LOWX)
+               : (highq ? C_HIGHQ : lowq ? C_LOWQ : C_IN);
+  return r;
+}
+
+// ---- alpha_s (Sec. 2.3): constant outside, log-cubic inside ----------------
+__device__ __forceinline__ double alphas_eval(const GridView &g, const long long *akeys, double q2) {
+  if (!((q2 > 0.0) && (q2 < INFINITY))) return NAN;
+  if (q2 < g.aq2lo) return g.as_lo;
+  if (q2 > g.aq2hi) return g.as_hi;
+  int j = search_cell(akeys, g.na, g.astep, __double_as_longlong(q2));
+  const double *c = g.acell + 6 * j;
+  double u = (log(q2) - c[0]) * c[1];
+  return fma(fma(fma(c[5], u, c[4]), u, c[3]), u, c[2]);
+}
+__device__ __forceinline__ float alphas_eval(const GridView &g, const int *akeys, float q2) {
+  if (!((q2 > 0.f) && (q2 < INFINITY))) return NAN;
+  if (q2 < g.aq2lo_ru) return g.as_lo32;
+  if (q2 > g.aq2hi_rd) return g.as_hi32;
+  int j = search_cell(akeys, g.na, g.astep, __float_as_int(q2));
+  const float *c = g.acell32 + 6 * j;
+  float u = log1pf(fmaf(q2, c[0], -1.f)) * c[1];
+  return fmaf(fmaf(fmaf(c[5], u, c[4]), u, c[3]), u, c[2]);
+}
+
+template <typename T>
+__device__ __forceinline__ void load_keys(const GridView &g, typename Prec<T>::K *keys, int which);
+
+template <>
+__device__ __forceinline__ void load_keys<double>(const GridView &g, long long *keys, int which) {
+  const double *src = which == 0 ? g.xk : which == 1 ? g.q2k : g.aq2;
+  int n = which == 0 ? g.nx : which == 1 ? g.nrows : g.na;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) keys[i] = __double_as_longlong(src[i]);
+}
+template <>
+__device__ __forceinline__ void load_keys<float>(const GridView &g, int *keys, int which) {
+  const float *src = which == 0 ? g.xthr32 : which == 1 ? g.q2thr32 : g.aq2thr32;
+  int n = which == 0 ? g.nx : which == 1 ? g.nrows : g.na;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) keys[i] = __float_as_int(src[i]);
+}
+
+__host__ __device__ inline size_t keys_bytes(int nkeys, size_t ksize) {
+  return ((nkeys * ksize + 15) / 16) * 16;
+}
+
+enum { MODE_POINTS = 0, MODE_MC = 1 };
+
+// Evaluate one (point slot, column) item from the warp record.
+template <typename T>
+__device__ __forceinline__ T eval_item(const GridView &g, const WarpRec<T> &R, int p, int col,
+                                       T ln101) {
+  const T *cb = Prec<T>::coef(g) + (size_t)col * 16;
+  const int cl = R.cls[p];
+  const size_t stride = (size_t)g.nf * 16;
+  if (cl == C_IN)
+    return patch(cb + ((size_t)R.qc0[p] * g.nx + R.xc0[p]) * stride, R.t0[p], R.u0[p]);
+  auto F = [&](int a, int b) -> T {
+    int xc = a ? R.xc1[p] : R.xc0[p];
+    int qc = b ? R.qc1[p] : R.qc0[p];
+    T t = a ? R.t1[p] : R.t0[p];
+    T u = b ? R.u1[p] : R.u0[p];
+    return patch(cb + ((size_t)qc * g.nx + xc) * stride, t, u);
+  };
+  return combine<T>(cl, R.px[p], R.pq[p], R.lr[p], ln101, F);
+}
+
+// MODE_POINTS: points xa[n], qa[n]; out[n][ncol] for columns col0..col0+ncol-1.
+// MODE_MC:     events xa[n] (x1), xb[n] (x2), Q^2 = x1 x2 s; out[n][2 nf + 1].
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kThreads)
+k_xf(GridView g, const T *__restrict__ xa, const T *__restrict__ qa, const T *__restrict__ xb,
+     T s, long long n, int col0, int ncol, T *__restrict__ out) {
+  using K = typename Prec<T>::K;
+  extern __shared__ __align__(16) unsigned char smem[];
+  K *xkeys = reinterpret_cast<K *>(smem);
+  K *qkeys = reinterpret_cast<K *>(smem + keys_bytes(g.nx, sizeof(K)));
+  K *akeys = reinterpret_cast<K *>(smem + keys_bytes(g.nx, sizeof(K)) + keys_bytes(g.nrows, sizeof(K)));
+  size_t rec_off = keys_bytes(g.nx, sizeof(K)) + keys_bytes(g.nrows, sizeof(K)) +
+                   (MODE == MODE_MC ? keys_bytes(g.na, sizeof(K)) : 0);
+  WarpRec<T> *recs = reinterpret_cast<WarpRec<T> *>(smem + rec_off);
+  load_keys<T>(g, xkeys, 0);
+  load_keys<T>(g, qkeys, 1);
+  if (MODE == MODE_MC) load_keys<T>(g, akeys, 2);
+  __syncthreads();
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  WarpRec<T> &R = recs[warp];
+  const int per_tile = MODE == MODE_MC ? 16 : 32;
+  const int per = MODE == MODE_MC ? 2 * g.nf + 1 : ncol;  // outputs per tile unit
+  const int dp = 32 / per, dc = 32 - dp * per;
+  const T ln101 = sizeof(T) == 8 ? (T)g.ln101 : (T)g.ln101_32;
+  const long long ntiles = (n + per_tile - 1) / per_tile;
+  const long long nwarps = (long long)gridDim.x * kWarps;
+
+  for (long long tile = (long long)blockIdx.x * kWarps + warp; tile < ntiles; tile += nwarps) {
+    const long long e0 = tile * per_tile;
+    const int ne = (int)(n - e0 < per_tile ? n - e0 : per_tile);
+
+    // ---- phase 1: lane = point ----
+    bool present;
+    T x = T(0), q2 = T(0);
+    if (MODE == MODE_POINTS) {
+      present = lane < ne;
+      if (present) { x = xa[e0 + lane]; q2 = qa[e0 + lane]; }
+    } else {
+      const int e = lane >> 1;
+      present = e < ne;
+      if (present) {
+        T x1 = xa[e0 + e], x2 = xb[e0 + e];
+        q2 = x1 * x2 * s;
+        x = (lane & 1) ? x2 : x1;
+      }
+    }
+    PointSites<T> ps;
+    ps.cls = NCLASS;
+    if (present) ps = sites(g, xkeys, qkeys, x, q2);
+    unsigned inv = __ballot_sync(0xffffffffu, present && ps.cls == C_INVALID);
+    if (lane == 0 && inv) atomicAdd(g.invalid, (unsigned long long)__popc(inv));
+
+    int slot = lane;
+    if (MODE == MODE_POINTS) {  // order points by class (counting sort over the warp)
+      int base = 0;
+      const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+      for (int c = 0; c <= NCLASS; c++) {
+        unsigned m = __ballot_sync(0xffffffffu, ps.cls == c);
+        if (ps.cls == c) slot = base + __popc(m & lt);
+        base += __popc(m);
+      }
+    }
+    R.cls[slot] = ps.cls; R.orig[slot] = lane;
+    R.xc0[slot] = ps.xc0; R.xc1[slot] = ps.xc1; R.qc0[slot] = ps.qc0; R.qc1[slot] = ps.qc1;
+    R.t0[slot] = ps.t0; R.t1[slot] = ps.t1; R.u0[slot] = ps.u0; R.u1[slot] = ps.u1;
+    R.px[slot] = ps.px; R.pq[slot] = ps.pq; R.lr[slot] = ps.lr;
+    if (MODE == MODE_MC && (lane & 1) == 0) R.as[lane >> 1] = present ? alphas_eval(g, akeys, q2) : T(0);
+    __syncwarp();
+
+    // ---- phase 2: lane = (point, column) item ----
+    const int nitems = ne * per;
+    int p = lane / per, c = lane - (lane / per) * per;
+    for (int k = lane; k < nitems; k += 32) {
+      T v;
+      long long o;
+      if (MODE == MODE_POINTS) {
+        v = eval_item<T>(g, R, p, col0 + c, ln101);
+        o = (e0 + R.orig[p]) * (long long)per + c;
+      } else {
+        if (c == 2 * g.nf) {
+          v = R.as[p];
+        } else {
+          const int side = c >= g.nf;
+          v = eval_item<T>(g, R, 2 * p + side, c - side * g.nf, ln101);
+        }
+        o = (e0 + p) * (long long)per + c;
+      }
+      out[o] = v;
+      c += dc;
+      p += dp;
+      if (c >= per) { c -= per; p++; }
+    }
+    __syncwarp();
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_alphas(GridView g, const T *__restrict__ qa,
+                                                     long long n, T *__restrict__ out) {
+  using K = typename Prec<T>::K;
+  extern __shared__ __align__(16) unsigned char smem[];
+  K *akeys = reinterpret_cast<K *>(smem);
+  load_keys<T>(g, akeys, 2);
+  __syncthreads();
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += stride) {
+    long long i = base + threadIdx.x;
+    bool present = i < n;
+    T q2 = present ? qa[i] : T(1);
+    bool bad = present && !((q2 > T(0)) && (q2 < T(INFINITY)));
+    unsigned inv = __ballot_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0 && inv) atomicAdd(g.invalid, (unsigned long long)__popc(inv));
+    if (present) out[i] = alphas_eval(g, akeys, q2);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launch helpers
+// ---------------------------------------------------------------------------
+static int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+template <typename T, int MODE>
+static size_t xf_smem(const GridView &g) {
+  using K = typename std::conditional<sizeof(T) == 8, long long, int>::type;
+  return keys_bytes(g.nx, sizeof(K)) + keys_bytes(g.nrows, sizeof(K)) +
+         (MODE == MODE_MC ? keys_bytes(g.na, sizeof(K)) : 0) + kWarps * sizeof(WarpRec<T>);
+}
+
+template <typename T, int MODE>
+static int launch_xf(const pdf_grid *grid, const T *xa, const T *qa, const T *xb, T s,
+                     long long n, int col0, int ncol, T *out, cudaStream_t st) {
+  const GridView &g = grid->v;
+  size_t smem = xf_smem<T, MODE>(g);
+  auto kern = k_xf<T, MODE>;
+  static int configured = 0;
+  if (smem > 48 * 1024 || !configured) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    configured = 1;
+  }
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+  if (per_sm < 1) per_sm = 1;
+  const int per_tile = MODE == MODE_MC ? 16 : 32;
+  long long ntiles = (n + per_tile - 1) / per_tile;
+  long long blocks = (ntiles + kWarps - 1) / kWarps;
+  long long cap = (long long)num_sms() * per_sm;
+  if (blocks > cap) blocks = cap;
+  kern<<<(unsigned)blocks, kThreads, smem, st>>>(g, xa, qa, xb, s, n, col0, ncol, out);
+  return check_launch(MODE == MODE_MC ? "pdf_mc_event kernel" : "xfxq2 kernel");
+}
+
+template <typename T>
+static int launch_alphas(const pdf_grid *grid, const T *q2, long long n, T *out, cudaStream_t st) {
+  const GridView &g = grid->v;
+  using K = typename std::conditional<sizeof(T) == 8, long long, int>::type;
+  size_t smem = keys_bytes(g.na, sizeof(K));
+  long long blocks = (n + kThreads - 1) / kThreads;
+  long long cap = (long long)num_sms() * 8;
+  if (blocks > cap) blocks = cap;
+  k_alphas<T><<<(unsigned)blocks, kThreads, smem, st>>>(g, q2, n, out);
+  return check_launch("alphas_q2 kernel");
+}
+
+static int check_common(const pdf_grid *g, const void *a, const void *b, const void *o, size_t n,
+                        const char *what) {
+  if (!g) return set_error(PDF_ERR_NULL, "%s: grid is NULL", what);
+  if (n > 0 && (!a || !b || !o)) return set_error(PDF_ERR_NULL, "%s: NULL array", what);
+  if (n > (size_t)1 << 40) return set_error(PDF_ERR_ARG, "%s: n = %zu too large", what, n);
+  return PDF_OK;
+}
+
+template <typename T>
+static int do_xfxq2(const pdf_grid *g, int pid, const T *x, const T *q2, size_t n, T *out,
+                    cudaStream_t st) {
+  int rc = check_common(g, x, q2, out, n, "xfxq2");
+  if (rc) return rc;
+  int col = pdf_grid_pid_column(g, pid);
+  if (col < 0) return set_error(PDF_ERR_PID, "xfxq2: pid %d not in the grid", pid);
+  if (n == 0) return PDF_OK;
+  return launch_xf<T, MODE_POINTS>(g, x, q2, nullptr, T(0), (long long)n, col, 1, out, st);
+}
+
+template <typename T>
+static int do_all(const pdf_grid *g, const T *x, const T *q2, size_t n, T *out, cudaStream_t st) {
+  int rc = check_common(g, x, q2, out, n, "xfxq2_all_flavours");
+  if (rc) return rc;
+  if (n == 0) return PDF_OK;
+  return launch_xf<T, MODE_POINTS>(g, x, q2, nullptr, T(0), (long long)n, 0, g->v.nf, out, st);
+}
+
+template <typename T>
+static int do_alphas(const pdf_grid *g, const T *q2, size_t n, T *out, cudaStream_t st) {
+  int rc = check_common(g, q2, q2, out, n, "alphas_q2");
+  if (rc) return rc;
+  if (g->v.na == 0) return set_error(PDF_ERR_NO_ALPHAS, "alphas_q2: grid has no alpha_s nodes");
+  if (n == 0) return PDF_OK;
+  return launch_alphas<T>(g, q2, (long long)n, out, st);
+}
+
+template <typename T>
+static int do_mc(const pdf_grid *g, const T *x1, const T *x2, T s, size_t n, T *out, cudaStream_t st) {
+  int rc = check_common(g, x1, x2, out, n, "pdf_mc_event");
+  if (rc) return rc;
+  if (g->v.na == 0) return set_error(PDF_ERR_NO_ALPHAS, "pdf_mc_event: grid has no alpha_s nodes");
+  if (!(s > T(0)) || !(s < T(INFINITY))) return set_error(PDF_ERR_ARG, "pdf_mc_event: s must be positive and finite");
+  if (n == 0) return PDF_OK;
+  return launch_xf<T, MODE_MC>(g, x1, nullptr, x2, s, (long long)n, 0, 0, out, st);
+}
+
+// Used by the host-memory path.
+int launch_alphas_f64(const pdf_grid *g, const double *q2, long long n, double *out, cudaStream_t st) {
+  return launch_alphas<double>(g, q2, n, out, st);
+}
+int launch_all_f64(const pdf_grid *g, const double *x, const double *q2, long long n, double *out,
+                   cudaStream_t st) {
+  return launch_xf<double, MODE_POINTS>(g, x, q2, nullptr, 0.0, n, 0, g->v.nf, out, st);
+}
+
+}  // namespace pdfgb
+
+using namespace pdfgb;
+
+extern "C" int xfxq2(const pdf_grid *g, int pid, const double *x, const double *q2, size_t n,
+                     double *out, cudaStream_t st) {
+  return do_xfxq2<double>(g, pid, x, q2, n, out, st);
+}
+extern "C" int xfxq2_f32(const pdf_grid *g, int pid, const float *x, const float *q2, size_t n,
+                         float *out, cudaStream_t st) {
+  return do_xfxq2<float>(g, pid, x, q2, n, out, st);
+}
+extern "C" int xfxq2_all_flavours(const pdf_grid *g, const double *x, const double *q2, size_t n,
+                                  double *out, cudaStream_t st) {
+  return do_all<double>(g, x, q2, n, out, st);
+}
+extern "C" int xfxq2_all_flavours_f32(const pdf_grid *g, const float *x, const float *q2, size_t n,
+                                      float *out, cudaStream_t st) {
+  return do_all<float>(g, x, q2, n, out, st);
+}
+extern "C" int alphas_q2(const pdf_grid *g, const double *q2, size_t n, double *out, cudaStream_t st) {
+  return do_alphas<double>(g, q2, n, out, st);
+}
+extern "C" int alphas_q2_f32(const pdf_grid *g, const float *q2, size_t n, float *out, cudaStream_t st) {
+  return do_alphas<float>(g, q2, n, out, st);
+}
+extern "C" int pdf_mc_event(const pdf_grid *g, const double *x1, const double *x2, double s, size_t n,
+                            double *out, cudaStream_t st) {
+  return do_mc<double>(g, x1, x2, s, n, out, st);
+}
+extern "C" int pdf_mc_event_f32(const pdf_grid *g, const float *x1, const float *x2, float s, size_t n,
+                                float *out, cudaStream_t st) {
+  return do_mc<float>(g, x1, x2, s, n, out, st);
+}

@@ -1,0 +1,187 @@
+"""PyTorch-facing API over the C ABI (names as in include/pdf_gb300.h).
+
+    grid = pdf_load_grid(synthetic.grid_full())      # PDFFlow mkPDF (Sec. 2.1)
+    out  = xfxq2_all_flavours(grid, x, q2)           # xfxQ2_allpid
+    a    = alphas_q2(grid, q2)                       # alphas_Q2
+
+Tensors must be CUDA, contiguous, float64 (or float32 for the *_f32 paths);
+work is enqueued on torch's current stream of the tensors' device.  PyTorch
+only provides device memory and the stream; the evaluation is the library's.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _native
+from ._native import PdfError, check
+
+
+def _stream_handle(dev: torch.device) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+
+
+def _dev_ptr(t: torch.Tensor, dtype, name: str) -> ctypes.c_void_p:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Grid:
+    """A loaded PDF set (owns the device-side handle)."""
+
+    def __init__(self, handle: int, pids, device: torch.device):
+        self._h = ctypes.c_void_p(handle)
+        self.pids = list(pids)
+        self.nflav = len(self.pids)
+        self.device = device
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if not self._h:
+            raise PdfError(-1, "grid has been freed")
+        return self._h
+
+    def free(self):
+        if self._h:
+            check(_native.load().pdf_free_grid(self._h), "pdf_free_grid")
+            self._h = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def column(self, pid: int) -> int:
+        return int(_native.load().pdf_grid_pid_column(self.handle, int(pid)))
+
+    def invalid_count(self) -> int:
+        c = ctypes.c_ulonglong(0)
+        check(_native.load().pdf_grid_invalid_count(self.handle, ctypes.byref(c)), "pdf_grid_invalid_count")
+        return int(c.value)
+
+    def reset_invalid_count(self):
+        check(_native.load().pdf_grid_reset_invalid_count(self.handle), "pdf_grid_reset_invalid_count")
+
+
+def pdf_load_grid(grid=None, *, x_knots=None, nq=None, q2_knots=None, pids=None, values=None,
+                  as_q2=None, as_vals=None, device=None) -> Grid:
+    """Load a PDF set (any object with x_knots, nq, q2_knots, pids, values,
+    as_q2, as_vals, or the same as keywords) onto the current CUDA device."""
+    if grid is not None:
+        x_knots, nq, q2_knots, pids, values = grid.x_knots, grid.nq, grid.q2_knots, grid.pids, grid.values
+        as_q2, as_vals = grid.as_q2, grid.as_vals
+    lib = _native.load()
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    xk = np.ascontiguousarray(x_knots, dtype=np.float64)
+    nqa = np.ascontiguousarray(nq, dtype=np.int32)
+    q2k = np.ascontiguousarray(q2_knots, dtype=np.float64)
+    pa = np.ascontiguousarray(pids, dtype=np.int32)
+    va = np.ascontiguousarray(values, dtype=np.float64)
+    aq = np.ascontiguousarray([] if as_q2 is None else as_q2, dtype=np.float64)
+    av = np.ascontiguousarray([] if as_vals is None else as_vals, dtype=np.float64)
+    if va.ndim != 3 or va.shape != (q2k.shape[0], xk.shape[0], pa.shape[0]):
+        raise PdfError(-2, f"values shape {va.shape} != (rows, nx, nflav)")
+    d = _native.GridDesc(
+        int(xk.shape[0]), xk.ctypes.data, int(nqa.shape[0]), nqa.ctypes.data, q2k.ctypes.data,
+        int(pa.shape[0]), pa.ctypes.data, va.ctypes.data, int(aq.shape[0]),
+        aq.ctypes.data if aq.size else None, av.ctypes.data if av.size else None)
+    h = ctypes.c_void_p(None)
+    with torch.cuda.device(dev):
+        check(lib.pdf_load_grid(ctypes.byref(d), ctypes.byref(h)), "pdf_load_grid")
+    return Grid(h.value, pa.tolist(), dev)
+
+
+def _out(out, shape, like: torch.Tensor):
+    if out is None:
+        return torch.empty(shape, dtype=like.dtype, device=like.device)
+    if tuple(out.shape) != tuple(shape):
+        raise ValueError(f"out has shape {tuple(out.shape)}, expected {tuple(shape)}")
+    return out
+
+
+def _check_pair(x: torch.Tensor, q2: torch.Tensor):
+    if x.shape != q2.shape or x.dim() != 1:
+        raise ValueError("x and q2 must be 1-D tensors of the same length")
+
+
+def xfxq2(grid: Grid, pid: int, x: torch.Tensor, q2: torch.Tensor, out=None) -> torch.Tensor:
+    """x f(x, Q^2) of one flavour (FP64 or FP32 by the input dtype)."""
+    _check_pair(x, q2)
+    out = _out(out, (x.shape[0],), x)
+    lib = _native.load()
+    f32 = x.dtype == torch.float32
+    dt = torch.float32 if f32 else torch.float64
+    fn = lib.xfxq2_f32 if f32 else lib.xfxq2
+    check(fn(grid.handle, int(pid), _dev_ptr(x, dt, "x"), _dev_ptr(q2, dt, "q2"), x.shape[0],
+             _dev_ptr(out, dt, "out"), _stream_handle(x.device)), "xfxq2")
+    return out
+
+
+def xfxq2_all_flavours(grid: Grid, x: torch.Tensor, q2: torch.Tensor, out=None) -> torch.Tensor:
+    """All flavours, [n][nflav] (FP64 or FP32 by the input dtype)."""
+    _check_pair(x, q2)
+    out = _out(out, (x.shape[0], grid.nflav), x)
+    lib = _native.load()
+    f32 = x.dtype == torch.float32
+    dt = torch.float32 if f32 else torch.float64
+    fn = lib.xfxq2_all_flavours_f32 if f32 else lib.xfxq2_all_flavours
+    check(fn(grid.handle, _dev_ptr(x, dt, "x"), _dev_ptr(q2, dt, "q2"), x.shape[0],
+             _dev_ptr(out, dt, "out"), _stream_handle(x.device)), "xfxq2_all_flavours")
+    return out
+
+
+def alphas_q2(grid: Grid, q2: torch.Tensor, out=None) -> torch.Tensor:
+    """alpha_s(Q^2) (FP64 or FP32 by the input dtype)."""
+    if q2.dim() != 1:
+        raise ValueError("q2 must be 1-D")
+    out = _out(out, (q2.shape[0],), q2)
+    lib = _native.load()
+    f32 = q2.dtype == torch.float32
+    dt = torch.float32 if f32 else torch.float64
+    fn = lib.alphas_q2_f32 if f32 else lib.alphas_q2
+    check(fn(grid.handle, _dev_ptr(q2, dt, "q2"), q2.shape[0], _dev_ptr(out, dt, "out"),
+             _stream_handle(q2.device)), "alphas_q2")
+    return out
+
+
+def pdf_mc_event(grid: Grid, x1: torch.Tensor, x2: torch.Tensor, s: float, out=None) -> torch.Tensor:
+    """Fused Monte Carlo event evaluation: [n][2 nflav + 1] with Q^2 = x1 x2 s."""
+    _check_pair(x1, x2)
+    out = _out(out, (x1.shape[0], 2 * grid.nflav + 1), x1)
+    lib = _native.load()
+    f32 = x1.dtype == torch.float32
+    dt = torch.float32 if f32 else torch.float64
+    fn = lib.pdf_mc_event_f32 if f32 else lib.pdf_mc_event
+    check(fn(grid.handle, _dev_ptr(x1, dt, "x1"), _dev_ptr(x2, dt, "x2"), float(s), x1.shape[0],
+             _dev_ptr(out, dt, "out"), _stream_handle(x1.device)), "pdf_mc_event")
+    return out
+
+
+def xfxq2_all_flavours_host(grid: Grid, x, q2, out=None, alphas_out=None, with_alphas: bool = False):
+    """Host arrays in (numpy or CPU tensors, float64), host [n][nflav] out (and
+    alpha_s [n] when with_alphas or alphas_out is given).  Pinned CPU tensors
+    give overlapped copies.  Returns out, or (out, alphas_out)."""
+    xs = x if isinstance(x, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64))
+    qs = q2 if isinstance(q2, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(q2, dtype=np.float64))
+    for t, name in ((xs, "x"), (qs, "q2")):
+        if t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+            raise TypeError(f"{name} must be a contiguous float64 host array")
+    if out is None:
+        out = torch.empty((xs.shape[0], grid.nflav), dtype=torch.float64)
+    if alphas_out is None and with_alphas:
+        alphas_out = torch.empty((xs.shape[0],), dtype=torch.float64)
+    lib = _native.load()
+    aptr = ctypes.c_void_p(alphas_out.data_ptr()) if alphas_out is not None else None
+    with torch.cuda.device(grid.device):
+        check(lib.xfxq2_all_flavours_host(grid.handle, ctypes.c_void_p(xs.data_ptr()),
+                                          ctypes.c_void_p(qs.data_ptr()), xs.shape[0],
+                                          ctypes.c_void_p(out.data_ptr()), aptr), "xfxq2_all_flavours_host")
+    return out if alphas_out is None else (out, alphas_out)
