@@ -25,6 +25,12 @@
  *            secant at the first/last knot of the x grid and of each Q
  *            subgrid; Hermite tangent = slope * cell width.
  *   R-order  x first, then Q.
+ *   R-ends   the position inside a cell is carried as the pair (t, 1 - t),
+ *            each taken from its own knot, t = (ln x - ln x_i)/d and
+ *            1 - t = (ln x_{i+1} - ln x)/d, and the Hermite basis is
+ *            evaluated in factored form; so a point within rounding of the
+ *            far knot (x -> 1, where xf ~ (1 - t)) keeps its relative
+ *            precision.  The cubic is the textbook one.
  *   R-ties   cells are chosen on the raw inputs (x, Q^2) against the raw
  *            knots: a point on an interior knot belongs to the cell on its
  *            right; the last knot closes the last cell; Q^2 on a subgrid
@@ -205,21 +211,25 @@ og *og_prepare(int nx, const double *xk, int nsub, const int *nq, const double *
 /* ------------------------------------------------------------------ */
 
 /* Cubic Hermite segment on t in [0, 1] with end values f0, f1 and end
- * tangents m0, m1 (already multiplied by the cell width). */
-static num hermite(num t, num f0, num f1, num m0, num m1) {
-  num t2 = mul(t, t), t3 = mul(t2, t);
-  num h00 = add(sub(mul(cst(2.0), t3), mul(cst(3.0), t2)), cst(1.0));
-  num h01 = add(mul(cst(-2.0), t3), mul(cst(3.0), t2));
-  num h10 = add(sub(t3, mul(cst(2.0), t2)), t);
-  num h11 = sub(t3, t2);
+ * tangents m0, m1 (already multiplied by the cell width); tm = 1 - t.
+ * Basis h00 = 2t^3 - 3t^2 + 1, h01 = -2t^3 + 3t^2, h10 = t^3 - 2t^2 + t,
+ * h11 = t^3 - t^2, written in factored form:
+ * h00 = (1 + 2t) tm^2, h01 = t^2 (1 + 2 tm), h10 = t tm^2, h11 = -t^2 tm. */
+static num hermite(num t, num tm, num f0, num f1, num m0, num m1) {
+  num t2 = mul(t, t), tm2 = mul(tm, tm);
+  num h00 = mul(add(cst(1.0), mul(cst(2.0), t)), tm2);
+  num h01 = mul(t2, add(cst(1.0), mul(cst(2.0), tm)));
+  num h10 = mul(t, tm2);
+  num h11 = sub(cst(0.0), mul(t2, tm));
   return add(add(mul(h00, f0), mul(h01, f1)), add(mul(h10, m0), mul(h11, m1)));
 }
 
 /* Knot slope from a 1-D sequence f[lo..hi] at knots l[lo..hi] (R-slope). */
 static num secant(num fa, num fb, num la, num lb) { return dvd(sub(fb, fa), sub(lb, la)); }
 
-/* x-direction interpolation of knot row `row` in cell i at parameter t. */
-static num row_interp(const og *g, int row, int i, num t, int f, ctx *c) {
+/* x-direction interpolation of knot row `row` in cell i at parameter t
+ * (tm = 1 - t). */
+static num row_interp(const og *g, int row, int i, num t, num tm, int f, ctx *c) {
   int n = g->nx;
   num fi = knot(g, row, i, f, c), fi1 = knot(g, row, i + 1, f, c);
   num s0, s1;
@@ -230,7 +240,7 @@ static num row_interp(const og *g, int row, int i, num t, int f, ctx *c) {
   else s1 = mul(cst(0.5), add(secant(fi, fi1, g->lx[i], g->lx[i + 1]),
                                secant(fi1, knot(g, row, i + 2, f, c), g->lx[i + 1], g->lx[i + 2])));
   num dx = sub(g->lx[i + 1], g->lx[i]);
-  return hermite(t, fi, fi1, mul(dx, s0), mul(dx, s1));
+  return hermite(t, tm, fi, fi1, mul(dx, s0), mul(dx, s1));
 }
 
 /* ------------------------------------------------------------------ */
@@ -248,21 +258,22 @@ static num interp2(const og *g, num X, num Q2, int f, ctx *c) {
   int j = j0;
   while (j + 1 < j1 && g->q2k[j + 1] <= Q2.v) j++;
 
-  num t = dvd(sub(nlog(X), g->lx[i]), sub(g->lx[i + 1], g->lx[i]));
-  num u = dvd(sub(nlog(Q2), g->lq[j]), sub(g->lq[j + 1], g->lq[j]));
+  num lxv = nlog(X), lqv = nlog(Q2);
+  num dx = sub(g->lx[i + 1], g->lx[i]), dq = sub(g->lq[j + 1], g->lq[j]);
+  num t = dvd(sub(lxv, g->lx[i]), dx), tm = dvd(sub(g->lx[i + 1], lxv), dx);  /* R-ends */
+  num u = dvd(sub(lqv, g->lq[j]), dq), um = dvd(sub(g->lq[j + 1], lqv), dq);
 
   /* x direction on the rows the Q stencil needs (R-order) */
-  num gj = row_interp(g, j, i, t, f, c);
-  num gj1 = row_interp(g, j + 1, i, t, f, c);
+  num gj = row_interp(g, j, i, t, tm, f, c);
+  num gj1 = row_interp(g, j + 1, i, t, tm, f, c);
   num s0, s1;
   if (j == j0) s0 = secant(gj, gj1, g->lq[j], g->lq[j + 1]);
-  else s0 = mul(cst(0.5), add(secant(row_interp(g, j - 1, i, t, f, c), gj, g->lq[j - 1], g->lq[j]),
+  else s0 = mul(cst(0.5), add(secant(row_interp(g, j - 1, i, t, tm, f, c), gj, g->lq[j - 1], g->lq[j]),
                                secant(gj, gj1, g->lq[j], g->lq[j + 1])));
   if (j + 1 == j1) s1 = secant(gj, gj1, g->lq[j], g->lq[j + 1]);
   else s1 = mul(cst(0.5), add(secant(gj, gj1, g->lq[j], g->lq[j + 1]),
-                               secant(gj1, row_interp(g, j + 2, i, t, f, c), g->lq[j + 1], g->lq[j + 2])));
-  num dq = sub(g->lq[j + 1], g->lq[j]);
-  return hermite(u, gj, gj1, mul(dq, s0), mul(dq, s1));
+                               secant(gj1, row_interp(g, j + 2, i, t, tm, f, c), g->lq[j + 1], g->lq[j + 2])));
+  return hermite(u, um, gj, gj1, mul(dq, s0), mul(dq, s1));
 }
 
 /* ------------------------------------------------------------------ */
@@ -337,14 +348,14 @@ static num alphas_one(const og *g, double q2, int wrt_q2) {
   num Q2 = {q2, wrt_q2 ? 1.0 : 0.0, 0.0, 0.0};
   const num *l = g->alq;
   num fj = dat(g->aval[j]), fj1 = dat(g->aval[j + 1]);
-  num u = dvd(sub(nlog(Q2), l[j]), sub(l[j + 1], l[j]));
+  num lqv = nlog(Q2), dq = sub(l[j + 1], l[j]);
+  num u = dvd(sub(lqv, l[j]), dq), um = dvd(sub(l[j + 1], lqv), dq);
   num s0, s1;
   if (j == a0) s0 = secant(fj, fj1, l[j], l[j + 1]);
   else s0 = mul(cst(0.5), add(secant(dat(g->aval[j - 1]), fj, l[j - 1], l[j]), secant(fj, fj1, l[j], l[j + 1])));
   if (j + 1 == a1) s1 = secant(fj, fj1, l[j], l[j + 1]);
   else s1 = mul(cst(0.5), add(secant(fj, fj1, l[j], l[j + 1]), secant(fj1, dat(g->aval[j + 2]), l[j + 1], l[j + 2])));
-  num dq = sub(l[j + 1], l[j]);
-  return hermite(u, fj, fj1, mul(dq, s0), mul(dq, s1));
+  return hermite(u, um, fj, fj1, mul(dq, s0), mul(dq, s1));
 }
 
 /* ------------------------------------------------------------------ */
@@ -435,7 +446,7 @@ void og_alphas(const og *g, const double *q2, long n, double *out_v, double *out
 
 /* The bare Hermite segment, exposed for the cubic-exactness pin. */
 double og_hermite(double t, double f0, double f1, double m0, double m1) {
-  return hermite(cst(t), cst(f0), cst(f1), cst(m0), cst(m1)).v;
+  return hermite(cst(t), cst(1.0 - t), cst(f0), cst(f1), cst(m0), cst(m1)).v;
 }
 
 int og_max_threads(void) {

@@ -571,3 +571,21 @@ def test_x_and_q2_derivatives_match_finite_differences(oracle_mod, synth):
         err = np.abs(fd - d) / (np.abs(d) + s / arr[:, None])
         assert ok.mean() > 0.95
         assert (err[ok] < 1e-5).all(), wrt
+
+
+def test_relative_precision_next_to_a_vanishing_knot(oracle_mod, synth):
+    """R-ends: within rounding distance of a knot where xf vanishes (x -> 1,
+    xf ~ (1 - x)^b) the value keeps its relative precision: it matches the
+    exact-rational evaluation relative to |xf| itself, not only to the data
+    mass."""
+    x = synth.geom_knots(1e-3, 1.0, 6)
+    subs = [synth.geom_knots(2.0, 100.0, 5)]
+    g = mk(synth, x, subs, lambda xk, q2: ((1.0 - xk) ** 3)[None, :, None] * (1.0 + 0.1 * np.log(q2))[:, None, None], 1)
+    og = oracle_mod.OracleGrid(g)
+    xs = np.array([np.nextafter(1.0, 0), 1.0 - 1e-12, 1.0 - 1e-9, np.nextafter(x[2], 0)])
+    qs = np.array([7.0, 13.0, np.nextafter(100.0, 0), 3.0])
+    v, _, _ = og.xfxq2(xs, qs)
+    for p in range(len(xs)):
+        want = float(_frac_eval(g, xs[p], qs[p], 0))
+        assert want != 0.0
+        assert abs(v[p, 0] - want) <= 1e-12 * abs(want), (p, v[p, 0], want)
