@@ -7,9 +7,11 @@
 //     knot tangent is the mean of the two adjacent secant slopes, one-sided
 //     at the x edges and at the ends of each Q subgrid (Sec. 2.2's special
 //     care at edges and thresholds), times the cell width;
-//   - per cell and flavour, the bicubic patch sum_ab w_a(t) w_b(u) f_ab in
-//     monomial form (16 coefficients), in FP64 and rounded to FP32;
-//   - per alpha_s cell the cubic in u (Sec. 2.3), same tangents per subgrid;
+//   - per cell and flavour, the bicubic patch sum_ab w_a(t) w_b(u) f_ab as
+//     its 4x4 Bezier control points (Bernstein basis), in FP64 and rounded
+//     to FP32;
+//   - per alpha_s cell the cubic in u in monomial form (Sec. 2.3; one
+//     dimension, four well-scaled coefficients), same tangents per subgrid;
 //   - a degenerate cell on the last x knot and on the top Q knot (t = 0
 //     there; its patch carries only that knot's column or row), so the last
 //     knots are reproduced exactly;
@@ -41,24 +43,25 @@ int check_launch(const char *what) {
   return PDF_OK;
 }
 
-// Hermite basis in monomial form, coefficients of t^0..t^3.
-__device__ __constant__ double kH00[4] = {1.0, 0.0, -3.0, 2.0};
-__device__ __constant__ double kH01[4] = {0.0, 0.0, 3.0, -2.0};
-__device__ __constant__ double kH10[4] = {0.0, 1.0, -2.0, 1.0};
-__device__ __constant__ double kH11[4] = {0.0, 0.0, -1.0, 1.0};
-
-// Knot weights of one cell: tangent at the left knot = aL * right secant +
-// bL * left secant, at the right knot = dR * cell secant + gR * next secant
-// (secants as differences of values over differences of logs); the tangent
-// multiplies the cell width d, so the left-secant term carries d/d_prev and
-// the next-secant term d/d_next.
+// Knot weights of one cell in the cubic Bernstein basis
+// B_k(t) = C(3,k) t^k (1-t)^(3-k):  w_a(t) = sum_k W[a][k] B_k(t) is the
+// weight of knot i-1+a.  A cubic Hermite segment with end values f_i, f_{i+1}
+// and end tangents m0, m1 (slope times cell width d) has the Bezier control
+// points f_i, f_i + m0/3, f_{i+1} - m1/3, f_{i+1}.  The tangents are the
+// finite differences of Sec. 2.2: at the left knot m0 = aL (f_{i+1} - f_i) +
+// bm (f_i - f_{i-1}), at the right knot m1 = dR (f_{i+1} - f_i) +
+// gp (f_{i+2} - f_{i+1}); inside the grid aL = dR = 1/2, bm = d/(2 d_prev),
+// gp = d/(2 d_next); at an edge the one-sided secant (aL = 1, bm = 0 or
+// dR = 1, gp = 0).  Bernstein weights are non-negative and sum to one, so a
+// patch evaluated in this basis suffers no cancellation.
 __device__ void cell_weights(double aL, double bm, double dR, double gp, double *W) {
-  for (int k = 0; k < 4; k++) {
-    W[0 * 4 + k] = -bm * kH10[k];
-    W[1 * 4 + k] = kH00[k] - (aL - bm) * kH10[k] - dR * kH11[k];
-    W[2 * 4 + k] = kH01[k] + aL * kH10[k] + (dR - gp) * kH11[k];
-    W[3 * 4 + k] = gp * kH11[k];
-  }
+  const double third = 1.0 / 3.0;
+  double V[4][4] = {{0.0, 1.0, 0.0, 0.0},
+                    {-bm * third, 1.0 + (bm - aL) * third, aL * third, 0.0},
+                    {0.0, dR * third, 1.0 - (dR - gp) * third, -gp * third},
+                    {0.0, 0.0, 1.0, 0.0}};  // V[k][a]
+  for (int a = 0; a < 4; a++)
+    for (int k = 0; k < 4; k++) W[a * 4 + k] = V[k][a];
 }
 
 struct Stage {
@@ -81,28 +84,42 @@ __global__ void k_logs(Stage S) {
   if (i < S.na) { S.alq[i] = log(S.aq2[i]); S.aq2thr32[i] = __double2float_ru(S.aq2[i]); }
 }
 
-// Degenerate cell on a last knot: all weight on the knot itself (a = 1).
+// FP32 cell table: both end knots rounded to float (k0f, k1f), their float
+// reciprocals, the FP64 corrections ln(kf / k) that undo the rounding, the
+// inverse cell width in ln, and the geometric midpoint that picks the nearer
+// end as the reference of the logarithm:
+//   {k0f, 1/k0f, ln(k0f/k0), 1/d, k1f, 1/k1f, ln(k1f/k1), mid}.
+__device__ void cell32(double k0, double k1, double inv_d, double mid, float *o) {
+  float k0f = (float)k0, k1f = (float)k1;
+  o[0] = k0f; o[1] = (float)(1.0 / (double)k0f); o[2] = (float)log((double)k0f / k0); o[3] = (float)inv_d;
+  o[4] = k1f; o[5] = (float)(1.0 / (double)k1f); o[6] = (float)log((double)k1f / k1); o[7] = (float)mid;
+}
+
+// Degenerate cell on a last knot: all weight on the knot itself (a = 1),
+// whatever t (every Bernstein coefficient of w_1 is one).
 __device__ void knot_weights(double *W) {
   for (int m = 0; m < 16; m++) W[m] = 0.0;
-  W[1 * 4 + 0] = 1.0;
+  for (int k = 0; k < 4; k++) W[1 * 4 + k] = 1.0;
 }
 
 __global__ void k_xcells(Stage S) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= S.nx) return;
-  if (i == S.nx - 1) {
-    S.xcell[2 * i] = S.lx[i];
-    S.xcell[2 * i + 1] = 0.0;
-    S.xcell32[2 * i] = (float)(1.0 / S.xk[i]);
-    S.xcell32[2 * i + 1] = 0.f;
+  if (i == S.nx - 1) {  // {ln x_i, 0, ln x_i, 1}: t = 0 and 1 - t = 1 exactly
+    S.xcell[4 * i] = S.lx[i];
+    S.xcell[4 * i + 1] = 0.0;
+    S.xcell[4 * i + 2] = S.lx[i];
+    S.xcell[4 * i + 3] = 1.0;
+    cell32(S.xk[i], S.xk[i], 0.0, INFINITY, S.xcell32 + 8 * i);
     knot_weights(S.xW + 16 * i);
     return;
   }
   double d = S.lx[i + 1] - S.lx[i];
-  S.xcell[2 * i] = S.lx[i];
-  S.xcell[2 * i + 1] = 1.0 / d;
-  S.xcell32[2 * i] = (float)(1.0 / S.xk[i]);
-  S.xcell32[2 * i + 1] = (float)(1.0 / d);
+  S.xcell[4 * i] = S.lx[i];
+  S.xcell[4 * i + 1] = 1.0 / d;
+  S.xcell[4 * i + 2] = S.lx[i + 1];
+  S.xcell[4 * i + 3] = 0.0;
+  cell32(S.xk[i], S.xk[i + 1], 1.0 / d, sqrt(S.xk[i] * S.xk[i + 1]), S.xcell32 + 8 * i);
   double aL = 1.0, bm = 0.0, dR = 1.0, gp = 0.0;
   if (i > 0) { aL = 0.5; bm = 0.5 * d / (S.lx[i] - S.lx[i - 1]); }
   if (i + 1 < S.nx - 1) { dR = 0.5; gp = 0.5 * d / (S.lx[i + 2] - S.lx[i + 1]); }
@@ -118,22 +135,28 @@ __global__ void k_qcells(Stage S) {
   if (j == S.nrows - 1) {  // top knot: degenerate cell nqc
     S.row_qc[j] = S.nqc;
     S.qc_row[S.nqc] = j;
-    S.qcell[2 * j] = S.lq[j];
-    S.qcell[2 * j + 1] = 0.0;
-    S.qcell32[2 * j] = (float)(1.0 / S.q2k[j]);
-    S.qcell32[2 * j + 1] = 0.f;
+    S.qcell[4 * j] = S.lq[j];
+    S.qcell[4 * j + 1] = 0.0;
+    S.qcell[4 * j + 2] = S.lq[j];
+    S.qcell[4 * j + 3] = 1.0;
+    cell32(S.q2k[j], S.q2k[j], 0.0, INFINITY, S.qcell32 + 8 * j);
     knot_weights(S.qW + 16 * S.nqc);
     return;
   }
-  if (j >= j1) { S.row_qc[j] = -1; return; }  // last row of a lower subgrid starts no cell
+  if (j >= j1) {  // last row of a lower subgrid starts no cell
+    S.row_qc[j] = -1;
+    for (int m = 0; m < 4; m++) S.qcell[4 * j + m] = 0.0;
+    return;
+  }
   int qc = qc0 + (j - j0);
   S.row_qc[j] = qc;
   S.qc_row[qc] = j;
   double d = S.lq[j + 1] - S.lq[j];
-  S.qcell[2 * j] = S.lq[j];
-  S.qcell[2 * j + 1] = 1.0 / d;
-  S.qcell32[2 * j] = (float)(1.0 / S.q2k[j]);
-  S.qcell32[2 * j + 1] = (float)(1.0 / d);
+  S.qcell[4 * j] = S.lq[j];
+  S.qcell[4 * j + 1] = 1.0 / d;
+  S.qcell[4 * j + 2] = S.lq[j + 1];
+  S.qcell[4 * j + 3] = 0.0;
+  cell32(S.q2k[j], S.q2k[j + 1], 1.0 / d, sqrt(S.q2k[j] * S.q2k[j + 1]), S.qcell32 + 8 * j);
   double aL = 1.0, bm = 0.0, dR = 1.0, gp = 0.0;
   if (j > j0) { aL = 0.5; bm = 0.5 * d / (S.lq[j] - S.lq[j - 1]); }
   if (j + 1 < j1) { dR = 0.5; gp = 0.5 * d / (S.lq[j + 2] - S.lq[j + 1]); }
@@ -141,7 +164,7 @@ __global__ void k_qcells(Stage S) {
 }
 
 // One thread per (q cell, x cell, flavour) slot, degenerate ones included:
-// expand sum_ab w_a(t) w_b(u) f_ab into monomials.
+// control point b[l][k] = sum_ab W_x[a][k] W_q[b][l] f_ab.
 __global__ void k_coef(Stage S) {
   long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   long long total = (long long)(S.nqc + 1) * S.nx * S.nf;
@@ -217,11 +240,11 @@ __global__ void k_scalars(Stage S) {
   int j = 0;  // same rule as the query search: the last row with Q^2_j <= v
   while (j + 1 < S.nrows && S.q2k[j + 1] <= v) j++;
   o[3] = (double)S.row_qc[j];
-  o[4] = (log(v) - S.qcell[2 * j]) * S.qcell[2 * j + 1];
+  o[4] = (log(v) - S.qcell[4 * j]) * S.qcell[4 * j + 1];
   o[5] = S.xcell[0];
   o[6] = S.xcell[1];
   o[7] = S.lq[S.nrows - 1];
-  o[8] = S.qcell[2 * top + 1];
+  o[8] = S.qcell[4 * top + 1];
   o[9] = log(1.01);
 }
 
@@ -335,14 +358,14 @@ extern "C" int pdf_load_grid(const pdf_grid_desc *d, pdf_grid **out) {
     S.aq2 = A.take<double>(na > 0 ? na : 1); S.aval = A.take<double>(na > 0 ? na : 1);
     S.first = A.take<int>(nsub); S.nq = A.take<int>(nsub);
     S.lx = A.take<double>(nx); S.lq = A.take<double>(nrows); S.alq = A.take<double>(na > 0 ? na : 1);
-    S.xcell = A.take<double>(2 * nx); S.qcell = A.take<double>(2 * nrows);
+    S.xcell = A.take<double>(4 * nx); S.qcell = A.take<double>(4 * nrows);
     S.xW = A.take<double>(16 * nx); S.qW = A.take<double>(16 * (nqc + 1));
     S.coef = A.take<double>((size_t)(nqc + 1) * nx * nf * 16);
     S.coef32 = A.take<float>((size_t)(nqc + 1) * nx * nf * 16);
     S.acell = A.take<double>(6 * (na > 0 ? na : 1));
     S.acell32 = A.take<float>(6 * (na > 0 ? na : 1));
     S.xthr32 = A.take<float>(nx); S.q2thr32 = A.take<float>(nrows); S.aq2thr32 = A.take<float>(na > 0 ? na : 1);
-    S.xcell32 = A.take<float>(2 * nx); S.qcell32 = A.take<float>(2 * nrows);
+    S.xcell32 = A.take<float>(8 * nx); S.qcell32 = A.take<float>(8 * nrows);
     S.row_qc = A.take<int>(nrows); S.qc_row = A.take<int>(nqc + 1);
     S.scal = A.take<double>(16);
     *inv = A.take<unsigned long long>(1);

@@ -2,15 +2,20 @@
 // shared by the evaluation kernels.
 //
 // Layout in HBM (all staged once by pdf_load_grid, PDFFlow Sec. 2.2):
-//   coef   [nqc+1][nx][nflav][16]  bicubic patch of every cell and flavour in
-//          monomial form, c[l*4 + k] multiplies t^k u^l, t and u the
-//          positions inside the cell in ln x and ln Q^2.  One evaluation
-//          reads one contiguous, 128-byte aligned block (FP64) or 64 bytes
-//          (FP32), instead of gathering 16 knots and forming weights.
+//   coef   [nqc+1][nx][nflav][16]  bicubic patch of every cell and flavour as
+//          its 4x4 Bezier control points b[l*4 + k] (Bernstein basis in t,
+//          the position inside the cell in ln x, index k; in u, ln Q^2,
+//          index l).  One evaluation reads one contiguous, 128-byte aligned
+//          block (FP64) or 64 bytes (FP32), instead of gathering 16 knots;
+//          the Bernstein weights are non-negative and sum to one, so the
+//          evaluation has no cancellation beyond that of the data.
 //   xk/q2k raw knots, searched as integer bit patterns (positive doubles
 //          order like their bits), so a cell choice never depends on a log.
-//   xcell  per x cell {ln x_i, 1/(ln x_{i+1} - ln x_i)}; qcell likewise per
-//          cell-start row; row_qc maps a cell-start row to its Q-cell index.
+//   xcell  per x cell {ln x_i, 1/d, ln x_{i+1}, 0}, d = ln x_{i+1} - ln x_i;
+//          qcell likewise per cell-start row; row_qc maps a cell-start row
+//          to its Q-cell index.  The position in a cell is carried as the
+//          pair t = (ln x - ln x_i)/d, 1 - t = (ln x_{i+1} - ln x)/d, each
+//          from its own knot, so the smaller keeps its relative precision.
 //          One extra, degenerate cell sits on the last x knot and one on the
 //          top Q knot ({ln knot, 0}: t = 0 there, and its patch holds only
 //          that knot's column or row), so a query exactly on the last knot
@@ -52,14 +57,14 @@ struct GridView {
   int xstep, qstep, astep;  // largest power of two <= n-1 (binary search start)
 
   const double *xk, *q2k;     // raw knots (bit patterns searched)
-  const double *xcell;        // [nx][2]
-  const double *qcell;        // [nrows][2] (cell-start rows and the top row)
+  const double *xcell;        // [nx][4]
+  const double *qcell;        // [nrows][4] (cell-start rows and the top row)
   const int *row_qc;          // [nrows]
   const double *coef;         // [nqc + 1][nx][nf][16]
   const float *coef32;
   const double *xW, *qW;      // [nx][16], [nqc + 1][16]
   const float *xthr32, *q2thr32;   // smallest float >= knot
-  const float *xcell32, *qcell32;  // {1/knot, 1/dln}
+  const float *xcell32, *qcell32;  // [n][8], see cell32 in grid.cu
 
   // alpha_s
   const double *aq2;          // [na]
@@ -106,27 +111,16 @@ __device__ __forceinline__ int search_cell(const K *keys, int n, int step, K key
 }
 
 // ---------------------------------------------------------------------------
-// patch evaluation: P_l(t) = sum_k c[l][k] t^k, F = sum_l P_l(t) u^l (Horner)
+// cubic Bernstein basis B_k(t) = C(3,k) t^k (1-t)^(3-k); B(0) = (1,0,0,0)
+// exactly, so a site on a knot picks the control point (= knot value) alone.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double patch(const double *c, double t, double u) {
-  const double2 *p = reinterpret_cast<const double2 *>(c);
-  double2 a0 = __ldg(p + 0), b0 = __ldg(p + 1), a1 = __ldg(p + 2), b1 = __ldg(p + 3);
-  double2 a2 = __ldg(p + 4), b2 = __ldg(p + 5), a3 = __ldg(p + 6), b3 = __ldg(p + 7);
-  double P0 = fma(fma(fma(b0.y, t, b0.x), t, a0.y), t, a0.x);
-  double P1 = fma(fma(fma(b1.y, t, b1.x), t, a1.y), t, a1.x);
-  double P2 = fma(fma(fma(b2.y, t, b2.x), t, a2.y), t, a2.x);
-  double P3 = fma(fma(fma(b3.y, t, b3.x), t, a3.y), t, a3.x);
-  return fma(fma(fma(P3, u, P2), u, P1), u, P0);
-}
-
-__device__ __forceinline__ float patch(const float *c, float t, float u) {
-  const float4 *p = reinterpret_cast<const float4 *>(c);
-  float4 q0 = __ldg(p + 0), q1 = __ldg(p + 1), q2 = __ldg(p + 2), q3 = __ldg(p + 3);
-  float P0 = fmaf(fmaf(fmaf(q0.w, t, q0.z), t, q0.y), t, q0.x);
-  float P1 = fmaf(fmaf(fmaf(q1.w, t, q1.z), t, q1.y), t, q1.x);
-  float P2 = fmaf(fmaf(fmaf(q2.w, t, q2.z), t, q2.y), t, q2.x);
-  float P3 = fmaf(fmaf(fmaf(q3.w, t, q3.z), t, q3.y), t, q3.x);
-  return fmaf(fmaf(fmaf(P3, u, P2), u, P1), u, P0);
+template <typename T>
+__device__ __forceinline__ void bernstein(T t, T s, T *B) {  // s = 1 - t
+  T t2 = t * t, s2 = s * s;
+  B[0] = s2 * s;
+  B[1] = T(3) * t * s2;
+  B[2] = T(3) * t2 * s;
+  B[3] = t2 * t;
 }
 
 // ---------------------------------------------------------------------------

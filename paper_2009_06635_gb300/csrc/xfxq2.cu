@@ -3,12 +3,19 @@
 // One warp owns a tile of 32 query points (16 events in the Monte Carlo
 // layout).  Phase 1 (lane = point): read x and Q^2 (coalesced), classify
 // against the grid edges, search the cells on the raw bit patterns (knots in
-// shared memory), take ln x and ln Q^2 once, and record the patch sites and
-// continuation parameters of the point; points are then ordered by class so
-// that lanes of one instruction take the same branch.  Phase 2 (lane =
-// (point, flavour) item): evaluate the patch at each site -- 16 coefficients,
-// 15 FMAs -- combine by class, and write the output; consecutive lanes write
-// consecutive outputs, so the [n][nflav] stores are coalesced.
+// shared memory), take ln x and ln Q^2 once, and record the Bernstein weights
+// of the patch sites and the continuation parameters of the point; points
+// are then ordered by class so that lanes of one instruction take the same
+// branch.  Phase 2 (items = (point, flavour)): contract the weights with the
+// cell's 16 control points, combine the sites by class, write the output.
+//   FP64: one lane per item, 16 FMAs on weight products formed once per
+//         point (the FP64 pipe is the bottleneck on GB300, so per-item FP64
+//         work is kept minimal; sites on knots collapse to 4- or 1-term sums).
+//   FP32: four lanes per item, each loading one float4 row of control
+//         points, reduced with two shuffles: one load instruction covers
+//         eight items, 512 contiguous bytes (the FP32 path is bound by the
+//         L1/L2 gather, not arithmetic).
+// Consecutive items are consecutive outputs, so [n][nflav] stores coalesce.
 #include <cmath>
 #include <type_traits>
 
@@ -35,17 +42,23 @@ struct Prec<float> {
 };
 
 // Per-warp record of the points of one tile, indexed by class-sorted slot.
+// W holds, per slot: for FP64 in-grid points the 16 products Bx[k] Bq[l] at
+// [l*4 + k]; otherwise (and always for FP32) Bx0 | Bx1 | Bq0 | Bq1.
 template <typename T>
 struct WarpRec {
   int cls[32], orig[32], xc0[32], xc1[32], qc0[32], qc1[32];
-  T t0[32], t1[32], u0[32], u1[32], px[32], pq[32], lr[32], as[32];
+  T W[16][33];  // padded: rows of one slot fall in different banks
+  T px[32], pq[32], lr[32], as[32];
 };
 
-// Sites and continuation parameters of one point.
+// Sites and continuation parameters of one point.  pq is the high-Q^2
+// continuation parameter, or rho = Q^2/Q2min for the low-Q^2 classes.
+// ts0 = 1 - t0 and us0 = 1 - u0, carried separately so that whichever of a
+// position and its complement is small keeps its relative precision.
 template <typename T>
 struct PointSites {
   int cls, xc0, xc1, qc0, qc1;
-  T t0, t1, u0, u1, px, pq, lr;
+  T t0, t1, u0, u1, ts0, us0, px, pq, lr;
 };
 
 // ---- FP64 classification and sites ---------------------------------------
@@ -54,6 +67,7 @@ __device__ __forceinline__ PointSites<double> sites(const GridView &g, const lon
   PointSites<double> r;
   r.xc0 = r.xc1 = r.qc0 = r.qc1 = 0;
   r.t0 = r.t1 = r.u0 = r.u1 = r.px = r.pq = r.lr = 0.0;
+  r.ts0 = r.us0 = 1.0;
   bool valid = (x > 0.0) && (x <= g.xlast) && (q2 > 0.0) && (q2 < INFINITY);
   if (!valid) { r.cls = C_INVALID; return r; }
   bool lowx = x < g.x0, lowq = q2 < g.q2min, highq = q2 > g.q2max;
@@ -61,7 +75,10 @@ __device__ __forceinline__ PointSites<double> sites(const GridView &g, const lon
   if (!lowx) {
     int i = search_cell(xkeys, g.nx, g.xstep, __double_as_longlong(x));
     r.xc0 = i;
-    r.t0 = (lx - g.xcell[2 * i]) * g.xcell[2 * i + 1];
+    const double2 c0 = *reinterpret_cast<const double2 *>(g.xcell + 4 * i);
+    const double2 c1 = *reinterpret_cast<const double2 *>(g.xcell + 4 * i + 2);
+    r.t0 = (lx - c0.x) * c0.y;
+    r.ts0 = fma(c1.x - lx, c0.y, c1.y);
   } else {
     r.xc1 = 1;
     r.px = (lx - g.lx0) * g.idx0;
@@ -69,7 +86,11 @@ __device__ __forceinline__ PointSites<double> sites(const GridView &g, const lon
   if (!lowq && !highq) {
     int j = search_cell(qkeys, g.nrows, g.qstep, __double_as_longlong(q2));
     r.qc0 = g.row_qc[j];
-    r.u0 = (log(q2) - g.qcell[2 * j]) * g.qcell[2 * j + 1];
+    const double2 c0 = *reinterpret_cast<const double2 *>(g.qcell + 4 * j);
+    const double2 c1 = *reinterpret_cast<const double2 *>(g.qcell + 4 * j + 2);
+    const double lq = log(q2);
+    r.u0 = (lq - c0.x) * c0.y;
+    r.us0 = fma(c1.x - lq, c0.y, c1.y);
   } else if (highq) {
     r.qc0 = g.nqc;
     r.qc1 = g.top_qc;
@@ -88,20 +109,37 @@ __device__ __forceinline__ PointSites<double> sites(const GridView &g, const lon
 // ---- FP32 classification and sites -----------------------------------------
 // The comparisons against rounded-up/down float thresholds decide exactly as
 // FP64 comparisons of the float input against the FP64 knots would.  ln x
-// enters only relative to a knot, ln(x / x_i) = log1p(x * (1/x_i) - 1), so no
-// large absolute logarithm is rounded to FP32.
+// enters only relative to the nearer end knot k of the cell,
+//   ln(x / k) = log1p((x - kf) / kf) + ln(kf / k)   (kf = k rounded to float,
+// x - kf exact for x within a factor 2 of kf), so the small one of t and
+// 1 - t keeps its relative precision: where xf varies steeply (x -> 1, where
+// (1 - x)^b makes the value sensitive to t) the position is still good to a
+// float ulp.  No absolute logarithm of x is rounded to FP32.
+__device__ __forceinline__ void cell_pos32(const float *c, float v, float &t, float &ts) {
+  const float4 a = __ldg(reinterpret_cast<const float4 *>(c));
+  const float4 b = __ldg(reinterpret_cast<const float4 *>(c) + 1);
+  if (v < b.w) {
+    t = (log1pf((v - a.x) * a.y) + a.z) * a.w;
+    ts = 1.f - t;
+  } else {
+    ts = -(log1pf((v - b.x) * b.y) + b.z) * a.w;
+    t = 1.f - ts;
+  }
+}
+
 __device__ __forceinline__ PointSites<float> sites(const GridView &g, const int *xkeys,
                                                    const int *qkeys, float x, float q2) {
   PointSites<float> r;
   r.xc0 = r.xc1 = r.qc0 = r.qc1 = 0;
   r.t0 = r.t1 = r.u0 = r.u1 = r.px = r.pq = r.lr = 0.f;
+  r.ts0 = r.us0 = 1.f;
   bool valid = (x > 0.f) && (x <= g.xlast_rd) && (q2 > 0.f) && (q2 < INFINITY);
   if (!valid) { r.cls = C_INVALID; return r; }
   bool lowx = x < g.x0_ru, lowq = q2 < g.q2min_ru, highq = q2 > g.q2max_rd;
   if (!lowx) {
     int i = search_cell(xkeys, g.nx, g.xstep, __float_as_int(x));
     r.xc0 = i;
-    r.t0 = log1pf(fmaf(x, g.xcell32[2 * i], -1.f)) * g.xcell32[2 * i + 1];
+    cell_pos32(g.xcell32 + 8 * i, x, r.t0, r.ts0);
   } else {
     r.xc1 = 1;
     r.px = logf(x * g.x0inv32) * g.idx0_32;
@@ -109,7 +147,7 @@ __device__ __forceinline__ PointSites<float> sites(const GridView &g, const int 
   if (!lowq && !highq) {
     int j = search_cell(qkeys, g.nrows, g.qstep, __float_as_int(q2));
     r.qc0 = g.row_qc[j];
-    r.u0 = log1pf(fmaf(q2, g.qcell32[2 * j], -1.f)) * g.qcell32[2 * j + 1];
+    cell_pos32(g.qcell32 + 8 * j, q2, r.u0, r.us0);
   } else if (highq) {
     r.qc0 = g.nqc;
     r.qc1 = g.top_qc;
@@ -167,32 +205,170 @@ __host__ __device__ inline size_t keys_bytes(int nkeys, size_t ksize) {
 
 enum { MODE_POINTS = 0, MODE_MC = 1 };
 
-// Evaluate one (point slot, column) item from the warp record.
-template <typename T>
-__device__ __forceinline__ T eval_item(const GridView &g, const WarpRec<T> &R, int p, int col,
-                                       T ln101) {
-  const T *cb = Prec<T>::coef(g) + (size_t)col * 16;
-  const int cl = R.cls[p];
+// ---- FP64 item evaluation (one lane per item) ----------------------------
+__device__ __forceinline__ double dot_w16(const double *c, const WarpRec<double> &R, int p) {
+  const double2 *q = reinterpret_cast<const double2 *>(c);
+  double2 v = __ldg(q);
+  double acc = R.W[0][p] * v.x;
+  acc = fma(R.W[1][p], v.y, acc);
+#pragma unroll
+  for (int m = 1; m < 8; m++) {
+    v = __ldg(q + m);
+    acc = fma(R.W[2 * m][p], v.x, acc);
+    acc = fma(R.W[2 * m + 1][p], v.y, acc);
+  }
+  return acc;
+}
+// site with t general, u general: sum_l Bq[l] sum_k Bx[k] b[l][k]
+__device__ __forceinline__ double site_tu(const double *c, const WarpRec<double> &R, int p, int a, int b) {
+  double f = 0.0;
+#pragma unroll
+  for (int l = 0; l < 4; l++) {
+    const double2 *q = reinterpret_cast<const double2 *>(c + 4 * l);
+    double2 v0 = __ldg(q), v1 = __ldg(q + 1);
+    double r = R.W[4 * a][p] * v0.x;
+    r = fma(R.W[4 * a + 1][p], v0.y, r);
+    r = fma(R.W[4 * a + 2][p], v1.x, r);
+    r = fma(R.W[4 * a + 3][p], v1.y, r);
+    f = l == 0 ? R.W[8 + 4 * b][p] * r : fma(R.W[8 + 4 * b + l][p], r, f);
+  }
+  return f;
+}
+// site on an x knot (t = 0): sum_l Bq[l] b[l][0]
+__device__ __forceinline__ double site_u(const double *c, const WarpRec<double> &R, int p, int b) {
+  double f = R.W[8 + 4 * b][p] * __ldg(c);
+  f = fma(R.W[8 + 4 * b + 1][p], __ldg(c + 4), f);
+  f = fma(R.W[8 + 4 * b + 2][p], __ldg(c + 8), f);
+  return fma(R.W[8 + 4 * b + 3][p], __ldg(c + 12), f);
+}
+// site on a Q knot (u = 0): sum_k Bx[k] b[0][k]
+__device__ __forceinline__ double site_t(const double *c, const WarpRec<double> &R, int p, int a) {
+  const double2 *q = reinterpret_cast<const double2 *>(c);
+  double2 v0 = __ldg(q), v1 = __ldg(q + 1);
+  double f = R.W[4 * a][p] * v0.x;
+  f = fma(R.W[4 * a + 1][p], v0.y, f);
+  f = fma(R.W[4 * a + 2][p], v1.x, f);
+  return fma(R.W[4 * a + 3][p], v1.y, f);
+}
+
+__device__ __forceinline__ double eval_item64(const GridView &g, const WarpRec<double> &R, int p, int col) {
+  const double *cb = g.coef + (size_t)col * 16;
   const size_t stride = (size_t)g.nf * 16;
-  if (cl == C_IN)
-    return patch(cb + ((size_t)R.qc0[p] * g.nx + R.xc0[p]) * stride, R.t0[p], R.u0[p]);
-  auto F = [&](int a, int b) -> T {
+  auto C = [&](int a, int b) {
     int xc = a ? R.xc1[p] : R.xc0[p];
     int qc = b ? R.qc1[p] : R.qc0[p];
-    T t = a ? R.t1[p] : R.t0[p];
-    T u = b ? R.u1[p] : R.u0[p];
-    return patch(cb + ((size_t)qc * g.nx + xc) * stride, t, u);
+    return cb + ((size_t)qc * g.nx + xc) * stride;
   };
-  return combine<T>(cl, R.px[p], R.pq[p], R.lr[p], ln101, F);
+  switch (R.cls[p]) {
+    case C_IN: return dot_w16(C(0, 0), R, p);
+    case C_LOWX:  // sites (x0, Q^2), (x1, Q^2): t = 0
+      return pair_rule(site_u(C(0, 0), R, p, 0), site_u(C(1, 0), R, p, 0), R.px[p]);
+    case C_HIGHQ:  // sites (x, Q2max), (x, knot below): u = 0
+      return pair_rule(site_t(C(0, 0), R, p, 0), site_t(C(0, 1), R, p, 0), R.pq[p]);
+    case C_LOWQ:  // sites (x, Q2min): u = 0; (x, 1.01 Q2min): general
+      return lowq_rule(site_t(C(0, 0), R, p, 0), site_tu(C(0, 1), R, p, 0, 1), R.pq[p], R.lr[p], g.ln101);
+    case C_LOWX_HIGHQ: {  // all four sites are knots
+      double a = pair_rule(__ldg(C(0, 0)), __ldg(C(0, 1)), R.pq[p]);
+      double b = pair_rule(__ldg(C(1, 0)), __ldg(C(1, 1)), R.pq[p]);
+      return pair_rule(a, b, R.px[p]);
+    }
+    case C_LOWX_LOWQ: {
+      double a = lowq_rule(__ldg(C(0, 0)), site_u(C(0, 1), R, p, 1), R.pq[p], R.lr[p], g.ln101);
+      double b = lowq_rule(__ldg(C(1, 0)), site_u(C(1, 1), R, p, 1), R.pq[p], R.lr[p], g.ln101);
+      return pair_rule(a, b, R.px[p]);
+    }
+    default: return NAN;
+  }
+}
+
+// ---- FP32 evaluation -------------------------------------------------------
+// One lane, whole patch: sum_l Bq[l] sum_k Bx[k] b[l][k] (four float4 rows).
+__device__ __forceinline__ float site32_full(const float *c, const WarpRec<float> &R, int p, int a, int b) {
+  const float4 *q = reinterpret_cast<const float4 *>(c);
+  float f = 0.f;
+#pragma unroll
+  for (int l = 0; l < 4; l++) {
+    float4 v = __ldg(q + l);
+    float rr = R.W[4 * a][p] * v.x;
+    rr = fmaf(R.W[4 * a + 1][p], v.y, rr);
+    rr = fmaf(R.W[4 * a + 2][p], v.z, rr);
+    rr = fmaf(R.W[4 * a + 3][p], v.w, rr);
+    f = fmaf(R.W[8 + 4 * b + l][p], rr, f);
+  }
+  return f;
+}
+
+__device__ __forceinline__ float eval_point32(const GridView &g, const WarpRec<float> &R, int p, int col) {
+  const float *cb = g.coef32 + (size_t)col * 16;
+  const size_t stride = (size_t)g.nf * 16;
+  auto F = [&](int a, int b) {
+    int xc = a ? R.xc1[p] : R.xc0[p];
+    int qc = b ? R.qc1[p] : R.qc0[p];
+    return site32_full(cb + ((size_t)qc * g.nx + xc) * stride, R, p, a, b);
+  };
+  return combine<float>(R.cls[p], R.px[p], R.pq[p], R.lr[p], g.ln101_32, F);
+}
+
+// Four lanes per item, lane r owns row l = r of the control points.
+__device__ __forceinline__ float site32(const float *c, const WarpRec<float> &R, int p, int a, int b,
+                                        int r, unsigned gm) {
+  float4 v = __ldg(reinterpret_cast<const float4 *>(c) + r);
+  float part = R.W[4 * a][p] * v.x;
+  part = fmaf(R.W[4 * a + 1][p], v.y, part);
+  part = fmaf(R.W[4 * a + 2][p], v.z, part);
+  part = fmaf(R.W[4 * a + 3][p], v.w, part);
+  part *= R.W[8 + 4 * b + r][p];
+  part += __shfl_xor_sync(gm, part, 1);
+  part += __shfl_xor_sync(gm, part, 2);
+  return part;
+}
+
+__device__ __forceinline__ float eval_item32(const GridView &g, const WarpRec<float> &R, int p, int col,
+                                             int r, unsigned gm) {
+  const float *cb = g.coef32 + (size_t)col * 16;
+  const size_t stride = (size_t)g.nf * 16;
+  auto F = [&](int a, int b) {
+    int xc = a ? R.xc1[p] : R.xc0[p];
+    int qc = b ? R.qc1[p] : R.qc0[p];
+    return site32(cb + ((size_t)qc * g.nx + xc) * stride, R, p, a, b, r, gm);
+  };
+  return combine<float>(R.cls[p], R.px[p], R.pq[p], R.lr[p], g.ln101_32, F);
+}
+
+// Write the Bernstein weights of a point's sites into its record slot.
+template <typename T>
+__device__ __forceinline__ void store_weights(WarpRec<T> &R, int slot, const PointSites<T> &ps,
+                                              const GridView &g) {
+  T bx0[4], bx1[4], bq0[4], bq1[4];
+  bernstein<T>(ps.t0, ps.ts0, bx0);
+  bernstein<T>(ps.t1, T(1) - ps.t1, bx1);
+  bernstein<T>(ps.u0, ps.us0, bq0);
+  bernstein<T>(ps.u1, T(1) - ps.u1, bq1);
+  if (sizeof(T) == 8 && ps.cls == C_IN) {
+#pragma unroll
+    for (int l = 0; l < 4; l++)
+#pragma unroll
+      for (int k = 0; k < 4; k++) R.W[l * 4 + k][slot] = bx0[k] * bq0[l];
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      R.W[k][slot] = bx0[k];
+      R.W[4 + k][slot] = bx1[k];
+      R.W[8 + k][slot] = bq0[k];
+      R.W[12 + k][slot] = bq1[k];
+    }
+  }
 }
 
 // MODE_POINTS: points xa[n], qa[n]; out[n][ncol] for columns col0..col0+ncol-1.
 // MODE_MC:     events xa[n] (x1), xb[n] (x2), Q^2 = x1 x2 s; out[n][2 nf + 1].
 template <typename T, int MODE>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 3)
 k_xf(GridView g, const T *__restrict__ xa, const T *__restrict__ qa, const T *__restrict__ xb,
      T s, long long n, int col0, int ncol, T *__restrict__ out) {
   using K = typename Prec<T>::K;
+  constexpr int LPI = sizeof(T) == 8 ? 1 : 4;  // lanes per item
+  constexpr int IPI = 32 / LPI;                // items per warp instruction (FP64 loop)
   extern __shared__ __align__(16) unsigned char smem[];
   K *xkeys = reinterpret_cast<K *>(smem);
   K *qkeys = reinterpret_cast<K *>(smem + keys_bytes(g.nx, sizeof(K)));
@@ -209,8 +385,9 @@ k_xf(GridView g, const T *__restrict__ xa, const T *__restrict__ qa, const T *__
   WarpRec<T> &R = recs[warp];
   const int per_tile = MODE == MODE_MC ? 16 : 32;
   const int per = MODE == MODE_MC ? 2 * g.nf + 1 : ncol;  // outputs per tile unit
-  const int dp = 32 / per, dc = 32 - dp * per;
-  const T ln101 = sizeof(T) == 8 ? (T)g.ln101 : (T)g.ln101_32;
+  const int dp = IPI / per, dc = IPI - dp * per;
+  const int r = lane & (LPI - 1);
+  const unsigned gm = LPI == 1 ? 1u << lane : 0xFu << (lane & ~3);
   const long long ntiles = (n + per_tile - 1) / per_tile;
   const long long nwarps = (long long)gridDim.x * kWarps;
 
@@ -252,28 +429,55 @@ k_xf(GridView g, const T *__restrict__ xa, const T *__restrict__ qa, const T *__
     }
     R.cls[slot] = ps.cls; R.orig[slot] = lane;
     R.xc0[slot] = ps.xc0; R.xc1[slot] = ps.xc1; R.qc0[slot] = ps.qc0; R.qc1[slot] = ps.qc1;
-    R.t0[slot] = ps.t0; R.t1[slot] = ps.t1; R.u0[slot] = ps.u0; R.u1[slot] = ps.u1;
     R.px[slot] = ps.px; R.pq[slot] = ps.pq; R.lr[slot] = ps.lr;
+    if (present && ps.cls != C_INVALID) store_weights<T>(R, slot, ps, g);
     if (MODE == MODE_MC && (lane & 1) == 0) R.as[lane >> 1] = present ? alphas_eval(g, akeys, q2) : T(0);
     __syncwarp();
 
-    // ---- phase 2: lane = (point, column) item ----
+    // ---- phase 2, FP32: per point, lanes over (column, row) ----
+    if constexpr (sizeof(T) == 4) {
+      const WarpRec<float> &RF = reinterpret_cast<const WarpRec<float> &>(R);
+      if (MODE == MODE_POINTS && ncol == 1) {  // one column: a lane per point
+        if (lane < ne) out[e0 + RF.orig[lane]] = eval_point32(g, RF, lane, col0);
+      } else {
+        const int nc = MODE == MODE_MC ? g.nf : ncol;
+        const int npts = MODE == MODE_MC ? 2 * ne : ne;
+        for (int q = 0; q < npts; q++) {  // warp-uniform: no divergence by class
+          const long long ob = MODE == MODE_POINTS ? (e0 + RF.orig[q]) * (long long)ncol
+                                                   : (e0 + (q >> 1)) * (long long)per + (q & 1) * g.nf;
+          for (int k = lane; k < 4 * nc; k += 32) {
+            const int f = k >> 2;
+            const float v = eval_item32(g, RF, q, col0 + f, r, gm);
+            if (r == 0) out[ob + f] = v;
+          }
+        }
+        if (MODE == MODE_MC && lane < ne) out[(e0 + lane) * (long long)per + 2 * g.nf] = RF.as[lane];
+      }
+      __syncwarp();
+      continue;
+    }
+
+    // ---- phase 2, FP64: items = (point, column), one lane each ----
     const int nitems = ne * per;
-    int p = lane / per, c = lane - (lane / per) * per;
-    for (int k = lane; k < nitems; k += 32) {
+    int p = (lane / LPI) / per, c = (lane / LPI) - ((lane / LPI) / per) * per;
+    for (int k = lane / LPI; k < nitems; k += IPI) {
       T v;
       long long o;
+      int pt, col;
       if (MODE == MODE_POINTS) {
-        v = eval_item<T>(g, R, p, col0 + c, ln101);
+        pt = p;
+        col = col0 + c;
         o = (e0 + R.orig[p]) * (long long)per + c;
       } else {
-        if (c == 2 * g.nf) {
-          v = R.as[p];
-        } else {
-          const int side = c >= g.nf;
-          v = eval_item<T>(g, R, 2 * p + side, c - side * g.nf, ln101);
-        }
+        const int side = c >= g.nf;
+        pt = 2 * p + side;
+        col = c - side * g.nf;
         o = (e0 + p) * (long long)per + c;
+      }
+      if (MODE == MODE_MC && c == 2 * g.nf) {
+        v = R.as[p];
+      } else {
+        v = (T)eval_item64(g, reinterpret_cast<const WarpRec<double> &>(R), pt, col);
       }
       out[o] = v;
       c += dc;
