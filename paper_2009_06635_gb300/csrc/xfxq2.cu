@@ -79,6 +79,8 @@ __device__ __forceinline__ PointSites<double> sites(const GridView &g, const lon
     const double2 c1 = *reinterpret_cast<const double2 *>(g.xcell + 4 * i + 2);
     r.t0 = (lx - c0.x) * c0.y;
     r.ts0 = fma(c1.x - lx, c0.y, c1.y);
+    if (r.t0 <= r.ts0) r.ts0 = 1.0 - r.t0;  // the larger one from the smaller:
+    else r.t0 = 1.0 - r.ts0;                // exact at both knots
   } else {
     r.xc1 = 1;
     r.px = (lx - g.lx0) * g.idx0;
@@ -91,6 +93,8 @@ __device__ __forceinline__ PointSites<double> sites(const GridView &g, const lon
     const double lq = log(q2);
     r.u0 = (lq - c0.x) * c0.y;
     r.us0 = fma(c1.x - lq, c0.y, c1.y);
+    if (r.u0 <= r.us0) r.us0 = 1.0 - r.u0;
+    else r.u0 = 1.0 - r.us0;
   } else if (highq) {
     r.qc0 = g.nqc;
     r.qc1 = g.top_qc;
@@ -282,10 +286,12 @@ __device__ __forceinline__ double eval_item64(const GridView &g, const WarpRec<d
 }
 
 // ---- FP32 evaluation -------------------------------------------------------
-// One lane, whole patch: sum_l Bq[l] sum_k Bx[k] b[l][k] (four float4 rows).
+// One lane, whole patch: sum_l Bq[l] sum_k Bx[k] b[l][k] (four float4 rows),
+// rounded in the same order as the four-lane version ((p0 + p1) + (p2 + p3)),
+// so one flavour alone and all flavours give identical bits.
 __device__ __forceinline__ float site32_full(const float *c, const WarpRec<float> &R, int p, int a, int b) {
   const float4 *q = reinterpret_cast<const float4 *>(c);
-  float f = 0.f;
+  float pl[4];
 #pragma unroll
   for (int l = 0; l < 4; l++) {
     float4 v = __ldg(q + l);
@@ -293,9 +299,9 @@ __device__ __forceinline__ float site32_full(const float *c, const WarpRec<float
     rr = fmaf(R.W[4 * a + 1][p], v.y, rr);
     rr = fmaf(R.W[4 * a + 2][p], v.z, rr);
     rr = fmaf(R.W[4 * a + 3][p], v.w, rr);
-    f = fmaf(R.W[8 + 4 * b + l][p], rr, f);
+    pl[l] = __fmul_rn(rr, R.W[8 + 4 * b + l][p]);
   }
-  return f;
+  return (pl[0] + pl[1]) + (pl[2] + pl[3]);
 }
 
 __device__ __forceinline__ float eval_point32(const GridView &g, const WarpRec<float> &R, int p, int col) {
@@ -317,7 +323,7 @@ __device__ __forceinline__ float site32(const float *c, const WarpRec<float> &R,
   part = fmaf(R.W[4 * a + 1][p], v.y, part);
   part = fmaf(R.W[4 * a + 2][p], v.z, part);
   part = fmaf(R.W[4 * a + 3][p], v.w, part);
-  part *= R.W[8 + 4 * b + r][p];
+  part = __fmul_rn(part, R.W[8 + 4 * b + r][p]);
   part += __shfl_xor_sync(gm, part, 1);
   part += __shfl_xor_sync(gm, part, 2);
   return part;
@@ -363,7 +369,7 @@ __device__ __forceinline__ void store_weights(WarpRec<T> &R, int slot, const Poi
 // MODE_POINTS: points xa[n], qa[n]; out[n][ncol] for columns col0..col0+ncol-1.
 // MODE_MC:     events xa[n] (x1), xb[n] (x2), Q^2 = x1 x2 s; out[n][2 nf + 1].
 template <typename T, int MODE>
-__global__ void __launch_bounds__(kThreads, 3)
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 8 ? 3 : 4)
 k_xf(GridView g, const T *__restrict__ xa, const T *__restrict__ qa, const T *__restrict__ xb,
      T s, long long n, int col0, int ncol, T *__restrict__ out) {
   using K = typename Prec<T>::K;
@@ -445,10 +451,29 @@ k_xf(GridView g, const T *__restrict__ xa, const T *__restrict__ qa, const T *__
         for (int q = 0; q < npts; q++) {  // warp-uniform: no divergence by class
           const long long ob = MODE == MODE_POINTS ? (e0 + RF.orig[q]) * (long long)ncol
                                                    : (e0 + (q >> 1)) * (long long)per + (q & 1) * g.nf;
-          for (int k = lane; k < 4 * nc; k += 32) {
-            const int f = k >> 2;
-            const float v = eval_item32(g, RF, q, col0 + f, r, gm);
-            if (r == 0) out[ob + f] = v;
+          if (RF.cls[q] == C_IN) {
+            // the point's column blocks are contiguous: lane k reads row k & 3
+            // of column k >> 2 at cell_base + 4 k
+            const float *cbp = g.coef32 + ((size_t)RF.qc0[q] * g.nx + RF.xc0[q]) * g.nf * 16 + col0 * 16;
+            const float b0 = RF.W[0][q], b1 = RF.W[1][q], b2 = RF.W[2][q], b3 = RF.W[3][q];
+            const float bq = RF.W[8 + r][q];
+            for (int k = lane; k < 4 * nc; k += 32) {
+              const float4 v = __ldg(reinterpret_cast<const float4 *>(cbp) + k);
+              float part = b0 * v.x;
+              part = fmaf(b1, v.y, part);
+              part = fmaf(b2, v.z, part);
+              part = fmaf(b3, v.w, part);
+              part = __fmul_rn(part, bq);
+              part += __shfl_xor_sync(gm, part, 1);
+              part += __shfl_xor_sync(gm, part, 2);
+              if (r == 0) out[ob + (k >> 2)] = part;
+            }
+          } else {
+            for (int k = lane; k < 4 * nc; k += 32) {
+              const int f = k >> 2;
+              const float v = eval_item32(g, RF, q, col0 + f, r, gm);
+              if (r == 0) out[ob + f] = v;
+            }
           }
         }
         if (MODE == MODE_MC && lane < ne) out[(e0 + lane) * (long long)per + 2 * g.nf] = RF.as[lane];
