@@ -158,6 +158,31 @@ PDF_API int pdf_mc_event_f32(const pdf_grid *grid, const float *x1, const float 
 PDF_API int xfxq2_all_flavours_host(const pdf_grid *grid, const double *x, const double *q2, size_t n,
                                     double *out, double *alphas_out);
 
+/* No-allocation variant of xfxq2_all_flavours_host (the paper has no
+ * counterpart).  For callers that must not have the library allocate device
+ * memory: a generator or integrator that calls the PDF inside its own loop,
+ * where a cudaMalloc/cudaFree would synchronise the device and stall it; a
+ * program whose device memory is wholly managed by another pool or framework;
+ * a process that allows no allocation after start-up.  The host variant above
+ * allocates its staging buffers on first use; this one stages through a fixed
+ * 16 MiB array (2^21 doubles) compiled into the library, which every GPU that
+ * loads the library's kernels holds until the process exits.
+ *   - n must not exceed 2^21 / (3 + nflav) points (131072 for 13 flavours);
+ *     larger batches are rejected with PDF_ERR_ARG (split them).
+ *   - x, q2, out (and alphas_out if not NULL) are HOST memory, as for the host
+ *     variant; the copies and kernels run on `stream`, and the call returns
+ *     when the outputs are in host memory.  It calls no allocator.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) and caches it; make that first call on each
+ *     device before any stream capture.
+ *   - All calls share the one array and it keeps the last call's contents
+ *     (each call writes every word it reads, so nothing needs clearing).
+ *     Calls whose work overlaps on the GPU -- from several threads or on
+ *     several streams of one device -- race on it and must be serialised by
+ *     the caller. */
+PDF_API int xfxq2_all_flavours_host_noalloc(const pdf_grid *grid, const double *x, const double *q2,
+                                            size_t n, double *out, double *alphas_out, cudaStream_t stream);
+
 /* Invalid-point counter: read (synchronous) and reset. */
 PDF_API int pdf_grid_invalid_count(const pdf_grid *grid, unsigned long long *count);
 PDF_API int pdf_grid_reset_invalid_count(pdf_grid *grid);
