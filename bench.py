@@ -36,6 +36,7 @@ sys.path.insert(0, str(ROOT))
 METRIC = "PDF evals/s (points×flavours) FP64 vs FP32 vs surrogate at stated max rel err"
 N_POINTS = 10_000_000
 MC_EVENTS = 1_000_000
+ADJ_POINTS = 1_000_000
 WORKLOAD = ("three Q subgrids (12/15/25 Q knots split at Q = 1.51 and 4.92 GeV, Q in [1, 1e5] GeV), "
             "196 x knots in [1e-9, 1], 13 flavours; 1e7 queries per rank, x log-uniform in [1e-10, 1], "
             "Q log-uniform in [1, 2e5] GeV (15% outside the grid); all flavours + alpha_s per point")
@@ -362,6 +363,19 @@ def our_arm(args):
     ms_mc32 = run_timed(lambda: P.pdf_mc_event(G, x1f, x2f, float(np.float32(s2)), out=mco32),
                         args.steps, 2, world, sync)
 
+    # adjoint: 1e6 points of the same law, standard-normal cotangents on all
+    # flavours; gradients in x, Q^2 and every knot value (zeroed each step)
+    ax, aq, acot = S.adjoint_inputs(ADJ_POINTS, nf, 5 + 1000 * rank, 6 + 1000 * rank)
+    axd, aqd, acd = torch.from_numpy(ax).to(dev), torch.from_numpy(aq).to(dev), torch.from_numpy(acot).to(dev)
+    agx, agq = torch.empty_like(axd), torch.empty_like(aqd)
+    agv = torch.zeros((G.nrows, G.nx, nf), dtype=torch.float64, device=dev)
+
+    def step_adj():
+        agv.zero_()
+        P.xfxq2_all_flavours_vjp(G, axd, aqd, acd, agx, agq, agv)
+
+    ms_adj = run_timed(step_adj, args.steps, 2, world, sync)
+
     # end to end through the C ABI with host buffers (pinned), copies timed
     hx = torch.from_numpy(x).pin_memory()
     hq = torch.from_numpy(q2).pin_memory()
@@ -428,6 +442,9 @@ def our_arm(args):
                               "events": MC_EVENTS},
             "mc_event_fp32": {"value": world * MC_EVENTS * (2 * nf + 1) / (ms_mc32 * 1e-3),
                               "ms_per_step": ms_mc32, "events": MC_EVENTS},
+            "adjoint_fp64": {"value": world * ADJ_POINTS * nf / (ms_adj * 1e-3), "ms_per_step": ms_adj,
+                             "points": ADJ_POINTS, "unit": "(point, flavour) gradients/s",
+                             "outputs": "d/dx, d/dQ^2 per point and d/d(knot values), FP64 atomics"},
         },
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

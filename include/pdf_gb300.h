@@ -183,6 +183,26 @@ PDF_API int xfxq2_all_flavours_host(const pdf_grid *grid, const double *x, const
 PDF_API int xfxq2_all_flavours_host_noalloc(const pdf_grid *grid, const double *x, const double *q2,
                                             size_t n, double *out, double *alphas_out, cudaStream_t stream);
 
+/* Vector-Jacobian product of xfxq2_all_flavours (growth beyond the paper:
+ * gradients for fitting a PDF).  With L = sum_p sum_f cot[p][f] xf_f(x_p, Q2_p):
+ *   grad_x[p] = dL/dx_p, grad_q2[p] = dL/dQ2_p        ([n] FP64, either may be NULL);
+ *   grad_values[rows][nx][nflav] += dL/d(knot values)  (may be NULL; accumulated
+ *                                   with FP64 atomics, so the summation order --
+ *                                   and the last bits -- vary between runs).
+ * cot is [n][nflav] FP64.  All pointers are device memory; enqueued on
+ * `stream`.  Invalid points get NaN gradients and add nothing to
+ * grad_values.  A point exactly on the last x (top Q^2) knot gets the
+ * one-sided derivative of the last cell. */
+PDF_API int xfxq2_all_flavours_vjp(const pdf_grid *grid, const double *x, const double *q2, size_t n,
+                                   const double *cot, double *grad_x, double *grad_q2, double *grad_values,
+                                   cudaStream_t stream);
+
+/* Replace the grid's knot values with `values` ([rows][nx][nflav] FP64,
+ * DEVICE memory) and re-stage the patch coefficients on `stream` (the knots
+ * and subgrids stay).  For fitting loops: no host round trip.  Work on other
+ * streams that reads the grid must be ordered after it by the caller. */
+PDF_API int pdf_grid_set_values(pdf_grid *grid, const double *values, cudaStream_t stream);
+
 /* Invalid-point counter: read (synchronous) and reset. */
 PDF_API int pdf_grid_invalid_count(const pdf_grid *grid, unsigned long long *count);
 PDF_API int pdf_grid_reset_invalid_count(pdf_grid *grid);

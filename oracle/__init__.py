@@ -67,7 +67,7 @@ def _load():
     lib.og_xfxq2.restype = None
     lib.og_dxfxq2.argtypes = [P, i32, i32, P, P, P, i64, P, i32]
     lib.og_dxfxq2.restype = None
-    lib.og_knot_grad.argtypes = [P, P, P, i64, P, P]
+    lib.og_knot_grad.argtypes = [P, P, P, i64, P, P, P]
     lib.og_knot_grad.restype = None
     lib.og_knots_read.argtypes = [P, dbl, dbl, i32, P, i32]
     lib.og_knots_read.restype = i32
@@ -172,12 +172,16 @@ class OracleGrid:
                           x.shape[0], _ptr(d), nthreads)
         return d
 
-    def knot_grad(self, x, q2, cot):
+    def knot_grad(self, x, q2, cot, with_abs: bool = False):
+        """dL/d(values) for L = sum cot * xf; with_abs also returns the sum of
+        the contributions' magnitudes."""
         x, q2 = _f64(x).ravel(), _f64(q2).ravel()
         cot = _f64(cot).reshape(x.shape[0], self.nflav)
         g = np.zeros_like(self._val)
-        _load().og_knot_grad(self._h, _ptr(x), _ptr(q2), x.shape[0], _ptr(cot), _ptr(g))
-        return g
+        ga = np.zeros_like(self._val) if with_abs else None
+        _load().og_knot_grad(self._h, _ptr(x), _ptr(q2), x.shape[0], _ptr(cot), _ptr(g),
+                             _ptr(ga) if with_abs else None)
+        return (g, ga) if with_abs else g
 
     def knots_read(self, x: float, q2: float, col: int):
         buf = np.zeros((512, 2), dtype=np.int32)

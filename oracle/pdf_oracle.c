@@ -402,9 +402,11 @@ void og_dxfxq2(const og *g, int wrt, int ncols, const int *cols, const double *x
 /* Knot-value gradient of L = sum_p sum_f cot[p][f] xf_f(x_p, Q2_p):
  * gvals[row][ix][f] += dL / d values[row][ix][f].  Each contribution is a
  * forward-mode derivative seeded on one knot that the evaluation read.
- * Points with a NaN value contribute nothing.  Serial. */
+ * Points with a NaN value contribute nothing.  gabs (may be NULL) receives
+ * the sum of the contributions' magnitudes, the scale of the sum's rounding.
+ * Serial. */
 void og_knot_grad(const og *g, const double *x, const double *q2, long n, const double *cot,
-                  double *gvals) {
+                  double *gvals, double *gabs) {
   int rec[2 * 512];
   for (long p = 0; p < n; p++) {
     for (int f = 0; f < g->nf; f++) {
@@ -418,6 +420,7 @@ void og_knot_grad(const og *g, const double *x, const double *q2, long n, const 
         s.wrt = WRT_KNOT; s.row = rec[2 * k]; s.ix = rec[2 * k + 1];
         double d = xf_one(g, x[p], q2[p], f, &s).d;
         gvals[((size_t)s.row * g->nx + s.ix) * g->nf + f] += w * d;
+        if (gabs) gabs[((size_t)s.row * g->nx + s.ix) * g->nf + f] += fabs(w * d);
       }
     }
   }

@@ -59,6 +59,8 @@ SIGNATURES = {
     "pdf_mc_event_f32": (I32, [P, P, P, F32, SZ, P, P]),
     "xfxq2_all_flavours_host": (I32, [P, P, P, SZ, P, P]),
     "xfxq2_all_flavours_host_noalloc": (I32, [P, P, P, SZ, P, P, P]),
+    "xfxq2_all_flavours_vjp": (I32, [P, P, P, SZ, P, P, P, P, P]),
+    "pdf_grid_set_values": (I32, [P, P, P]),
     "pdf_grid_invalid_count": (I32, [P, ctypes.POINTER(ctypes.c_ulonglong)]),
     "pdf_grid_reset_invalid_count": (I32, [P]),
     "pdf_last_error": (ctypes.c_char_p, []),

@@ -430,6 +430,7 @@ extern "C" int pdf_load_grid(const pdf_grid_desc *d, pdf_grid **out) {
   v.nx = nx; v.nrows = nrows; v.nf = nf; v.nxc = nxc; v.nqc = nqc; v.na = na; v.nsub = nsub;
   v.xstep = pow2_floor(nx - 1); v.qstep = pow2_floor(nrows - 1); v.astep = na > 1 ? pow2_floor(na - 1) : 0;
   v.xk = S.xk; v.q2k = S.q2k; v.xcell = S.xcell; v.qcell = S.qcell; v.row_qc = S.row_qc;
+  v.qc_row = S.qc_row; v.vals = const_cast<double *>(S.vals);
   v.coef = S.coef; v.coef32 = S.coef32; v.xW = S.xW; v.qW = S.qW;
   v.xthr32 = S.xthr32; v.q2thr32 = S.q2thr32; v.xcell32 = S.xcell32; v.qcell32 = S.qcell32;
   v.aq2 = S.aq2; v.acell = S.acell; v.acell32 = S.acell32; v.aq2thr32 = S.aq2thr32;
@@ -483,6 +484,22 @@ extern "C" int pdf_grid_invalid_count(const pdf_grid *g, unsigned long long *cou
   cudaError_t e = cudaMemcpy(count, g->v.invalid, sizeof *count, cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return set_error(PDF_ERR_CUDA, "pdf_grid_invalid_count: %s", cudaGetErrorString(e));
   return PDF_OK;
+}
+
+extern "C" int pdf_grid_set_values(pdf_grid *g, const double *values, cudaStream_t stream) {
+  if (!g || !values) return set_error(PDF_ERR_NULL, "pdf_grid_set_values: NULL argument");
+  const GridView &v = g->v;
+  size_t bytes = (size_t)v.nrows * v.nx * v.nf * sizeof(double);
+  cudaError_t e = cudaMemcpyAsync(v.vals, values, bytes, cudaMemcpyDeviceToDevice, stream);
+  if (e != cudaSuccess) return set_error(PDF_ERR_CUDA, "pdf_grid_set_values: %s", cudaGetErrorString(e));
+  Stage S{};
+  S.nx = v.nx; S.nrows = v.nrows; S.nf = v.nf; S.nqc = v.nqc; S.nxc = v.nxc;
+  S.vals = v.vals; S.qc_row = const_cast<int *>(v.qc_row);
+  S.xW = const_cast<double *>(v.xW); S.qW = const_cast<double *>(v.qW);
+  S.coef = const_cast<double *>(v.coef); S.coef32 = const_cast<float *>(v.coef32);
+  long long ncoef = (long long)(v.nqc + 1) * v.nx * v.nf;
+  k_coef<<<(unsigned)((ncoef + 127) / 128), 128, 0, stream>>>(S);
+  return check_launch("pdf_grid_set_values");
 }
 
 extern "C" int pdf_grid_reset_invalid_count(pdf_grid *g) {

@@ -60,6 +60,8 @@ struct GridView {
   const double *xcell;        // [nx][4]
   const double *qcell;        // [nrows][4] (cell-start rows and the top row)
   const int *row_qc;          // [nrows]
+  const int *qc_row;          // [nqc + 1] first row of each Q cell
+  double *vals;               // [nrows][nx][nf] device copy of the knot values
   const double *coef;         // [nqc + 1][nx][nf][16]
   const float *coef32;
   const double *xW, *qW;      // [nx][16], [nqc + 1][16]

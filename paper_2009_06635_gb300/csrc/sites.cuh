@@ -1,0 +1,183 @@
+// sites.cuh -- per-point classification, cell search, patch-site positions
+// and alpha_s, shared by the evaluation and adjoint kernels.
+#pragma once
+
+#include <cmath>
+
+#include "pdf_internal.cuh"
+
+namespace pdfgb {
+
+template <typename T>
+struct Prec;
+template <>
+struct Prec<double> {
+  using K = long long;
+  static __device__ __forceinline__ K key(double v) { return __double_as_longlong(v); }
+  static __device__ __forceinline__ const double *coef(const GridView &g) { return g.coef; }
+};
+template <>
+struct Prec<float> {
+  using K = int;
+  static __device__ __forceinline__ K key(float v) { return __float_as_int(v); }
+  static __device__ __forceinline__ const float *coef(const GridView &g) { return g.coef32; }
+};
+
+// Sites and continuation parameters of one point.  pq is the high-Q^2
+// continuation parameter, or rho = Q^2/Q2min for the low-Q^2 classes.
+// ts0 = 1 - t0 and us0 = 1 - u0, carried separately so that whichever of a
+// position and its complement is small keeps its relative precision.
+template <typename T>
+struct PointSites {
+  int cls, xc0, xc1, qc0, qc1;
+  T t0, t1, u0, u1, ts0, us0, px, pq, lr;
+};
+
+// ---- FP64 classification and sites ---------------------------------------
+__device__ __forceinline__ PointSites<double> sites(const GridView &g, const long long *xkeys,
+                                                    const long long *qkeys, double x, double q2) {
+  PointSites<double> r;
+  r.xc0 = r.xc1 = r.qc0 = r.qc1 = 0;
+  r.t0 = r.t1 = r.u0 = r.u1 = r.px = r.pq = r.lr = 0.0;
+  r.ts0 = r.us0 = 1.0;
+  bool valid = (x > 0.0) && (x <= g.xlast) && (q2 > 0.0) && (q2 < INFINITY);
+  if (!valid) { r.cls = C_INVALID; return r; }
+  bool lowx = x < g.x0, lowq = q2 < g.q2min, highq = q2 > g.q2max;
+  double lx = log(x);
+  if (!lowx) {
+    int i = search_cell(xkeys, g.nx, g.xstep, __double_as_longlong(x));
+    r.xc0 = i;
+    const double2 c0 = *reinterpret_cast<const double2 *>(g.xcell + 4 * i);
+    const double2 c1 = *reinterpret_cast<const double2 *>(g.xcell + 4 * i + 2);
+    r.t0 = (lx - c0.x) * c0.y;
+    r.ts0 = fma(c1.x - lx, c0.y, c1.y);
+    if (r.t0 <= r.ts0) r.ts0 = 1.0 - r.t0;  // the larger one from the smaller:
+    else r.t0 = 1.0 - r.ts0;                // exact at both knots
+  } else {
+    r.xc1 = 1;
+    r.px = (lx - g.lx0) * g.idx0;
+  }
+  if (!lowq && !highq) {
+    int j = search_cell(qkeys, g.nrows, g.qstep, __double_as_longlong(q2));
+    r.qc0 = g.row_qc[j];
+    const double2 c0 = *reinterpret_cast<const double2 *>(g.qcell + 4 * j);
+    const double2 c1 = *reinterpret_cast<const double2 *>(g.qcell + 4 * j + 2);
+    const double lq = log(q2);
+    r.u0 = (lq - c0.x) * c0.y;
+    r.us0 = fma(c1.x - lq, c0.y, c1.y);
+    if (r.u0 <= r.us0) r.us0 = 1.0 - r.u0;
+    else r.u0 = 1.0 - r.us0;
+  } else if (highq) {
+    r.qc0 = g.nqc;
+    r.qc1 = g.top_qc;
+    r.pq = -(log(q2) - g.lq2max) * g.idq_top;
+  } else {
+    r.qc1 = g.q101_qc;
+    r.u1 = g.q101_u;
+    r.pq = q2 / g.q2min;
+    r.lr = log(r.pq);
+  }
+  r.cls = lowx ? (highq ? C_LOWX_HIGHQ : lowq ? C_LOWX_LOWQ : C_LOWX)
+               : (highq ? C_HIGHQ : lowq ? C_LOWQ : C_IN);
+  return r;
+}
+
+// ---- FP32 classification and sites -----------------------------------------
+// The comparisons against rounded-up/down float thresholds decide exactly as
+// FP64 comparisons of the float input against the FP64 knots would.  ln x
+// enters only relative to the nearer end knot k of the cell,
+//   ln(x / k) = log1p((x - kf) / kf) + ln(kf / k)   (kf = k rounded to float,
+// x - kf exact for x within a factor 2 of kf), so the small one of t and
+// 1 - t keeps its relative precision: where xf varies steeply (x -> 1, where
+// (1 - x)^b makes the value sensitive to t) the position is still good to a
+// float ulp.  No absolute logarithm of x is rounded to FP32.
+__device__ __forceinline__ void cell_pos32(const float *c, float v, float &t, float &ts) {
+  const float4 a = __ldg(reinterpret_cast<const float4 *>(c));
+  const float4 b = __ldg(reinterpret_cast<const float4 *>(c) + 1);
+  if (v < b.w) {
+    t = (log1pf((v - a.x) * a.y) + a.z) * a.w;
+    ts = 1.f - t;
+  } else {
+    ts = -(log1pf((v - b.x) * b.y) + b.z) * a.w;
+    t = 1.f - ts;
+  }
+}
+
+__device__ __forceinline__ PointSites<float> sites(const GridView &g, const int *xkeys,
+                                                   const int *qkeys, float x, float q2) {
+  PointSites<float> r;
+  r.xc0 = r.xc1 = r.qc0 = r.qc1 = 0;
+  r.t0 = r.t1 = r.u0 = r.u1 = r.px = r.pq = r.lr = 0.f;
+  r.ts0 = r.us0 = 1.f;
+  bool valid = (x > 0.f) && (x <= g.xlast_rd) && (q2 > 0.f) && (q2 < INFINITY);
+  if (!valid) { r.cls = C_INVALID; return r; }
+  bool lowx = x < g.x0_ru, lowq = q2 < g.q2min_ru, highq = q2 > g.q2max_rd;
+  if (!lowx) {
+    int i = search_cell(xkeys, g.nx, g.xstep, __float_as_int(x));
+    r.xc0 = i;
+    cell_pos32(g.xcell32 + 8 * i, x, r.t0, r.ts0);
+  } else {
+    r.xc1 = 1;
+    r.px = logf(x * g.x0inv32) * g.idx0_32;
+  }
+  if (!lowq && !highq) {
+    int j = search_cell(qkeys, g.nrows, g.qstep, __float_as_int(q2));
+    r.qc0 = g.row_qc[j];
+    cell_pos32(g.qcell32 + 8 * j, q2, r.u0, r.us0);
+  } else if (highq) {
+    r.qc0 = g.nqc;
+    r.qc1 = g.top_qc;
+    r.pq = -logf(q2 * g.q2maxinv32) * g.idq_top32;
+  } else {
+    r.qc1 = g.q101_qc;
+    r.u1 = g.q101_u32;
+    r.pq = q2 / g.q2min32;
+    r.lr = logf(r.pq);
+  }
+  r.cls = lowx ? (highq ? C_LOWX_HIGHQ : lowq ? C_LOWX_LOWQ : C_LOWX)
+               : (highq ? C_HIGHQ : lowq ? C_LOWQ : C_IN);
+  return r;
+}
+
+// ---- alpha_s (Sec. 2.3): constant outside, log-cubic inside ----------------
+__device__ __forceinline__ double alphas_eval(const GridView &g, const long long *akeys, double q2) {
+  if (!((q2 > 0.0) && (q2 < INFINITY))) return NAN;
+  if (q2 < g.aq2lo) return g.as_lo;
+  if (q2 > g.aq2hi) return g.as_hi;
+  int j = search_cell(akeys, g.na, g.astep, __double_as_longlong(q2));
+  const double *c = g.acell + 6 * j;
+  double u = (log(q2) - c[0]) * c[1];
+  return fma(fma(fma(c[5], u, c[4]), u, c[3]), u, c[2]);
+}
+__device__ __forceinline__ float alphas_eval(const GridView &g, const int *akeys, float q2) {
+  if (!((q2 > 0.f) && (q2 < INFINITY))) return NAN;
+  if (q2 < g.aq2lo_ru) return g.as_lo32;
+  if (q2 > g.aq2hi_rd) return g.as_hi32;
+  int j = search_cell(akeys, g.na, g.astep, __float_as_int(q2));
+  const float *c = g.acell32 + 6 * j;
+  float u = log1pf(fmaf(q2, c[0], -1.f)) * c[1];
+  return fmaf(fmaf(fmaf(c[5], u, c[4]), u, c[3]), u, c[2]);
+}
+
+template <typename T>
+__device__ __forceinline__ void load_keys(const GridView &g, typename Prec<T>::K *keys, int which);
+
+template <>
+__device__ __forceinline__ void load_keys<double>(const GridView &g, long long *keys, int which) {
+  const double *src = which == 0 ? g.xk : which == 1 ? g.q2k : g.aq2;
+  int n = which == 0 ? g.nx : which == 1 ? g.nrows : g.na;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) keys[i] = __double_as_longlong(src[i]);
+}
+template <>
+__device__ __forceinline__ void load_keys<float>(const GridView &g, int *keys, int which) {
+  const float *src = which == 0 ? g.xthr32 : which == 1 ? g.q2thr32 : g.aq2thr32;
+  int n = which == 0 ? g.nx : which == 1 ? g.nrows : g.na;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) keys[i] = __float_as_int(src[i]);
+}
+
+__host__ __device__ inline size_t keys_bytes(int nkeys, size_t ksize) {
+  return ((nkeys * ksize + 15) / 16) * 16;
+}
+
+
+}  // namespace pdfgb

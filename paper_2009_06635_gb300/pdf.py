@@ -36,10 +36,12 @@ def _dev_ptr(t: torch.Tensor, dtype, name: str) -> ctypes.c_void_p:
 class Grid:
     """A loaded PDF set (owns the device-side handle)."""
 
-    def __init__(self, handle: int, pids, device: torch.device):
+    def __init__(self, handle: int, pids, device: torch.device, nx: int, nrows: int):
         self._h = ctypes.c_void_p(handle)
         self.pids = list(pids)
         self.nflav = len(self.pids)
+        self.nx = nx
+        self.nrows = nrows
         self.device = device
 
     @property
@@ -96,7 +98,7 @@ def pdf_load_grid(grid=None, *, x_knots=None, nq=None, q2_knots=None, pids=None,
     h = ctypes.c_void_p(None)
     with torch.cuda.device(dev):
         check(lib.pdf_load_grid(ctypes.byref(d), ctypes.byref(h)), "pdf_load_grid")
-    return Grid(h.value, pa.tolist(), dev)
+    return Grid(h.value, pa.tolist(), dev, int(xk.shape[0]), int(q2k.shape[0]))
 
 
 def _out(out, shape, like: torch.Tensor):
@@ -185,3 +187,60 @@ def xfxq2_all_flavours_host(grid: Grid, x, q2, out=None, alphas_out=None, with_a
                                           ctypes.c_void_p(qs.data_ptr()), xs.shape[0],
                                           ctypes.c_void_p(out.data_ptr()), aptr), "xfxq2_all_flavours_host")
     return out if alphas_out is None else (out, alphas_out)
+
+
+def pdf_grid_set_values(grid: Grid, values: torch.Tensor):
+    """Replace the grid's knot values ([rows][nx][nflav] float64 CUDA tensor)
+    and re-stage its patch coefficients on the current stream."""
+    check(_native.load().pdf_grid_set_values(grid.handle, _dev_ptr(values, torch.float64, "values"),
+                                             _stream_handle(values.device)), "pdf_grid_set_values")
+
+
+def xfxq2_all_flavours_vjp(grid: Grid, x: torch.Tensor, q2: torch.Tensor, cot: torch.Tensor,
+                           grad_x=None, grad_q2=None, grad_values=None):
+    """Gradients of L = sum(cot * xf): fills grad_x [n], grad_q2 [n] (either
+    may be None) and accumulates into grad_values [rows][nx][nflav] (None to
+    skip).  Returns (grad_x, grad_q2, grad_values)."""
+    _check_pair(x, q2)
+    if tuple(cot.shape) != (x.shape[0], grid.nflav):
+        raise ValueError(f"cot must be [n][nflav], got {tuple(cot.shape)}")
+    dt = torch.float64
+    opt = lambda t, name: _dev_ptr(t, dt, name) if t is not None else None  # noqa: E731
+    check(_native.load().xfxq2_all_flavours_vjp(
+        grid.handle, _dev_ptr(x, dt, "x"), _dev_ptr(q2, dt, "q2"), x.shape[0], _dev_ptr(cot, dt, "cot"),
+        opt(grad_x, "grad_x"), opt(grad_q2, "grad_q2"), opt(grad_values, "grad_values"),
+        _stream_handle(x.device)), "xfxq2_all_flavours_vjp")
+    return grad_x, grad_q2, grad_values
+
+
+class XfxQ2AllFlavours(torch.autograd.Function):
+    """xf for all flavours, differentiable in x, Q^2 and the knot values.
+
+    forward(grid, x, q2, values): if `values` is given it is staged into the
+    grid first (so the output is a function of it); backward runs the
+    library's adjoint kernel."""
+
+    @staticmethod
+    def forward(ctx, grid, x, q2, values):
+        if values is not None:
+            pdf_grid_set_values(grid, values.detach())
+        out = xfxq2_all_flavours(grid, x.detach(), q2.detach())
+        ctx.grid = grid
+        ctx.vshape = None if values is None else tuple(values.shape)
+        ctx.save_for_backward(x, q2)
+        return out
+
+    @staticmethod
+    def backward(ctx, gout):
+        x, q2 = ctx.saved_tensors
+        _, nx, nq, nv = ctx.needs_input_grad
+        gx = torch.empty_like(x) if nx else None
+        gq = torch.empty_like(q2) if nq else None
+        gv = torch.zeros(ctx.vshape, dtype=torch.float64, device=x.device) if (nv and ctx.vshape) else None
+        xfxq2_all_flavours_vjp(ctx.grid, x.detach(), q2.detach(), gout.contiguous(), gx, gq, gv)
+        return None, gx, gq, gv
+
+
+def xfxq2_all_flavours_diff(grid: Grid, x: torch.Tensor, q2: torch.Tensor, values: torch.Tensor = None):
+    """Differentiable all-flavour evaluation (see XfxQ2AllFlavours)."""
+    return XfxQ2AllFlavours.apply(grid, x, q2, values)

@@ -1,0 +1,126 @@
+"""GPU adjoint (vector-Jacobian product of xfxq2_all_flavours) against the
+oracle's forward-mode gradients and against central finite differences, and
+the torch.autograd.Function built on it.  Workload: points of the
+three-subgrid query law with standard-normal cotangents (the adjoint config);
+the paper has no counterpart."""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+P = pytest.importorskip("paper_2009_06635_gb300")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    torch.cuda.set_device(0)
+
+
+@pytest.fixture(scope="module")
+def full(synth, oracle_mod):
+    g = synth.grid_full()
+    return g, P.pdf_load_grid(g), oracle_mod.OracleGrid(g)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def run_vjp(G, x, q2, cot, with_values=True):
+    xd, qd, cd = dev(x), dev(q2), dev(cot)
+    gx, gq = torch.empty_like(xd), torch.empty_like(qd)
+    gv = torch.zeros((G.nrows, G.nx, G.nflav), dtype=torch.float64, device="cuda") if with_values else None
+    P.xfxq2_all_flavours_vjp(G, xd, qd, cd, gx, gq, gv)
+    torch.cuda.synchronize()
+    return gx.cpu().numpy(), gq.cpu().numpy(), (gv.cpu().numpy() if with_values else None)
+
+
+def min_log_spacing(k):
+    d = np.diff(np.log(k))
+    return d[d > 0].min()
+
+
+def test_gradients_match_oracle(full, synth):
+    g, G, og = full
+    x, q2, cot = synth.adjoint_inputs(4000, g.nflav, 5, 6)
+    gx, gq, gv = run_vjp(G, x, q2, cot)
+    dx = og.dxfxq2(x, q2, "x")
+    dq = og.dxfxq2(x, q2, "q2")
+    v, s, fl = og.xfxq2(x, q2)
+    ok = ~fl.any(axis=1)
+    want_x = (cot * dx).sum(axis=1)
+    want_q = (cot * dq).sum(axis=1)
+    # scale: the terms of the sum, plus the data-mass scale of a derivative
+    # in ln x (ln Q^2), s / (coordinate * smallest knot spacing)
+    sx = np.abs(cot * dx).sum(axis=1) + (np.abs(cot) * s).sum(axis=1) / (x * min_log_spacing(g.x_knots))
+    sq = np.abs(cot * dq).sum(axis=1) + (np.abs(cot) * s).sum(axis=1) / (q2 * min_log_spacing(g.q2_knots))
+    ex = np.abs(gx - want_x) / sx
+    eq = np.abs(gq - want_q) / sq
+    assert ex[ok].max() < 1e-10, ex[ok].max()
+    assert eq[ok].max() < 1e-10, eq[ok].max()
+    go, gabs = og.knot_grad(x[ok], q2[ok], cot[ok], with_abs=True)
+    gv_ok = run_vjp(G, x[ok], q2[ok], cot[ok])[2]
+    err = np.abs(gv_ok - go)
+    # where no evaluation touches a knot (gabs = 0) the GPU must add exactly nothing
+    assert (err <= 1e-10 * gabs + 1e-300).all(), (err / np.maximum(gabs, 1e-300)).max()
+
+
+def test_gradients_match_central_differences(full, synth):
+    g, G, og = full
+    x, q2, cot = synth.adjoint_inputs(3000, g.nflav, 15, 16)
+    gx, gq, _ = run_vjp(G, x, q2, cot, with_values=False)
+    h = 1e-6
+    f = lambda a, b: P.xfxq2_all_flavours(G, dev(a), dev(b)).cpu().numpy()  # noqa: E731
+    fdx = ((f(x * (1 + h), q2) - f(x * (1 - h), q2)) * cot).sum(axis=1) / (2 * h * x)
+    fdq = ((f(x, q2 * (1 + h)) - f(x, q2 * (1 - h))) * cot).sum(axis=1) / (2 * h * q2)
+    # skip points whose difference stencil straddles a knot, an edge, a threshold
+    # or the 1.01 Q2min site (the interpolant is C1 inside a subgrid only)
+    kx = np.log(g.x_knots)
+    kq = np.log(np.concatenate([g.q2_knots, [1.01 * g.q2_knots[0]]]))
+    far_x = np.min(np.abs(np.log(x)[:, None] - kx[None, :]), axis=1) > 3 * h
+    far_q = np.min(np.abs(np.log(q2)[:, None] - kq[None, :]), axis=1) > 3 * h
+    v, s, _ = og.xfxq2(x, q2)
+    scale_x = np.abs(gx) + (np.abs(cot) * s).sum(axis=1) / x * 1e-3
+    scale_q = np.abs(gq) + (np.abs(cot) * s).sum(axis=1) / q2 * 1e-3
+    ok = far_x & far_q
+    assert ok.mean() > 0.9
+    assert (np.abs(fdx - gx)[ok] / scale_x[ok]).max() < 1e-4
+    assert (np.abs(fdq - gq)[ok] / scale_q[ok]).max() < 1e-4
+
+
+def test_invalid_points_give_nan_and_no_knot_gradient(full):
+    g, G, og = full
+    x = np.array([0.0, 0.5, -1.0, 0.3])
+    q2 = np.array([10.0, -1.0, 10.0, 10.0])
+    cot = np.ones((4, g.nflav))
+    gx, gq, gv = run_vjp(G, x, q2, cot)
+    assert np.isnan(gx[:3]).all() and np.isnan(gq[:3]).all()
+    assert np.isfinite(gx[3]) and np.isfinite(gq[3])
+    _, _, gv1 = run_vjp(G, x[3:], q2[3:], cot[3:])
+    assert np.allclose(gv, gv1, rtol=1e-14, atol=0)
+
+
+def test_autograd_function_and_value_restaging(full, synth):
+    g, G, og = full
+    x, q2 = synth.ingrid_samples(g, 2000, 17)
+    cot = np.random.default_rng(18).standard_normal((2000, g.nflav))
+    vals = torch.from_numpy(g.values).cuda().requires_grad_(True)
+    xd = dev(x).requires_grad_(True)
+    qd = dev(q2).requires_grad_(True)
+    out = P.xfxq2_all_flavours_diff(G, xd, qd, vals)
+    (out * dev(cot)).sum().backward()
+    go = og.knot_grad(x, q2, cot)
+    assert np.allclose(vals.grad.cpu().numpy(), go, rtol=1e-10, atol=1e-12 * np.abs(go).max())
+    want_x = (cot * og.dxfxq2(x, q2, "x")).sum(axis=1)
+    assert np.allclose(xd.grad.cpu().numpy(), want_x, rtol=1e-9, atol=1e-12 * np.abs(want_x).max())
+    # staging new values reproduces a freshly loaded grid bit for bit
+    new = g.values * 1.5 + 0.25
+    P.pdf_grid_set_values(G, torch.from_numpy(new).cuda())
+    fresh = P.pdf_load_grid(x_knots=g.x_knots, nq=g.nq, q2_knots=g.q2_knots, pids=g.pids, values=new,
+                            as_q2=g.as_q2, as_vals=g.as_vals)
+    a = P.xfxq2_all_flavours(G, dev(x), dev(q2)).cpu().numpy()
+    b = P.xfxq2_all_flavours(fresh, dev(x), dev(q2)).cpu().numpy()
+    assert np.array_equal(a, b)
+    P.pdf_grid_set_values(G, torch.from_numpy(g.values).cuda())  # restore for other tests
