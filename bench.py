@@ -120,8 +120,9 @@ class Clocks:
         self.path.parent.mkdir(exist_ok=True)
         self.fh = open(self.path, "w")
         self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                      "--format=csv,noheader,nounits", "-lms", "200"],
+                                      "--format=csv,noheader,nounits", "-lms", "50"],
                                      stdout=self.fh, stderr=subprocess.DEVNULL)
+        time.sleep(0.5)  # let the sampler start before the measured work
 
     def stop(self):
         if not self.proc:
@@ -370,9 +371,12 @@ def our_arm(args):
     agx, agq = torch.empty_like(axd), torch.empty_like(aqd)
     agv = torch.zeros((G.nrows, G.nx, nf), dtype=torch.float64, device=dev)
 
-    def step_adj():
+    from paper_2009_06635_gb300.sharding import allreduce_knot_gradient
+
+    def step_adj():  # each rank its own block; the knot gradient is summed over ranks
         agv.zero_()
         P.xfxq2_all_flavours_vjp(G, axd, aqd, acd, agx, agq, agv)
+        allreduce_knot_gradient(agv)
 
     ms_adj = run_timed(step_adj, args.steps, 2, world, sync)
 
@@ -465,7 +469,7 @@ def our_arm(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--points", type=int, default=N_POINTS)
