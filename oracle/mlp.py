@@ -1,0 +1,116 @@
+"""CPU oracle for the learned surrogate -- TEST INFRASTRUCTURE.
+
+Only the tests, the smoke check and the CPU-baseline leg of the benchmark
+use it.  Plain numpy FP64, written from the network's definition, sharing
+no code with the CUDA kernels (paper_2009_06635_gb300/csrc/surrogate.cu).
+
+The surrogate (no counterpart in the paper; the growth axis that replaces
+the interpolator where a network is accurate enough) maps a query point to
+all flavours:
+  z   = (2 (ln x - lx_lo)/(lx_hi - lx_lo) - 1, 2 (ln Q^2 - lq_lo)/(lq_hi - lq_lo) - 1)
+  a_j = pi (F[j,0] z_0 + F[j,1] z_1),  phi = [sin a_0..15, cos a_0..15]   (32 features)
+  h1  = silu(W1 phi + b1), h2..h4 = silu(W h + b)   (width 128)
+  y   = W5 h4 + b5                                    (one output per flavour)
+  xf_f = c_f sinh(y_f)     (inverse of the training target y_f = asinh(xf_f / c_f))
+silu(v) = v sigmoid(v) = v (1 + tanh(v/2)) / 2.
+Training loss: mean over batch and flavours of (y - asinh(xf/c))^2.
+
+With bf16=True the oracle rounds to bfloat16 exactly where the GPU keeps
+bfloat16 values (weights, features, activations, and the backward signals
+that feed matrix products), so the comparison isolates accumulation order.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+WIDTH = 128
+NFEAT = 16  # frequencies; features = 2 * NFEAT
+
+
+def bf16(a):
+    """Round to bfloat16 (round to nearest even), returned as float64."""
+    a32 = np.ascontiguousarray(np.asarray(a, dtype=np.float64).astype(np.float32))
+    u = a32.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def silu(v):
+    return 0.5 * v * (1.0 + np.tanh(0.5 * v))
+
+
+def dsilu(v):
+    s = 0.5 * (1.0 + np.tanh(0.5 * v))
+    return s + v * s * (1.0 - s)
+
+
+def unpack(params, nflav):
+    """Flat parameter vector -> [(W, b)] for the five layers, W as [out][in]."""
+    shapes = [(WIDTH, 2 * NFEAT), (WIDTH, WIDTH), (WIDTH, WIDTH), (WIDTH, WIDTH), (nflav, WIDTH)]
+    out, k = [], 0
+    p = np.asarray(params, dtype=np.float64)
+    for (o, i) in shapes:
+        W = p[k:k + o * i].reshape(o, i)
+        k += o * i
+        b = p[k:k + o]
+        k += o
+        out.append((W, b))
+    assert k == p.size, (k, p.size)
+    return out
+
+
+def features(x, q2, freq, bounds, bf=False):
+    lx_lo, lx_hi, lq_lo, lq_hi = bounds
+    z0 = 2.0 * (np.log(x) - lx_lo) / (lx_hi - lx_lo) - 1.0
+    z1 = 2.0 * (np.log(q2) - lq_lo) / (lq_hi - lq_lo) - 1.0
+    a = np.pi * (np.outer(z0, freq[:, 0]) + np.outer(z1, freq[:, 1]))
+    phi = np.concatenate([np.sin(a), np.cos(a)], axis=1)
+    return bf16(phi) if bf else phi
+
+
+def forward(params, x, q2, freq, bounds, nflav, bf=False):
+    """-> (y [n][nflav], cache for backward)."""
+    layers = unpack(params, nflav)
+    r = bf16 if bf else (lambda t: t)
+    h = features(x, q2, freq, bounds, bf)
+    cache = {"h": [h], "z": []}
+    for li, (W, b) in enumerate(layers):
+        z = h @ r(W).T + b
+        if li < 4:
+            cache["z"].append(z)
+            h = r(silu(z))
+            cache["h"].append(h)
+        else:
+            y = z
+    return y, cache
+
+
+def target(xf, scale):
+    return np.arcsinh(np.asarray(xf) / scale)
+
+
+def loss_grad(params, x, q2, xf, scale, freq, bounds, nflav, bf=False):
+    """Mean-square loss on asinh targets and its gradient (flat, FP64)."""
+    layers = unpack(params, nflav)
+    r = bf16 if bf else (lambda t: t)
+    y, c = forward(params, x, q2, freq, bounds, nflav, bf)
+    t = target(xf, scale)
+    n = y.shape[0]
+    diff = y - t
+    loss = float(np.mean(diff * diff))
+    g = r(2.0 * diff / (n * nflav))  # dL/dy
+    grads = [None] * 5
+    for li in range(4, -1, -1):
+        W, b = layers[li]
+        h_in = c["h"][li]
+        grads[li] = (g.T @ h_in, g.sum(axis=0))
+        if li > 0:
+            dh = g @ r(W)
+            g = r(dh * dsilu(c["z"][li - 1]))
+    flat = np.concatenate([np.concatenate([gw.ravel(), gb]) for gw, gb in grads])
+    return loss, flat
+
+
+def predict(params, x, q2, scale, freq, bounds, nflav, bf=False):
+    y, _ = forward(params, x, q2, freq, bounds, nflav, bf)
+    return scale * np.sinh(y)

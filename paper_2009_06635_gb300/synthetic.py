@@ -215,3 +215,31 @@ def ingrid_samples(grid: Grid, n: int, seed: int):
     lx = r.uniform(np.log(grid.x_knots[0]), np.log(grid.x_knots[-1]), n)
     lq2 = r.uniform(np.log(grid.q2_knots[0]), np.log(grid.q2_knots[-1]), n)
     return np.exp(lx), np.exp(lq2)
+
+
+# --------------------------------------------------------------------------
+# Learned surrogate: seeded initial parameters (random numbers the training
+# draws, passed to the GPU and to any checker alike)
+# --------------------------------------------------------------------------
+
+SURROGATE_WIDTH = 128
+SURROGATE_NFREQ = 16
+
+
+def surrogate_init(nflav: int, seed: int = 9, freq_sigma: float = 2.0):
+    """-> (params float32 flat, freq float32 [16][2]).
+
+    params: W1 [128][32], b1 [128], W2..W4 [128][128], b2..b4, W5 [nflav][128],
+    b5 [nflav]; weights uniform in +-sqrt(6/fan_in) (He-uniform), biases zero.
+    freq: the fixed Fourier-feature frequencies, normal with sigma freq_sigma."""
+    r = _rng(seed)
+    W = SURROGATE_WIDTH
+    shapes = [(W, 2 * SURROGATE_NFREQ), (W, W), (W, W), (W, W), (nflav, W)]
+    parts = []
+    for (o, i) in shapes:
+        lim = np.sqrt(6.0 / i)
+        parts.append(r.uniform(-lim, lim, o * i))
+        parts.append(np.zeros(o))
+    params = np.concatenate(parts).astype(np.float32)
+    freq = r.normal(0.0, freq_sigma, (SURROGATE_NFREQ, 2)).astype(np.float32)
+    return params, freq
