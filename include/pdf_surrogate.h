@@ -1,0 +1,87 @@
+/*
+ * pdf_surrogate.h -- learned surrogate of the PDF interpolator.
+ *
+ * No counterpart in the paper: a growth axis that replaces the
+ * interpolation of PDFFlow Sec. 2.2 by a small network where the network is
+ * accurate enough, with the interpolator as fallback and as the judge of the
+ * network's error.
+ *
+ * Network: (ln x, ln Q^2) scaled to [-1, 1]^2 -> 32 Fourier features
+ * (sin and cos of pi (F z), F a fixed [16][2] matrix) -> four layers of width
+ * 128 with SiLU -> one output per flavour; xf_f = c_f sinh(y_f) with
+ * c_f = 1e-5 max |xf_f| over the grid's knots (training target
+ * y_f = asinh(xf_f / c_f)).  Products run on BF16 tensor cores with FP32
+ * accumulation; BF16 weight copies are made from FP32 master weights.
+ * The parameter vector is flat FP32: W1 [128][32], b1 [128], W2..W4
+ * [128][128], b2..b4 [128], W5 [nflav][128], b5 [nflav] (W as [out][in]).
+ *
+ * All array arguments are DEVICE memory unless noted; calls return PDF_OK or
+ * a PDF_ERR_* code (see pdf_gb300.h).  At most 16 flavours.
+ */
+#ifndef PDF_SURROGATE_H
+#define PDF_SURROGATE_H
+
+#include "pdf_gb300.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pdf_surrogate pdf_surrogate;
+
+typedef struct {
+  int batch;                /* points per step                                   */
+  int steps;                /* optimiser steps                                   */
+  float lr, lr_min;         /* Adam learning rate: linear warm-up, cosine decay  */
+  int warmup;               /* warm-up steps                                     */
+} pdf_train_config;
+
+/* Make a surrogate for `grid` from HOST parameters (flat FP32, see above)
+ * and HOST frequencies freq[16][2]; scratch for batches of up to max_batch
+ * points is allocated here.  Synchronous. */
+PDF_API int pdf_surrogate_create(const pdf_grid *grid, const float *params, const float *freq, int max_batch,
+                                 pdf_surrogate **out);
+PDF_API int pdf_surrogate_free(pdf_surrogate *s);
+PDF_API int pdf_surrogate_nparams(const pdf_surrogate *s, size_t *n);
+/* Copy the FP32 master parameters to / from HOST memory (synchronous). */
+PDF_API int pdf_surrogate_get_params(const pdf_surrogate *s, float *params);
+PDF_API int pdf_surrogate_set_params(pdf_surrogate *s, const float *params);
+
+/* One forward and backward pass on n <= max_batch points with given target
+ * values xf [n][nflav] (FP64): *loss (HOST) is the mean-square error of the
+ * asinh targets, grad (HOST, nparams FP32) its gradient.  Synchronous. */
+PDF_API int pdf_surrogate_loss_grad(pdf_surrogate *s, const double *x, const double *q2, const double *xf,
+                                    size_t n, double *loss, float *grad);
+
+/* Train on the n points (x, q2), targets from the FP64 interpolator of
+ * `grid`, batches taken in order.  *final_loss (HOST, may be NULL) is the
+ * last batch's loss.  Enqueued on `stream`; returns after the last step. */
+PDF_API int pdf_surrogate_train(pdf_surrogate *s, const pdf_grid *grid, const double *x, const double *q2,
+                                size_t n, const pdf_train_config *cfg, double *final_loss, cudaStream_t stream);
+
+/* Network output for n points inside the grid: out [n][nflav] FP32. */
+PDF_API int pdf_surrogate_eval(const pdf_surrogate *s, const double *x, const double *q2, size_t n, float *out,
+                               cudaStream_t stream);
+
+/* Error map: evaluate the network and the FP64 interpolator on n validation
+ * points, record per tile of a 64 x 64 partition of the scaled (ln x, ln Q^2)
+ * square the largest error |s - v| / max(|v|, c_f) over points and
+ * flavours, and accept a tile when it was sampled and its error is at most
+ * `threshold`.  stats (HOST, may be NULL) receives [tiles accepted, tiles
+ * sampled, largest error, median tile error].  Synchronous. */
+PDF_API int pdf_surrogate_build_error_map(pdf_surrogate *s, const pdf_grid *grid, const double *x,
+                                          const double *q2, size_t n, double threshold, double *stats);
+
+/* x f for all flavours, out [n][nflav] FP64: the network on accepted tiles,
+ * the FP64 interpolator everywhere else (rejected tiles, outside the grid,
+ * invalid points).  *n_fallback (HOST, may be NULL) counts the points that
+ * took the interpolator.  Needs an error map; reads the fallback count back,
+ * so it synchronises `stream`. */
+PDF_API int pdf_surrogate_eval_fallback(pdf_surrogate *s, const pdf_grid *grid, const double *x, const double *q2,
+                                        size_t n, double *out, unsigned long long *n_fallback, cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PDF_SURROGATE_H */

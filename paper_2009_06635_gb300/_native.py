@@ -65,7 +65,22 @@ SIGNATURES = {
     "pdf_grid_reset_invalid_count": (I32, [P]),
     "pdf_last_error": (ctypes.c_char_p, []),
     "pdf_probe_fma_rate": (I32, [I32, I32, ctypes.POINTER(ctypes.c_double)]),
+    "pdf_surrogate_create": (I32, [P, P, P, I32, ctypes.POINTER(P)]),
+    "pdf_surrogate_free": (I32, [P]),
+    "pdf_surrogate_nparams": (I32, [P, ctypes.POINTER(SZ)]),
+    "pdf_surrogate_get_params": (I32, [P, P]),
+    "pdf_surrogate_set_params": (I32, [P, P]),
+    "pdf_surrogate_loss_grad": (I32, [P, P, P, P, SZ, ctypes.POINTER(ctypes.c_double), P]),
+    "pdf_surrogate_train": (I32, [P, P, P, P, SZ, P, ctypes.POINTER(ctypes.c_double), P]),
+    "pdf_surrogate_eval": (I32, [P, P, P, SZ, P, P]),
+    "pdf_surrogate_build_error_map": (I32, [P, P, P, P, SZ, F64, P]),
+    "pdf_surrogate_eval_fallback": (I32, [P, P, P, P, SZ, P, ctypes.POINTER(ctypes.c_ulonglong), P]),
 }
+
+
+class TrainConfig(ctypes.Structure):
+    _fields_ = [("batch", ctypes.c_int), ("steps", ctypes.c_int), ("lr", ctypes.c_float),
+                ("lr_min", ctypes.c_float), ("warmup", ctypes.c_int)]
 
 
 def header_functions() -> list[str]:

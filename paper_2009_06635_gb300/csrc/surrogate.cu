@@ -1,0 +1,846 @@
+// surrogate.cu -- learned surrogate of the interpolator: a small MLP on BF16
+// tensor cores (mma.sync m16n8k16, FP32 accumulation), its training kernels,
+// and evaluation with fallback to the interpolator.
+//
+// Network (for points inside the grid):
+//   z   = (2 (ln x - lx_lo)/(lx_hi - lx_lo) - 1,  2 (ln Q^2 - lq_lo)/(lq_hi - lq_lo) - 1)
+//   a_j = pi (F[j][0] z0 + F[j][1] z1), features [sin a_0..15 | cos a_0..15] (32, BF16)
+//   h_l = silu(W_l h_{l-1} + b_l), width 128, four layers (BF16 activations)
+//   y   = W_5 h_4 + b_5 (FP32), one output per flavour
+//   xf_f = c_f sinh(y_f); training target y_f = asinh(xf_f / c_f), c_f = 1e-5 max|xf_f|
+// silu(v) = v (1 + tanh(v/2)) / 2 with the hardware tanh approximation.
+// Weights are FP32 masters (Adam) with BF16 copies for the products.
+//
+// The interpolator is the judge: an error map over 64 x 64 tiles of (z0, z1)
+// records the surrogate's largest error against the FP64 interpolator
+// (|s - v| / max(|v|, c_f), over flavours and validation points); evaluation
+// with fallback uses the surrogate only on tiles whose error is below the
+// threshold, and the interpolator everywhere else (and outside the grid).
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "pdf_internal.cuh"
+#include "pdf_surrogate.h"
+
+namespace pdfgb {
+int launch_all_f64(const pdf_grid *g, const double *x, const double *q2, long long n, double *out,
+                   cudaStream_t st);
+}
+
+namespace {
+
+using namespace pdfgb;
+using bf16 = __nv_bfloat16;
+
+constexpr int SW = 128;   // hidden width
+constexpr int SNQ = 16;   // Fourier frequencies
+constexpr int SIN = 32;   // features
+constexpr int SOUT = 16;  // outputs, padded
+constexpr int MAPN = 64;  // error-map tiles per axis
+constexpr float kPi = 3.14159265358979f;
+
+struct SurrConst {
+  float freq[SNQ][2];
+  float lx_lo, inv_lx, lq_lo, inv_lq;  // z = 2 (l - lo) inv - 1
+  float scale[SOUT];
+  int nf;
+};
+
+// parameter offsets in the flat FP32 vector
+struct Layout {
+  size_t w[5], b[5], total;
+  int in[5], out[5];
+  void set(int nf) {
+    const int ins[5] = {SIN, SW, SW, SW, SW}, outs[5] = {SW, SW, SW, SW, nf};
+    size_t k = 0;
+    for (int l = 0; l < 5; l++) {
+      in[l] = ins[l];
+      out[l] = outs[l];
+      w[l] = k;
+      k += (size_t)outs[l] * ins[l];
+      b[l] = k;
+      k += outs[l];
+    }
+    total = k;
+  }
+};
+// BF16 weight copies: W1 [128][32], W2..4 [128][128], W5 [16][128] (rows >= nf zero)
+__host__ __device__ constexpr size_t wbf_off(int l) { return l == 0 ? 0 : 128 * 32 + (size_t)(l - 1) * 128 * 128; }
+constexpr size_t kWbfTotal = 128 * 32 + 3 * 128 * 128 + 16 * 128;
+
+__device__ __forceinline__ float tanh_fast(float v) {
+  float r;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(r) : "f"(v));
+  return r;
+}
+__device__ __forceinline__ float silu_f(float v) { return 0.5f * v * (1.f + tanh_fast(0.5f * v)); }
+__device__ __forceinline__ float dsilu_f(float v) {
+  float s = 0.5f * (1.f + tanh_fast(0.5f * v));
+  return s + v * s * (1.f - s);
+}
+
+__device__ __forceinline__ void point_z(const SurrConst &c, double x, double q2, float &z0, float &z1) {
+  z0 = 2.f * (logf((float)x) - c.lx_lo) * c.inv_lx - 1.f;
+  z1 = 2.f * (logf((float)q2) - c.lq_lo) * c.inv_lq - 1.f;
+}
+
+// feature k (0..31) of a point
+__device__ __forceinline__ float feature(const SurrConst &c, float z0, float z1, int k) {
+  int j = k & 15;
+  float a = kPi * (c.freq[j][0] * z0 + c.freq[j][1] * z1);
+  return k < 16 ? sinf(a) : cosf(a);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t *>(&v);
+}
+
+__device__ __forceinline__ void mma16816(float *d, const uint32_t *a, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// ---------------------------------------------------------------------------
+// training kernels
+// ---------------------------------------------------------------------------
+
+__global__ void k_features(SurrConst c, const double *x, const double *q2, int n, bf16 *h0) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * SIN) return;
+  int p = i / SIN, k = i % SIN;
+  float z0, z1;
+  point_z(c, x[p], q2[p], z0, z1);
+  h0[i] = __float2bfloat16_rn(feature(c, z0, z1, k));
+}
+
+enum { EPI_FWD_SILU = 0, EPI_OUT = 1, EPI_BWD_SILU = 2, EPI_ATOMIC = 3 };
+
+struct GemmArgs {
+  const bf16 *A;
+  long long sam, sak;
+  const bf16 *B;
+  long long sbk, sbn;
+  int M, N, K, kchunk;
+  const float *bias;  // FWD / OUT
+  int nbias;          // columns that have a bias (OUT: the real flavours)
+  float *Z;           // FWD: pre-activation out; BWD: pre-activation in
+  bf16 *H;            // FWD: activation out; BWD: gradient out
+  float *C;           // OUT: y, ATOMIC: accumulated result
+  long long ldc;
+};
+
+// C[M][N] = sum_k A(m,k) B(k,n) over this block's K chunk; 64x64 tile,
+// four warps of 32x32, K step 32, operands staged in shared memory in
+// K-contiguous rows (padded to 40 so fragment reads hit distinct banks).
+template <int EPI>
+__global__ void __launch_bounds__(128) k_gemm(GemmArgs g) {
+  __shared__ __align__(16) bf16 As[64][40];
+  __shared__ __align__(16) bf16 Bs[64][40];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+  const int kbeg = blockIdx.z * g.kchunk;
+  const int kend = min(g.K, kbeg + g.kchunk);
+  const int gid = lane >> 2, tig = lane & 3;
+  float acc[2][4][4];
+  for (int i = 0; i < 2; i++)
+    for (int j = 0; j < 4; j++)
+      for (int e = 0; e < 4; e++) acc[i][j][e] = 0.f;
+  const bf16 zero = __float2bfloat16_rn(0.f);
+  for (int k0 = kbeg; k0 < kend; k0 += 32) {
+    for (int e = tid; e < 64 * 32; e += 128) {
+      int r = e >> 5, kk = e & 31;
+      int m = m0 + r, n = n0 + r, k = k0 + kk;
+      As[r][kk] = (m < g.M && k < kend) ? g.A[m * g.sam + k * g.sak] : zero;
+      Bs[r][kk] = (n < g.N && k < kend) ? g.B[k * g.sbk + n * g.sbn] : zero;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ks = 0; ks < 32; ks += 16) {
+      uint32_t a[2][4], b[4][2];
+#pragma unroll
+      for (int i = 0; i < 2; i++) {
+        const bf16 *r0 = &As[wm + 16 * i + gid][ks + 2 * tig];
+        const bf16 *r1 = &As[wm + 16 * i + gid + 8][ks + 2 * tig];
+        a[i][0] = *reinterpret_cast<const uint32_t *>(r0);
+        a[i][1] = *reinterpret_cast<const uint32_t *>(r1);
+        a[i][2] = *reinterpret_cast<const uint32_t *>(r0 + 8);
+        a[i][3] = *reinterpret_cast<const uint32_t *>(r1 + 8);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        const bf16 *c0 = &Bs[wn + 8 * j + gid][ks + 2 * tig];
+        b[j][0] = *reinterpret_cast<const uint32_t *>(c0);
+        b[j][1] = *reinterpret_cast<const uint32_t *>(c0 + 8);
+      }
+#pragma unroll
+      for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) mma16816(acc[i][j], a[i], b[j][0], b[j][1]);
+    }
+    __syncthreads();
+  }
+  // epilogue: element (row, col) of fragment e: row = gid + 8 (e >= 2), col = 2 tig + (e & 1)
+#pragma unroll
+  for (int i = 0; i < 2; i++)
+#pragma unroll
+    for (int j = 0; j < 4; j++)
+#pragma unroll
+      for (int e = 0; e < 4; e++) {
+        int m = m0 + wm + 16 * i + gid + ((e >> 1) << 3);
+        int n = n0 + wn + 8 * j + 2 * tig + (e & 1);
+        if (m >= g.M || n >= g.N) continue;
+        float v = acc[i][j][e];
+        long long o = (long long)m * g.ldc + n;
+        if (EPI == EPI_FWD_SILU) {
+          float z = v + g.bias[n];
+          g.Z[o] = z;
+          g.H[o] = __float2bfloat16_rn(silu_f(z));
+        } else if (EPI == EPI_OUT) {
+          g.C[o] = v + (n < g.nbias ? g.bias[n] : 0.f);
+        } else if (EPI == EPI_BWD_SILU) {
+          g.H[o] = __float2bfloat16_rn(v * dsilu_f(g.Z[o]));
+        } else {
+          atomicAdd(g.C + o, v);
+        }
+      }
+}
+
+// dL/dy for the mean-square loss on asinh targets; the loss sum accumulates in FP64.
+__global__ void k_loss(const float *y, const float *t, int n, int nf, bf16 *g, double *loss) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  float part = 0.f;
+  if (i < n * SOUT) {
+    int f = i % SOUT;
+    float d = f < nf ? y[i] - t[i] : 0.f;
+    g[i] = __float2bfloat16_rn(2.f * d / ((float)n * (float)nf));
+    part = d * d;
+  }
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  if ((threadIdx.x & 31) == 0 && part != 0.f) atomicAdd(loss, (double)part);
+}
+
+// db[n] += sum_b G[b][n] (G BF16, [rows][ld]); one block per column.
+__global__ void k_colsum(const bf16 *G, int rows, int ld, int ncol, float *db) {
+  int n = blockIdx.x;
+  if (n >= ncol) return;
+  float s = 0.f;
+  for (int b = threadIdx.x; b < rows; b += blockDim.x) s += __bfloat162float(G[(long long)b * ld + n]);
+  __shared__ float red[32];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) db[n] += s;
+  }
+}
+
+struct AdamArgs {
+  float *p, *gr, *m, *v;
+  size_t n;
+  float lr, b1, b2, eps, c1, c2;  // c1 = 1 - b1^t, c2 = 1 - b2^t
+};
+__global__ void k_adam(AdamArgs a) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  float g = a.gr[i];
+  float m = a.b1 * a.m[i] + (1.f - a.b1) * g;
+  float v = a.b2 * a.v[i] + (1.f - a.b2) * g * g;
+  a.m[i] = m;
+  a.v[i] = v;
+  a.p[i] -= a.lr * (m / a.c1) / (sqrtf(v / a.c2) + a.eps);
+}
+
+// FP32 masters -> BF16 weight copies (W5 padded to 16 rows).
+struct CastArgs {
+  const float *p;
+  bf16 *w;
+  size_t woff[5], boff[5];
+  int nf;
+};
+__global__ void k_cast(CastArgs a) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int)kWbfTotal) return;
+  int l = 4;
+  while (l > 0 && (size_t)i < wbf_off(l)) l--;
+  int r = i - (int)wbf_off(l);
+  int in = l == 0 ? SIN : SW;
+  int row = r / in, col = r % in;
+  float v = (l == 4 && row >= a.nf) ? 0.f : a.p[a.woff[l] + (size_t)row * in + col];
+  a.w[i] = __float2bfloat16_rn(v);
+}
+
+// training targets y = asinh(xf / c) as FP32 [n][16]
+__global__ void k_targets(const double *xf, int n, int nf, const float *scale, float *t) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * SOUT) return;
+  int p = i / SOUT, f = i % SOUT;
+  t[i] = f < nf ? (float)asinh(xf[(size_t)p * nf + f] / (double)scale[f]) : 0.f;
+}
+
+// ---------------------------------------------------------------------------
+// fused inference: weights in shared memory, 16 points per warp, activations
+// chained through registers (the m16n8 accumulator fragments of two adjacent
+// n-tiles are exactly the m16k16 A fragment of the next layer's k-step)
+// ---------------------------------------------------------------------------
+constexpr int IW = 8;                      // warps per block
+constexpr int LD1 = SIN + 8, LDH = SW + 8;  // padded smem row strides (bf16)
+constexpr size_t kInferSmem = (size_t)(128 * LD1 + 3 * 128 * LDH + 16 * LDH) * sizeof(bf16) +
+                              (4 * SW + SOUT) * sizeof(float);
+
+__device__ __forceinline__ void silu_pack(const float (*acc)[4], const float *bias, int tig, uint32_t (*afr)[4]) {
+#pragma unroll
+  for (int s = 0; s < 8; s++) {
+    const int c0 = 16 * s + 2 * tig, c1 = c0 + 8;
+    afr[s][0] = pack_bf16(silu_f(acc[2 * s][0] + bias[c0]), silu_f(acc[2 * s][1] + bias[c0 + 1]));
+    afr[s][1] = pack_bf16(silu_f(acc[2 * s][2] + bias[c0]), silu_f(acc[2 * s][3] + bias[c0 + 1]));
+    afr[s][2] = pack_bf16(silu_f(acc[2 * s + 1][0] + bias[c1]), silu_f(acc[2 * s + 1][1] + bias[c1 + 1]));
+    afr[s][3] = pack_bf16(silu_f(acc[2 * s + 1][2] + bias[c1]), silu_f(acc[2 * s + 1][3] + bias[c1 + 1]));
+  }
+}
+
+__global__ void __launch_bounds__(32 * IW, 1)
+k_infer(SurrConst c, const bf16 *__restrict__ wg, const float *__restrict__ params, Layout L,
+        const double *__restrict__ xa, const double *__restrict__ qa, long long n, float *__restrict__ outf,
+        double *__restrict__ outd, const unsigned char *__restrict__ mask, unsigned int *nfb,
+        unsigned int *fb_idx) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  bf16 *W1 = reinterpret_cast<bf16 *>(smem);
+  bf16 *Wh = W1 + 128 * LD1;  // three [128][LDH]
+  bf16 *W5 = Wh + 3 * 128 * LDH;
+  float *bs = reinterpret_cast<float *>(W5 + 16 * LDH);  // b1..b4 [4][128], b5 [16]
+  for (int i = threadIdx.x; i < 128 * SIN; i += blockDim.x) W1[(i / SIN) * LD1 + i % SIN] = wg[wbf_off(0) + i];
+  for (int l = 0; l < 3; l++)
+    for (int i = threadIdx.x; i < 128 * SW; i += blockDim.x)
+      Wh[l * 128 * LDH + (i / SW) * LDH + i % SW] = wg[wbf_off(l + 1) + i];
+  for (int i = threadIdx.x; i < 16 * SW; i += blockDim.x) W5[(i / SW) * LDH + i % SW] = wg[wbf_off(4) + i];
+  for (int i = threadIdx.x; i < 4 * SW; i += blockDim.x) bs[i] = params[L.b[i / SW] + i % SW];
+  for (int i = threadIdx.x; i < SOUT; i += blockDim.x) bs[4 * SW + i] = i < c.nf ? params[L.b[4] + i] : 0.f;
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gid = lane >> 2, tig = lane & 3;
+  const long long stride = (long long)gridDim.x * IW * 16;
+  for (long long p0 = ((long long)blockIdx.x * IW + warp) * 16; p0 < n; p0 += stride) {
+    // rows gid and gid + 8 of this 16-point tile
+    long long pr[2] = {p0 + gid, p0 + gid + 8};
+    float z0[2], z1[2];
+    bool use[2];
+    for (int h = 0; h < 2; h++) {
+      const bool in = pr[h] < n;
+      double x = in ? xa[pr[h]] : 0.5, q = in ? qa[pr[h]] : 10.0;
+      point_z(c, x, q, z0[h], z1[h]);
+      use[h] = in;
+      if (mask) {  // fallback: outside the grid, or on a tile the map rejects
+        bool inside = z0[h] >= -1.f && z0[h] <= 1.f && z1[h] >= -1.f && z1[h] <= 1.f && x > 0.0 && q > 0.0;
+        int tx = min(MAPN - 1, max(0, (int)((z0[h] + 1.f) * 0.5f * MAPN)));
+        int tq = min(MAPN - 1, max(0, (int)((z1[h] + 1.f) * 0.5f * MAPN)));
+        bool ok = inside && mask[tq * MAPN + tx];
+        if (in && !ok && tig == 0) fb_idx[atomicAdd(nfb, 1u)] = (unsigned int)pr[h];
+        use[h] = in && ok;
+        if (!inside) { z0[h] = 0.f; z1[h] = 0.f; }
+      }
+    }
+    // layer 1 A fragments: features k = 16 s + 2 tig + {0,1} (+8)
+    uint32_t f1[2][4];
+#pragma unroll
+    for (int s = 0; s < 2; s++) {
+      const int k0 = 16 * s + 2 * tig, k1 = k0 + 8;
+      f1[s][0] = pack_bf16(feature(c, z0[0], z1[0], k0), feature(c, z0[0], z1[0], k0 + 1));
+      f1[s][1] = pack_bf16(feature(c, z0[1], z1[1], k0), feature(c, z0[1], z1[1], k0 + 1));
+      f1[s][2] = pack_bf16(feature(c, z0[0], z1[0], k1), feature(c, z0[0], z1[0], k1 + 1));
+      f1[s][3] = pack_bf16(feature(c, z0[1], z1[1], k1), feature(c, z0[1], z1[1], k1 + 1));
+    }
+    float acc[16][4];
+#pragma unroll
+    for (int j = 0; j < 16; j++) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+#pragma unroll
+    for (int s = 0; s < 2; s++)
+#pragma unroll
+      for (int j = 0; j < 16; j++) {
+        const bf16 *w = W1 + (8 * j + gid) * LD1 + 16 * s + 2 * tig;
+        mma16816(acc[j], f1[s], *reinterpret_cast<const uint32_t *>(w), *reinterpret_cast<const uint32_t *>(w + 8));
+      }
+    uint32_t afr[8][4];
+    silu_pack(acc, bs, tig, afr);
+    for (int l = 0; l < 3; l++) {
+      const bf16 *Wl = Wh + l * 128 * LDH;
+#pragma unroll
+      for (int j = 0; j < 16; j++) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+#pragma unroll
+      for (int s = 0; s < 8; s++)
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+          const bf16 *w = Wl + (8 * j + gid) * LDH + 16 * s + 2 * tig;
+          mma16816(acc[j], afr[s], *reinterpret_cast<const uint32_t *>(w),
+                   *reinterpret_cast<const uint32_t *>(w + 8));
+        }
+      silu_pack(acc, bs + (l + 1) * SW, tig, afr);
+    }
+    float y[2][4];
+#pragma unroll
+    for (int j = 0; j < 2; j++) y[j][0] = y[j][1] = y[j][2] = y[j][3] = 0.f;
+#pragma unroll
+    for (int s = 0; s < 8; s++)
+#pragma unroll
+      for (int j = 0; j < 2; j++) {
+        const bf16 *w = W5 + (8 * j + gid) * LDH + 16 * s + 2 * tig;
+        mma16816(y[j], afr[s], *reinterpret_cast<const uint32_t *>(w), *reinterpret_cast<const uint32_t *>(w + 8));
+      }
+    // outputs: fragment e of n-tile j is row gid + 8 (e >= 2), flavour 8 j + 2 tig + (e & 1)
+#pragma unroll
+    for (int j = 0; j < 2; j++)
+#pragma unroll
+      for (int e = 0; e < 4; e++) {
+        const int h = e >> 1, f = 8 * j + 2 * tig + (e & 1);
+        if (!use[h] || f >= c.nf) continue;
+        const float v = c.scale[f] * sinhf(y[j][e] + bs[4 * SW + f]);
+        if (outf) outf[pr[h] * c.nf + f] = v;
+        if (outd) outd[pr[h] * c.nf + f] = (double)v;
+      }
+  }
+}
+
+// error map: per tile the largest |s - v| / max(|v|, c_f) over points and flavours
+__global__ void k_tile_err(SurrConst c, const double *xa, const double *qa, long long n, const float *s,
+                           const double *v, unsigned int *tile_err_bits, unsigned int *tile_cnt) {
+  long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  float z0, z1;
+  point_z(c, xa[p], qa[p], z0, z1);
+  if (!(z0 >= -1.f && z0 <= 1.f && z1 >= -1.f && z1 <= 1.f)) return;
+  int tx = min(MAPN - 1, (int)((z0 + 1.f) * 0.5f * MAPN)), tq = min(MAPN - 1, (int)((z1 + 1.f) * 0.5f * MAPN));
+  float e = 0.f;
+  for (int f = 0; f < c.nf; f++) {
+    double vv = v[p * c.nf + f];
+    double d = fabs((double)s[p * c.nf + f] - vv) / fmax(fabs(vv), (double)c.scale[f]);
+    e = fmaxf(e, (float)d);
+  }
+  if (isnan(e)) e = 1e30f;
+  atomicMax(tile_err_bits + tq * MAPN + tx, __float_as_uint(e));  // e >= 0: bits order like values
+  atomicAdd(tile_cnt + tq * MAPN + tx, 1u);
+}
+
+__global__ void k_make_mask(const unsigned int *tile_err_bits, const unsigned int *tile_cnt, float thr,
+                            unsigned char *mask) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= MAPN * MAPN) return;
+  mask[t] = (tile_cnt[t] > 0 && __uint_as_float(tile_err_bits[t]) <= thr) ? 1 : 0;
+}
+
+__global__ void k_gather(const double *x, const double *q2, const unsigned int *idx, unsigned int m, double *gx,
+                         double *gq) {
+  unsigned int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  gx[i] = x[idx[i]];
+  gq[i] = q2[idx[i]];
+}
+__global__ void k_scatter(const double *src, const unsigned int *idx, unsigned int m, int nf, double *out) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)m * nf) return;
+  long long r = i / nf;
+  out[(long long)idx[r] * nf + (i % nf)] = src[i];
+}
+
+int cuda_err(cudaError_t e, const char *what) {
+  if (e == cudaSuccess) return PDF_OK;
+  return set_error(PDF_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+}  // namespace
+
+struct pdf_surrogate {
+  int nf, max_batch, device;
+  Layout L;
+  SurrConst c;
+  float *params, *grads, *am, *av;  // device FP32
+  float *scale_d;                   // device copy of c_f
+  bf16 *wbf;                        // device BF16 copies
+  // training scratch (max_batch rows)
+  bf16 *h[5], *g[5];  // h0 [B][32], h1..h4 [B][128]; g1..g4 [B][128], g5 [B][16] at index 0..4 (g[l] for layer l)
+  float *z[4], *y, *t;
+  double *xfbuf, *loss;
+  long long step;
+  // error map and fallback
+  unsigned char *mask;
+  unsigned int *tile_bits, *tile_cnt, *nfb, *fb_idx;
+  double *fb_x, *fb_q, *fb_out;
+  size_t fb_cap;
+  bool has_map;
+  std::vector<void *> blocks;
+  template <typename T>
+  int alloc(T **p, size_t count) {
+    void *q = nullptr;
+    if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) return set_error(PDF_ERR_ALLOC, "surrogate: cudaMalloc");
+    blocks.push_back(q);
+    *p = static_cast<T *>(q);
+    return PDF_OK;
+  }
+};
+
+namespace {
+
+void launch_gemm(int epi, const GemmArgs &a, int ksplit, cudaStream_t st) {
+  dim3 grid((a.N + 63) / 64, (a.M + 63) / 64, ksplit);
+  switch (epi) {
+    case EPI_FWD_SILU: k_gemm<EPI_FWD_SILU><<<grid, 128, 0, st>>>(a); break;
+    case EPI_OUT: k_gemm<EPI_OUT><<<grid, 128, 0, st>>>(a); break;
+    case EPI_BWD_SILU: k_gemm<EPI_BWD_SILU><<<grid, 128, 0, st>>>(a); break;
+    default: k_gemm<EPI_ATOMIC><<<grid, 128, 0, st>>>(a); break;
+  }
+}
+
+GemmArgs gemm_args(const bf16 *A, long long sam, long long sak, const bf16 *B, long long sbk, long long sbn, int M,
+                   int N, int K) {
+  GemmArgs a{};
+  a.A = A; a.sam = sam; a.sak = sak; a.B = B; a.sbk = sbk; a.sbn = sbn;
+  a.M = M; a.N = N; a.K = K; a.kchunk = ((K + 31) / 32) * 32;
+  a.ldc = N;
+  a.nbias = N;
+  return a;
+}
+
+// One forward + backward pass on a batch already in h[0] (features) and t
+// (targets); gradients accumulate into s->grads (zeroed here).
+int forward_backward(pdf_surrogate *s, int B, cudaStream_t st) {
+  const Layout &L = s->L;
+  cudaMemsetAsync(s->grads, 0, L.total * sizeof(float), st);
+  cudaMemsetAsync(s->loss, 0, sizeof(double), st);
+  // forward
+  for (int l = 0; l < 4; l++) {
+    int K = l == 0 ? SIN : SW;
+    GemmArgs a = gemm_args(s->h[l], K, 1, s->wbf + wbf_off(l), 1, K, B, SW, K);
+    a.bias = s->params + L.b[l];
+    a.Z = s->z[l];
+    a.H = s->h[l + 1];
+    launch_gemm(EPI_FWD_SILU, a, 1, st);
+  }
+  {
+    GemmArgs a = gemm_args(s->h[4], SW, 1, s->wbf + wbf_off(4), 1, SW, B, SOUT, SW);
+    a.bias = s->params + L.b[4];
+    a.nbias = s->nf;  // padded output columns carry no bias
+    a.C = s->y;
+    launch_gemm(EPI_OUT, a, 1, st);
+  }
+  k_loss<<<(B * SOUT + 255) / 256, 256, 0, st>>>(s->y, s->t, B, s->nf, s->g[4], s->loss);
+  // backward
+  const int ksplit = (B + 1023) / 1024;
+  for (int l = 4; l >= 0; l--) {
+    const int in = l == 0 ? SIN : SW, out = l == 4 ? SOUT : SW, nout = l == 4 ? s->nf : SW;
+    const bf16 *G = s->g[l];
+    // dW[o][j] += sum_b G[b][o] H[b][j]
+    GemmArgs a = gemm_args(G, 1, out, s->h[l], in, 1, nout, in, B);
+    a.kchunk = ((B + ksplit - 1) / ksplit + 31) / 32 * 32;
+    a.C = s->grads + L.w[l];
+    a.ldc = in;
+    launch_gemm(EPI_ATOMIC, a, ksplit, st);
+    k_colsum<<<nout, 256, 0, st>>>(G, B, out, nout, s->grads + L.b[l]);
+    if (l > 0) {
+      // dH_{l}[b][j] = sum_o G[b][o] W[o][j]  ->  G_{l-1} = dH * silu'(Z_{l-1})
+      GemmArgs d = gemm_args(G, out, 1, s->wbf + wbf_off(l), in, 1, B, in, out);
+      d.Z = s->z[l - 1];
+      d.H = s->g[l - 1];
+      launch_gemm(EPI_BWD_SILU, d, 1, st);
+    }
+  }
+  return check_launch("surrogate forward/backward");
+}
+
+void cast_weights(pdf_surrogate *s, cudaStream_t st) {
+  CastArgs a;
+  a.p = s->params;
+  a.w = s->wbf;
+  for (int l = 0; l < 5; l++) { a.woff[l] = s->L.w[l]; a.boff[l] = s->L.b[l]; }
+  a.nf = s->nf;
+  k_cast<<<(unsigned)((kWbfTotal + 255) / 256), 256, 0, st>>>(a);
+}
+
+int features_targets(pdf_surrogate *s, const pdf_grid *grid, const double *x, const double *q2, int B,
+                     const double *xf_given, cudaStream_t st) {
+  k_features<<<(B * SIN + 255) / 256, 256, 0, st>>>(s->c, x, q2, B, s->h[0]);
+  const double *xf = xf_given;
+  if (!xf) {
+    int rc = launch_all_f64(grid, x, q2, B, s->xfbuf, st);
+    if (rc) return rc;
+    xf = s->xfbuf;
+  }
+  k_targets<<<(B * SOUT + 255) / 256, 256, 0, st>>>(xf, B, s->nf, s->scale_d, s->t);
+  return check_launch("surrogate features/targets");
+}
+
+}  // namespace
+
+using namespace pdfgb;
+
+extern "C" int pdf_surrogate_create(const pdf_grid *grid, const float *params, const float *freq, int max_batch,
+                                    pdf_surrogate **out) {
+  if (!grid || !params || !freq || !out) return set_error(PDF_ERR_NULL, "pdf_surrogate_create: NULL argument");
+  *out = nullptr;
+  const int nf = grid->v.nf;
+  if (nf > SOUT) return set_error(PDF_ERR_ARG, "pdf_surrogate_create: at most %d flavours", SOUT);
+  if (max_batch < 16 || max_batch > (1 << 22))
+    return set_error(PDF_ERR_ARG, "pdf_surrogate_create: max_batch %d outside [16, 4M]", max_batch);
+  pdf_surrogate *s = new (std::nothrow) pdf_surrogate();
+  if (!s) return set_error(PDF_ERR_ALLOC, "pdf_surrogate_create: host allocation");
+  s->nf = nf;
+  s->max_batch = max_batch;
+  cudaGetDevice(&s->device);
+  s->L.set(nf);
+  // constants: input normalisation from the grid's knot range, flavour scales
+  // c_f = 1e-5 max |xf_f| over the knots
+  const GridView &v = grid->v;
+  std::vector<double> vals((size_t)v.nrows * v.nx * v.nf);
+  int rc = cuda_err(cudaMemcpy(vals.data(), v.vals, vals.size() * sizeof(double), cudaMemcpyDeviceToHost),
+                    "pdf_surrogate_create");
+  if (rc) { delete s; return rc; }
+  for (int f = 0; f < SOUT; f++) s->c.scale[f] = 1.f;
+  for (int f = 0; f < nf; f++) {
+    double m = 0.0;
+    for (size_t k = f; k < vals.size(); k += nf) m = fmax(m, fabs(vals[k]));
+    s->c.scale[f] = (float)(1e-5 * (m > 0.0 ? m : 1.0));
+  }
+  double lxlo = log(v.x0), lxhi = log(v.xlast), lqlo = log(v.q2min), lqhi = log(v.q2max);
+  s->c.lx_lo = (float)lxlo; s->c.inv_lx = (float)(1.0 / (lxhi - lxlo));
+  s->c.lq_lo = (float)lqlo; s->c.inv_lq = (float)(1.0 / (lqhi - lqlo));
+  for (int j = 0; j < SNQ; j++) { s->c.freq[j][0] = freq[2 * j]; s->c.freq[j][1] = freq[2 * j + 1]; }
+  s->c.nf = nf;
+  const size_t P = s->L.total, B = (size_t)max_batch;
+  rc = s->alloc(&s->params, P);
+  if (!rc) rc = s->alloc(&s->grads, P);
+  if (!rc) rc = s->alloc(&s->am, P);
+  if (!rc) rc = s->alloc(&s->av, P);
+  if (!rc) rc = s->alloc(&s->scale_d, SOUT);
+  if (!rc) rc = s->alloc(&s->wbf, kWbfTotal);
+  if (!rc) rc = s->alloc(&s->h[0], B * SIN);
+  for (int l = 1; l < 5 && !rc; l++) rc = s->alloc(&s->h[l], B * SW);
+  for (int l = 0; l < 4 && !rc; l++) rc = s->alloc(&s->g[l], B * SW);
+  if (!rc) rc = s->alloc(&s->g[4], B * SOUT);
+  for (int l = 0; l < 4 && !rc; l++) rc = s->alloc(&s->z[l], B * SW);
+  if (!rc) rc = s->alloc(&s->y, B * SOUT);
+  if (!rc) rc = s->alloc(&s->t, B * SOUT);
+  if (!rc) rc = s->alloc(&s->xfbuf, B * nf);
+  if (!rc) rc = s->alloc(&s->loss, 1);
+  if (!rc) rc = s->alloc(&s->mask, MAPN * MAPN);
+  if (!rc) rc = s->alloc(&s->tile_bits, MAPN * MAPN);
+  if (!rc) rc = s->alloc(&s->tile_cnt, MAPN * MAPN);
+  if (!rc) rc = s->alloc(&s->nfb, 1);
+  if (rc) { pdf_surrogate_free(s); return rc; }
+  cudaMemcpy(s->params, params, P * sizeof(float), cudaMemcpyHostToDevice);
+  cudaMemcpy(s->scale_d, s->c.scale, SOUT * sizeof(float), cudaMemcpyHostToDevice);
+  cudaMemset(s->am, 0, P * sizeof(float));
+  cudaMemset(s->av, 0, P * sizeof(float));
+  cudaMemset(s->mask, 0, MAPN * MAPN);
+  cast_weights(s, 0);
+  rc = cuda_err(cudaDeviceSynchronize(), "pdf_surrogate_create");
+  if (rc) { pdf_surrogate_free(s); return rc; }
+  *out = s;
+  return PDF_OK;
+}
+
+extern "C" int pdf_surrogate_free(pdf_surrogate *s) {
+  if (!s) return PDF_OK;
+  for (void *p : s->blocks) cudaFree(p);
+  delete s;
+  return PDF_OK;
+}
+
+extern "C" int pdf_surrogate_nparams(const pdf_surrogate *s, size_t *n) {
+  if (!s || !n) return set_error(PDF_ERR_NULL, "pdf_surrogate_nparams: NULL argument");
+  *n = s->L.total;
+  return PDF_OK;
+}
+
+extern "C" int pdf_surrogate_get_params(const pdf_surrogate *s, float *params) {
+  if (!s || !params) return set_error(PDF_ERR_NULL, "pdf_surrogate_get_params: NULL argument");
+  return cuda_err(cudaMemcpy(params, s->params, s->L.total * sizeof(float), cudaMemcpyDeviceToHost),
+                  "pdf_surrogate_get_params");
+}
+
+extern "C" int pdf_surrogate_set_params(pdf_surrogate *s, const float *params) {
+  if (!s || !params) return set_error(PDF_ERR_NULL, "pdf_surrogate_set_params: NULL argument");
+  int rc = cuda_err(cudaMemcpy(s->params, params, s->L.total * sizeof(float), cudaMemcpyHostToDevice),
+                    "pdf_surrogate_set_params");
+  if (rc) return rc;
+  cast_weights(s, 0);
+  s->has_map = false;
+  return cuda_err(cudaDeviceSynchronize(), "pdf_surrogate_set_params");
+}
+
+extern "C" int pdf_surrogate_loss_grad(pdf_surrogate *s, const double *x, const double *q2, const double *xf,
+                                       size_t n, double *loss, float *grad) {
+  if (!s || !x || !q2 || !xf || !loss || !grad) return set_error(PDF_ERR_NULL, "pdf_surrogate_loss_grad: NULL argument");
+  if (n < 1 || n > (size_t)s->max_batch)
+    return set_error(PDF_ERR_ARG, "pdf_surrogate_loss_grad: n = %zu outside [1, %d]", n, s->max_batch);
+  int rc = features_targets(s, nullptr, x, q2, (int)n, xf, 0);
+  if (!rc) rc = forward_backward(s, (int)n, 0);
+  if (rc) return rc;
+  double sum = 0.0;
+  rc = cuda_err(cudaMemcpy(&sum, s->loss, sizeof(double), cudaMemcpyDeviceToHost), "pdf_surrogate_loss_grad");
+  if (!rc) rc = cuda_err(cudaMemcpy(grad, s->grads, s->L.total * sizeof(float), cudaMemcpyDeviceToHost),
+                         "pdf_surrogate_loss_grad");
+  *loss = sum / ((double)n * s->nf);
+  return rc;
+}
+
+extern "C" int pdf_surrogate_train(pdf_surrogate *s, const pdf_grid *grid, const double *x, const double *q2,
+                                   size_t n, const pdf_train_config *cfg, double *final_loss, cudaStream_t st) {
+  if (!s || !grid || !x || !q2 || !cfg) return set_error(PDF_ERR_NULL, "pdf_surrogate_train: NULL argument");
+  const int B = cfg->batch;
+  if (B < 16 || B > s->max_batch || (size_t)B > n)
+    return set_error(PDF_ERR_ARG, "pdf_surrogate_train: batch %d outside [16, min(max_batch, n)]", B);
+  if (grid->v.nf != s->nf) return set_error(PDF_ERR_ARG, "pdf_surrogate_train: grid flavours differ");
+  const size_t nb = n / (size_t)B;  // whole batches per pass
+  double last = 0.0;
+  for (int it = 0; it < cfg->steps; it++) {
+    const size_t bi = (size_t)it % nb;
+    const double *xb = x + bi * B, *qb = q2 + bi * B;
+    int rc = features_targets(s, grid, xb, qb, B, nullptr, st);
+    if (!rc) rc = forward_backward(s, B, st);
+    if (rc) return rc;
+    s->step++;
+    float lr = cfg->lr;
+    if (it < cfg->warmup) lr = cfg->lr * (float)(it + 1) / (float)cfg->warmup;
+    else {
+      float prog = (float)(it - cfg->warmup) / (float)(cfg->steps - cfg->warmup > 0 ? cfg->steps - cfg->warmup : 1);
+      lr = cfg->lr_min + 0.5f * (cfg->lr - cfg->lr_min) * (1.f + cosf(3.14159265f * prog));
+    }
+    AdamArgs a{s->params, s->grads, s->am, s->av, s->L.total, lr, 0.9f, 0.999f, 1e-8f,
+               1.f - powf(0.9f, (float)s->step), 1.f - powf(0.999f, (float)s->step)};
+    k_adam<<<(unsigned)((s->L.total + 255) / 256), 256, 0, st>>>(a);
+    cast_weights(s, st);
+    if (it == cfg->steps - 1) {
+      int e = cuda_err(cudaMemcpyAsync(&last, s->loss, sizeof(double), cudaMemcpyDeviceToHost, st), "train");
+      if (!e) e = cuda_err(cudaStreamSynchronize(st), "pdf_surrogate_train");
+      if (e) return e;
+    }
+  }
+  s->has_map = false;
+  if (final_loss) *final_loss = last / ((double)B * s->nf);
+  return check_launch("pdf_surrogate_train");
+}
+
+static int launch_infer(const pdf_surrogate *s, const double *x, const double *q2, size_t n, float *outf,
+                        double *outd, const unsigned char *mask, unsigned int *nfb, unsigned int *idx,
+                        cudaStream_t st) {
+  static bool configured = false;
+  if (!configured) {
+    cudaFuncSetAttribute(k_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kInferSmem);
+    configured = true;
+  }
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+  long long tiles = ((long long)n + 15) / 16;
+  long long blocks = (tiles + IW - 1) / IW;
+  if (blocks > sms) blocks = sms;
+  k_infer<<<(unsigned)blocks, 32 * IW, kInferSmem, st>>>(s->c, s->wbf, s->params, s->L, x, q2, (long long)n, outf,
+                                                          outd, mask, nfb, idx);
+  return check_launch("surrogate inference");
+}
+
+extern "C" int pdf_surrogate_eval(const pdf_surrogate *s, const double *x, const double *q2, size_t n, float *out,
+                                  cudaStream_t st) {
+  if (!s) return set_error(PDF_ERR_NULL, "pdf_surrogate_eval: surrogate is NULL");
+  if (n > 0 && (!x || !q2 || !out)) return set_error(PDF_ERR_NULL, "pdf_surrogate_eval: NULL array");
+  if (n == 0) return PDF_OK;
+  return launch_infer(s, x, q2, n, out, nullptr, nullptr, nullptr, nullptr, st);
+}
+
+extern "C" int pdf_surrogate_build_error_map(pdf_surrogate *s, const pdf_grid *grid, const double *x,
+                                             const double *q2, size_t n, double threshold, double *stats) {
+  if (!s || !grid || !x || !q2) return set_error(PDF_ERR_NULL, "pdf_surrogate_build_error_map: NULL argument");
+  if (n == 0) return set_error(PDF_ERR_ARG, "pdf_surrogate_build_error_map: no validation points");
+  float *sv = nullptr;
+  double *iv = nullptr;
+  int rc = cuda_err(cudaMalloc(&sv, n * s->nf * sizeof(float)), "error map");
+  if (!rc) rc = cuda_err(cudaMalloc(&iv, n * s->nf * sizeof(double)), "error map");
+  if (!rc) rc = launch_infer(s, x, q2, n, sv, nullptr, nullptr, nullptr, nullptr, 0);
+  if (!rc) rc = launch_all_f64(grid, x, q2, (long long)n, iv, 0);
+  if (!rc) {
+    cudaMemset(s->tile_bits, 0, MAPN * MAPN * sizeof(unsigned int));
+    cudaMemset(s->tile_cnt, 0, MAPN * MAPN * sizeof(unsigned int));
+    k_tile_err<<<(unsigned)((n + 255) / 256), 256>>>(s->c, x, q2, (long long)n, sv, iv, s->tile_bits, s->tile_cnt);
+    k_make_mask<<<(MAPN * MAPN + 255) / 256, 256>>>(s->tile_bits, s->tile_cnt, (float)threshold, s->mask);
+    rc = check_launch("error map");
+  }
+  std::vector<unsigned int> bits(MAPN * MAPN), cnt(MAPN * MAPN);
+  std::vector<unsigned char> m(MAPN * MAPN);
+  if (!rc) rc = cuda_err(cudaMemcpy(bits.data(), s->tile_bits, bits.size() * 4, cudaMemcpyDeviceToHost), "error map");
+  if (!rc) rc = cuda_err(cudaMemcpy(cnt.data(), s->tile_cnt, cnt.size() * 4, cudaMemcpyDeviceToHost), "error map");
+  if (!rc) rc = cuda_err(cudaMemcpy(m.data(), s->mask, m.size(), cudaMemcpyDeviceToHost), "error map");
+  cudaFree(sv);
+  cudaFree(iv);
+  if (rc) return rc;
+  // stats: [tiles accepted, tiles with samples, largest error on sampled tiles, median tile error]
+  int ok = 0, sampled = 0;
+  float worst = 0.f;
+  std::vector<float> errs;
+  for (size_t t = 0; t < bits.size(); t++) {
+    ok += m[t];
+    if (cnt[t] > 0) {
+      sampled++;
+      float e;
+      std::memcpy(&e, &bits[t], 4);
+      worst = fmaxf(worst, e);
+      errs.push_back(e);
+    }
+  }
+  if (stats) {
+    stats[0] = ok;
+    stats[1] = sampled;
+    stats[2] = worst;
+    if (!errs.empty()) {
+      std::nth_element(errs.begin(), errs.begin() + errs.size() / 2, errs.end());
+      stats[3] = errs[errs.size() / 2];
+    } else {
+      stats[3] = 0.0;
+    }
+  }
+  s->has_map = true;
+  return PDF_OK;
+}
+
+extern "C" int pdf_surrogate_eval_fallback(pdf_surrogate *s, const pdf_grid *grid, const double *x,
+                                           const double *q2, size_t n, double *out, unsigned long long *n_fallback,
+                                           cudaStream_t st) {
+  if (!s || !grid) return set_error(PDF_ERR_NULL, "pdf_surrogate_eval_fallback: NULL argument");
+  if (n > 0 && (!x || !q2 || !out)) return set_error(PDF_ERR_NULL, "pdf_surrogate_eval_fallback: NULL array");
+  if (!s->has_map) return set_error(PDF_ERR_ARG, "pdf_surrogate_eval_fallback: build the error map first");
+  if (n > 0xFFFFFFFFull) return set_error(PDF_ERR_ARG, "pdf_surrogate_eval_fallback: n too large");
+  if (n == 0) { if (n_fallback) *n_fallback = 0; return PDF_OK; }
+  if (n > s->fb_cap) {
+    for (void *p : {(void *)s->fb_idx, (void *)s->fb_x, (void *)s->fb_q, (void *)s->fb_out}) if (p) cudaFree(p);
+    s->fb_idx = nullptr; s->fb_x = s->fb_q = s->fb_out = nullptr; s->fb_cap = 0;
+    int rc = cuda_err(cudaMalloc(&s->fb_idx, n * sizeof(unsigned int)), "fallback buffers");
+    if (!rc) rc = cuda_err(cudaMalloc(&s->fb_x, n * sizeof(double)), "fallback buffers");
+    if (!rc) rc = cuda_err(cudaMalloc(&s->fb_q, n * sizeof(double)), "fallback buffers");
+    if (!rc) rc = cuda_err(cudaMalloc(&s->fb_out, n * s->nf * sizeof(double)), "fallback buffers");
+    if (rc) return rc;
+    s->fb_cap = n;
+  }
+  cudaMemsetAsync(s->nfb, 0, sizeof(unsigned int), st);
+  int rc = launch_infer(s, x, q2, n, nullptr, out, s->mask, s->nfb, s->fb_idx, st);
+  if (rc) return rc;
+  unsigned int m = 0;
+  rc = cuda_err(cudaMemcpyAsync(&m, s->nfb, sizeof(m), cudaMemcpyDeviceToHost, st), "fallback count");
+  if (!rc) rc = cuda_err(cudaStreamSynchronize(st), "fallback count");
+  if (rc) return rc;
+  if (m > 0) {
+    k_gather<<<(m + 255) / 256, 256, 0, st>>>(x, q2, s->fb_idx, m, s->fb_x, s->fb_q);
+    rc = launch_all_f64(grid, s->fb_x, s->fb_q, (long long)m, s->fb_out, st);
+    if (rc) return rc;
+    k_scatter<<<(unsigned)(((long long)m * s->nf + 255) / 256), 256, 0, st>>>(s->fb_out, s->fb_idx, m, s->nf, out);
+  }
+  if (n_fallback) *n_fallback = m;
+  return check_launch("pdf_surrogate_eval_fallback");
+}
