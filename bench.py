@@ -37,6 +37,9 @@ METRIC = "PDF evals/s (points×flavours) FP64 vs FP32 vs surrogate at stated max
 N_POINTS = 10_000_000
 MC_EVENTS = 1_000_000
 ADJ_POINTS = 1_000_000
+SURR_TRAIN, SURR_VAL, SURR_INFER = 20_000_000, 1_000_000, 100_000_000
+SURR_FLOPS_PER_POINT = 2 * (32 * 128 + 3 * 128 * 128 + 128 * 16)  # padded output layer
+SURR_SFU_PER_POINT = 4 * 128 + 32  # tanh per SiLU, sin/cos per feature
 WORKLOAD = ("three Q subgrids (12/15/25 Q knots split at Q = 1.51 and 4.92 GeV, Q in [1, 1e5] GeV), "
             "196 x knots in [1e-9, 1], 13 flavours; 1e7 queries per rank, x log-uniform in [1e-10, 1], "
             "Q log-uniform in [1, 2e5] GeV (15% outside the grid); all flavours + alpha_s per point")
@@ -277,6 +280,84 @@ def cpu_baseline_leg(g, x, q2, out_gpu, a_gpu, x32, q32, out32, target_s=10.0):
              "marginal_excluded": int(fl.sum()), "sample_points": m})
 
 
+def surrogate_leg(args, G, g, dev, world, sync, rank, nf, ms_per_eval64):
+    """Learned surrogate: train on 2e7 in-grid samples, map its error against
+    the FP64 interpolator on 1e6 validation points, infer on 1e8 points."""
+    import torch
+
+    from paper_2009_06635_gb300 import synthetic as S
+    from paper_2009_06635_gb300.surrogate import Surrogate
+
+    peaks = json.loads((ROOT / "MEASURED_PEAKS.json").read_text()) if (ROOT / "MEASURED_PEAKS.json").exists() else {}
+    bf16_peak = peaks.get("bf16_tflops", 1900.0)
+    s = Surrogate(G, max_batch=8192)
+    xt, qt = S.ingrid_samples(g, SURR_TRAIN, 7 + 1000 * rank)
+    xtd, qtd = torch.from_numpy(xt).to(dev), torch.from_numpy(qt).to(dev)
+    del xt, qt
+    steps = 2 * SURR_TRAIN // 8192
+    sync()
+    t0 = time.perf_counter()
+    final_loss = s.train(G, xtd, qtd, batch=8192, steps=steps, lr=2e-3, lr_min=1e-5, warmup=200)
+    sync()
+    train_s = time.perf_counter() - t0
+    del xtd, qtd
+    xv, qv = S.ingrid_samples(g, SURR_VAL, 11 + 1000 * rank)
+    stats = s.build_error_map(G, torch.from_numpy(xv).to(dev), torch.from_numpy(qv).to(dev), threshold=1e-3)
+    xi, qi = S.ingrid_samples(g, SURR_INFER, 8 + 1000 * rank)
+    xid, qid = torch.from_numpy(xi).to(dev), torch.from_numpy(qi).to(dev)
+    del xi, qi
+    out = torch.empty((SURR_INFER, nf), dtype=torch.float32, device=dev)
+    ev = []
+
+    def step():
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        s.eval(xid, qid, out=out)
+        b.record()
+        ev.append((a, b))
+
+    ms = run_timed(step, max(3, args.steps // 10), 2, world, sync)
+    kms = float(np.mean([a.elapsed_time(b) for a, b in ev[2:]]))
+    # accuracy of the network alone on 1e6 of the inference points, against the interpolator
+    k = 1_000_000
+    ref = P_xf(G, xid[:k], qid[:k])
+    net = out[:k].double()
+    scale = torch.from_numpy(1e-5 * np.abs(g.values).reshape(-1, nf).max(axis=0)).to(dev)
+    err = ((net - ref).abs() / torch.maximum(ref.abs(), scale)).max(dim=0).values.cpu().numpy()
+    within = float((((net - ref).abs() / torch.maximum(ref.abs(), scale)).max(dim=1).values <= 1e-3).float().mean())
+    fb_out, nfb = s.eval_fallback(G, xid[:k], qid[:k])
+    sync()
+    t0 = time.perf_counter()
+    for _ in range(3):
+        s.eval_fallback(G, xid, qid)
+    sync()
+    fb_s = (time.perf_counter() - t0) / 3
+    flops = SURR_FLOPS_PER_POINT * SURR_INFER
+    sfu_peak = SMS * 16 * SM_MHZ * 1e6
+    return {
+        "value": world * SURR_INFER * nf / (ms * 1e-3), "unit": "evals/s (network only)", "ms_per_step": ms,
+        "points": SURR_INFER, "train": {"samples": SURR_TRAIN, "steps": steps, "batch": 8192, "seconds": train_s,
+                                        "final_loss": final_loss},
+        "error_map": stats,
+        "max_rel_err_per_flavour": [float(e) for e in err],
+        "rel_err": "|net - interp| / max(|interp|, 1e-5 max|xf_f|), network alone, 1e6 inference points",
+        "fraction_within_1e-3": within,
+        "fallback": {"threshold": 1e-3, "fallback_fraction": nfb / k,
+                     "value": world * SURR_INFER * nf / fb_s, "unit": "evals/s with fallback (FP64 out)"},
+        "gain_vs_fp64_interpolator": (SURR_INFER * nf / (kms * 1e-3)) * ms_per_eval64 * 1e-3,
+        "roofline": {"bound": "tensor", "achieved": flops / (kms * 1e-3) / 1e12, "peak": bf16_peak, "unit": "TFLOP/s",
+                     "frac": flops / (kms * 1e-3) / 1e12 / bf16_peak,
+                     "peak_source": "measured bf16 burst (MEASURED_PEAKS.json)",
+                     "sfu_bound_ms": SURR_SFU_PER_POINT * SURR_INFER / sfu_peak * 1e3, "kernel_ms": kms},
+    }
+
+
+def P_xf(G, x, q2):
+    import paper_2009_06635_gb300 as P
+
+    return P.xfxq2_all_flavours(G, x, q2)
+
+
 def our_arm(args):
     import torch
 
@@ -380,6 +461,8 @@ def our_arm(args):
 
     ms_adj = run_timed(step_adj, args.steps, 2, world, sync)
 
+    surrogate = None if args.no_surrogate else surrogate_leg(args, G, g, dev, world, sync, rank, nf, ms64 / (n * (nf + 1)))
+
     # end to end through the C ABI with host buffers (pinned), copies timed
     hx = torch.from_numpy(x).pin_memory()
     hq = torch.from_numpy(q2).pin_memory()
@@ -446,6 +529,7 @@ def our_arm(args):
                               "events": MC_EVENTS},
             "mc_event_fp32": {"value": world * MC_EVENTS * (2 * nf + 1) / (ms_mc32 * 1e-3),
                               "ms_per_step": ms_mc32, "events": MC_EVENTS},
+            "surrogate_bf16": surrogate,
             "adjoint_fp64": {"value": world * ADJ_POINTS * nf / (ms_adj * 1e-3), "ms_per_step": ms_adj,
                              "points": ADJ_POINTS, "unit": "(point, flavour) gradients/s",
                              "outputs": "d/dx, d/dQ^2 per point and d/d(knot values), FP64 atomics"},
@@ -474,6 +558,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--points", type=int, default=N_POINTS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--only", choices=["fp64", "fp32"], default=None,
                     help="run only that path's step (a small case for profiling); prints its timing")
     args = ap.parse_args()
