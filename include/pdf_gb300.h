@@ -199,7 +199,9 @@ PDF_API int xfxq2_all_flavours_vjp(const pdf_grid *grid, const double *x, const 
 
 /* Replace the grid's knot values with `values` ([rows][nx][nflav] FP64,
  * DEVICE memory) and re-stage the patch coefficients on `stream` (the knots
- * and subgrids stay).  For fitting loops: no host round trip.  Work on other
+ * and subgrids stay).  For fitting loops: no host round trip of the values;
+ * the call synchronises `stream` once to learn whether the new values keep
+ * the float-float contraction of the FP64 path in range.  Work on other
  * streams that reads the grid must be ordered after it by the caller. */
 PDF_API int pdf_grid_set_values(pdf_grid *grid, const double *values, cudaStream_t stream);
 

@@ -73,6 +73,8 @@ struct Stage {
   double *lx, *lq, *alq;
   double *xcell, *qcell, *xW, *qW, *coef, *acell;
   float *coef32, *xthr32, *q2thr32, *aq2thr32, *xcell32, *qcell32, *acell32;
+  float2 *coefff;
+  int *ffbad;  // set when a control point is outside the float-float range
   int *row_qc, *qc_row;
   double *scal;  // scalar outputs, see k_scalars
 };
@@ -191,7 +193,20 @@ __global__ void k_coef(Stage S) {
   }
   double *o = S.coef + (size_t)id * 16;
   float *o32 = S.coef32 + (size_t)id * 16;
-  for (int m = 0; m < 16; m++) { o[m] = c[m]; o32[m] = (float)c[m]; }
+  float2 *off = S.coefff + (size_t)id * 16;
+  bool bad = false;
+  for (int m = 0; m < 16; m++) {
+    o[m] = c[m];
+    o32[m] = (float)c[m];
+    // float-float split: hi = round(c), lo = round(c - hi); exact to 2^-48 of c
+    // while |c| stays well inside the float exponent range
+    float hi = __double2float_rn(c[m]);
+    float lo = __double2float_rn(c[m] - (double)hi);
+    off[m] = make_float2(hi, lo);
+    double a = fabs(c[m]);
+    if (a != 0.0 && (a < 1e-30 || a > 1e30)) bad = true;
+  }
+  if (bad && S.ffbad) atomicOr(S.ffbad, 1);
 }
 
 // alpha_s cells: one thread per node; the last node gets a degenerate cell.
@@ -362,6 +377,8 @@ extern "C" int pdf_load_grid(const pdf_grid_desc *d, pdf_grid **out) {
     S.xW = A.take<double>(16 * nx); S.qW = A.take<double>(16 * (nqc + 1));
     S.coef = A.take<double>((size_t)(nqc + 1) * nx * nf * 16);
     S.coef32 = A.take<float>((size_t)(nqc + 1) * nx * nf * 16);
+    S.coefff = A.take<float2>((size_t)(nqc + 1) * nx * nf * 16);
+    S.ffbad = A.take<int>(1);
     S.acell = A.take<double>(6 * (na > 0 ? na : 1));
     S.acell32 = A.take<float>(6 * (na > 0 ? na : 1));
     S.xthr32 = A.take<float>(nx); S.q2thr32 = A.take<float>(nrows); S.aq2thr32 = A.take<float>(na > 0 ? na : 1);
@@ -404,6 +421,7 @@ extern "C" int pdf_load_grid(const pdf_grid_desc *d, pdf_grid **out) {
   H2D(S.first, first, sizeof(int) * nsub);
   H2D(S.nq, d->nq, sizeof(int) * nsub);
   if (e == cudaSuccess) e = cudaMemset(inv, 0, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(S.ffbad, 0, sizeof(int));
   if (e != cudaSuccess) {
     pdf_free_grid(g);
     return set_error(PDF_ERR_CUDA, "pdf_load_grid: copy to device: %s", cudaGetErrorString(e));
@@ -420,7 +438,9 @@ extern "C" int pdf_load_grid(const pdf_grid_desc *d, pdf_grid **out) {
   k_scalars<<<1, 32>>>(S);
   if ((rc = check_launch("pdf_load_grid staging"))) { pdf_free_grid(g); return rc; }
   double scal[16];
+  int ffbad = 1;
   e = cudaMemcpy(scal, S.scal, sizeof scal, cudaMemcpyDeviceToHost);  // synchronises
+  if (e == cudaSuccess) e = cudaMemcpy(&ffbad, S.ffbad, sizeof(int), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) {
     pdf_free_grid(g);
     return set_error(PDF_ERR_CUDA, "pdf_load_grid: staging: %s", cudaGetErrorString(e));
@@ -432,6 +452,8 @@ extern "C" int pdf_load_grid(const pdf_grid_desc *d, pdf_grid **out) {
   v.xk = S.xk; v.q2k = S.q2k; v.xcell = S.xcell; v.qcell = S.qcell; v.row_qc = S.row_qc;
   v.qc_row = S.qc_row; v.vals = const_cast<double *>(S.vals);
   v.coef = S.coef; v.coef32 = S.coef32; v.xW = S.xW; v.qW = S.qW;
+  v.coefff = S.coefff; v.ff = ffbad ? 0 : 1;
+  g->ffbad = S.ffbad;
   v.xthr32 = S.xthr32; v.q2thr32 = S.q2thr32; v.xcell32 = S.xcell32; v.qcell32 = S.qcell32;
   v.aq2 = S.aq2; v.acell = S.acell; v.acell32 = S.acell32; v.aq2thr32 = S.aq2thr32;
   v.as_lo = na > 0 ? d->as_vals[0] : NAN;
@@ -497,9 +519,21 @@ extern "C" int pdf_grid_set_values(pdf_grid *g, const double *values, cudaStream
   S.vals = v.vals; S.qc_row = const_cast<int *>(v.qc_row);
   S.xW = const_cast<double *>(v.xW); S.qW = const_cast<double *>(v.qW);
   S.coef = const_cast<double *>(v.coef); S.coef32 = const_cast<float *>(v.coef32);
+  S.coefff = const_cast<float2 *>(v.coefff);
+  S.ffbad = g->ffbad;
+  e = cudaMemsetAsync(g->ffbad, 0, sizeof(int), stream);
+  if (e != cudaSuccess) return set_error(PDF_ERR_CUDA, "pdf_grid_set_values: %s", cudaGetErrorString(e));
   long long ncoef = (long long)(v.nqc + 1) * v.nx * v.nf;
   k_coef<<<(unsigned)((ncoef + 127) / 128), 128, 0, stream>>>(S);
-  return check_launch("pdf_grid_set_values");
+  int rc = check_launch("pdf_grid_set_values");
+  if (rc) return rc;
+  // the float-float fast path stays on only if the new values allow it
+  int bad = 1;
+  e = cudaMemcpyAsync(&bad, g->ffbad, sizeof(int), cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return set_error(PDF_ERR_CUDA, "pdf_grid_set_values: %s", cudaGetErrorString(e));
+  g->v.ff = bad ? 0 : 1;
+  return PDF_OK;
 }
 
 extern "C" int pdf_grid_reset_invalid_count(pdf_grid *g) {

@@ -42,7 +42,8 @@ enum : int {
   C_LOWX_HIGHQ = 4,  // both
   C_LOWX_LOWQ = 5,
   C_INVALID = 6,
-  NCLASS = 7
+  C_INF = 7,         // inside, contraction in float-float (FP64 path, FP64-level accuracy)
+  NCLASS = 8
 };
 
 // A place where the in-grid interpolant is evaluated: patch cell + position.
@@ -64,6 +65,8 @@ struct GridView {
   double *vals;               // [nrows][nx][nf] device copy of the knot values
   const double *coef;         // [nqc + 1][nx][nf][16]
   const float *coef32;
+  const float2 *coefff;       // [nqc + 1][nx][nf][16] float-float (hi, lo) copy of coef
+  int ff;                     // 1 if every control point is safe for float-float
   const double *xW, *qW;      // [nx][16], [nqc + 1][16]
   const float *xthr32, *q2thr32;   // smallest float >= knot
   const float *xcell32, *qcell32;  // [n][8], see cell32 in grid.cu
@@ -179,6 +182,7 @@ int check_launch(const char *what);
 // The opaque handle.
 struct pdf_grid {
   pdfgb::GridView v;
+  int *ffbad;  // device flag: a control point is outside the float-float range
   int device;
   int pids[PDF_MAX_NFLAV];
   // device allocations owned by the handle

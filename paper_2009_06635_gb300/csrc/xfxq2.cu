@@ -38,6 +38,57 @@ struct WarpRec {
 
 enum { MODE_POINTS = 0, MODE_MC = 1 };
 
+// ---- float-float arithmetic (a value is hi + lo, two floats, ~48 bits) -----
+// Error-free product (FMA) and sum (TwoSum); the _rn intrinsics keep the
+// compiler from contracting or reordering the error terms.
+struct ff2 {
+  float h, l;
+};
+__device__ __forceinline__ ff2 ff_of(double a) {
+  float h = __double2float_rn(a);
+  return {h, __double2float_rn(a - (double)h)};
+}
+__device__ __forceinline__ ff2 ff_mul(ff2 a, ff2 b) {
+  float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, e));
+  float h = __fadd_rn(p, e);
+  return {h, __fsub_rn(e, __fsub_rn(h, p))};
+}
+__device__ __forceinline__ void ff_bernstein(double t, double s, ff2 *B) {
+  const ff2 tf = ff_of(t), sf = ff_of(s), three = {3.f, 0.f};
+  const ff2 t2 = ff_mul(tf, tf), s2 = ff_mul(sf, sf);
+  B[0] = ff_mul(s2, sf);
+  B[1] = ff_mul(three, ff_mul(tf, s2));
+  B[2] = ff_mul(three, ff_mul(t2, sf));
+  B[3] = ff_mul(t2, tf);
+}
+// sum_m w_m b_m with w (hi, lo) from the record and b (hi, lo) from the
+// float-float control points: exact products, TwoSum accumulation, the
+// cross terms and the rounding errors gathered in a second float.
+__device__ __forceinline__ double dot_ff16(const float2 *c, const double (*W)[33], int p) {
+  const float4 *q = reinterpret_cast<const float4 *>(c);
+  float sh = 0.f, sl = 0.f;
+#pragma unroll
+  for (int m2 = 0; m2 < 8; m2++) {
+    const float4 v = __ldg(q + m2);
+#pragma unroll
+    for (int half = 0; half < 2; half++) {
+      const float bh = half ? v.z : v.x, bl = half ? v.w : v.y;
+      const float2 w = *reinterpret_cast<const float2 *>(&W[2 * m2 + half][p]);
+      const float ph = __fmul_rn(w.x, bh);
+      float pe = __fmaf_rn(w.x, bh, -ph);
+      pe = __fmaf_rn(w.x, bl, __fmaf_rn(w.y, bh, pe));
+      const float t = __fadd_rn(sh, ph);
+      const float bp = __fsub_rn(t, sh);
+      const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bp)), __fsub_rn(ph, bp));
+      sh = t;
+      sl = __fadd_rn(sl, __fadd_rn(err, pe));
+    }
+  }
+  return (double)sh + (double)sl;
+}
+
 // ---- FP64 item evaluation (one lane per item) ----------------------------
 __device__ __forceinline__ double dot_w16(const double *c, const WarpRec<double> &R, int p) {
   const double2 *q = reinterpret_cast<const double2 *>(c);
@@ -93,6 +144,10 @@ __device__ __forceinline__ double eval_item64(const GridView &g, const WarpRec<d
     return cb + ((size_t)qc * g.nx + xc) * stride;
   };
   switch (R.cls[p]) {
+    case C_INF: {
+      const int xc = R.xc0[p], qc = R.qc0[p];
+      return dot_ff16(g.coefff + (((size_t)qc * g.nx + xc) * g.nf + col) * 16, R.W, p);
+    }
     case C_IN: return dot_w16(C(0, 0), R, p);
     case C_LOWX:  // sites (x0, Q^2), (x1, Q^2): t = 0
       return pair_rule(site_u(C(0, 0), R, p, 0), site_u(C(1, 0), R, p, 0), R.px[p]);
@@ -174,6 +229,20 @@ __device__ __forceinline__ float eval_item32(const GridView &g, const WarpRec<fl
 template <typename T>
 __device__ __forceinline__ void store_weights(WarpRec<T> &R, int slot, const PointSites<T> &ps,
                                               const GridView &g) {
+  if (sizeof(T) == 8 && ps.cls == C_INF) {  // float-float weights for the FP64 contraction
+    ff2 bx[4], bq[4];
+    ff_bernstein((double)ps.t0, (double)ps.ts0, bx);
+    ff_bernstein((double)ps.u0, (double)ps.us0, bq);
+#pragma unroll
+    for (int l = 0; l < 4; l++)
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        const ff2 w = ff_mul(bx[k], bq[l]);
+        float2 *slot_ptr = reinterpret_cast<float2 *>(&R.W[l * 4 + k][slot]);
+        *slot_ptr = make_float2(w.h, w.l);
+      }
+    return;
+  }
   T bx0[4], bx1[4], bq0[4], bq1[4];
   bernstein<T>(ps.t0, ps.ts0, bx0);
   bernstein<T>(ps.t1, T(1) - ps.t1, bx1);
@@ -248,6 +317,9 @@ k_xf(GridView g, const T *__restrict__ xa, const T *__restrict__ qa, const T *__
     PointSites<T> ps;
     ps.cls = NCLASS;
     if (present) ps = sites(g, xkeys, qkeys, x, q2);
+    // FP64 in-grid points contract in float-float, except exact knot hits
+    // (t = u = 0), which keep the FP64 path so that knots stay bit-exact
+    if (sizeof(T) == 8 && ps.cls == C_IN && g.ff && !(ps.t0 == T(0) && ps.u0 == T(0))) ps.cls = C_INF;
     unsigned inv = __ballot_sync(0xffffffffu, present && ps.cls == C_INVALID);
     if (lane == 0 && inv) atomicAdd(g.invalid, (unsigned long long)__popc(inv));
 
