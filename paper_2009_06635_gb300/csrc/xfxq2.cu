@@ -32,6 +32,7 @@ constexpr int kThreads = 32 * kWarps;
 template <typename T>
 struct WarpRec {
   int cls[32], orig[32], xc0[32], xc1[32], qc0[32], qc1[32];
+  int off4[32];  // FP32 in-grid points: float4 offset of the cell's first flavour block
   T W[16][33];  // padded: rows of one slot fall in different banks
   T px[32], pq[32], lr[32], as[32];
 };
@@ -335,6 +336,7 @@ k_xf(GridView g, const T *__restrict__ xa, const T *__restrict__ qa, const T *__
       }
     }
     R.cls[slot] = ps.cls; R.orig[slot] = lane;
+    if (sizeof(T) == 4) R.off4[slot] = ((ps.qc0 * g.nx + ps.xc0) * g.nf + col0) * 4;
     R.xc0[slot] = ps.xc0; R.xc1[slot] = ps.xc1; R.qc0[slot] = ps.qc0; R.qc1[slot] = ps.qc1;
     R.px[slot] = ps.px; R.pq[slot] = ps.pq; R.lr[slot] = ps.lr;
     if (present && ps.cls != C_INVALID) store_weights<T>(R, slot, ps, g);
@@ -353,21 +355,27 @@ k_xf(GridView g, const T *__restrict__ xa, const T *__restrict__ qa, const T *__
           const long long ob = MODE == MODE_POINTS ? (e0 + RF.orig[q]) * (long long)ncol
                                                    : (e0 + (q >> 1)) * (long long)per + (q & 1) * g.nf;
           if (RF.cls[q] == C_IN) {
-            // the point's column blocks are contiguous: lane k reads row k & 3
-            // of column k >> 2 at cell_base + 4 k
-            const float *cbp = g.coef32 + ((size_t)RF.qc0[q] * g.nx + RF.xc0[q]) * g.nf * 16 + col0 * 16;
+            // the point's column blocks are contiguous: lane k owns rows 2h, 2h+1
+            // (h = k & 1) of column k >> 1, 32 bytes at cell_base + 8 k floats
+            const float4 *cbp = reinterpret_cast<const float4 *>(g.coef32) + RF.off4[q];
             const float b0 = RF.W[0][q], b1 = RF.W[1][q], b2 = RF.W[2][q], b3 = RF.W[3][q];
-            const float bq = RF.W[8 + r][q];
-            for (int k = lane; k < 4 * nc; k += 32) {
-              const float4 v = __ldg(reinterpret_cast<const float4 *>(cbp) + k);
-              float part = b0 * v.x;
-              part = fmaf(b1, v.y, part);
-              part = fmaf(b2, v.z, part);
-              part = fmaf(b3, v.w, part);
-              part = __fmul_rn(part, bq);
-              part += __shfl_xor_sync(gm, part, 1);
-              part += __shfl_xor_sync(gm, part, 2);
-              if (r == 0) out[ob + (k >> 2)] = part;
+            const int hr = lane & 1;
+            const float bqa = RF.W[8 + 2 * hr][q], bqb = RF.W[9 + 2 * hr][q];
+            const unsigned pm = 3u << (lane & 30);
+            for (int k = lane; k < 2 * nc; k += 32) {
+              const float4 v0 = __ldg(cbp + 2 * k), v1 = __ldg(cbp + 2 * k + 1);
+              float ra = b0 * v0.x;
+              ra = fmaf(b1, v0.y, ra);
+              ra = fmaf(b2, v0.z, ra);
+              ra = fmaf(b3, v0.w, ra);
+              float rb = b0 * v1.x;
+              rb = fmaf(b1, v1.y, rb);
+              rb = fmaf(b2, v1.z, rb);
+              rb = fmaf(b3, v1.w, rb);
+              // (p0 + p1) + (p2 + p3), the order of every FP32 patch sum
+              float part = __fadd_rn(__fmul_rn(ra, bqa), __fmul_rn(rb, bqb));
+              const float other = __shfl_xor_sync(pm, part, 1);
+              if (hr == 0) out[ob + (k >> 1)] = __fadd_rn(part, other);
             }
           } else {
             for (int k = lane; k < 4 * nc; k += 32) {
