@@ -38,6 +38,9 @@ N_POINTS = 10_000_000
 MC_EVENTS = 1_000_000
 ADJ_POINTS = 1_000_000
 SURR_TRAIN, SURR_VAL, SURR_INFER = 20_000_000, 1_000_000, 100_000_000
+# PDFFlow Table 2 (Sec. 4.3): all 13 flavours of N_rep members at 2415 x
+# points, PDFFlow on a TITAN V or RTX 2080 Ti (system P1), seconds
+TABLE2 = {10: 0.07, 50: 0.35, 100: 0.69, 200: 1.46, 300: 1.29, 400: 1.69}
 SURR_FLOPS_PER_POINT = 2 * (32 * 128 + 3 * 128 * 128 + 128 * 16)  # padded output layer
 SURR_SFU_PER_POINT = 4 * 128 + 32  # tanh per SiLU, sin/cos per feature
 WORKLOAD = ("three Q subgrids (12/15/25 Q knots split at Q = 1.51 and 4.92 GeV, Q in [1, 1e5] GeV), "
@@ -352,6 +355,31 @@ def surrogate_leg(args, G, g, dev, world, sync, rank, nf, ms_per_eval64):
     }
 
 
+def members_leg(args, dev, world, sync, rank):
+    """PDFFlow Table 2 workload: 13 flavours x N_rep members x 2415 x points
+    (x log-spaced in [1e-9, 1), Q = 1.65 GeV), one launch per N_rep."""
+    import torch
+
+    import paper_2009_06635_gb300 as P
+    from paper_2009_06635_gb300 import synthetic as S
+
+    g0, vals = S.grid_members(max(TABLE2), seed=12 + 1000 * rank)
+    x, q2 = S.fit_points()
+    xd, qd = torch.from_numpy(x).to(dev), torch.from_numpy(q2).to(dev)
+    rows = []
+    for nrep in sorted(TABLE2):
+        G = P.pdf_load_grid(g0, member_values=vals[:nrep])
+        out = torch.empty((nrep, len(x), g0.nflav), dtype=torch.float64, device=dev)
+        ms = run_timed(lambda: P.xfxq2_all_members(G, xd, qd, out=out), max(5, args.steps // 5), 3, world, sync)
+        evals = nrep * len(x) * g0.nflav
+        rows.append({"n_rep": nrep, "evals": evals, "ms": ms, "evals_per_s": world * evals / (ms * 1e-3),
+                     "paper_gpu_s": TABLE2[nrep], "paper_gpu_evals_per_s": evals / TABLE2[nrep]})
+        del G, out
+    return {"rows": rows, "workload": "13 flavours x N_rep members x 2415 x points (log-spaced in [1e-9, 1)), "
+            "Q = 1.65 GeV; members perturb the synthetic set's flavour parameters",
+            "paper_hardware": "PDFFlow v1.0 on TITAN V or RTX 2080 Ti (system P1); context, not the target"}
+
+
 def P_xf(G, x, q2):
     import paper_2009_06635_gb300 as P
 
@@ -461,6 +489,7 @@ def our_arm(args):
 
     ms_adj = run_timed(step_adj, args.steps, 2, world, sync)
 
+    members = None if args.no_members else members_leg(args, dev, world, sync, rank)
     surrogate = None if args.no_surrogate else surrogate_leg(args, G, g, dev, world, sync, rank, nf, ms64 / (n * (nf + 1)))
 
     # end to end through the C ABI with host buffers (pinned), copies timed
@@ -530,6 +559,7 @@ def our_arm(args):
             "mc_event_fp32": {"value": world * MC_EVENTS * (2 * nf + 1) / (ms_mc32 * 1e-3),
                               "ms_per_step": ms_mc32, "events": MC_EVENTS},
             "surrogate_bf16": surrogate,
+            "members_table2": members,
             "adjoint_fp64": {"value": world * ADJ_POINTS * nf / (ms_adj * 1e-3), "ms_per_step": ms_adj,
                              "points": ADJ_POINTS, "unit": "(point, flavour) gradients/s",
                              "outputs": "d/dx, d/dQ^2 per point and d/d(knot values), FP64 atomics"},
@@ -559,6 +589,7 @@ def main():
     ap.add_argument("--points", type=int, default=N_POINTS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--no-members", action="store_true")
     ap.add_argument("--only", choices=["fp64", "fp32"], default=None,
                     help="run only that path's step (a small case for profiling); prints its timing")
     args = ap.parse_args()

@@ -110,6 +110,15 @@ typedef struct {
  * Synchronous; uses the current CUDA device.  *out receives the handle. */
 PDF_API int pdf_load_grid(const pdf_grid_desc *desc, pdf_grid **out);
 
+/* A set of PDF members (replicas of a fit) that share the knots, subgrids
+ * and flavours of `desc`: member m's values are member_values[m] laid out as
+ * desc->values ([nmem][rows][nx][nflav] host FP64; desc->values is ignored).
+ * Every other call evaluates member 0; xfxq2_all_members evaluates all of
+ * them.  PDFFlow Sec. 4.3 (multi-member evaluation for fits, Table 2). */
+PDF_API int pdf_load_grid_members(const pdf_grid_desc *desc, int nmem, const double *member_values,
+                                  pdf_grid **out);
+PDF_API int pdf_grid_nmembers(const pdf_grid *grid);
+
 /* Free a handle and all its device memory (NULL is a no-op).  Waits for
  * work the handle's own streams still run. */
 PDF_API int pdf_free_grid(pdf_grid *grid);
@@ -126,6 +135,12 @@ PDF_API int xfxq2(const pdf_grid *grid, int pid, const double *x, const double *
 /* All flavours at n points: out is [n][nflav] FP64.  PDFFlow (xfxQ2_allpid). */
 PDF_API int xfxq2_all_flavours(const pdf_grid *grid, const double *x, const double *q2, size_t n,
                        double *out, cudaStream_t stream);
+
+/* All flavours of all members at n points: out is [nmem][n][nflav] FP64.
+ * The cell search, logarithms and weights of a point are computed once and
+ * reused for every member.  PDFFlow Sec. 4.3. */
+PDF_API int xfxq2_all_members(const pdf_grid *grid, const double *x, const double *q2, size_t n,
+                              double *out, cudaStream_t stream);
 
 /* alpha_s(Q^2) at n points, FP64 [n].  PDFFlow Sec. 2.3 (alphas_Q2). */
 PDF_API int alphas_q2(const pdf_grid *grid, const double *q2, size_t n, double *out,

@@ -48,6 +48,9 @@ SIGNATURES = {
     "pdf_load_grid": (I32, [ctypes.POINTER(GridDesc), ctypes.POINTER(P)]),
     "pdf_free_grid": (I32, [P]),
     "pdf_grid_nflav": (I32, [P]),
+    "pdf_load_grid_members": (I32, [ctypes.POINTER(GridDesc), I32, P, ctypes.POINTER(P)]),
+    "pdf_grid_nmembers": (I32, [P]),
+    "xfxq2_all_members": (I32, [P, P, P, SZ, P, P]),
     "pdf_grid_pid_column": (I32, [P, I32]),
     "xfxq2": (I32, [P, I32, P, P, SZ, P, P]),
     "xfxq2_all_flavours": (I32, [P, P, P, SZ, P, P]),

@@ -69,6 +69,7 @@ struct Stage {
   const double *xk, *q2k, *vals, *aq2, *aval;
   const int *first, *nq;
   int nx, nrows, nf, na, nsub, nxc, nqc;
+  int nmem;  // members: values and control points repeat per member
   // outputs
   double *lx, *lq, *alq;
   double *xcell, *qcell, *xW, *qW, *coef, *acell;
@@ -165,12 +166,14 @@ __global__ void k_qcells(Stage S) {
   cell_weights(aL, bm, dR, gp, S.qW + 16 * qc);
 }
 
-// One thread per (q cell, x cell, flavour) slot, degenerate ones included:
-// control point b[l][k] = sum_ab W_x[a][k] W_q[b][l] f_ab.
+// One thread per (member, q cell, x cell, flavour) slot, degenerate ones
+// included: control point b[l][k] = sum_ab W_x[a][k] W_q[b][l] f_ab.
 __global__ void k_coef(Stage S) {
-  long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  long long total = (long long)(S.nqc + 1) * S.nx * S.nf;
-  if (id >= total) return;
+  long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long per = (long long)(S.nqc + 1) * S.nx * S.nf;
+  if (gid >= per * (S.nmem > 0 ? S.nmem : 1)) return;
+  const long long mem = gid / per, id = gid - mem * per;
+  const double *vals = S.vals + mem * (long long)S.nrows * S.nx * S.nf;
   int f = (int)(id % S.nf);
   long long cell = id / S.nf;
   int xc = (int)(cell % S.nx), qc = (int)(cell / S.nx);
@@ -184,16 +187,16 @@ __global__ void k_coef(Stage S) {
     for (int a = 0; a < 4; a++) {
       int col = i - 1 + a;
       if (col < 0 || col >= S.nx) continue;
-      double fv = S.vals[((size_t)row * S.nx + col) * S.nf + f];
+      double fv = vals[((size_t)row * S.nx + col) * S.nf + f];
       for (int l = 0; l < 4; l++) {
         double wl = Wq[b * 4 + l] * fv;
         for (int k = 0; k < 4; k++) c[l * 4 + k] = fma(Wx[a * 4 + k], wl, c[l * 4 + k]);
       }
     }
   }
-  double *o = S.coef + (size_t)id * 16;
-  float *o32 = S.coef32 + (size_t)id * 16;
-  float2 *off = S.coefff + (size_t)id * 16;
+  double *o = S.coef + (size_t)gid * 16;
+  float *o32 = S.coef32 + (size_t)gid * 16;
+  float2 *off = S.coefff + (size_t)gid * 16;
   bool bad = false;
   for (int m = 0; m < 16; m++) {
     o[m] = c[m];
@@ -356,28 +359,39 @@ using namespace pdfgb;
 
 extern "C" const char *pdf_last_error(void) { return g_errbuf; }
 
-extern "C" int pdf_load_grid(const pdf_grid_desc *d, pdf_grid **out) {
+static int load_impl(const pdf_grid_desc *d, int nmem, const double *member_values, pdf_grid **out) {
   g_errbuf[0] = 0;
   if (!out) return set_error(PDF_ERR_NULL, "pdf_load_grid: out is NULL");
   *out = nullptr;
+  if (!d) return set_error(PDF_ERR_NULL, "pdf_load_grid: descriptor is NULL");
+  pdf_grid_desc dd = *d;  // a member set is validated on its first member
+  if (member_values) dd.values = member_values;
   int nrows = 0;
-  int rc = validate(d, &nrows);
+  int rc = validate(&dd, &nrows);
   if (rc) return rc;
+  d = &dd;
+  if (nmem < 1) return set_error(PDF_ERR_ARG, "pdf_load_grid_members: nmem = %d < 1", nmem);
+  if (member_values) {
+    size_t nv = (size_t)nmem * nrows * d->nx * d->nflav;
+    for (size_t k = 0; k < nv; k++)
+      if (!std::isfinite(member_values[k])) return set_error(PDF_ERR_GRID, "pdf_load_grid_members: value %zu not finite", k);
+  }
+  const double *values0 = member_values ? member_values : d->values;
   const int nx = d->nx, nf = d->nflav, na = d->na, nsub = d->nsub;
   const int nxc = nx - 1, nqc = nrows - nsub;
 
   // sizes (a dry run of the arena)
   auto layout = [&](Arena &A, Stage &S, unsigned long long **inv) {
     S.xk = A.take<double>(nx); S.q2k = A.take<double>(nrows);
-    S.vals = A.take<double>((size_t)nrows * nx * nf);
+    S.vals = A.take<double>((size_t)nmem * nrows * nx * nf);
     S.aq2 = A.take<double>(na > 0 ? na : 1); S.aval = A.take<double>(na > 0 ? na : 1);
     S.first = A.take<int>(nsub); S.nq = A.take<int>(nsub);
     S.lx = A.take<double>(nx); S.lq = A.take<double>(nrows); S.alq = A.take<double>(na > 0 ? na : 1);
     S.xcell = A.take<double>(4 * nx); S.qcell = A.take<double>(4 * nrows);
     S.xW = A.take<double>(16 * nx); S.qW = A.take<double>(16 * (nqc + 1));
-    S.coef = A.take<double>((size_t)(nqc + 1) * nx * nf * 16);
-    S.coef32 = A.take<float>((size_t)(nqc + 1) * nx * nf * 16);
-    S.coefff = A.take<float2>((size_t)(nqc + 1) * nx * nf * 16);
+    S.coef = A.take<double>((size_t)nmem * (nqc + 1) * nx * nf * 16);
+    S.coef32 = A.take<float>((size_t)nmem * (nqc + 1) * nx * nf * 16);
+    S.coefff = A.take<float2>((size_t)nmem * (nqc + 1) * nx * nf * 16);
     S.ffbad = A.take<int>(1);
     S.acell = A.take<double>(6 * (na > 0 ? na : 1));
     S.acell32 = A.take<float>(6 * (na > 0 ? na : 1));
@@ -408,6 +422,7 @@ extern "C" int pdf_load_grid(const pdf_grid_desc *d, pdf_grid **out) {
   A.cap = dry.off;
   layout(A, S, &inv);
   S.nx = nx; S.nrows = nrows; S.nf = nf; S.na = na; S.nsub = nsub; S.nxc = nxc; S.nqc = nqc;
+  S.nmem = nmem;
 
   int first[1024];
   for (int s = 0, r = 0; s < nsub; s++) { first[s] = r; r += d->nq[s]; }
@@ -416,7 +431,7 @@ extern "C" int pdf_load_grid(const pdf_grid_desc *d, pdf_grid **out) {
   };
   H2D(S.xk, d->x_knots, sizeof(double) * nx);
   H2D(S.q2k, d->q2_knots, sizeof(double) * nrows);
-  H2D(S.vals, d->values, sizeof(double) * (size_t)nrows * nx * nf);
+  H2D(S.vals, values0, sizeof(double) * (size_t)nmem * nrows * nx * nf);
   if (na > 0) { H2D(S.aq2, d->as_q2, sizeof(double) * na); H2D(S.aval, d->as_vals, sizeof(double) * na); }
   H2D(S.first, first, sizeof(int) * nsub);
   H2D(S.nq, d->nq, sizeof(int) * nsub);
@@ -432,7 +447,7 @@ extern "C" int pdf_load_grid(const pdf_grid_desc *d, pdf_grid **out) {
   k_logs<<<(nmax + 127) / 128, 128>>>(S);
   k_xcells<<<(nx + 127) / 128, 128>>>(S);
   k_qcells<<<(nrows + 127) / 128, 128>>>(S);
-  long long ncoef = (long long)(nqc + 1) * nx * nf;
+  long long ncoef = (long long)nmem * (nqc + 1) * nx * nf;
   k_coef<<<(unsigned)((ncoef + 127) / 128), 128>>>(S);
   if (na > 1) k_acells<<<(na + 127) / 128, 128>>>(S);
   k_scalars<<<1, 32>>>(S);
@@ -453,6 +468,8 @@ extern "C" int pdf_load_grid(const pdf_grid_desc *d, pdf_grid **out) {
   v.qc_row = S.qc_row; v.vals = const_cast<double *>(S.vals);
   v.coef = S.coef; v.coef32 = S.coef32; v.xW = S.xW; v.qW = S.qW;
   v.coefff = S.coefff; v.ff = ffbad ? 0 : 1;
+  v.nmem = nmem;
+  v.mstride = (size_t)(nqc + 1) * nx * nf * 16;
   g->ffbad = S.ffbad;
   v.xthr32 = S.xthr32; v.q2thr32 = S.q2thr32; v.xcell32 = S.xcell32; v.qcell32 = S.qcell32;
   v.aq2 = S.aq2; v.acell = S.acell; v.acell32 = S.acell32; v.aq2thr32 = S.aq2thr32;
@@ -479,6 +496,16 @@ extern "C" int pdf_load_grid(const pdf_grid_desc *d, pdf_grid **out) {
   *out = g;
   return PDF_OK;
 }
+
+extern "C" int pdf_load_grid(const pdf_grid_desc *d, pdf_grid **out) { return load_impl(d, 1, nullptr, out); }
+
+extern "C" int pdf_load_grid_members(const pdf_grid_desc *d, int nmem, const double *member_values,
+                                     pdf_grid **out) {
+  if (!member_values) return set_error(PDF_ERR_NULL, "pdf_load_grid_members: member_values is NULL");
+  return load_impl(d, nmem, member_values, out);
+}
+
+extern "C" int pdf_grid_nmembers(const pdf_grid *g) { return g ? g->v.nmem : set_error(PDF_ERR_NULL, "grid is NULL"); }
 
 extern "C" int pdf_free_grid(pdf_grid *g) {
   if (!g) return PDF_OK;
@@ -516,6 +543,7 @@ extern "C" int pdf_grid_set_values(pdf_grid *g, const double *values, cudaStream
   if (e != cudaSuccess) return set_error(PDF_ERR_CUDA, "pdf_grid_set_values: %s", cudaGetErrorString(e));
   Stage S{};
   S.nx = v.nx; S.nrows = v.nrows; S.nf = v.nf; S.nqc = v.nqc; S.nxc = v.nxc;
+  S.nmem = 1;  // member 0
   S.vals = v.vals; S.qc_row = const_cast<int *>(v.qc_row);
   S.xW = const_cast<double *>(v.xW); S.qW = const_cast<double *>(v.qW);
   S.coef = const_cast<double *>(v.coef); S.coef32 = const_cast<float *>(v.coef32);

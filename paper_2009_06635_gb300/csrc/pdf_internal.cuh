@@ -67,6 +67,8 @@ struct GridView {
   const float *coef32;
   const float2 *coefff;       // [nqc + 1][nx][nf][16] float-float (hi, lo) copy of coef
   int ff;                     // 1 if every control point is safe for float-float
+  int nmem;                   // members (replicas) sharing the knots; member m's
+  size_t mstride;             // control points start m * mstride elements further
   const double *xW, *qW;      // [nx][16], [nqc + 1][16]
   const float *xthr32, *q2thr32;   // smallest float >= knot
   const float *xcell32, *qcell32;  // [n][8], see cell32 in grid.cu

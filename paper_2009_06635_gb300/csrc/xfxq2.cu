@@ -37,7 +37,7 @@ struct WarpRec {
   T px[32], pq[32], lr[32], as[32];
 };
 
-enum { MODE_POINTS = 0, MODE_MC = 1 };
+enum { MODE_POINTS = 0, MODE_MC = 1, MODE_MEMBERS = 2 };
 
 // ---- float-float arithmetic (a value is hi + lo, two floats, ~48 bits) -----
 // Error-free product (FMA) and sum (TwoSum); the _rn intrinsics keep the
@@ -136,8 +136,9 @@ __device__ __forceinline__ double site_t(const double *c, const WarpRec<double> 
   return fma(R.W[4 * a + 3][p], v1.y, f);
 }
 
-__device__ __forceinline__ double eval_item64(const GridView &g, const WarpRec<double> &R, int p, int col) {
-  const double *cb = g.coef + (size_t)col * 16;
+__device__ __forceinline__ double eval_item64(const GridView &g, const WarpRec<double> &R, int p, int col,
+                                              size_t moff = 0) {
+  const double *cb = g.coef + moff + (size_t)col * 16;
   const size_t stride = (size_t)g.nf * 16;
   auto C = [&](int a, int b) {
     int xc = a ? R.xc1[p] : R.xc0[p];
@@ -147,7 +148,7 @@ __device__ __forceinline__ double eval_item64(const GridView &g, const WarpRec<d
   switch (R.cls[p]) {
     case C_INF: {
       const int xc = R.xc0[p], qc = R.qc0[p];
-      return dot_ff16(g.coefff + (((size_t)qc * g.nx + xc) * g.nf + col) * 16, R.W, p);
+      return dot_ff16(g.coefff + moff + (((size_t)qc * g.nx + xc) * g.nf + col) * 16, R.W, p);
     }
     case C_IN: return dot_w16(C(0, 0), R, p);
     case C_LOWX:  // sites (x0, Q^2), (x1, Q^2): t = 0
@@ -265,12 +266,15 @@ __device__ __forceinline__ void store_weights(WarpRec<T> &R, int slot, const Poi
   }
 }
 
-// MODE_POINTS: points xa[n], qa[n]; out[n][ncol] for columns col0..col0+ncol-1.
-// MODE_MC:     events xa[n] (x1), xb[n] (x2), Q^2 = x1 x2 s; out[n][2 nf + 1].
+// MODE_POINTS:  points xa[n], qa[n]; out[n][ncol] for columns col0..col0+ncol-1.
+// MODE_MC:      events xa[n] (x1), xb[n] (x2), Q^2 = x1 x2 s; out[n][2 nf + 1].
+// MODE_MEMBERS: points xa[n], qa[n]; out[nmem][n][nf], FP64 only.  A warp's
+//               unit is (tile, chunk of mchunk members), so a few points times
+//               many members still fill the GPU; phase 1 repeats per chunk.
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 8 ? 3 : 4)
 k_xf(GridView g, const T *__restrict__ xa, const T *__restrict__ qa, const T *__restrict__ xb,
-     T s, long long n, int col0, int ncol, T *__restrict__ out) {
+     T s, long long n, int col0, int ncol, int mchunk, T *__restrict__ out) {
   using K = typename Prec<T>::K;
   constexpr int LPI = sizeof(T) == 8 ? 1 : 4;  // lanes per item
   constexpr int IPI = 32 / LPI;                // items per warp instruction (FP64 loop)
@@ -294,19 +298,23 @@ k_xf(GridView g, const T *__restrict__ xa, const T *__restrict__ qa, const T *__
   const int r = lane & (LPI - 1);
   const unsigned gm = LPI == 1 ? 1u << lane : 0xFu << (lane & ~3);
   const long long ntiles = (n + per_tile - 1) / per_tile;
+  const int nchunks = MODE == MODE_MEMBERS ? (g.nmem + mchunk - 1) / mchunk : 1;
+  const long long nunits = ntiles * nchunks;
   const long long nwarps = (long long)gridDim.x * kWarps;
 
-  for (long long tile = (long long)blockIdx.x * kWarps + warp; tile < ntiles; tile += nwarps) {
+  for (long long unit = (long long)blockIdx.x * kWarps + warp; unit < nunits; unit += nwarps) {
+    const long long tile = unit / nchunks;
+    const int chunk = (int)(unit - tile * nchunks);
     const long long e0 = tile * per_tile;
     const int ne = (int)(n - e0 < per_tile ? n - e0 : per_tile);
 
     // ---- phase 1: lane = point ----
     bool present;
     T x = T(0), q2 = T(0);
-    if (MODE == MODE_POINTS) {
+    if (MODE != MODE_MC) {  // points (also member sets): xa[n], qa[n]
       present = lane < ne;
       if (present) { x = xa[e0 + lane]; q2 = qa[e0 + lane]; }
-    } else {
+    } else {  // events: x1 = xa, x2 = xb
       const int e = lane >> 1;
       present = e < ne;
       if (present) {
@@ -325,7 +333,7 @@ k_xf(GridView g, const T *__restrict__ xa, const T *__restrict__ qa, const T *__
     if (lane == 0 && inv) atomicAdd(g.invalid, (unsigned long long)__popc(inv));
 
     int slot = lane;
-    if (MODE == MODE_POINTS) {  // order points by class (counting sort over the warp)
+    if (MODE != MODE_MC) {  // order points by class (counting sort over the warp)
       int base = 0;
       const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
@@ -386,6 +394,25 @@ k_xf(GridView g, const T *__restrict__ xa, const T *__restrict__ qa, const T *__
           }
         }
         if (MODE == MODE_MC && lane < ne) out[(e0 + lane) * (long long)per + 2 * g.nf] = RF.as[lane];
+      }
+      __syncwarp();
+      continue;
+    }
+
+    // ---- phase 2, FP64, member sets: the same sites for every member ----
+    if constexpr (MODE == MODE_MEMBERS) {
+      const WarpRec<double> &RD = reinterpret_cast<const WarpRec<double> &>(R);
+      const int m1 = min(g.nmem, (chunk + 1) * mchunk);
+      for (int m = chunk * mchunk; m < m1; m++) {
+        const size_t moff = (size_t)m * g.mstride;
+        const int nitems = ne * per;
+        int p = lane / per, c = lane - (lane / per) * per;
+        for (int k = lane; k < nitems; k += 32) {
+          out[((long long)m * n + e0 + RD.orig[p]) * per + c] = (T)eval_item64(g, RD, p, c, moff);
+          c += dc;
+          p += dp;
+          if (c >= per) { c -= per; p++; }
+        }
       }
       __syncwarp();
       continue;
@@ -479,10 +506,23 @@ static int launch_xf(const pdf_grid *grid, const T *xa, const T *qa, const T *xb
   if (per_sm < 1) per_sm = 1;
   const int per_tile = MODE == MODE_MC ? 16 : 32;
   long long ntiles = (n + per_tile - 1) / per_tile;
-  long long blocks = (ntiles + kWarps - 1) / kWarps;
   long long cap = (long long)num_sms() * per_sm;
+  // member sets: split the members into chunks until there are about two
+  // units per resident warp (one chunk when the points alone suffice)
+  int mchunk = 1;
+  long long nunits = ntiles;
+  if (MODE == MODE_MEMBERS) {
+    const long long target = 2 * cap * kWarps;
+    long long nchunks = (target + ntiles - 1) / ntiles;
+    if (nchunks > g.nmem) nchunks = g.nmem;
+    if (nchunks < 1) nchunks = 1;
+    mchunk = (int)((g.nmem + nchunks - 1) / nchunks);
+    nchunks = (g.nmem + mchunk - 1) / mchunk;
+    nunits = ntiles * nchunks;
+  }
+  long long blocks = (nunits + kWarps - 1) / kWarps;
   if (blocks > cap) blocks = cap;
-  kern<<<(unsigned)blocks, kThreads, smem, st>>>(g, xa, qa, xb, s, n, col0, ncol, out);
+  kern<<<(unsigned)blocks, kThreads, smem, st>>>(g, xa, qa, xb, s, n, col0, ncol, mchunk, out);
   return check_launch(MODE == MODE_MC ? "pdf_mc_event kernel" : "xfxq2 kernel");
 }
 
@@ -544,6 +584,11 @@ static int do_mc(const pdf_grid *g, const T *x1, const T *x2, T s, size_t n, T *
   return launch_xf<T, MODE_MC>(g, x1, nullptr, x2, s, (long long)n, 0, 0, out, st);
 }
 
+int launch_members_f64(const pdf_grid *g, const double *x, const double *q2, long long n, double *out,
+                       cudaStream_t st) {
+  return launch_xf<double, MODE_MEMBERS>(g, x, q2, nullptr, 0.0, n, 0, g->v.nf, out, st);
+}
+
 // Used by the host-memory path.
 int launch_alphas_f64(const pdf_grid *g, const double *q2, long long n, double *out, cudaStream_t st) {
   return launch_alphas<double>(g, q2, n, out, st);
@@ -579,6 +624,14 @@ extern "C" int alphas_q2(const pdf_grid *g, const double *q2, size_t n, double *
 extern "C" int alphas_q2_f32(const pdf_grid *g, const float *q2, size_t n, float *out, cudaStream_t st) {
   return do_alphas<float>(g, q2, n, out, st);
 }
+extern "C" int xfxq2_all_members(const pdf_grid *g, const double *x, const double *q2, size_t n, double *out,
+                                 cudaStream_t st) {
+  int rc = check_common(g, x, q2, out, n, "xfxq2_all_members");
+  if (rc) return rc;
+  if (n == 0) return PDF_OK;
+  return launch_members_f64(g, x, q2, (long long)n, out, st);
+}
+
 extern "C" int pdf_mc_event(const pdf_grid *g, const double *x1, const double *x2, double s, size_t n,
                             double *out, cudaStream_t st) {
   return do_mc<double>(g, x1, x2, s, n, out, st);

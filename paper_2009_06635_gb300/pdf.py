@@ -36,12 +36,13 @@ def _dev_ptr(t: torch.Tensor, dtype, name: str) -> ctypes.c_void_p:
 class Grid:
     """A loaded PDF set (owns the device-side handle)."""
 
-    def __init__(self, handle: int, pids, device: torch.device, nx: int, nrows: int):
+    def __init__(self, handle: int, pids, device: torch.device, nx: int, nrows: int, nmem: int = 1):
         self._h = ctypes.c_void_p(handle)
         self.pids = list(pids)
         self.nflav = len(self.pids)
         self.nx = nx
         self.nrows = nrows
+        self.nmem = nmem
         self.device = device
 
     @property
@@ -74,9 +75,10 @@ class Grid:
 
 
 def pdf_load_grid(grid=None, *, x_knots=None, nq=None, q2_knots=None, pids=None, values=None,
-                  as_q2=None, as_vals=None, device=None) -> Grid:
+                  as_q2=None, as_vals=None, device=None, member_values=None) -> Grid:
     """Load a PDF set (any object with x_knots, nq, q2_knots, pids, values,
-    as_q2, as_vals, or the same as keywords) onto the current CUDA device."""
+    as_q2, as_vals, or the same as keywords) onto the current CUDA device.
+    member_values [nmem][rows][nx][nflav] loads a member set sharing the knots."""
     if grid is not None:
         x_knots, nq, q2_knots, pids, values = grid.x_knots, grid.nq, grid.q2_knots, grid.pids, grid.values
         as_q2, as_vals = grid.as_q2, grid.as_vals
@@ -91,14 +93,23 @@ def pdf_load_grid(grid=None, *, x_knots=None, nq=None, q2_knots=None, pids=None,
     av = np.ascontiguousarray([] if as_vals is None else as_vals, dtype=np.float64)
     if va.ndim != 3 or va.shape != (q2k.shape[0], xk.shape[0], pa.shape[0]):
         raise PdfError(-2, f"values shape {va.shape} != (rows, nx, nflav)")
+    mv = None
+    if member_values is not None:
+        mv = np.ascontiguousarray(member_values, dtype=np.float64)
+        if mv.ndim != 4 or mv.shape[1:] != va.shape:
+            raise PdfError(-2, f"member_values shape {mv.shape} != (nmem, rows, nx, nflav)")
     d = _native.GridDesc(
         int(xk.shape[0]), xk.ctypes.data, int(nqa.shape[0]), nqa.ctypes.data, q2k.ctypes.data,
         int(pa.shape[0]), pa.ctypes.data, va.ctypes.data, int(aq.shape[0]),
         aq.ctypes.data if aq.size else None, av.ctypes.data if av.size else None)
     h = ctypes.c_void_p(None)
     with torch.cuda.device(dev):
-        check(lib.pdf_load_grid(ctypes.byref(d), ctypes.byref(h)), "pdf_load_grid")
-    return Grid(h.value, pa.tolist(), dev, int(xk.shape[0]), int(q2k.shape[0]))
+        if mv is None:
+            check(lib.pdf_load_grid(ctypes.byref(d), ctypes.byref(h)), "pdf_load_grid")
+        else:
+            check(lib.pdf_load_grid_members(ctypes.byref(d), int(mv.shape[0]), mv.ctypes.data, ctypes.byref(h)),
+                  "pdf_load_grid_members")
+    return Grid(h.value, pa.tolist(), dev, int(xk.shape[0]), int(q2k.shape[0]), 1 if mv is None else int(mv.shape[0]))
 
 
 def _out(out, shape, like: torch.Tensor):
@@ -137,6 +148,16 @@ def xfxq2_all_flavours(grid: Grid, x: torch.Tensor, q2: torch.Tensor, out=None) 
     fn = lib.xfxq2_all_flavours_f32 if f32 else lib.xfxq2_all_flavours
     check(fn(grid.handle, _dev_ptr(x, dt, "x"), _dev_ptr(q2, dt, "q2"), x.shape[0],
              _dev_ptr(out, dt, "out"), _stream_handle(x.device)), "xfxq2_all_flavours")
+    return out
+
+
+def xfxq2_all_members(grid: Grid, x: torch.Tensor, q2: torch.Tensor, out=None) -> torch.Tensor:
+    """All flavours of every member: [nmem][n][nflav] FP64."""
+    _check_pair(x, q2)
+    out = _out(out, (grid.nmem, x.shape[0], grid.nflav), x)
+    dt = torch.float64
+    check(_native.load().xfxq2_all_members(grid.handle, _dev_ptr(x, dt, "x"), _dev_ptr(q2, dt, "q2"), x.shape[0],
+                                           _dev_ptr(out, dt, "out"), _stream_handle(x.device)), "xfxq2_all_members")
     return out
 
 

@@ -243,3 +243,40 @@ def surrogate_init(nflav: int, seed: int = 9, freq_sigma: float = 2.0):
     params = np.concatenate(parts).astype(np.float32)
     freq = r.normal(0.0, freq_sigma, (SURROGATE_NFREQ, 2)).astype(np.float32)
     return params, freq
+
+
+# --------------------------------------------------------------------------
+# Members (replicas) of the three-subgrid set, and the fitting x grid
+# --------------------------------------------------------------------------
+
+def grid_members(nmem: int, seed: int = 12, base_seed: int = 1, spread: float = 0.05):
+    """-> (Grid with member 0's values, values [nmem][rows][nx][nflav]).
+
+    Member m perturbs the base flavour parameters with seeded normals:
+    A *= 1 + spread N, a += 0.2 spread N, b, c, d += spread N (drawn member by
+    member, parameter-major within a member)."""
+    g = grid_full(base_seed)
+    base = g.params["flavour_params"]
+    nf = base.shape[0]
+    r = _rng(seed)
+    vals = np.empty((nmem,) + g.values.shape)
+    for m in range(nmem):
+        p = base.copy()
+        p[:, 0] *= 1.0 + spread * r.standard_normal(nf)
+        p[:, 1] += 0.2 * spread * r.standard_normal(nf)
+        p[:, 2] += spread * r.standard_normal(nf)
+        p[:, 3] += spread * r.standard_normal(nf)
+        p[:, 4] += spread * r.standard_normal(nf)
+        vals[m] = closed_form_values(g.x_knots, g.q2_knots, p)
+    g0 = make_grid(g.x_knots, [g.q2_knots[a:a + n] for a, n in zip(np.cumsum([0] + g.nq)[:-1], g.nq)], g.pids,
+                   values_fn=lambda x, q: vals[0])
+    return g0, vals
+
+
+FIT_Q = 1.65  # GeV, the parametrisation scale of an NNPDF3.1-style fit
+
+
+def fit_points(n: int = 2415, q: float = FIT_Q):
+    """x grid of a fit's convolution tables: n points log-spaced in [1e-9, 1), at Q^2 = q^2."""
+    x = np.geomspace(1e-9, 1.0, n + 1)[:-1]
+    return x, np.full(n, q * q)
