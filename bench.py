@@ -89,7 +89,7 @@ def algorithmic_flops(counts, nflav):
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for name in ("xfxq2.cu", "pdf_internal.cuh", "grid.cu"):
+    for name in ("xf64.cu", "tang.cuh", "sites.cuh", "pdf_internal.cuh", "grid.cu"):
         h.update((ROOT / "paper_2009_06635_gb300" / "csrc" / name).read_bytes())
     return h.hexdigest()[:16]
 
@@ -414,21 +414,24 @@ def our_arm(args):
     # per-launch duration of the dominant kernel, on the launching stream
     ev = []
 
-    def step64(record=False):
+    def step64(record=False):  # one launch: all flavours and alpha_s
         if record:
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
-            P.xfxq2_all_flavours(G, xd, qd, out=out)
+            P.xfxq2_all_flavours_alphas(G, xd, qd, out=out, alphas_out=aout)
             b.record()
             ev.append((a, b))
         else:
-            P.xfxq2_all_flavours(G, xd, qd, out=out)
-        P.alphas_q2(G, qd, out=aout)
+            P.xfxq2_all_flavours_alphas(G, xd, qd, out=out, alphas_out=aout)
 
     if args.only:
-        xs = (xd, qd, out, aout) if args.only == "fp64" else (xd.float(), qd.float(), out.float(), aout.float())
-        ms = run_timed(lambda: (P.xfxq2_all_flavours(G, xs[0], xs[1], out=xs[2]), P.alphas_q2(G, xs[1], out=xs[3])),
-                       args.steps, args.warmup, world, sync)
+        if args.only == "fp64":
+            fn = lambda: P.xfxq2_all_flavours_alphas(G, xd, qd, out=out, alphas_out=aout)  # noqa: E731
+        else:
+            xs = (xd.float(), qd.float(), out.float(), aout.float())
+            fn = lambda: (P.xfxq2_all_flavours(G, xs[0], xs[1], out=xs[2]),  # noqa: E731
+                          P.alphas_q2(G, xs[1], out=xs[3]))
+        ms = run_timed(fn, args.steps, args.warmup, world, sync)
         if rank == 0:
             print(json.dumps({"only": args.only, "points": n, "ms_per_step": ms, "evals_per_s": evals_step / (ms * 1e-3)}))
         return 0
@@ -516,7 +519,7 @@ def our_arm(args):
 
     flops = algorithmic_flops(counts, nf)
     achieved = flops / (kern_ms * 1e-3)
-    traffic = profiled_traffic("k_xf<double,points>", n)
+    traffic = profiled_traffic("k_xf64<points>", n)
     bytes32 = n * (8 + 4 * nf)
     line = {
         "metric": METRIC,
@@ -534,7 +537,7 @@ def our_arm(args):
         "config": {"workload": WORKLOAD, "points_per_rank": n, "evals_per_step_per_rank": evals_step,
                    "class_counts": counts, "l2": "inputs + outputs 1.3 GB per step > 129 MB L2, no flush",
                    "parallelism": f"{world} independent replicas (weak scaling, no collective)"},
-        "roofline": {"bound": "alu", "kernel": "xfxq2_all_flavours FP64 (k_xf<double,points>)",
+        "roofline": {"bound": "alu", "kernel": "xfxq2_all_flavours_alphas FP64 (k_xf64<points>, all flavours + alpha_s)",
                      "achieved": achieved / 1e12, "peak": FP64_PEAK / 1e12, "unit": "TFLOP/s",
                      "frac": achieved / FP64_PEAK, "traffic": traffic,
                      "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",

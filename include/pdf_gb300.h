@@ -142,6 +142,14 @@ PDF_API int xfxq2_all_flavours(const pdf_grid *grid, const double *x, const doub
 PDF_API int xfxq2_all_members(const pdf_grid *grid, const double *x, const double *q2, size_t n,
                               double *out, cudaStream_t stream);
 
+/* All flavours and alpha_s at the same n points in one pass: out is
+ * [n][nflav], alphas_out is [n], FP64 device arrays; ln Q^2 is taken once
+ * for both.  Values are those of xfxq2_all_flavours and alphas_q2, bit for
+ * bit.  PDFFlow Sec. 2.1 (xfxQ2_allpid), Sec. 2.3 (alphas_Q2).  Errors:
+ * PDF_ERR_NULL (alphas_out NULL with n > 0), PDF_ERR_NO_ALPHAS. */
+PDF_API int xfxq2_all_flavours_alphas(const pdf_grid *grid, const double *x, const double *q2, size_t n,
+                                      double *out, double *alphas_out, cudaStream_t stream);
+
 /* alpha_s(Q^2) at n points, FP64 [n].  PDFFlow Sec. 2.3 (alphas_Q2). */
 PDF_API int alphas_q2(const pdf_grid *grid, const double *q2, size_t n, double *out,
               cudaStream_t stream);

@@ -54,6 +54,7 @@ SIGNATURES = {
     "pdf_grid_pid_column": (I32, [P, I32]),
     "xfxq2": (I32, [P, I32, P, P, SZ, P, P]),
     "xfxq2_all_flavours": (I32, [P, P, P, SZ, P, P]),
+    "xfxq2_all_flavours_alphas": (I32, [P, P, P, SZ, P, P, P]),
     "alphas_q2": (I32, [P, P, SZ, P, P]),
     "xfxq2_f32": (I32, [P, I32, P, P, SZ, P, P]),
     "xfxq2_all_flavours_f32": (I32, [P, P, P, SZ, P, P]),

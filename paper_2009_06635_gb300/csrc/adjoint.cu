@@ -99,7 +99,8 @@ k_vjp(GridView g, const double *__restrict__ xa, const double *__restrict__ qa, 
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
     const double x = xa[p], q2 = qa[p];
-    PointSites<double> ps = sites(g, xkeys, qkeys, x, q2);
+    double lq;
+    PointSites<double> ps = sites(g, xkeys, qkeys, x, q2, g.tlogtab, lq);
     if (ps.cls == C_INVALID) {
       if (gx) gx[p] = NAN;
       if (gq) gq[p] = NAN;

@@ -2,7 +2,8 @@
 //
 // Staging (PDFFlow Sec. 2.2, the LHAPDF data loaded once into device
 // memory) precomputes everything that depends only on the grid:
-//   - ln of every knot (device log, so a query on a knot gets t = 0 exactly);
+//   - ln of every knot (the evaluation kernels' own table-driven logarithm,
+//     so a query on a knot gets t = 0 exactly);
 //   - per cell, the tangent-augmented Hermite weights w_a(t) as cubics: the
 //     knot tangent is the mean of the two adjacent secant slopes, one-sided
 //     at the x edges and at the ends of each Q subgrid (Sec. 2.2's special
@@ -75,6 +76,8 @@ struct Stage {
   double *xcell, *qcell, *xW, *qW, *coef, *acell;
   float *coef32, *xthr32, *q2thr32, *aq2thr32, *xcell32, *qcell32, *acell32;
   float2 *coefff;
+  double2 *tlogtab;  // tang.cuh tables, filled on the host before staging
+  double *texptab;
   int *ffbad;  // set when a control point is outside the float-float range
   int *row_qc, *qc_row;
   double *scal;  // scalar outputs, see k_scalars
@@ -82,9 +85,19 @@ struct Stage {
 
 __global__ void k_logs(Stage S) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < S.nx) { S.lx[i] = log(S.xk[i]); S.xthr32[i] = __double2float_ru(S.xk[i]); }
-  if (i < S.nrows) { S.lq[i] = log(S.q2k[i]); S.q2thr32[i] = __double2float_ru(S.q2k[i]); }
-  if (i < S.na) { S.alq[i] = log(S.aq2[i]); S.aq2thr32[i] = __double2float_ru(S.aq2[i]); }
+  const double2 *LT = S.tlogtab;
+  if (i < S.nx) { S.lx[i] = tlog(S.xk[i], LT); S.xthr32[i] = __double2float_ru(S.xk[i]); }
+  if (i < S.nrows) { S.lq[i] = tlog(S.q2k[i], LT); S.q2thr32[i] = __double2float_ru(S.q2k[i]); }
+  if (i < S.na) { S.alq[i] = tlog(S.aq2[i], LT); S.aq2thr32[i] = __double2float_ru(S.aq2[i]); }
+}
+
+void tang_tables(double *logtab, double *exptab) {
+  for (int j = 0; j < kLogTab; j++) {
+    const double F = 1.0 + j / 256.0;
+    logtab[2 * j] = 1.0 / F;
+    logtab[2 * j + 1] = j == kLogTab - 1 ? kLn2 : (double)logl((long double)F);
+  }
+  for (int k = 0; k < kExpTab; k++) exptab[k] = (double)exp2l((long double)k / 256.0L);
 }
 
 // FP32 cell table: both end knots rounded to float (k0f, k1f), their float
@@ -258,12 +271,12 @@ __global__ void k_scalars(Stage S) {
   int j = 0;  // same rule as the query search: the last row with Q^2_j <= v
   while (j + 1 < S.nrows && S.q2k[j + 1] <= v) j++;
   o[3] = (double)S.row_qc[j];
-  o[4] = (log(v) - S.qcell[4 * j]) * S.qcell[4 * j + 1];
+  o[4] = (tlog(v, S.tlogtab) - S.qcell[4 * j]) * S.qcell[4 * j + 1];
   o[5] = S.xcell[0];
   o[6] = S.xcell[1];
   o[7] = S.lq[S.nrows - 1];
   o[8] = S.qcell[4 * top + 1];
-  o[9] = log(1.01);
+  o[9] = tlog(1.01, S.tlogtab);
 }
 
 static int pow2_floor(int n) {
@@ -393,6 +406,7 @@ static int load_impl(const pdf_grid_desc *d, int nmem, const double *member_valu
     S.coef32 = A.take<float>((size_t)nmem * (nqc + 1) * nx * nf * 16);
     S.coefff = A.take<float2>((size_t)nmem * (nqc + 1) * nx * nf * 16);
     S.ffbad = A.take<int>(1);
+    S.tlogtab = A.take<double2>(kLogTab); S.texptab = A.take<double>(kExpTab);
     S.acell = A.take<double>(6 * (na > 0 ? na : 1));
     S.acell32 = A.take<float>(6 * (na > 0 ? na : 1));
     S.xthr32 = A.take<float>(nx); S.q2thr32 = A.take<float>(nrows); S.aq2thr32 = A.take<float>(na > 0 ? na : 1);
@@ -435,6 +449,12 @@ static int load_impl(const pdf_grid_desc *d, int nmem, const double *member_valu
   if (na > 0) { H2D(S.aq2, d->as_q2, sizeof(double) * na); H2D(S.aval, d->as_vals, sizeof(double) * na); }
   H2D(S.first, first, sizeof(int) * nsub);
   H2D(S.nq, d->nq, sizeof(int) * nsub);
+  {
+    double lt[2 * kLogTab], et[kExpTab];
+    tang_tables(lt, et);
+    H2D(S.tlogtab, lt, sizeof lt);
+    H2D(S.texptab, et, sizeof et);
+  }
   if (e == cudaSuccess) e = cudaMemset(inv, 0, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(S.ffbad, 0, sizeof(int));
   if (e != cudaSuccess) {
@@ -468,6 +488,7 @@ static int load_impl(const pdf_grid_desc *d, int nmem, const double *member_valu
   v.qc_row = S.qc_row; v.vals = const_cast<double *>(S.vals);
   v.coef = S.coef; v.coef32 = S.coef32; v.xW = S.xW; v.qW = S.qW;
   v.coefff = S.coefff; v.ff = ffbad ? 0 : 1;
+  v.tlogtab = S.tlogtab; v.texptab = S.texptab;
   v.nmem = nmem;
   v.mstride = (size_t)(nqc + 1) * nx * nf * 16;
   g->ffbad = S.ffbad;

@@ -9,12 +9,6 @@
 // are reused across calls.
 #include "pdf_internal.cuh"
 
-namespace pdfgb {
-int launch_all_f64(const pdf_grid *g, const double *x, const double *q2, long long n, double *out,
-                   cudaStream_t st);
-int launch_alphas_f64(const pdf_grid *g, const double *q2, long long n, double *out, cudaStream_t st);
-}
-
 using namespace pdfgb;
 
 static const size_t kChunk = (size_t)1 << 20;  // points per chunk
@@ -60,8 +54,7 @@ extern "C" int xfxq2_all_flavours_host(const pdf_grid *cg, const double *x, cons
     double *dout = da + g->io_cap;
     e = cudaMemcpyAsync(dx, x + off, m * sizeof(double), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dq, q2 + off, m * sizeof(double), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) rc = launch_all_f64(g, dx, dq, (long long)m, dout, st);
-    if (e == cudaSuccess && rc == PDF_OK && alphas_out) rc = launch_alphas_f64(g, dq, (long long)m, da, st);
+    if (e == cudaSuccess) rc = launch_all_f64(g, dx, dq, (long long)m, dout, alphas_out ? da : nullptr, st);
     if (e == cudaSuccess && rc == PDF_OK)
       e = cudaMemcpyAsync(out + off * nf, dout, m * nf * sizeof(double), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess && rc == PDF_OK && alphas_out)

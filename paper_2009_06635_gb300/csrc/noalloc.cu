@@ -20,12 +20,6 @@
 
 #include "pdf_internal.cuh"
 
-namespace pdfgb {
-int launch_all_f64(const pdf_grid *g, const double *x, const double *q2, long long n, double *out,
-                   cudaStream_t st);
-int launch_alphas_f64(const pdf_grid *g, const double *q2, long long n, double *out, cudaStream_t st);
-}  // namespace pdfgb
-
 using namespace pdfgb;
 
 namespace {
@@ -85,7 +79,7 @@ extern "C" int xfxq2_all_flavours_host_noalloc(const pdf_grid *g, const double *
   if (e == cudaSuccess) e = cudaMemcpyAsync(sq, q2, n * sizeof(double), cudaMemcpyHostToDevice, stream);
   if (e != cudaSuccess)
     return set_error(PDF_ERR_CUDA, "xfxq2_all_flavours_host_noalloc: copy in: %s", cudaGetErrorString(e));
-  rc = launch_all_f64(g, sx, sq, (long long)n, so, stream);
+  rc = launch_all_f64(g, sx, sq, (long long)n, so, nullptr, stream);
   if (rc == PDF_OK && alphas_out) rc = launch_alphas_f64(g, sq, (long long)n, sa, stream);
   if (rc) return rc;
   e = cudaMemcpyAsync(out, so, n * nf * sizeof(double), cudaMemcpyDeviceToHost, stream);

@@ -29,6 +29,7 @@
 #include <cuda_runtime.h>
 
 #include "pdf_gb300.h"
+#include "tang.cuh"
 
 namespace pdfgb {
 
@@ -72,6 +73,8 @@ struct GridView {
   const double *xW, *qW;      // [nx][16], [nqc + 1][16]
   const float *xthr32, *q2thr32;   // smallest float >= knot
   const float *xcell32, *qcell32;  // [n][8], see cell32 in grid.cu
+  const double2 *tlogtab;     // [kLogTab] {1/F_j, ln F_j} (tang.cuh)
+  const double *texptab;      // [kExpTab] 2^(k/256)
 
   // alpha_s
   const double *aq2;          // [na]
@@ -135,8 +138,10 @@ __device__ __forceinline__ void bernstein(T t, T s, T *B) {  // s = 1 - t
 // ---------------------------------------------------------------------------
 // From g0 at one knot (p = 0) and g1 at the next one inwards (p = 1):
 // log-linear if both are positive, linear otherwise.
-__device__ __forceinline__ double pair_rule(double g0, double g1, double p) {
-  if (g0 > 0.0 && g1 > 0.0) return g0 * exp(p * log(g1 / g0));
+__device__ __forceinline__ double pair_rule(double g0, double g1, double p, const double2 *LT,
+                                            const double *ET) {
+  if (__double_as_longlong(g0) > 0 && __double_as_longlong(g1) > 0)  // both > 0 (NaN: log-linear, NaN)
+    return g0 * texp(p * tlog(g1 / g0, LT), ET);
   return g0 + (g1 - g0) * p;
 }
 __device__ __forceinline__ float pair_rule(float g0, float g1, float p) {
@@ -146,10 +151,10 @@ __device__ __forceinline__ float pair_rule(float g0, float g1, float p) {
 
 // Low Q^2: f0 = F(Q2min), f1 = F(1.01 Q2min); rho = Q^2/Q2min, lr = ln rho.
 __device__ __forceinline__ double lowq_rule(double f0, double f1, double rho, double lr,
-                                            double ln101) {
-  double gam = (f0 > 0.0 && f1 > 0.0) ? log(f1 / f0) / ln101 : 1.0;
+                                            double ln101, const double2 *LT, const double *ET) {
+  double gam = (__double_as_longlong(f0) > 0 && __double_as_longlong(f1) > 0) ? tlog(f1 / f0, LT) / ln101 : 1.0;
   double ex = (gam * rho + 1.0) - rho;
-  return f0 * exp(ex * lr);
+  return f0 * texp(ex * lr, ET);
 }
 __device__ __forceinline__ float lowq_rule(float f0, float f1, float rho, float lr, float ln101) {
   float gam = (f0 > 0.f && f1 > 0.f) ? logf(f1 / f0) / ln101 : 1.f;
@@ -179,6 +184,9 @@ __device__ __forceinline__ T combine(int cls, T px, T pq, T lr, T ln101, FN F) {
 int set_error(int code, const char *fmt, ...);
 int check_launch(const char *what);
 
+// Evaluation layouts (see the kernels in xf64.cu and xfxq2.cu).
+enum { MODE_POINTS = 0, MODE_MC = 1, MODE_MEMBERS = 2 };
+
 }  // namespace pdfgb
 
 // The opaque handle.
@@ -196,3 +204,15 @@ struct pdf_grid {
   void *io_buf[2];
   size_t io_cap;  // points per buffer
 };
+
+namespace pdfgb {
+// FP64 evaluation (xf64.cu), mode = MODE_*: points xa, qa (columns
+// col0..col0+ncol-1; alpha_s into as_out when not null), events xa, xb with
+// Q^2 = xa xb s, or every member of the set.  Arguments already validated.
+int launch_xf64(const pdf_grid *grid, int mode, const double *xa, const double *qa, const double *xb, double s,
+                long long n, int col0, int ncol, double *out, double *as_out, cudaStream_t st);
+// xfxq2.cu: all flavours (+ alpha_s when as_out is not null); alpha_s alone.
+int launch_all_f64(const pdf_grid *g, const double *x, const double *q2, long long n, double *out,
+                   double *as_out, cudaStream_t st);
+int launch_alphas_f64(const pdf_grid *g, const double *q2, long long n, double *out, cudaStream_t st);
+}  // namespace pdfgb

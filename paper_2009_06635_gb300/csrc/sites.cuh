@@ -34,48 +34,58 @@ struct PointSites {
 };
 
 // ---- FP64 classification and sites ---------------------------------------
+// Range tests compare raw bit patterns: for positive doubles the integer
+// order is the numeric order, and zero, negative values, infinities and NaN
+// fail them exactly as the FP64 tests would, so the FP64 pipe is left to the
+// logarithms and positions.  lq receives ln Q^2 whenever Q^2 is positive and
+// finite (alpha_s needs it even where x is invalid).  LT: tlog's table.
 __device__ __forceinline__ PointSites<double> sites(const GridView &g, const long long *xkeys,
-                                                    const long long *qkeys, double x, double q2) {
+                                                    const long long *qkeys, double x, double q2,
+                                                    const double2 *LT, double &lq) {
   PointSites<double> r;
   r.xc0 = r.xc1 = r.qc0 = r.qc1 = 0;
   r.t0 = r.t1 = r.u0 = r.u1 = r.px = r.pq = r.lr = 0.0;
   r.ts0 = r.us0 = 1.0;
-  bool valid = (x > 0.0) && (x <= g.xlast) && (q2 > 0.0) && (q2 < INFINITY);
-  if (!valid) { r.cls = C_INVALID; return r; }
-  bool lowx = x < g.x0, lowq = q2 < g.q2min, highq = q2 > g.q2max;
-  double lx = log(x);
+  const long long kx = __double_as_longlong(x), kq = __double_as_longlong(q2);
+  const bool qv = kq > 0 && kq < 0x7FF0000000000000LL;
+  lq = qv ? tlog(q2, LT) : 0.0;
+  if (!(qv && kx > 0 && kx <= __double_as_longlong(g.xlast))) { r.cls = C_INVALID; return r; }
+  const bool lowx = kx < __double_as_longlong(g.x0);
+  const bool lowq = kq < __double_as_longlong(g.q2min), highq = kq > __double_as_longlong(g.q2max);
+  const double lx = tlog(x, LT);
   if (!lowx) {
-    int i = search_cell(xkeys, g.nx, g.xstep, __double_as_longlong(x));
+    int i = search_cell(xkeys, g.nx, g.xstep, kx);
     r.xc0 = i;
     const double2 c0 = *reinterpret_cast<const double2 *>(g.xcell + 4 * i);
     const double2 c1 = *reinterpret_cast<const double2 *>(g.xcell + 4 * i + 2);
     r.t0 = (lx - c0.x) * c0.y;
     r.ts0 = fma(c1.x - lx, c0.y, c1.y);
-    if (r.t0 <= r.ts0) r.ts0 = 1.0 - r.t0;  // the larger one from the smaller:
-    else r.t0 = 1.0 - r.ts0;                // exact at both knots
+    // the larger one from the smaller (exact at both knots); t + ts ~ 1, so
+    // at most one is negative and the integer order decides as FP64 would
+    if (__double_as_longlong(r.t0) <= __double_as_longlong(r.ts0)) r.ts0 = 1.0 - r.t0;
+    else r.t0 = 1.0 - r.ts0;
   } else {
     r.xc1 = 1;
     r.px = (lx - g.lx0) * g.idx0;
   }
   if (!lowq && !highq) {
-    int j = search_cell(qkeys, g.nrows, g.qstep, __double_as_longlong(q2));
+    int j = search_cell(qkeys, g.nrows, g.qstep, kq);
     r.qc0 = g.row_qc[j];
     const double2 c0 = *reinterpret_cast<const double2 *>(g.qcell + 4 * j);
     const double2 c1 = *reinterpret_cast<const double2 *>(g.qcell + 4 * j + 2);
-    const double lq = log(q2);
     r.u0 = (lq - c0.x) * c0.y;
     r.us0 = fma(c1.x - lq, c0.y, c1.y);
-    if (r.u0 <= r.us0) r.us0 = 1.0 - r.u0;
+    if (__double_as_longlong(r.u0) <= __double_as_longlong(r.us0)) r.us0 = 1.0 - r.u0;
     else r.u0 = 1.0 - r.us0;
   } else if (highq) {
     r.qc0 = g.nqc;
     r.qc1 = g.top_qc;
-    r.pq = -(log(q2) - g.lq2max) * g.idq_top;
+    r.pq = -(lq - g.lq2max) * g.idq_top;
   } else {
     r.qc1 = g.q101_qc;
     r.u1 = g.q101_u;
     r.pq = q2 / g.q2min;
-    r.lr = log(r.pq);
+    r.lr = tlog(r.pq, LT);
   }
   r.cls = lowx ? (highq ? C_LOWX_HIGHQ : lowq ? C_LOWX_LOWQ : C_LOWX)
                : (highq ? C_HIGHQ : lowq ? C_LOWQ : C_IN);
@@ -140,13 +150,15 @@ __device__ __forceinline__ PointSites<float> sites(const GridView &g, const int 
 }
 
 // ---- alpha_s (Sec. 2.3): constant outside, log-cubic inside ----------------
-__device__ __forceinline__ double alphas_eval(const GridView &g, const long long *akeys, double q2) {
-  if (!((q2 > 0.0) && (q2 < INFINITY))) return NAN;
-  if (q2 < g.aq2lo) return g.as_lo;
-  if (q2 > g.aq2hi) return g.as_hi;
-  int j = search_cell(akeys, g.na, g.astep, __double_as_longlong(q2));
+// lq = ln Q^2 from tlog, used only inside the node range.
+__device__ __forceinline__ double alphas_eval(const GridView &g, const long long *akeys, double q2, double lq) {
+  const long long kq = __double_as_longlong(q2);
+  if (!(kq > 0 && kq < 0x7FF0000000000000LL)) return NAN;
+  if (kq < __double_as_longlong(g.aq2lo)) return g.as_lo;
+  if (kq > __double_as_longlong(g.aq2hi)) return g.as_hi;
+  int j = search_cell(akeys, g.na, g.astep, kq);
   const double *c = g.acell + 6 * j;
-  double u = (log(q2) - c[0]) * c[1];
+  double u = (lq - c[0]) * c[1];
   return fma(fma(fma(c[5], u, c[4]), u, c[3]), u, c[2]);
 }
 __device__ __forceinline__ float alphas_eval(const GridView &g, const int *akeys, float q2) {

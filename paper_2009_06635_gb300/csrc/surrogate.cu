@@ -27,11 +27,6 @@
 #include "pdf_internal.cuh"
 #include "pdf_surrogate.h"
 
-namespace pdfgb {
-int launch_all_f64(const pdf_grid *g, const double *x, const double *q2, long long n, double *out,
-                   cudaStream_t st);
-}
-
 namespace {
 
 using namespace pdfgb;
@@ -571,7 +566,7 @@ int features_targets(pdf_surrogate *s, const pdf_grid *grid, const double *x, co
   k_features<<<(B * SIN + 255) / 256, 256, 0, st>>>(s->c, x, q2, B, s->h[0]);
   const double *xf = xf_given;
   if (!xf) {
-    int rc = launch_all_f64(grid, x, q2, B, s->xfbuf, st);
+    int rc = launch_all_f64(grid, x, q2, B, s->xfbuf, nullptr, st);
     if (rc) return rc;
     xf = s->xfbuf;
   }
@@ -765,7 +760,7 @@ extern "C" int pdf_surrogate_build_error_map(pdf_surrogate *s, const pdf_grid *g
   int rc = cuda_err(cudaMalloc(&sv, n * s->nf * sizeof(float)), "error map");
   if (!rc) rc = cuda_err(cudaMalloc(&iv, n * s->nf * sizeof(double)), "error map");
   if (!rc) rc = launch_infer(s, x, q2, n, sv, nullptr, nullptr, nullptr, nullptr, 0);
-  if (!rc) rc = launch_all_f64(grid, x, q2, (long long)n, iv, 0);
+  if (!rc) rc = launch_all_f64(grid, x, q2, (long long)n, iv, nullptr, 0);
   if (!rc) {
     cudaMemset(s->tile_bits, 0, MAPN * MAPN * sizeof(unsigned int));
     cudaMemset(s->tile_cnt, 0, MAPN * MAPN * sizeof(unsigned int));
@@ -837,7 +832,7 @@ extern "C" int pdf_surrogate_eval_fallback(pdf_surrogate *s, const pdf_grid *gri
   if (rc) return rc;
   if (m > 0) {
     k_gather<<<(m + 255) / 256, 256, 0, st>>>(x, q2, s->fb_idx, m, s->fb_x, s->fb_q);
-    rc = launch_all_f64(grid, s->fb_x, s->fb_q, (long long)m, s->fb_out, st);
+    rc = launch_all_f64(grid, s->fb_x, s->fb_q, (long long)m, s->fb_out, nullptr, st);
     if (rc) return rc;
     k_scatter<<<(unsigned)(((long long)m * s->nf + 255) / 256), 256, 0, st>>>(s->fb_out, s->fb_idx, m, s->nf, out);
   }

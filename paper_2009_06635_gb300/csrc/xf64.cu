@@ -1,0 +1,480 @@
+// xf64.cu -- FP64 evaluation of x f(x, Q^2): points (all flavours or a
+// column range), Monte Carlo events, member sets; alpha_s(Q^2) optionally
+// in the same pass.
+//
+// One warp owns a tile of 32 points (16 events).  Phase 1 (lane = point):
+// load (coalesced), classify and search on bit patterns, ln x and ln Q^2 by
+// the table-driven logarithm (tang.cuh), alpha_s.  Points inside the grid
+// (and invalid ones) take a slot of the warp's record.  Points that need a
+// continuation rule (x < x0 or Q^2 outside the grid) are pushed onto the
+// warp's queue in shared memory instead and evaluated 32 at a time once the
+// queue holds a full tile (the rest at the end): their logarithms and
+// exponentials then run in full warps, not in the few lanes a mixed tile
+// would leave them.  Member sets skip the queue (a point's hundreds of
+// member items fill the warp anyway).
+// Phase 2 (lane = item (point, column); consecutive items are consecutive
+// outputs, so stores coalesce): in-grid points contract the cell's 16
+// float-float control points with float-float Bernstein weights on the FP32
+// pipe (GB300 issues FP32 at 64x its FP64 rate; the result is good to about
+// 2^-46 of the data scale); exact knot hits and continuation sites use FP64.
+// The continuation classes share one copy of the pair rule, so lanes of
+// different classes reconverge before its logarithm and exponential.
+#include <cmath>
+
+#include "sites.cuh"
+
+namespace pdfgb {
+
+namespace {
+
+constexpr int kWarps = 8;
+constexpr int kThreads = 32 * kWarps;
+constexpr unsigned kFull = 0xffffffffu;
+
+// Per-warp record of the points of one tile, by class-sorted slot.  W holds
+// for C_INF the 16 float-float weight products (hi, lo) at [l*4 + k], for
+// C_IN the 16 FP64 products, otherwise Bx0 | Bx1 | Bq0 | Bq1.
+struct alignas(16) Rec64 {
+  int cls[32], xc0[32], xc1[32], qc0[32], qc1[32];
+  long long ob[32];  // output offset of the point's first column
+  double W[16][33];  // padded: the rows of one slot fall in different banks
+  double px[32], pq[32], lr[32];
+};
+// Continuation points waiting for a full tile (at most 31 + 32).
+struct alignas(16) Queue64 {
+  double x[64], q2[64];
+  long long ob[64];
+};
+
+// ---- float-float arithmetic (a value is hi + lo, two floats, ~48 bits) -----
+// Error-free product (FMA) and sum (TwoSum); the _rn intrinsics keep the
+// compiler from contracting or reordering the error terms.
+struct ff2 {
+  float h, l;
+};
+__device__ __forceinline__ ff2 ff_of(double a) {
+  float h = __double2float_rn(a);
+  return {h, __double2float_rn(a - (double)h)};
+}
+__device__ __forceinline__ ff2 ff_mul(ff2 a, ff2 b) {
+  float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, e));
+  float h = __fadd_rn(p, e);
+  return {h, __fsub_rn(e, __fsub_rn(h, p))};
+}
+__device__ __forceinline__ void ff_bernstein(double t, double s, ff2 *B) {
+  const ff2 tf = ff_of(t), sf = ff_of(s), three = {3.f, 0.f};
+  const ff2 t2 = ff_mul(tf, tf), s2 = ff_mul(sf, sf);
+  B[0] = ff_mul(s2, sf);
+  B[1] = ff_mul(three, ff_mul(tf, s2));
+  B[2] = ff_mul(three, ff_mul(t2, sf));
+  B[3] = ff_mul(t2, tf);
+}
+// Exact float -> double on the integer pipe for normal floats and zeros (the
+// FP64 pipe's conversion costs as much as an FMA on GB300); subnormals,
+// infinities and NaN take the hardware conversion.
+__device__ __forceinline__ double f2d(float f) {
+  const unsigned b = __float_as_uint(f), a = b & 0x7FFFFFFFu;
+  if (a - 0x00800000u < 0x7F000000u)  // biased exponent in [1, 254]
+    return __hiloint2double((int)(((a >> 3) + 0x38000000u) | (b & 0x80000000u)), (int)(b << 29));
+  if (a == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
+  return (double)f;
+}
+// sum_m w_m b_m with w (hi, lo) from the record and b (hi, lo) from the
+// float-float control points: exact products, TwoSum accumulation, the
+// cross terms and the rounding errors gathered in a second float.
+__device__ __forceinline__ double dot_ff16(const float2 *c, const double (*W)[33], int p) {
+  const float4 *q = reinterpret_cast<const float4 *>(c);
+  float sh = 0.f, sl = 0.f;
+#pragma unroll
+  for (int m2 = 0; m2 < 8; m2++) {
+    const float4 v = __ldg(q + m2);
+#pragma unroll
+    for (int half = 0; half < 2; half++) {
+      const float bh = half ? v.z : v.x, bl = half ? v.w : v.y;
+      const float2 w = *reinterpret_cast<const float2 *>(&W[2 * m2 + half][p]);
+      const float ph = __fmul_rn(w.x, bh);
+      float pe = __fmaf_rn(w.x, bh, -ph);
+      pe = __fmaf_rn(w.x, bl, __fmaf_rn(w.y, bh, pe));
+      const float t = __fadd_rn(sh, ph);
+      const float bp = __fsub_rn(t, sh);
+      const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bp)), __fsub_rn(ph, bp));
+      sh = t;
+      sl = __fadd_rn(sl, __fadd_rn(err, pe));
+    }
+  }
+  return f2d(sh) + f2d(sl);
+}
+
+// ---- FP64 site evaluation ---------------------------------------------------
+__device__ __forceinline__ double dot_w16(const double *c, const Rec64 &R, int p) {
+  const double2 *q = reinterpret_cast<const double2 *>(c);
+  double2 v = __ldg(q);
+  double acc = R.W[0][p] * v.x;
+  acc = fma(R.W[1][p], v.y, acc);
+#pragma unroll
+  for (int m = 1; m < 8; m++) {
+    v = __ldg(q + m);
+    acc = fma(R.W[2 * m][p], v.x, acc);
+    acc = fma(R.W[2 * m + 1][p], v.y, acc);
+  }
+  return acc;
+}
+// site with t general, u general: sum_l Bq[l] sum_k Bx[k] b[l][k]
+__device__ __forceinline__ double site_tu(const double *c, const Rec64 &R, int p, int a, int b) {
+  double f = 0.0;
+#pragma unroll
+  for (int l = 0; l < 4; l++) {
+    const double2 *q = reinterpret_cast<const double2 *>(c + 4 * l);
+    double2 v0 = __ldg(q), v1 = __ldg(q + 1);
+    double r = R.W[4 * a][p] * v0.x;
+    r = fma(R.W[4 * a + 1][p], v0.y, r);
+    r = fma(R.W[4 * a + 2][p], v1.x, r);
+    r = fma(R.W[4 * a + 3][p], v1.y, r);
+    f = l == 0 ? R.W[8 + 4 * b][p] * r : fma(R.W[8 + 4 * b + l][p], r, f);
+  }
+  return f;
+}
+// site on an x knot (t = 0): sum_l Bq[l] b[l][0]
+__device__ __forceinline__ double site_u(const double *c, const Rec64 &R, int p, int b) {
+  double f = R.W[8 + 4 * b][p] * __ldg(c);
+  f = fma(R.W[8 + 4 * b + 1][p], __ldg(c + 4), f);
+  f = fma(R.W[8 + 4 * b + 2][p], __ldg(c + 8), f);
+  return fma(R.W[8 + 4 * b + 3][p], __ldg(c + 12), f);
+}
+// site on a Q knot (u = 0): sum_k Bx[k] b[0][k]
+__device__ __forceinline__ double site_t(const double *c, const Rec64 &R, int p, int a) {
+  const double2 *q = reinterpret_cast<const double2 *>(c);
+  double2 v0 = __ldg(q), v1 = __ldg(q + 1);
+  double f = R.W[4 * a][p] * v0.x;
+  f = fma(R.W[4 * a + 1][p], v0.y, f);
+  f = fma(R.W[4 * a + 2][p], v1.x, f);
+  return fma(R.W[4 * a + 3][p], v1.y, f);
+}
+
+// One item: column col of the point in slot p.  moff: the member's offset
+// into the control points.
+__device__ __forceinline__ double eval_item64(const GridView &g, const Rec64 &R, int p, int col, size_t moff,
+                                              const double2 *LT, const double *ET) {
+  const double *cb = g.coef + moff + (size_t)col * 16;
+  const size_t stride = (size_t)g.nf * 16;
+  auto C = [&](int a, int b) {
+    int xc = a ? R.xc1[p] : R.xc0[p];
+    int qc = b ? R.qc1[p] : R.qc0[p];
+    return cb + ((size_t)qc * g.nx + xc) * stride;
+  };
+  const int cls = R.cls[p];
+  if (cls == C_INF)
+    return dot_ff16(g.coefff + moff + (((size_t)R.qc0[p] * g.nx + R.xc0[p]) * g.nf + col) * 16, R.W, p);
+  if (cls == C_IN) return dot_w16(C(0, 0), R, p);
+  if (cls == C_INVALID) return NAN;
+  // continuation: the two values the final rule combines, then one shared rule
+  double a, b, prm = R.px[p];
+  bool lowq = false;
+  switch (cls) {
+    case C_LOWX:  // sites (x0, Q^2), (x1, Q^2): t = 0
+      a = site_u(C(0, 0), R, p, 0);
+      b = site_u(C(1, 0), R, p, 0);
+      break;
+    case C_HIGHQ:  // sites (x, Q2max), (x, knot below): u = 0
+      a = site_t(C(0, 0), R, p, 0);
+      b = site_t(C(0, 1), R, p, 0);
+      prm = R.pq[p];
+      break;
+    case C_LOWQ:  // sites (x, Q2min): u = 0; (x, 1.01 Q2min): general
+      a = site_t(C(0, 0), R, p, 0);
+      b = site_tu(C(0, 1), R, p, 0, 1);
+      lowq = true;
+      break;
+    case C_LOWX_HIGHQ:  // all four sites are knots
+      a = pair_rule(__ldg(C(0, 0)), __ldg(C(0, 1)), R.pq[p], LT, ET);
+      b = pair_rule(__ldg(C(1, 0)), __ldg(C(1, 1)), R.pq[p], LT, ET);
+      break;
+    default:  // C_LOWX_LOWQ
+      a = lowq_rule(__ldg(C(0, 0)), site_u(C(0, 1), R, p, 1), R.pq[p], R.lr[p], g.ln101, LT, ET);
+      b = lowq_rule(__ldg(C(1, 0)), site_u(C(1, 1), R, p, 1), R.pq[p], R.lr[p], g.ln101, LT, ET);
+      break;
+  }
+  if (lowq) return lowq_rule(a, b, R.pq[p], R.lr[p], g.ln101, LT, ET);
+  return pair_rule(a, b, prm, LT, ET);
+}
+
+// Bernstein weights of a point's sites into its record slot.
+__device__ __forceinline__ void store_point(Rec64 &R, int slot, const PointSites<double> &ps, long long ob) {
+  R.cls[slot] = ps.cls;
+  R.xc0[slot] = ps.xc0; R.xc1[slot] = ps.xc1; R.qc0[slot] = ps.qc0; R.qc1[slot] = ps.qc1;
+  R.ob[slot] = ob;
+  R.px[slot] = ps.px; R.pq[slot] = ps.pq; R.lr[slot] = ps.lr;
+  if (ps.cls == C_INVALID) return;
+  if (ps.cls == C_INF) {
+    ff2 bx[4], bq[4];
+    ff_bernstein(ps.t0, ps.ts0, bx);
+    ff_bernstein(ps.u0, ps.us0, bq);
+#pragma unroll
+    for (int l = 0; l < 4; l++)
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        const ff2 w = ff_mul(bx[k], bq[l]);
+        *reinterpret_cast<float2 *>(&R.W[l * 4 + k][slot]) = make_float2(w.h, w.l);
+      }
+    return;
+  }
+  double bx0[4], bq0[4];
+  bernstein<double>(ps.t0, ps.ts0, bx0);
+  bernstein<double>(ps.u0, ps.us0, bq0);
+  if (ps.cls == C_IN) {
+#pragma unroll
+    for (int l = 0; l < 4; l++)
+#pragma unroll
+      for (int k = 0; k < 4; k++) R.W[l * 4 + k][slot] = bx0[k] * bq0[l];
+    return;
+  }
+  double bx1[4], bq1[4];
+  bernstein<double>(ps.t1, 1.0 - ps.t1, bx1);
+  bernstein<double>(ps.u1, 1.0 - ps.u1, bq1);
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    R.W[k][slot] = bx0[k];
+    R.W[4 + k][slot] = bx1[k];
+    R.W[8 + k][slot] = bq0[k];
+    R.W[12 + k][slot] = bq1[k];
+  }
+}
+
+// Phase 2 over the first np slots: items (slot, column) in order, lane-strided.
+__device__ __forceinline__ void items64(const GridView &g, const Rec64 &R, int np, int nc, int cbase,
+                                        size_t moff, long long mo, double *__restrict__ out, const double2 *LT,
+                                        const double *ET, int lane) {
+  const int nitems = np * nc;
+  int p = lane / nc, c = lane - (lane / nc) * nc;
+  const int dp = 32 / nc, dc = 32 - dp * nc;
+  for (int k = lane; k < nitems; k += 32) {
+    out[mo + R.ob[p] + c] = eval_item64(g, R, p, cbase + c, moff, LT, ET);
+    c += dc;
+    p += dp;
+    if (c >= nc) { c -= nc; p++; }
+  }
+}
+
+__device__ __forceinline__ bool is_far(int cls) { return cls >= C_LOWX && cls <= C_LOWX_LOWQ; }
+
+// Counting sort of the lanes whose key is one of the classes Cs (in that
+// order), by ballots; returns the number of slots used.
+template <int... Cs>
+__device__ __forceinline__ int sort_slots(int key, int lane, int &slot) {
+  const unsigned lt = (1u << lane) - 1u;
+  int base = 0;
+  auto one = [&](int c) {
+    const unsigned m = __ballot_sync(kFull, key == c);
+    if (key == c) slot = base + __popc(m & lt);
+    base += __popc(m);
+  };
+  (one(Cs), ...);
+  return base;
+}
+
+}  // namespace
+
+// MODE_POINTS:  points xa[n], qa[n]; out[n][ncol] for columns col0..col0+ncol-1;
+//               as_out[n] (alpha_s) when not null.
+// MODE_MC:      events xa[n] (x1), xb[n] (x2), Q^2 = x1 x2 s; out[n][2 nf + 1]
+//               (the flavours at x1, at x2, alpha_s).
+// MODE_MEMBERS: points xa[n], qa[n]; out[nmem][n][nf].  A warp's unit is
+//               (tile, chunk of mchunk members); phase 1 repeats per chunk.
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 3)
+k_xf64(GridView g, const double *__restrict__ xa, const double *__restrict__ qa, const double *__restrict__ xb,
+       double s, long long n, int col0, int ncol, int mchunk, double *__restrict__ out,
+       double *__restrict__ as_out) {
+  constexpr bool kQueue = MODE != MODE_MEMBERS;
+  extern __shared__ __align__(16) unsigned char smem[];
+  size_t off = 0;
+  long long *xkeys = reinterpret_cast<long long *>(smem + off);
+  off += keys_bytes(g.nx, 8);
+  long long *qkeys = reinterpret_cast<long long *>(smem + off);
+  off += keys_bytes(g.nrows, 8);
+  long long *akeys = reinterpret_cast<long long *>(smem + off);
+  off += keys_bytes(g.na, 8);
+  double2 *LT = reinterpret_cast<double2 *>(smem + off);
+  off += sizeof(double2) * kLogTab;
+  double *ET = reinterpret_cast<double *>(smem + off);
+  off += sizeof(double) * kExpTab;
+  Rec64 *recs = reinterpret_cast<Rec64 *>(smem + off);
+  off += kWarps * sizeof(Rec64);
+  Queue64 *queues = reinterpret_cast<Queue64 *>(smem + off);
+
+  const bool want_as = MODE == MODE_MC || (MODE == MODE_POINTS && as_out != nullptr);
+  load_keys<double>(g, xkeys, 0);
+  load_keys<double>(g, qkeys, 1);
+  if (want_as) load_keys<double>(g, akeys, 2);
+  for (int i = threadIdx.x; i < kLogTab; i += kThreads) LT[i] = g.tlogtab[i];
+  for (int i = threadIdx.x; i < kExpTab; i += kThreads) ET[i] = g.texptab[i];
+  __syncthreads();
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  Rec64 &R = recs[warp];
+  Queue64 &Q = queues[warp];  // not touched for member sets (no room reserved)
+  const int per_tile = MODE == MODE_MC ? 16 : 32;
+  const int nc = MODE == MODE_MC ? g.nf : ncol;  // columns per point
+  const int cbase = MODE == MODE_MC ? 0 : col0;
+  const long long ntiles = (n + per_tile - 1) / per_tile;
+  const int nchunks = MODE == MODE_MEMBERS ? (g.nmem + mchunk - 1) / mchunk : 1;
+  const long long nunits = ntiles * nchunks;
+  const long long nwarps = (long long)gridDim.x * kWarps;
+  int nq = 0;  // queued continuation points (warp-uniform)
+
+  // a full (or final partial) tile of queued points, entries [base, base + cnt)
+  auto drain = [&](int base, int cnt) {
+    const bool present = lane < cnt;
+    double x = 0.0, q2 = 0.0, lq;
+    long long ob = 0;
+    if (present) { x = Q.x[base + lane]; q2 = Q.q2[base + lane]; ob = Q.ob[base + lane]; }
+    PointSites<double> ps;
+    ps.cls = -1;
+    if (present) ps = sites(g, xkeys, qkeys, x, q2, LT, lq);
+    int slot = 0;
+    const int np = sort_slots<C_LOWX, C_HIGHQ, C_LOWQ, C_LOWX_HIGHQ, C_LOWX_LOWQ>(ps.cls, lane, slot);
+    if (present) store_point(R, slot, ps, ob);
+    __syncwarp();
+    items64(g, R, np, nc, cbase, 0, 0, out, LT, ET, lane);
+    __syncwarp();
+  };
+
+  for (long long unit = (long long)blockIdx.x * kWarps + warp; unit < nunits; unit += nwarps) {
+    const long long tile = unit / nchunks;
+    const int chunk = (int)(unit - tile * nchunks);
+    const long long e0 = tile * per_tile;
+    const int ne = (int)(n - e0 < per_tile ? n - e0 : per_tile);
+
+    // ---- phase 1: lane = point ----
+    bool present;
+    double x = 0.0, q2 = 0.0, lq = 0.0;
+    long long ob;
+    if (MODE != MODE_MC) {
+      present = lane < ne;
+      if (present) { x = xa[e0 + lane]; q2 = qa[e0 + lane]; }
+      ob = (e0 + lane) * (long long)nc;
+    } else {
+      const int e = lane >> 1;
+      present = e < ne;
+      if (present) {
+        const double x1 = xa[e0 + e], x2 = xb[e0 + e];
+        q2 = x1 * x2 * s;
+        x = (lane & 1) ? x2 : x1;
+      }
+      ob = (e0 + e) * (long long)(2 * g.nf + 1) + (lane & 1) * g.nf;
+    }
+    PointSites<double> ps;
+    ps.cls = -1;
+    if (present) ps = sites(g, xkeys, qkeys, x, q2, LT, lq);
+    // in-grid points contract in float-float, except exact knot hits
+    // (t = u = 0), which keep FP64 so that knot values come back bit-exact
+    if (ps.cls == C_IN && g.ff &&
+        !((__double_as_longlong(ps.t0) << 1) == 0 && (__double_as_longlong(ps.u0) << 1) == 0))
+      ps.cls = C_INF;
+    if (MODE != MODE_MEMBERS || chunk == 0) {
+      const unsigned inv = __ballot_sync(kFull, ps.cls == C_INVALID);
+      if (lane == 0 && inv) atomicAdd(g.invalid, (unsigned long long)__popc(inv));
+    }
+    if (MODE == MODE_MC) {
+      if (present && (lane & 1) == 0) out[ob + 2 * g.nf] = alphas_eval(g, akeys, q2, lq);
+    } else if (MODE == MODE_POINTS) {
+      if (present && as_out) as_out[e0 + lane] = alphas_eval(g, akeys, q2, lq);
+    }
+
+    int key = ps.cls, slot = 0, np;
+    if (kQueue) {
+      const bool far = is_far(ps.cls);
+      const unsigned fm = __ballot_sync(kFull, far);
+      if (far) {
+        const int at = nq + __popc(fm & ((1u << lane) - 1u));
+        Q.x[at] = x;
+        Q.q2[at] = q2;
+        Q.ob[at] = ob;
+        key = -1;
+      }
+      nq += __popc(fm);
+      np = sort_slots<C_INF, C_IN, C_INVALID>(key, lane, slot);
+    } else {
+      np = sort_slots<C_INF, C_IN, C_LOWX, C_HIGHQ, C_LOWQ, C_LOWX_HIGHQ, C_LOWX_LOWQ, C_INVALID>(key, lane, slot);
+    }
+    if (key >= 0) store_point(R, slot, ps, ob);
+    __syncwarp();
+
+    // ---- phase 2: items ----
+    if (MODE == MODE_MEMBERS) {
+      const int m1 = min(g.nmem, (chunk + 1) * mchunk);
+      for (int m = chunk * mchunk; m < m1; m++)
+        items64(g, R, np, nc, cbase, (size_t)m * g.mstride, (long long)m * n * nc, out, LT, ET, lane);
+    } else {
+      items64(g, R, np, nc, cbase, 0, 0, out, LT, ET, lane);
+    }
+    __syncwarp();
+    if (kQueue && nq >= 32) {
+      nq -= 32;
+      drain(nq, 32);
+    }
+  }
+  if (kQueue && nq > 0) drain(0, nq);
+}
+
+static int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+template <int MODE>
+static size_t xf64_smem(const GridView &g) {
+  return keys_bytes(g.nx, 8) + keys_bytes(g.nrows, 8) + keys_bytes(g.na, 8) + sizeof(double2) * kLogTab +
+         sizeof(double) * kExpTab + kWarps * (sizeof(Rec64) + (MODE == MODE_MEMBERS ? 0 : sizeof(Queue64)));
+}
+
+template <int MODE>
+static int launch_mode(const pdf_grid *grid, const double *xa, const double *qa, const double *xb, double s,
+                       long long n, int col0, int ncol, double *out, double *as_out, cudaStream_t st) {
+  const GridView &g = grid->v;
+  const size_t smem = xf64_smem<MODE>(g);
+  auto kern = k_xf64<MODE>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+  if (per_sm < 1) per_sm = 1;
+  const int per_tile = MODE == MODE_MC ? 16 : 32;
+  const long long ntiles = (n + per_tile - 1) / per_tile;
+  const long long cap = (long long)num_sms() * per_sm;
+  // member sets: split the members into chunks until there are about two
+  // units per resident warp (one chunk when the points alone suffice)
+  int mchunk = 1;
+  long long nunits = ntiles;
+  if (MODE == MODE_MEMBERS) {
+    const long long target = 2 * cap * kWarps;
+    long long nchunks = (target + ntiles - 1) / ntiles;
+    if (nchunks > g.nmem) nchunks = g.nmem;
+    if (nchunks < 1) nchunks = 1;
+    mchunk = (int)((g.nmem + nchunks - 1) / nchunks);
+    nchunks = (g.nmem + mchunk - 1) / mchunk;
+    nunits = ntiles * nchunks;
+  }
+  long long blocks = (nunits + kWarps - 1) / kWarps;
+  if (blocks > cap) blocks = cap;
+  kern<<<(unsigned)blocks, kThreads, smem, st>>>(g, xa, qa, xb, s, n, col0, ncol, mchunk, out, as_out);
+  return check_launch(MODE == MODE_MC ? "pdf_mc_event kernel" : "xfxq2 kernel (FP64)");
+}
+
+int launch_xf64(const pdf_grid *grid, int mode, const double *xa, const double *qa, const double *xb, double s,
+                long long n, int col0, int ncol, double *out, double *as_out, cudaStream_t st) {
+  switch (mode) {
+    case MODE_POINTS: return launch_mode<MODE_POINTS>(grid, xa, qa, xb, s, n, col0, ncol, out, as_out, st);
+    case MODE_MC: return launch_mode<MODE_MC>(grid, xa, qa, xb, s, n, col0, ncol, out, nullptr, st);
+    default: return launch_mode<MODE_MEMBERS>(grid, xa, qa, xb, s, n, col0, ncol, out, nullptr, st);
+  }
+}
+
+}  // namespace pdfgb
