@@ -209,7 +209,9 @@ __global__ void k_coef(Stage S) {
   }
   double *o = S.coef + (size_t)gid * 16;
   float *o32 = S.coef32 + (size_t)gid * 16;
-  float2 *off = S.coefff + (size_t)gid * 16;
+  // float-float copy flavour-minor, [cell][m][flavour]: the lanes of one load
+  // (consecutive flavours of a point) read consecutive words
+  float2 *off = S.coefff + (size_t)(gid / S.nf) * 16 * S.nf + f;
   bool bad = false;
   for (int m = 0; m < 16; m++) {
     o[m] = c[m];
@@ -218,7 +220,7 @@ __global__ void k_coef(Stage S) {
     // while |c| stays well inside the float exponent range
     float hi = __double2float_rn(c[m]);
     float lo = __double2float_rn(c[m] - (double)hi);
-    off[m] = make_float2(hi, lo);
+    off[(size_t)m * S.nf] = make_float2(hi, lo);
     double a = fabs(c[m]);
     if (a != 0.0 && (a < 1e-30 || a > 1e30)) bad = true;
   }

@@ -9,6 +9,9 @@
 //          block (FP64) or 64 bytes (FP32), instead of gathering 16 knots;
 //          the Bernstein weights are non-negative and sum to one, so the
 //          evaluation has no cancellation beyond that of the data.
+//   coefff the same control points as float-float pairs (hi, lo), laid out
+//          [nqc+1][nx][16][nflav] so that one load instruction over the
+//          flavours of a point reads consecutive words.
 //   xk/q2k raw knots, searched as integer bit patterns (positive doubles
 //          order like their bits), so a cell choice never depends on a log.
 //   xcell  per x cell {ln x_i, 1/d, ln x_{i+1}, 0}, d = ln x_{i+1} - ln x_i;
@@ -66,7 +69,7 @@ struct GridView {
   double *vals;               // [nrows][nx][nf] device copy of the knot values
   const double *coef;         // [nqc + 1][nx][nf][16]
   const float *coef32;
-  const float2 *coefff;       // [nqc + 1][nx][nf][16] float-float (hi, lo) copy of coef
+  const float2 *coefff;       // [nqc + 1][nx][16][nf] float-float (hi, lo) copy of coef
   int ff;                     // 1 if every control point is safe for float-float
   int nmem;                   // members (replicas) sharing the knots; member m's
   size_t mstride;             // control points start m * mstride elements further

@@ -31,13 +31,16 @@ constexpr int kWarps = 8;
 constexpr int kThreads = 32 * kWarps;
 constexpr unsigned kFull = 0xffffffffu;
 
-// Per-warp record of the points of one tile, by class-sorted slot.  W holds
-// for C_INF the 16 float-float weight products (hi, lo) at [l*4 + k], for
-// C_IN the 16 FP64 products, otherwise Bx0 | Bx1 | Bq0 | Bq1.
+// Per-warp record of the points of one tile, by class-sorted slot.  Each
+// slot owns one 144-byte row of weights: for C_INF the 16 float-float
+// products Bx[k] Bq[l] (hi, lo) at [l*4 + k], for C_IN the same products in
+// FP64, otherwise Bx0 | Bx1 | Bq0 | Bq1 in FP64.  Rows are padded from 128
+// to 144 bytes so that the few slots one load instruction touches fall in
+// different banks, and stay 16-byte aligned for paired loads.
 struct alignas(16) Rec64 {
   int cls[32], xc0[32], xc1[32], qc0[32], qc1[32];
   long long ob[32];  // output offset of the point's first column
-  double W[16][33];  // padded: the rows of one slot fall in different banks
+  double W[32][18];
   double px[32], pq[32], lr[32];
 };
 // Continuation points waiting for a full tile (at most 31 + 32).
@@ -82,21 +85,21 @@ __device__ __forceinline__ double f2d(float f) {
   return (double)f;
 }
 // sum_m w_m b_m with w (hi, lo) from the record and b (hi, lo) from the
-// float-float control points: exact products, TwoSum accumulation, the
-// cross terms and the rounding errors gathered in a second float.
-__device__ __forceinline__ double dot_ff16(const float2 *c, const double (*W)[33], int p) {
-  const float4 *q = reinterpret_cast<const float4 *>(c);
+// float-float control points (stride nf between consecutive m): exact
+// products, TwoSum accumulation, the cross terms and the rounding errors
+// gathered in a second float.
+__device__ __forceinline__ double dot_ff16(const float2 *c, int nf, const float2 *w) {
   float sh = 0.f, sl = 0.f;
 #pragma unroll
   for (int m2 = 0; m2 < 8; m2++) {
-    const float4 v = __ldg(q + m2);
+    const float4 ww = *reinterpret_cast<const float4 *>(w + 2 * m2);
 #pragma unroll
     for (int half = 0; half < 2; half++) {
-      const float bh = half ? v.z : v.x, bl = half ? v.w : v.y;
-      const float2 w = *reinterpret_cast<const float2 *>(&W[2 * m2 + half][p]);
-      const float ph = __fmul_rn(w.x, bh);
-      float pe = __fmaf_rn(w.x, bh, -ph);
-      pe = __fmaf_rn(w.x, bl, __fmaf_rn(w.y, bh, pe));
+      const float2 b = __ldg(c + (size_t)(2 * m2 + half) * nf);
+      const float wh = half ? ww.z : ww.x, wl = half ? ww.w : ww.y;
+      const float ph = __fmul_rn(wh, b.x);
+      float pe = __fmaf_rn(wh, b.x, -ph);
+      pe = __fmaf_rn(wh, b.y, __fmaf_rn(wl, b.x, pe));
       const float t = __fadd_rn(sh, ph);
       const float bp = __fsub_rn(t, sh);
       const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bp)), __fsub_rn(ph, bp));
@@ -111,13 +114,13 @@ __device__ __forceinline__ double dot_ff16(const float2 *c, const double (*W)[33
 __device__ __forceinline__ double dot_w16(const double *c, const Rec64 &R, int p) {
   const double2 *q = reinterpret_cast<const double2 *>(c);
   double2 v = __ldg(q);
-  double acc = R.W[0][p] * v.x;
-  acc = fma(R.W[1][p], v.y, acc);
+  double acc = R.W[p][0] * v.x;
+  acc = fma(R.W[p][1], v.y, acc);
 #pragma unroll
   for (int m = 1; m < 8; m++) {
     v = __ldg(q + m);
-    acc = fma(R.W[2 * m][p], v.x, acc);
-    acc = fma(R.W[2 * m + 1][p], v.y, acc);
+    acc = fma(R.W[p][2 * m], v.x, acc);
+    acc = fma(R.W[p][2 * m + 1], v.y, acc);
   }
   return acc;
 }
@@ -128,29 +131,29 @@ __device__ __forceinline__ double site_tu(const double *c, const Rec64 &R, int p
   for (int l = 0; l < 4; l++) {
     const double2 *q = reinterpret_cast<const double2 *>(c + 4 * l);
     double2 v0 = __ldg(q), v1 = __ldg(q + 1);
-    double r = R.W[4 * a][p] * v0.x;
-    r = fma(R.W[4 * a + 1][p], v0.y, r);
-    r = fma(R.W[4 * a + 2][p], v1.x, r);
-    r = fma(R.W[4 * a + 3][p], v1.y, r);
-    f = l == 0 ? R.W[8 + 4 * b][p] * r : fma(R.W[8 + 4 * b + l][p], r, f);
+    double r = R.W[p][4 * a] * v0.x;
+    r = fma(R.W[p][4 * a + 1], v0.y, r);
+    r = fma(R.W[p][4 * a + 2], v1.x, r);
+    r = fma(R.W[p][4 * a + 3], v1.y, r);
+    f = l == 0 ? R.W[p][8 + 4 * b] * r : fma(R.W[p][8 + 4 * b + l], r, f);
   }
   return f;
 }
 // site on an x knot (t = 0): sum_l Bq[l] b[l][0]
 __device__ __forceinline__ double site_u(const double *c, const Rec64 &R, int p, int b) {
-  double f = R.W[8 + 4 * b][p] * __ldg(c);
-  f = fma(R.W[8 + 4 * b + 1][p], __ldg(c + 4), f);
-  f = fma(R.W[8 + 4 * b + 2][p], __ldg(c + 8), f);
-  return fma(R.W[8 + 4 * b + 3][p], __ldg(c + 12), f);
+  double f = R.W[p][8 + 4 * b] * __ldg(c);
+  f = fma(R.W[p][8 + 4 * b + 1], __ldg(c + 4), f);
+  f = fma(R.W[p][8 + 4 * b + 2], __ldg(c + 8), f);
+  return fma(R.W[p][8 + 4 * b + 3], __ldg(c + 12), f);
 }
 // site on a Q knot (u = 0): sum_k Bx[k] b[0][k]
 __device__ __forceinline__ double site_t(const double *c, const Rec64 &R, int p, int a) {
   const double2 *q = reinterpret_cast<const double2 *>(c);
   double2 v0 = __ldg(q), v1 = __ldg(q + 1);
-  double f = R.W[4 * a][p] * v0.x;
-  f = fma(R.W[4 * a + 1][p], v0.y, f);
-  f = fma(R.W[4 * a + 2][p], v1.x, f);
-  return fma(R.W[4 * a + 3][p], v1.y, f);
+  double f = R.W[p][4 * a] * v0.x;
+  f = fma(R.W[p][4 * a + 1], v0.y, f);
+  f = fma(R.W[p][4 * a + 2], v1.x, f);
+  return fma(R.W[p][4 * a + 3], v1.y, f);
 }
 
 // One item: column col of the point in slot p.  moff: the member's offset
@@ -166,7 +169,8 @@ __device__ __forceinline__ double eval_item64(const GridView &g, const Rec64 &R,
   };
   const int cls = R.cls[p];
   if (cls == C_INF)
-    return dot_ff16(g.coefff + moff + (((size_t)R.qc0[p] * g.nx + R.xc0[p]) * g.nf + col) * 16, R.W, p);
+    return dot_ff16(g.coefff + moff + ((size_t)R.qc0[p] * g.nx + R.xc0[p]) * 16 * g.nf + col, g.nf,
+                    reinterpret_cast<const float2 *>(R.W[p]));
   if (cls == C_IN) return dot_w16(C(0, 0), R, p);
   if (cls == C_INVALID) return NAN;
   // continuation: the two values the final rule combines, then one shared rule
@@ -216,7 +220,7 @@ __device__ __forceinline__ void store_point(Rec64 &R, int slot, const PointSites
 #pragma unroll
       for (int k = 0; k < 4; k++) {
         const ff2 w = ff_mul(bx[k], bq[l]);
-        *reinterpret_cast<float2 *>(&R.W[l * 4 + k][slot]) = make_float2(w.h, w.l);
+        reinterpret_cast<float2 *>(R.W[slot])[l * 4 + k] = make_float2(w.h, w.l);
       }
     return;
   }
@@ -227,7 +231,7 @@ __device__ __forceinline__ void store_point(Rec64 &R, int slot, const PointSites
 #pragma unroll
     for (int l = 0; l < 4; l++)
 #pragma unroll
-      for (int k = 0; k < 4; k++) R.W[l * 4 + k][slot] = bx0[k] * bq0[l];
+      for (int k = 0; k < 4; k++) R.W[slot][l * 4 + k] = bx0[k] * bq0[l];
     return;
   }
   double bx1[4], bq1[4];
@@ -235,10 +239,10 @@ __device__ __forceinline__ void store_point(Rec64 &R, int slot, const PointSites
   bernstein<double>(ps.u1, 1.0 - ps.u1, bq1);
 #pragma unroll
   for (int k = 0; k < 4; k++) {
-    R.W[k][slot] = bx0[k];
-    R.W[4 + k][slot] = bx1[k];
-    R.W[8 + k][slot] = bq0[k];
-    R.W[12 + k][slot] = bq1[k];
+    R.W[slot][k] = bx0[k];
+    R.W[slot][4 + k] = bx1[k];
+    R.W[slot][8 + k] = bq0[k];
+    R.W[slot][12 + k] = bq1[k];
   }
 }
 
