@@ -36,6 +36,7 @@ sys.path.insert(0, str(ROOT))
 METRIC = "PDF evals/s (points×flavours) FP64 vs FP32 vs surrogate at stated max rel err"
 N_POINTS = 10_000_000
 MC_EVENTS = 1_000_000
+MC_INTEGRATE_EVENTS = 100_000_000
 ADJ_POINTS = 1_000_000
 SURR_TRAIN, SURR_VAL, SURR_INFER = 20_000_000, 1_000_000, 100_000_000
 # PDFFlow Table 2 (Sec. 4.3): all 13 flavours of N_rep members at 2415 x
@@ -380,6 +381,37 @@ def members_leg(args, dev, world, sync, rank):
             "paper_hardware": "PDFFlow v1.0 on TITAN V or RTX 2080 Ti (system P1); context, not the target"}
 
 
+def mc_leg(G, world, sync, rank):
+    """Monte Carlo integration (SURVEY cfg 3): 1e8 events per rank in 100
+    chunks of 1e6, device RNG, fused PDF + alpha_s load, weights summed on the
+    device; the three sums are added over ranks (the integration's one
+    exchange step)."""
+    import paper_2009_06635_gb300 as P
+
+    n, chunk = MC_INTEGRATE_EVENTS, MC_EVENTS
+    cfg = dict(sqrt_s=13000.0, x_min=1e-6, shat_min=100.0, seed=4)
+    P.pdf_mc_integrate(G, cfg["sqrt_s"], cfg["x_min"], cfg["shat_min"], cfg["seed"], 3 * chunk, chunk=chunk)  # warm-up
+    sync()
+    barrier(world)
+    t0 = time.perf_counter()
+    r = P.pdf_mc_integrate(G, cfg["sqrt_s"], cfg["x_min"], cfg["shat_min"], cfg["seed"], n, first_event=rank * n,
+                           chunk=chunk)
+    sync()
+    s = max_over_ranks(world, time.perf_counter() - t0)
+    sums = [r.sum_w, r.sum_w2, r.sum_abs]
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        t = torch.tensor(sums, dtype=torch.float64, device="cuda")
+        dist.all_reduce(t)
+        sums = t.tolist()
+    tot = P.McResult(sums, world * n)
+    return {"events": world * n, "chunk": chunk, "s": s, "events_per_s": world * n / s,
+            "evals_per_s": world * n * (2 * 13 + 1) / s, "estimate": tot.estimate, "std_error": tot.std_error,
+            "config": dict(cfg, observable="toy LO: L^2/s-hat [sum_q e_q^2 (q qbar + qbar q) + alpha_s^2 g g]")}
+
+
 def P_xf(G, x, q2):
     import paper_2009_06635_gb300 as P
 
@@ -492,6 +524,7 @@ def our_arm(args):
 
     ms_adj = run_timed(step_adj, args.steps, 2, world, sync)
 
+    mc_int = mc_leg(G, world, sync, rank)
     members = None if args.no_members else members_leg(args, dev, world, sync, rank)
     surrogate = None if args.no_surrogate else surrogate_leg(args, G, g, dev, world, sync, rank, nf, ms64 / (n * (nf + 1)))
 
@@ -563,6 +596,7 @@ def our_arm(args):
                               "ms_per_step": ms_mc32, "events": MC_EVENTS},
             "surrogate_bf16": surrogate,
             "members_table2": members,
+            "mc_integrate_fp64": mc_int,
             "adjoint_fp64": {"value": world * ADJ_POINTS * nf / (ms_adj * 1e-3), "ms_per_step": ms_adj,
                              "points": ADJ_POINTS, "unit": "(point, flavour) gradients/s",
                              "outputs": "d/dx, d/dQ^2 per point and d/d(knot values), FP64 atomics"},

@@ -174,6 +174,38 @@ PDF_API int pdf_mc_event(const pdf_grid *grid, const double *x1, const double *x
 PDF_API int pdf_mc_event_f32(const pdf_grid *grid, const float *x1, const float *x2, float s, size_t n,
                      float *out, cudaStream_t stream);
 
+/* Monte Carlo integration driven by the PDF load (PDFFlow Sec. 4.1; the
+ * VegasFlow use of Sec. 5): events are generated on the device, their
+ * flavours and alpha_s evaluated by the fused event kernel, and their weights
+ * summed on the device in a fixed order, chunk by chunk.
+ *   Event i (global index): u1 = U(z_{2i}), u2 = U(z_{2i+1}), z_k the k-th
+ *   output of SplitMix64 seeded with `seed` (Steele, Lea, Flood, OOPSLA 2014:
+ *   state seed + (k+1) * 0x9E3779B97F4A7C15 through its 64-bit finaliser),
+ *   U(z) = (z >> 11) * 2^-53; ln x_j = ln x_max + u_j (ln x_min - ln x_max),
+ *   x_max = the grid's last x knot; s-hat = x1 x2 sqrt_s^2 = Q^2.
+ *   Weight (a toy leading-order observable standing in for the paper's
+ *   processes, whose matrix elements are not part of this library):
+ *     w = L^2 / s-hat * [ sum_{q=1..5} e_q^2 (xf_q(x1) xf_-q(x2) + xf_-q(x1) xf_q(x2))
+ *                         + alpha_s(s-hat)^2 xf_g(x1) xf_g(x2) ]   if s-hat >= shat_min,
+ *     w = 0 otherwise; L = ln x_max - ln x_min, e_q = -1/3, 2/3, -1/3, 2/3, -1/3
+ *     (d, u, s, c, b).  The mean of w estimates the integral over x1, x2 in
+ *     [x_min, x_max] of [...] / (x1 x2 s-hat).
+ * sums: HOST [3], receives (sum w, sum w^2, sum |w|) over the events
+ * [first_event, first_event + n_events).  chunk: events per launch (>= 1).
+ * Requires alpha_s and pids 1..5, -1..-5, 21 (PDF_ERR_NO_ALPHAS, PDF_ERR_PID);
+ * 0 < x_min < last x knot, sqrt_s > 0, shat_min >= 0 (PDF_ERR_ARG).  The
+ * device scratch (chunk x (2 nflav + 1) doubles) belongs to the grid and is
+ * reused: calls on one grid must not overlap.  Returns when sums are on the
+ * host; the result is bit-reproducible for given (seed, events, chunk). */
+typedef struct {
+  double sqrt_s;           /* collider energy, GeV */
+  double x_min;            /* lower end of the x1, x2 sampling range */
+  double shat_min;         /* cut on s-hat, GeV^2 */
+  unsigned long long seed; /* SplitMix64 seed */
+} pdf_mc_config;
+PDF_API int pdf_mc_integrate(const pdf_grid *grid, const pdf_mc_config *cfg, unsigned long long first_event,
+                             unsigned long long n_events, size_t chunk, double *sums, cudaStream_t stream);
+
 /* Host-memory variant of xfxq2_all_flavours (end-to-end use: host inputs,
  * host outputs): out is [n][nflav]; if alphas_out is not NULL it receives
  * alpha_s(q2) [n] as well (the grid then needs alpha_s nodes).  Synchronous;

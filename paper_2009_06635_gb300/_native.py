@@ -55,6 +55,7 @@ SIGNATURES = {
     "xfxq2": (I32, [P, I32, P, P, SZ, P, P]),
     "xfxq2_all_flavours": (I32, [P, P, P, SZ, P, P]),
     "xfxq2_all_flavours_alphas": (I32, [P, P, P, SZ, P, P, P]),
+    "pdf_mc_integrate": (I32, [P, P, ctypes.c_ulonglong, ctypes.c_ulonglong, SZ, P, P]),
     "alphas_q2": (I32, [P, P, SZ, P, P]),
     "xfxq2_f32": (I32, [P, I32, P, P, SZ, P, P]),
     "xfxq2_all_flavours_f32": (I32, [P, P, P, SZ, P, P]),
@@ -80,6 +81,11 @@ SIGNATURES = {
     "pdf_surrogate_build_error_map": (I32, [P, P, P, P, SZ, F64, P]),
     "pdf_surrogate_eval_fallback": (I32, [P, P, P, P, SZ, P, ctypes.POINTER(ctypes.c_ulonglong), P]),
 }
+
+
+class McConfig(ctypes.Structure):
+    _fields_ = [("sqrt_s", ctypes.c_double), ("x_min", ctypes.c_double), ("shat_min", ctypes.c_double),
+                ("seed", ctypes.c_ulonglong)]
 
 
 class TrainConfig(ctypes.Structure):

@@ -536,6 +536,8 @@ extern "C" int pdf_free_grid(pdf_grid *g) {
     if (g->io_stream[k]) { cudaStreamSynchronize(g->io_stream[k]); cudaStreamDestroy(g->io_stream[k]); }
     if (g->io_buf[k]) cudaFree(g->io_buf[k]);
   }
+  if (g->mc_buf) cudaFree(g->mc_buf);
+  if (g->mc_part) cudaFree(g->mc_part);
   for (int b = 0; b < g->nblocks; b++) cudaFree(g->blocks[b]);
   delete g;
   return PDF_OK;

@@ -206,14 +206,22 @@ struct pdf_grid {
   cudaEvent_t io_event[2];
   void *io_buf[2];
   size_t io_cap;  // points per buffer
+  // Monte Carlo integration scratch (lazily created): event rows, per-block
+  // partial sums, the running sums
+  double *mc_buf;
+  size_t mc_cap;  // events per chunk the buffer holds
+  double *mc_part, *mc_acc;
 };
 
 namespace pdfgb {
 // FP64 evaluation (xf64.cu), mode = MODE_*: points xa, qa (columns
 // col0..col0+ncol-1; alpha_s into as_out when not null), events xa, xb with
 // Q^2 = xa xb s, or every member of the set.  Arguments already validated.
+// With gen (MODE_MC only) the events are generated on the device (mc.cuh).
+struct McGen;
 int launch_xf64(const pdf_grid *grid, int mode, const double *xa, const double *qa, const double *xb, double s,
-                long long n, int col0, int ncol, double *out, double *as_out, cudaStream_t st);
+                long long n, int col0, int ncol, double *out, double *as_out, cudaStream_t st,
+                const McGen *gen = nullptr);
 // xfxq2.cu: all flavours (+ alpha_s when as_out is not null); alpha_s alone.
 int launch_all_f64(const pdf_grid *g, const double *x, const double *q2, long long n, double *out,
                    double *as_out, cudaStream_t st);

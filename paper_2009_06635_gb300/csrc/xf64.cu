@@ -21,6 +21,7 @@
 // different classes reconverge before its logarithm and exponential.
 #include <cmath>
 
+#include "mc.cuh"
 #include "sites.cuh"
 
 namespace pdfgb {
@@ -283,14 +284,15 @@ __device__ __forceinline__ int sort_slots(int key, int lane, int &slot) {
 // MODE_POINTS:  points xa[n], qa[n]; out[n][ncol] for columns col0..col0+ncol-1;
 //               as_out[n] (alpha_s) when not null.
 // MODE_MC:      events xa[n] (x1), xb[n] (x2), Q^2 = x1 x2 s; out[n][2 nf + 1]
-//               (the flavours at x1, at x2, alpha_s).
+//               (the flavours at x1, at x2, alpha_s); with gen.on the events
+//               are generated (mc.cuh) and xa, xb are not read.
 // MODE_MEMBERS: points xa[n], qa[n]; out[nmem][n][nf].  A warp's unit is
 //               (tile, chunk of mchunk members); phase 1 repeats per chunk.
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, 3)
 k_xf64(GridView g, const double *__restrict__ xa, const double *__restrict__ qa, const double *__restrict__ xb,
        double s, long long n, int col0, int ncol, int mchunk, double *__restrict__ out,
-       double *__restrict__ as_out) {
+       double *__restrict__ as_out, McGen gen) {
   constexpr bool kQueue = MODE != MODE_MEMBERS;
   extern __shared__ __align__(16) unsigned char smem[];
   size_t off = 0;
@@ -363,7 +365,9 @@ k_xf64(GridView g, const double *__restrict__ xa, const double *__restrict__ qa,
       const int e = lane >> 1;
       present = e < ne;
       if (present) {
-        const double x1 = xa[e0 + e], x2 = xb[e0 + e];
+        double x1, x2;
+        if (gen.on) mc_event(gen, (unsigned long long)(e0 + e), x1, x2);
+        else { x1 = xa[e0 + e]; x2 = xb[e0 + e]; }
         q2 = x1 * x2 * s;
         x = (lane & 1) ? x2 : x1;
       }
@@ -442,7 +446,8 @@ static size_t xf64_smem(const GridView &g) {
 
 template <int MODE>
 static int launch_mode(const pdf_grid *grid, const double *xa, const double *qa, const double *xb, double s,
-                       long long n, int col0, int ncol, double *out, double *as_out, cudaStream_t st) {
+                       long long n, int col0, int ncol, double *out, double *as_out, const McGen &gen,
+                       cudaStream_t st) {
   const GridView &g = grid->v;
   const size_t smem = xf64_smem<MODE>(g);
   auto kern = k_xf64<MODE>;
@@ -468,16 +473,18 @@ static int launch_mode(const pdf_grid *grid, const double *xa, const double *qa,
   }
   long long blocks = (nunits + kWarps - 1) / kWarps;
   if (blocks > cap) blocks = cap;
-  kern<<<(unsigned)blocks, kThreads, smem, st>>>(g, xa, qa, xb, s, n, col0, ncol, mchunk, out, as_out);
+  kern<<<(unsigned)blocks, kThreads, smem, st>>>(g, xa, qa, xb, s, n, col0, ncol, mchunk, out, as_out, gen);
   return check_launch(MODE == MODE_MC ? "pdf_mc_event kernel" : "xfxq2 kernel (FP64)");
 }
 
 int launch_xf64(const pdf_grid *grid, int mode, const double *xa, const double *qa, const double *xb, double s,
-                long long n, int col0, int ncol, double *out, double *as_out, cudaStream_t st) {
+                long long n, int col0, int ncol, double *out, double *as_out, cudaStream_t st, const McGen *gen) {
+  McGen off{};
+  const McGen &G = gen ? *gen : off;
   switch (mode) {
-    case MODE_POINTS: return launch_mode<MODE_POINTS>(grid, xa, qa, xb, s, n, col0, ncol, out, as_out, st);
-    case MODE_MC: return launch_mode<MODE_MC>(grid, xa, qa, xb, s, n, col0, ncol, out, nullptr, st);
-    default: return launch_mode<MODE_MEMBERS>(grid, xa, qa, xb, s, n, col0, ncol, out, nullptr, st);
+    case MODE_POINTS: return launch_mode<MODE_POINTS>(grid, xa, qa, xb, s, n, col0, ncol, out, as_out, off, st);
+    case MODE_MC: return launch_mode<MODE_MC>(grid, xa, qa, xb, s, n, col0, ncol, out, nullptr, G, st);
+    default: return launch_mode<MODE_MEMBERS>(grid, xa, qa, xb, s, n, col0, ncol, out, nullptr, off, st);
   }
 }
 

@@ -163,6 +163,42 @@ def xfxq2_all_flavours_alphas(grid: Grid, x: torch.Tensor, q2: torch.Tensor, out
     return out, alphas_out
 
 
+class McResult:
+    """Sums of a Monte Carlo run and the estimate they give (the mean weight
+    and its standard error)."""
+
+    def __init__(self, sums, n):
+        self.sum_w, self.sum_w2, self.sum_abs = (float(v) for v in sums)
+        self.n = int(n)
+
+    @property
+    def estimate(self) -> float:
+        return self.sum_w / self.n
+
+    @property
+    def std_error(self) -> float:
+        m = self.estimate
+        var = max(self.sum_w2 / self.n - m * m, 0.0)
+        return (var / max(self.n - 1, 1)) ** 0.5
+
+    def __repr__(self):
+        return f"McResult(n={self.n}, estimate={self.estimate:.10g} +- {self.std_error:.3g})"
+
+
+def pdf_mc_integrate(grid: Grid, sqrt_s: float, x_min: float, shat_min: float, seed: int, n_events: int,
+                     first_event: int = 0, chunk: int = 1 << 20) -> McResult:
+    """Monte Carlo integration of the toy leading-order observable of
+    pdf_mc_integrate (include/pdf_gb300.h) over events [first_event,
+    first_event + n_events): device RNG, fused PDF + alpha_s load, weights
+    summed on the device.  Runs on the grid's device, current stream."""
+    cfg = _native.McConfig(float(sqrt_s), float(x_min), float(shat_min), int(seed) & (2**64 - 1))
+    sums = (ctypes.c_double * 3)()
+    dev = grid.device if isinstance(grid.device, torch.device) else torch.device("cuda", grid.device)
+    check(_native.load().pdf_mc_integrate(grid.handle, ctypes.byref(cfg), int(first_event), int(n_events),
+                                          int(chunk), sums, _stream_handle(dev)), "pdf_mc_integrate")
+    return McResult(sums, n_events)
+
+
 def xfxq2_all_members(grid: Grid, x: torch.Tensor, q2: torch.Tensor, out=None) -> torch.Tensor:
     """All flavours of every member: [nmem][n][nflav] FP64."""
     _check_pair(x, q2)
