@@ -119,6 +119,32 @@ PDF_API int pdf_load_grid_members(const pdf_grid_desc *desc, int nmem, const dou
                                   pdf_grid **out);
 PDF_API int pdf_grid_nmembers(const pdf_grid *grid);
 
+/* LHAPDF6 sets in the "lhagrid1" text format, read directly as PDFFlow
+ * Sec. 2.2 does (no conversion step); the alpha_s nodes come from the set's
+ * metadata (Sec. 2.3).  A set is a directory NAME/ with NAME.info (YAML:
+ * Flavors, AlphaS_Qs, AlphaS_Vals are read; lists may span lines) and
+ * NAME_0000.dat, NAME_0001.dat, ... (a YAML header closed by "---", then per
+ * Q subgrid: a line of x knots, a line of Q knots in GeV, a line of pids,
+ * nx * nq lines of nflav values xf with x the outer loop, and "---").  The
+ * subgrids must share the x knots and the flavours.
+ *
+ * pdf_load_lhapdf: members first_member .. first_member + nmem - 1 of the set
+ * in set_dir onto the current device (nmem = 1: pdf_load_grid; nmem > 1:
+ * pdf_load_grid_members, every member with the same knots and flavours).
+ * Errors: PDF_ERR_NULL, PDF_ERR_ARG (unreadable file, bad member range),
+ * PDF_ERR_GRID (malformed file; the message names the file and the line's
+ * subgrid), and those of pdf_load_grid.
+ *
+ * pdf_lhapdf_read / pdf_lhapdf_desc / pdf_lhapdf_free: the parser alone, on
+ * the host (no device work): read one .info + .dat pair into a host object,
+ * describe it as a pdf_grid_desc whose arrays point into that object (valid
+ * until pdf_lhapdf_free), free it. */
+typedef struct pdf_lhapdf_set pdf_lhapdf_set;
+PDF_API int pdf_load_lhapdf(const char *set_dir, int first_member, int nmem, pdf_grid **out);
+PDF_API int pdf_lhapdf_read(const char *info_path, const char *dat_path, pdf_lhapdf_set **out);
+PDF_API int pdf_lhapdf_desc(const pdf_lhapdf_set *set, pdf_grid_desc *desc);
+PDF_API int pdf_lhapdf_free(pdf_lhapdf_set *set);
+
 /* Free a handle and all its device memory (NULL is a no-op).  Waits for
  * work the handle's own streams still run. */
 PDF_API int pdf_free_grid(pdf_grid *grid);

@@ -13,9 +13,10 @@ from ._native import PdfError
 from .pdf import (Grid, XfxQ2AllFlavours, alphas_q2, pdf_grid_set_values, pdf_load_grid, pdf_mc_event,
                   xfxq2, xfxq2_all_flavours, xfxq2_all_flavours_diff, xfxq2_all_flavours_host,
                   xfxq2_all_flavours_vjp, xfxq2_all_members, xfxq2_all_flavours_alphas,
-                  McResult, pdf_mc_integrate)
+                  McResult, pdf_mc_integrate, pdf_load_lhapdf, read_lhapdf)
 
 __all__ = ["synthetic", "PdfError", "Grid", "pdf_load_grid", "xfxq2", "xfxq2_all_flavours",
            "alphas_q2", "pdf_mc_event", "xfxq2_all_flavours_host", "xfxq2_all_flavours_vjp",
            "pdf_grid_set_values", "XfxQ2AllFlavours", "xfxq2_all_flavours_diff", "xfxq2_all_members",
-           "xfxq2_all_flavours_alphas", "McResult", "pdf_mc_integrate"]
+           "xfxq2_all_flavours_alphas", "McResult", "pdf_mc_integrate",
+           "pdf_load_lhapdf", "read_lhapdf"]

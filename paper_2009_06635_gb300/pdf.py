@@ -163,6 +163,53 @@ def xfxq2_all_flavours_alphas(grid: Grid, x: torch.Tensor, q2: torch.Tensor, out
     return out, alphas_out
 
 
+def _lhapdf_paths(set_dir, member: int):
+    import os
+    d = os.fspath(set_dir).rstrip("/")
+    name = os.path.basename(d)
+    return os.path.join(d, name + ".info"), os.path.join(d, f"{name}_{member:04d}.dat")
+
+
+def read_lhapdf(info_path, dat_path) -> dict:
+    """Parse one LHAPDF6 member (lhagrid1 text) on the host, with the
+    library's own reader: x_knots, nq, q2_knots, pids, values [rows][nx][nflav],
+    as_q2, as_vals as numpy arrays."""
+    import os
+    lib = _native.load()
+    h = ctypes.c_void_p(None)
+    check(lib.pdf_lhapdf_read(os.fsencode(info_path), os.fsencode(dat_path), ctypes.byref(h)), "pdf_lhapdf_read")
+    try:
+        d = _native.GridDesc()
+        check(lib.pdf_lhapdf_desc(h, ctypes.byref(d)), "pdf_lhapdf_desc")
+
+        def arr(ptr, n, ct):
+            return np.ctypeslib.as_array(ctypes.cast(ptr, ctypes.POINTER(ct)), shape=(n,)).copy() if n else \
+                np.zeros(0, dtype=np.float64 if ct is ctypes.c_double else np.int32)
+        nq = arr(d.nq, d.nsub, ctypes.c_int)
+        rows = int(nq.sum())
+        return {"x_knots": arr(d.x_knots, d.nx, ctypes.c_double), "nq": [int(v) for v in nq],
+                "q2_knots": arr(d.q2_knots, rows, ctypes.c_double),
+                "pids": [int(v) for v in arr(d.pids, d.nflav, ctypes.c_int)],
+                "values": arr(d.values, rows * d.nx * d.nflav, ctypes.c_double).reshape(rows, d.nx, d.nflav),
+                "as_q2": arr(d.as_q2, d.na, ctypes.c_double), "as_vals": arr(d.as_vals, d.na, ctypes.c_double)}
+    finally:
+        lib.pdf_lhapdf_free(h)
+
+
+def pdf_load_lhapdf(set_dir, member: int = 0, nmem: int = 1) -> Grid:
+    """Members member .. member + nmem - 1 of an LHAPDF6 set directory (the
+    lhagrid1 text format, read by the library's native reader) onto the
+    current CUDA device."""
+    import os
+    info, dat = _lhapdf_paths(set_dir, member)
+    meta = read_lhapdf(info, dat)
+    h = ctypes.c_void_p(None)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    check(_native.load().pdf_load_lhapdf(os.fsencode(os.fspath(set_dir)), int(member), int(nmem), ctypes.byref(h)),
+          "pdf_load_lhapdf")
+    return Grid(h.value, meta["pids"], dev, len(meta["x_knots"]), len(meta["q2_knots"]), nmem)
+
+
 class McResult:
     """Sums of a Monte Carlo run and the estimate they give (the mean weight
     and its standard error)."""

@@ -280,3 +280,52 @@ def fit_points(n: int = 2415, q: float = FIT_Q):
     """x grid of a fit's convolution tables: n points log-spaced in [1e-9, 1), at Q^2 = q^2."""
     x = np.geomspace(1e-9, 1.0, n + 1)[:-1]
     return x, np.full(n, q * q)
+
+
+# --------------------------------------------------------------------------
+# LHAPDF6 text files (lhagrid1) of a synthetic set
+# --------------------------------------------------------------------------
+
+def write_lhapdf(grid: Grid, set_dir, member_values=None, digits: int = 17):
+    """Write grid as an LHAPDF6 set directory (NAME.info + NAME_%04d.dat, one
+    file per member; member_values [nmem][rows][nx][nflav] or the grid's own
+    values).  Q knots are written as sqrt(Q^2); with 17 digits every number
+    reads back exactly (the Q^2 knots as sqrt(Q^2)^2).  Returns the paths."""
+    import os
+    d = os.fspath(set_dir).rstrip("/")
+    name = os.path.basename(d)
+    os.makedirs(d, exist_ok=True)
+    fmt = f"%.{digits - 1}e"
+    members = [grid.values] if member_values is None else list(member_values)
+    nums = lambda a: " ".join(fmt % v for v in np.asarray(a, dtype=np.float64).ravel())  # noqa: E731
+    with open(os.path.join(d, name + ".info"), "w") as f:
+        f.write(f"SetDesc: \"synthetic LHAPDF-shaped set written by write_lhapdf\"\n")
+        f.write("Format: lhagrid1\n")
+        f.write(f"NumMembers: {len(members)}\n")
+        f.write("Flavors: [" + ", ".join(str(p) for p in grid.pids) + "]\n")
+        f.write(f"XMin: {fmt % grid.x_knots[0]}\nXMax: {fmt % grid.x_knots[-1]}\n")
+        if len(grid.as_q2):
+            qs = [fmt % q for q in np.sqrt(np.asarray(grid.as_q2))]
+            f.write("AlphaS_Type: ipol\n")
+            # a list continued over lines, as long metadata lists often are
+            f.write("AlphaS_Qs: [" + ",\n  ".join(", ".join(qs[i:i + 8]) for i in range(0, len(qs), 8)) + "]\n")
+            f.write("AlphaS_Vals: [" + ", ".join(fmt % v for v in grid.as_vals) + "]\n")
+    paths = []
+    starts = np.concatenate([[0], np.cumsum(grid.nq)])
+    for m, vals in enumerate(members):
+        p = os.path.join(d, f"{name}_{m:04d}.dat")
+        with open(p, "w") as f:
+            f.write(f"PdfType: {'central' if m == 0 else 'replica'}\nFormat: lhagrid1\n---\n")
+            for s in range(len(grid.nq)):
+                r0, r1 = starts[s], starts[s + 1]
+                f.write(nums(grid.x_knots) + "\n")
+                f.write(nums(np.sqrt(grid.q2_knots[r0:r1])) + "\n")
+                f.write(" ".join(str(p_) for p_ in grid.pids) + "\n")
+                block = np.asarray(vals)[r0:r1]  # [nq][nx][nf]
+                for ix in range(len(grid.x_knots)):
+                    for iq in range(r1 - r0):
+                        f.write(nums(block[iq, ix]) + "\n")
+                f.write("---\n")
+        paths.append(p)
+    return paths
+
