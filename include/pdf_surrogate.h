@@ -8,9 +8,18 @@
  *
  * Network: (ln x, ln Q^2) scaled to [-1, 1]^2 -> 32 Fourier features
  * (sin and cos of pi (F z), F a fixed [16][2] matrix) -> four layers of width
- * 128 with SiLU -> one output per flavour; xf_f = c_f sinh(y_f) with
- * c_f = 1e-5 max |xf_f| over the grid's knots (training target
- * y_f = asinh(xf_f / c_f)).  Products run on BF16 tensor cores with FP32
+ * 128 with SiLU -> one output per flavour y_f, mapped to xf_f by the
+ * surrogate's target:
+ *   PDF_SURR_ASINH     xf_f = c_f sinh(y_f), trained on asinh(xf_f / c_f),
+ *                      c_f = 1e-5 max |xf_f| over the grid's knots (a signed
+ *                      logarithm: steep where xf_f changes sign);
+ *   PDF_SURR_ENVELOPE  xf_f = E_f(x) y_f, trained on xf_f / E_f(x), with
+ *                      E_f(x_i) = max over the Q knots of |xf_f(x_i, Q)| (at
+ *                      least c_f), ln E_f linear in ln x between x knots and
+ *                      tabulated at 1025 equal steps of ln x over the grid
+ *                      (the network then learns an O(1) function, smooth
+ *                      through the zeros of xf_f).
+ * Products run on BF16 tensor cores with FP32
  * accumulation; BF16 weight copies are made from FP32 master weights.
  * The parameter vector is flat FP32: W1 [128][32], b1 [128], W2..W4
  * [128][128], b2..b4 [128], W5 [nflav][128], b5 [nflav] (W as [out][in]).
@@ -36,11 +45,17 @@ typedef struct {
   int warmup;               /* warm-up steps                                     */
 } pdf_train_config;
 
+#define PDF_SURR_ASINH 0
+#define PDF_SURR_ENVELOPE 1
+
 /* Make a surrogate for `grid` from HOST parameters (flat FP32, see above)
  * and HOST frequencies freq[16][2]; scratch for batches of up to max_batch
- * points is allocated here.  Synchronous. */
+ * points is allocated here.  pdf_surrogate_create uses PDF_SURR_ASINH;
+ * _ex takes the target (PDF_ERR_ARG if unknown).  Synchronous. */
 PDF_API int pdf_surrogate_create(const pdf_grid *grid, const float *params, const float *freq, int max_batch,
                                  pdf_surrogate **out);
+PDF_API int pdf_surrogate_create_ex(const pdf_grid *grid, const float *params, const float *freq, int max_batch,
+                                    int target, pdf_surrogate **out);
 PDF_API int pdf_surrogate_free(pdf_surrogate *s);
 PDF_API int pdf_surrogate_nparams(const pdf_surrogate *s, size_t *n);
 /* Copy the FP32 master parameters to / from HOST memory (synchronous). */
@@ -49,7 +64,8 @@ PDF_API int pdf_surrogate_set_params(pdf_surrogate *s, const float *params);
 
 /* One forward and backward pass on n <= max_batch points with given target
  * values xf [n][nflav] (FP64): *loss (HOST) is the mean-square error of the
- * asinh targets, grad (HOST, nparams FP32) its gradient.  Synchronous. */
+ * targets (asinh or envelope-scaled, by the surrogate's target), grad (HOST,
+ * nparams FP32) its gradient.  Synchronous. */
 PDF_API int pdf_surrogate_loss_grad(pdf_surrogate *s, const double *x, const double *q2, const double *xf,
                                     size_t n, double *loss, float *grad);
 

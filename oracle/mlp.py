@@ -11,9 +11,12 @@ all flavours:
   a_j = pi (F[j,0] z_0 + F[j,1] z_1),  phi = [sin a_0..15, cos a_0..15]   (32 features)
   h1  = silu(W1 phi + b1), h2..h4 = silu(W h + b)   (width 128)
   y   = W5 h4 + b5                                    (one output per flavour)
-  xf_f = c_f sinh(y_f)     (inverse of the training target y_f = asinh(xf_f / c_f))
+  xf_f = c_f sinh(y_f)     (inverse of the training target y_f = asinh(xf_f / c_f)),
+  or, with the envelope target, xf_f = E_f(x) y_f (target xf_f / E_f(x)), where
+  E_f(x_i) = max over the Q knots of |xf_f(x_i, Q)| (at least c_f) and ln E_f is
+  linear in ln x between knots, tabulated at ENV_N + 1 equal steps of ln x.
 silu(v) = v sigmoid(v) = v (1 + tanh(v/2)) / 2.
-Training loss: mean over batch and flavours of (y - asinh(xf/c))^2.
+Training loss: mean over batch and flavours of (y - target)^2.
 
 With bf16=True the oracle rounds to bfloat16 exactly where the GPU keeps
 bfloat16 values (weights, features, activations, and the backward signals
@@ -25,6 +28,7 @@ import numpy as np
 
 WIDTH = 128
 NFEAT = 16  # frequencies; features = 2 * NFEAT
+ENV_N = 1024  # envelope table intervals
 
 
 def bf16(a):
@@ -85,16 +89,37 @@ def forward(params, x, q2, freq, bounds, nflav, bf=False):
     return y, cache
 
 
-def target(xf, scale):
-    return np.arcsinh(np.asarray(xf) / scale)
+def target(xf, scale, env=None):
+    return np.asarray(xf) / env if env is not None else np.arcsinh(np.asarray(xf) / scale)
 
 
-def loss_grad(params, x, q2, xf, scale, freq, bounds, nflav, bf=False):
-    """Mean-square loss on asinh targets and its gradient (flat, FP64)."""
+def envelope_table(x_knots, values, bounds):
+    """ln E_f at ENV_N + 1 equal steps of ln x over [bounds[0], bounds[1]]: [nflav][ENV_N + 1]."""
+    v = np.abs(np.asarray(values, dtype=np.float64))  # [rows][nx][nflav]
+    m = v.reshape(-1, v.shape[2]).max(axis=0)
+    floor = 1e-5 * np.where(m > 0, m, 1.0)
+    E = np.maximum(v.max(axis=0), floor)  # [nx][nflav]
+    lxt = bounds[0] + (bounds[1] - bounds[0]) * np.arange(ENV_N + 1) / ENV_N
+    lx = np.log(np.asarray(x_knots, dtype=np.float64))
+    return np.stack([np.interp(lxt, lx, np.log(E[:, f])) for f in range(E.shape[1])])
+
+
+def envelope(table, x, bounds):
+    """E_f(x) for every point and flavour: [n][nflav]."""
+    z0 = 2.0 * (np.log(x) - bounds[0]) / (bounds[1] - bounds[0]) - 1.0
+    u = np.clip((z0 + 1.0) * 0.5 * ENV_N, 0.0, ENV_N)
+    k = np.minimum(np.floor(u).astype(int), ENV_N - 1)
+    a, b = table[:, k], table[:, k + 1]
+    return np.exp(a + (u - k) * (b - a)).T
+
+
+def loss_grad(params, x, q2, xf, scale, freq, bounds, nflav, bf=False, env=None):
+    """Mean-square loss on the targets (asinh, or xf / E with env = E [n][nflav])
+    and its gradient (flat, FP64)."""
     layers = unpack(params, nflav)
     r = bf16 if bf else (lambda t: t)
     y, c = forward(params, x, q2, freq, bounds, nflav, bf)
-    t = target(xf, scale)
+    t = target(xf, scale, env)
     n = y.shape[0]
     diff = y - t
     loss = float(np.mean(diff * diff))
@@ -111,6 +136,6 @@ def loss_grad(params, x, q2, xf, scale, freq, bounds, nflav, bf=False):
     return loss, flat
 
 
-def predict(params, x, q2, scale, freq, bounds, nflav, bf=False):
+def predict(params, x, q2, scale, freq, bounds, nflav, bf=False, env=None):
     y, _ = forward(params, x, q2, freq, bounds, nflav, bf)
-    return scale * np.sinh(y)
+    return env * y if env is not None else scale * np.sinh(y)

@@ -75,6 +75,7 @@ SIGNATURES = {
     "pdf_last_error": (ctypes.c_char_p, []),
     "pdf_probe_fma_rate": (I32, [I32, I32, ctypes.POINTER(ctypes.c_double)]),
     "pdf_surrogate_create": (I32, [P, P, P, I32, ctypes.POINTER(P)]),
+    "pdf_surrogate_create_ex": (I32, [P, P, P, I32, I32, ctypes.POINTER(P)]),
     "pdf_surrogate_free": (I32, [P]),
     "pdf_surrogate_nparams": (I32, [P, ctypes.POINTER(SZ)]),
     "pdf_surrogate_get_params": (I32, [P, P]),

@@ -7,7 +7,10 @@
 //   a_j = pi (F[j][0] z0 + F[j][1] z1), features [sin a_0..15 | cos a_0..15] (32, BF16)
 //   h_l = silu(W_l h_{l-1} + b_l), width 128, four layers (BF16 activations)
 //   y   = W_5 h_4 + b_5 (FP32), one output per flavour
-//   xf_f = c_f sinh(y_f); training target y_f = asinh(xf_f / c_f), c_f = 1e-5 max|xf_f|
+//   target PDF_SURR_ASINH:    xf_f = c_f sinh(y_f), trained on y_f = asinh(xf_f / c_f),
+//                             c_f = 1e-5 max|xf_f| (a signed logarithm);
+//   target PDF_SURR_ENVELOPE: xf_f = E_f(x) y_f, trained on y_f = xf_f / E_f(x), with
+//                             E_f the per-flavour envelope of |xf_f| over Q (see env_table)
 // silu(v) = v (1 + tanh(v/2)) / 2 with the hardware tanh approximation.
 // Weights are FP32 masters (Adam) with BF16 copies for the products.
 //
@@ -37,6 +40,7 @@ constexpr int SNQ = 16;   // Fourier frequencies
 constexpr int SIN = 32;   // features
 constexpr int SOUT = 16;  // outputs, padded
 constexpr int MAPN = 64;  // error-map tiles per axis
+constexpr int ENVN = 1024;  // envelope table intervals over [lx_lo, lx_hi]
 constexpr float kPi = 3.14159265358979f;
 
 struct SurrConst {
@@ -44,6 +48,8 @@ struct SurrConst {
   float lx_lo, inv_lx, lq_lo, inv_lq;  // z = 2 (l - lo) inv - 1
   float scale[SOUT];
   int nf;
+  int target;          // PDF_SURR_ASINH or PDF_SURR_ENVELOPE
+  const float *envt;   // [nf][ENVN + 1] ln E_f at lx_lo + k (lx_hi - lx_lo) / ENVN
 };
 
 // parameter offsets in the flat FP32 vector
@@ -82,6 +88,18 @@ __device__ __forceinline__ float dsilu_f(float v) {
 __device__ __forceinline__ void point_z(const SurrConst &c, double x, double q2, float &z0, float &z1) {
   z0 = 2.f * (logf((float)x) - c.lx_lo) * c.inv_lx - 1.f;
   z1 = 2.f * (logf((float)q2) - c.lq_lo) * c.inv_lq - 1.f;
+}
+
+// E_f at a point of scaled coordinate z0 (ln E linear between table points)
+__device__ __forceinline__ float envelope(const SurrConst &c, float z0, int f) {
+  const float u = fminf(fmaxf((z0 + 1.f) * (0.5f * ENVN), 0.f), (float)ENVN);
+  const int k = min((int)u, ENVN - 1);
+  const float *t = c.envt + f * (ENVN + 1) + k;
+  const float a = __ldg(t), b = __ldg(t + 1);
+  return expf(a + (u - (float)k) * (b - a));
+}
+__device__ __forceinline__ float output_of(const SurrConst &c, float y, float z0, int f) {
+  return c.target == PDF_SURR_ENVELOPE ? envelope(c, z0, f) * y : c.scale[f] * sinhf(y);
 }
 
 // feature k (0..31) of a point
@@ -276,12 +294,20 @@ __global__ void k_cast(CastArgs a) {
   a.w[i] = __float2bfloat16_rn(v);
 }
 
-// training targets y = asinh(xf / c) as FP32 [n][16]
-__global__ void k_targets(const double *xf, int n, int nf, const float *scale, float *t) {
+// training targets as FP32 [n][16]: asinh(xf / c), or xf / E(x)
+__global__ void k_targets(SurrConst c, const double *x, const double *q2, const double *xf, int n, float *t) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n * SOUT) return;
   int p = i / SOUT, f = i % SOUT;
-  t[i] = f < nf ? (float)asinh(xf[(size_t)p * nf + f] / (double)scale[f]) : 0.f;
+  if (f >= c.nf) { t[i] = 0.f; return; }
+  const double v = xf[(size_t)p * c.nf + f];
+  if (c.target == PDF_SURR_ENVELOPE) {
+    float z0, z1;
+    point_z(c, x[p], q2[p], z0, z1);
+    t[i] = (float)(v / (double)envelope(c, z0, f));
+  } else {
+    t[i] = (float)asinh(v / (double)c.scale[f]);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -400,7 +426,7 @@ k_infer(SurrConst c, const bf16 *__restrict__ wg, const float *__restrict__ para
       for (int e = 0; e < 4; e++) {
         const int h = e >> 1, f = 8 * j + 2 * tig + (e & 1);
         if (!use[h] || f >= c.nf) continue;
-        const float v = c.scale[f] * sinhf(y[j][e] + bs[4 * SW + f]);
+        const float v = output_of(c, y[j][e] + bs[4 * SW + f], z0[h], f);
         if (outf) outf[pr[h] * c.nf + f] = v;
         if (outd) outd[pr[h] * c.nf + f] = (double)v;
       }
@@ -570,7 +596,7 @@ int features_targets(pdf_surrogate *s, const pdf_grid *grid, const double *x, co
     if (rc) return rc;
     xf = s->xfbuf;
   }
-  k_targets<<<(B * SOUT + 255) / 256, 256, 0, st>>>(xf, B, s->nf, s->scale_d, s->t);
+  k_targets<<<(B * SOUT + 255) / 256, 256, 0, st>>>(s->c, x, q2, xf, B, s->t);
   return check_launch("surrogate features/targets");
 }
 
@@ -578,10 +604,12 @@ int features_targets(pdf_surrogate *s, const pdf_grid *grid, const double *x, co
 
 using namespace pdfgb;
 
-extern "C" int pdf_surrogate_create(const pdf_grid *grid, const float *params, const float *freq, int max_batch,
-                                    pdf_surrogate **out) {
+extern "C" int pdf_surrogate_create_ex(const pdf_grid *grid, const float *params, const float *freq, int max_batch,
+                                       int target, pdf_surrogate **out) {
   if (!grid || !params || !freq || !out) return set_error(PDF_ERR_NULL, "pdf_surrogate_create: NULL argument");
   *out = nullptr;
+  if (target != PDF_SURR_ASINH && target != PDF_SURR_ENVELOPE)
+    return set_error(PDF_ERR_ARG, "pdf_surrogate_create: unknown target %d", target);
   const int nf = grid->v.nf;
   if (nf > SOUT) return set_error(PDF_ERR_ARG, "pdf_surrogate_create: at most %d flavours", SOUT);
   if (max_batch < 16 || max_batch > (1 << 22))
@@ -606,6 +634,31 @@ extern "C" int pdf_surrogate_create(const pdf_grid *grid, const float *params, c
     s->c.scale[f] = (float)(1e-5 * (m > 0.0 ? m : 1.0));
   }
   double lxlo = log(v.x0), lxhi = log(v.xlast), lqlo = log(v.q2min), lqhi = log(v.q2max);
+  // envelope table: E_f(x_i) = max over Q rows of |xf_f(x_i, Q)| (at least c_f),
+  // ln E_f linear in ln x between knots, sampled at ENVN + 1 equal steps
+  std::vector<double> xk(v.nx);
+  rc = cuda_err(cudaMemcpy(xk.data(), v.xk, v.nx * sizeof(double), cudaMemcpyDeviceToHost), "pdf_surrogate_create");
+  if (rc) { delete s; return rc; }
+  std::vector<float> envt((size_t)nf * (ENVN + 1));
+  {
+    std::vector<double> lx(v.nx), le(v.nx);
+    for (int i = 0; i < v.nx; i++) lx[i] = log(xk[i]);
+    for (int f = 0; f < nf; f++) {
+      for (int i = 0; i < v.nx; i++) {
+        double m = 0.0;
+        for (int j = 0; j < v.nrows; j++) m = fmax(m, fabs(vals[((size_t)j * v.nx + i) * nf + f]));
+        le[i] = log(fmax(m, (double)s->c.scale[f]));
+      }
+      for (int k = 0; k <= ENVN; k++) {
+        const double l = lxlo + (lxhi - lxlo) * k / ENVN;
+        int i = 0;
+        while (i + 2 < v.nx && lx[i + 1] <= l) i++;
+        const double t = fmin(fmax((l - lx[i]) / (lx[i + 1] - lx[i]), 0.0), 1.0);
+        envt[(size_t)f * (ENVN + 1) + k] = (float)(le[i] + t * (le[i + 1] - le[i]));
+      }
+    }
+  }
+  s->c.target = target;
   s->c.lx_lo = (float)lxlo; s->c.inv_lx = (float)(1.0 / (lxhi - lxlo));
   s->c.lq_lo = (float)lqlo; s->c.inv_lq = (float)(1.0 / (lqhi - lqlo));
   for (int j = 0; j < SNQ; j++) { s->c.freq[j][0] = freq[2 * j]; s->c.freq[j][1] = freq[2 * j + 1]; }
@@ -616,6 +669,8 @@ extern "C" int pdf_surrogate_create(const pdf_grid *grid, const float *params, c
   if (!rc) rc = s->alloc(&s->am, P);
   if (!rc) rc = s->alloc(&s->av, P);
   if (!rc) rc = s->alloc(&s->scale_d, SOUT);
+  float *envt_d = nullptr;
+  if (!rc) rc = s->alloc(&envt_d, envt.size());
   if (!rc) rc = s->alloc(&s->wbf, kWbfTotal);
   if (!rc) rc = s->alloc(&s->h[0], B * SIN);
   for (int l = 1; l < 5 && !rc; l++) rc = s->alloc(&s->h[l], B * SW);
@@ -633,6 +688,8 @@ extern "C" int pdf_surrogate_create(const pdf_grid *grid, const float *params, c
   if (rc) { pdf_surrogate_free(s); return rc; }
   cudaMemcpy(s->params, params, P * sizeof(float), cudaMemcpyHostToDevice);
   cudaMemcpy(s->scale_d, s->c.scale, SOUT * sizeof(float), cudaMemcpyHostToDevice);
+  cudaMemcpy(envt_d, envt.data(), envt.size() * sizeof(float), cudaMemcpyHostToDevice);
+  s->c.envt = envt_d;
   cudaMemset(s->am, 0, P * sizeof(float));
   cudaMemset(s->av, 0, P * sizeof(float));
   cudaMemset(s->mask, 0, MAPN * MAPN);
@@ -641,6 +698,11 @@ extern "C" int pdf_surrogate_create(const pdf_grid *grid, const float *params, c
   if (rc) { pdf_surrogate_free(s); return rc; }
   *out = s;
   return PDF_OK;
+}
+
+extern "C" int pdf_surrogate_create(const pdf_grid *grid, const float *params, const float *freq, int max_batch,
+                                    pdf_surrogate **out) {
+  return pdf_surrogate_create_ex(grid, params, freq, max_batch, PDF_SURR_ASINH, out);
 }
 
 extern "C" int pdf_surrogate_free(pdf_surrogate *s) {

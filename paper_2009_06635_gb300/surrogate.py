@@ -18,7 +18,10 @@ from .pdf import Grid, _dev_ptr, _stream_handle
 
 
 class Surrogate:
-    def __init__(self, grid: Grid, params=None, freq=None, max_batch: int = 16384, seed: int = 9):
+    TARGETS = {"asinh": 0, "envelope": 1}  # PDF_SURR_ASINH, PDF_SURR_ENVELOPE
+
+    def __init__(self, grid: Grid, params=None, freq=None, max_batch: int = 16384, seed: int = 9,
+                 target: str = "asinh"):
         if params is None or freq is None:
             p0, f0 = synthetic.surrogate_init(grid.nflav, seed)
             params = p0 if params is None else params
@@ -27,8 +30,10 @@ class Surrogate:
         f = np.ascontiguousarray(freq, dtype=np.float32)
         h = ctypes.c_void_p(None)
         with torch.cuda.device(grid.device):
-            check(_native.load().pdf_surrogate_create(grid.handle, p.ctypes.data, f.ctypes.data, int(max_batch),
-                                                      ctypes.byref(h)), "pdf_surrogate_create")
+            check(_native.load().pdf_surrogate_create_ex(grid.handle, p.ctypes.data, f.ctypes.data, int(max_batch),
+                                                         self.TARGETS[target], ctypes.byref(h)),
+                  "pdf_surrogate_create")
+        self.target = target
         self._h = h
         self.nflav = grid.nflav
         self.max_batch = max_batch

@@ -99,3 +99,22 @@ def test_prediction_inverts_the_target_map():
     p0 = params.copy()
     p0[-(NF * mlp.WIDTH + NF):] = 0.0
     assert np.array_equal(mlp.predict(p0, x, q2, scale, freq, bounds, NF), np.zeros((len(x), NF)))
+
+
+def test_envelope_reproduces_power_laws_and_the_floor():
+    # |xf| maximal over Q = 2 x^-0.3 (1 + 0.1 * row): a power law in x, so
+    # ln E is linear in ln x and the tabulated envelope is exact everywhere
+    xk = np.geomspace(1e-6, 1.0, 37)
+    rows = 5
+    vals = np.zeros((rows, len(xk), 3))
+    for j in range(rows):
+        vals[j, :, 0] = 2.0 * xk ** -0.3 * (1 + 0.1 * j) / 1.4  # largest at the top row: 2 x^-0.3
+        vals[j, :, 1] = -(0.5 + j) * xk ** 0.7                    # sign does not matter: 4.5 x^0.7
+    bounds = (np.log(1e-6), 0.0, 0.0, 1.0)
+    T = mlp.envelope_table(xk, vals, bounds)
+    x = np.exp(np.random.default_rng(8).uniform(np.log(1e-6), 0.0, 1000))
+    E = mlp.envelope(T, x, bounds)
+    assert np.allclose(E[:, 0], 2.0 * x ** -0.3, rtol=1e-12)
+    assert np.allclose(E[:, 1], 4.5 * x ** 0.7, rtol=1e-12)
+    assert np.allclose(E[:, 2], 1e-5, rtol=1e-12)  # an all-zero flavour sits on the floor
+
