@@ -208,14 +208,16 @@ __global__ void k_coef(Stage S) {
     }
   }
   double *o = S.coef + (size_t)gid * 16;
-  float *o32 = S.coef32 + (size_t)gid * 16;
+  // FP32 copy row-major by control-point row, then flavour: [cell][l][f][4], so
+  // one load instruction over the flavours of a point reads consecutive rows
+  float *o32 = S.coef32 + (size_t)(gid / S.nf) * 16 * S.nf + (size_t)f * 4;
   // float-float copy flavour-minor, [cell][m][flavour]: the lanes of one load
   // (consecutive flavours of a point) read consecutive words
   float2 *off = S.coefff + (size_t)(gid / S.nf) * 16 * S.nf + f;
   bool bad = false;
   for (int m = 0; m < 16; m++) {
     o[m] = c[m];
-    o32[m] = (float)c[m];
+    o32[(size_t)(m >> 2) * 4 * S.nf + (m & 3)] = (float)c[m];
     // float-float split: hi = round(c), lo = round(c - hi); exact to 2^-48 of c
     // while |c| stays well inside the float exponent range
     float hi = __double2float_rn(c[m]);

@@ -9,6 +9,9 @@
 //          block (FP64) or 64 bytes (FP32), instead of gathering 16 knots;
 //          the Bernstein weights are non-negative and sum to one, so the
 //          evaluation has no cancellation beyond that of the data.
+//   coef32 the same control points rounded to FP32, [nqc+1][nx][4][nflav][4]
+//          (row l = 0..3 of every flavour, then the next row), so one load
+//          instruction over the flavours of a point reads consecutive rows.
 //   coefff the same control points as float-float pairs (hi, lo), laid out
 //          [nqc+1][nx][16][nflav] so that one load instruction over the
 //          flavours of a point reads consecutive words.
@@ -68,7 +71,7 @@ struct GridView {
   const int *qc_row;          // [nqc + 1] first row of each Q cell
   double *vals;               // [nrows][nx][nf] device copy of the knot values
   const double *coef;         // [nqc + 1][nx][nf][16]
-  const float *coef32;
+  const float *coef32;        // [nqc + 1][nx][4][nf][4]: row l of every flavour, then the next row
   const float2 *coefff;       // [nqc + 1][nx][16][nf] float-float (hi, lo) copy of coef
   int ff;                     // 1 if every control point is safe for float-float
   int nmem;                   // members (replicas) sharing the knots; member m's

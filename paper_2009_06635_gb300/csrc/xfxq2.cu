@@ -3,14 +3,14 @@
 //
 // One warp owns a tile of 32 query points (16 events in the Monte Carlo
 // layout).  Phase 1 (lane = point): read x and Q^2 (coalesced), classify
-// against the grid edges, search the cells on the raw bit patterns (knots in
-// shared memory), and record the Bernstein weights of the patch sites and the
-// continuation parameters of the point.  Phase 2, per point (warp-uniform,
-// so classes never diverge): in-grid points spread (column, row pair) over
-// the lanes, one float4 pair of control points each and one shuffle per
-// evaluation; continuation points use four lanes per item, each loading one
-// float4 row of control points, reduced with two shuffles.  The FP32 path is
-// bound by the L1/L2 gather, not arithmetic.
+// against the grid edges with exact float thresholds, search the cells on the
+// raw bit patterns (knots in shared memory), record the Bernstein weights of
+// the patch sites (one slot-major row per point) and the continuation
+// parameters; points are ordered by class so that lanes of one instruction
+// take the same branch.  Phase 2 (lane = item (point, column), consecutive
+// items are consecutive outputs): one lane evaluates a whole item, four
+// float4 rows of the cell's control points against weights read as two
+// 16-byte shared loads, so one instruction covers 32 items.
 #include <cmath>
 #include <type_traits>
 
@@ -21,92 +21,74 @@ namespace pdfgb {
 constexpr int kWarps = 8;
 constexpr int kThreads = 32 * kWarps;
 
-// Per-warp record of the points of one tile, indexed by class-sorted slot.
-// W holds, per slot, Bx0 | Bx1 | Bq0 | Bq1.
-template <typename T>
-struct WarpRec {
-  int cls[32], orig[32], xc0[32], xc1[32], qc0[32], qc1[32];
-  int off4[32];  // FP32 in-grid points: float4 offset of the cell's first flavour block
-  T W[16][33];  // padded: rows of one slot fall in different banks
-  T px[32], pq[32], lr[32], as[32];
+// Per-warp record of the points of one tile, by class-sorted slot.  Row W[s]
+// holds Bx0 | Bx1 | Bq0 | Bq1 (16 floats), padded to 80 bytes so that the few
+// slots one load instruction touches fall in different banks (and stay
+// 16-byte aligned).
+struct alignas(16) Rec32 {
+  int cls[32], xc0[32], xc1[32], qc0[32], qc1[32];
+  long long ob[32];  // output offset of the point's first column
+  float W[32][20];
+  float px[32], pq[32], lr[32];
 };
 
-// ---- FP32 evaluation -------------------------------------------------------
-// One lane, whole patch: sum_l Bq[l] sum_k Bx[k] b[l][k] (four float4 rows),
-// rounded in the same order as the four-lane version ((p0 + p1) + (p2 + p3)),
-// so one flavour alone and all flavours give identical bits.
-__device__ __forceinline__ float site32_full(const float *c, const WarpRec<float> &R, int p, int a, int b) {
-  const float4 *q = reinterpret_cast<const float4 *>(c);
+// One site: sum_l Bq_b[l] (sum_k Bx_a[k] b[l][k]), rounded as
+// (p0 + p1) + (p2 + p3) with p_l = Bq_b[l] * (the row's dot product).
+// q: the item's first row; rows are nf float4 apart.
+__device__ __forceinline__ float site32(const float4 *q, int nf, const float *w, int a, int b) {
+  const float4 bx = *reinterpret_cast<const float4 *>(w + 4 * a);
+  const float4 bq = *reinterpret_cast<const float4 *>(w + 8 + 4 * b);
+  const float bqv[4] = {bq.x, bq.y, bq.z, bq.w};
   float pl[4];
 #pragma unroll
   for (int l = 0; l < 4; l++) {
-    float4 v = __ldg(q + l);
-    float rr = R.W[4 * a][p] * v.x;
-    rr = fmaf(R.W[4 * a + 1][p], v.y, rr);
-    rr = fmaf(R.W[4 * a + 2][p], v.z, rr);
-    rr = fmaf(R.W[4 * a + 3][p], v.w, rr);
-    pl[l] = __fmul_rn(rr, R.W[8 + 4 * b + l][p]);
+    const float4 v = __ldg(q + (size_t)l * nf);
+    float rr = bx.x * v.x;
+    rr = fmaf(bx.y, v.y, rr);
+    rr = fmaf(bx.z, v.z, rr);
+    rr = fmaf(bx.w, v.w, rr);
+    pl[l] = __fmul_rn(rr, bqv[l]);
   }
   return (pl[0] + pl[1]) + (pl[2] + pl[3]);
 }
 
-__device__ __forceinline__ float eval_point32(const GridView &g, const WarpRec<float> &R, int p, int col) {
-  const float *cb = g.coef32 + (size_t)col * 16;
-  const size_t stride = (size_t)g.nf * 16;
+// One item: column col of the point in slot p (the same arithmetic for every
+// column count, so one flavour alone and all flavours give identical bits).
+__device__ __forceinline__ float eval_item32(const GridView &g, const Rec32 &R, int p, int col) {
+  const float4 *cb = reinterpret_cast<const float4 *>(g.coef32) + col;
+  const size_t stride = (size_t)g.nf * 4;  // float4 per cell
+  const float *w = R.W[p];
   auto F = [&](int a, int b) {
     int xc = a ? R.xc1[p] : R.xc0[p];
     int qc = b ? R.qc1[p] : R.qc0[p];
-    return site32_full(cb + ((size_t)qc * g.nx + xc) * stride, R, p, a, b);
+    return site32(cb + ((size_t)qc * g.nx + xc) * stride, g.nf, w, a, b);
   };
   return combine<float>(R.cls[p], R.px[p], R.pq[p], R.lr[p], g.ln101_32, F);
 }
 
-// Four lanes per item, lane r owns row l = r of the control points.
-__device__ __forceinline__ float site32(const float *c, const WarpRec<float> &R, int p, int a, int b,
-                                        int r, unsigned gm) {
-  float4 v = __ldg(reinterpret_cast<const float4 *>(c) + r);
-  float part = R.W[4 * a][p] * v.x;
-  part = fmaf(R.W[4 * a + 1][p], v.y, part);
-  part = fmaf(R.W[4 * a + 2][p], v.z, part);
-  part = fmaf(R.W[4 * a + 3][p], v.w, part);
-  part = __fmul_rn(part, R.W[8 + 4 * b + r][p]);
-  part += __shfl_xor_sync(gm, part, 1);
-  part += __shfl_xor_sync(gm, part, 2);
-  return part;
-}
-
-__device__ __forceinline__ float eval_item32(const GridView &g, const WarpRec<float> &R, int p, int col,
-                                             int r, unsigned gm) {
-  const float *cb = g.coef32 + (size_t)col * 16;
-  const size_t stride = (size_t)g.nf * 16;
-  auto F = [&](int a, int b) {
-    int xc = a ? R.xc1[p] : R.xc0[p];
-    int qc = b ? R.qc1[p] : R.qc0[p];
-    return site32(cb + ((size_t)qc * g.nx + xc) * stride, R, p, a, b, r, gm);
-  };
-  return combine<float>(R.cls[p], R.px[p], R.pq[p], R.lr[p], g.ln101_32, F);
-}
-
-// Write the Bernstein weights of a point's sites into its record slot.
-__device__ __forceinline__ void store_weights(WarpRec<float> &R, int slot, const PointSites<float> &ps) {
+// Write a point into its record slot.
+__device__ __forceinline__ void store_point32(Rec32 &R, int slot, const PointSites<float> &ps, long long ob) {
+  R.cls[slot] = ps.cls;
+  R.xc0[slot] = ps.xc0; R.xc1[slot] = ps.xc1; R.qc0[slot] = ps.qc0; R.qc1[slot] = ps.qc1;
+  R.ob[slot] = ob;
+  R.px[slot] = ps.px; R.pq[slot] = ps.pq; R.lr[slot] = ps.lr;
+  if (ps.cls == C_INVALID) return;
   float bx0[4], bx1[4], bq0[4], bq1[4];
   bernstein<float>(ps.t0, ps.ts0, bx0);
   bernstein<float>(ps.t1, 1.f - ps.t1, bx1);
   bernstein<float>(ps.u0, ps.us0, bq0);
   bernstein<float>(ps.u1, 1.f - ps.u1, bq1);
-#pragma unroll
-  for (int k = 0; k < 4; k++) {
-    R.W[k][slot] = bx0[k];
-    R.W[4 + k][slot] = bx1[k];
-    R.W[8 + k][slot] = bq0[k];
-    R.W[12 + k][slot] = bq1[k];
-  }
+  float4 *row = reinterpret_cast<float4 *>(R.W[slot]);
+  row[0] = make_float4(bx0[0], bx0[1], bx0[2], bx0[3]);
+  row[1] = make_float4(bx1[0], bx1[1], bx1[2], bx1[3]);
+  row[2] = make_float4(bq0[0], bq0[1], bq0[2], bq0[3]);
+  row[3] = make_float4(bq1[0], bq1[1], bq1[2], bq1[3]);
 }
 
 // MODE_POINTS: points xa[n], qa[n]; out[n][ncol] for columns col0..col0+ncol-1.
 // MODE_MC:     events xa[n] (x1), xb[n] (x2), Q^2 = x1 x2 s; out[n][2 nf + 1].
 template <int MODE>
-__global__ void __launch_bounds__(kThreads, 4)
+__global__ void __launch_bounds__(kThreads, 3)
 k_xf32(GridView g, const float *__restrict__ xa, const float *__restrict__ qa, const float *__restrict__ xb,
        float s, long long n, int col0, int ncol, float *__restrict__ out) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -114,20 +96,21 @@ k_xf32(GridView g, const float *__restrict__ xa, const float *__restrict__ qa, c
   int *qkeys = reinterpret_cast<int *>(smem + keys_bytes(g.nx, 4));
   int *akeys = reinterpret_cast<int *>(smem + keys_bytes(g.nx, 4) + keys_bytes(g.nrows, 4));
   size_t rec_off = keys_bytes(g.nx, 4) + keys_bytes(g.nrows, 4) + (MODE == MODE_MC ? keys_bytes(g.na, 4) : 0);
-  WarpRec<float> *recs = reinterpret_cast<WarpRec<float> *>(smem + rec_off);
+  Rec32 *recs = reinterpret_cast<Rec32 *>(smem + rec_off);
   load_keys<float>(g, xkeys, 0);
   load_keys<float>(g, qkeys, 1);
   if (MODE == MODE_MC) load_keys<float>(g, akeys, 2);
   __syncthreads();
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  WarpRec<float> &R = recs[warp];
+  Rec32 &R = recs[warp];
   const int per_tile = MODE == MODE_MC ? 16 : 32;
-  const int per = MODE == MODE_MC ? 2 * g.nf + 1 : ncol;  // outputs per tile unit
-  const int r = lane & 3;                                  // row of a four-lane item
-  const unsigned gm = 0xFu << (lane & ~3);
+  const int nc = MODE == MODE_MC ? g.nf : ncol;  // columns per point
+  const int cbase = MODE == MODE_MC ? 0 : col0;
   const long long ntiles = (n + per_tile - 1) / per_tile;
   const long long nwarps = (long long)gridDim.x * kWarps;
+  const unsigned lt = (1u << lane) - 1u;
+  const int dp = 32 / nc, dc = 32 - dp * nc;
 
   for (long long tile = (long long)blockIdx.x * kWarps + warp; tile < ntiles; tile += nwarps) {
     const long long e0 = tile * per_tile;
@@ -136,9 +119,11 @@ k_xf32(GridView g, const float *__restrict__ xa, const float *__restrict__ qa, c
     // ---- phase 1: lane = point ----
     bool present;
     float x = 0.f, q2 = 0.f;
+    long long ob;
     if (MODE == MODE_POINTS) {
       present = lane < ne;
       if (present) { x = xa[e0 + lane]; q2 = qa[e0 + lane]; }
+      ob = (e0 + lane) * (long long)nc;
     } else {  // events: x1 = xa, x2 = xb
       const int e = lane >> 1;
       present = e < ne;
@@ -147,63 +132,33 @@ k_xf32(GridView g, const float *__restrict__ xa, const float *__restrict__ qa, c
         q2 = x1 * x2 * s;
         x = (lane & 1) ? x2 : x1;
       }
+      ob = (e0 + e) * (long long)(2 * g.nf + 1) + (lane & 1) * g.nf;
     }
     PointSites<float> ps;
-    ps.cls = NCLASS;
+    ps.cls = -1;
     if (present) ps = sites(g, xkeys, qkeys, x, q2);
-    unsigned inv = __ballot_sync(0xffffffffu, present && ps.cls == C_INVALID);
+    unsigned inv = __ballot_sync(0xffffffffu, ps.cls == C_INVALID);
     if (lane == 0 && inv) atomicAdd(g.invalid, (unsigned long long)__popc(inv));
-
-    const int slot = lane;  // phase 2 walks the points in order: no sort needed
-    R.cls[slot] = ps.cls; R.orig[slot] = lane;
-    R.off4[slot] = ((ps.qc0 * g.nx + ps.xc0) * g.nf + col0) * 4;
-    R.xc0[slot] = ps.xc0; R.xc1[slot] = ps.xc1; R.qc0[slot] = ps.qc0; R.qc1[slot] = ps.qc1;
-    R.px[slot] = ps.px; R.pq[slot] = ps.pq; R.lr[slot] = ps.lr;
-    if (present && ps.cls != C_INVALID) store_weights(R, slot, ps);
-    if (MODE == MODE_MC && (lane & 1) == 0) R.as[lane >> 1] = present ? alphas_eval(g, akeys, q2) : 0.f;
+    if (MODE == MODE_MC && present && (lane & 1) == 0) out[ob + 2 * g.nf] = alphas_eval(g, akeys, q2);
+    // order the points by class (counting sort over the warp)
+    int slot = 0, base = 0;
+#pragma unroll
+    for (int c = 0; c < NCLASS; c++) {
+      const unsigned m = __ballot_sync(0xffffffffu, ps.cls == c);
+      if (ps.cls == c) slot = base + __popc(m & lt);
+      base += __popc(m);
+    }
+    const int np = base;
+    if (present) store_point32(R, slot, ps, ob);
     __syncwarp();
 
-    // ---- phase 2: per point, lanes over (column, row) ----
-    if (MODE == MODE_POINTS && ncol == 1) {  // one column: a lane per point
-      if (lane < ne) out[e0 + R.orig[lane]] = eval_point32(g, R, lane, col0);
-    } else {
-      const int nc = MODE == MODE_MC ? g.nf : ncol;
-      const int npts = MODE == MODE_MC ? 2 * ne : ne;
-      for (int q = 0; q < npts; q++) {  // warp-uniform: no divergence by class
-        const long long ob = MODE == MODE_POINTS ? (e0 + R.orig[q]) * (long long)ncol
-                                                 : (e0 + (q >> 1)) * (long long)per + (q & 1) * g.nf;
-        if (R.cls[q] == C_IN) {
-          // the point's column blocks are contiguous: lane k owns rows 2h, 2h+1
-          // (h = k & 1) of column k >> 1, 32 bytes at cell_base + 8 k floats
-          const float4 *cbp = reinterpret_cast<const float4 *>(g.coef32) + R.off4[q];
-          const float b0 = R.W[0][q], b1 = R.W[1][q], b2 = R.W[2][q], b3 = R.W[3][q];
-          const int hr = lane & 1;
-          const float bqa = R.W[8 + 2 * hr][q], bqb = R.W[9 + 2 * hr][q];
-          const unsigned pm = 3u << (lane & 30);
-          for (int k = lane; k < 2 * nc; k += 32) {
-            const float4 v0 = __ldg(cbp + 2 * k), v1 = __ldg(cbp + 2 * k + 1);
-            float ra = b0 * v0.x;
-            ra = fmaf(b1, v0.y, ra);
-            ra = fmaf(b2, v0.z, ra);
-            ra = fmaf(b3, v0.w, ra);
-            float rb = b0 * v1.x;
-            rb = fmaf(b1, v1.y, rb);
-            rb = fmaf(b2, v1.z, rb);
-            rb = fmaf(b3, v1.w, rb);
-            // (p0 + p1) + (p2 + p3), the order of every FP32 patch sum
-            float part = __fadd_rn(__fmul_rn(ra, bqa), __fmul_rn(rb, bqb));
-            const float other = __shfl_xor_sync(pm, part, 1);
-            if (hr == 0) out[ob + (k >> 1)] = __fadd_rn(part, other);
-          }
-        } else {
-          for (int k = lane; k < 4 * nc; k += 32) {
-            const int f = k >> 2;
-            const float v = eval_item32(g, R, q, col0 + f, r, gm);
-            if (r == 0) out[ob + f] = v;
-          }
-        }
-      }
-      if (MODE == MODE_MC && lane < ne) out[(e0 + lane) * (long long)per + 2 * g.nf] = R.as[lane];
+    // ---- phase 2: items (point, column) ----
+    int p = lane / nc, c = lane - (lane / nc) * nc;
+    for (int k = lane; k < np * nc; k += 32) {
+      out[R.ob[p] + c] = eval_item32(g, R, p, cbase + c);
+      c += dc;
+      p += dp;
+      if (c >= nc) { c -= nc; p++; }
     }
     __syncwarp();
   }
@@ -249,7 +204,7 @@ static int num_sms() {
 template <int MODE>
 static size_t xf32_smem(const GridView &g) {
   return keys_bytes(g.nx, 4) + keys_bytes(g.nrows, 4) + (MODE == MODE_MC ? keys_bytes(g.na, 4) : 0) +
-         kWarps * sizeof(WarpRec<float>);
+         kWarps * sizeof(Rec32);
 }
 
 template <int MODE>
