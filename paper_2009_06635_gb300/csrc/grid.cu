@@ -211,9 +211,10 @@ __global__ void k_coef(Stage S) {
   // FP32 copy row-major by control-point row, then flavour: [cell][l][f][4], so
   // one load instruction over the flavours of a point reads consecutive rows
   float *o32 = S.coef32 + (size_t)(gid / S.nf) * 16 * S.nf + (size_t)f * 4;
-  // float-float copy flavour-minor, [cell][m][flavour]: the lanes of one load
-  // (consecutive flavours of a point) read consecutive words
-  float2 *off = S.coefff + (size_t)(gid / S.nf) * 16 * S.nf + f;
+  // float-float copy flavour-minor by pairs of control points,
+  // [cell][m / 2][flavour][m % 2]: one 16-byte load per pair and flavour, and
+  // the lanes of one load (consecutive flavours of a point) read consecutive bytes
+  float2 *off = S.coefff + (size_t)(gid / S.nf) * 16 * S.nf + (size_t)f * 2;
   bool bad = false;
   for (int m = 0; m < 16; m++) {
     o[m] = c[m];
@@ -222,7 +223,7 @@ __global__ void k_coef(Stage S) {
     // while |c| stays well inside the float exponent range
     float hi = __double2float_rn(c[m]);
     float lo = __double2float_rn(c[m] - (double)hi);
-    off[(size_t)m * S.nf] = make_float2(hi, lo);
+    off[(size_t)(m >> 1) * 2 * S.nf + (m & 1)] = make_float2(hi, lo);
     double a = fabs(c[m]);
     if (a != 0.0 && (a < 1e-30 || a > 1e30)) bad = true;
   }

@@ -13,8 +13,9 @@
 //          (row l = 0..3 of every flavour, then the next row), so one load
 //          instruction over the flavours of a point reads consecutive rows.
 //   coefff the same control points as float-float pairs (hi, lo), laid out
-//          [nqc+1][nx][16][nflav] so that one load instruction over the
-//          flavours of a point reads consecutive words.
+//          [nqc+1][nx][8][nflav][2] (pairs of control points m, m+1 of a
+//          flavour adjacent): one 16-byte load per pair, and one load
+//          instruction over the flavours of a point reads consecutive bytes.
 //   xk/q2k raw knots, searched as integer bit patterns (positive doubles
 //          order like their bits), so a cell choice never depends on a log.
 //   xcell  per x cell {ln x_i, 1/d, ln x_{i+1}, 0}, d = ln x_{i+1} - ln x_i;
@@ -72,7 +73,7 @@ struct GridView {
   double *vals;               // [nrows][nx][nf] device copy of the knot values
   const double *coef;         // [nqc + 1][nx][nf][16]
   const float *coef32;        // [nqc + 1][nx][4][nf][4]: row l of every flavour, then the next row
-  const float2 *coefff;       // [nqc + 1][nx][16][nf] float-float (hi, lo) copy of coef
+  const float2 *coefff;       // [nqc + 1][nx][8][nf][2] float-float (hi, lo) copy of coef
   int ff;                     // 1 if every control point is safe for float-float
   int nmem;                   // members (replicas) sharing the knots; member m's
   size_t mstride;             // control points start m * mstride elements further

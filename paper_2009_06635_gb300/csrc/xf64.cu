@@ -86,21 +86,22 @@ __device__ __forceinline__ double f2d(float f) {
   return (double)f;
 }
 // sum_m w_m b_m with w (hi, lo) from the record and b (hi, lo) from the
-// float-float control points (stride nf between consecutive m): exact
-// products, TwoSum accumulation, the cross terms and the rounding errors
-// gathered in a second float.
-__device__ __forceinline__ double dot_ff16(const float2 *c, int nf, const float2 *w) {
+// float-float control points (c: the item's first pair; pairs of control
+// points nf float4 apart): exact products, TwoSum accumulation, the cross
+// terms and the rounding errors gathered in a second float.
+__device__ __forceinline__ double dot_ff16(const float4 *c, int nf, const float2 *w) {
   float sh = 0.f, sl = 0.f;
 #pragma unroll
   for (int m2 = 0; m2 < 8; m2++) {
     const float4 ww = *reinterpret_cast<const float4 *>(w + 2 * m2);
+    const float4 bb = __ldg(c + (size_t)m2 * nf);
 #pragma unroll
     for (int half = 0; half < 2; half++) {
-      const float2 b = __ldg(c + (size_t)(2 * m2 + half) * nf);
+      const float bh = half ? bb.z : bb.x, bl = half ? bb.w : bb.y;
       const float wh = half ? ww.z : ww.x, wl = half ? ww.w : ww.y;
-      const float ph = __fmul_rn(wh, b.x);
-      float pe = __fmaf_rn(wh, b.x, -ph);
-      pe = __fmaf_rn(wh, b.y, __fmaf_rn(wl, b.x, pe));
+      const float ph = __fmul_rn(wh, bh);
+      float pe = __fmaf_rn(wh, bh, -ph);
+      pe = __fmaf_rn(wh, bl, __fmaf_rn(wl, bh, pe));
       const float t = __fadd_rn(sh, ph);
       const float bp = __fsub_rn(t, sh);
       const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bp)), __fsub_rn(ph, bp));
@@ -170,8 +171,9 @@ __device__ __forceinline__ double eval_item64(const GridView &g, const Rec64 &R,
   };
   const int cls = R.cls[p];
   if (cls == C_INF)
-    return dot_ff16(g.coefff + moff + ((size_t)R.qc0[p] * g.nx + R.xc0[p]) * 16 * g.nf + col, g.nf,
-                    reinterpret_cast<const float2 *>(R.W[p]));
+    return dot_ff16(reinterpret_cast<const float4 *>(g.coefff + moff +
+                                                     ((size_t)R.qc0[p] * g.nx + R.xc0[p]) * 16 * g.nf) + col,
+                    g.nf, reinterpret_cast<const float2 *>(R.W[p]));
   if (cls == C_IN) return dot_w16(C(0, 0), R, p);
   if (cls == C_INVALID) return NAN;
   // continuation: the two values the final rule combines, then one shared rule
