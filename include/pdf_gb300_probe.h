@@ -22,6 +22,15 @@ extern "C" {
  * Synchronous; returns PDF_OK or a PDF_ERR_* code. */
 PDF_API int pdf_probe_fma_rate(int precision, int iters, double *flops_per_s);
 
+/* The evaluation kernels' own FP64 elementary functions, elementwise on n
+ * DEVICE values, for testing them against the C library: fn 0: out = ln a
+ * (table-driven, Tang's method; within 2 ulp or 2e-17 absolute); fn 1:
+ * out = e^a (within 2 ulp); fn 2: out = a / b (reciprocal approximation and
+ * Newton steps, within 2 ulp; b may be NULL otherwise).  The tables are the
+ * grid's.  Asynchronous on `stream`. */
+PDF_API int pdf_probe_math(const pdf_grid *grid, int fn, const double *a, const double *b, size_t n,
+                           double *out, cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

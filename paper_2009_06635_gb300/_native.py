@@ -57,6 +57,7 @@ SIGNATURES = {
     "xfxq2_all_flavours_alphas": (I32, [P, P, P, SZ, P, P, P]),
     "pdf_mc_integrate": (I32, [P, P, ctypes.c_ulonglong, ctypes.c_ulonglong, SZ, P, P]),
     "pdf_load_lhapdf": (I32, [ctypes.c_char_p, I32, I32, ctypes.POINTER(P)]),
+    "pdf_probe_math": (I32, [P, I32, P, P, SZ, P, P]),
     "pdf_lhapdf_read": (I32, [ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(P)]),
     "pdf_lhapdf_desc": (I32, [P, ctypes.POINTER(GridDesc)]),
     "pdf_lhapdf_free": (I32, [P]),

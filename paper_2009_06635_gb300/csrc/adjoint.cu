@@ -100,7 +100,7 @@ k_vjp(GridView g, const double *__restrict__ xa, const double *__restrict__ qa, 
   for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
     const double x = xa[p], q2 = qa[p];
     double lq;
-    PointSites<double> ps = sites(g, xkeys, qkeys, x, q2, g.tlogtab, lq);
+    PointSites<double> ps = sites(g, xkeys, qkeys, x, q2, LogTabs{g.tlogtab, g.tloghtab}, lq);
     if (ps.cls == C_INVALID) {
       if (gx) gx[p] = NAN;
       if (gq) gq[p] = NAN;

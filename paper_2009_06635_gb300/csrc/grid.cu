@@ -77,7 +77,7 @@ struct Stage {
   float *coef32, *xthr32, *q2thr32, *aq2thr32, *xcell32, *qcell32, *acell32;
   float2 *coefff;
   double2 *tlogtab;  // tang.cuh tables, filled on the host before staging
-  double *texptab;
+  double *tloghtab, *texptab;
   int *ffbad;  // set when a control point is outside the float-float range
   int *row_qc, *qc_row;
   double *scal;  // scalar outputs, see k_scalars
@@ -85,17 +85,18 @@ struct Stage {
 
 __global__ void k_logs(Stage S) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const double2 *LT = S.tlogtab;
+  const LogTabs LT{S.tlogtab, S.tloghtab};
   if (i < S.nx) { S.lx[i] = tlog(S.xk[i], LT); S.xthr32[i] = __double2float_ru(S.xk[i]); }
   if (i < S.nrows) { S.lq[i] = tlog(S.q2k[i], LT); S.q2thr32[i] = __double2float_ru(S.q2k[i]); }
   if (i < S.na) { S.alq[i] = tlog(S.aq2[i], LT); S.aq2thr32[i] = __double2float_ru(S.aq2[i]); }
 }
 
-void tang_tables(double *logtab, double *exptab) {
+void tang_tables(double *logtab, double *loghtab, double *exptab) {
   for (int j = 0; j < kLogTab; j++) {
     const double F = 1.0 + j / 256.0;
     logtab[2 * j] = 1.0 / F;
     logtab[2 * j + 1] = j == kLogTab - 1 ? kLn2 : (double)logl((long double)F);
+    loghtab[j] = (double)logl((long double)F / 2.0L);
   }
   for (int k = 0; k < kExpTab; k++) exptab[k] = (double)exp2l((long double)k / 256.0L);
 }
@@ -276,12 +277,13 @@ __global__ void k_scalars(Stage S) {
   int j = 0;  // same rule as the query search: the last row with Q^2_j <= v
   while (j + 1 < S.nrows && S.q2k[j + 1] <= v) j++;
   o[3] = (double)S.row_qc[j];
-  o[4] = (tlog(v, S.tlogtab) - S.qcell[4 * j]) * S.qcell[4 * j + 1];
+  const LogTabs LT{S.tlogtab, S.tloghtab};
+  o[4] = (tlog(v, LT) - S.qcell[4 * j]) * S.qcell[4 * j + 1];
   o[5] = S.xcell[0];
   o[6] = S.xcell[1];
   o[7] = S.lq[S.nrows - 1];
   o[8] = S.qcell[4 * top + 1];
-  o[9] = tlog(1.01, S.tlogtab);
+  o[9] = tlog(1.01, LT);
 }
 
 static int pow2_floor(int n) {
@@ -411,7 +413,8 @@ static int load_impl(const pdf_grid_desc *d, int nmem, const double *member_valu
     S.coef32 = A.take<float>((size_t)nmem * (nqc + 1) * nx * nf * 16);
     S.coefff = A.take<float2>((size_t)nmem * (nqc + 1) * nx * nf * 16);
     S.ffbad = A.take<int>(1);
-    S.tlogtab = A.take<double2>(kLogTab); S.texptab = A.take<double>(kExpTab);
+    S.tlogtab = A.take<double2>(kLogTab); S.tloghtab = A.take<double>(kLogTab);
+    S.texptab = A.take<double>(kExpTab);
     S.acell = A.take<double>(6 * (na > 0 ? na : 1));
     S.acell32 = A.take<float>(6 * (na > 0 ? na : 1));
     S.xthr32 = A.take<float>(nx); S.q2thr32 = A.take<float>(nrows); S.aq2thr32 = A.take<float>(na > 0 ? na : 1);
@@ -455,9 +458,10 @@ static int load_impl(const pdf_grid_desc *d, int nmem, const double *member_valu
   H2D(S.first, first, sizeof(int) * nsub);
   H2D(S.nq, d->nq, sizeof(int) * nsub);
   {
-    double lt[2 * kLogTab], et[kExpTab];
-    tang_tables(lt, et);
+    double lt[2 * kLogTab], lh[kLogTab], et[kExpTab];
+    tang_tables(lt, lh, et);
     H2D(S.tlogtab, lt, sizeof lt);
+    H2D(S.tloghtab, lh, sizeof lh);
     H2D(S.texptab, et, sizeof et);
   }
   if (e == cudaSuccess) e = cudaMemset(inv, 0, sizeof(unsigned long long));
@@ -493,7 +497,7 @@ static int load_impl(const pdf_grid_desc *d, int nmem, const double *member_valu
   v.qc_row = S.qc_row; v.vals = const_cast<double *>(S.vals);
   v.coef = S.coef; v.coef32 = S.coef32; v.xW = S.xW; v.qW = S.qW;
   v.coefff = S.coefff; v.ff = ffbad ? 0 : 1;
-  v.tlogtab = S.tlogtab; v.texptab = S.texptab;
+  v.tlogtab = S.tlogtab; v.tloghtab = S.tloghtab; v.texptab = S.texptab;
   v.nmem = nmem;
   v.mstride = (size_t)(nqc + 1) * nx * nf * 16;
   g->ffbad = S.ffbad;

@@ -81,6 +81,7 @@ struct GridView {
   const float *xthr32, *q2thr32;   // smallest float >= knot
   const float *xcell32, *qcell32;  // [n][8], see cell32 in grid.cu
   const double2 *tlogtab;     // [kLogTab] {1/F_j, ln F_j} (tang.cuh)
+  const double *tloghtab;     // [kLogTab] ln(F_j / 2)
   const double *texptab;      // [kExpTab] 2^(k/256)
 
   // alpha_s
@@ -145,10 +146,9 @@ __device__ __forceinline__ void bernstein(T t, T s, T *B) {  // s = 1 - t
 // ---------------------------------------------------------------------------
 // From g0 at one knot (p = 0) and g1 at the next one inwards (p = 1):
 // log-linear if both are positive, linear otherwise.
-__device__ __forceinline__ double pair_rule(double g0, double g1, double p, const double2 *LT,
-                                            const double *ET) {
+__device__ __forceinline__ double pair_rule(double g0, double g1, double p, LogTabs LT, const double *ET) {
   if (__double_as_longlong(g0) > 0 && __double_as_longlong(g1) > 0)  // both > 0 (NaN: log-linear, NaN)
-    return g0 * texp(p * tlog(g1 / g0, LT), ET);
+    return g0 * texp(p * tlog(ddiv(g1, g0), LT), ET);
   return g0 + (g1 - g0) * p;
 }
 __device__ __forceinline__ float pair_rule(float g0, float g1, float p) {
@@ -158,8 +158,9 @@ __device__ __forceinline__ float pair_rule(float g0, float g1, float p) {
 
 // Low Q^2: f0 = F(Q2min), f1 = F(1.01 Q2min); rho = Q^2/Q2min, lr = ln rho.
 __device__ __forceinline__ double lowq_rule(double f0, double f1, double rho, double lr,
-                                            double ln101, const double2 *LT, const double *ET) {
-  double gam = (__double_as_longlong(f0) > 0 && __double_as_longlong(f1) > 0) ? tlog(f1 / f0, LT) / ln101 : 1.0;
+                                            double ln101, LogTabs LT, const double *ET) {
+  double gam =
+      (__double_as_longlong(f0) > 0 && __double_as_longlong(f1) > 0) ? tlog(ddiv(f1, f0), LT) / ln101 : 1.0;
   double ex = (gam * rho + 1.0) - rho;
   return f0 * texp(ex * lr, ET);
 }

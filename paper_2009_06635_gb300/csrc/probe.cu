@@ -43,7 +43,24 @@ static int probe(int iters, double *out) {
   return check_launch("probe");
 }
 
+// The evaluation kernels' own elementary functions, elementwise (tang.cuh).
+__global__ void k_math(GridView g, int fn, const double *a, const double *b, long long n, double *out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  out[i] = fn == 0 ? tlog(a[i], LogTabs{g.tlogtab, g.tloghtab}) : fn == 1 ? texp(a[i], g.texptab) : ddiv(a[i], b[i]);
+}
+
 }  // namespace pdfgb
+
+extern "C" int pdf_probe_math(const pdf_grid *grid, int fn, const double *a, const double *b, size_t n,
+                              double *out, cudaStream_t stream) {
+  using namespace pdfgb;
+  if (!grid || (n > 0 && (!a || !out || (fn == 2 && !b)))) return set_error(PDF_ERR_NULL, "pdf_probe_math: NULL argument");
+  if (fn < 0 || fn > 2) return set_error(PDF_ERR_ARG, "pdf_probe_math: fn must be 0, 1 or 2");
+  if (n == 0) return PDF_OK;
+  k_math<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(grid->v, fn, a, b, (long long)n, out);
+  return check_launch("pdf_probe_math");
+}
 
 extern "C" int pdf_probe_fma_rate(int precision, int iters, double *flops_per_s) {
   using namespace pdfgb;

@@ -41,7 +41,7 @@ struct PointSites {
 // finite (alpha_s needs it even where x is invalid).  LT: tlog's table.
 __device__ __forceinline__ PointSites<double> sites(const GridView &g, const long long *xkeys,
                                                     const long long *qkeys, double x, double q2,
-                                                    const double2 *LT, double &lq) {
+                                                    LogTabs LT, double &lq) {
   PointSites<double> r;
   r.xc0 = r.xc1 = r.qc0 = r.qc1 = 0;
   r.t0 = r.t1 = r.u0 = r.u1 = r.px = r.pq = r.lr = 0.0;

@@ -19,12 +19,17 @@
 //          places for |y| < 700), |r| <= ln2/512, e^r - 1 by Taylor to r^4
 //          (truncation below 4e-17 relative).
 //
-// Tables: {1/F_j, ln F_j} for j = 0..256 and 2^(k/256) for k = 0..255,
-// computed on the host by the C library and staged with every grid (both
-// functions read them from shared memory in the evaluation kernels, from
-// global memory elsewhere).  ln F_256 is stored as the same double as the
-// constant ln2 below, so ln a for a just under 1 (e = -1, j = 256) loses
-// nothing to cancellation: fma(-1, ln2, ln2) = 0 exactly.
+// ddiv: a / b by the hardware reciprocal approximation, two Newton steps and
+// one product (within ~1.5 ulp; not correctly rounded), for finite nonzero
+// normal b; anything else takes the exact division.
+//
+// Tables: {1/F_j, ln F_j} and ln(F_j / 2) for j = 0..256, 2^(k/256) for
+// k = 0..255, computed on the host by the C library and staged with every
+// grid (read from shared memory in the evaluation kernels, from global memory
+// elsewhere).  For a in [1/2, 1) (e = -1) the sum e ln2 + ln F_j is the table
+// value ln(F_j / 2) itself, so ln a for a just below 1 is not the small
+// difference of two rounded logarithms (Tang's method treats the neighbourhood
+// of 1 with the same aim).
 //
 // Domain: tlog takes a > 0 (subnormals scaled first; +inf and NaN go to the
 // device library); texp takes |y| < 700 on the fast path and hands anything
@@ -44,10 +49,17 @@ constexpr double kLn2d256Hi = 0x1.62e42fefa0000p-9;      // ln2/256, 36 signific
 constexpr double kLn2d256Lo = 0x1.cf79abc9e3b3ap-48;     // ln2/256 - kLn2d256Hi
 constexpr double kShifter = 0x1.8p52;                    // 1.5 * 2^52: rounds to an integer
 
-// Host: fill the tables (logtab[2 j] = 1/F_j, logtab[2 j + 1] = ln F_j).
-void tang_tables(double *logtab, double *exptab);
+// Host: fill the tables (logtab[2 j] = 1/F_j, logtab[2 j + 1] = ln F_j,
+// loghtab[j] = ln(F_j / 2)).
+void tang_tables(double *logtab, double *loghtab, double *exptab);
 
-__device__ __forceinline__ double tlog(double a, const double2 *LT) {
+// The logarithm's tables: {1/F_j, ln F_j} and ln(F_j / 2).
+struct LogTabs {
+  const double2 *t;
+  const double *h;
+};
+
+__device__ __forceinline__ double tlog(double a, LogTabs LT) {
   long long b = __double_as_longlong(a);
   int e = (int)(b >> 52) - 1023;
   if (e == -1023) {  // subnormal: bring into the normal range
@@ -60,13 +72,26 @@ __device__ __forceinline__ double tlog(double a, const double2 *LT) {
   const int j = (((int)(b >> 43) & 0x1FF) + 1) >> 1;  // top 8 mantissa bits, rounded
   const double m = __longlong_as_double((b & 0x000FFFFFFFFFFFFFLL) | 0x3FF0000000000000LL);
   const double F = __longlong_as_double(0x3FF0000000000000LL + ((long long)j << 44));
-  const double2 t = LT[j];
+  const double2 t = LT.t[j];
   const double u = (m - F) * t.x;
   double q = fma(u, 0.2, -0.25);
   q = fma(u, q, 1.0 / 3.0);
   q = fma(u, q, -0.5);
   const double p = fma(u * u, q, u);
-  return fma((double)e, kLn2, t.y) + p;
+  // a in [1/2, 1): ln(F/2) from its own table entry, so that a just below 1
+  // keeps its relative precision (-ln2 + ln F would cancel)
+  const double K = e == -1 ? LT.h[j] : fma((double)e, kLn2, t.y);
+  return K + p;
+}
+
+__device__ __forceinline__ double ddiv(double a, double b) {
+  const unsigned e = ((unsigned)(__double_as_longlong(b) >> 52)) & 0x7FFu;
+  if (e < 2u || e > 2044u) return a / b;  // zero, subnormal, near over/underflow, inf, NaN
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(b));
+  y = fma(y, fma(-b, y, 1.0), y);
+  y = fma(y, fma(-b, y, 1.0), y);
+  return a * y;
 }
 
 __device__ __forceinline__ double texp(double y, const double *ET) {

@@ -161,7 +161,7 @@ __device__ __forceinline__ double site_t(const double *c, const Rec64 &R, int p,
 // One item: column col of the point in slot p.  moff: the member's offset
 // into the control points.
 __device__ __forceinline__ double eval_item64(const GridView &g, const Rec64 &R, int p, int col, size_t moff,
-                                              const double2 *LT, const double *ET) {
+                                              LogTabs LT, const double *ET) {
   const double *cb = g.coef + moff + (size_t)col * 16;
   const size_t stride = (size_t)g.nf * 16;
   auto C = [&](int a, int b) {
@@ -251,7 +251,7 @@ __device__ __forceinline__ void store_point(Rec64 &R, int slot, const PointSites
 
 // Phase 2 over the first np slots: items (slot, column) in order, lane-strided.
 __device__ __forceinline__ void items64(const GridView &g, const Rec64 &R, int np, int nc, int cbase,
-                                        size_t moff, long long mo, double *__restrict__ out, const double2 *LT,
+                                        size_t moff, long long mo, double *__restrict__ out, LogTabs LT,
                                         const double *ET, int lane) {
   const int nitems = np * nc;
   int p = lane / nc, c = lane - (lane / nc) * nc;
@@ -304,8 +304,10 @@ k_xf64(GridView g, const double *__restrict__ xa, const double *__restrict__ qa,
   off += keys_bytes(g.nrows, 8);
   long long *akeys = reinterpret_cast<long long *>(smem + off);
   off += keys_bytes(g.na, 8);
-  double2 *LT = reinterpret_cast<double2 *>(smem + off);
+  double2 *LTt = reinterpret_cast<double2 *>(smem + off);
   off += sizeof(double2) * kLogTab;
+  double *LTh = reinterpret_cast<double *>(smem + off);
+  off += keys_bytes(kLogTab, 8);
   double *ET = reinterpret_cast<double *>(smem + off);
   off += sizeof(double) * kExpTab;
   Rec64 *recs = reinterpret_cast<Rec64 *>(smem + off);
@@ -316,7 +318,8 @@ k_xf64(GridView g, const double *__restrict__ xa, const double *__restrict__ qa,
   load_keys<double>(g, xkeys, 0);
   load_keys<double>(g, qkeys, 1);
   if (want_as) load_keys<double>(g, akeys, 2);
-  for (int i = threadIdx.x; i < kLogTab; i += kThreads) LT[i] = g.tlogtab[i];
+  for (int i = threadIdx.x; i < kLogTab; i += kThreads) { LTt[i] = g.tlogtab[i]; LTh[i] = g.tloghtab[i]; }
+  const LogTabs LT{LTt, LTh};
   for (int i = threadIdx.x; i < kExpTab; i += kThreads) ET[i] = g.texptab[i];
   __syncthreads();
 
@@ -443,7 +446,7 @@ static int num_sms() {
 template <int MODE>
 static size_t xf64_smem(const GridView &g) {
   return keys_bytes(g.nx, 8) + keys_bytes(g.nrows, 8) + keys_bytes(g.na, 8) + sizeof(double2) * kLogTab +
-         sizeof(double) * kExpTab + kWarps * (sizeof(Rec64) + (MODE == MODE_MEMBERS ? 0 : sizeof(Queue64)));
+         keys_bytes(kLogTab, 8) + sizeof(double) * kExpTab + kWarps * (sizeof(Rec64) + (MODE == MODE_MEMBERS ? 0 : sizeof(Queue64)));
 }
 
 template <int MODE>

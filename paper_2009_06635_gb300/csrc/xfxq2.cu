@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(kThreads) k_alphas(GridView g, const T *__rest
     unsigned inv = __ballot_sync(0xffffffffu, bad);
     if ((threadIdx.x & 31) == 0 && inv) atomicAdd(g.invalid, (unsigned long long)__popc(inv));
     if (present) {
-      if constexpr (sizeof(T) == 8) out[i] = alphas_eval(g, akeys, q2, bad ? 0.0 : tlog(q2, g.tlogtab));
+      if constexpr (sizeof(T) == 8) out[i] = alphas_eval(g, akeys, q2, bad ? 0.0 : tlog(q2, LogTabs{g.tlogtab, g.tloghtab}));
       else out[i] = alphas_eval(g, akeys, q2);
     }
   }

@@ -1,0 +1,79 @@
+"""The FP64 evaluation kernels' own elementary functions (tang.cuh: Tang's
+table-driven logarithm and exponential, and the Newton division) against the
+C library's, which round within one ulp: over the ranges the kernels use,
+and at the special values they must get right."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+P = pytest.importorskip("paper_2009_06635_gb300")
+
+
+@pytest.fixture(scope="module")
+def grid(synth):
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    torch.cuda.set_device(0)
+    return P.pdf_load_grid(synth.grid_single_subgrid())
+
+
+def run(G, fn, a, b=None):
+    from paper_2009_06635_gb300 import _native
+    ad = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+    bd = torch.from_numpy(np.ascontiguousarray(b, dtype=np.float64)).cuda() if b is not None else None
+    out = torch.empty_like(ad)
+    _native.check(_native.load().pdf_probe_math(G.handle, fn, ctypes.c_void_p(ad.data_ptr()),
+                                                ctypes.c_void_p(bd.data_ptr() if bd is not None else 0), len(a),
+                                                ctypes.c_void_p(out.data_ptr()), None), "pdf_probe_math")
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def ulps(got, want):
+    return np.abs(got - want) / np.spacing(np.abs(want))
+
+
+def test_log(grid):
+    r = np.random.default_rng(1)
+    a = np.concatenate([np.exp(r.uniform(-700, 700, 200_000)), r.uniform(0.5, 2.0, 200_000),
+                        1 + r.uniform(-1e-3, 1e-3, 100_000), [1.0, 2.0, 0.5, np.nextafter(1, 0), np.nextafter(1, 2),
+                                                              5e-324, 1e-310, np.finfo(float).max]])
+    got = run(grid, 0, a)
+    want = np.log(a)
+    # the documented bound: two roundings (e ln2 + ln F, then + log1p(u)),
+    # the rounding of ln2 times the exponent, and the degree-5 series'
+    # truncation (|u|^6 / 6 <= 2^-54 / 6): 2 ulp of ln a or 2e-17 absolute
+    err = np.abs(got - want)
+    assert np.all(err <= 2 * np.spacing(np.abs(want)) + 2e-17), (err / (2 * np.spacing(np.abs(want)) + 2e-17)).max()
+    # near a = 1 the result is not the difference of two rounded logarithms
+    # (a just below 1 reads ln(F/2) from its table): no cancellation beyond that bound
+    near = np.abs(want) < 1e-4
+    assert np.all(err[near] <= 2 * np.spacing(np.abs(want[near]))), (err[near] / np.spacing(np.abs(want[near]))).max()
+    assert got[-8] == 0.0 and got[-7] == np.log(2.0)
+    assert np.array_equal(run(grid, 0, np.array([0.0, np.inf])), np.array([-np.inf, np.inf]))
+    assert np.isnan(run(grid, 0, np.array([np.nan]))[0])
+
+
+def test_exp(grid):
+    r = np.random.default_rng(2)
+    y = np.concatenate([r.uniform(-699, 699, 300_000), r.uniform(-1e-3, 1e-3, 100_000), [0.0, -0.0, 1e-300,
+                                                                                           -745.2, 709.9, 800.0]])
+    got = run(grid, 1, y)
+    want = np.exp(y)
+    fin = np.isfinite(want) & (want > 1e-300)
+    assert np.all(ulps(got[fin], want[fin]) <= 2.0), ulps(got[fin], want[fin]).max()
+    assert got[-6] == 1.0 and got[-5] == 1.0 and np.isinf(got[-1])
+
+
+def test_division(grid):
+    r = np.random.default_rng(3)
+    a = r.normal(0, 1, 300_000) * 10.0 ** r.integers(-30, 30, 300_000)
+    b = r.normal(0, 1, 300_000) * 10.0 ** r.integers(-30, 30, 300_000)
+    got = run(grid, 2, a, b)
+    want = a / b
+    assert np.all(ulps(got, want) <= 2.0), ulps(got, want).max()
+    special = run(grid, 2, np.array([1.0, 1.0, 1.0, 0.0]), np.array([0.0, 5e-324, np.inf, 2.0]))
+    assert np.isinf(special[0]) and special[1] == 1.0 / 5e-324 and special[2] == 0.0 and special[3] == 0.0
