@@ -70,6 +70,7 @@ struct Stage {
   const double *xk, *q2k, *vals, *aq2, *aval;
   const int *first, *nq;
   int nx, nrows, nf, na, nsub, nxc, nqc;
+  int nfp;   // flavour stride of the FP32 and float-float copies (nf rounded up to 8)
   int nmem;  // members: values and control points repeat per member
   // outputs
   double *lx, *lq, *alq;
@@ -210,21 +211,22 @@ __global__ void k_coef(Stage S) {
   }
   double *o = S.coef + (size_t)gid * 16;
   // FP32 copy row-major by control-point row, then flavour: [cell][l][f][4], so
-  // one load instruction over the flavours of a point reads consecutive rows
-  float *o32 = S.coef32 + (size_t)(gid / S.nf) * 16 * S.nf + (size_t)f * 4;
+  // one load instruction over the flavours of a point reads consecutive rows;
+  // the flavour stride nfp (a multiple of 8) makes each row block whole lines
+  float *o32 = S.coef32 + (size_t)(gid / S.nf) * 16 * S.nfp + (size_t)f * 4;
   // float-float copy flavour-minor by pairs of control points,
   // [cell][m / 2][flavour][m % 2]: one 16-byte load per pair and flavour, and
   // the lanes of one load (consecutive flavours of a point) read consecutive bytes
-  float2 *off = S.coefff + (size_t)(gid / S.nf) * 16 * S.nf + (size_t)f * 2;
+  float2 *off = S.coefff + (size_t)(gid / S.nf) * 16 * S.nfp + (size_t)f * 2;
   bool bad = false;
   for (int m = 0; m < 16; m++) {
     o[m] = c[m];
-    o32[(size_t)(m >> 2) * 4 * S.nf + (m & 3)] = (float)c[m];
+    o32[(size_t)(m >> 2) * 4 * S.nfp + (m & 3)] = (float)c[m];
     // float-float split: hi = round(c), lo = round(c - hi); exact to 2^-48 of c
     // while |c| stays well inside the float exponent range
     float hi = __double2float_rn(c[m]);
     float lo = __double2float_rn(c[m] - (double)hi);
-    off[(size_t)(m >> 1) * 2 * S.nf + (m & 1)] = make_float2(hi, lo);
+    off[(size_t)(m >> 1) * 2 * S.nfp + (m & 1)] = make_float2(hi, lo);
     double a = fabs(c[m]);
     if (a != 0.0 && (a < 1e-30 || a > 1e30)) bad = true;
   }
@@ -399,6 +401,7 @@ static int load_impl(const pdf_grid_desc *d, int nmem, const double *member_valu
   const double *values0 = member_values ? member_values : d->values;
   const int nx = d->nx, nf = d->nflav, na = d->na, nsub = d->nsub;
   const int nxc = nx - 1, nqc = nrows - nsub;
+  const int nfp = (nf + 7) & ~7;
 
   // sizes (a dry run of the arena)
   auto layout = [&](Arena &A, Stage &S, unsigned long long **inv) {
@@ -410,8 +413,8 @@ static int load_impl(const pdf_grid_desc *d, int nmem, const double *member_valu
     S.xcell = A.take<double>(4 * nx); S.qcell = A.take<double>(4 * nrows);
     S.xW = A.take<double>(16 * nx); S.qW = A.take<double>(16 * (nqc + 1));
     S.coef = A.take<double>((size_t)nmem * (nqc + 1) * nx * nf * 16);
-    S.coef32 = A.take<float>((size_t)nmem * (nqc + 1) * nx * nf * 16);
-    S.coefff = A.take<float2>((size_t)nmem * (nqc + 1) * nx * nf * 16);
+    S.coef32 = A.take<float>((size_t)nmem * (nqc + 1) * nx * nfp * 16);
+    S.coefff = A.take<float2>((size_t)nmem * (nqc + 1) * nx * nfp * 16);
     S.ffbad = A.take<int>(1);
     S.tlogtab = A.take<double2>(kLogTab); S.tloghtab = A.take<double>(kLogTab);
     S.texptab = A.take<double>(kExpTab);
@@ -444,6 +447,7 @@ static int load_impl(const pdf_grid_desc *d, int nmem, const double *member_valu
   A.cap = dry.off;
   layout(A, S, &inv);
   S.nx = nx; S.nrows = nrows; S.nf = nf; S.na = na; S.nsub = nsub; S.nxc = nxc; S.nqc = nqc;
+  S.nfp = nfp;
   S.nmem = nmem;
 
   int first[1024];
@@ -500,6 +504,8 @@ static int load_impl(const pdf_grid_desc *d, int nmem, const double *member_valu
   v.tlogtab = S.tlogtab; v.tloghtab = S.tloghtab; v.texptab = S.texptab;
   v.nmem = nmem;
   v.mstride = (size_t)(nqc + 1) * nx * nf * 16;
+  v.nfp = nfp;
+  v.mstride_ff = (size_t)(nqc + 1) * nx * nfp * 16;
   g->ffbad = S.ffbad;
   v.xthr32 = S.xthr32; v.q2thr32 = S.q2thr32; v.xcell32 = S.xcell32; v.qcell32 = S.qcell32;
   v.aq2 = S.aq2; v.acell = S.acell; v.acell32 = S.acell32; v.aq2thr32 = S.aq2thr32;
@@ -575,6 +581,7 @@ extern "C" int pdf_grid_set_values(pdf_grid *g, const double *values, cudaStream
   if (e != cudaSuccess) return set_error(PDF_ERR_CUDA, "pdf_grid_set_values: %s", cudaGetErrorString(e));
   Stage S{};
   S.nx = v.nx; S.nrows = v.nrows; S.nf = v.nf; S.nqc = v.nqc; S.nxc = v.nxc;
+  S.nfp = v.nfp;
   S.nmem = 1;  // member 0
   S.vals = v.vals; S.qc_row = const_cast<int *>(v.qc_row);
   S.xW = const_cast<double *>(v.xW); S.qW = const_cast<double *>(v.qW);

@@ -9,13 +9,16 @@
 //          block (FP64) or 64 bytes (FP32), instead of gathering 16 knots;
 //          the Bernstein weights are non-negative and sum to one, so the
 //          evaluation has no cancellation beyond that of the data.
-//   coef32 the same control points rounded to FP32, [nqc+1][nx][4][nflav][4]
-//          (row l = 0..3 of every flavour, then the next row), so one load
-//          instruction over the flavours of a point reads consecutive rows.
+//   coef32 the same control points rounded to FP32, [nqc+1][nx][4][nfp][4]
+//          (row l = 0..3 of every flavour, then the next row; nfp = nflav
+//          rounded up to 8, so every row block is whole 128-byte lines), so
+//          one load instruction over the flavours of a point reads
+//          consecutive rows of as few lines as possible.
 //   coefff the same control points as float-float pairs (hi, lo), laid out
-//          [nqc+1][nx][8][nflav][2] (pairs of control points m, m+1 of a
-//          flavour adjacent): one 16-byte load per pair, and one load
-//          instruction over the flavours of a point reads consecutive bytes.
+//          [nqc+1][nx][8][nfp][2] (pairs of control points m, m+1 of a
+//          flavour adjacent; flavour stride nfp as for coef32): one 16-byte
+//          load per pair, and one load instruction over the flavours of a
+//          point reads consecutive bytes of whole lines.
 //   xk/q2k raw knots, searched as integer bit patterns (positive doubles
 //          order like their bits), so a cell choice never depends on a log.
 //   xcell  per x cell {ln x_i, 1/d, ln x_{i+1}, 0}, d = ln x_{i+1} - ln x_i;
@@ -72,11 +75,13 @@ struct GridView {
   const int *qc_row;          // [nqc + 1] first row of each Q cell
   double *vals;               // [nrows][nx][nf] device copy of the knot values
   const double *coef;         // [nqc + 1][nx][nf][16]
-  const float *coef32;        // [nqc + 1][nx][4][nf][4]: row l of every flavour, then the next row
-  const float2 *coefff;       // [nqc + 1][nx][8][nf][2] float-float (hi, lo) copy of coef
+  const float *coef32;        // [nqc + 1][nx][4][nfp][4]: row l of every flavour, then the next row
+  const float2 *coefff;       // [nqc + 1][nx][8][nfp][2] float-float (hi, lo) copy of coef
   int ff;                     // 1 if every control point is safe for float-float
   int nmem;                   // members (replicas) sharing the knots; member m's
   size_t mstride;             // control points start m * mstride elements further
+  int nfp;                    // flavour stride of coef32 / coefff (nf rounded up to 8)
+  size_t mstride_ff;          // member stride of coefff (float2 elements)
   const double *xW, *qW;      // [nx][16], [nqc + 1][16]
   const float *xthr32, *q2thr32;   // smallest float >= knot
   const float *xcell32, *qcell32;  // [n][8], see cell32 in grid.cu

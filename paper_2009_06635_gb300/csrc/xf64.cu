@@ -158,11 +158,10 @@ __device__ __forceinline__ double site_t(const double *c, const Rec64 &R, int p,
   return fma(R.W[p][4 * a + 3], v1.y, f);
 }
 
-// One item: column col of the point in slot p.  moff: the member's offset
-// into the control points.
-__device__ __forceinline__ double eval_item64(const GridView &g, const Rec64 &R, int p, int col, size_t moff,
+// One item: column col of the point in slot p, of member m.
+__device__ __forceinline__ double eval_item64(const GridView &g, const Rec64 &R, int p, int col, int m,
                                               LogTabs LT, const double *ET) {
-  const double *cb = g.coef + moff + (size_t)col * 16;
+  const double *cb = g.coef + (size_t)m * g.mstride + (size_t)col * 16;
   const size_t stride = (size_t)g.nf * 16;
   auto C = [&](int a, int b) {
     int xc = a ? R.xc1[p] : R.xc0[p];
@@ -171,9 +170,9 @@ __device__ __forceinline__ double eval_item64(const GridView &g, const Rec64 &R,
   };
   const int cls = R.cls[p];
   if (cls == C_INF)
-    return dot_ff16(reinterpret_cast<const float4 *>(g.coefff + moff +
-                                                     ((size_t)R.qc0[p] * g.nx + R.xc0[p]) * 16 * g.nf) + col,
-                    g.nf, reinterpret_cast<const float2 *>(R.W[p]));
+    return dot_ff16(reinterpret_cast<const float4 *>(g.coefff + (size_t)m * g.mstride_ff +
+                                                     ((size_t)R.qc0[p] * g.nx + R.xc0[p]) * 16 * g.nfp) + col,
+                    g.nfp, reinterpret_cast<const float2 *>(R.W[p]));
   if (cls == C_IN) return dot_w16(C(0, 0), R, p);
   if (cls == C_INVALID) return NAN;
   // continuation: the two values the final rule combines, then one shared rule
@@ -251,13 +250,13 @@ __device__ __forceinline__ void store_point(Rec64 &R, int slot, const PointSites
 
 // Phase 2 over the first np slots: items (slot, column) in order, lane-strided.
 __device__ __forceinline__ void items64(const GridView &g, const Rec64 &R, int np, int nc, int cbase,
-                                        size_t moff, long long mo, double *__restrict__ out, LogTabs LT,
+                                        int m, long long mo, double *__restrict__ out, LogTabs LT,
                                         const double *ET, int lane) {
   const int nitems = np * nc;
   int p = lane / nc, c = lane - (lane / nc) * nc;
   const int dp = 32 / nc, dc = 32 - dp * nc;
   for (int k = lane; k < nitems; k += 32) {
-    out[mo + R.ob[p] + c] = eval_item64(g, R, p, cbase + c, moff, LT, ET);
+    out[mo + R.ob[p] + c] = eval_item64(g, R, p, cbase + c, m, LT, ET);
     c += dc;
     p += dp;
     if (c >= nc) { c -= nc; p++; }
@@ -419,7 +418,7 @@ k_xf64(GridView g, const double *__restrict__ xa, const double *__restrict__ qa,
     if (MODE == MODE_MEMBERS) {
       const int m1 = min(g.nmem, (chunk + 1) * mchunk);
       for (int m = chunk * mchunk; m < m1; m++)
-        items64(g, R, np, nc, cbase, (size_t)m * g.mstride, (long long)m * n * nc, out, LT, ET, lane);
+        items64(g, R, np, nc, cbase, m, (long long)m * n * nc, out, LT, ET, lane);
     } else {
       items64(g, R, np, nc, cbase, 0, 0, out, LT, ET, lane);
     }

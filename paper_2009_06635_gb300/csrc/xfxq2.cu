@@ -56,12 +56,12 @@ __device__ __forceinline__ float site32(const float4 *q, int nf, const float *w,
 // column count, so one flavour alone and all flavours give identical bits).
 __device__ __forceinline__ float eval_item32(const GridView &g, const Rec32 &R, int p, int col) {
   const float4 *cb = reinterpret_cast<const float4 *>(g.coef32) + col;
-  const size_t stride = (size_t)g.nf * 4;  // float4 per cell
+  const size_t stride = (size_t)g.nfp * 4;  // float4 per cell
   const float *w = R.W[p];
   auto F = [&](int a, int b) {
     int xc = a ? R.xc1[p] : R.xc0[p];
     int qc = b ? R.qc1[p] : R.qc0[p];
-    return site32(cb + ((size_t)qc * g.nx + xc) * stride, g.nf, w, a, b);
+    return site32(cb + ((size_t)qc * g.nx + xc) * stride, g.nfp, w, a, b);
   };
   return combine<float>(R.cls[p], R.px[p], R.pq[p], R.lr[p], g.ln101_32, F);
 }

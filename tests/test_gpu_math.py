@@ -62,7 +62,8 @@ def test_exp(grid):
     y = np.concatenate([r.uniform(-699, 699, 300_000), r.uniform(-1e-3, 1e-3, 100_000), [0.0, -0.0, 1e-300,
                                                                                            -745.2, 709.9, 800.0]])
     got = run(grid, 1, y)
-    want = np.exp(y)
+    with np.errstate(over="ignore"):
+        want = np.exp(y)
     fin = np.isfinite(want) & (want > 1e-300)
     assert np.all(ulps(got[fin], want[fin]) <= 2.0), ulps(got[fin], want[fin]).max()
     assert got[-6] == 1.0 and got[-5] == 1.0 and np.isinf(got[-1])
