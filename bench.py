@@ -551,6 +551,18 @@ def our_arm(args):
     for _ in range(e2e_steps):
         P.xfxq2_all_flavours_host(G, hx, hq, out=hout, alphas_out=hal)
     e2e_s = max_over_ranks(world, (time.perf_counter() - t0) / e2e_steps)
+    # the host link's device-to-host rate on the step's output (the e2e bound)
+    dsrc = torch.empty((n, nf), dtype=torch.float64, device=dev)
+    hout.copy_(dsrc, non_blocking=True)
+    sync()
+    la, lb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    la.record()
+    hout.copy_(dsrc, non_blocking=True)
+    lb.record()
+    sync()
+    link_d2h = 8 * n * nf / (la.elapsed_time(lb) * 1e-3) / 1e9
+    del dsrc
+    e2e_bound_s = 8 * n * (nf + 1) / (link_d2h * 1e9)
 
     # ceilings measured on this GPU
     fp64_meas = ctypes.c_double(0.0)
@@ -591,7 +603,9 @@ def our_arm(args):
         "clocks": clk,
         "e2e": {"value": world * evals_step / e2e_s, "unit": "evals/s", "h2d_bytes_per_step": 16 * n,
                 "d2h_bytes_per_step": 8 * n * (nf + 1), "ms_per_step": e2e_s * 1e3,
-                "call": "xfxq2_all_flavours_host (pinned host buffers, alpha_s included)"},
+                "call": "xfxq2_all_flavours_host (pinned host buffers, alpha_s included)",
+                "host_link_d2h_gbs": link_d2h, "link_bound_ms": e2e_bound_s * 1e3,
+                "frac_of_link_bound": e2e_bound_s / e2e_s},
         "paths": {
             "fp32": {"value": world * evals_step / (ms32 * 1e-3), "ms_per_step": ms32, "kernel_ms": k32,
                      "roofline": {"bound": "hbm", "achieved": bytes32 / (k32 * 1e-3) / 1e9, "peak": hbm,
