@@ -400,20 +400,15 @@ def mc_leg(G, world, sync, rank):
     P.pdf_mc_integrate(G, cfg["sqrt_s"], cfg["x_min"], cfg["shat_min"], cfg["seed"], 3 * chunk, chunk=chunk)  # warm-up
     sync()
     barrier(world)
+    from paper_2009_06635_gb300.sharding import allreduce_mc_sums, mc_event_range
+
+    first, count = mc_event_range(rank, n)
     t0 = time.perf_counter()
-    r = P.pdf_mc_integrate(G, cfg["sqrt_s"], cfg["x_min"], cfg["shat_min"], cfg["seed"], n, first_event=rank * n,
+    r = P.pdf_mc_integrate(G, cfg["sqrt_s"], cfg["x_min"], cfg["shat_min"], cfg["seed"], count, first_event=first,
                            chunk=chunk)
     sync()
     s = max_over_ranks(world, time.perf_counter() - t0)
-    sums = [r.sum_w, r.sum_w2, r.sum_abs]
-    if world > 1:
-        import torch
-        import torch.distributed as dist
-
-        t = torch.tensor(sums, dtype=torch.float64, device="cuda")
-        dist.all_reduce(t)
-        sums = t.tolist()
-    tot = P.McResult(sums, world * n)
+    tot = P.McResult(allreduce_mc_sums([r.sum_w, r.sum_w2, r.sum_abs]), world * n)
     return {"events": world * n, "chunk": chunk, "s": s, "events_per_s": world * n / s,
             "evals_per_s": world * n * (2 * 13 + 1) / s, "estimate": tot.estimate, "std_error": tot.std_error,
             "config": dict(cfg, observable="toy LO: L^2/s-hat [sum_q e_q^2 (q qbar + qbar q) + alpha_s^2 g g]")}
@@ -468,8 +463,7 @@ def our_arm(args):
             fn = lambda: P.xfxq2_all_flavours_alphas(G, xd, qd, out=out, alphas_out=aout)  # noqa: E731
         else:
             xs = (xd.float(), qd.float(), out.float(), aout.float())
-            fn = lambda: (P.xfxq2_all_flavours(G, xs[0], xs[1], out=xs[2]),  # noqa: E731
-                          P.alphas_q2(G, xs[1], out=xs[3]))
+            fn = lambda: P.xfxq2_all_flavours_alphas(G, xs[0], xs[1], out=xs[2], alphas_out=xs[3])  # noqa: E731
         ms = run_timed(fn, args.steps, args.warmup, world, sync)
         if rank == 0:
             print(json.dumps({"only": args.only, "points": n, "ms_per_step": ms, "evals_per_s": evals_step / (ms * 1e-3)}))
@@ -491,13 +485,12 @@ def our_arm(args):
     aout32 = torch.empty((n,), dtype=torch.float32, device=dev)
     ev32 = []
 
-    def step32():
+    def step32():  # one launch: all flavours and alpha_s
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        P.xfxq2_all_flavours(G, xd32, qd32, out=out32)
+        P.xfxq2_all_flavours_alphas(G, xd32, qd32, out=out32, alphas_out=aout32)
         b.record()
         ev32.append((a, b))
-        P.alphas_q2(G, qd32, out=aout32)
 
     ms32 = max_over_ranks(world, run_timed(step32, args.steps, args.warmup, world, sync))
     k32 = float(np.mean([a.elapsed_time(b) for a, b in ev32[args.warmup:]]))

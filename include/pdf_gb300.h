@@ -190,6 +190,10 @@ PDF_API int xfxq2_all_flavours_f32(const pdf_grid *grid, const float *x, const f
                            float *out, cudaStream_t stream);
 PDF_API int alphas_q2_f32(const pdf_grid *grid, const float *q2, size_t n, float *out,
                   cudaStream_t stream);
+/* FP32 all flavours and alpha_s in one pass (as xfxq2_all_flavours_alphas);
+ * bit-identical to xfxq2_all_flavours_f32 and alphas_q2_f32. */
+PDF_API int xfxq2_all_flavours_alphas_f32(const pdf_grid *grid, const float *x, const float *q2, size_t n,
+                                          float *out, float *alphas_out, cudaStream_t stream);
 
 /* One Monte Carlo event batch in a single launch (PDFFlow Sec. 4.1: the PDF
  * load of a hadronic integrand): for event e, Q^2 = x1[e] x2[e] s, and

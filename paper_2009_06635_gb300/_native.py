@@ -55,6 +55,7 @@ SIGNATURES = {
     "xfxq2": (I32, [P, I32, P, P, SZ, P, P]),
     "xfxq2_all_flavours": (I32, [P, P, P, SZ, P, P]),
     "xfxq2_all_flavours_alphas": (I32, [P, P, P, SZ, P, P, P]),
+    "xfxq2_all_flavours_alphas_f32": (I32, [P, P, P, SZ, P, P, P]),
     "pdf_mc_integrate": (I32, [P, P, ctypes.c_ulonglong, ctypes.c_ulonglong, SZ, P, P]),
     "pdf_load_lhapdf": (I32, [ctypes.c_char_p, I32, I32, ctypes.POINTER(P)]),
     "pdf_probe_math": (I32, [P, I32, P, P, SZ, P, P]),

@@ -85,21 +85,22 @@ __device__ __forceinline__ void store_point32(Rec32 &R, int slot, const PointSit
   row[3] = make_float4(bq1[0], bq1[1], bq1[2], bq1[3]);
 }
 
-// MODE_POINTS: points xa[n], qa[n]; out[n][ncol] for columns col0..col0+ncol-1.
+// MODE_POINTS: points xa[n], qa[n]; out[n][ncol] for columns col0..col0+ncol-1;
+//              as_out[n] (alpha_s) when not null.
 // MODE_MC:     events xa[n] (x1), xb[n] (x2), Q^2 = x1 x2 s; out[n][2 nf + 1].
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, 3)
 k_xf32(GridView g, const float *__restrict__ xa, const float *__restrict__ qa, const float *__restrict__ xb,
-       float s, long long n, int col0, int ncol, float *__restrict__ out) {
+       float s, long long n, int col0, int ncol, float *__restrict__ out, float *__restrict__ as_out) {
   extern __shared__ __align__(16) unsigned char smem[];
   int *xkeys = reinterpret_cast<int *>(smem);
   int *qkeys = reinterpret_cast<int *>(smem + keys_bytes(g.nx, 4));
   int *akeys = reinterpret_cast<int *>(smem + keys_bytes(g.nx, 4) + keys_bytes(g.nrows, 4));
-  size_t rec_off = keys_bytes(g.nx, 4) + keys_bytes(g.nrows, 4) + (MODE == MODE_MC ? keys_bytes(g.na, 4) : 0);
+  size_t rec_off = keys_bytes(g.nx, 4) + keys_bytes(g.nrows, 4) + keys_bytes(g.na, 4);
   Rec32 *recs = reinterpret_cast<Rec32 *>(smem + rec_off);
   load_keys<float>(g, xkeys, 0);
   load_keys<float>(g, qkeys, 1);
-  if (MODE == MODE_MC) load_keys<float>(g, akeys, 2);
+  if (MODE == MODE_MC || as_out) load_keys<float>(g, akeys, 2);
   __syncthreads();
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -140,6 +141,7 @@ k_xf32(GridView g, const float *__restrict__ xa, const float *__restrict__ qa, c
     unsigned inv = __ballot_sync(0xffffffffu, ps.cls == C_INVALID);
     if (lane == 0 && inv) atomicAdd(g.invalid, (unsigned long long)__popc(inv));
     if (MODE == MODE_MC && present && (lane & 1) == 0) out[ob + 2 * g.nf] = alphas_eval(g, akeys, q2);
+    if (MODE == MODE_POINTS && present && as_out) as_out[e0 + lane] = alphas_eval(g, akeys, q2);
     // order the points by class (counting sort over the warp)
     int slot = 0, base = 0;
 #pragma unroll
@@ -203,13 +205,12 @@ static int num_sms() {
 
 template <int MODE>
 static size_t xf32_smem(const GridView &g) {
-  return keys_bytes(g.nx, 4) + keys_bytes(g.nrows, 4) + (MODE == MODE_MC ? keys_bytes(g.na, 4) : 0) +
-         kWarps * sizeof(Rec32);
+  return keys_bytes(g.nx, 4) + keys_bytes(g.nrows, 4) + keys_bytes(g.na, 4) + kWarps * sizeof(Rec32);
 }
 
 template <int MODE>
 static int launch_xf32(const pdf_grid *grid, const float *xa, const float *qa, const float *xb, float s,
-                       long long n, int col0, int ncol, float *out, cudaStream_t st) {
+                       long long n, int col0, int ncol, float *out, cudaStream_t st, float *as_out = nullptr) {
   const GridView &g = grid->v;
   const size_t smem = xf32_smem<MODE>(g);
   auto kern = k_xf32<MODE>;
@@ -222,7 +223,7 @@ static int launch_xf32(const pdf_grid *grid, const float *xa, const float *qa, c
   long long blocks = (ntiles + kWarps - 1) / kWarps;
   const long long cap = (long long)num_sms() * per_sm;
   if (blocks > cap) blocks = cap;
-  kern<<<(unsigned)blocks, kThreads, smem, st>>>(g, xa, qa, xb, s, n, col0, ncol, out);
+  kern<<<(unsigned)blocks, kThreads, smem, st>>>(g, xa, qa, xb, s, n, col0, ncol, out, as_out);
   return check_launch(MODE == MODE_MC ? "pdf_mc_event kernel (FP32)" : "xfxq2 kernel (FP32)");
 }
 
@@ -335,6 +336,15 @@ extern "C" int xfxq2_all_flavours_alphas(const pdf_grid *g, const double *x, con
   if (g->v.na == 0) return set_error(PDF_ERR_NO_ALPHAS, "xfxq2_all_flavours_alphas: grid has no alpha_s nodes");
   if (n == 0) return PDF_OK;
   return launch_all_f64(g, x, q2, (long long)n, out, alphas_out, st);
+}
+extern "C" int xfxq2_all_flavours_alphas_f32(const pdf_grid *g, const float *x, const float *q2, size_t n,
+                                             float *out, float *alphas_out, cudaStream_t st) {
+  int rc = check_common(g, x, q2, out, n, "xfxq2_all_flavours_alphas_f32");
+  if (rc) return rc;
+  if (n > 0 && !alphas_out) return set_error(PDF_ERR_NULL, "xfxq2_all_flavours_alphas_f32: alphas_out is NULL");
+  if (g->v.na == 0) return set_error(PDF_ERR_NO_ALPHAS, "xfxq2_all_flavours_alphas_f32: grid has no alpha_s nodes");
+  if (n == 0) return PDF_OK;
+  return launch_xf32<MODE_POINTS>(g, x, q2, nullptr, 0.f, (long long)n, 0, g->v.nf, out, st, alphas_out);
 }
 extern "C" int alphas_q2(const pdf_grid *g, const double *q2, size_t n, double *out, cudaStream_t st) {
   return do_alphas<double>(g, q2, n, out, st);

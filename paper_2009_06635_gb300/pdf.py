@@ -152,14 +152,17 @@ def xfxq2_all_flavours(grid: Grid, x: torch.Tensor, q2: torch.Tensor, out=None) 
 
 
 def xfxq2_all_flavours_alphas(grid: Grid, x: torch.Tensor, q2: torch.Tensor, out=None, alphas_out=None):
-    """All flavours [n][nflav] and alpha_s [n] in one pass (FP64)."""
+    """All flavours [n][nflav] and alpha_s [n] in one pass (FP64 or FP32 by
+    the input dtype)."""
     _check_pair(x, q2)
     out = _out(out, (x.shape[0], grid.nflav), x)
     alphas_out = _out(alphas_out, (x.shape[0],), x)
-    dt = torch.float64
-    check(_native.load().xfxq2_all_flavours_alphas(
-        grid.handle, _dev_ptr(x, dt, "x"), _dev_ptr(q2, dt, "q2"), x.shape[0], _dev_ptr(out, dt, "out"),
-        _dev_ptr(alphas_out, dt, "alphas_out"), _stream_handle(x.device)), "xfxq2_all_flavours_alphas")
+    f32 = x.dtype == torch.float32
+    dt = torch.float32 if f32 else torch.float64
+    lib = _native.load()
+    fn = lib.xfxq2_all_flavours_alphas_f32 if f32 else lib.xfxq2_all_flavours_alphas
+    check(fn(grid.handle, _dev_ptr(x, dt, "x"), _dev_ptr(q2, dt, "q2"), x.shape[0], _dev_ptr(out, dt, "out"),
+             _dev_ptr(alphas_out, dt, "alphas_out"), _stream_handle(x.device)), "xfxq2_all_flavours_alphas")
     return out, alphas_out
 
 

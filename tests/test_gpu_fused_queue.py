@@ -67,6 +67,20 @@ def test_fused_alphas_bitwise_and_parity(full, synth):
     assert_parity(al, a, sa, np.zeros(a.shape, bool), RTOL_FP64, "fused alphas")
 
 
+def test_fused_alphas_fp32_bitwise(full, synth):
+    g, G, og = full
+    x, q2 = synth.queries_full(30_011, 25)
+    sx, sq = special_points(g)
+    x = np.concatenate([x, sx]).astype(np.float32)
+    q2 = np.concatenate([q2, sq]).astype(np.float32)
+    xd = torch.from_numpy(x).cuda()
+    qd = torch.from_numpy(q2).cuda()
+    out, al = P.xfxq2_all_flavours_alphas(G, xd, qd)
+    assert out.dtype == torch.float32 and al.dtype == torch.float32
+    assert np.array_equal(host(out), host(P.xfxq2_all_flavours(G, xd, qd)), equal_nan=True)
+    assert np.array_equal(host(al), host(P.alphas_q2(G, qd)), equal_nan=True)
+
+
 @pytest.mark.parametrize("n", [1, 31, 33, 1000, 65_537])
 def test_queue_heavy_batches(full, n):
     g, G, og = full

@@ -1,7 +1,9 @@
-"""Multi-rank path on CPU: two gloo ranks split a batch into contiguous
-blocks and sum their knot-value gradients; the result equals the gradient
-of the whole batch.  Per-rank gradients come from the oracle (no GPU here),
-so this checks the splitting and the exchange, not the kernel."""
+"""Multi-rank paths on CPU: two gloo ranks split a batch into contiguous
+blocks and sum their knot-value gradients (the result equals the gradient of
+the whole batch), and split a Monte Carlo run into event ranges and sum their
+weight sums (the result equals one run over all events).  Per-rank values
+come from the oracles (no GPU here), so this checks the splitting and the
+exchange, not the kernels."""
 import os
 import socket
 
@@ -11,7 +13,7 @@ import torch
 import torch.distributed as dist
 import torch.multiprocessing as mp
 
-from paper_2009_06635_gb300.sharding import allreduce_knot_gradient, shard_bounds
+from paper_2009_06635_gb300.sharding import allreduce_knot_gradient, allreduce_mc_sums, mc_event_range, shard_bounds
 
 
 def test_shard_bounds_cover_the_batch():
@@ -63,3 +65,42 @@ def test_two_rank_knot_gradient_allreduce():
         p.join(timeout=300)
         assert p.exitcode == 0
     assert q.get() is True
+
+
+def _mc_worker(rank, world, port, q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import oracle
+    from oracle import mc
+    from paper_2009_06635_gb300 import synthetic as S
+
+    g = S.grid_full()
+    og = oracle.OracleGrid(g)
+    cfg = (13000.0, 1e-6, 100.0, 2024)
+    per = 3000
+    first, count = mc_event_range(rank, per)
+    w = mc.weights(og, g.pids, *cfg, first, count, g.x_knots[-1])
+    tot = allreduce_mc_sums(mc.sums(w))
+    if rank == 0:
+        whole = mc.sums(mc.weights(og, g.pids, *cfg, 0, world * per, g.x_knots[-1]))
+        ok = all(abs(a - b) <= 1e-12 * whole[2] for a, b in zip(tot[:1] + tot[2:], whole[:1] + whole[2:]))
+        ok = ok and abs(tot[1] - whole[1]) <= 1e-12 * whole[1]
+        q.put(ok)
+    dist.destroy_process_group()
+
+
+def test_two_rank_mc_sums_allreduce():
+    assert mc_event_range(3, 10) == (30, 10)
+    assert allreduce_mc_sums([1.0, 2.0, 3.0]) == [1.0, 2.0, 3.0]  # no process group: unchanged
+    ctx = mp.get_context("spawn")
+    q = ctx.SimpleQueue()
+    port = _free_port()
+    procs = [ctx.Process(target=_mc_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=300)
+    assert all(p.exitcode == 0 for p in procs)
+    assert q.get() is True
+
