@@ -87,24 +87,20 @@ __device__ __forceinline__ double lowq_d(double f0, double f1, double rho, doubl
   return v;
 }
 
-__global__ void __launch_bounds__(kAdjThreads, 2)
-k_vjp(GridView g, const double *__restrict__ xa, const double *__restrict__ qa, const double *__restrict__ cot,
-      long long n, double *__restrict__ gx, double *__restrict__ gq, double *__restrict__ gv) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  long long *xkeys = reinterpret_cast<long long *>(smem);
-  long long *qkeys = reinterpret_cast<long long *>(smem + keys_bytes(g.nx, 8));
-  load_keys<double>(g, xkeys, 0);
-  load_keys<double>(g, qkeys, 1);
-  __syncthreads();
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
+// The whole vector-Jacobian product of one point: d/dx, d/dQ^2 into gx[p],
+// gq[p], knot-value contributions added to gv.
+__device__ __forceinline__ void vjp_point(const GridView &g, const long long *xkeys, const long long *qkeys,
+                                          long long p, const double *__restrict__ xa,
+                                          const double *__restrict__ qa, const double *__restrict__ cot,
+                                          double *__restrict__ gx, double *__restrict__ gq,
+                                          double *__restrict__ gv) {
     const double x = xa[p], q2 = qa[p];
     double lq;
     PointSites<double> ps = sites(g, xkeys, qkeys, x, q2, LogTabs{g.tlogtab, g.tloghtab}, lq);
     if (ps.cls == C_INVALID) {
       if (gx) gx[p] = NAN;
       if (gq) gq[p] = NAN;
-      continue;
+      return;
     }
     const bool lowx = ps.cls == C_LOWX || ps.cls == C_LOWX_HIGHQ || ps.cls == C_LOWX_LOWQ;
     const bool realq = ps.cls == C_IN || ps.cls == C_LOWX;
@@ -173,17 +169,20 @@ k_vjp(GridView g, const double *__restrict__ xa, const double *__restrict__ qa, 
           dx = fma(lam[a][b] * Ft[a][b], X[a].dpos, dx);
           dq = fma(lam[a][b] * Fu[a][b], Q[b].dpos, dq);
           if (gv) {
+            // zero tests on bit patterns (the FP64 pipe is the busy unit);
+            // c lam w_b folded once per row, then times each w_a
             const double m = c * lam[a][b];
-            if (m == 0.0) continue;
+            if ((__double_as_longlong(m) << 1) == 0) continue;
             for (int bb = 0; bb < 4; bb++) {
               const int row = Q[b].k0 + bb;
               const double wq = Q[b].w[bb];
-              if (wq == 0.0 || row < 0 || row >= g.nrows) continue;
+              if ((__double_as_longlong(wq) << 1) == 0 || row < 0 || row >= g.nrows) continue;
+              const double mq = m * wq;
               for (int aa = 0; aa < 4; aa++) {
                 const int col = X[a].k0 + aa;
-                const double w = X[a].w[aa] * wq;
-                if (w == 0.0 || col < 0 || col >= g.nx) continue;
-                atomicAdd(gv + ((size_t)row * g.nx + col) * g.nf + f, m * w);
+                const double wx = X[a].w[aa];
+                if ((__double_as_longlong(wx) << 1) == 0 || col < 0 || col >= g.nx) continue;
+                atomicAdd(gv + ((size_t)row * g.nx + col) * g.nf + f, mq * wx);
               }
             }
           }
@@ -193,6 +192,63 @@ k_vjp(GridView g, const double *__restrict__ xa, const double *__restrict__ qa, 
     }
     if (gx) gx[p] = sx;
     if (gq) gq[p] = sq;
+}
+
+// One warp per tile of 32 points, a lane per point.  Points that need a
+// continuation rule (found by integer range tests on the raw inputs) are
+// queued per warp and processed 32 at a time, so that a warp of in-grid
+// points never runs the continuation code (log, exp, division, four sites)
+// for a few lanes -- the FP64 pipe would pay for all 32.
+constexpr int kAdjWarps = kAdjThreads / 32;
+
+__global__ void __launch_bounds__(kAdjThreads, 1)
+k_vjp(GridView g, const double *__restrict__ xa, const double *__restrict__ qa, const double *__restrict__ cot,
+      long long n, double *__restrict__ gx, double *__restrict__ gq, double *__restrict__ gv) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ long long queue[kAdjWarps][64];
+  long long *xkeys = reinterpret_cast<long long *>(smem);
+  long long *qkeys = reinterpret_cast<long long *>(smem + keys_bytes(g.nx, 8));
+  load_keys<double>(g, xkeys, 0);
+  load_keys<double>(g, qkeys, 1);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  long long *Q = queue[warp];
+  const unsigned lt = (1u << lane) - 1u;
+  const long long kxlast = __double_as_longlong(g.xlast), kx0 = __double_as_longlong(g.x0);
+  const long long kqmin = __double_as_longlong(g.q2min), kqmax = __double_as_longlong(g.q2max);
+  int nq = 0;  // queued points (warp-uniform)
+  const long long ntiles = (n + 31) / 32, nwarps = (long long)gridDim.x * kAdjWarps;
+  long long tile = (long long)blockIdx.x * kAdjWarps + warp;
+  // one call site: each round either drains 32 queued points, or takes the
+  // in-grid points of the next tile (queueing its continuation points), or
+  // drains the rest of the queue at the end (every branch is warp-uniform)
+  while (true) {
+    long long pp = -1;
+    if (nq >= 32) {
+      nq -= 32;
+      pp = Q[nq + lane];
+    } else if (tile < ntiles) {
+      const long long p = tile * 32 + lane;
+      bool far = false;
+      if (p < n) {
+        const long long kx = __double_as_longlong(xa[p]), kq = __double_as_longlong(qa[p]);
+        const bool valid = kq > 0 && kq < 0x7FF0000000000000LL && kx > 0 && kx <= kxlast;
+        far = valid && (kx < kx0 || kq < kqmin || kq > kqmax);
+        if (!far) pp = p;
+      }
+      const unsigned fm = __ballot_sync(0xffffffffu, far);
+      if (far) Q[nq + __popc(fm & lt)] = p;
+      nq += __popc(fm);
+      tile += nwarps;
+    } else if (nq > 0) {
+      if (lane < nq) pp = Q[lane];
+      nq = 0;
+    } else {
+      break;
+    }
+    __syncwarp();
+    if (pp >= 0) vjp_point(g, xkeys, qkeys, pp, xa, qa, cot, gx, gq, gv);
+    __syncwarp();
   }
 }
 
@@ -211,7 +267,7 @@ extern "C" int xfxq2_all_flavours_vjp(const pdf_grid *grid, const double *x, con
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   size_t smem = keys_bytes(g.nx, 8) + keys_bytes(g.nrows, 8);
-  long long blocks = ((long long)n + kAdjThreads - 1) / kAdjThreads;
+  long long blocks = ((long long)n + kAdjThreads - 1) / kAdjThreads;  // one tile per warp at most
   long long cap = (long long)(sms > 0 ? sms : 1) * 8;
   if (blocks > cap) blocks = cap;
   k_vjp<<<(unsigned)blocks, kAdjThreads, smem, stream>>>(g, x, q2, cot, (long long)n, grad_x, grad_q2,
