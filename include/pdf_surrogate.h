@@ -75,7 +75,10 @@ PDF_API int pdf_surrogate_loss_grad(pdf_surrogate *s, const double *x, const dou
 PDF_API int pdf_surrogate_train(pdf_surrogate *s, const pdf_grid *grid, const double *x, const double *q2,
                                 size_t n, const pdf_train_config *cfg, double *final_loss, cudaStream_t stream);
 
-/* Network output for n points inside the grid: out [n][nflav] FP32. */
+/* Network output for n points inside the grid: out [n][nflav] FP32.
+ * Inference runs on the tensor cores with bounded waits; a wait that runs
+ * out (never expected) is reported by the next pdf_surrogate_build_error_map
+ * or pdf_surrogate_eval_fallback as PDF_ERR_CUDA. */
 PDF_API int pdf_surrogate_eval(const pdf_surrogate *s, const double *x, const double *q2, size_t n, float *out,
                                cudaStream_t stream);
 

@@ -1,6 +1,7 @@
 // surrogate.cu -- learned surrogate of the interpolator: a small MLP on BF16
-// tensor cores (mma.sync m16n8k16, FP32 accumulation), its training kernels,
-// and evaluation with fallback to the interpolator.
+// tensor cores with FP32 accumulation (inference: tcgen05 with TMEM
+// accumulators; training: mma.sync m16n8k16 tiles), its training kernels, and
+// evaluation with fallback to the interpolator.
 //
 // Network (for points inside the grid):
 //   z   = (2 (ln x - lx_lo)/(lx_hi - lx_lo) - 1,  2 (ln Q^2 - lq_lo)/(lq_hi - lq_lo) - 1)
@@ -49,7 +50,7 @@ struct SurrConst {
   float scale[SOUT];
   int nf;
   int target;          // PDF_SURR_ASINH or PDF_SURR_ENVELOPE
-  const float *envt;   // [nf][ENVN + 1] ln E_f at lx_lo + k (lx_hi - lx_lo) / ENVN
+  const float *envt;   // [ENVN + 1][SOUT] ln E_f at lx_lo + k (lx_hi - lx_lo) / ENVN, zero for f >= nf
 };
 
 // parameter offsets in the flat FP32 vector
@@ -94,8 +95,8 @@ __device__ __forceinline__ void point_z(const SurrConst &c, double x, double q2,
 __device__ __forceinline__ float envelope(const SurrConst &c, float z0, int f) {
   const float u = fminf(fmaxf((z0 + 1.f) * (0.5f * ENVN), 0.f), (float)ENVN);
   const int k = min((int)u, ENVN - 1);
-  const float *t = c.envt + f * (ENVN + 1) + k;
-  const float a = __ldg(t), b = __ldg(t + 1);
+  const float *t = c.envt + k * SOUT + f;
+  const float a = __ldg(t), b = __ldg(t + SOUT);
   return expf(a + (u - (float)k) * (b - a));
 }
 __device__ __forceinline__ float output_of(const SurrConst &c, float y, float z0, int f) {
@@ -311,126 +312,392 @@ __global__ void k_targets(SurrConst c, const double *x, const double *q2, const 
 }
 
 // ---------------------------------------------------------------------------
-// fused inference: weights in shared memory, 16 points per warp, activations
-// chained through registers (the m16n8 accumulator fragments of two adjacent
-// n-tiles are exactly the m16k16 A fragment of the next layer's k-step)
+// fused inference on the 5th-generation tensor cores (tcgen05, TMEM)
+//
+// One CTA per SM keeps every BF16 weight matrix in shared memory (K-major; the
+// K = 128 operands in 128-byte rows with the 16-byte chunks of row r permuted
+// by XOR with r % 8, the layout the tensor core reads at full rate; the
+// K = 32 and bias operands in plain 8 x 8 core matrices) and runs two groups
+// of eight warps.  A group owns a tile of 128 points, the rows of every
+// activation matrix, and 200 TMEM columns: the FP32 accumulator D (128), the
+// BF16 activations A of the next layer packed two per column (64, row = lane),
+// and a constant block (8) whose K columns 0..2 are 1.  Warp w of the group
+// reads lanes 32 (w % 4) .. + 31 and the column half w / 4.
+//
+// Per layer one thread issues K/16 tcgen05.mma with A from TMEM and B from
+// shared memory (M = 128, N = 128 or 16, K = 16, FP32 accumulation), then one
+// more K = 16 step against the constant block whose B columns hold the bias
+// as three BF16 parts (hi + mid + lo = the FP32 bias exactly), and commits to
+// the group's mbarrier.  Every thread then reads its 64 accumulator columns
+// (tcgen05.ld, the second half-load in flight while the first is used),
+// applies SiLU and writes the BF16 pairs back as the next layer's A
+// (tcgen05.st).  Activations never touch shared memory.  While one group's
+// products run on the tensor core, the other group's epilogue runs.
+//
+// The SiLU layers' weights and biases are held at half scale (exact in BF16),
+// so the accumulator is h = z / 2 and silu(z) = h + h tanh(h): one hardware
+// tanh and one FMA per element.  The next tile's x and Q^2 are loaded while
+// the current tile runs, and its envelope rows are copied (cp.async) into
+// shared memory at the start of the tile.  Outputs are staged in shared
+// memory and written as whole contiguous rows of the tile.  Every wait is
+// bounded: a wait that runs out sets the surrogate's error flag and the group
+// stops.
 // ---------------------------------------------------------------------------
-constexpr int IW = 8;                      // warps per block
-constexpr int LD1 = SIN + 8, LDH = SW + 8;  // padded smem row strides (bf16)
-constexpr size_t kInferSmem = (size_t)(128 * LD1 + 3 * 128 * LDH + 16 * LDH) * sizeof(bf16) +
-                              (4 * SW + SOUT) * sizeof(float);
+constexpr int TG = 2;                 // tile groups per CTA
+constexpr int kGW = 8;                // warps per group: four TMEM lane quarters x two column halves
+constexpr int kGT = 32 * kGW;         // threads per group
+constexpr int kTcThreads = kGT * TG;  // 512
+constexpr int kTmemGroup = 256;       // TMEM columns per group (200 used)
+constexpr int kTmemCols = kTmemGroup * TG;
+constexpr size_t kSW1 = 128 * 32 * 2, kSWh = 128 * 128 * 2, kSW5 = 16 * 128 * 2, kSWb = 128 * 16 * 2;
+constexpr size_t kSE = 128 * 2 * SOUT * sizeof(float);  // envelope rows (k, k + 1) of one tile
+constexpr size_t kSO = 128 * SOUT * sizeof(float);      // output staging of one tile
+constexpr size_t kOffWh = kSW1, kOffW5 = kOffWh + 3 * kSWh, kOffWb = kOffW5 + kSW5, kOffE = kOffWb + 5 * kSWb;
+constexpr size_t kOffO = kOffE + TG * kSE, kEnd = kOffO + TG * kSO;
+constexpr size_t kTcSmem = kEnd + 1024;  // + alignment of the base to 1 KB
+static_assert(kTcSmem + 1024 <= 227 * 1024, "inference shared memory");
+static_assert(kOffWh % 1024 == 0 && kOffW5 % 1024 == 0, "swizzled operands start on 1 KB boundaries");
+static_assert(kOffWb % 16 == 0 && kOffE % 16 == 0 && kOffO % 16 == 0, "16-byte aligned shared buffers");
 
-__device__ __forceinline__ void silu_pack(const float (*acc)[4], const float *bias, int tig, uint32_t (*afr)[4]) {
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+// element (r, k) of an R x K K-major matrix in 8 x 8 core matrices:
+// byte (r/8) (K/8) 128 + (k/8) 128 + (r%8) 16 + (k%8) 2
+__device__ __forceinline__ int cm_off(int r, int k, int K) {
+  return (r >> 3) * (K >> 3) * 64 + (k >> 3) * 64 + (r & 7) * 8 + (k & 7);
+}
+// element (r, k) of an R x 128 K-major matrix in 128-byte rows: K blocks of 64
+// elements (R x 128 bytes each), the 16-byte chunk j of row r at chunk j ^ (r % 8)
+__device__ __forceinline__ int sw_off(int r, int k, int R) {
+  return (k >> 6) * R * 64 + r * 64 + ((((k >> 3) & 7) ^ (r & 7)) << 3) + (k & 7);
+}
+// shared-memory matrix descriptor: start, leading (K) and stride (M/N) byte
+// offsets between core matrices, no swizzle, descriptor version 1 (bit 46)
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) |
+         ((uint64_t)1 << 46);
+}
+// the same for the 128-byte swizzled layout (mode 2 at bit 61): 1 KB between
+// groups of eight rows; a K step of 16 elements inside a row adds 32 bytes
+__device__ __forceinline__ uint64_t smem_desc_sw(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024u >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+// instruction descriptor, kind::f16: D F32 (bit 4), A and B BF16 (bits 7, 10),
+// both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+__device__ __forceinline__ uint32_t mma_idesc(int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+// D (TMEM) (+)= A (TMEM, BF16 pairs) B^T (shared memory)
+__device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a, uint64_t bdesc, uint32_t id, uint32_t acc) {
+  asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n"
+               ::"r"(d), "r"(a), "l"(bdesc), "r"(id), "r"(acc));
+}
+// the products of layer l: K/16 steps over the activations, then the bias step
+__device__ __forceinline__ void layer_mma(int l, uint32_t d, uint32_t a, uint32_t ones, uint32_t w1, uint32_t wh,
+                                          uint32_t w5, uint32_t wb) {
+  const uint32_t bias = smem_desc(wb + (uint32_t)l * (uint32_t)kSWb, 256);
+  if (l == 0) {
+    const uint32_t id = mma_idesc(128);
 #pragma unroll
-  for (int s = 0; s < 8; s++) {
-    const int c0 = 16 * s + 2 * tig, c1 = c0 + 8;
-    afr[s][0] = pack_bf16(silu_f(acc[2 * s][0] + bias[c0]), silu_f(acc[2 * s][1] + bias[c0 + 1]));
-    afr[s][1] = pack_bf16(silu_f(acc[2 * s][2] + bias[c0]), silu_f(acc[2 * s][3] + bias[c0 + 1]));
-    afr[s][2] = pack_bf16(silu_f(acc[2 * s + 1][0] + bias[c1]), silu_f(acc[2 * s + 1][1] + bias[c1 + 1]));
-    afr[s][3] = pack_bf16(silu_f(acc[2 * s + 1][2] + bias[c1]), silu_f(acc[2 * s + 1][3] + bias[c1 + 1]));
+    for (int s = 0; s < SIN / 16; s++) mma_ts(d, a + 8 * s, smem_desc(w1 + 256 * s, (SIN / 8) * 128), id, s > 0);
+    mma_ts(d, ones, bias, id, 1);
+  } else if (l < 4) {
+    const uint32_t id = mma_idesc(128), b = wh + (uint32_t)(l - 1) * (uint32_t)kSWh;
+#pragma unroll
+    for (int s = 0; s < SW / 16; s++)
+      mma_ts(d, a + 8 * s, smem_desc_sw(b + (uint32_t)(s >> 2) * 128 * 128 + (uint32_t)(s & 3) * 32), id, s > 0);
+    mma_ts(d, ones, bias, id, 1);
+  } else {
+    const uint32_t id = mma_idesc(16);
+#pragma unroll
+    for (int s = 0; s < SW / 16; s++)
+      mma_ts(d, a + 8 * s, smem_desc_sw(w5 + (uint32_t)(s >> 2) * 16 * 128 + (uint32_t)(s & 3) * 32), id, s > 0);
+    mma_ts(d, ones, bias, id, 1);
+  }
+}
+__device__ __forceinline__ void tc_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar));
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
+  uint32_t done = 0;
+  for (int it = 0; it < (1 << 24) && !done; it++)
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(done) : "r"(mbar), "r"(phase));
+  return done != 0;
+}
+// 32 consecutive FP32 columns of this warp's 32 TMEM lanes; the registers are
+// valid only after tmem_wait32 on the same array
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t *r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+// waits for every outstanding tcgen05.ld of the thread; the operands tie the
+// wait to the registers of r so that no use of them moves above it
+__device__ __forceinline__ void tmem_wait32(uint32_t *r) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                 "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                 "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                 "+r"(r[29]), "+r"(r[30]), "+r"(r[31]));
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]));
+#pragma unroll
+  for (int j = 0; j < 8; j++) v[j] = __uint_as_float(r[j]);
+}
+// stores to this warp's 32 TMEM lanes (one register per column); complete after tcgen05.wait::st
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t *r) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+               ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+               "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]));
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t *r) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+               ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]));
+}
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint32_t *r) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};"
+               ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]));
+}
+// the group's threads: their TMEM writes ordered before the tensor core's reads, then a barrier
+__device__ __forceinline__ void group_sync(int g) {
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(kGT));
+}
+// barrier of the group that also returns whether v held on any of its threads
+__device__ __forceinline__ bool group_any(int g, bool v) {
+  uint32_t r;
+  asm volatile("{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.or.pred q, %2, %3, p;\nselp.u32 %0, 1, 0, q;\n}\n"
+               : "=r"(r) : "r"((uint32_t)v), "r"(1 + g), "r"(kGT));
+  return r != 0;
+}
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// silu(2h) = h + h tanh(h) of 32 accumulator columns (h = z / 2, bias included),
+// packed in place as 16 BF16 pairs (r[0..15])
+__device__ __forceinline__ void silu_pack(uint32_t *r) {
+#pragma unroll
+  for (int j = 0; j < 16; j++) {
+    const float h0 = __uint_as_float(r[2 * j]), h1 = __uint_as_float(r[2 * j + 1]);
+    r[j] = pack_bf16(fmaf(h0, tanh_fast(h0), h0), fmaf(h1, tanh_fast(h1), h1));
   }
 }
 
-__global__ void __launch_bounds__(32 * IW, 1)
+__global__ void __launch_bounds__(kTcThreads, 1)
 k_infer(SurrConst c, const bf16 *__restrict__ wg, const float *__restrict__ params, Layout L,
         const double *__restrict__ xa, const double *__restrict__ qa, long long n, float *__restrict__ outf,
         double *__restrict__ outd, const unsigned char *__restrict__ mask, unsigned int *nfb,
-        unsigned int *fb_idx) {
-  extern __shared__ __align__(16) unsigned char smem[];
+        unsigned int *fb_idx, int *err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) unsigned long long mbar[TG];
+  __shared__ uint32_t tbase;
+  __shared__ float sfreq[SNQ][2], sscale[SOUT];  // indexed by the warp's half: kept out of the parameter space
+  unsigned char *smem = smem_raw + (((smem_u32(smem_raw) + 1023u) & ~1023u) - smem_u32(smem_raw));
   bf16 *W1 = reinterpret_cast<bf16 *>(smem);
-  bf16 *Wh = W1 + 128 * LD1;  // three [128][LDH]
-  bf16 *W5 = Wh + 3 * 128 * LDH;
-  float *bs = reinterpret_cast<float *>(W5 + 16 * LDH);  // b1..b4 [4][128], b5 [16]
-  for (int i = threadIdx.x; i < 128 * SIN; i += blockDim.x) W1[(i / SIN) * LD1 + i % SIN] = wg[wbf_off(0) + i];
+  bf16 *Wh = reinterpret_cast<bf16 *>(smem + kOffWh);
+  bf16 *W5 = reinterpret_cast<bf16 *>(smem + kOffW5);
+  bf16 *Wb = reinterpret_cast<bf16 *>(smem + kOffWb);  // bias columns of the five layers
+  const bf16 half_w = __float2bfloat16(0.5f);
+  for (int i = threadIdx.x; i < 128 * SIN; i += kTcThreads)
+    W1[cm_off(i / SIN, i % SIN, SIN)] = __hmul(wg[wbf_off(0) + i], half_w);
   for (int l = 0; l < 3; l++)
-    for (int i = threadIdx.x; i < 128 * SW; i += blockDim.x)
-      Wh[l * 128 * LDH + (i / SW) * LDH + i % SW] = wg[wbf_off(l + 1) + i];
-  for (int i = threadIdx.x; i < 16 * SW; i += blockDim.x) W5[(i / SW) * LDH + i % SW] = wg[wbf_off(4) + i];
-  for (int i = threadIdx.x; i < 4 * SW; i += blockDim.x) bs[i] = params[L.b[i / SW] + i % SW];
-  for (int i = threadIdx.x; i < SOUT; i += blockDim.x) bs[4 * SW + i] = i < c.nf ? params[L.b[4] + i] : 0.f;
+    for (int i = threadIdx.x; i < 128 * SW; i += kTcThreads)
+      Wh[l * 128 * SW + sw_off(i / SW, i % SW, 128)] = __hmul(wg[wbf_off(l + 1) + i], half_w);
+  for (int i = threadIdx.x; i < 16 * SW; i += kTcThreads) W5[sw_off(i / SW, i % SW, 16)] = wg[wbf_off(4) + i];
+  // bias b (b / 2 for the SiLU layers) as three BF16 parts hi + mid + lo = b exactly, in K columns 0..2
+#pragma unroll
+  for (int l = 0; l < 5; l++) {
+    const int rows = l < 4 ? SW : SOUT;
+    for (int i = threadIdx.x; i < rows * 16; i += kTcThreads) {
+      const int r = i >> 4, k = i & 15;
+      const float b = l < 4 ? 0.5f * params[L.b[l] + r] : (r < c.nf ? params[L.b[4] + r] : 0.f);
+      const bf16 hi = __float2bfloat16_rn(b);
+      const float r1 = b - __bfloat162float(hi);
+      const bf16 mid = __float2bfloat16_rn(r1);
+      const bf16 lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
+      Wb[l * 128 * 16 + cm_off(r, k, 16)] = k == 0 ? hi : k == 1 ? mid : k == 2 ? lo : __float2bfloat16(0.f);
+    }
+  }
+  if (threadIdx.x < 2 * SNQ) sfreq[threadIdx.x >> 1][threadIdx.x & 1] = c.freq[threadIdx.x >> 1][threadIdx.x & 1];
+  if (threadIdx.x < SOUT) sscale[threadIdx.x] = c.scale[threadIdx.x];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x < TG) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[threadIdx.x])));
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tbase)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;");
+  asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
 
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int gid = lane >> 2, tig = lane & 3;
-  const long long stride = (long long)gridDim.x * IW * 16;
-  for (long long p0 = ((long long)blockIdx.x * IW + warp) * 16; p0 < n; p0 += stride) {
-    // rows gid and gid + 8 of this 16-point tile
-    long long pr[2] = {p0 + gid, p0 + gid + 8};
-    float z0[2], z1[2];
-    bool use[2];
-    for (int h = 0; h < 2; h++) {
-      const bool in = pr[h] < n;
-      double x = in ? xa[pr[h]] : 0.5, q = in ? qa[pr[h]] : 10.0;
-      point_z(c, x, q, z0[h], z1[h]);
-      use[h] = in;
-      if (mask) {  // fallback: outside the grid, or on a tile the map rejects
-        bool inside = z0[h] >= -1.f && z0[h] <= 1.f && z1[h] >= -1.f && z1[h] <= 1.f && x > 0.0 && q > 0.0;
-        int tx = min(MAPN - 1, max(0, (int)((z0[h] + 1.f) * 0.5f * MAPN)));
-        int tq = min(MAPN - 1, max(0, (int)((z1[h] + 1.f) * 0.5f * MAPN)));
-        bool ok = inside && mask[tq * MAPN + tx];
-        if (in && !ok && tig == 0) fb_idx[atomicAdd(nfb, 1u)] = (unsigned int)pr[h];
-        use[h] = in && ok;
-        if (!inside) { z0[h] = 0.f; z1[h] = 0.f; }
-      }
+  const int g = warp / kGW, gw = warp % kGW, half = gw >> 2;  // group, warp in group, column half
+  const int t = 32 * (gw & 3) + lane;                          // row of the tile
+  const int gt = threadIdx.x - g * kGT;                        // thread in group
+  const int nf = c.nf;
+  float *E = reinterpret_cast<float *>(smem + kOffE + g * kSE);  // [rows][8 chunks of 4], chunk j at j ^ (t % 8)
+  float *O = reinterpret_cast<float *>(smem + kOffO + g * kSO);  // [rows][nf]
+  const uint32_t mb = smem_u32(&mbar[g]);
+  const uint32_t e_row = smem_u32(E + t * 2 * SOUT);
+  const uint32_t tg = tbase + (uint32_t)(g * kTmemGroup);                // the group's columns
+  const uint32_t tD = tg, tA = tg + 128, tOne = tg + 192;               // accumulator, activations, ones
+  const uint32_t lanes = (uint32_t)(32 * (gw & 3)) << 16;               // this warp's lanes
+  const uint32_t w1 = smem_u32(W1), wh = smem_u32(Wh), w5 = smem_u32(W5), wb = smem_u32(Wb);
+  if (half == 0) {  // the constant K columns (1, 1, 1, 0, ...) that meet the bias parts
+    uint32_t o[8] = {0x3F803F80u, 0x00003F80u, 0u, 0u, 0u, 0u, 0u, 0u};
+    tmem_st8(tOne + lanes, o);
+    asm volatile("tcgen05.wait::st.sync.aligned;");
+  }
+  uint32_t phase = 0;
+  const long long ntiles = (n + 127) / 128, tstride = (long long)gridDim.x * TG;
+  long long tile = (long long)blockIdx.x * TG + g;
+  double xn = 0.5, qn = 10.0;  // this thread's point of the next tile (defaults for rows past n)
+  if (tile * 128 + t < n) { xn = xa[tile * 128 + t]; qn = qa[tile * 128 + t]; }
+  for (; tile < ntiles; tile += tstride) {
+    const long long p0 = tile * 128, p = p0 + t;
+    const bool in = p < n;
+    const double x = xn, q = qn;
+    {
+      const long long pn = p + tstride * 128;
+      xn = 0.5; qn = 10.0;
+      if (pn < n) { xn = xa[pn]; qn = qa[pn]; }
     }
-    // layer 1 A fragments: features k = 16 s + 2 tig + {0,1} (+8)
-    uint32_t f1[2][4];
-#pragma unroll
-    for (int s = 0; s < 2; s++) {
-      const int k0 = 16 * s + 2 * tig, k1 = k0 + 8;
-      f1[s][0] = pack_bf16(feature(c, z0[0], z1[0], k0), feature(c, z0[0], z1[0], k0 + 1));
-      f1[s][1] = pack_bf16(feature(c, z0[1], z1[1], k0), feature(c, z0[1], z1[1], k0 + 1));
-      f1[s][2] = pack_bf16(feature(c, z0[0], z1[0], k1), feature(c, z0[0], z1[0], k1 + 1));
-      f1[s][3] = pack_bf16(feature(c, z0[1], z1[1], k1), feature(c, z0[1], z1[1], k1 + 1));
-    }
-    float acc[16][4];
-#pragma unroll
-    for (int j = 0; j < 16; j++) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-#pragma unroll
-    for (int s = 0; s < 2; s++)
-#pragma unroll
-      for (int j = 0; j < 16; j++) {
-        const bf16 *w = W1 + (8 * j + gid) * LD1 + 16 * s + 2 * tig;
-        mma16816(acc[j], f1[s], *reinterpret_cast<const uint32_t *>(w), *reinterpret_cast<const uint32_t *>(w + 8));
-      }
-    uint32_t afr[8][4];
-    silu_pack(acc, bs, tig, afr);
-    for (int l = 0; l < 3; l++) {
-      const bf16 *Wl = Wh + l * 128 * LDH;
-#pragma unroll
-      for (int j = 0; j < 16; j++) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-#pragma unroll
-      for (int s = 0; s < 8; s++)
-#pragma unroll
-        for (int j = 0; j < 16; j++) {
-          const bf16 *w = Wl + (8 * j + gid) * LDH + 16 * s + 2 * tig;
-          mma16816(acc[j], afr[s], *reinterpret_cast<const uint32_t *>(w),
-                   *reinterpret_cast<const uint32_t *>(w + 8));
-        }
-      silu_pack(acc, bs + (l + 1) * SW, tig, afr);
-    }
-    float y[2][4];
-#pragma unroll
-    for (int j = 0; j < 2; j++) y[j][0] = y[j][1] = y[j][2] = y[j][3] = 0.f;
-#pragma unroll
-    for (int s = 0; s < 8; s++)
+    float z0, z1;
+    point_z(c, x, q, z0, z1);
+    // envelope rows k and k + 1 of this point, this half's eight flavours (chunks 2 half, 2 half + 1)
+    const float u = fminf(fmaxf((z0 + 1.f) * (0.5f * ENVN), 0.f), (float)ENVN);
+    const int k = min((int)u, ENVN - 1);
+    const float fr = u - (float)k;
+    if (c.target == PDF_SURR_ENVELOPE) {
+      const float *src = c.envt + (size_t)k * SOUT + 8 * half;
 #pragma unroll
       for (int j = 0; j < 2; j++) {
-        const bf16 *w = W5 + (8 * j + gid) * LDH + 16 * s + 2 * tig;
-        mma16816(y[j], afr[s], *reinterpret_cast<const uint32_t *>(w), *reinterpret_cast<const uint32_t *>(w + 8));
+        cp_async16(e_row + (uint32_t)(((2 * half + j) ^ (t & 7)) * 16), src + 4 * j);
+        cp_async16(e_row + (uint32_t)(((4 + 2 * half + j) ^ (t & 7)) * 16), src + SOUT + 4 * j);
       }
-    // outputs: fragment e of n-tile j is row gid + 8 (e >= 2), flavour 8 j + 2 tig + (e & 1)
-#pragma unroll
-    for (int j = 0; j < 2; j++)
-#pragma unroll
-      for (int e = 0; e < 4; e++) {
-        const int h = e >> 1, f = 8 * j + 2 * tig + (e & 1);
-        if (!use[h] || f >= c.nf) continue;
-        const float v = output_of(c, y[j][e] + bs[4 * SW + f], z0[h], f);
-        if (outf) outf[pr[h] * c.nf + f] = v;
-        if (outd) outd[pr[h] * c.nf + f] = (double)v;
+    }
+    if (mask) {  // fallback: outside the grid, or on a tile the map rejects
+      const bool inside = z0 >= -1.f && z0 <= 1.f && z1 >= -1.f && z1 <= 1.f && x > 0.0 && q > 0.0;
+      const int tx = min(MAPN - 1, max(0, (int)((z0 + 1.f) * 0.5f * MAPN)));
+      const int tq = min(MAPN - 1, max(0, (int)((z1 + 1.f) * 0.5f * MAPN)));
+      const bool bad = in && !(inside && mask[tq * MAPN + tx]);
+      if (half == 0) {  // one record per point
+        const unsigned int bb = __ballot_sync(0xffffffffu, bad);
+        unsigned int base = 0;
+        if (bb && lane == 0) base = atomicAdd(nfb, (unsigned int)__popc(bb));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (bad) fb_idx[base + __popc(bb & ((1u << lane) - 1u))] = (unsigned int)p;
       }
+      if (!inside) { z0 = 0.f; z1 = 0.f; }
+    }
+    {  // features: this half's eight angles a_j; sin into K columns j, cos into 16 + j (BF16 pairs)
+      const int j0 = 8 * half;
+      float sv[8], cv[8];
+#pragma unroll
+      for (int j = 0; j < 8; j++) sincospif(sfreq[j0 + j][0] * z0 + sfreq[j0 + j][1] * z1, &sv[j], &cv[j]);
+      uint32_t a[4], b[4];
+#pragma unroll
+      for (int j = 0; j < 4; j++) { a[j] = pack_bf16(sv[2 * j], sv[2 * j + 1]); b[j] = pack_bf16(cv[2 * j], cv[2 * j + 1]); }
+      tmem_st4(tA + lanes + (uint32_t)(4 * half), a);
+      tmem_st4(tA + lanes + (uint32_t)(8 + 4 * half), b);
+      asm volatile("tcgen05.wait::st.sync.aligned;");
+    }
+    bool ok = true;
+    for (int l = 0; l < 5; l++) {
+      group_sync(g);
+      if (gt == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        layer_mma(l, tD, tA, tOne, w1, wh, w5, wb);
+        tc_commit(mb);
+      }
+      const bool done = mbar_wait(mb, phase);
+      phase ^= 1u;
+      if (group_any(g, !done)) { ok = false; break; }  // every thread of the group leaves together
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      if (l < 4) {  // SiLU of this half's 64 columns into the next layer's K columns (BF16 pairs)
+        const uint32_t c0 = 64 * half;
+        uint32_t r0[32], r1[32];
+        tmem_ld32(tD + lanes + c0, r0);
+        tmem_wait32(r0);
+        tmem_ld32(tD + lanes + c0 + 32, r1);
+        silu_pack(r0);
+        tmem_st16(tA + lanes + c0 / 2, r0);
+        tmem_wait32(r1);
+        silu_pack(r1);
+        tmem_st16(tA + lanes + c0 / 2 + 16, r1);
+        asm volatile("tcgen05.wait::st.sync.aligned;");
+      } else {  // outputs of this half's eight flavours, staged as whole rows
+        float v[8];
+        tmem_ld8(tD + lanes + 8 * half, v);
+        float o[8];
+        if (c.target == PDF_SURR_ENVELOPE) {
+          cp_async_wait_all();
+          const float *er = E + t * 2 * SOUT;
+          const float4 a0 = *reinterpret_cast<const float4 *>(er + (((2 * half) ^ (t & 7)) << 2));
+          const float4 a1 = *reinterpret_cast<const float4 *>(er + (((2 * half + 1) ^ (t & 7)) << 2));
+          const float4 b0 = *reinterpret_cast<const float4 *>(er + (((4 + 2 * half) ^ (t & 7)) << 2));
+          const float4 b1 = *reinterpret_cast<const float4 *>(er + (((5 + 2 * half) ^ (t & 7)) << 2));
+          const float ea[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+          const float eb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+          for (int i = 0; i < 8; i++) o[i] = expf(ea[i] + fr * (eb[i] - ea[i])) * v[i];
+        } else {
+#pragma unroll
+          for (int i = 0; i < 8; i++) o[i] = sscale[8 * half + i] * sinhf(v[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < 8; i++)
+          if (8 * half + i < nf) O[t * nf + 8 * half + i] = o[i];
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(kGT));
+        const long long rows = min(128LL, n - p0);
+        const int cnt = (int)rows * nf;
+        if (outf) {
+          float *dst = outf + p0 * nf;
+          int i0 = 0;
+          if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+            for (int i = gt; i < cnt / 4; i += kGT) __stcs(reinterpret_cast<float4 *>(dst) + i, reinterpret_cast<const float4 *>(O)[i]);
+            i0 = cnt & ~3;
+          }
+          for (int i = i0 + gt; i < cnt; i += kGT) __stcs(dst + i, O[i]);
+        }
+        if (outd) {
+          double *dst = outd + p0 * nf;
+          int i0 = 0;
+          if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+            for (int i = gt; i < cnt / 2; i += kGT) {
+              const float2 w = reinterpret_cast<const float2 *>(O)[i];
+              __stcs(reinterpret_cast<double2 *>(dst) + i, make_double2((double)w.x, (double)w.y));
+            }
+            i0 = cnt & ~1;
+          }
+          for (int i = i0 + gt; i < cnt; i += kGT) __stcs(dst + i, (double)O[i]);
+        }
+      }
+    }
+    if (!ok) {
+      if (gt == 0) atomicExch(err, 1);
+      break;
+    }
   }
+  cp_async_wait_all();
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kTmemCols));
 }
 
 // error map: per tile the largest |s - v| / max(|v|, c_f) over points and flavours
@@ -496,6 +763,7 @@ struct pdf_surrogate {
   // error map and fallback
   unsigned char *mask;
   unsigned int *tile_bits, *tile_cnt, *nfb, *fb_idx;
+  int *tc_err;  // set by the inference kernel when a tensor-core wait ran out
   double *fb_x, *fb_q, *fb_out;
   size_t fb_cap;
   bool has_map;
@@ -639,7 +907,7 @@ extern "C" int pdf_surrogate_create_ex(const pdf_grid *grid, const float *params
   std::vector<double> xk(v.nx);
   rc = cuda_err(cudaMemcpy(xk.data(), v.xk, v.nx * sizeof(double), cudaMemcpyDeviceToHost), "pdf_surrogate_create");
   if (rc) { delete s; return rc; }
-  std::vector<float> envt((size_t)nf * (ENVN + 1));
+  std::vector<float> envt((size_t)(ENVN + 1) * SOUT, 0.f);
   {
     std::vector<double> lx(v.nx), le(v.nx);
     for (int i = 0; i < v.nx; i++) lx[i] = log(xk[i]);
@@ -654,7 +922,7 @@ extern "C" int pdf_surrogate_create_ex(const pdf_grid *grid, const float *params
         int i = 0;
         while (i + 2 < v.nx && lx[i + 1] <= l) i++;
         const double t = fmin(fmax((l - lx[i]) / (lx[i + 1] - lx[i]), 0.0), 1.0);
-        envt[(size_t)f * (ENVN + 1) + k] = (float)(le[i] + t * (le[i + 1] - le[i]));
+        envt[(size_t)k * SOUT + f] = (float)(le[i] + t * (le[i + 1] - le[i]));
       }
     }
   }
@@ -685,6 +953,7 @@ extern "C" int pdf_surrogate_create_ex(const pdf_grid *grid, const float *params
   if (!rc) rc = s->alloc(&s->tile_bits, MAPN * MAPN);
   if (!rc) rc = s->alloc(&s->tile_cnt, MAPN * MAPN);
   if (!rc) rc = s->alloc(&s->nfb, 1);
+  if (!rc) rc = s->alloc(&s->tc_err, 1);
   if (rc) { pdf_surrogate_free(s); return rc; }
   cudaMemcpy(s->params, params, P * sizeof(float), cudaMemcpyHostToDevice);
   cudaMemcpy(s->scale_d, s->c.scale, SOUT * sizeof(float), cudaMemcpyHostToDevice);
@@ -693,6 +962,7 @@ extern "C" int pdf_surrogate_create_ex(const pdf_grid *grid, const float *params
   cudaMemset(s->am, 0, P * sizeof(float));
   cudaMemset(s->av, 0, P * sizeof(float));
   cudaMemset(s->mask, 0, MAPN * MAPN);
+  cudaMemset(s->tc_err, 0, sizeof(int));
   cast_weights(s, 0);
   rc = cuda_err(cudaDeviceSynchronize(), "pdf_surrogate_create");
   if (rc) { pdf_surrogate_free(s); return rc; }
@@ -787,21 +1057,25 @@ extern "C" int pdf_surrogate_train(pdf_surrogate *s, const pdf_grid *grid, const
   return check_launch("pdf_surrogate_train");
 }
 
+// After a synchronisation: did an inference kernel give up on a tensor-core wait?
+static int check_tc(const pdf_surrogate *s, const char *what) {
+  int e = 0;
+  int rc = cuda_err(cudaMemcpy(&e, s->tc_err, sizeof(int), cudaMemcpyDeviceToHost), what);
+  if (!rc && e) rc = set_error(PDF_ERR_CUDA, "%s: a tensor-core wait in the inference kernel ran out", what);
+  return rc;
+}
+
 static int launch_infer(const pdf_surrogate *s, const double *x, const double *q2, size_t n, float *outf,
                         double *outd, const unsigned char *mask, unsigned int *nfb, unsigned int *idx,
                         cudaStream_t st) {
-  static bool configured = false;
-  if (!configured) {
-    cudaFuncSetAttribute(k_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kInferSmem);
-    configured = true;
-  }
+  cudaFuncSetAttribute(k_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
-  long long tiles = ((long long)n + 15) / 16;
-  long long blocks = (tiles + IW - 1) / IW;
+  long long tiles = ((long long)n + 127) / 128;
+  long long blocks = (tiles + TG - 1) / TG;
   if (blocks > sms) blocks = sms;
-  k_infer<<<(unsigned)blocks, 32 * IW, kInferSmem, st>>>(s->c, s->wbf, s->params, s->L, x, q2, (long long)n, outf,
-                                                          outd, mask, nfb, idx);
+  k_infer<<<(unsigned)blocks, kTcThreads, kTcSmem, st>>>(s->c, s->wbf, s->params, s->L, x, q2, (long long)n, outf,
+                                                          outd, mask, nfb, idx, s->tc_err);
   return check_launch("surrogate inference");
 }
 
@@ -837,6 +1111,7 @@ extern "C" int pdf_surrogate_build_error_map(pdf_surrogate *s, const pdf_grid *g
   if (!rc) rc = cuda_err(cudaMemcpy(m.data(), s->mask, m.size(), cudaMemcpyDeviceToHost), "error map");
   cudaFree(sv);
   cudaFree(iv);
+  if (!rc) rc = check_tc(s, "pdf_surrogate_build_error_map");
   if (rc) return rc;
   // stats: [tiles accepted, tiles with samples, largest error on sampled tiles, median tile error]
   int ok = 0, sampled = 0;
@@ -891,6 +1166,7 @@ extern "C" int pdf_surrogate_eval_fallback(pdf_surrogate *s, const pdf_grid *gri
   unsigned int m = 0;
   rc = cuda_err(cudaMemcpyAsync(&m, s->nfb, sizeof(m), cudaMemcpyDeviceToHost, st), "fallback count");
   if (!rc) rc = cuda_err(cudaStreamSynchronize(st), "fallback count");
+  if (!rc) rc = check_tc(s, "pdf_surrogate_eval_fallback");
   if (rc) return rc;
   if (m > 0) {
     k_gather<<<(m + 255) / 256, 256, 0, st>>>(x, q2, s->fb_idx, m, s->fb_x, s->fb_q);
