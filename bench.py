@@ -43,7 +43,7 @@ SURR_TRAIN, SURR_VAL, SURR_INFER = 20_000_000, 1_000_000, 100_000_000
 # points, PDFFlow on a TITAN V or RTX 2080 Ti (system P1), seconds
 TABLE2 = {10: 0.07, 50: 0.35, 100: 0.69, 200: 1.46, 300: 1.29, 400: 1.69}
 SURR_FLOPS_PER_POINT = 2 * (32 * 128 + 3 * 128 * 128 + 128 * 16)  # padded output layer
-SURR_SFU_PER_POINT = 4 * 128 + 32  # tanh per SiLU, sin/cos per feature
+SURR_SFU_PER_POINT = 4 * 128  # one hardware tanh per SiLU (features use sincospif on the FMA pipe)
 WORKLOAD = ("three Q subgrids (12/15/25 Q knots split at Q = 1.51 and 4.92 GeV, Q in [1, 1e5] GeV), "
             "196 x knots in [1e-9, 1], 13 flavours; 1e7 queries per rank, x log-uniform in [1e-10, 1], "
             "Q log-uniform in [1, 2e5] GeV (15% outside the grid); all flavours + alpha_s per point")
@@ -458,6 +458,19 @@ def our_arm(args):
         else:
             P.xfxq2_all_flavours_alphas(G, xd, qd, out=out, alphas_out=aout)
 
+    if args.only == "surrogate":  # inference alone on in-grid points (its cost does not depend on training)
+        from paper_2009_06635_gb300 import synthetic as S
+        from paper_2009_06635_gb300.surrogate import Surrogate
+
+        s = Surrogate(G, max_batch=1024, target="envelope")
+        xi, qi = S.ingrid_samples(g, n, 8 + 1000 * rank)
+        xid, qid = torch.from_numpy(xi).to(dev), torch.from_numpy(qi).to(dev)
+        so = torch.empty((n, nf), dtype=torch.float32, device=dev)
+        ms = run_timed(lambda: s.eval(xid, qid, out=so), args.steps, args.warmup, world, sync)
+        if rank == 0:
+            print(json.dumps({"only": args.only, "points": n, "ms_per_step": ms, "evals_per_s": n * nf / (ms * 1e-3),
+                              "tflops": SURR_FLOPS_PER_POINT * n / (ms * 1e-3) / 1e12}))
+        return 0
     if args.only:
         if args.only == "fp64":
             fn = lambda: P.xfxq2_all_flavours_alphas(G, xd, qd, out=out, alphas_out=aout)  # noqa: E731
@@ -645,7 +658,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-members", action="store_true")
-    ap.add_argument("--only", choices=["fp64", "fp32"], default=None,
+    ap.add_argument("--only", choices=["fp64", "fp32", "surrogate"], default=None,
                     help="run only that path's step (a small case for profiling); prints its timing")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

@@ -395,7 +395,7 @@ __device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a, uint64_t bdesc, u
 // the products of layer l: K/16 steps over the activations, then the bias step
 __device__ __forceinline__ void layer_mma(int l, uint32_t d, uint32_t a, uint32_t ones, uint32_t w1, uint32_t wh,
                                           uint32_t w5, uint32_t wb) {
-  const uint32_t bias = smem_desc(wb + (uint32_t)l * (uint32_t)kSWb, 256);
+  const uint64_t bias = smem_desc(wb + (uint32_t)l * (uint32_t)kSWb, 256);
   if (l == 0) {
     const uint32_t id = mma_idesc(128);
 #pragma unroll

@@ -67,6 +67,37 @@ def test_fused_inference_matches_oracle(setup, synth):
     assert np.quantile(dy, 0.99) < 2e-2 and dy.max() < 1e-1, (np.quantile(dy, 0.99), dy.max())
 
 
+@pytest.mark.parametrize("target", ["asinh", "envelope"])
+def test_fused_inference_with_biases_matches_oracle(setup, synth, target):
+    """Every layer with its own random bias per output row (the initial
+    network has zero biases): the fused kernel's bias path and row mapping
+    against the oracle."""
+    from oracle import mlp
+
+    g, G, Surrogate, params, freq, scale, bounds, og = setup
+    p = params.astype(np.float64).copy()
+    rng = np.random.default_rng(41)
+    k = 0
+    for (o, i) in [(128, 32), (128, 128), (128, 128), (128, 128), (g.nflav, 128)]:
+        k += o * i
+        p[k:k + o] = rng.uniform(-1.0, 1.0, o)
+        k += o
+    assert k == p.size
+    p32 = p.astype(np.float32)
+    s = Surrogate(G, p32, freq, max_batch=1024, target=target)
+    x, q2 = synth.ingrid_samples(g, 4001, 23)
+    out = s.eval(dev(x), dev(q2)).cpu().numpy().astype(np.float64)
+    if target == "envelope":
+        env = mlp.envelope(mlp.envelope_table(g.x_knots, g.values, bounds), x, bounds)
+        want = mlp.predict(p32.astype(np.float64), x, q2, scale, freq.astype(np.float64), bounds, g.nflav, bf=True,
+                           env=env)
+        dy = np.abs(out - want) / env
+    else:
+        want = mlp.predict(p32.astype(np.float64), x, q2, scale, freq.astype(np.float64), bounds, g.nflav, bf=True)
+        dy = np.abs(np.arcsinh(out / scale) - np.arcsinh(want / scale))
+    assert np.quantile(dy, 0.99) < 2e-2 and dy.max() < 1e-1, (np.quantile(dy, 0.99), dy.max())
+
+
 def test_training_error_map_and_fallback(setup, synth):
     g, G, Surrogate, params, freq, scale, bounds, og = setup
     s = Surrogate(G, params, freq, max_batch=8192)
