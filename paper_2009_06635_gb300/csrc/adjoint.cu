@@ -57,75 +57,94 @@ __device__ __forceinline__ void patch_d(const double *b, const Site64 &X, const 
   }
 }
 
-// Pair rule with its partial derivatives in g0, g1, p.
-__device__ __forceinline__ double pair_d(double g0, double g1, double p, double &d0, double &d1, double &dp) {
-  if (g0 > 0.0 && g1 > 0.0) {
-    double lr = log(g1 / g0);
-    double v = g0 * exp(p * lr);
-    d0 = v * (1.0 - p) / g0;
-    d1 = v * p / g1;
-    dp = v * lr;
-    return v;
+// A continuation rule and its partial derivatives.  Both rules are of the
+// log form v = f0 exp(a ln(f1/f0) + b): the pair rule with a = p, b = 0 (and
+// v = f0 + (f1 - f0) p when f0 or f1 is not positive), the low-Q^2 rule with
+// a = rho lr / ln1.01, b = (1 - rho) lr (a = 0, b = lr when f0 or f1 is not
+// positive: gamma = 1).  Then dv/df0 = e (1 - a), dv/df1 = e a / r with
+// e = exp(a ln r + b), r = f1/f0, and dv/dpar = dv/da da/dpar + dv/db db/dpar
+// for the rule's parameter (p, or rho with lr = ln rho).  The same
+// table-driven logarithm, exponential and reciprocal as the evaluation.
+struct RuleD {
+  double v, d0, d1, dpar;
+};
+__device__ __forceinline__ RuleD rule_d(double f0, double f1, double p, bool lowq, double rho, double lr,
+                                        double irho, double iL, LogTabs LT, const double *ET) {
+  RuleD R;
+  const bool pos = __double_as_longlong(f0) > 0 && __double_as_longlong(f1) > 0;
+  double r = 1.0, lnr = 0.0;
+  if (pos) {
+    r = ddiv(f1, f0);
+    lnr = tlog(r, LT);
   }
-  d0 = 1.0 - p;
-  d1 = p;
-  dp = g1 - g0;
-  return g0 + (g1 - g0) * p;
-}
-
-// Low-Q^2 rule with its partial derivatives in f0, f1, rho.
-__device__ __forceinline__ double lowq_d(double f0, double f1, double rho, double lr, double L, double &d0,
-                                         double &d1, double &drho) {
-  bool pos = f0 > 0.0 && f1 > 0.0;
-  double gam = pos ? log(f1 / f0) / L : 1.0;
-  double ex = (gam * rho + 1.0) - rho;
-  double e = exp(ex * lr);
-  double v = f0 * e;
-  d0 = pos ? e * (1.0 - lr * rho / L) : e;
-  d1 = pos ? v * lr * rho / (f1 * L) : 0.0;
-  drho = v * ((gam - 1.0) * lr + ex / rho);
-  return v;
+  double a = p, b = 0.0;
+  if (lowq) {
+    a = pos ? rho * lr * iL : 0.0;
+    b = pos ? (1.0 - rho) * lr : lr;
+  }
+  if (pos || lowq) {
+    const double e = texp(fma(a, lnr, b), ET);
+    R.v = f0 * e;
+    R.d0 = e * (1.0 - a);
+    R.d1 = pos ? ddiv(e * a, r) : 0.0;
+    const double da = R.v * lnr, db = R.v;
+    R.dpar = !lowq ? da : pos ? da * (lr + 1.0) * iL + db * ((1.0 - rho) * irho - lr) : db * irho;
+  } else {
+    R.v = f0 + (f1 - f0) * p;
+    R.d0 = 1.0 - p;
+    R.d1 = p;
+    R.dpar = f1 - f0;
+  }
+  return R;
 }
 
 // The whole vector-Jacobian product of one point: d/dx, d/dQ^2 into gx[p],
 // gq[p], knot-value contributions added to gv.
 __device__ __forceinline__ void vjp_point(const GridView &g, const long long *xkeys, const long long *qkeys,
-                                          long long p, const double *__restrict__ xa,
+                                          LogTabs LT, const double *ET, long long p, const double *__restrict__ xa,
                                           const double *__restrict__ qa, const double *__restrict__ cot,
                                           double *__restrict__ gx, double *__restrict__ gq,
                                           double *__restrict__ gv) {
     const double x = xa[p], q2 = qa[p];
     double lq;
-    PointSites<double> ps = sites(g, xkeys, qkeys, x, q2, LogTabs{g.tlogtab, g.tloghtab}, lq);
+    PointSites<double> ps = sites(g, xkeys, qkeys, x, q2, LT, lq);
     if (ps.cls == C_INVALID) {
       if (gx) gx[p] = NAN;
       if (gq) gq[p] = NAN;
       return;
     }
-    const bool lowx = ps.cls == C_LOWX || ps.cls == C_LOWX_HIGHQ || ps.cls == C_LOWX_LOWQ;
-    const bool realq = ps.cls == C_IN || ps.cls == C_LOWX;
+    const int cls = ps.cls;
+    const bool lowx = cls == C_LOWX || cls == C_LOWX_HIGHQ || cls == C_LOWX_LOWQ;
+    const bool realq = cls == C_IN || cls == C_LOWX;
+    const bool lowq = cls == C_LOWQ || cls == C_LOWX_LOWQ;
     // a query on the last knot: derivative of the last proper cell at t = 1
     if (!lowx && ps.xc0 == g.nx - 1) { ps.xc0 = g.nx - 2; ps.t0 = 1.0; ps.ts0 = 0.0; }
     if (realq && ps.qc0 == g.nqc) { ps.qc0 = g.top_qc; ps.u0 = 1.0; ps.us0 = 0.0; }
+    const double ix = ddiv(1.0, x), iq = ddiv(1.0, q2);
     Site64 X[2], Q[2];
     for (int a = 0; a < 2; a++) {
       int xc = a ? ps.xc1 : ps.xc0;
       double t = a ? ps.t1 : ps.t0, s = a ? 1.0 - ps.t1 : ps.ts0;
-      double dpos = (a == 0 && !lowx) ? g.xcell[4 * xc + 1] / x : 0.0;
+      double dpos = (a == 0 && !lowx) ? g.xcell[4 * xc + 1] * ix : 0.0;
       make_site(X[a], g.xW + 16 * xc, t, s, xc, xc - 1, dpos);
     }
     for (int b = 0; b < 2; b++) {
       int qc = b ? ps.qc1 : ps.qc0;
       double u = b ? ps.u1 : ps.u0, s = b ? 1.0 - ps.u1 : ps.us0;
       int row = g.qc_row[qc];
-      double dpos = (b == 0 && realq) ? g.qcell[4 * row + 1] / q2 : 0.0;
+      double dpos = (b == 0 && realq) ? g.qcell[4 * row + 1] * iq : 0.0;
       make_site(Q[b], g.qW + 16 * qc, u, s, qc, row - 1, dpos);
     }
     const int nsx = lowx ? 2 : 1;
-    const int nsq = (ps.cls == C_IN || ps.cls == C_LOWX) ? 1 : 2;
-    const double dpx = lowx ? g.idx0 / x : 0.0;
-    const double dpq = (ps.cls == C_HIGHQ || ps.cls == C_LOWX_HIGHQ) ? -g.idq_top / q2 : 0.0;
-    const double drho = (ps.cls == C_LOWQ || ps.cls == C_LOWX_LOWQ) ? 1.0 / g.q2min : 0.0;
+    const int nsq = realq ? 1 : 2;
+    const double dpx = lowx ? g.idx0 * ix : 0.0;
+    // the q rule's parameter per unit Q^2: p_q = -(ln Q^2 - ln Q2max) idq_top, or rho = Q^2 / Q2min
+    const double dpq = lowq ? g.inv_q2min : -g.idq_top * iq;
+    double irho = 0.0, iL = 0.0;
+    if (lowq) {
+      irho = ddiv(1.0, ps.pq);
+      iL = ddiv(1.0, g.ln101);
+    }
     double sx = 0.0, sq = 0.0;
     for (int f = 0; f < g.nf; f++) {
       const double c = cot[p * g.nf + f];
@@ -135,35 +154,37 @@ __device__ __forceinline__ void vjp_point(const GridView &g, const long long *xk
           const double *blk = g.coef + (((size_t)Q[b].c * g.nx + X[a].c) * g.nf + f) * 16;
           patch_d(blk, X[a], Q[b], F[a][b], Ft[a][b], Fu[a][b]);
         }
-      double lam[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
-      double dvpx = 0.0, dvpq = 0.0, dvrho = 0.0, d0, d1, dp;
-      switch (ps.cls) {
-        case C_IN: lam[0][0] = 1.0; break;
-        case C_LOWX: pair_d(F[0][0], F[1][0], ps.px, lam[0][0], lam[1][0], dvpx); break;
-        case C_HIGHQ: pair_d(F[0][0], F[0][1], ps.pq, lam[0][0], lam[0][1], dvpq); break;
-        case C_LOWQ: lowq_d(F[0][0], F[0][1], ps.pq, ps.lr, g.ln101, lam[0][0], lam[0][1], dvrho); break;
-        case C_LOWX_HIGHQ: {
-          double a0, a1, ap, b0, b1, bp;
-          double A = pair_d(F[0][0], F[0][1], ps.pq, a0, a1, ap);
-          double B = pair_d(F[1][0], F[1][1], ps.pq, b0, b1, bp);
-          pair_d(A, B, ps.px, d0, d1, dp);
-          lam[0][0] = d0 * a0; lam[0][1] = d0 * a1; lam[1][0] = d1 * b0; lam[1][1] = d1 * b1;
-          dvpq = d0 * ap + d1 * bp;
-          dvpx = dp;
-          break;
-        }
-        case C_LOWX_LOWQ: {
-          double a0, a1, ar, b0, b1, br;
-          double A = lowq_d(F[0][0], F[0][1], ps.pq, ps.lr, g.ln101, a0, a1, ar);
-          double B = lowq_d(F[1][0], F[1][1], ps.pq, ps.lr, g.ln101, b0, b1, br);
-          pair_d(A, B, ps.px, d0, d1, dp);
-          lam[0][0] = d0 * a0; lam[0][1] = d0 * a1; lam[1][0] = d1 * b0; lam[1][1] = d1 * b1;
-          dvrho = d0 * ar + d1 * br;
-          dvpx = dp;
-          break;
+      // the q rule on each x site (lam_q: dA/dF(a, 0), dA/dF(a, 1), dA/dpar), then the x rule
+      double A[2], l0[2], l1[2], lpar[2];
+      for (int a = 0; a < nsx; a++) {
+        if (!realq) {
+          const RuleD R = rule_d(F[a][0], F[a][1], ps.pq, lowq, ps.pq, ps.lr, irho, iL, LT, ET);
+          A[a] = R.v; l0[a] = R.d0; l1[a] = R.d1; lpar[a] = R.dpar;
+        } else {
+          A[a] = F[a][0]; l0[a] = 1.0; l1[a] = 0.0; lpar[a] = 0.0;
         }
       }
-      double dx = dvpx * dpx, dq = dvpq * dpq + dvrho * drho;
+      double o0 = 1.0, o1 = 0.0, dvpx = 0.0;
+      if (lowx) {
+        const RuleD R = rule_d(A[0], A[1], ps.px, false, 0.0, 0.0, 0.0, 0.0, LT, ET);
+        o0 = R.d0; o1 = R.d1; dvpx = R.dpar;
+      }
+      double lam[2][2];
+      lam[0][0] = o0 * l0[0];
+      double dx = 0.0, dq = 0.0;
+      if (lowx) {
+        lam[1][0] = o1 * l0[1];
+        dx = dvpx * dpx;
+      }
+      if (!realq) {
+        lam[0][1] = o0 * l1[0];
+        double dpar = o0 * lpar[0];
+        if (lowx) {
+          lam[1][1] = o1 * l1[1];
+          dpar = fma(o1, lpar[1], dpar);
+        }
+        dq = dpar * dpq;
+      }
       for (int a = 0; a < nsx; a++)
         for (int b = 0; b < nsq; b++) {
           dx = fma(lam[a][b] * Ft[a][b], X[a].dpos, dx);
@@ -196,58 +217,80 @@ __device__ __forceinline__ void vjp_point(const GridView &g, const long long *xk
 
 // One warp per tile of 32 points, a lane per point.  Points that need a
 // continuation rule (found by integer range tests on the raw inputs) are
-// queued per warp and processed 32 at a time, so that a warp of in-grid
-// points never runs the continuation code (log, exp, division, four sites)
-// for a few lanes -- the FP64 pipe would pay for all 32.
+// queued per warp in three queues -- x rule only, Q rule only, both -- and
+// processed 32 of one kind at a time: a warp of in-grid points never runs
+// the continuation code for a few lanes, and a continuation warp runs one
+// kind of rule sequence (the FP64 pipe pays for every lane of an
+// instruction, so mixed kinds would run each sequence for a few lanes).
+// What is left in the queues at the end goes in mixed warps of 32.
 constexpr int kAdjWarps = kAdjThreads / 32;
+constexpr int kAdjQ = 64;  // queue capacity: below 32 before a tile adds at most 32
 
 __global__ void __launch_bounds__(kAdjThreads, 1)
 k_vjp(GridView g, const double *__restrict__ xa, const double *__restrict__ qa, const double *__restrict__ cot,
       long long n, double *__restrict__ gx, double *__restrict__ gq, double *__restrict__ gv) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ long long queue[kAdjWarps][64];
+  __shared__ long long queue[kAdjWarps][3][kAdjQ];
   long long *xkeys = reinterpret_cast<long long *>(smem);
   long long *qkeys = reinterpret_cast<long long *>(smem + keys_bytes(g.nx, 8));
+  size_t off = keys_bytes(g.nx, 8) + keys_bytes(g.nrows, 8);
+  double2 *LTt = reinterpret_cast<double2 *>(smem + off);  // the logarithm's and exponential's tables
+  off += sizeof(double2) * kLogTab;
+  double *LTh = reinterpret_cast<double *>(smem + off);
+  off += sizeof(double) * kLogTab;
+  double *ET = reinterpret_cast<double *>(smem + off);
   load_keys<double>(g, xkeys, 0);
   load_keys<double>(g, qkeys, 1);
+  for (int i = threadIdx.x; i < kLogTab; i += kAdjThreads) { LTt[i] = g.tlogtab[i]; LTh[i] = g.tloghtab[i]; }
+  for (int i = threadIdx.x; i < kExpTab; i += kAdjThreads) ET[i] = g.texptab[i];
+  const LogTabs LT{LTt, LTh};
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  long long *Q = queue[warp];
   const unsigned lt = (1u << lane) - 1u;
   const long long kxlast = __double_as_longlong(g.xlast), kx0 = __double_as_longlong(g.x0);
   const long long kqmin = __double_as_longlong(g.q2min), kqmax = __double_as_longlong(g.q2max);
-  int nq = 0;  // queued points (warp-uniform)
+  int n0 = 0, n1 = 0, n2 = 0;  // queued points per kind (warp-uniform)
   const long long ntiles = (n + 31) / 32, nwarps = (long long)gridDim.x * kAdjWarps;
   long long tile = (long long)blockIdx.x * kAdjWarps + warp;
-  // one call site: each round either drains 32 queued points, or takes the
-  // in-grid points of the next tile (queueing its continuation points), or
-  // drains the rest of the queue at the end (every branch is warp-uniform)
+  // one call site: each round either drains 32 queued points of one kind, or
+  // takes the in-grid points of the next tile (queueing its continuation
+  // points), or drains what is left of a queue at the end (every branch is
+  // warp-uniform)
   while (true) {
     long long pp = -1;
-    if (nq >= 32) {
-      nq -= 32;
-      pp = Q[nq + lane];
+    const int full = n0 >= 32 ? 0 : n1 >= 32 ? 1 : n2 >= 32 ? 2 : -1;
+    if (full >= 0) {
+      const int c = (full == 0 ? n0 : full == 1 ? n1 : n2) - 32;
+      pp = queue[warp][full][c + lane];
+      if (full == 0) n0 = c; else if (full == 1) n1 = c; else n2 = c;
     } else if (tile < ntiles) {
       const long long p = tile * 32 + lane;
-      bool far = false;
+      int kind = -1;
       if (p < n) {
         const long long kx = __double_as_longlong(xa[p]), kq = __double_as_longlong(qa[p]);
         const bool valid = kq > 0 && kq < 0x7FF0000000000000LL && kx > 0 && kx <= kxlast;
-        far = valid && (kx < kx0 || kq < kqmin || kq > kqmax);
-        if (!far) pp = p;
+        const bool fx = kx < kx0, fq = kq < kqmin || kq > kqmax;
+        if (valid && (fx || fq)) kind = fx ? (fq ? 2 : 0) : 1;
+        else pp = p;
       }
-      const unsigned fm = __ballot_sync(0xffffffffu, far);
-      if (far) Q[nq + __popc(fm & lt)] = p;
-      nq += __popc(fm);
+      const unsigned m0 = __ballot_sync(0xffffffffu, kind == 0), m1 = __ballot_sync(0xffffffffu, kind == 1),
+                     m2 = __ballot_sync(0xffffffffu, kind == 2);
+      if (kind == 0) queue[warp][0][n0 + __popc(m0 & lt)] = p;
+      if (kind == 1) queue[warp][1][n1 + __popc(m1 & lt)] = p;
+      if (kind == 2) queue[warp][2][n2 + __popc(m2 & lt)] = p;
+      n0 += __popc(m0); n1 += __popc(m1); n2 += __popc(m2);
       tile += nwarps;
-    } else if (nq > 0) {
-      if (lane < nq) pp = Q[lane];
-      nq = 0;
+    } else if (n0 + n1 + n2 > 0) {  // the rest, kinds mixed, up to 32 at a time
+      const int t0 = min(n0, 32), t1 = min(n1, 32 - t0), t2 = min(n2, 32 - t0 - t1);
+      if (lane < t0) pp = queue[warp][0][n0 - t0 + lane];
+      else if (lane < t0 + t1) pp = queue[warp][1][n1 - t1 + lane - t0];
+      else if (lane < t0 + t1 + t2) pp = queue[warp][2][n2 - t2 + lane - t0 - t1];
+      n0 -= t0; n1 -= t1; n2 -= t2;
     } else {
       break;
     }
     __syncwarp();
-    if (pp >= 0) vjp_point(g, xkeys, qkeys, pp, xa, qa, cot, gx, gq, gv);
+    if (pp >= 0) vjp_point(g, xkeys, qkeys, LT, ET, pp, xa, qa, cot, gx, gq, gv);
     __syncwarp();
   }
 }
@@ -266,9 +309,12 @@ extern "C" int xfxq2_all_flavours_vjp(const pdf_grid *grid, const double *x, con
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  size_t smem = keys_bytes(g.nx, 8) + keys_bytes(g.nrows, 8);
-  long long blocks = ((long long)n + kAdjThreads - 1) / kAdjThreads;  // one tile per warp at most
-  long long cap = (long long)(sms > 0 ? sms : 1) * 8;
+  size_t smem = keys_bytes(g.nx, 8) + keys_bytes(g.nrows, 8) + (sizeof(double2) + sizeof(double)) * kLogTab +
+                sizeof(double) * kExpTab;
+  // one resident block per SM (its registers fill the SM), each warp taking many
+  // tiles so that its continuation queues fill to whole warps
+  long long blocks = ((long long)n + kAdjThreads - 1) / kAdjThreads;
+  long long cap = (long long)(sms > 0 ? sms : 1);
   if (blocks > cap) blocks = cap;
   k_vjp<<<(unsigned)blocks, kAdjThreads, smem, stream>>>(g, x, q2, cot, (long long)n, grad_x, grad_q2,
                                                          grad_values);
