@@ -458,6 +458,17 @@ def our_arm(args):
         else:
             P.xfxq2_all_flavours_alphas(G, xd, qd, out=out, alphas_out=aout)
 
+    if args.only == "adjoint":  # the adjoint alone on --points points of the same law
+        ax, aq, acot = S.adjoint_inputs(n, nf, 5 + 1000 * rank, 6 + 1000 * rank)
+        axd, aqd, acd = torch.from_numpy(ax).to(dev), torch.from_numpy(aq).to(dev), torch.from_numpy(acot).to(dev)
+        agx, agq = torch.empty_like(axd), torch.empty_like(aqd)
+        agv = torch.zeros((G.nrows, G.nx, nf), dtype=torch.float64, device=dev)
+        ms = run_timed(lambda: P.xfxq2_all_flavours_vjp(G, axd, aqd, acd, agx, agq, agv), args.steps, args.warmup,
+                       world, sync)
+        if rank == 0:
+            print(json.dumps({"only": args.only, "points": n, "ms_per_step": ms,
+                              "gradients_per_s": n * nf / (ms * 1e-3)}))
+        return 0
     if args.only == "surrogate":  # inference alone on in-grid points (its cost does not depend on training)
         from paper_2009_06635_gb300 import synthetic as S
         from paper_2009_06635_gb300.surrogate import Surrogate
@@ -658,7 +669,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-members", action="store_true")
-    ap.add_argument("--only", choices=["fp64", "fp32", "surrogate"], default=None,
+    ap.add_argument("--only", choices=["fp64", "fp32", "surrogate", "adjoint"], default=None,
                     help="run only that path's step (a small case for profiling); prints its timing")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
