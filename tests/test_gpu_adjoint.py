@@ -124,3 +124,34 @@ def test_autograd_function_and_value_restaging(full, synth):
     b = P.xfxq2_all_flavours(fresh, dev(x), dev(q2)).cpu().numpy()
     assert np.array_equal(a, b)
     P.pdf_grid_set_values(G, torch.from_numpy(g.values).cuda())  # restore for other tests
+
+
+def test_full_size_batch_in_the_benchmark_configuration(full, synth):
+    """The benchmark's adjoint step (1e6 points, its seeds, one launch): every
+    warp takes many tiles, so the continuation queues fill and drain whole
+    warps of one kind.  Per-point gradients are functions of the point alone,
+    so a sample of them must match, bit for bit, the same points run as a
+    small batch (mixed remainders), and the oracle on a subsample; the knot
+    gradient must equal the sum of four quarter batches up to the order of
+    the FP64 additions."""
+    g, G, og = full
+    n = 1_000_000
+    x, q2, cot = synth.adjoint_inputs(n, g.nflav, 5, 6)
+    gx, gq, gv = run_vjp(G, x, q2, cot)
+    rng = np.random.default_rng(77)
+    sub = np.sort(rng.choice(n, 20_000, replace=False))
+    sx, sq, _ = run_vjp(G, x[sub], q2[sub], cot[sub], with_values=False)
+    assert np.array_equal(gx[sub], sx, equal_nan=True) and np.array_equal(gq[sub], sq, equal_nan=True)
+    few = sub[:1500]
+    dx = og.dxfxq2(x[few], q2[few], "x")
+    dq = og.dxfxq2(x[few], q2[few], "q2")
+    v, s, fl = og.xfxq2(x[few], q2[few])
+    ok = ~fl.any(axis=1)
+    c = cot[few]
+    sxs = np.abs(c * dx).sum(axis=1) + (np.abs(c) * s).sum(axis=1) / (x[few] * min_log_spacing(g.x_knots))
+    sqs = np.abs(c * dq).sum(axis=1) + (np.abs(c) * s).sum(axis=1) / (q2[few] * min_log_spacing(g.q2_knots))
+    assert (np.abs(gx[few] - (c * dx).sum(axis=1)) / sxs)[ok].max() < 1e-10
+    assert (np.abs(gq[few] - (c * dq).sum(axis=1)) / sqs)[ok].max() < 1e-10
+    parts = sum(run_vjp(G, x[k::4], q2[k::4], cot[k::4])[2] for k in range(4))
+    scale = np.abs(gv).max(axis=(0, 1))  # per flavour
+    assert (np.abs(gv - parts) / scale).max() < 1e-11
