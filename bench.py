@@ -90,7 +90,7 @@ def algorithmic_flops(counts, nflav):
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for name in ("xf64.cu", "tang.cuh", "sites.cuh", "pdf_internal.cuh", "grid.cu"):
+    for name in ("xf64.cu", "ff.cuh", "tang.cuh", "sites.cuh", "pdf_internal.cuh", "grid.cu"):
         h.update((ROOT / "paper_2009_06635_gb300" / "csrc" / name).read_bytes())
     return h.hexdigest()[:16]
 

@@ -13,6 +13,7 @@
 // A query exactly on the last x (or top Q^2) knot is taken in the last
 // proper cell at t = 1 (u = 1), so the derivative there is the one-sided one
 // of that cell.
+#include "ff.cuh"
 #include "sites.cuh"
 
 namespace pdfgb {
@@ -98,6 +99,64 @@ __device__ __forceinline__ RuleD rule_d(double f0, double f1, double p, bool low
   return R;
 }
 
+// ---- in-grid points on a float-float-safe grid ------------------------------
+// An in-grid point: F_t dt/dx = sum_lk B_l(u) B'_k(t) dt/dx c_lk and F_u du/dQ^2
+// (likewise) for every flavour in float-float on the FMA pipe from the
+// float-float control points (good to ~2^-46 of sum |w c|); the coordinate
+// sums and the knot scatter (the patch is linear in the knot values with
+// weights w_a(t) w_b(u)) in FP64.
+__device__ __forceinline__ void vjp_ingrid_ff(const GridView &g, const Site64 &X, const Site64 &Q, long long p,
+                                              const double *__restrict__ cot, double *__restrict__ gx,
+                                              double *__restrict__ gq, double *__restrict__ gv) {
+  ff2 wt[16], wu[16];
+  {
+    ff2 xb[4], xd[4], qb[4], qd[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      xb[k] = ff_of(X.B[k]);
+      xd[k] = ff_of(X.dB[k] * X.dpos);
+      qb[k] = ff_of(Q.B[k]);
+      qd[k] = ff_of(Q.dB[k] * Q.dpos);
+    }
+#pragma unroll
+    for (int m = 0; m < 16; m++) {
+      wt[m] = ff_mul(qb[m >> 2], xd[m & 3]);
+      wu[m] = ff_mul(qd[m >> 2], xb[m & 3]);
+    }
+  }
+  double W[16];  // knot weights w_b(u) w_a(t), 0 where the knot is outside the grid
+#pragma unroll
+  for (int m = 0; m < 16; m++) {
+    const int row = Q.k0 + (m >> 2), col = X.k0 + (m & 3);
+    W[m] = (row >= 0 && row < g.nrows && col >= 0 && col < g.nx) ? Q.w[m >> 2] * X.w[m & 3] : 0.0;
+  }
+  const float4 *cb = reinterpret_cast<const float4 *>(g.coefff + ((size_t)Q.c * g.nx + X.c) * 16 * g.nfp);
+  const long long k0 = ((long long)Q.k0 * g.nx + X.k0) * g.nf;  // knot (Q.k0, X.k0); the used ones are >= 0
+  double sx = 0.0, sq = 0.0;
+  for (int f = 0; f < g.nf; f++) {
+    const double c = cot[p * g.nf + f];
+    float th = 0.f, tl = 0.f, uh = 0.f, ul = 0.f;
+#pragma unroll
+    for (int m2 = 0; m2 < 8; m2++) {
+      const float4 b = __ldg(cb + (size_t)m2 * g.nfp + f);
+      ff_acc(th, tl, wt[2 * m2], b.x, b.y);
+      ff_acc(uh, ul, wu[2 * m2], b.x, b.y);
+      ff_acc(th, tl, wt[2 * m2 + 1], b.z, b.w);
+      ff_acc(uh, ul, wu[2 * m2 + 1], b.z, b.w);
+    }
+    sx = fma(c, f2d(th) + f2d(tl), sx);
+    sq = fma(c, f2d(uh) + f2d(ul), sq);
+    if (gv && (__double_as_longlong(c) << 1) != 0) {
+#pragma unroll
+      for (int m = 0; m < 16; m++)
+        if ((__double_as_longlong(W[m]) << 1) != 0)
+          atomicAdd(gv + (k0 + ((long long)(m >> 2) * g.nx + (m & 3)) * g.nf + f), c * W[m]);
+    }
+  }
+  if (gx) gx[p] = sx;
+  if (gq) gq[p] = sq;
+}
+
 // The whole vector-Jacobian product of one point: d/dx, d/dQ^2 into gx[p],
 // gq[p], knot-value contributions added to gv.
 __device__ __forceinline__ void vjp_point(const GridView &g, const long long *xkeys, const long long *qkeys,
@@ -122,18 +181,22 @@ __device__ __forceinline__ void vjp_point(const GridView &g, const long long *xk
     if (realq && ps.qc0 == g.nqc) { ps.qc0 = g.top_qc; ps.u0 = 1.0; ps.us0 = 0.0; }
     const double ix = ddiv(1.0, x), iq = ddiv(1.0, q2);
     Site64 X[2], Q[2];
-    for (int a = 0; a < 2; a++) {
+    for (int a = 0; a < (lowx ? 2 : 1); a++) {
       int xc = a ? ps.xc1 : ps.xc0;
       double t = a ? ps.t1 : ps.t0, s = a ? 1.0 - ps.t1 : ps.ts0;
       double dpos = (a == 0 && !lowx) ? g.xcell[4 * xc + 1] * ix : 0.0;
       make_site(X[a], g.xW + 16 * xc, t, s, xc, xc - 1, dpos);
     }
-    for (int b = 0; b < 2; b++) {
+    for (int b = 0; b < (realq ? 1 : 2); b++) {
       int qc = b ? ps.qc1 : ps.qc0;
       double u = b ? ps.u1 : ps.u0, s = b ? 1.0 - ps.u1 : ps.us0;
       int row = g.qc_row[qc];
       double dpos = (b == 0 && realq) ? g.qcell[4 * row + 1] * iq : 0.0;
       make_site(Q[b], g.qW + 16 * qc, u, s, qc, row - 1, dpos);
+    }
+    if (cls == C_IN && g.ff) {
+      vjp_ingrid_ff(g, X[0], Q[0], p, cot, gx, gq, gv);
+      return;
     }
     const int nsx = lowx ? 2 : 1;
     const int nsq = realq ? 1 : 2;

@@ -22,6 +22,7 @@
 #include <cmath>
 
 #include "mc.cuh"
+#include "ff.cuh"
 #include "sites.cuh"
 
 namespace pdfgb {
@@ -50,41 +51,6 @@ struct alignas(16) Queue64 {
   long long ob[64];
 };
 
-// ---- float-float arithmetic (a value is hi + lo, two floats, ~48 bits) -----
-// Error-free product (FMA) and sum (TwoSum); the _rn intrinsics keep the
-// compiler from contracting or reordering the error terms.
-struct ff2 {
-  float h, l;
-};
-__device__ __forceinline__ ff2 ff_of(double a) {
-  float h = __double2float_rn(a);
-  return {h, __double2float_rn(a - (double)h)};
-}
-__device__ __forceinline__ ff2 ff_mul(ff2 a, ff2 b) {
-  float p = __fmul_rn(a.h, b.h);
-  float e = __fmaf_rn(a.h, b.h, -p);
-  e = __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, e));
-  float h = __fadd_rn(p, e);
-  return {h, __fsub_rn(e, __fsub_rn(h, p))};
-}
-__device__ __forceinline__ void ff_bernstein(double t, double s, ff2 *B) {
-  const ff2 tf = ff_of(t), sf = ff_of(s), three = {3.f, 0.f};
-  const ff2 t2 = ff_mul(tf, tf), s2 = ff_mul(sf, sf);
-  B[0] = ff_mul(s2, sf);
-  B[1] = ff_mul(three, ff_mul(tf, s2));
-  B[2] = ff_mul(three, ff_mul(t2, sf));
-  B[3] = ff_mul(t2, tf);
-}
-// Exact float -> double on the integer pipe for normal floats and zeros (the
-// FP64 pipe's conversion costs as much as an FMA on GB300); subnormals,
-// infinities and NaN take the hardware conversion.
-__device__ __forceinline__ double f2d(float f) {
-  const unsigned b = __float_as_uint(f), a = b & 0x7FFFFFFFu;
-  if (a - 0x00800000u < 0x7F000000u)  // biased exponent in [1, 254]
-    return __hiloint2double((int)(((a >> 3) + 0x38000000u) | (b & 0x80000000u)), (int)(b << 29));
-  if (a == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
-  return (double)f;
-}
 // sum_m w_m b_m with w (hi, lo) from the record and b (hi, lo) from the
 // float-float control points (c: the item's first pair; pairs of control
 // points nf float4 apart): exact products, TwoSum accumulation, the cross
