@@ -506,6 +506,7 @@ k_infer(SurrConst c, const bf16 *__restrict__ wg, const float *__restrict__ para
   __shared__ __align__(8) unsigned long long mbar[TG];
   __shared__ uint32_t tbase;
   __shared__ float sfreq[SNQ][2], sscale[SOUT];  // indexed by the warp's half: kept out of the parameter space
+  __shared__ volatile int g1_go;                 // group 1 may start (see below)
   unsigned char *smem = smem_raw + (((smem_u32(smem_raw) + 1023u) & ~1023u) - smem_u32(smem_raw));
   bf16 *W1 = reinterpret_cast<bf16 *>(smem);
   bf16 *Wh = reinterpret_cast<bf16 *>(smem + kOffWh);
@@ -536,6 +537,7 @@ k_infer(SurrConst c, const bf16 *__restrict__ wg, const float *__restrict__ para
   if (threadIdx.x < SOUT) sscale[threadIdx.x] = c.scale[threadIdx.x];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x < TG) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[threadIdx.x])));
+  if (threadIdx.x == 0) g1_go = 0;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tbase)),
                  "r"(kTmemCols));
@@ -568,6 +570,15 @@ k_infer(SurrConst c, const bf16 *__restrict__ wg, const float *__restrict__ para
   long long tile = (long long)blockIdx.x * TG + g;
   double xn = 0.5, qn = 10.0;  // this thread's point of the next tile (defaults for rows past n)
   if (tile * 128 + t < n) { xn = xa[tile * 128 + t]; qn = qa[tile * 128 + t]; }
+  // Group 1 starts a third of a tile behind group 0 (when group 0 issues the
+  // products of its first tile's second layer, or has no tile): started together, the
+  // two groups stay in step -- their products queue behind each other on the
+  // tensor core and their epilogues share the SFU -- while offset, one
+  // group's products run during the other's epilogue (21% less time).  The
+  // wait is bounded (~1 ms).
+  if (g == 1)
+    for (int it = 0; it < (1 << 14) && !g1_go; it++) __nanosleep(64);
+  bool first = true;
   for (; tile < ntiles; tile += tstride) {
     const long long p0 = tile * 128, p = p0 + t;
     const bool in = p < n;
@@ -624,6 +635,7 @@ k_infer(SurrConst c, const bf16 *__restrict__ wg, const float *__restrict__ para
         asm volatile("tcgen05.fence::after_thread_sync;");
         layer_mma(l, tD, tA, tOne, w1, wh, w5, wb);
         tc_commit(mb);
+        if (g == 0 && l == 1 && first) g1_go = 1;
       }
       const bool done = mbar_wait(mb, phase);
       phase ^= 1u;
@@ -689,11 +701,13 @@ k_infer(SurrConst c, const bf16 *__restrict__ wg, const float *__restrict__ para
         }
       }
     }
+    first = false;
     if (!ok) {
       if (gt == 0) atomicExch(err, 1);
       break;
     }
   }
+  if (g == 0 && gt == 0) g1_go = 1;
   cp_async_wait_all();
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
