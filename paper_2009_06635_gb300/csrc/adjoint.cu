@@ -43,18 +43,20 @@ __device__ __forceinline__ void make_site(Site64 &S, const double *Wc, double t,
   S.dpos = dpos;
 }
 
-// Patch value and its derivatives in t and u.
-__device__ __forceinline__ void patch_d(const double *b, const Site64 &X, const Site64 &Q, double &F,
+// Patch value and its derivatives in t (when the x site moves with x) and u.
+__device__ __forceinline__ void patch_d(const double *b, const Site64 &X, const Site64 &Q, bool need_t, double &F,
                                         double &Ft, double &Fu) {
   F = Ft = Fu = 0.0;
   for (int l = 0; l < 4; l++) {
     const double2 *q = reinterpret_cast<const double2 *>(b + 4 * l);
     double2 v0 = __ldg(q), v1 = __ldg(q + 1);
     double r = X.B[0] * v0.x + X.B[1] * v0.y + X.B[2] * v1.x + X.B[3] * v1.y;
-    double rt = X.dB[0] * v0.x + X.dB[1] * v0.y + X.dB[2] * v1.x + X.dB[3] * v1.y;
     F = fma(Q.B[l], r, F);
-    Ft = fma(Q.B[l], rt, Ft);
     Fu = fma(Q.dB[l], r, Fu);
+    if (need_t) {
+      double rt = X.dB[0] * v0.x + X.dB[1] * v0.y + X.dB[2] * v1.x + X.dB[3] * v1.y;
+      Ft = fma(Q.B[l], rt, Ft);
+    }
   }
 }
 
@@ -215,7 +217,7 @@ __device__ __forceinline__ void vjp_point(const GridView &g, const long long *xk
       for (int a = 0; a < nsx; a++)
         for (int b = 0; b < nsq; b++) {
           const double *blk = g.coef + (((size_t)Q[b].c * g.nx + X[a].c) * g.nf + f) * 16;
-          patch_d(blk, X[a], Q[b], F[a][b], Ft[a][b], Fu[a][b]);
+          patch_d(blk, X[a], Q[b], !lowx, F[a][b], Ft[a][b], Fu[a][b]);  // x sites of the x rule are fixed
         }
       // the q rule on each x site (lam_q: dA/dF(a, 0), dA/dF(a, 1), dA/dpar), then the x rule
       double A[2], l0[2], l1[2], lpar[2];
