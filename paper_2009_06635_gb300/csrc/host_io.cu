@@ -3,7 +3,10 @@
 // The batch is cut into chunks that alternate between two streams the grid
 // owns; each chunk is copied in, evaluated and copied out on its stream, so
 // the copy-in of one chunk, the kernel of another and the copy-out of a third
-// overlap (the copy engines and the SMs work at the same time).  With pinned
+// overlap (the copy engines and the SMs work at the same time).  The output
+// (8 nf bytes per point against 16 in) sets the pace: the device-to-host
+// link is busy from the first copy-out to the end, so the first chunks are
+// small (1/8, 1/4, 1/2 of a full one) to start that copy-out early.  With pinned
 // host memory the copies are asynchronous DMA; with pageable memory they are
 // correct but serialise.  The device staging buffers belong to the grid and
 // are reused across calls.
@@ -43,9 +46,10 @@ extern "C" int xfxq2_all_flavours_host(const pdf_grid *cg, const double *x, cons
   if (rc) return rc;
   const int nf = g->v.nf;
   cudaError_t e = cudaSuccess;
-  size_t c = 0;
-  for (size_t off = 0; off < n && e == cudaSuccess && rc == PDF_OK; off += g->io_cap, c++) {
-    const size_t m = n - off < g->io_cap ? n - off : g->io_cap;
+  size_t c = 0, m = 0;
+  for (size_t off = 0; off < n && e == cudaSuccess && rc == PDF_OK; off += m, c++) {
+    const size_t want = c < 3 ? g->io_cap >> (3 - c) : g->io_cap;  // ramp: 1/8, 1/4, 1/2, then whole chunks
+    m = n - off < want ? n - off : want;
     const int k = (int)(c & 1);
     cudaStream_t st = g->io_stream[k];
     double *dx = static_cast<double *>(g->io_buf[k]);
