@@ -123,3 +123,28 @@ def test_training_error_map_and_fallback(setup, synth):
     err = np.where(np.isnan(ref).any(axis=1), 0.0, err)
     assert err.max() < 5e-3, err.max()
     print(f"fallback {nfb} of {len(xt)} points; network served {len(xt) - nfb}")
+
+
+def test_fused_inference_ragged_sizes_and_unaligned_output(setup, synth):
+    """Each output row is a function of its own point alone (per-row dot
+    products in a fixed order), so any prefix run on its own -- fewer points
+    than a tile, exactly one, ragged tails, more tiles than the grid has
+    groups -- must reproduce the full run bit for bit, and so must a run
+    whose output starts 4 bytes past a 16-byte boundary (the scalar store
+    path of the staged output)."""
+    g, G, Surrogate, params, freq, scale, bounds, og = setup
+    p = params.astype(np.float64).copy()
+    p[128 * 32:128 * 32 + 128] = np.random.default_rng(5).uniform(-0.5, 0.5, 128)  # b1
+    s = Surrogate(G, p.astype(np.float32), freq, max_batch=1024)
+    x, q2 = synth.ingrid_samples(g, 80_001, 24)
+    xd, qd = dev(x), dev(q2)
+    full = s.eval(xd, qd).cpu().numpy()
+    for n in (1, 31, 127, 128, 129, 255, 257, 1000, 40_000):
+        part = s.eval(xd[:n], qd[:n]).cpu().numpy()
+        assert np.array_equal(part, full[:n]), n
+    n = 1001
+    buf = torch.empty(n * g.nflav + 1, dtype=torch.float32, device="cuda")
+    out = buf[1:].view(n, g.nflav)  # 4 bytes past the allocation's alignment
+    assert out.data_ptr() % 16 == 4
+    s.eval(xd[:n], qd[:n], out=out)
+    assert np.array_equal(out.cpu().numpy(), full[:n])
