@@ -1075,7 +1075,10 @@ extern "C" int pdf_surrogate_train(pdf_surrogate *s, const pdf_grid *grid, const
 static int check_tc(const pdf_surrogate *s, const char *what) {
   int e = 0;
   int rc = cuda_err(cudaMemcpy(&e, s->tc_err, sizeof(int), cudaMemcpyDeviceToHost), what);
-  if (!rc && e) rc = set_error(PDF_ERR_CUDA, "%s: a tensor-core wait in the inference kernel ran out", what);
+  if (!rc && e) {
+    cudaMemset(s->tc_err, 0, sizeof(int));  // reported once
+    rc = set_error(PDF_ERR_CUDA, "%s: a tensor-core wait in the inference kernel ran out", what);
+  }
   return rc;
 }
 
