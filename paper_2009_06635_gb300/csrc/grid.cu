@@ -545,7 +545,7 @@ extern "C" int pdf_grid_nmembers(const pdf_grid *g) { return g ? g->v.nmem : set
 
 extern "C" int pdf_free_grid(pdf_grid *g) {
   if (!g) return PDF_OK;
-  for (int k = 0; k < 2; k++) {
+  for (int k = 0; k < pdf_grid::kIoStreams; k++) {
     if (g->io_stream[k]) { cudaStreamSynchronize(g->io_stream[k]); cudaStreamDestroy(g->io_stream[k]); }
     if (g->io_buf[k]) cudaFree(g->io_buf[k]);
   }

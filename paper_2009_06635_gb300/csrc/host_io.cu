@@ -1,7 +1,6 @@
 // host_io.cu -- xfxq2_all_flavours_host: host buffers in, host buffers out.
 //
-// The batch is cut into chunks that alternate between two streams the grid
-// owns; each chunk is copied in, evaluated and copied out on its stream, so
+// The batch is cut into chunks that rotate over three streams the grid owns; each chunk is copied in, evaluated and copied out on its stream, so
 // the copy-in of one chunk, the kernel of another and the copy-out of a third
 // overlap (the copy engines and the SMs work at the same time).  The output
 // (8 nf bytes per point against 16 in) sets the pace: the device-to-host
@@ -19,7 +18,7 @@ static const size_t kChunk = (size_t)1 << 20;  // points per chunk
 static int ensure_io(pdf_grid *g) {
   if (g->io_buf[0]) return PDF_OK;
   const size_t bytes = kChunk * (3 + (size_t)g->v.nf) * sizeof(double);
-  for (int k = 0; k < 2; k++) {
+  for (int k = 0; k < pdf_grid::kIoStreams; k++) {
     cudaError_t e = cudaStreamCreateWithFlags(&g->io_stream[k], cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&g->io_buf[k], bytes);
     if (e != cudaSuccess) {
@@ -50,7 +49,7 @@ extern "C" int xfxq2_all_flavours_host(const pdf_grid *cg, const double *x, cons
   for (size_t off = 0; off < n && e == cudaSuccess && rc == PDF_OK; off += m, c++) {
     const size_t want = c < 3 ? g->io_cap >> (3 - c) : g->io_cap;  // ramp: 1/8, 1/4, 1/2, then whole chunks
     m = n - off < want ? n - off : want;
-    const int k = (int)(c & 1);
+    const int k = (int)(c % pdf_grid::kIoStreams);
     cudaStream_t st = g->io_stream[k];
     double *dx = static_cast<double *>(g->io_buf[k]);
     double *dq = dx + g->io_cap;
@@ -64,10 +63,11 @@ extern "C" int xfxq2_all_flavours_host(const pdf_grid *cg, const double *x, cons
     if (e == cudaSuccess && rc == PDF_OK && alphas_out)
       e = cudaMemcpyAsync(alphas_out + off, da, m * sizeof(double), cudaMemcpyDeviceToHost, st);
   }
-  cudaError_t e0 = cudaStreamSynchronize(g->io_stream[0]);
-  cudaError_t e1 = cudaStreamSynchronize(g->io_stream[1]);
+  for (int k = 0; k < pdf_grid::kIoStreams; k++) {
+    const cudaError_t ek = cudaStreamSynchronize(g->io_stream[k]);
+    if (e == cudaSuccess) e = ek;
+  }
   if (rc) return rc;
-  if (e == cudaSuccess) e = e0 != cudaSuccess ? e0 : e1;
   if (e != cudaSuccess) return set_error(PDF_ERR_CUDA, "xfxq2_all_flavours_host: %s", cudaGetErrorString(e));
   return PDF_OK;
 }

@@ -211,10 +211,11 @@ struct pdf_grid {
   // device allocations owned by the handle
   void *blocks[32];
   int nblocks;
-  // host-I/O pipeline (lazily created)
-  cudaStream_t io_stream[2];
-  cudaEvent_t io_event[2];
-  void *io_buf[2];
+  // host-I/O pipeline (lazily created): kIoStreams streams, one staging buffer each
+  static constexpr int kIoStreams = 3;
+  cudaStream_t io_stream[kIoStreams];
+  cudaEvent_t io_event[kIoStreams];
+  void *io_buf[kIoStreams];
   size_t io_cap;  // points per buffer
   // Monte Carlo integration scratch (lazily created): event rows, per-block
   // partial sums, the running sums
