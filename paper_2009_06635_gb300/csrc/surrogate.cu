@@ -244,20 +244,17 @@ __global__ void k_loss(const float *y, const float *t, int n, int nf, bf16 *g, d
 }
 
 // db[n] += sum_b G[b][n] (G BF16, [rows][ld]); one block per column.
-__global__ void k_colsum(const bf16 *G, int rows, int ld, int ncol, float *db) {
-  int n = blockIdx.x;
+// db[n] += sum over rows of G[b][n]: a block per slab of kColRows rows, a thread
+// per column (consecutive threads read consecutive columns of a row), one
+// atomic per column and block
+constexpr int kColRows = 64;
+__global__ void __launch_bounds__(128) k_colsum(const bf16 *G, int rows, int ld, int ncol, float *db) {
+  const int n = threadIdx.x;
   if (n >= ncol) return;
+  const int b0 = blockIdx.x * kColRows, b1 = min(rows, b0 + kColRows);
   float s = 0.f;
-  for (int b = threadIdx.x; b < rows; b += blockDim.x) s += __bfloat162float(G[(long long)b * ld + n]);
-  __shared__ float red[32];
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (threadIdx.x == 0) db[n] += s;
-  }
+  for (int b = b0; b < b1; b++) s += __bfloat162float(G[(long long)b * ld + n]);
+  atomicAdd(db + n, s);
 }
 
 struct AdamArgs {
@@ -838,7 +835,9 @@ int forward_backward(pdf_surrogate *s, int B, cudaStream_t st) {
   }
   k_loss<<<(B * SOUT + 255) / 256, 256, 0, st>>>(s->y, s->t, B, s->nf, s->g[4], s->loss);
   // backward
-  const int ksplit = (B + 1023) / 1024;
+  // the weight gradients reduce over the batch: chunks of 128 rows give ~256 CTAs
+  // per product (a 128 x 128 output is only four 64 x 64 tiles)
+  const int ksplit = (B + 127) / 128;
   for (int l = 4; l >= 0; l--) {
     const int in = l == 0 ? SIN : SW, out = l == 4 ? SOUT : SW, nout = l == 4 ? s->nf : SW;
     const bf16 *G = s->g[l];
@@ -848,7 +847,7 @@ int forward_backward(pdf_surrogate *s, int B, cudaStream_t st) {
     a.C = s->grads + L.w[l];
     a.ldc = in;
     launch_gemm(EPI_ATOMIC, a, ksplit, st);
-    k_colsum<<<nout, 256, 0, st>>>(G, B, out, nout, s->grads + L.b[l]);
+    k_colsum<<<(B + kColRows - 1) / kColRows, 128, 0, st>>>(G, B, out, nout, s->grads + L.b[l]);
     if (l > 0) {
       // dH_{l}[b][j] = sum_o G[b][o] W[o][j]  ->  G_{l-1} = dH * silu'(Z_{l-1})
       GemmArgs d = gemm_args(G, out, 1, s->wbf + wbf_off(l), in, 1, B, in, out);
