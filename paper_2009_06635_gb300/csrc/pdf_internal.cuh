@@ -35,6 +35,7 @@
 //          of a cell is sum_ab w_a(t) w_b(u) f_ab; coef is that sum expanded.
 #pragma once
 
+#include <mutex>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -196,6 +197,33 @@ __device__ __forceinline__ T combine(int cls, T px, T pq, T lr, T ln101, FN F) {
 // Host-side helpers shared by the translation units.
 int set_error(int code, const char *fmt, ...);
 int check_launch(const char *what);
+
+// Blocks per SM of a kernel at a dynamic shared-memory size, found once per
+// size (a small launch would otherwise pay for the attribute and occupancy
+// queries on every call).  The size attribute only grows, so concurrent
+// callers never lower it under one another's launch.  One device per process.
+struct LaunchCache {
+  std::mutex mu;
+  size_t attr = 0, sizes[16] = {};
+  int occ[16] = {}, nc = 0;
+  template <typename K>
+  int blocks_per_sm(K kern, int threads, size_t smem) {
+    std::lock_guard<std::mutex> lock(mu);
+    for (int i = 0; i < nc; i++)
+      if (sizes[i] == smem) return occ[i];
+    if (smem > attr) {
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      attr = smem;
+    }
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+    if (per_sm < 1) per_sm = 1;
+    const int slot = nc < 16 ? nc++ : 15;
+    sizes[slot] = smem;
+    occ[slot] = per_sm;
+    return per_sm;
+  }
+};
 
 // Evaluation layouts (see the kernels in xf64.cu and xfxq2.cu).
 enum { MODE_POINTS = 0, MODE_MC = 1, MODE_MEMBERS = 2 };

@@ -1,7 +1,7 @@
-// surrogate.cu -- learned surrogate of the interpolator: a small MLP on BF16
-// tensor cores with FP32 accumulation (inference: tcgen05 with TMEM
-// accumulators; training: mma.sync m16n8k16 tiles), its training kernels, and
-// evaluation with fallback to the interpolator.
+// surrogate.cu -- learned surrogate of the interpolator: a small MLP on the
+// BF16 tensor cores (tcgen05, FP32 accumulation in TMEM) for both inference
+// and training, its training kernels, and evaluation with fallback to the
+// interpolator.
 //
 // Network (for points inside the grid):
 //   z   = (2 (ln x - lx_lo)/(lx_hi - lx_lo) - 1,  2 (ln Q^2 - lq_lo)/(lq_hi - lq_lo) - 1)
@@ -74,6 +74,10 @@ struct Layout {
 // BF16 weight copies: W1 [128][32], W2..4 [128][128], W5 [16][128] (rows >= nf zero)
 __host__ __device__ constexpr size_t wbf_off(int l) { return l == 0 ? 0 : 128 * 32 + (size_t)(l - 1) * 128 * 128; }
 constexpr size_t kWbfTotal = 128 * 32 + 3 * 128 * 128 + 16 * 128;
+// their transposes for layers 1..4: W_2..W_4^T [128][128], W_5^T [128][16]
+__host__ __device__ constexpr size_t wt_off(int l) { return (size_t)(l - 1) * 128 * 128; }
+constexpr size_t kWtTotal = 3 * 128 * 128 + 128 * 16;
+constexpr int kTgBatch = 256;  // batch rows per chunk of a weight-gradient product
 
 __device__ __forceinline__ float tanh_fast(float v) {
   float r;
@@ -99,9 +103,6 @@ __device__ __forceinline__ float envelope(const SurrConst &c, float z0, int f) {
   const float a = __ldg(t), b = __ldg(t + SOUT);
   return expf(a + (u - (float)k) * (b - a));
 }
-__device__ __forceinline__ float output_of(const SurrConst &c, float y, float z0, int f) {
-  return c.target == PDF_SURR_ENVELOPE ? envelope(c, z0, f) * y : c.scale[f] * sinhf(y);
-}
 
 // feature k (0..31) of a point
 __device__ __forceinline__ float feature(const SurrConst &c, float z0, float z1, int k) {
@@ -115,128 +116,33 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return *reinterpret_cast<uint32_t *>(&v);
 }
 
-__device__ __forceinline__ void mma16816(float *d, const uint32_t *a, uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
 // ---------------------------------------------------------------------------
 // training kernels
 // ---------------------------------------------------------------------------
 
-__global__ void k_features(SurrConst c, const double *x, const double *q2, int n, bf16 *h0) {
+__global__ void k_features(SurrConst c, const double *x, const double *q2, int n, bf16 *h0, bf16 *h0t,
+                           long long ldt) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n * SIN) return;
   int p = i / SIN, k = i % SIN;
   float z0, z1;
   point_z(c, x[p], q2[p], z0, z1);
-  h0[i] = __float2bfloat16_rn(feature(c, z0, z1, k));
-}
-
-enum { EPI_FWD_SILU = 0, EPI_OUT = 1, EPI_BWD_SILU = 2, EPI_ATOMIC = 3 };
-
-struct GemmArgs {
-  const bf16 *A;
-  long long sam, sak;
-  const bf16 *B;
-  long long sbk, sbn;
-  int M, N, K, kchunk;
-  const float *bias;  // FWD / OUT
-  int nbias;          // columns that have a bias (OUT: the real flavours)
-  float *Z;           // FWD: pre-activation out; BWD: pre-activation in
-  bf16 *H;            // FWD: activation out; BWD: gradient out
-  float *C;           // OUT: y, ATOMIC: accumulated result
-  long long ldc;
-};
-
-// C[M][N] = sum_k A(m,k) B(k,n) over this block's K chunk; 64x64 tile,
-// four warps of 32x32, K step 32, operands staged in shared memory in
-// K-contiguous rows (padded to 40 so fragment reads hit distinct banks).
-template <int EPI>
-__global__ void __launch_bounds__(128) k_gemm(GemmArgs g) {
-  __shared__ __align__(16) bf16 As[64][40];
-  __shared__ __align__(16) bf16 Bs[64][40];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
-  const int kbeg = blockIdx.z * g.kchunk;
-  const int kend = min(g.K, kbeg + g.kchunk);
-  const int gid = lane >> 2, tig = lane & 3;
-  float acc[2][4][4];
-  for (int i = 0; i < 2; i++)
-    for (int j = 0; j < 4; j++)
-      for (int e = 0; e < 4; e++) acc[i][j][e] = 0.f;
-  const bf16 zero = __float2bfloat16_rn(0.f);
-  for (int k0 = kbeg; k0 < kend; k0 += 32) {
-    for (int e = tid; e < 64 * 32; e += 128) {
-      int r = e >> 5, kk = e & 31;
-      int m = m0 + r, n = n0 + r, k = k0 + kk;
-      As[r][kk] = (m < g.M && k < kend) ? g.A[m * g.sam + k * g.sak] : zero;
-      Bs[r][kk] = (n < g.N && k < kend) ? g.B[k * g.sbk + n * g.sbn] : zero;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int ks = 0; ks < 32; ks += 16) {
-      uint32_t a[2][4], b[4][2];
-#pragma unroll
-      for (int i = 0; i < 2; i++) {
-        const bf16 *r0 = &As[wm + 16 * i + gid][ks + 2 * tig];
-        const bf16 *r1 = &As[wm + 16 * i + gid + 8][ks + 2 * tig];
-        a[i][0] = *reinterpret_cast<const uint32_t *>(r0);
-        a[i][1] = *reinterpret_cast<const uint32_t *>(r1);
-        a[i][2] = *reinterpret_cast<const uint32_t *>(r0 + 8);
-        a[i][3] = *reinterpret_cast<const uint32_t *>(r1 + 8);
-      }
-#pragma unroll
-      for (int j = 0; j < 4; j++) {
-        const bf16 *c0 = &Bs[wn + 8 * j + gid][ks + 2 * tig];
-        b[j][0] = *reinterpret_cast<const uint32_t *>(c0);
-        b[j][1] = *reinterpret_cast<const uint32_t *>(c0 + 8);
-      }
-#pragma unroll
-      for (int i = 0; i < 2; i++)
-#pragma unroll
-        for (int j = 0; j < 4; j++) mma16816(acc[i][j], a[i], b[j][0], b[j][1]);
-    }
-    __syncthreads();
-  }
-  // epilogue: element (row, col) of fragment e: row = gid + 8 (e >= 2), col = 2 tig + (e & 1)
-#pragma unroll
-  for (int i = 0; i < 2; i++)
-#pragma unroll
-    for (int j = 0; j < 4; j++)
-#pragma unroll
-      for (int e = 0; e < 4; e++) {
-        int m = m0 + wm + 16 * i + gid + ((e >> 1) << 3);
-        int n = n0 + wn + 8 * j + 2 * tig + (e & 1);
-        if (m >= g.M || n >= g.N) continue;
-        float v = acc[i][j][e];
-        long long o = (long long)m * g.ldc + n;
-        if (EPI == EPI_FWD_SILU) {
-          float z = v + g.bias[n];
-          g.Z[o] = z;
-          g.H[o] = __float2bfloat16_rn(silu_f(z));
-        } else if (EPI == EPI_OUT) {
-          g.C[o] = v + (n < g.nbias ? g.bias[n] : 0.f);
-        } else if (EPI == EPI_BWD_SILU) {
-          g.H[o] = __float2bfloat16_rn(v * dsilu_f(g.Z[o]));
-        } else {
-          atomicAdd(g.C + o, v);
-        }
-      }
+  const bf16 v = __float2bfloat16_rn(feature(c, z0, z1, k));
+  h0[i] = v;
+  h0t[(long long)k * ldt + p] = v;
 }
 
 // dL/dy for the mean-square loss on asinh targets; the loss sum accumulates in FP64.
-__global__ void k_loss(const float *y, const float *t, int n, int nf, bf16 *g, double *loss) {
+__global__ void k_loss(const float *y, const float *t, int n, int nf, bf16 *g, bf16 *gt, long long ldt,
+                       double *loss) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   float part = 0.f;
   if (i < n * SOUT) {
     int f = i % SOUT;
     float d = f < nf ? y[i] - t[i] : 0.f;
-    g[i] = __float2bfloat16_rn(2.f * d / ((float)n * (float)nf));
+    const bf16 v = __float2bfloat16_rn(2.f * d / ((float)n * (float)nf));
+    g[i] = v;
+    gt[(long long)f * ldt + i / SOUT] = v;
     part = d * d;
   }
   for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
@@ -276,13 +182,24 @@ __global__ void k_adam(AdamArgs a) {
 // FP32 masters -> BF16 weight copies (W5 padded to 16 rows).
 struct CastArgs {
   const float *p;
-  bf16 *w;
+  bf16 *w, *wt;
   size_t woff[5], boff[5];
   int nf;
 };
+// BF16 weights [out][in] (wbf_off), and for the backward products of layers
+// 1..4 their transposes [in][out] (wt_off); rows of W_5 beyond nf are zero
 __global__ void k_cast(CastArgs a) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (int)kWbfTotal) return;
+  if (i >= (int)(kWbfTotal + kWtTotal)) return;
+  if (i >= (int)kWbfTotal) {
+    const int r = i - (int)kWbfTotal;
+    const int l = r < 3 * SW * SW ? 1 + r / (SW * SW) : 4;
+    const int q = r - (int)wt_off(l), out = l == 4 ? SOUT : SW;
+    const int j = q / out, o = q % out;  // transposed element (j, o) = W_l[o][j]
+    const float v = (l == 4 && o >= a.nf) ? 0.f : a.p[a.woff[l] + (size_t)o * SW + j];
+    a.wt[r] = __float2bfloat16_rn(v);
+    return;
+  }
   int l = 4;
   while (l > 0 && (size_t)i < wbf_off(l)) l--;
   int r = i - (int)wbf_off(l);
@@ -711,6 +628,191 @@ k_infer(SurrConst c, const bf16 *__restrict__ wg, const float *__restrict__ para
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kTmemCols));
 }
 
+// ---------------------------------------------------------------------------
+// training products on tcgen05: C[M][N] = A[M][K] B[N][K]^T with both operands
+// K-contiguous in global memory (the training keeps transposed copies of its
+// activations, gradients and weights so that every product reads rows),
+// staged through two shared-memory stages of 64 K columns in the swizzled
+// layout, accumulated in TMEM (FP32), with the layer's epilogue on the way
+// out.  One CTA per 128-row tile, NT columns (grid z: column tiles) and one
+// K chunk (grid y: a split of the batch sum for the weight gradients, which
+// then add their partial tiles atomically).  Waits are bounded as in the
+// inference kernel.
+// ---------------------------------------------------------------------------
+enum { EPI_FWD_SILU = 0, EPI_OUT = 1, EPI_BWD_SILU = 2, EPI_ATOMIC = 3 };
+
+struct TGemm {
+  const bf16 *A;
+  long long lda;
+  const bf16 *B;
+  long long ldb;
+  int M, N, K, kchunk;
+  const float *bias;  // FWD / OUT: per column
+  int nvalid;         // OUT: columns with a bias; ATOMIC: columns added
+  float *Z;           // FWD: pre-activation out; BWD: pre-activation in ([M][ldz])
+  long long ldz;
+  bf16 *H;            // FWD: activation out; BWD: gradient out ([M][ldh])
+  long long ldh;
+  bf16 *Ht;           // the same transposed ([N][ldht])
+  long long ldht;
+  float *C;           // OUT: y [M][ldc]; ATOMIC: C[m][n], or C[n][m] with ctrans
+  long long ldc;
+  int ctrans;
+  int *err;
+};
+constexpr int kTgK = 64;                                    // K columns per stage
+constexpr size_t kTgStage = 2 * 128 * kTgK * sizeof(bf16);  // A and B tiles of up to 128 rows
+constexpr size_t kTgSmem = 2 * kTgStage + 1024;
+
+__device__ __forceinline__ void mma_ss(uint32_t d, uint64_t adesc, uint64_t bdesc, uint32_t id, uint32_t acc) {
+  asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+               ::"r"(d), "l"(adesc), "l"(bdesc), "r"(id), "r"(acc));
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t *r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                 "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]));
+}
+
+// rows [r0, r0 + R) and K columns [k0, k0 + 64) of a K-contiguous operand into one
+// swizzled stage; zero outside rows < nrows and columns < ke
+template <int R>
+__device__ __forceinline__ void tg_load(bf16 *dst, const bf16 *src, long long ld, int r0, int nrows, int k0, int ke,
+                                        bool vec) {
+  for (int i = threadIdx.x; i < R * 8; i += 128) {
+    const int r = i >> 3, c = i & 7, row = r0 + r, k = k0 + 8 * c;
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (row < nrows && k < ke) {
+      const bf16 *p = src + (long long)row * ld + k;
+      if (vec && k + 8 <= ke) {
+        v = __ldg(reinterpret_cast<const uint4 *>(p));
+      } else {
+        uint32_t e[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++) e[j] = k + j < ke ? (uint32_t)__bfloat16_as_ushort(p[j]) : 0u;
+        v = make_uint4(e[0] | (e[1] << 16), e[2] | (e[3] << 16), e[4] | (e[5] << 16), e[6] | (e[7] << 16));
+      }
+    }
+    *reinterpret_cast<uint4 *>(dst + r * 64 + ((c ^ (r & 7)) << 3)) = v;
+  }
+}
+
+template <int EPI, int NT>
+__global__ void __launch_bounds__(128) k_tgemm(TGemm g) {
+  extern __shared__ __align__(16) unsigned char tg_raw[];
+  __shared__ __align__(8) unsigned long long mbar[3];  // the two stages, and the last product
+  __shared__ uint32_t tbase;
+  unsigned char *sm = tg_raw + (((smem_u32(tg_raw) + 1023u) & ~1023u) - smem_u32(tg_raw));
+  constexpr int NCOL = NT < 32 ? 32 : NT;  // TMEM columns (at least 32)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * 128, n0 = blockIdx.z * NT;
+  const int kb = blockIdx.y * g.kchunk, ke = min(g.K, kb + g.kchunk);
+  const bool vec = ((reinterpret_cast<uintptr_t>(g.A) | reinterpret_cast<uintptr_t>(g.B)) & 15) == 0 &&
+                   (g.lda & 7) == 0 && (g.ldb & 7) == 0;
+  if (threadIdx.x < 3) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[threadIdx.x])));
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tbase)),
+                 "r"(NCOL));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;");
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tbase, id = mma_idesc(NT);
+  bool ok = true;
+  int it = 0;
+  for (int k0 = kb; k0 < ke; k0 += kTgK, it++) {
+    const int s = it & 1;
+    // the stage's previous products (two iterations back) must have read it
+    const bool done = it < 2 || mbar_wait(smem_u32(&mbar[s]), (uint32_t)(((it - 2) >> 1) & 1));
+    if (__syncthreads_or(!done)) { ok = false; break; }
+    bf16 *As = reinterpret_cast<bf16 *>(sm + s * kTgStage), *Bs = As + 128 * kTgK;
+    tg_load<128>(As, g.A, g.lda, m0, g.M, k0, ke, vec);
+    tg_load<NT>(Bs, g.B, g.ldb, n0, g.N, k0, ke, vec);
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t a = smem_u32(As), b = smem_u32(Bs);
+#pragma unroll
+      for (int q = 0; q < kTgK / 16; q++)
+        mma_ss(tmem, smem_desc_sw(a + 32 * q), smem_desc_sw(b + 32 * q), id, (it > 0 || q > 0) ? 1u : 0u);
+      tc_commit(smem_u32(&mbar[s]));
+    }
+  }
+  if (ok && it > 0) {  // one more commit covers every product of the CTA
+    if (threadIdx.x == 0) tc_commit(smem_u32(&mbar[2]));
+    const bool done = mbar_wait(smem_u32(&mbar[2]), 0u);
+    if (__syncthreads_or(!done)) ok = false;
+  }
+  if (ok && it > 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const int m = m0 + 32 * warp + lane;
+    const bool live = m < g.M;
+    const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+    constexpr int CW = NT < 32 ? 16 : 32;  // columns per TMEM load
+#pragma unroll 1
+    for (int c0 = 0; c0 < NT; c0 += CW) {
+      uint32_t r[32];
+      if (CW == 16) tmem_ld16(trow + c0, r);
+      else { tmem_ld32(trow + c0, r); tmem_wait32(r); }
+      const int nb = n0 + c0;  // first column of the chunk
+      if (!live || nb >= g.N) continue;
+      float v[CW];
+#pragma unroll
+      for (int j = 0; j < CW; j++) v[j] = __uint_as_float(r[j]);
+      if (EPI == EPI_FWD_SILU || EPI == EPI_BWD_SILU) {
+        float *zr = g.Z + (long long)m * g.ldz + nb;
+        bf16 *hr = g.H + (long long)m * g.ldh + nb;
+#pragma unroll
+        for (int j8 = 0; j8 < CW; j8 += 8) {
+          float o[8];
+          if (EPI == EPI_FWD_SILU) {
+            float zz[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++) { zz[j] = v[j8 + j] + __ldg(g.bias + nb + j8 + j); o[j] = silu_f(zz[j]); }
+            *reinterpret_cast<float4 *>(zr + j8) = make_float4(zz[0], zz[1], zz[2], zz[3]);
+            *reinterpret_cast<float4 *>(zr + j8 + 4) = make_float4(zz[4], zz[5], zz[6], zz[7]);
+          } else {
+            const float4 za = *reinterpret_cast<const float4 *>(zr + j8);
+            const float4 zb = *reinterpret_cast<const float4 *>(zr + j8 + 4);
+            const float zz[8] = {za.x, za.y, za.z, za.w, zb.x, zb.y, zb.z, zb.w};
+#pragma unroll
+            for (int j = 0; j < 8; j++) o[j] = v[j8 + j] * dsilu_f(zz[j]);
+          }
+          uint4 pk;
+          pk.x = pack_bf16(o[0], o[1]); pk.y = pack_bf16(o[2], o[3]);
+          pk.z = pack_bf16(o[4], o[5]); pk.w = pack_bf16(o[6], o[7]);
+          *reinterpret_cast<uint4 *>(hr + j8) = pk;
+          const bf16 *hb = reinterpret_cast<const bf16 *>(&pk);
+#pragma unroll
+          for (int j = 0; j < 8; j++) g.Ht[(long long)(nb + j8 + j) * g.ldht + m] = hb[j];
+        }
+      } else if (EPI == EPI_OUT) {
+        float *cr = g.C + (long long)m * g.ldc + nb;
+#pragma unroll
+        for (int j = 0; j < CW; j++) cr[j] = v[j] + (nb + j < g.nvalid ? __ldg(g.bias + nb + j) : 0.f);
+      } else {
+#pragma unroll
+        for (int j = 0; j < CW; j++)
+          if (nb + j < g.nvalid)
+            atomicAdd(g.ctrans ? g.C + (long long)(nb + j) * g.ldc + m : g.C + (long long)m * g.ldc + nb + j, v[j]);
+      }
+    }
+  } else if (!ok && threadIdx.x == 0) {
+    atomicExch(g.err, 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOL));
+}
+
 // error map: per tile the largest |s - v| / max(|v|, c_f) over points and flavours
 __global__ void k_tile_err(SurrConst c, const double *xa, const double *qa, long long n, const float *s,
                            const double *v, unsigned int *tile_err_bits, unsigned int *tile_cnt) {
@@ -768,6 +870,9 @@ struct pdf_surrogate {
   bf16 *wbf;                        // device BF16 copies
   // training scratch (max_batch rows)
   bf16 *h[5], *g[5];  // h0 [B][32], h1..h4 [B][128]; g1..g4 [B][128], g5 [B][16] at index 0..4 (g[l] for layer l)
+  bf16 *ht[5], *gt[5];  // their transposes [columns][bt]
+  bf16 *wt;             // transposed BF16 weights of layers 1..4 (wt_off)
+  long long bt;         // row stride of the transposes (max_batch rounded up to 64)
   float *z[4], *y, *t;
   double *xfbuf, *loss;
   long long step;
@@ -791,69 +896,64 @@ struct pdf_surrogate {
 
 namespace {
 
-void launch_gemm(int epi, const GemmArgs &a, int ksplit, cudaStream_t st) {
-  dim3 grid((a.N + 63) / 64, (a.M + 63) / 64, ksplit);
-  switch (epi) {
-    case EPI_FWD_SILU: k_gemm<EPI_FWD_SILU><<<grid, 128, 0, st>>>(a); break;
-    case EPI_OUT: k_gemm<EPI_OUT><<<grid, 128, 0, st>>>(a); break;
-    case EPI_BWD_SILU: k_gemm<EPI_BWD_SILU><<<grid, 128, 0, st>>>(a); break;
-    default: k_gemm<EPI_ATOMIC><<<grid, 128, 0, st>>>(a); break;
-  }
+template <int EPI, int NT>
+void tg_launch(const TGemm &a, int ksplit, cudaStream_t st) {
+  static const bool attr =  // once per instantiation (one device per process)
+      cudaFuncSetAttribute(k_tgemm<EPI, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTgSmem) ==
+      cudaSuccess;
+  (void)attr;
+  dim3 grid((unsigned)((a.M + 127) / 128), (unsigned)ksplit, (unsigned)((a.N + NT - 1) / NT));
+  k_tgemm<EPI, NT><<<grid, 128, kTgSmem, st>>>(a);
 }
 
-GemmArgs gemm_args(const bf16 *A, long long sam, long long sak, const bf16 *B, long long sbk, long long sbn, int M,
-                   int N, int K) {
-  GemmArgs a{};
-  a.A = A; a.sam = sam; a.sak = sak; a.B = B; a.sbk = sbk; a.sbn = sbn;
-  a.M = M; a.N = N; a.K = K; a.kchunk = ((K + 31) / 32) * 32;
-  a.ldc = N;
-  a.nbias = N;
-  return a;
-}
-
-// One forward + backward pass on a batch already in h[0] (features) and t
-// (targets); gradients accumulate into s->grads (zeroed here).
+// One forward + backward pass on a batch already in h[0] / ht[0] (features)
+// and t (targets); gradients accumulate into s->grads (zeroed here).  Every
+// product reads K-contiguous rows: forward H W^T; backward dH = G W (with the
+// transposed weights), dW = G^T H over the batch (with the transposed
+// gradients and activations the epilogues write).
 int forward_backward(pdf_surrogate *s, int B, cudaStream_t st) {
   const Layout &L = s->L;
+  const long long BT = s->bt;
   cudaMemsetAsync(s->grads, 0, L.total * sizeof(float), st);
   cudaMemsetAsync(s->loss, 0, sizeof(double), st);
-  // forward
+  TGemm a{};
+  a.err = s->tc_err;
+  // forward: Z_l = H_l W_l^T + b_l, H_{l+1} = silu(Z_l)
   for (int l = 0; l < 4; l++) {
-    int K = l == 0 ? SIN : SW;
-    GemmArgs a = gemm_args(s->h[l], K, 1, s->wbf + wbf_off(l), 1, K, B, SW, K);
+    const int K = l == 0 ? SIN : SW;
+    a.A = s->h[l]; a.lda = K; a.B = s->wbf + wbf_off(l); a.ldb = K;
+    a.M = B; a.N = SW; a.K = K; a.kchunk = K;
     a.bias = s->params + L.b[l];
-    a.Z = s->z[l];
-    a.H = s->h[l + 1];
-    launch_gemm(EPI_FWD_SILU, a, 1, st);
+    a.Z = s->z[l]; a.ldz = SW; a.H = s->h[l + 1]; a.ldh = SW; a.Ht = s->ht[l + 1]; a.ldht = BT;
+    tg_launch<EPI_FWD_SILU, 64>(a, 1, st);
   }
-  {
-    GemmArgs a = gemm_args(s->h[4], SW, 1, s->wbf + wbf_off(4), 1, SW, B, SOUT, SW);
-    a.bias = s->params + L.b[4];
-    a.nbias = s->nf;  // padded output columns carry no bias
-    a.C = s->y;
-    launch_gemm(EPI_OUT, a, 1, st);
-  }
-  k_loss<<<(B * SOUT + 255) / 256, 256, 0, st>>>(s->y, s->t, B, s->nf, s->g[4], s->loss);
-  // backward
-  // the weight gradients reduce over the batch: chunks of 128 rows give ~256 CTAs
-  // per product (a 128 x 128 output is only four 64 x 64 tiles)
-  const int ksplit = (B + 127) / 128;
+  a.A = s->h[4]; a.lda = SW; a.B = s->wbf + wbf_off(4); a.ldb = SW;
+  a.M = B; a.N = SOUT; a.K = SW; a.kchunk = SW;
+  a.bias = s->params + L.b[4]; a.nvalid = s->nf;  // padded output columns carry no bias
+  a.C = s->y; a.ldc = SOUT; a.ctrans = 0;
+  tg_launch<EPI_OUT, SOUT>(a, 1, st);
+  k_loss<<<(B * SOUT + 255) / 256, 256, 0, st>>>(s->y, s->t, B, s->nf, s->g[4], s->gt[4], BT, s->loss);
+  // backward; the weight gradients sum over the batch in chunks of kTgBatch rows, added atomically
+  const int ksplit = (B + kTgBatch - 1) / kTgBatch;
   for (int l = 4; l >= 0; l--) {
     const int in = l == 0 ? SIN : SW, out = l == 4 ? SOUT : SW, nout = l == 4 ? s->nf : SW;
-    const bf16 *G = s->g[l];
-    // dW[o][j] += sum_b G[b][o] H[b][j]
-    GemmArgs a = gemm_args(G, 1, out, s->h[l], in, 1, nout, in, B);
-    a.kchunk = ((B + ksplit - 1) / ksplit + 31) / 32 * 32;
-    a.C = s->grads + L.w[l];
-    a.ldc = in;
-    launch_gemm(EPI_ATOMIC, a, ksplit, st);
-    k_colsum<<<(B + kColRows - 1) / kColRows, 128, 0, st>>>(G, B, out, nout, s->grads + L.b[l]);
-    if (l > 0) {
-      // dH_{l}[b][j] = sum_o G[b][o] W[o][j]  ->  G_{l-1} = dH * silu'(Z_{l-1})
-      GemmArgs d = gemm_args(G, out, 1, s->wbf + wbf_off(l), in, 1, B, in, out);
-      d.Z = s->z[l - 1];
-      d.H = s->g[l - 1];
-      launch_gemm(EPI_BWD_SILU, d, 1, st);
+    a.K = B; a.kchunk = kTgBatch; a.C = s->grads + L.w[l];
+    if (l == 4) {  // dW_4^T[j][o] = sum_b H_4[b][j] G_4[b][o] (rows j: a 128-row tile)
+      a.A = s->ht[4]; a.lda = BT; a.B = s->gt[4]; a.ldb = BT;
+      a.M = SW; a.N = SOUT; a.nvalid = nout; a.ldc = SW; a.ctrans = 1;
+      tg_launch<EPI_ATOMIC, SOUT>(a, ksplit, st);
+    } else {       // dW_l[o][j] = sum_b G_l[b][o] H_l[b][j]
+      a.A = s->gt[l]; a.lda = BT; a.B = s->ht[l]; a.ldb = BT;
+      a.M = SW; a.N = in; a.nvalid = in; a.ldc = in; a.ctrans = 0;
+      if (l == 0) tg_launch<EPI_ATOMIC, SIN>(a, ksplit, st);
+      else tg_launch<EPI_ATOMIC, 64>(a, ksplit, st);
+    }
+    k_colsum<<<(B + kColRows - 1) / kColRows, 128, 0, st>>>(s->g[l], B, out, nout, s->grads + L.b[l]);
+    if (l > 0) {  // dH_l[b][j] = sum_o G_l[b][o] W_l[o][j] -> G_{l-1} = dH silu'(Z_{l-1})
+      a.A = s->g[l]; a.lda = out; a.B = s->wt + wt_off(l); a.ldb = out;
+      a.M = B; a.N = in; a.K = out; a.kchunk = out;
+      a.Z = s->z[l - 1]; a.ldz = SW; a.H = s->g[l - 1]; a.ldh = SW; a.Ht = s->gt[l - 1]; a.ldht = BT;
+      tg_launch<EPI_BWD_SILU, 64>(a, 1, st);
     }
   }
   return check_launch("surrogate forward/backward");
@@ -863,14 +963,15 @@ void cast_weights(pdf_surrogate *s, cudaStream_t st) {
   CastArgs a;
   a.p = s->params;
   a.w = s->wbf;
+  a.wt = s->wt;
   for (int l = 0; l < 5; l++) { a.woff[l] = s->L.w[l]; a.boff[l] = s->L.b[l]; }
   a.nf = s->nf;
-  k_cast<<<(unsigned)((kWbfTotal + 255) / 256), 256, 0, st>>>(a);
+  k_cast<<<(unsigned)((kWbfTotal + kWtTotal + 255) / 256), 256, 0, st>>>(a);
 }
 
 int features_targets(pdf_surrogate *s, const pdf_grid *grid, const double *x, const double *q2, int B,
                      const double *xf_given, cudaStream_t st) {
-  k_features<<<(B * SIN + 255) / 256, 256, 0, st>>>(s->c, x, q2, B, s->h[0]);
+  k_features<<<(B * SIN + 255) / 256, 256, 0, st>>>(s->c, x, q2, B, s->h[0], s->ht[0], s->bt);
   const double *xf = xf_given;
   if (!xf) {
     int rc = launch_all_f64(grid, x, q2, B, s->xfbuf, nullptr, st);
@@ -958,6 +1059,12 @@ extern "C" int pdf_surrogate_create_ex(const pdf_grid *grid, const float *params
   for (int l = 0; l < 4 && !rc; l++) rc = s->alloc(&s->g[l], B * SW);
   if (!rc) rc = s->alloc(&s->g[4], B * SOUT);
   for (int l = 0; l < 4 && !rc; l++) rc = s->alloc(&s->z[l], B * SW);
+  s->bt = (long long)((B + 63) / 64 * 64);
+  if (!rc) rc = s->alloc(&s->ht[0], (size_t)SIN * s->bt);
+  for (int l = 1; l < 5 && !rc; l++) rc = s->alloc(&s->ht[l], (size_t)SW * s->bt);
+  for (int l = 0; l < 4 && !rc; l++) rc = s->alloc(&s->gt[l], (size_t)SW * s->bt);
+  if (!rc) rc = s->alloc(&s->gt[4], (size_t)SOUT * s->bt);
+  if (!rc) rc = s->alloc(&s->wt, kWtTotal);
   if (!rc) rc = s->alloc(&s->y, B * SOUT);
   if (!rc) rc = s->alloc(&s->t, B * SOUT);
   if (!rc) rc = s->alloc(&s->xfbuf, B * nf);
@@ -1017,6 +1124,8 @@ extern "C" int pdf_surrogate_set_params(pdf_surrogate *s, const float *params) {
   return cuda_err(cudaDeviceSynchronize(), "pdf_surrogate_set_params");
 }
 
+static int check_tc(const pdf_surrogate *s, const char *what);
+
 extern "C" int pdf_surrogate_loss_grad(pdf_surrogate *s, const double *x, const double *q2, const double *xf,
                                        size_t n, double *loss, float *grad) {
   if (!s || !x || !q2 || !xf || !loss || !grad) return set_error(PDF_ERR_NULL, "pdf_surrogate_loss_grad: NULL argument");
@@ -1029,6 +1138,7 @@ extern "C" int pdf_surrogate_loss_grad(pdf_surrogate *s, const double *x, const 
   rc = cuda_err(cudaMemcpy(&sum, s->loss, sizeof(double), cudaMemcpyDeviceToHost), "pdf_surrogate_loss_grad");
   if (!rc) rc = cuda_err(cudaMemcpy(grad, s->grads, s->L.total * sizeof(float), cudaMemcpyDeviceToHost),
                          "pdf_surrogate_loss_grad");
+  if (!rc) rc = check_tc(s, "pdf_surrogate_loss_grad");
   *loss = sum / ((double)n * s->nf);
   return rc;
 }
@@ -1062,6 +1172,7 @@ extern "C" int pdf_surrogate_train(pdf_surrogate *s, const pdf_grid *grid, const
     if (it == cfg->steps - 1) {
       int e = cuda_err(cudaMemcpyAsync(&last, s->loss, sizeof(double), cudaMemcpyDeviceToHost, st), "train");
       if (!e) e = cuda_err(cudaStreamSynchronize(st), "pdf_surrogate_train");
+      if (!e) e = check_tc(s, "pdf_surrogate_train");
       if (e) return e;
     }
   }
@@ -1084,9 +1195,15 @@ static int check_tc(const pdf_surrogate *s, const char *what) {
 static int launch_infer(const pdf_surrogate *s, const double *x, const double *q2, size_t n, float *outf,
                         double *outd, const unsigned char *mask, unsigned int *nfb, unsigned int *idx,
                         cudaStream_t st) {
-  cudaFuncSetAttribute(k_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
-  int sms = 0;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+  static const bool attr =  // once (one device per process)
+      cudaFuncSetAttribute(k_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem) == cudaSuccess;
+  (void)attr;
+  static const int sms = [] {
+    int d = 0, m = 0;
+    cudaGetDevice(&d);
+    cudaDeviceGetAttribute(&m, cudaDevAttrMultiProcessorCount, d);
+    return m > 0 ? m : 1;
+  }();
   long long tiles = ((long long)n + 127) / 128;
   long long blocks = (tiles + TG - 1) / TG;
   if (blocks > sms) blocks = sms;

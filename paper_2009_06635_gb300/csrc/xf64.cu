@@ -421,10 +421,8 @@ static int launch_mode(const pdf_grid *grid, const double *xa, const double *qa,
   const GridView &g = grid->v;
   const size_t smem = xf64_smem<MODE>(g);
   auto kern = k_xf64<MODE>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
-  if (per_sm < 1) per_sm = 1;
+  static LaunchCache cache;
+  const int per_sm = cache.blocks_per_sm(kern, kThreads, smem);
   const int per_tile = MODE == MODE_MC ? 16 : 32;
   const long long ntiles = (n + per_tile - 1) / per_tile;
   const long long cap = (long long)num_sms() * per_sm;

@@ -214,10 +214,8 @@ static int launch_xf32(const pdf_grid *grid, const float *xa, const float *qa, c
   const GridView &g = grid->v;
   const size_t smem = xf32_smem<MODE>(g);
   auto kern = k_xf32<MODE>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
-  if (per_sm < 1) per_sm = 1;
+  static LaunchCache cache;
+  const int per_sm = cache.blocks_per_sm(kern, kThreads, smem);
   const int per_tile = MODE == MODE_MC ? 16 : 32;
   const long long ntiles = (n + per_tile - 1) / per_tile;
   long long blocks = (ntiles + kWarps - 1) / kWarps;
