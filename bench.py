@@ -269,6 +269,12 @@ def cpu_baseline_leg(g, x, q2, out_gpu, a_gpu, x32, q32, out32, target_s=10.0):
     av, asv = og.alphas(q2[idx])
     dt = time.perf_counter() - t0
     rate = m * (g.nflav + 1) / dt
+    # the same oracle on one host core, on the first tenth of the sample
+    m1 = max(probe, m // 10)
+    t0 = time.perf_counter()
+    og.xfxq2(x[idx[:m1]], q2[idx[:m1]], nthreads=1)
+    og.alphas(q2[idx[:m1]], nthreads=1)
+    rate1 = m1 * (g.nflav + 1) / (time.perf_counter() - t0)
     err64 = np.abs(out_gpu[idx] - v) / np.maximum(np.abs(v), s)
     err64 = np.where(fl, 0.0, err64)
     aerr = float((np.abs(a_gpu[idx] - av) / np.maximum(np.abs(av), asv)).max())
@@ -277,11 +283,46 @@ def cpu_baseline_leg(g, x, q2, out_gpu, a_gpu, x32, q32, out32, target_s=10.0):
     v3, s3, f3 = og.xfxq2(x32[idx[:k]].astype(np.float64), q32[idx[:k]].astype(np.float64))
     err32 = np.where(f3, 0.0, np.abs(out32[idx[:k]] - v3) / np.maximum(np.abs(v3), s3))
     return ({"value": rate, "unit": "evals/s", "cores": cores, "kind": "oracle",
-             "sample": f"{m} of the {len(x)} points (all flavours + alpha_s), {dt:.1f} s on {cores} threads"},
+             "sample": f"{m} of the {len(x)} points (all flavours + alpha_s), {dt:.1f} s on {cores} threads",
+             "one_core": {"value": rate1, "unit": "evals/s", "sample": f"{m1} of those points on 1 thread"}},
             {"fp64_max_scaled_err": float(np.nanmax(err64)), "alphas_max_scaled_err": aerr,
              "fp32_max_scaled_err_per_flavour": [float(e) for e in np.nanmax(err32, axis=0)],
              "scaled_err": "|gpu - oracle| / max(|oracle|, sum|w f|), on the sampled points",
              "marginal_excluded": int(fl.sum()), "sample_points": m})
+
+
+def small_grid_leg(dev, sync, reps=200):
+    """The single-subgrid workload (50 x 40 knots, 11 flavours, 1e4 in-grid
+    queries): latency-dominated, so the time of one call matters; FP64 and
+    FP32 all flavours + alpha_s, device buffers, CUDA events around `reps`
+    back-to-back calls after a warm-up."""
+    import torch
+
+    import paper_2009_06635_gb300 as P
+    from paper_2009_06635_gb300 import synthetic as S
+
+    g = S.grid_single_subgrid()
+    G = P.pdf_load_grid(g)
+    x, q2 = S.queries_single_subgrid(10_000, 2)
+    n, nf = len(x), g.nflav
+    res = {"workload": "single subgrid: 50 x knots in [1e-7, 1], 40 Q^2 knots in [2.7, 1e8], 11 flavours; "
+                       "1e4 in-grid queries (seed 2)", "points": n}
+    for tag, dt in (("fp64", torch.float64), ("fp32", torch.float32)):
+        xd, qd = torch.from_numpy(x).to(dev, dt), torch.from_numpy(q2).to(dev, dt)
+        out = torch.empty((n, nf), dtype=dt, device=dev)
+        aout = torch.empty((n,), dtype=dt, device=dev)
+        for _ in range(10):
+            P.xfxq2_all_flavours_alphas(G, xd, qd, out=out, alphas_out=aout)
+        sync()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            P.xfxq2_all_flavours_alphas(G, xd, qd, out=out, alphas_out=aout)
+        b.record()
+        sync()
+        us = a.elapsed_time(b) / reps * 1e3
+        res[tag] = {"us_per_call": us, "value": n * (nf + 1) / (us * 1e-6), "unit": "evals/s"}
+    return res
 
 
 def surrogate_leg(args, G, g, dev, world, sync, rank, nf, ms_per_eval64, target="envelope"):
@@ -549,6 +590,7 @@ def our_arm(args):
     ms_adj = run_timed(step_adj, args.steps, 2, world, sync)
 
     mc_int = mc_leg(G, world, sync, rank)
+    small = small_grid_leg(dev, sync)
     members = None if args.no_members else members_leg(args, dev, world, sync, rank)
     surrogate = None if args.no_surrogate else surrogate_leg(args, G, g, dev, world, sync, rank, nf,
                                                              ms64 / (n * (nf + 1)), target="envelope")
@@ -639,6 +681,7 @@ def our_arm(args):
             "surrogate_bf16_asinh_target": surrogate_asinh,
             "members_table2": members,
             "mc_integrate_fp64": mc_int,
+            "single_subgrid_1e4": small,
             "adjoint_fp64": {"value": world * ADJ_POINTS * nf / (ms_adj * 1e-3), "ms_per_step": ms_adj,
                              "points": ADJ_POINTS, "unit": "(point, flavour) gradients/s",
                              "outputs": "d/dx, d/dQ^2 per point and d/d(knot values), FP64 atomics"},
