@@ -28,8 +28,9 @@
  *     (0 = the legacy default stream) and returns without waiting.
  *   - "_host" calls take HOST memory (pinned memory gives the overlapped
  *     fast path), copy through device buffers the grid owns, and return only
- *     when the outputs are in host memory.  Two "_host" calls on one grid
- *     must not run concurrently from different threads.
+ *     when the outputs are in host memory.  Such calls on one grid from
+ *     several threads are serialised by the grid (as are pdf_mc_integrate
+ *     calls, which share the grid's event scratch).
  *   - Arrays are dense and row-major; outputs of the all-flavour calls are
  *     [n][nflav] in the column order the grid was loaded with.
  *   - A query point with x <= 0, x above the last x knot, Q^2 <= 0,

@@ -41,6 +41,7 @@ extern "C" int xfxq2_all_flavours_host(const pdf_grid *cg, const double *x, cons
     return set_error(PDF_ERR_NO_ALPHAS, "xfxq2_all_flavours_host: grid has no alpha_s nodes");
   if (n == 0) return PDF_OK;
   pdf_grid *g = const_cast<pdf_grid *>(cg);
+  std::lock_guard<std::mutex> lock(g->io_mu);  // one host-buffer call at a time per grid
   int rc = ensure_io(g);
   if (rc) return rc;
   const int nf = g->v.nf;

@@ -129,6 +129,7 @@ extern "C" int pdf_mc_integrate(const pdf_grid *cg, const pdf_mc_config *cfg, un
   c.g = pdf_grid_pid_column(cg, 21);
   if (c.g < 0) return set_error(PDF_ERR_PID, "pdf_mc_integrate: the grid lacks the gluon (pid 21)");
   pdf_grid *g = const_cast<pdf_grid *>(cg);
+  std::lock_guard<std::mutex> lock(g->mc_mu);  // one integration at a time per grid (shared scratch)
   const size_t cap = n_events < chunk ? (size_t)(n_events > 0 ? n_events : 1) : chunk;
   int rc = ensure_mc(g, cap);
   if (rc) return rc;

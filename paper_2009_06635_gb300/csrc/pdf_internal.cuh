@@ -239,7 +239,9 @@ struct pdf_grid {
   // device allocations owned by the handle
   void *blocks[32];
   int nblocks;
-  // host-I/O pipeline (lazily created): kIoStreams streams, one staging buffer each
+  // host-I/O pipeline (lazily created): kIoStreams streams, one staging buffer each;
+  // io_mu serialises the calls that use it (and mc_mu those that use the MC scratch)
+  std::mutex io_mu, mc_mu;
   static constexpr int kIoStreams = 3;
   cudaStream_t io_stream[kIoStreams];
   cudaEvent_t io_event[kIoStreams];

@@ -234,3 +234,34 @@ def test_full_size_mc_chunk_sampled(full, synth):
     for side, xs in ((0, x1[idx]), (1, x2[idx])):
         v, s, fl = og.xfxq2(xs, q2)
         assert_parity(got[:, side * nf:(side + 1) * nf], v, s, fl, RTOL_FP64, f"mc chunk side {side}")
+
+
+def test_host_path_and_mc_from_concurrent_threads(full, synth):
+    """Host-buffer calls (and Monte Carlo integrations) on one grid from
+    several host threads share the grid's staging buffers; the grid
+    serialises them, so every thread gets the result of a call made alone."""
+    import threading
+
+    g, G, og = full
+    xs = [synth.queries_full(1_500_001, 60 + k) for k in range(4)]
+    alone = [P.xfxq2_all_flavours_host(G, torch.from_numpy(x).pin_memory(), torch.from_numpy(q).pin_memory()).numpy()
+             for x, q in xs]
+    mc_alone = P.pdf_mc_integrate(G, 13000.0, 1e-6, 100.0, 4, 2_000_000)
+    res, mc = [None] * 4, [None] * 2
+    def host_call(k):
+        x, q = xs[k]
+        res[k] = P.xfxq2_all_flavours_host(G, torch.from_numpy(x).pin_memory(), torch.from_numpy(q).pin_memory())
+    def mc_call(k):
+        torch.cuda.set_device(0)
+        mc[k] = P.pdf_mc_integrate(G, 13000.0, 1e-6, 100.0, 4, 2_000_000)
+    threads = [threading.Thread(target=host_call, args=(k,)) for k in range(4)]
+    threads += [threading.Thread(target=mc_call, args=(k,)) for k in range(2)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    for k in range(4):
+        assert np.array_equal(res[k].numpy(), alone[k], equal_nan=True), k
+    want = (mc_alone.sum_w, mc_alone.sum_w2, mc_alone.sum_abs)  # fixed-order device sums
+    for k in range(2):
+        assert (mc[k].sum_w, mc[k].sum_w2, mc[k].sum_abs) == want, k
