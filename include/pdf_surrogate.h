@@ -19,13 +19,16 @@
  *                      tabulated at 1025 equal steps of ln x over the grid
  *                      (the network then learns an O(1) function, smooth
  *                      through the zeros of xf_f).
- * Products run on BF16 tensor cores with FP32
- * accumulation; BF16 weight copies are made from FP32 master weights.
+ * Products run on the BF16 tensor cores (tcgen05) with FP32 accumulation;
+ * BF16 weight copies are made from FP32 master weights.
  * The parameter vector is flat FP32: W1 [128][32], b1 [128], W2..W4
  * [128][128], b2..b4 [128], W5 [nflav][128], b5 [nflav] (W as [out][in]).
  *
  * All array arguments are DEVICE memory unless noted; calls return PDF_OK or
- * a PDF_ERR_* code (see pdf_gb300.h).  At most 16 flavours.
+ * a PDF_ERR_* code (see pdf_gb300.h).  At most 16 flavours.  The calls that
+ * use the surrogate's own buffers (training, loss/gradient, error map,
+ * evaluation with fallback, setting parameters) are serialised per
+ * surrogate; pdf_surrogate_eval uses none and runs concurrently.
  */
 #ifndef PDF_SURROGATE_H
 #define PDF_SURROGATE_H

@@ -862,6 +862,7 @@ int cuda_err(cudaError_t e, const char *what) {
 }  // namespace
 
 struct pdf_surrogate {
+  std::mutex mu;  // serialises the calls that use the scratch below (all but pdf_surrogate_eval)
   int nf, max_batch, device;
   Layout L;
   SurrConst c;
@@ -1116,6 +1117,7 @@ extern "C" int pdf_surrogate_get_params(const pdf_surrogate *s, float *params) {
 
 extern "C" int pdf_surrogate_set_params(pdf_surrogate *s, const float *params) {
   if (!s || !params) return set_error(PDF_ERR_NULL, "pdf_surrogate_set_params: NULL argument");
+  std::lock_guard<std::mutex> lock(s->mu);
   int rc = cuda_err(cudaMemcpy(s->params, params, s->L.total * sizeof(float), cudaMemcpyHostToDevice),
                     "pdf_surrogate_set_params");
   if (rc) return rc;
@@ -1131,6 +1133,7 @@ extern "C" int pdf_surrogate_loss_grad(pdf_surrogate *s, const double *x, const 
   if (!s || !x || !q2 || !xf || !loss || !grad) return set_error(PDF_ERR_NULL, "pdf_surrogate_loss_grad: NULL argument");
   if (n < 1 || n > (size_t)s->max_batch)
     return set_error(PDF_ERR_ARG, "pdf_surrogate_loss_grad: n = %zu outside [1, %d]", n, s->max_batch);
+  std::lock_guard<std::mutex> lock(s->mu);
   int rc = features_targets(s, nullptr, x, q2, (int)n, xf, 0);
   if (!rc) rc = forward_backward(s, (int)n, 0);
   if (rc) return rc;
@@ -1150,6 +1153,7 @@ extern "C" int pdf_surrogate_train(pdf_surrogate *s, const pdf_grid *grid, const
   if (B < 16 || B > s->max_batch || (size_t)B > n)
     return set_error(PDF_ERR_ARG, "pdf_surrogate_train: batch %d outside [16, min(max_batch, n)]", B);
   if (grid->v.nf != s->nf) return set_error(PDF_ERR_ARG, "pdf_surrogate_train: grid flavours differ");
+  std::lock_guard<std::mutex> lock(s->mu);
   const size_t nb = n / (size_t)B;  // whole batches per pass
   double last = 0.0;
   for (int it = 0; it < cfg->steps; it++) {
@@ -1224,6 +1228,7 @@ extern "C" int pdf_surrogate_build_error_map(pdf_surrogate *s, const pdf_grid *g
                                              const double *q2, size_t n, double threshold, double *stats) {
   if (!s || !grid || !x || !q2) return set_error(PDF_ERR_NULL, "pdf_surrogate_build_error_map: NULL argument");
   if (n == 0) return set_error(PDF_ERR_ARG, "pdf_surrogate_build_error_map: no validation points");
+  std::lock_guard<std::mutex> lock(s->mu);
   float *sv = nullptr;
   double *iv = nullptr;
   int rc = cuda_err(cudaMalloc(&sv, n * s->nf * sizeof(float)), "error map");
@@ -1283,6 +1288,7 @@ extern "C" int pdf_surrogate_eval_fallback(pdf_surrogate *s, const pdf_grid *gri
   if (!s->has_map) return set_error(PDF_ERR_ARG, "pdf_surrogate_eval_fallback: build the error map first");
   if (n > 0xFFFFFFFFull) return set_error(PDF_ERR_ARG, "pdf_surrogate_eval_fallback: n too large");
   if (n == 0) { if (n_fallback) *n_fallback = 0; return PDF_OK; }
+  std::lock_guard<std::mutex> lock(s->mu);
   if (n > s->fb_cap) {
     for (void *p : {(void *)s->fb_idx, (void *)s->fb_x, (void *)s->fb_q, (void *)s->fb_out}) if (p) cudaFree(p);
     s->fb_idx = nullptr; s->fb_x = s->fb_q = s->fb_out = nullptr; s->fb_cap = 0;
