@@ -658,7 +658,7 @@ def our_arm(args):
                      "peak_measured_dfma": fp64_meas.value / 1e12,
                      "kernel_ms": kern_ms, "algorithmic_flops_per_launch": flops,
                      "hbm_frac": n * (16 + 8 * nf) / (kern_ms * 1e-3) / (hbm * 1e9)},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": args.steps,  # one k_xf64 launch per step (all flavours + alpha_s fused)
         "clocks": clk,
         "e2e": {"value": world * evals_step / e2e_s, "unit": "evals/s", "h2d_bytes_per_step": 16 * n,
                 "d2h_bytes_per_step": 8 * n * (nf + 1), "ms_per_step": e2e_s * 1e3,
