@@ -27,6 +27,7 @@ constexpr int kThreads = 32 * kWarps;
 // 16-byte aligned).
 struct alignas(16) Rec32 {
   int cls[32], xc0[32], xc1[32], qc0[32], qc1[32];
+  int cell0[32];     // float4 offset of the (qc0, xc0) control-point block in coef32
   long long ob[32];  // output offset of the point's first column
   float W[32][20];
   float px[32], pq[32], lr[32];
@@ -66,10 +67,19 @@ __device__ __forceinline__ float eval_item32(const GridView &g, const Rec32 &R, 
   return combine<float>(R.cls[p], R.px[p], R.pq[p], R.lr[p], g.ln101_32, F);
 }
 
+// An in-grid item: one site, its block offset taken once per point (the
+// same arithmetic as eval_item32's class switch gives for C_IN).
+__device__ __forceinline__ float eval_in32(const GridView &g, const Rec32 &R, int p, int col) {
+  const float4 *q = reinterpret_cast<const float4 *>(g.coef32) + R.cell0[p] + col;
+  return site32(q, g.nfp, R.W[p], 0, 0);
+}
+
 // Write a point into its record slot.
-__device__ __forceinline__ void store_point32(Rec32 &R, int slot, const PointSites<float> &ps, long long ob) {
+__device__ __forceinline__ void store_point32(Rec32 &R, int slot, const PointSites<float> &ps, long long ob,
+                                              const GridView &g) {
   R.cls[slot] = ps.cls;
   R.xc0[slot] = ps.xc0; R.xc1[slot] = ps.xc1; R.qc0[slot] = ps.qc0; R.qc1[slot] = ps.qc1;
+  R.cell0[slot] = (ps.qc0 * g.nx + ps.xc0) * g.nfp * 4;
   R.ob[slot] = ob;
   R.px[slot] = ps.px; R.pq[slot] = ps.pq; R.lr[slot] = ps.lr;
   if (ps.cls == C_INVALID) return;
@@ -142,22 +152,23 @@ k_xf32(GridView g, const float *__restrict__ xa, const float *__restrict__ qa, c
     if (lane == 0 && inv) atomicAdd(g.invalid, (unsigned long long)__popc(inv));
     if (MODE == MODE_MC && present && (lane & 1) == 0) out[ob + 2 * g.nf] = alphas_eval(g, akeys, q2);
     if (MODE == MODE_POINTS && present && as_out) as_out[e0 + lane] = alphas_eval(g, akeys, q2);
-    // order the points by class (counting sort over the warp)
-    int slot = 0, base = 0;
+    // order the points by class (counting sort over the warp); in-grid points first
+    int slot = 0, base = 0, nin = 0;
 #pragma unroll
     for (int c = 0; c < NCLASS; c++) {
       const unsigned m = __ballot_sync(0xffffffffu, ps.cls == c);
       if (ps.cls == c) slot = base + __popc(m & lt);
       base += __popc(m);
+      if (c == C_IN) nin = base;
     }
     const int np = base;
-    if (present) store_point32(R, slot, ps, ob);
+    if (present) store_point32(R, slot, ps, ob, g);
     __syncwarp();
 
     // ---- phase 2: items (point, column) ----
     int p = lane / nc, c = lane - (lane / nc) * nc;
     for (int k = lane; k < np * nc; k += 32) {
-      out[R.ob[p] + c] = eval_item32(g, R, p, cbase + c);
+      out[R.ob[p] + c] = p < nin ? eval_in32(g, R, p, cbase + c) : eval_item32(g, R, p, cbase + c);
       c += dc;
       p += dp;
       if (c >= nc) { c -= nc; p++; }
