@@ -17,6 +17,7 @@ Prints one JSON line on rank 0.
 from __future__ import annotations
 
 import argparse
+import tempfile
 import ctypes
 import hashlib
 import json
@@ -119,7 +120,7 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = ROOT / "gpurun_out" / f"clocks_{os.getpid()}.csv"
+        self.path = Path(tempfile.gettempdir()) / f"pdf_gb300_clocks_{os.getpid()}.csv"
 
     def start(self):
         if not shutil.which("nvidia-smi"):
@@ -430,7 +431,7 @@ def members_leg(args, dev, world, sync, rank):
 
 
 def mc_leg(G, world, sync, rank):
-    """Monte Carlo integration (SURVEY cfg 3): 1e8 events per rank in 100
+    """Monte Carlo integration (the event workload at full size): 1e8 events per rank in 100
     chunks of 1e6, device RNG, fused PDF + alpha_s load, weights summed on the
     device; the three sums are added over ranks (the integration's one
     exchange step)."""

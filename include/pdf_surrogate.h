@@ -3,8 +3,8 @@
  *
  * No counterpart in the paper: a growth axis that replaces the
  * interpolation of PDFFlow Sec. 2.2 by a small network where the network is
- * accurate enough, with the interpolator as fallback and as the judge of the
- * network's error.
+ * accurate enough, with the interpolator as fallback and as the reference
+ * for the network's error.
  *
  * Network: (ln x, ln Q^2) scaled to [-1, 1]^2 -> 32 Fourier features
  * (sin and cos of pi (F z), F a fixed [16][2] matrix) -> four layers of width

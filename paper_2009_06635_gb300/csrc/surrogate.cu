@@ -15,7 +15,7 @@
 // silu(v) = v (1 + tanh(v/2)) / 2 with the hardware tanh approximation.
 // Weights are FP32 masters (Adam) with BF16 copies for the products.
 //
-// The interpolator is the judge: an error map over 64 x 64 tiles of (z0, z1)
+// The interpolator is the reference: an error map over 64 x 64 tiles of (z0, z1)
 // records the surrogate's largest error against the FP64 interpolator
 // (|s - v| / max(|v|, c_f), over flavours and validation points); evaluation
 // with fallback uses the surrogate only on tiles whose error is below the
