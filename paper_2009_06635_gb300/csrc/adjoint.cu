@@ -208,7 +208,7 @@ __device__ __forceinline__ void vjp_point(const GridView &g, const long long *xk
     double irho = 0.0, iL = 0.0;
     if (lowq) {
       irho = ddiv(1.0, ps.pq);
-      iL = ddiv(1.0, g.ln101);
+      iL = g.iln101;
     }
     double sx = 0.0, sq = 0.0;
     for (int f = 0; f < g.nf; f++) {

@@ -526,6 +526,7 @@ static int load_impl(const pdf_grid_desc *d, int nmem, const double *member_valu
   v.x0inv32 = (float)(1.0 / v.x0); v.idx0_32 = (float)v.idx0;
   v.q2maxinv32 = (float)(1.0 / v.q2max); v.idq_top32 = (float)v.idq_top;
   v.q2min32 = (float)v.q2min; v.ln101_32 = (float)v.ln101;
+  v.iln101 = 1.0 / v.ln101; v.iln101_32 = (float)(1.0 / v.ln101);
   v.q101_u32 = (float)v.q101_u;
   v.invalid = inv;
   for (int f = 0; f < nf; f++) g->pids[f] = d->pids[f];

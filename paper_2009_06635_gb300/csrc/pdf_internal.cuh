@@ -105,7 +105,8 @@ struct GridView {
   double lx0, idx0;           // p_x = (ln x - lx0) * idx0
   double lq2max, idq_top;     // p_q = -(ln Q^2 - lq2max) * idq_top
   double inv_q2min, ln101;    // ln 1.01
-  float x0inv32, idx0_32, q2maxinv32, idq_top32, q2min32, ln101_32;
+  double iln101;              // 1 / ln 1.01 (the low-Q^2 rule multiplies by it)
+  float x0inv32, idx0_32, q2maxinv32, idq_top32, q2min32, ln101_32, iln101_32;
   // fixed sites: the second x knot is (cell 1, t = 0), Q2max is the
   // degenerate top cell at u = 0, the knot below it (top_qc, u = 0), and
   // 1.01 Q2min is (q101_qc, q101_u)
@@ -164,14 +165,14 @@ __device__ __forceinline__ float pair_rule(float g0, float g1, float p) {
 
 // Low Q^2: f0 = F(Q2min), f1 = F(1.01 Q2min); rho = Q^2/Q2min, lr = ln rho.
 __device__ __forceinline__ double lowq_rule(double f0, double f1, double rho, double lr,
-                                            double ln101, LogTabs LT, const double *ET) {
+                                            double iln101, LogTabs LT, const double *ET) {
   double gam =
-      (__double_as_longlong(f0) > 0 && __double_as_longlong(f1) > 0) ? tlog(ddiv(f1, f0), LT) / ln101 : 1.0;
+      (__double_as_longlong(f0) > 0 && __double_as_longlong(f1) > 0) ? tlog(ddiv(f1, f0), LT) * iln101 : 1.0;
   double ex = (gam * rho + 1.0) - rho;
   return f0 * texp(ex * lr, ET);
 }
-__device__ __forceinline__ float lowq_rule(float f0, float f1, float rho, float lr, float ln101) {
-  float gam = (f0 > 0.f && f1 > 0.f) ? logf(f1 / f0) / ln101 : 1.f;
+__device__ __forceinline__ float lowq_rule(float f0, float f1, float rho, float lr, float iln101) {
+  float gam = (f0 > 0.f && f1 > 0.f) ? logf(f1 / f0) * iln101 : 1.f;
   float ex = (gam * rho + 1.f) - rho;
   return f0 * expf(ex * lr);
 }
@@ -179,17 +180,17 @@ __device__ __forceinline__ float lowq_rule(float f0, float f1, float rho, float 
 // Combine the site values of one point and flavour according to its class.
 // F(a, b) is the patch at x-site a (0/1) and q-site b (0/1).
 template <typename T, typename FN>
-__device__ __forceinline__ T combine(int cls, T px, T pq, T lr, T ln101, FN F) {
+__device__ __forceinline__ T combine(int cls, T px, T pq, T lr, T iln101, FN F) {
   switch (cls) {
     case C_IN: return F(0, 0);
     case C_LOWX: return pair_rule(F(0, 0), F(1, 0), px);
     case C_HIGHQ: return pair_rule(F(0, 0), F(0, 1), pq);
-    case C_LOWQ: return lowq_rule(F(0, 0), F(0, 1), pq, lr, ln101);
+    case C_LOWQ: return lowq_rule(F(0, 0), F(0, 1), pq, lr, iln101);
     case C_LOWX_HIGHQ:
       return pair_rule(pair_rule(F(0, 0), F(0, 1), pq), pair_rule(F(1, 0), F(1, 1), pq), px);
     case C_LOWX_LOWQ:
-      return pair_rule(lowq_rule(F(0, 0), F(0, 1), pq, lr, ln101),
-                       lowq_rule(F(1, 0), F(1, 1), pq, lr, ln101), px);
+      return pair_rule(lowq_rule(F(0, 0), F(0, 1), pq, lr, iln101),
+                       lowq_rule(F(1, 0), F(1, 1), pq, lr, iln101), px);
     default: return T(NAN);
   }
 }

@@ -64,7 +64,7 @@ __device__ __forceinline__ float eval_item32(const GridView &g, const Rec32 &R, 
     int qc = b ? R.qc1[p] : R.qc0[p];
     return site32(cb + ((size_t)qc * g.nx + xc) * stride, g.nfp, w, a, b);
   };
-  return combine<float>(R.cls[p], R.px[p], R.pq[p], R.lr[p], g.ln101_32, F);
+  return combine<float>(R.cls[p], R.px[p], R.pq[p], R.lr[p], g.iln101_32, F);
 }
 
 // An in-grid item: one site, its block offset taken once per point (the
