@@ -105,8 +105,7 @@ struct GridView {
   double lx0, idx0;           // p_x = (ln x - lx0) * idx0
   double lq2max, idq_top;     // p_q = -(ln Q^2 - lq2max) * idq_top
   double inv_q2min, ln101;    // ln 1.01
-  double iln101;              // 1 / ln 1.01 (the low-Q^2 rule multiplies by it)
-  float x0inv32, idx0_32, q2maxinv32, idq_top32, q2min32, ln101_32, iln101_32;
+  float x0inv32, idx0_32, q2maxinv32, idq_top32, q2min32, ln101_32;
   // fixed sites: the second x knot is (cell 1, t = 0), Q2max is the
   // degenerate top cell at u = 0, the knot below it (top_qc, u = 0), and
   // 1.01 Q2min is (q101_qc, q101_u)
@@ -115,6 +114,10 @@ struct GridView {
   float q101_u32;
 
   unsigned long long *invalid;
+  // 1 / ln 1.01 (the low-Q^2 rule multiplies by it); last, so that adding it
+  // left the offsets of the fields above as they were
+  double iln101;
+  float iln101_32;
 };
 
 // ---------------------------------------------------------------------------
@@ -165,9 +168,9 @@ __device__ __forceinline__ float pair_rule(float g0, float g1, float p) {
 
 // Low Q^2: f0 = F(Q2min), f1 = F(1.01 Q2min); rho = Q^2/Q2min, lr = ln rho.
 __device__ __forceinline__ double lowq_rule(double f0, double f1, double rho, double lr,
-                                            double iln101, LogTabs LT, const double *ET) {
+                                            double ln101, LogTabs LT, const double *ET) {
   double gam =
-      (__double_as_longlong(f0) > 0 && __double_as_longlong(f1) > 0) ? tlog(ddiv(f1, f0), LT) * iln101 : 1.0;
+      (__double_as_longlong(f0) > 0 && __double_as_longlong(f1) > 0) ? tlog(ddiv(f1, f0), LT) / ln101 : 1.0;
   double ex = (gam * rho + 1.0) - rho;
   return f0 * texp(ex * lr, ET);
 }

@@ -164,11 +164,11 @@ __device__ __forceinline__ double eval_item64(const GridView &g, const Rec64 &R,
       b = pair_rule(__ldg(C(1, 0)), __ldg(C(1, 1)), R.pq[p], LT, ET);
       break;
     default:  // C_LOWX_LOWQ
-      a = lowq_rule(__ldg(C(0, 0)), site_u(C(0, 1), R, p, 1), R.pq[p], R.lr[p], g.iln101, LT, ET);
-      b = lowq_rule(__ldg(C(1, 0)), site_u(C(1, 1), R, p, 1), R.pq[p], R.lr[p], g.iln101, LT, ET);
+      a = lowq_rule(__ldg(C(0, 0)), site_u(C(0, 1), R, p, 1), R.pq[p], R.lr[p], g.ln101, LT, ET);
+      b = lowq_rule(__ldg(C(1, 0)), site_u(C(1, 1), R, p, 1), R.pq[p], R.lr[p], g.ln101, LT, ET);
       break;
   }
-  if (lowq) return lowq_rule(a, b, R.pq[p], R.lr[p], g.iln101, LT, ET);
+  if (lowq) return lowq_rule(a, b, R.pq[p], R.lr[p], g.ln101, LT, ET);
   return pair_rule(a, b, prm, LT, ET);
 }
 
