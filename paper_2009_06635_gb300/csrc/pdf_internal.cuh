@@ -174,6 +174,14 @@ __device__ __forceinline__ double lowq_rule(double f0, double f1, double rho, do
   double ex = (gam * rho + 1.0) - rho;
   return f0 * texp(ex * lr, ET);
 }
+// The same with 1 / ln 1.01 given (a multiplication instead of the division).
+__device__ __forceinline__ double lowq_rule_r(double f0, double f1, double rho, double lr,
+                                              double iln101, LogTabs LT, const double *ET) {
+  double gam =
+      (__double_as_longlong(f0) > 0 && __double_as_longlong(f1) > 0) ? tlog(ddiv(f1, f0), LT) * iln101 : 1.0;
+  double ex = (gam * rho + 1.0) - rho;
+  return f0 * texp(ex * lr, ET);
+}
 __device__ __forceinline__ float lowq_rule(float f0, float f1, float rho, float lr, float iln101) {
   float gam = (f0 > 0.f && f1 > 0.f) ? logf(f1 / f0) * iln101 : 1.f;
   float ex = (gam * rho + 1.f) - rho;

@@ -125,6 +125,10 @@ __device__ __forceinline__ double site_t(const double *c, const Rec64 &R, int p,
 }
 
 // One item: column col of the point in slot p, of member m.
+// RCP: the low-Q^2 rule multiplies by 1 / ln 1.01 (the Monte Carlo kernel,
+// where a fifth of the events take it; the other kernels keep the division,
+// which left their register allocation as measured fastest).
+template <bool RCP>
 __device__ __forceinline__ double eval_item64(const GridView &g, const Rec64 &R, int p, int col, int m,
                                               LogTabs LT, const double *ET) {
   const double *cb = g.coef + (size_t)m * g.mstride + (size_t)col * 16;
@@ -164,11 +168,20 @@ __device__ __forceinline__ double eval_item64(const GridView &g, const Rec64 &R,
       b = pair_rule(__ldg(C(1, 0)), __ldg(C(1, 1)), R.pq[p], LT, ET);
       break;
     default:  // C_LOWX_LOWQ
-      a = lowq_rule(__ldg(C(0, 0)), site_u(C(0, 1), R, p, 1), R.pq[p], R.lr[p], g.ln101, LT, ET);
-      b = lowq_rule(__ldg(C(1, 0)), site_u(C(1, 1), R, p, 1), R.pq[p], R.lr[p], g.ln101, LT, ET);
+      if constexpr (RCP) {
+        a = lowq_rule_r(__ldg(C(0, 0)), site_u(C(0, 1), R, p, 1), R.pq[p], R.lr[p], g.iln101, LT, ET);
+        b = lowq_rule_r(__ldg(C(1, 0)), site_u(C(1, 1), R, p, 1), R.pq[p], R.lr[p], g.iln101, LT, ET);
+      } else {
+        a = lowq_rule(__ldg(C(0, 0)), site_u(C(0, 1), R, p, 1), R.pq[p], R.lr[p], g.ln101, LT, ET);
+        b = lowq_rule(__ldg(C(1, 0)), site_u(C(1, 1), R, p, 1), R.pq[p], R.lr[p], g.ln101, LT, ET);
+      }
       break;
   }
-  if (lowq) return lowq_rule(a, b, R.pq[p], R.lr[p], g.ln101, LT, ET);
+  if constexpr (RCP) {
+    if (lowq) return lowq_rule_r(a, b, R.pq[p], R.lr[p], g.iln101, LT, ET);
+  } else {
+    if (lowq) return lowq_rule(a, b, R.pq[p], R.lr[p], g.ln101, LT, ET);
+  }
   return pair_rule(a, b, prm, LT, ET);
 }
 
@@ -215,6 +228,7 @@ __device__ __forceinline__ void store_point(Rec64 &R, int slot, const PointSites
 }
 
 // Phase 2 over the first np slots: items (slot, column) in order, lane-strided.
+template <bool RCP>
 __device__ __forceinline__ void items64(const GridView &g, const Rec64 &R, int np, int nc, int cbase,
                                         int m, long long mo, double *__restrict__ out, LogTabs LT,
                                         const double *ET, int lane) {
@@ -222,7 +236,7 @@ __device__ __forceinline__ void items64(const GridView &g, const Rec64 &R, int n
   int p = lane / nc, c = lane - (lane / nc) * nc;
   const int dp = 32 / nc, dc = 32 - dp * nc;
   for (int k = lane; k < nitems; k += 32) {
-    out[mo + R.ob[p] + c] = eval_item64(g, R, p, cbase + c, m, LT, ET);
+    out[mo + R.ob[p] + c] = eval_item64<RCP>(g, R, p, cbase + c, m, LT, ET);
     c += dc;
     p += dp;
     if (c >= nc) { c -= nc; p++; }
@@ -313,7 +327,7 @@ k_xf64(GridView g, const double *__restrict__ xa, const double *__restrict__ qa,
     const int np = sort_slots<C_LOWX, C_HIGHQ, C_LOWQ, C_LOWX_HIGHQ, C_LOWX_LOWQ>(ps.cls, lane, slot);
     if (present) store_point(R, slot, ps, ob);
     __syncwarp();
-    items64(g, R, np, nc, cbase, 0, 0, out, LT, ET, lane);
+    items64<MODE == MODE_MC>(g, R, np, nc, cbase, 0, 0, out, LT, ET, lane);
     __syncwarp();
   };
 
@@ -384,9 +398,9 @@ k_xf64(GridView g, const double *__restrict__ xa, const double *__restrict__ qa,
     if (MODE == MODE_MEMBERS) {
       const int m1 = min(g.nmem, (chunk + 1) * mchunk);
       for (int m = chunk * mchunk; m < m1; m++)
-        items64(g, R, np, nc, cbase, m, (long long)m * n * nc, out, LT, ET, lane);
+        items64<MODE == MODE_MC>(g, R, np, nc, cbase, m, (long long)m * n * nc, out, LT, ET, lane);
     } else {
-      items64(g, R, np, nc, cbase, 0, 0, out, LT, ET, lane);
+      items64<MODE == MODE_MC>(g, R, np, nc, cbase, 0, 0, out, LT, ET, lane);
     }
     __syncwarp();
     if (kQueue && nq >= 32) {
