@@ -163,20 +163,52 @@ __global__ void __launch_bounds__(128) k_colsum(const bf16 *G, int rows, int ld,
   atomicAdd(db + n, s);
 }
 
+// Per-step state of a training call, kept on the device so that one captured
+// step (a CUDA graph) replays for every step: the batch index and the
+// learning-rate schedule follow it, and the step's last kernel advances it.
+struct TrainState {
+  long long it;  // step within the call
+  long long t;   // Adam steps taken before this one (across calls)
+};
+__global__ void k_train_state(TrainState *ts, long long t) {
+  ts->it = 0;
+  ts->t = t;
+}
+// this step's batch (whole batches of B in turn) into the fixed batch buffers
+__global__ void k_batch(const double *x, const double *q2, long long nb, int B, const TrainState *ts, double *xb,
+                        double *qb) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= B) return;
+  const long long o = (ts->it % nb) * B + i;
+  xb[i] = x[o];
+  qb[i] = q2[o];
+}
+
 struct AdamArgs {
   float *p, *gr, *m, *v;
   size_t n;
-  float lr, b1, b2, eps, c1, c2;  // c1 = 1 - b1^t, c2 = 1 - b2^t
+  float lr, lr_min, b1, b2, eps;  // peak and final learning rate
+  int warmup, steps;              // linear warm-up, then cosine decay to lr_min
+  const TrainState *ts;
 };
 __global__ void k_adam(AdamArgs a) {
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
+  const long long it = a.ts->it, t = a.ts->t + 1;
+  float lr;
+  if (it < a.warmup) {
+    lr = a.lr * (float)(it + 1) / (float)a.warmup;
+  } else {
+    const float prog = (float)(it - a.warmup) / (float)(a.steps - a.warmup > 0 ? a.steps - a.warmup : 1);
+    lr = a.lr_min + 0.5f * (a.lr - a.lr_min) * (1.f + cosf(3.14159265f * prog));
+  }
+  const float c1 = 1.f - powf(a.b1, (float)t), c2 = 1.f - powf(a.b2, (float)t);
   float g = a.gr[i];
   float m = a.b1 * a.m[i] + (1.f - a.b1) * g;
   float v = a.b2 * a.v[i] + (1.f - a.b2) * g * g;
   a.m[i] = m;
   a.v[i] = v;
-  a.p[i] -= a.lr * (m / a.c1) / (sqrtf(v / a.c2) + a.eps);
+  a.p[i] -= lr * (m / c1) / (sqrtf(v / c2) + a.eps);
 }
 
 // FP32 masters -> BF16 weight copies (W5 padded to 16 rows).
@@ -185,11 +217,16 @@ struct CastArgs {
   bf16 *w, *wt;
   size_t woff[5], boff[5];
   int nf;
+  TrainState *ts;  // when training: advanced by one step here (the step's last kernel)
 };
 // BF16 weights [out][in] (wbf_off), and for the backward products of layers
 // 1..4 their transposes [in][out] (wt_off); rows of W_5 beyond nf are zero
 __global__ void k_cast(CastArgs a) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0 && a.ts) {
+    a.ts->it += 1;
+    a.ts->t += 1;
+  }
   if (i >= (int)(kWbfTotal + kWtTotal)) return;
   if (i >= (int)kWbfTotal) {
     const int r = i - (int)kWbfTotal;
@@ -874,6 +911,10 @@ struct pdf_surrogate {
   bf16 *ht[5], *gt[5];  // their transposes [columns][bt]
   bf16 *wt;             // transposed BF16 weights of layers 1..4 (wt_off)
   long long bt;         // row stride of the transposes (max_batch rounded up to 64)
+  double *xb, *qb;      // the training step's batch
+  TrainState *ts;       // the training call's step state
+  cudaStream_t tstream; // training runs here (a capturable stream), ordered with the caller's by events
+  cudaEvent_t tev[2];
   float *z[4], *y, *t;
   double *xfbuf, *loss;
   long long step;
@@ -960,8 +1001,9 @@ int forward_backward(pdf_surrogate *s, int B, cudaStream_t st) {
   return check_launch("surrogate forward/backward");
 }
 
-void cast_weights(pdf_surrogate *s, cudaStream_t st) {
+void cast_weights(pdf_surrogate *s, cudaStream_t st, TrainState *ts = nullptr) {
   CastArgs a;
+  a.ts = ts;
   a.p = s->params;
   a.w = s->wbf;
   a.wt = s->wt;
@@ -1066,6 +1108,14 @@ extern "C" int pdf_surrogate_create_ex(const pdf_grid *grid, const float *params
   for (int l = 0; l < 4 && !rc; l++) rc = s->alloc(&s->gt[l], (size_t)SW * s->bt);
   if (!rc) rc = s->alloc(&s->gt[4], (size_t)SOUT * s->bt);
   if (!rc) rc = s->alloc(&s->wt, kWtTotal);
+  if (!rc) rc = s->alloc(&s->xb, (size_t)B);
+  if (!rc) rc = s->alloc(&s->qb, (size_t)B);
+  if (!rc) rc = s->alloc(&s->ts, 1);
+  if (!rc && cudaStreamCreateWithFlags(&s->tstream, cudaStreamNonBlocking) != cudaSuccess)
+    rc = set_error(PDF_ERR_CUDA, "pdf_surrogate_create: training stream");
+  for (int k = 0; k < 2 && !rc; k++)
+    if (cudaEventCreateWithFlags(&s->tev[k], cudaEventDisableTiming) != cudaSuccess)
+      rc = set_error(PDF_ERR_CUDA, "pdf_surrogate_create: training events");
   if (!rc) rc = s->alloc(&s->y, B * SOUT);
   if (!rc) rc = s->alloc(&s->t, B * SOUT);
   if (!rc) rc = s->alloc(&s->xfbuf, B * nf);
@@ -1098,6 +1148,14 @@ extern "C" int pdf_surrogate_create(const pdf_grid *grid, const float *params, c
 
 extern "C" int pdf_surrogate_free(pdf_surrogate *s) {
   if (!s) return PDF_OK;
+  if (s->tstream) {
+    cudaStreamSynchronize(s->tstream);
+    cudaStreamDestroy(s->tstream);
+  }
+  for (cudaEvent_t e : s->tev)
+    if (e) cudaEventDestroy(e);
+  for (void *p : {(void *)s->fb_idx, (void *)s->fb_x, (void *)s->fb_q, (void *)s->fb_out})
+    if (p) cudaFree(p);
   for (void *p : s->blocks) cudaFree(p);
   delete s;
   return PDF_OK;
@@ -1153,36 +1211,56 @@ extern "C" int pdf_surrogate_train(pdf_surrogate *s, const pdf_grid *grid, const
   if (B < 16 || B > s->max_batch || (size_t)B > n)
     return set_error(PDF_ERR_ARG, "pdf_surrogate_train: batch %d outside [16, min(max_batch, n)]", B);
   if (grid->v.nf != s->nf) return set_error(PDF_ERR_ARG, "pdf_surrogate_train: grid flavours differ");
+  if (cfg->steps < 1) return set_error(PDF_ERR_ARG, "pdf_surrogate_train: steps must be >= 1");
   std::lock_guard<std::mutex> lock(s->mu);
-  const size_t nb = n / (size_t)B;  // whole batches per pass
-  double last = 0.0;
-  for (int it = 0; it < cfg->steps; it++) {
-    const size_t bi = (size_t)it % nb;
-    const double *xb = x + bi * B, *qb = q2 + bi * B;
-    int rc = features_targets(s, grid, xb, qb, B, nullptr, st);
-    if (!rc) rc = forward_backward(s, B, st);
+  const long long nb = (long long)(n / (size_t)B);  // whole batches per pass
+  cudaStream_t ts = s->tstream;
+  // one training step; everything that changes from step to step (the batch,
+  // the learning rate, Adam's step count) is read from the device state, so
+  // the same enqueued work serves every step
+  auto step = [&]() -> int {
+    k_batch<<<(B + 255) / 256, 256, 0, ts>>>(x, q2, nb, B, s->ts, s->xb, s->qb);
+    int rc = features_targets(s, grid, s->xb, s->qb, B, nullptr, ts);
+    if (!rc) rc = forward_backward(s, B, ts);
     if (rc) return rc;
-    s->step++;
-    float lr = cfg->lr;
-    if (it < cfg->warmup) lr = cfg->lr * (float)(it + 1) / (float)cfg->warmup;
-    else {
-      float prog = (float)(it - cfg->warmup) / (float)(cfg->steps - cfg->warmup > 0 ? cfg->steps - cfg->warmup : 1);
-      lr = cfg->lr_min + 0.5f * (cfg->lr - cfg->lr_min) * (1.f + cosf(3.14159265f * prog));
+    AdamArgs a{s->params, s->grads, s->am, s->av, s->L.total, cfg->lr, cfg->lr_min, 0.9f, 0.999f, 1e-8f,
+               cfg->warmup, cfg->steps, s->ts};
+    k_adam<<<(unsigned)((s->L.total + 255) / 256), 256, 0, ts>>>(a);
+    cast_weights(s, ts, s->ts);
+    return check_launch("pdf_surrogate_train");
+  };
+  int rc = cuda_err(cudaEventRecord(s->tev[0], st), "pdf_surrogate_train");  // after the caller's work
+  if (!rc) rc = cuda_err(cudaStreamWaitEvent(ts, s->tev[0], 0), "pdf_surrogate_train");
+  if (rc) return rc;
+  k_train_state<<<1, 1, 0, ts>>>(s->ts, s->step);
+  rc = step();  // the first step directly (it also settles every kernel's launch attributes)
+  if (!rc && cfg->steps > 1) {
+    // the rest: one step captured as a CUDA graph and replayed (a step is ~26
+    // small dependent launches; replaying the graph spares their launch cost)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    rc = cuda_err(cudaStreamBeginCapture(ts, cudaStreamCaptureModeThreadLocal), "pdf_surrogate_train capture");
+    if (!rc) {
+      const int rs = step();
+      const cudaError_t e = cudaStreamEndCapture(ts, &graph);
+      rc = rs ? rs : cuda_err(e, "pdf_surrogate_train capture");
     }
-    AdamArgs a{s->params, s->grads, s->am, s->av, s->L.total, lr, 0.9f, 0.999f, 1e-8f,
-               1.f - powf(0.9f, (float)s->step), 1.f - powf(0.999f, (float)s->step)};
-    k_adam<<<(unsigned)((s->L.total + 255) / 256), 256, 0, st>>>(a);
-    cast_weights(s, st);
-    if (it == cfg->steps - 1) {
-      int e = cuda_err(cudaMemcpyAsync(&last, s->loss, sizeof(double), cudaMemcpyDeviceToHost, st), "train");
-      if (!e) e = cuda_err(cudaStreamSynchronize(st), "pdf_surrogate_train");
-      if (!e) e = check_tc(s, "pdf_surrogate_train");
-      if (e) return e;
-    }
+    if (!rc) rc = cuda_err(cudaGraphInstantiate(&exec, graph, 0), "pdf_surrogate_train graph");
+    for (int it = 1; it < cfg->steps && !rc; it++) rc = cuda_err(cudaGraphLaunch(exec, ts), "pdf_surrogate_train");
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
   }
+  double last = 0.0;
+  if (!rc) rc = cuda_err(cudaMemcpyAsync(&last, s->loss, sizeof(double), cudaMemcpyDeviceToHost, ts), "train");
+  if (!rc) rc = cuda_err(cudaStreamSynchronize(ts), "pdf_surrogate_train");
+  if (!rc) rc = check_tc(s, "pdf_surrogate_train");
+  cudaEventRecord(s->tev[1], ts);  // the caller's later work comes after training
+  cudaStreamWaitEvent(st, s->tev[1], 0);
+  if (rc) return rc;
+  s->step += cfg->steps;
   s->has_map = false;
   if (final_loss) *final_loss = last / ((double)B * s->nf);
-  return check_launch("pdf_surrogate_train");
+  return PDF_OK;
 }
 
 // After a synchronisation: did an inference kernel give up on a tensor-core wait?
