@@ -265,3 +265,23 @@ def test_host_path_and_mc_from_concurrent_threads(full, synth):
     want = (mc_alone.sum_w, mc_alone.sum_w2, mc_alone.sum_abs)  # fixed-order device sums
     for k in range(2):
         assert (mc[k].sum_w, mc[k].sum_w2, mc[k].sum_abs) == want, k
+
+
+def test_full_size_fp32_batch_sampled(full, synth):
+    """The FP32 step of the benchmark (the 1e7-point batch rounded to float,
+    all flavours + alpha_s in one launch), sampled against the oracle at the
+    float inputs."""
+    g, G, og = full
+    n = 10_000_000
+    x, q2 = synth.queries_full(n, 3)
+    x32, q32 = x.astype(np.float32), q2.astype(np.float32)
+    out, a = P.xfxq2_all_flavours_alphas(G, torch.from_numpy(x32).cuda(), torch.from_numpy(q32).cuda())
+    torch.cuda.synchronize()
+    idx = np.concatenate([np.random.default_rng(9).choice(n, 100_000, replace=False), [0, n - 1]])
+    ti = torch.from_numpy(idx).cuda()
+    xs, qs = x32[idx].astype(np.float64), q32[idx].astype(np.float64)
+    v, s, fl = og.xfxq2(xs, qs)
+    assert_parity(out[ti].cpu().numpy().astype(np.float64), v, s, fl, RTOL_FP32, "full-size fp32 sample")
+    av, asv = og.alphas(qs)
+    assert_parity(a[ti].cpu().numpy().astype(np.float64), av, asv, np.zeros(av.shape, bool), RTOL_FP32,
+                  "full-size fp32 alphas sample")

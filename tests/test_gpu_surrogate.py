@@ -148,3 +148,30 @@ def test_fused_inference_ragged_sizes_and_unaligned_output(setup, synth):
     assert out.data_ptr() % 16 == 4
     s.eval(xd[:n], qd[:n], out=out)
     assert np.array_equal(out.cpu().numpy(), full[:n])
+
+
+def test_full_size_inference_sampled(setup, synth):
+    """The benchmark's inference size and law (1e8 in-grid points, seed 8):
+    sampled rows bit for bit against the same points run alone, and against
+    the oracle network on a smaller sample."""
+    from oracle import mlp
+
+    g, G, Surrogate, params, freq, scale, bounds, og = setup
+    p = params.astype(np.float64).copy()
+    p[128 * 32:128 * 32 + 128] = np.random.default_rng(6).uniform(-0.5, 0.5, 128)  # b1
+    p32 = p.astype(np.float32)
+    s = Surrogate(G, p32, freq, max_batch=1024)
+    n = 100_000_000
+    x, q2 = synth.ingrid_samples(g, n, 8)
+    xd, qd = dev(x), dev(q2)
+    out = s.eval(xd, qd)
+    idx = np.sort(np.random.default_rng(10).choice(n, 20_000, replace=False))
+    ti = torch.from_numpy(idx).cuda()
+    got = out[ti].cpu().numpy()
+    del out
+    alone = s.eval(xd[ti], qd[ti]).cpu().numpy()
+    assert np.array_equal(got, alone)
+    k = idx[:2000]
+    want = mlp.predict(p32.astype(np.float64), x[k], q2[k], scale, freq.astype(np.float64), bounds, g.nflav, bf=True)
+    dy = np.abs(np.arcsinh(got[:2000].astype(np.float64) / scale) - np.arcsinh(want / scale))
+    assert np.quantile(dy, 0.99) < 2e-2 and dy.max() < 1e-1, (np.quantile(dy, 0.99), dy.max())
