@@ -1,14 +1,16 @@
 // adjoint.cu -- vector-Jacobian product of xfxq2_all_flavours.
 //
 // For L = sum_p sum_f c[p][f] xf_f(x_p, Q^2_p) the kernel returns dL/dx_p,
-// dL/dQ^2_p and accumulates dL/d(knot values).  One thread per point loops
+// dL/dQ^2_p and accumulates dL/d(knot values).  One lane per point loops
 // over the flavours: per flavour and patch site it evaluates the patch F and
-// its derivatives F_t, F_u from the cell's Bezier control points, pushes them
-// through the continuation rule of the point's class (chain rule), and
-// scatters c * dxf/dF * w_a(t) w_b(u) into the knot-value gradient with FP64
-// atomics, w_a the tangent-augmented Hermite weight of knot a (the patch is
-// linear in the knot values: dF/df_ab = w_a(t) w_b(u)).  The x and Q^2
-// derivatives are summed over flavours in registers, in a fixed order.
+// its derivatives F_t, F_u from the cell's Bezier control points (in
+// float-float for in-grid points, FP64 otherwise), pushes them through the
+// continuation rule of the point's class (chain rule), and scatters
+// c * dxf/dF * w_a(t) w_b(u) into the knot-value gradient with FP64 atomics,
+// w_a the tangent-augmented Hermite weight of knot a (the patch is linear in
+// the knot values: dF/df_ab = w_a(t) w_b(u)).  The x and Q^2 derivatives are
+// summed over flavours in registers, in a fixed order.  Points that need a
+// continuation rule are queued per warp by kind (kernel comment below).
 //
 // A query exactly on the last x (or top Q^2) knot is taken in the last
 // proper cell at t = 1 (u = 1), so the derivative there is the one-sided one
