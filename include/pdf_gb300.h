@@ -23,6 +23,8 @@
  * Conventions for every call:
  *   - Return value: PDF_OK (0) on success, a negative PDF_ERR_* code
  *     otherwise; pdf_last_error() then describes the failure (per thread).
+ *     No C++ exception leaves the library: a failed host allocation inside a
+ *     call returns PDF_ERR_ALLOC.
  *   - Query and output pointers of the non-"_host" calls are DEVICE memory
  *     owned by the caller; the call enqueues its kernels on `stream`
  *     (0 = the legacy default stream) and returns without waiting.
@@ -132,9 +134,10 @@ PDF_API int pdf_grid_nmembers(const pdf_grid *grid);
  * pdf_load_lhapdf: members first_member .. first_member + nmem - 1 of the set
  * in set_dir onto the current device (nmem = 1: pdf_load_grid; nmem > 1:
  * pdf_load_grid_members, every member with the same knots and flavours).
- * Errors: PDF_ERR_NULL, PDF_ERR_ARG (unreadable file, bad member range),
- * PDF_ERR_GRID (malformed file; the message names the file and the line's
- * subgrid), and those of pdf_load_grid.
+ * Errors: PDF_ERR_NULL, PDF_ERR_ARG (unreadable file, a member range not
+ * inside the four-digit file numbers 0..9999), PDF_ERR_GRID (malformed file;
+ * the message names the file and the line's subgrid), PDF_ERR_ALLOC (host
+ * memory), and those of pdf_load_grid.
  *
  * pdf_lhapdf_read / pdf_lhapdf_desc / pdf_lhapdf_free: the parser alone, on
  * the host (no device work): read one .info + .dat pair into a host object,

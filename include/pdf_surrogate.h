@@ -28,7 +28,9 @@
  * a PDF_ERR_* code (see pdf_gb300.h).  At most 16 flavours.  The calls that
  * use the surrogate's own buffers (training, loss/gradient, error map,
  * evaluation with fallback, setting parameters) are serialised per
- * surrogate; pdf_surrogate_eval uses none and runs concurrently.
+ * surrogate; pdf_surrogate_eval uses none and runs concurrently.  A grid
+ * passed to training, the error map or the fallback must have as many
+ * flavours as the surrogate's own (PDF_ERR_ARG otherwise).
  */
 #ifndef PDF_SURROGATE_H
 #define PDF_SURROGATE_H

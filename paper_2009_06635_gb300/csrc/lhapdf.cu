@@ -22,10 +22,12 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <string>
 #include <vector>
 
+#include "guard.cuh"
 #include "pdf_internal.cuh"
 
 using pdfgb::set_error;
@@ -131,8 +133,9 @@ int parse_dat(const char *path, pdf_lhapdf_set &S) {
                        nx, nq, nf);
     std::vector<int> pid(nf);
     for (size_t f = 0; f < nf; f++) {
-      pid[f] = (int)std::lround(ps[f]);
-      if ((double)pid[f] != ps[f]) return set_error(PDF_ERR_GRID, "lhapdf: %s: flavour %g is not an integer", path, ps[f]);
+      if (!(std::fabs(ps[f]) <= 1e6) || std::nearbyint(ps[f]) != ps[f])
+        return set_error(PDF_ERR_GRID, "lhapdf: %s: flavour %g is not a particle id", path, ps[f]);
+      pid[f] = (int)ps[f];
     }
     if (nblock == 0) {
       S.x = xs;
@@ -212,13 +215,13 @@ std::string member_path(const std::string &dir, const std::string &name, int m) 
 extern "C" int pdf_lhapdf_read(const char *info_path, const char *dat_path, pdf_lhapdf_set **out) {
   if (!info_path || !dat_path || !out) return set_error(PDF_ERR_NULL, "pdf_lhapdf_read: NULL argument");
   *out = nullptr;
-  pdf_lhapdf_set *S = new (std::nothrow) pdf_lhapdf_set();
-  if (!S) return set_error(PDF_ERR_ALLOC, "pdf_lhapdf_read: host allocation failed");
-  int rc = parse_dat(dat_path, *S);
-  if (!rc) rc = parse_info(info_path, *S);
-  if (rc) { delete S; return rc; }
-  *out = S;
-  return PDF_OK;
+  return pdfgb::guarded("pdf_lhapdf_read", [&] {
+    std::unique_ptr<pdf_lhapdf_set> S(new pdf_lhapdf_set());
+    int rc = parse_dat(dat_path, *S);
+    if (!rc) rc = parse_info(info_path, *S);
+    if (!rc) *out = S.release();
+    return rc;
+  });
 }
 
 extern "C" int pdf_lhapdf_desc(const pdf_lhapdf_set *S, pdf_grid_desc *desc) {
@@ -232,25 +235,21 @@ extern "C" int pdf_lhapdf_free(pdf_lhapdf_set *S) {
   return PDF_OK;
 }
 
-extern "C" int pdf_load_lhapdf(const char *set_dir, int first_member, int nmem, pdf_grid **out) {
-  if (!set_dir || !out) return set_error(PDF_ERR_NULL, "pdf_load_lhapdf: NULL argument");
-  *out = nullptr;
-  if (first_member < 0 || nmem < 1) return set_error(PDF_ERR_ARG, "pdf_load_lhapdf: bad member range");
+namespace {
+
+int load_lhapdf(const char *set_dir, int first_member, int nmem, pdf_grid **out) {
   std::string dir(set_dir);
   while (dir.size() > 1 && dir.back() == '/') dir.pop_back();
   const size_t slash = dir.find_last_of('/');
   const std::string name = slash == std::string::npos ? dir : dir.substr(slash + 1);
   const std::string info = dir + "/" + name + ".info";
-  pdf_lhapdf_set *S0 = nullptr;
-  int rc = pdf_lhapdf_read(info.c_str(), member_path(dir, name, first_member).c_str(), &S0);
+  pdf_lhapdf_set *S0p = nullptr;
+  int rc = pdf_lhapdf_read(info.c_str(), member_path(dir, name, first_member).c_str(), &S0p);
   if (rc) return rc;
+  const std::unique_ptr<pdf_lhapdf_set> S0(S0p);
   pdf_grid_desc d;
   fill_desc(*S0, &d);
-  if (nmem == 1) {
-    rc = pdf_load_grid(&d, out);
-    delete S0;
-    return rc;
-  }
+  if (nmem == 1) return pdf_load_grid(&d, out);
   std::vector<double> all;
   all.reserve(S0->values.size() * (size_t)nmem);
   all.insert(all.end(), S0->values.begin(), S0->values.end());
@@ -264,6 +263,16 @@ extern "C" int pdf_load_lhapdf(const char *set_dir, int first_member, int nmem, 
     if (!rc) all.insert(all.end(), Sm.values.begin(), Sm.values.end());
   }
   if (!rc) rc = pdf_load_grid_members(&d, nmem, all.data(), out);
-  delete S0;
   return rc;
+}
+
+}  // namespace
+
+extern "C" int pdf_load_lhapdf(const char *set_dir, int first_member, int nmem, pdf_grid **out) {
+  if (!set_dir || !out) return set_error(PDF_ERR_NULL, "pdf_load_lhapdf: NULL argument");
+  *out = nullptr;
+  if (first_member < 0 || nmem < 1 || nmem > 10000 - first_member)
+    return set_error(PDF_ERR_ARG, "pdf_load_lhapdf: members %d..%lld outside 0..9999", first_member,
+                     (long long)first_member + (nmem > 0 ? nmem - 1 : 0));
+  return pdfgb::guarded("pdf_load_lhapdf", [&] { return load_lhapdf(set_dir, first_member, nmem, out); });
 }

@@ -28,6 +28,7 @@
 #include <new>
 #include <vector>
 
+#include "guard.cuh"
 #include "pdf_internal.cuh"
 #include "pdf_surrogate.h"
 
@@ -1029,18 +1030,10 @@ int features_targets(pdf_surrogate *s, const pdf_grid *grid, const double *x, co
 
 using namespace pdfgb;
 
-extern "C" int pdf_surrogate_create_ex(const pdf_grid *grid, const float *params, const float *freq, int max_batch,
-                                       int target, pdf_surrogate **out) {
-  if (!grid || !params || !freq || !out) return set_error(PDF_ERR_NULL, "pdf_surrogate_create: NULL argument");
-  *out = nullptr;
-  if (target != PDF_SURR_ASINH && target != PDF_SURR_ENVELOPE)
-    return set_error(PDF_ERR_ARG, "pdf_surrogate_create: unknown target %d", target);
+// Fills a new surrogate (its pointers null); on failure the caller frees it.
+static int create_body(pdf_surrogate *s, const pdf_grid *grid, const float *params, const float *freq,
+                       int max_batch, int target) {
   const int nf = grid->v.nf;
-  if (nf > SOUT) return set_error(PDF_ERR_ARG, "pdf_surrogate_create: at most %d flavours", SOUT);
-  if (max_batch < 16 || max_batch > (1 << 22))
-    return set_error(PDF_ERR_ARG, "pdf_surrogate_create: max_batch %d outside [16, 4M]", max_batch);
-  pdf_surrogate *s = new (std::nothrow) pdf_surrogate();
-  if (!s) return set_error(PDF_ERR_ALLOC, "pdf_surrogate_create: host allocation");
   s->nf = nf;
   s->max_batch = max_batch;
   cudaGetDevice(&s->device);
@@ -1051,7 +1044,7 @@ extern "C" int pdf_surrogate_create_ex(const pdf_grid *grid, const float *params
   std::vector<double> vals((size_t)v.nrows * v.nx * v.nf);
   int rc = cuda_err(cudaMemcpy(vals.data(), v.vals, vals.size() * sizeof(double), cudaMemcpyDeviceToHost),
                     "pdf_surrogate_create");
-  if (rc) { delete s; return rc; }
+  if (rc) return rc;
   for (int f = 0; f < SOUT; f++) s->c.scale[f] = 1.f;
   for (int f = 0; f < nf; f++) {
     double m = 0.0;
@@ -1063,7 +1056,7 @@ extern "C" int pdf_surrogate_create_ex(const pdf_grid *grid, const float *params
   // ln E_f linear in ln x between knots, sampled at ENVN + 1 equal steps
   std::vector<double> xk(v.nx);
   rc = cuda_err(cudaMemcpy(xk.data(), v.xk, v.nx * sizeof(double), cudaMemcpyDeviceToHost), "pdf_surrogate_create");
-  if (rc) { delete s; return rc; }
+  if (rc) return rc;
   std::vector<float> envt((size_t)(ENVN + 1) * SOUT, 0.f);
   {
     std::vector<double> lx(v.nx), le(v.nx);
@@ -1125,18 +1118,38 @@ extern "C" int pdf_surrogate_create_ex(const pdf_grid *grid, const float *params
   if (!rc) rc = s->alloc(&s->tile_cnt, MAPN * MAPN);
   if (!rc) rc = s->alloc(&s->nfb, 1);
   if (!rc) rc = s->alloc(&s->tc_err, 1);
-  if (rc) { pdf_surrogate_free(s); return rc; }
-  cudaMemcpy(s->params, params, P * sizeof(float), cudaMemcpyHostToDevice);
-  cudaMemcpy(s->scale_d, s->c.scale, SOUT * sizeof(float), cudaMemcpyHostToDevice);
-  cudaMemcpy(envt_d, envt.data(), envt.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (rc) return rc;
+  const char *what = "pdf_surrogate_create";
+  rc = cuda_err(cudaMemcpy(s->params, params, P * sizeof(float), cudaMemcpyHostToDevice), what);
+  if (!rc) rc = cuda_err(cudaMemcpy(s->scale_d, s->c.scale, SOUT * sizeof(float), cudaMemcpyHostToDevice), what);
+  if (!rc) rc = cuda_err(cudaMemcpy(envt_d, envt.data(), envt.size() * sizeof(float), cudaMemcpyHostToDevice), what);
+  if (!rc) rc = cuda_err(cudaMemset(s->am, 0, P * sizeof(float)), what);
+  if (!rc) rc = cuda_err(cudaMemset(s->av, 0, P * sizeof(float)), what);
+  if (!rc) rc = cuda_err(cudaMemset(s->mask, 0, MAPN * MAPN), what);
+  if (!rc) rc = cuda_err(cudaMemset(s->tc_err, 0, sizeof(int)), what);
+  if (rc) return rc;
   s->c.envt = envt_d;
-  cudaMemset(s->am, 0, P * sizeof(float));
-  cudaMemset(s->av, 0, P * sizeof(float));
-  cudaMemset(s->mask, 0, MAPN * MAPN);
-  cudaMemset(s->tc_err, 0, sizeof(int));
   cast_weights(s, 0);
-  rc = cuda_err(cudaDeviceSynchronize(), "pdf_surrogate_create");
-  if (rc) { pdf_surrogate_free(s); return rc; }
+  return cuda_err(cudaDeviceSynchronize(), what);
+}
+
+extern "C" int pdf_surrogate_create_ex(const pdf_grid *grid, const float *params, const float *freq, int max_batch,
+                                       int target, pdf_surrogate **out) {
+  if (!grid || !params || !freq || !out) return set_error(PDF_ERR_NULL, "pdf_surrogate_create: NULL argument");
+  *out = nullptr;
+  if (target != PDF_SURR_ASINH && target != PDF_SURR_ENVELOPE)
+    return set_error(PDF_ERR_ARG, "pdf_surrogate_create: unknown target %d", target);
+  if (grid->v.nf > SOUT) return set_error(PDF_ERR_ARG, "pdf_surrogate_create: at most %d flavours", SOUT);
+  if (max_batch < 16 || max_batch > (1 << 22))
+    return set_error(PDF_ERR_ARG, "pdf_surrogate_create: max_batch %d outside [16, 4M]", max_batch);
+  pdf_surrogate *s = new (std::nothrow) pdf_surrogate();
+  if (!s) return set_error(PDF_ERR_ALLOC, "pdf_surrogate_create: host allocation");
+  const int rc = guarded("pdf_surrogate_create",
+                         [&] { return create_body(s, grid, params, freq, max_batch, target); });
+  if (rc) {
+    pdf_surrogate_free(s);
+    return rc;
+  }
   *out = s;
   return PDF_OK;
 }
@@ -1302,11 +1315,14 @@ extern "C" int pdf_surrogate_eval(const pdf_surrogate *s, const double *x, const
   return launch_infer(s, x, q2, n, out, nullptr, nullptr, nullptr, nullptr, st);
 }
 
-extern "C" int pdf_surrogate_build_error_map(pdf_surrogate *s, const pdf_grid *grid, const double *x,
-                                             const double *q2, size_t n, double threshold, double *stats) {
-  if (!s || !grid || !x || !q2) return set_error(PDF_ERR_NULL, "pdf_surrogate_build_error_map: NULL argument");
-  if (n == 0) return set_error(PDF_ERR_ARG, "pdf_surrogate_build_error_map: no validation points");
+static int error_map_body(pdf_surrogate *s, const pdf_grid *grid, const double *x, const double *q2, size_t n,
+                          double threshold, double *stats) {
   std::lock_guard<std::mutex> lock(s->mu);
+  // host copies first, so that nothing below can throw while device scratch is held
+  std::vector<unsigned int> bits(MAPN * MAPN), cnt(MAPN * MAPN);
+  std::vector<unsigned char> m(MAPN * MAPN);
+  std::vector<float> errs;
+  errs.reserve(MAPN * MAPN);
   float *sv = nullptr;
   double *iv = nullptr;
   int rc = cuda_err(cudaMalloc(&sv, n * s->nf * sizeof(float)), "error map");
@@ -1320,8 +1336,6 @@ extern "C" int pdf_surrogate_build_error_map(pdf_surrogate *s, const pdf_grid *g
     k_make_mask<<<(MAPN * MAPN + 255) / 256, 256>>>(s->tile_bits, s->tile_cnt, (float)threshold, s->mask);
     rc = check_launch("error map");
   }
-  std::vector<unsigned int> bits(MAPN * MAPN), cnt(MAPN * MAPN);
-  std::vector<unsigned char> m(MAPN * MAPN);
   if (!rc) rc = cuda_err(cudaMemcpy(bits.data(), s->tile_bits, bits.size() * 4, cudaMemcpyDeviceToHost), "error map");
   if (!rc) rc = cuda_err(cudaMemcpy(cnt.data(), s->tile_cnt, cnt.size() * 4, cudaMemcpyDeviceToHost), "error map");
   if (!rc) rc = cuda_err(cudaMemcpy(m.data(), s->mask, m.size(), cudaMemcpyDeviceToHost), "error map");
@@ -1332,7 +1346,6 @@ extern "C" int pdf_surrogate_build_error_map(pdf_surrogate *s, const pdf_grid *g
   // stats: [tiles accepted, tiles with samples, largest error on sampled tiles, median tile error]
   int ok = 0, sampled = 0;
   float worst = 0.f;
-  std::vector<float> errs;
   for (size_t t = 0; t < bits.size(); t++) {
     ok += m[t];
     if (cnt[t] > 0) {
@@ -1358,11 +1371,21 @@ extern "C" int pdf_surrogate_build_error_map(pdf_surrogate *s, const pdf_grid *g
   return PDF_OK;
 }
 
+extern "C" int pdf_surrogate_build_error_map(pdf_surrogate *s, const pdf_grid *grid, const double *x,
+                                             const double *q2, size_t n, double threshold, double *stats) {
+  if (!s || !grid || !x || !q2) return set_error(PDF_ERR_NULL, "pdf_surrogate_build_error_map: NULL argument");
+  if (n == 0) return set_error(PDF_ERR_ARG, "pdf_surrogate_build_error_map: no validation points");
+  if (grid->v.nf != s->nf) return set_error(PDF_ERR_ARG, "pdf_surrogate_build_error_map: grid flavours differ");
+  return guarded("pdf_surrogate_build_error_map",
+                 [&] { return error_map_body(s, grid, x, q2, n, threshold, stats); });
+}
+
 extern "C" int pdf_surrogate_eval_fallback(pdf_surrogate *s, const pdf_grid *grid, const double *x,
                                            const double *q2, size_t n, double *out, unsigned long long *n_fallback,
                                            cudaStream_t st) {
   if (!s || !grid) return set_error(PDF_ERR_NULL, "pdf_surrogate_eval_fallback: NULL argument");
   if (n > 0 && (!x || !q2 || !out)) return set_error(PDF_ERR_NULL, "pdf_surrogate_eval_fallback: NULL array");
+  if (grid->v.nf != s->nf) return set_error(PDF_ERR_ARG, "pdf_surrogate_eval_fallback: grid flavours differ");
   if (!s->has_map) return set_error(PDF_ERR_ARG, "pdf_surrogate_eval_fallback: build the error map first");
   if (n > 0xFFFFFFFFull) return set_error(PDF_ERR_ARG, "pdf_surrogate_eval_fallback: n too large");
   if (n == 0) { if (n_fallback) *n_fallback = 0; return PDF_OK; }

@@ -59,6 +59,7 @@ def test_malformed_files_are_refused(tmp_path, synth):
         "bad number": "\n".join(lines[:6] + ["1.0 abc 2.0"] + lines[7:]) + "\n",
         "unclosed block": "\n".join(lines[:-1]) + "\n",
         "non-integer pid": "\n".join(lines[:5] + [lines[5].replace("21", "21.5")] + lines[6:]) + "\n",
+        "pid out of int range": "\n".join(lines[:5] + [lines[5].replace("21", "1e300")] + lines[6:]) + "\n",
     }
     for what, text in cases.items():
         bad = write(tmp_path / "bad.dat", text)
@@ -96,3 +97,18 @@ def test_comments_and_subgrids_with_other_x_knots(tmp_path, synth):
     lines[k] = " ".join(xs)
     with pytest.raises(P.PdfError, match="different x knots"):
         P.read_lhapdf(info, write(tmp_path / "x.dat", "\n".join(lines) + "\n"))
+
+
+def test_member_range_is_checked_before_any_file_or_device_work(tmp_path):
+    """Member files carry four-digit numbers: a range leaving 0..9999 (or one
+    whose end overflows an int) is refused with PDF_ERR_ARG before the set
+    directory is even opened."""
+    import ctypes
+    from paper_2009_06635_gb300 import _native
+    lib = _native.load()
+    h = ctypes.c_void_p(None)
+    for first, nmem in ((9999, 2), (-1, 1), (0, 0), (5, 2**31 - 1), (2**31 - 1, 1)):
+        rc = lib.pdf_load_lhapdf(str(tmp_path / "NOSET").encode(), first, nmem, ctypes.byref(h))
+        assert rc == -6, (first, nmem, rc)
+        assert "outside 0..9999" in _native.last_error()
+        assert h.value is None
