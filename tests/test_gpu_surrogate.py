@@ -175,3 +175,27 @@ def test_full_size_inference_sampled(setup, synth):
     want = mlp.predict(p32.astype(np.float64), x[k], q2[k], scale, freq.astype(np.float64), bounds, g.nflav, bf=True)
     dy = np.abs(np.arcsinh(got[:2000].astype(np.float64) / scale) - np.arcsinh(want / scale))
     assert np.quantile(dy, 0.99) < 2e-2 and dy.max() < 1e-1, (np.quantile(dy, 0.99), dy.max())
+
+
+def test_grid_with_other_flavours_is_refused(setup, synth):
+    """The error map, training and the fallback write [n][nflav] rows of the
+    surrogate's width: a grid with another flavour count is an argument
+    error, not an out-of-bounds write."""
+    g, G, Surrogate, params, freq, scale, bounds, og = setup
+    g11 = synth.grid_single_subgrid()
+    assert g11.nflav != g.nflav
+    G11 = P.pdf_load_grid(g11)
+    s = Surrogate(G, params, freq, max_batch=1024)
+    x, q2 = synth.ingrid_samples(g, 256, 23)
+    xd, qd = dev(x), dev(q2)
+    with pytest.raises(P.PdfError, match="flavours differ"):
+        s.build_error_map(G11, xd, qd)
+    with pytest.raises(P.PdfError, match="flavours differ"):
+        s.train(G11, xd, qd, batch=64, steps=1)
+    s.build_error_map(G, xd, qd)
+    with pytest.raises(P.PdfError, match="flavours differ"):
+        s.eval_fallback(G11, xd, qd)
+    out, _ = s.eval_fallback(G, xd, qd)  # the matching grid still works
+    assert torch.isfinite(out).all()
+    s.free()
+    G11.free()
