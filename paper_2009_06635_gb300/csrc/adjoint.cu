@@ -15,6 +15,9 @@
 // A query exactly on the last x (or top Q^2) knot is taken in the last
 // proper cell at t = 1 (u = 1), so the derivative there is the one-sided one
 // of that cell.
+#include <algorithm>
+#include <mutex>
+
 #include "ff.cuh"
 #include "sites.cuh"
 
@@ -103,15 +106,26 @@ __device__ __forceinline__ RuleD rule_d(double f0, double f1, double p, bool low
   return R;
 }
 
+// Where an in-grid point leaves its knot-weight terms for the warp's
+// contraction (k_vjp_sorted): its 16 weights w_b(u) w_a(t) and its nf
+// cotangents as float-float pairs, its cell and the cell's first knot.
+struct Staged {
+  float2 *w, *c;
+  int cell, xk0, qk0;
+  bool ing;
+};
+
 // ---- in-grid points on a float-float-safe grid ------------------------------
 // An in-grid point: F_t dt/dx = sum_lk B_l(u) B'_k(t) dt/dx c_lk and F_u du/dQ^2
 // (likewise) for every flavour in float-float on the FMA pipe from the
 // float-float control points (good to ~2^-46 of sum |w c|); the coordinate
-// sums and the knot scatter (the patch is linear in the knot values with
-// weights w_a(t) w_b(u)) in FP64.
+// sums in FP64.  The knot scatter (the patch is linear in the knot values
+// with weights w_a(t) w_b(u)): FP64 products and atomics per point, or
+// (STAGE) the weights and cotangents staged for the warp's contraction.
+template <bool STAGE>
 __device__ __forceinline__ void vjp_ingrid_ff(const GridView &g, const Site64 &X, const Site64 &Q, long long p,
                                               const double *__restrict__ cot, double *__restrict__ gx,
-                                              double *__restrict__ gq, double *__restrict__ gv) {
+                                              double *__restrict__ gq, double *__restrict__ gv, Staged *st) {
   ff2 wt[16], wu[16];
   {
     ff2 xb[4], xd[4], qb[4], qd[4];
@@ -129,10 +143,28 @@ __device__ __forceinline__ void vjp_ingrid_ff(const GridView &g, const Site64 &X
     }
   }
   double W[16];  // knot weights w_b(u) w_a(t), 0 where the knot is outside the grid
+  if (!STAGE) {
 #pragma unroll
-  for (int m = 0; m < 16; m++) {
-    const int row = Q.k0 + (m >> 2), col = X.k0 + (m & 3);
-    W[m] = (row >= 0 && row < g.nrows && col >= 0 && col < g.nx) ? Q.w[m >> 2] * X.w[m & 3] : 0.0;
+    for (int m = 0; m < 16; m++) {
+      const int row = Q.k0 + (m >> 2), col = X.k0 + (m & 3);
+      W[m] = (row >= 0 && row < g.nrows && col >= 0 && col < g.nx) ? Q.w[m >> 2] * X.w[m & 3] : 0.0;
+    }
+  } else if (gv) {
+    ff2 wq[4], wx[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      wq[k] = ff_of(Q.w[k]);
+      wx[k] = ff_of(X.w[k]);
+    }
+#pragma unroll
+    for (int m = 0; m < 16; m++) {
+      const ff2 w = ff_mul(wq[m >> 2], wx[m & 3]);
+      st->w[m] = make_float2(w.h, w.l);
+    }
+    st->cell = Q.c * g.nx + X.c;
+    st->xk0 = X.k0;
+    st->qk0 = Q.k0;
+    st->ing = true;
   }
   const float4 *cb = reinterpret_cast<const float4 *>(g.coefff + ((size_t)Q.c * g.nx + X.c) * 16 * g.nfp);
   const long long k0 = ((long long)Q.k0 * g.nx + X.k0) * g.nf;  // knot (Q.k0, X.k0); the used ones are >= 0
@@ -150,7 +182,12 @@ __device__ __forceinline__ void vjp_ingrid_ff(const GridView &g, const Site64 &X
     }
     sx = fma(c, f2d(th) + f2d(tl), sx);
     sq = fma(c, f2d(uh) + f2d(ul), sq);
-    if (gv && (__double_as_longlong(c) << 1) != 0) {
+    if (STAGE) {
+      if (gv) {
+        const ff2 cf = ff_of(c);
+        st->c[f] = make_float2(cf.h, cf.l);
+      }
+    } else if (gv && (__double_as_longlong(c) << 1) != 0) {
 #pragma unroll
       for (int m = 0; m < 16; m++)
         if ((__double_as_longlong(W[m]) << 1) != 0)
@@ -162,12 +199,14 @@ __device__ __forceinline__ void vjp_ingrid_ff(const GridView &g, const Site64 &X
 }
 
 // The whole vector-Jacobian product of one point: d/dx, d/dQ^2 into gx[p],
-// gq[p], knot-value contributions added to gv.
+// gq[p], knot-value contributions added to gv (an in-grid point's staged
+// for the warp's contraction instead, with STAGE).
+template <bool STAGE>
 __device__ __forceinline__ void vjp_point(const GridView &g, const long long *xkeys, const long long *qkeys,
                                           LogTabs LT, const double *ET, long long p, const double *__restrict__ xa,
                                           const double *__restrict__ qa, const double *__restrict__ cot,
                                           double *__restrict__ gx, double *__restrict__ gq,
-                                          double *__restrict__ gv) {
+                                          double *__restrict__ gv, Staged *st) {
     const double x = xa[p], q2 = qa[p];
     double lq;
     PointSites<double> ps = sites(g, xkeys, qkeys, x, q2, LT, lq);
@@ -199,7 +238,7 @@ __device__ __forceinline__ void vjp_point(const GridView &g, const long long *xk
       make_site(Q[b], g.qW + 16 * qc, u, s, qc, row - 1, dpos);
     }
     if (cls == C_IN && g.ff) {
-      vjp_ingrid_ff(g, X[0], Q[0], p, cot, gx, gq, gv);
+      vjp_ingrid_ff<STAGE>(g, X[0], Q[0], p, cot, gx, gq, gv, st);
       return;
     }
     const int nsx = lowx ? 2 : 1;
@@ -357,9 +396,210 @@ k_vjp(GridView g, const double *__restrict__ xa, const double *__restrict__ qa, 
       break;
     }
     __syncwarp();
-    if (pp >= 0) vjp_point(g, xkeys, qkeys, LT, ET, pp, xa, qa, cot, gx, gq, gv);
+    if (pp >= 0) vjp_point<false>(g, xkeys, qkeys, LT, ET, pp, xa, qa, cot, gx, gq, gv, nullptr);
     __syncwarp();
   }
+}
+
+// ---- large batches: points sorted by cell ------------------------------------
+// A counting sort puts the continuation points first (by kind: x rule, Q rule,
+// both; then invalid points) and the in-grid points after them, cell by cell.
+// A warp then takes 32 consecutive sorted points: continuation warps are of
+// one kind (as with the queues above), and in-grid warps hold runs of points
+// that share a cell, hence the same 16 knots.  Their knot-value gradient is
+// contracted over the run in float-float on the FMA pipe,
+//   dL/df_(ab, f) += sum_p c_pf w_b(u_p) w_a(t_p),
+// and added with one FP64 atomic per knot and flavour per run instead of one
+// per point (the per-point products were a third of an in-grid point's FP64
+// work, and their atomics a stream of L2 reductions).
+constexpr int kSortBins0 = 4;        // bins 0..2: continuation kinds, 3: invalid, then the cells
+constexpr int kSortMaxBins = 65540;  // above this the grid has too many cells for runs to form
+constexpr long long kSortMinN = 16384;
+constexpr int kStPad = 17;           // float2 per staged row (16 used): 2-way bank conflicts at most
+
+// Sort key of a point: its kind for a continuation or invalid point, else
+// kSortBins0 + (Q cell) nx + (x cell), from integer range tests and searches
+// on the raw bit patterns (no logarithm); counts per key in cnt.
+__global__ void __launch_bounds__(256) k_adj_key(GridView g, const double *__restrict__ xa,
+                                                 const double *__restrict__ qa, long long n, unsigned nb,
+                                                 unsigned *__restrict__ keys, unsigned *__restrict__ cnt) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  long long *xkeys = reinterpret_cast<long long *>(smem);
+  long long *qkeys = reinterpret_cast<long long *>(smem + keys_bytes(g.nx, 8));
+  load_keys<double>(g, xkeys, 0);
+  load_keys<double>(g, qkeys, 1);
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const long long kxlast = __double_as_longlong(g.xlast), kx0 = __double_as_longlong(g.x0);
+  const long long kqmin = __double_as_longlong(g.q2min), kqmax = __double_as_longlong(g.q2max);
+  // whole warps iterate together (blockDim is a multiple of 32) for the match
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += (long long)gridDim.x * blockDim.x) {
+    const long long p = base + threadIdx.x;
+    unsigned key = 0xFFFFFFFFu;
+    if (p < n) {
+      const long long kx = __double_as_longlong(xa[p]), kq = __double_as_longlong(qa[p]);
+      const bool valid = kq > 0 && kq < 0x7FF0000000000000LL && kx > 0 && kx <= kxlast;
+      const bool fx = kx < kx0, fq = kq < kqmin || kq > kqmax;
+      if (!valid) {
+        key = 3u;
+      } else if (fx || fq) {
+        key = fx ? (fq ? 2u : 0u) : 1u;
+      } else {
+        const int i = search_cell(xkeys, g.nx, g.xstep, kx);
+        const int j = search_cell(qkeys, g.nrows, g.qstep, kq);
+        key = min(kSortBins0 + (unsigned)max(g.row_qc[j], 0) * (unsigned)g.nx + (unsigned)i, nb - 1u);
+      }
+      keys[p] = key;
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    if (key != 0xFFFFFFFFu && lane == __ffs(peers) - 1) atomicAdd(cnt + key, (unsigned)__popc(peers));
+  }
+}
+
+// Exclusive prefix sum of cnt[0, nb) in place (one block of 1024 threads).
+__global__ void __launch_bounds__(1024) k_adj_scan(unsigned *cnt, int nb) {
+  __shared__ unsigned part[1024];
+  const int per = (nb + 1023) / 1024;
+  const int a = min((int)threadIdx.x * per, nb), b = min(a + per, nb);
+  unsigned sum = 0;
+  for (int i = a; i < b; i++) sum += cnt[i];
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  for (int d = 1; d < 1024; d <<= 1) {
+    const unsigned v = threadIdx.x >= (unsigned)d ? part[threadIdx.x - d] : 0u;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  unsigned run = threadIdx.x ? part[threadIdx.x - 1] : 0u;
+  for (int i = a; i < b; i++) {
+    const unsigned c = cnt[i];
+    cnt[i] = run;
+    run += c;
+  }
+}
+
+// perm[cursor[key]++] = p, one atomic per key per warp.
+__global__ void __launch_bounds__(256) k_adj_place(const unsigned *__restrict__ keys, long long n,
+                                                   unsigned *__restrict__ cursor, unsigned *__restrict__ perm) {
+  const int lane = threadIdx.x & 31;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += (long long)gridDim.x * blockDim.x) {
+    const long long p = base + threadIdx.x;
+    const unsigned key = p < n ? keys[p] : 0xFFFFFFFFu;
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const int leader = __ffs(peers) - 1;
+    unsigned at = 0;
+    if (key != 0xFFFFFFFFu && lane == leader) at = atomicAdd(cursor + key, (unsigned)__popc(peers));
+    at = __shfl_sync(0xffffffffu, at, leader);
+    if (key != 0xFFFFFFFFu) perm[at + __popc(peers & ((1u << lane) - 1u))] = (unsigned)p;
+  }
+}
+
+// One warp per 32 sorted points, tiles handed out in sorted order by a
+// counter (the costly continuation tiles first, the cheap in-grid ones fill
+// in at the end).  With GV, each run of lanes sharing a cell contracts its
+// staged terms: lane l owns knot m = l mod 16 of the cell and flavours
+// l / 16, l / 16 + 2, ... (at most 16 flavours).
+template <bool GV>
+__global__ void __launch_bounds__(kAdjThreads, 1)
+k_vjp_sorted(GridView g, const double *__restrict__ xa, const double *__restrict__ qa,
+             const double *__restrict__ cot, long long n, const unsigned *__restrict__ perm,
+             unsigned long long *__restrict__ next_tile, double *__restrict__ gx, double *__restrict__ gq,
+             double *__restrict__ gv) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  long long *xkeys = reinterpret_cast<long long *>(smem);
+  long long *qkeys = reinterpret_cast<long long *>(smem + keys_bytes(g.nx, 8));
+  size_t off = keys_bytes(g.nx, 8) + keys_bytes(g.nrows, 8);
+  double2 *LTt = reinterpret_cast<double2 *>(smem + off);
+  off += sizeof(double2) * kLogTab;
+  double *LTh = reinterpret_cast<double *>(smem + off);
+  off += sizeof(double) * kLogTab;
+  double *ET = reinterpret_cast<double *>(smem + off);
+  off += sizeof(double) * kExpTab;
+  float2 *stw = reinterpret_cast<float2 *>(smem + off);  // [warp][lane][kStPad] weights
+  float2 *stc = stw + kAdjThreads * kStPad;               // [warp][lane][kStPad] cotangents
+  load_keys<double>(g, xkeys, 0);
+  load_keys<double>(g, qkeys, 1);
+  for (int i = threadIdx.x; i < kLogTab; i += kAdjThreads) { LTt[i] = g.tlogtab[i]; LTh[i] = g.tloghtab[i]; }
+  for (int i = threadIdx.x; i < kExpTab; i += kAdjThreads) ET[i] = g.texptab[i];
+  const LogTabs LT{LTt, LTh};
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float2 *wrow = stw + (size_t)threadIdx.x * kStPad, *crow = stc + (size_t)threadIdx.x * kStPad;
+  const float2 *wwarp = stw + (size_t)warp * 32 * kStPad, *cwarp = stc + (size_t)warp * 32 * kStPad;
+  const long long ntiles = (n + 31) / 32;
+  while (true) {
+    unsigned long long t = 0;
+    if (lane == 0) t = atomicAdd(next_tile, 1ull);
+    const long long tile = (long long)__shfl_sync(0xffffffffu, t, 0);
+    if (tile >= ntiles) break;
+    const long long pos = tile * 32 + lane;
+    Staged st{wrow, crow, -1, 0, 0, false};
+    if (pos < n) vjp_point<GV>(g, xkeys, qkeys, LT, ET, (long long)perm[pos], xa, qa, cot, gx, gq, gv, &st);
+    if (GV) {
+      __syncwarp();
+      const int m = lane & 15, fh = lane >> 4;
+      unsigned todo = __ballot_sync(0xffffffffu, st.ing);
+      while (todo) {  // one run of lanes sharing a cell at a time
+        const int leader = __ffs(todo) - 1;
+        const int cell = __shfl_sync(0xffffffffu, st.cell, leader);
+        const int xk0 = __shfl_sync(0xffffffffu, st.xk0, leader);
+        const int qk0 = __shfl_sync(0xffffffffu, st.qk0, leader);
+        const unsigned run = __ballot_sync(0xffffffffu, st.ing && st.cell == cell);
+        todo &= ~run;
+        float ah[8], al[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++) ah[j] = al[j] = 0.f;
+        for (unsigned r = run; r; r &= r - 1) {
+          const int q = __ffs(r) - 1;
+          const float2 w = wwarp[q * kStPad + m];
+          const ff2 wf{w.x, w.y};
+#pragma unroll
+          for (int j = 0; j < 8; j++) {
+            const int f = fh + 2 * j;
+            if (f < g.nf) {
+              const float2 c = cwarp[q * kStPad + f];
+              ff_acc(ah[j], al[j], wf, c.x, c.y);
+            }
+          }
+        }
+        const int row = qk0 + (m >> 2), col = xk0 + (m & 3);
+        if (row >= 0 && row < g.nrows && col >= 0 && col < g.nx) {
+          double *dst = gv + ((size_t)row * g.nx + col) * g.nf;
+#pragma unroll
+          for (int j = 0; j < 8; j++) {
+            const int f = fh + 2 * j;
+            if (f < g.nf) atomicAdd(dst + f, f2d(ah[j]) + f2d(al[j]));
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// Scratch of the sorted path, from a pool of the device's own (stream-ordered,
+// kept between calls up to 256 MB so a call does not map memory afresh).
+static cudaMemPool_t sort_pool(int dev) {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  if (dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    if (cudaMemPoolCreate(&p, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    unsigned long long keep = 256ull << 20;
+    cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    pools[dev] = p;
+  }
+  return pools[dev];
 }
 
 }  // namespace pdfgb
@@ -376,13 +616,54 @@ extern "C" int xfxq2_all_flavours_vjp(const pdf_grid *grid, const double *x, con
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  size_t smem = keys_bytes(g.nx, 8) + keys_bytes(g.nrows, 8) + (sizeof(double2) + sizeof(double)) * kLogTab +
-                sizeof(double) * kExpTab;
+  if (sms < 1) sms = 1;
+  const size_t kbytes = keys_bytes(g.nx, 8) + keys_bytes(g.nrows, 8);
+  const size_t smem = kbytes + (sizeof(double2) + sizeof(double)) * kLogTab + sizeof(double) * kExpTab;
+  const long long nb = kSortBins0 + (long long)(g.nqc + 1) * g.nx;
+
+  // large batches on a float-float-safe grid: sorted by cell (see k_vjp_sorted)
+  if ((long long)n >= kSortMinN && n < (1ull << 31) && g.ff && g.nf <= 16 && nb <= kSortMaxBins) {
+    static LaunchCache cache_t, cache_f;
+    const size_t ssmem = smem + 2 * sizeof(float2) * kAdjThreads * kStPad;
+    LaunchCache &cache = grad_values ? cache_t : cache_f;
+    const int per_sm = grad_values ? cache.blocks_per_sm(k_vjp_sorted<true>, kAdjThreads, ssmem)
+                                   : cache.blocks_per_sm(k_vjp_sorted<false>, kAdjThreads, ssmem);
+    cudaMemPool_t pool = sort_pool(dev);
+    void *buf = nullptr;
+    const size_t cnt_bytes = ((size_t)nb * sizeof(unsigned) + 15) / 16 * 16;
+    const size_t bytes = cnt_bytes + 16 + 2 * ((n * sizeof(unsigned) + 15) / 16 * 16);
+    if (per_sm >= 1 && pool && cudaMallocFromPoolAsync(&buf, bytes, pool, stream) == cudaSuccess) {
+      unsigned *cnt = static_cast<unsigned *>(buf);
+      auto *next_tile = reinterpret_cast<unsigned long long *>(static_cast<char *>(buf) + cnt_bytes);
+      unsigned *keys = reinterpret_cast<unsigned *>(static_cast<char *>(buf) + cnt_bytes + 16);
+      unsigned *perm = keys + (n * sizeof(unsigned) + 15) / 16 * 4;
+      int rc = PDF_OK;
+      if (cudaMemsetAsync(buf, 0, cnt_bytes + 16, stream) != cudaSuccess)
+        rc = set_error(PDF_ERR_CUDA, "xfxq2_all_flavours_vjp: scratch");
+      const unsigned sblocks = (unsigned)std::min<long long>(((long long)n + 255) / 256, 8LL * sms);
+      if (!rc) {
+        k_adj_key<<<sblocks, 256, kbytes, stream>>>(g, x, q2, (long long)n, (unsigned)nb, keys, cnt);
+        k_adj_scan<<<1, 1024, 0, stream>>>(cnt, (int)nb);
+        k_adj_place<<<sblocks, 256, 0, stream>>>(keys, (long long)n, cnt, perm);
+        const unsigned blocks = (unsigned)std::min<long long>(((long long)n + kAdjThreads - 1) / kAdjThreads, sms);
+        if (grad_values)
+          k_vjp_sorted<true><<<blocks, kAdjThreads, ssmem, stream>>>(g, x, q2, cot, (long long)n, perm, next_tile,
+                                                                     grad_x, grad_q2, grad_values);
+        else
+          k_vjp_sorted<false><<<blocks, kAdjThreads, ssmem, stream>>>(g, x, q2, cot, (long long)n, perm, next_tile,
+                                                                      grad_x, grad_q2, grad_values);
+        rc = check_launch("xfxq2_all_flavours_vjp sorted kernels");
+      }
+      cudaFreeAsync(buf, stream);
+      return rc;
+    }
+    cudaGetLastError();  // no scratch: the unsorted kernel below needs none
+  }
+
   // one resident block per SM (its registers fill the SM), each warp taking many
   // tiles so that its continuation queues fill to whole warps
   long long blocks = ((long long)n + kAdjThreads - 1) / kAdjThreads;
-  long long cap = (long long)(sms > 0 ? sms : 1);
-  if (blocks > cap) blocks = cap;
+  if (blocks > sms) blocks = sms;
   k_vjp<<<(unsigned)blocks, kAdjThreads, smem, stream>>>(g, x, q2, cot, (long long)n, grad_x, grad_q2,
                                                          grad_values);
   return check_launch("xfxq2_all_flavours_vjp kernel");

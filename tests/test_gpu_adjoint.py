@@ -127,20 +127,21 @@ def test_autograd_function_and_value_restaging(full, synth):
 
 
 def test_full_size_batch_in_the_benchmark_configuration(full, synth):
-    """The benchmark's adjoint step (1e6 points, its seeds, one launch): every
-    warp takes many tiles, so the continuation queues fill and drain whole
-    warps of one kind.  Per-point gradients are functions of the point alone,
+    """The benchmark's adjoint step (1e6 points, its seeds, one launch of the
+    sorted path): continuation warps are of one kind and in-grid warps hold
+    runs of one cell.  Per-point gradients are functions of the point alone,
     so a sample of them must match, bit for bit, the same points run as a
-    small batch (mixed remainders), and the oracle on a subsample; the knot
-    gradient must equal the sum of four quarter batches up to the order of
-    the FP64 additions."""
+    smaller sorted batch (other neighbours, other runs), and the oracle on a
+    subsample; the knot gradient must equal the sum of four quarter batches
+    up to the rounding of the run contractions and the order of the FP64
+    additions."""
     g, G, og = full
     n = 1_000_000
     x, q2, cot = synth.adjoint_inputs(n, g.nflav, 5, 6)
     gx, gq, gv = run_vjp(G, x, q2, cot)
     rng = np.random.default_rng(77)
     sub = np.sort(rng.choice(n, 20_000, replace=False))
-    sx, sq, _ = run_vjp(G, x[sub], q2[sub], cot[sub], with_values=False)
+    sx, sq, _ = run_vjp(G, x[sub], q2[sub], cot[sub])
     assert np.array_equal(gx[sub], sx, equal_nan=True) and np.array_equal(gq[sub], sq, equal_nan=True)
     few = sub[:1500]
     dx = og.dxfxq2(x[few], q2[few], "x")
@@ -155,3 +156,59 @@ def test_full_size_batch_in_the_benchmark_configuration(full, synth):
     parts = sum(run_vjp(G, x[k::4], q2[k::4], cot[k::4])[2] for k in range(4))
     scale = np.abs(gv).max(axis=(0, 1))  # per flavour
     assert (np.abs(gv - parts) / scale).max() < 1e-11
+
+
+def test_sorted_batch_matches_oracle_and_small_batches(full, synth):
+    """Batches of 16384 points or more are sorted by cell, and the knot-value
+    terms of each warp's run of same-cell points are contracted in
+    float-float before one atomic per knot and flavour; smaller batches
+    scatter point by point.  Both are checked against the oracle's knot
+    gradient, on a batch that also holds points on knots, on the last x knot,
+    on the top and boundary Q^2 knots, in runs of one cell longer than a
+    warp, and invalid and continuation points."""
+    g, G, og = full
+    n = 24000
+    x, q2, cot = synth.adjoint_inputs(n, g.nflav, 25, 26)
+    rng = np.random.default_rng(27)
+    k = 0
+    for xi in (g.x_knots[0], g.x_knots[57], g.x_knots[-2], g.x_knots[-1]):
+        for qj in (g.q2_knots[0], g.q2_knots[11], g.q2_knots[12], g.q2_knots[30], g.q2_knots[-1]):
+            x[k], q2[k] = xi, qj
+            k += 1
+    # 100 points in one cell: runs cross tile boundaries
+    c0, c1 = np.log(g.x_knots[100]), np.log(g.x_knots[101])
+    d0, d1 = np.log(g.q2_knots[20]), np.log(g.q2_knots[21])
+    x[k:k + 100] = np.exp(rng.uniform(c0, c1, 100))
+    q2[k:k + 100] = np.exp(rng.uniform(d0, d1, 100))
+    k += 100
+    x[k:k + 3], q2[k:k + 3] = [0.0, 0.5, 2.0], [10.0, -1.0, 10.0]  # invalid
+    perm = rng.permutation(n)
+    x, q2, cot = x[perm], q2[perm], cot[perm]
+    gx, gq, gv = run_vjp(G, x, q2, cot)  # sorted
+    parts = [run_vjp(G, x[a:a + 6000], q2[a:a + 6000], cot[a:a + 6000]) for a in range(0, n, 6000)]
+    cx = np.concatenate([p[0] for p in parts])
+    cq = np.concatenate([p[1] for p in parts])
+    cv = sum(p[2] for p in parts)
+    valid = np.isfinite(cx)
+    assert (~valid).sum() == 3
+    assert np.array_equal(np.isfinite(gx), valid) and np.array_equal(np.isfinite(gq), valid)
+    # per point: the oracle's forward-mode gradients, for the sorted batch,
+    # the small batches and the sorted batch without the knot gradient
+    gx2, gq2, _ = run_vjp(G, x, q2, cot, with_values=False)
+    assert np.array_equal(np.isfinite(gx2), valid)
+    xv, qv, cv_ = x[valid], q2[valid], cot[valid]
+    dx, dq = og.dxfxq2(xv, qv, "x"), og.dxfxq2(xv, qv, "q2")
+    _, s, _ = og.xfxq2(xv, qv)
+    sx = np.abs(cv_ * dx).sum(axis=1) + (np.abs(cv_) * s).sum(axis=1) / (xv * min_log_spacing(g.x_knots))
+    sq = np.abs(cv_ * dq).sum(axis=1) + (np.abs(cv_) * s).sum(axis=1) / (qv * min_log_spacing(g.q2_knots))
+    # (at x = 1 every value is 0, so there sq = 0 and the error must vanish)
+    for ax, aq in ((gx, gq), (cx, cq), (gx2, gq2)):
+        assert (np.abs(ax[valid] - (cv_ * dx).sum(axis=1)) <= 1e-10 * sx + 1e-280).all()
+        assert (np.abs(aq[valid] - (cv_ * dq).sum(axis=1)) <= 1e-10 * sq + 1e-280).all()
+        assert (np.abs(ax[valid] - gx[valid]) <= 1e-13 * sx + 1e-280).all()
+        assert (np.abs(aq[valid] - gq[valid]) <= 1e-13 * sq + 1e-280).all()
+    go, gabs = og.knot_grad(x[valid], q2[valid], cot[valid], with_abs=True)
+    for got in (gv, cv):
+        err = np.abs(got - go)
+        assert (err <= 1e-10 * gabs + 1e-300).all(), (err / np.maximum(gabs, 1e-300)).max()
+    assert (np.abs(gv - cv) <= 1e-12 * gabs + 1e-300).all()
