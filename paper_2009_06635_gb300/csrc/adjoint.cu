@@ -9,8 +9,10 @@
 // c * dxf/dF * w_a(t) w_b(u) into the knot-value gradient with FP64 atomics,
 // w_a the tangent-augmented Hermite weight of knot a (the patch is linear in
 // the knot values: dF/df_ab = w_a(t) w_b(u)).  The x and Q^2 derivatives are
-// summed over flavours in registers, in a fixed order.  Points that need a
-// continuation rule are queued per warp by kind (kernel comment below).
+// summed over flavours in registers, in a fixed order.  Small batches run
+// k_vjp (continuation points queued per warp by kind); batches of 16384
+// points or more are first sorted by cell and run k_vjp_sorted, which
+// contracts the knot-value terms of same-cell runs before its atomics.
 //
 // A query exactly on the last x (or top Q^2) knot is taken in the last
 // proper cell at t = 1 (u = 1), so the derivative there is the one-sided one
@@ -31,6 +33,14 @@ struct Site64 {
   int c, k0;           // cell index (x: cell, q: Q cell) and first knot (col / row) of the stencil
   double dpos;         // d(position)/d(coordinate), 0 for a fixed site
 };
+
+// 0, or 2^-lim <= |v| < 2^lim: products of such weights and cotangents stay
+// far inside the float exponent range, error terms included.
+__device__ __forceinline__ bool ff_safe(double v, int lim) {
+  const long long b = __double_as_longlong(v);
+  const int e = (int)((b >> 52) & 0x7FF) - 1023;
+  return (b << 1) == 0 || (e >= -lim && e < lim);
+}
 
 __device__ __forceinline__ void bern_d(double t, double s, double *B, double *dB) {
   double t2 = t * t, s2 = s * s;
@@ -115,6 +125,26 @@ struct Staged {
   bool ing;
 };
 
+// FP64 knot scatter of one in-grid point, out of line: the staged path
+// takes it only for a point whose weights or cotangents are too small or
+// large for float-float (rare), and keeps its registers off the hot path.
+__device__ __noinline__ void scatter_point_f64(int nrows, int nx, int nf, double wq0, double wq1, double wq2,
+                                               double wq3, double wx0, double wx1, double wx2, double wx3,
+                                               int qk0, int xk0, const double *__restrict__ cp,
+                                               double *__restrict__ gv) {
+  const double wq[4] = {wq0, wq1, wq2, wq3}, wx[4] = {wx0, wx1, wx2, wx3};
+  for (int f = 0; f < nf; f++) {
+    const double c = cp[f];
+    if ((__double_as_longlong(c) << 1) == 0) continue;
+    for (int m = 0; m < 16; m++) {
+      const int row = qk0 + (m >> 2), col = xk0 + (m & 3);
+      const double w = wq[m >> 2] * wx[m & 3];
+      if (row >= 0 && row < nrows && col >= 0 && col < nx && (__double_as_longlong(w) << 1) != 0)
+        atomicAdd(gv + ((size_t)row * nx + col) * nf + f, c * w);
+    }
+  }
+}
+
 // ---- in-grid points on a float-float-safe grid ------------------------------
 // An in-grid point: F_t dt/dx = sum_lk B_l(u) B'_k(t) dt/dx c_lk and F_u du/dQ^2
 // (likewise) for every flavour in float-float on the FMA pipe from the
@@ -142,6 +172,16 @@ __device__ __forceinline__ void vjp_ingrid_ff(const GridView &g, const Site64 &X
       wu[m] = ff_mul(qd[m >> 2], xb[m & 3]);
     }
   }
+  // staged only when every weight and cotangent is 0 or of moderate size, so
+  // that each knot's float-float sum keeps its precision relative to that
+  // knot's own terms; otherwise this point scatters in FP64
+  // (the cotangents are checked as the flavour loop reads them)
+  bool stage = false;
+  if (STAGE && gv) {
+    stage = true;
+#pragma unroll
+    for (int k = 0; k < 4; k++) stage = stage && ff_safe(Q.w[k], 25) && ff_safe(X.w[k], 25);
+  }
   double W[16];  // knot weights w_b(u) w_a(t), 0 where the knot is outside the grid
   if (!STAGE) {
 #pragma unroll
@@ -149,7 +189,7 @@ __device__ __forceinline__ void vjp_ingrid_ff(const GridView &g, const Site64 &X
       const int row = Q.k0 + (m >> 2), col = X.k0 + (m & 3);
       W[m] = (row >= 0 && row < g.nrows && col >= 0 && col < g.nx) ? Q.w[m >> 2] * X.w[m & 3] : 0.0;
     }
-  } else if (gv) {
+  } else if (stage) {
     ff2 wq[4], wx[4];
 #pragma unroll
     for (int k = 0; k < 4; k++) {
@@ -183,7 +223,8 @@ __device__ __forceinline__ void vjp_ingrid_ff(const GridView &g, const Site64 &X
     sx = fma(c, f2d(th) + f2d(tl), sx);
     sq = fma(c, f2d(uh) + f2d(ul), sq);
     if (STAGE) {
-      if (gv) {
+      if (stage) {
+        stage = ff_safe(c, 50);
         const ff2 cf = ff_of(c);
         st->c[f] = make_float2(cf.h, cf.l);
       }
@@ -193,6 +234,11 @@ __device__ __forceinline__ void vjp_ingrid_ff(const GridView &g, const Site64 &X
         if ((__double_as_longlong(W[m]) << 1) != 0)
           atomicAdd(gv + (k0 + ((long long)(m >> 2) * g.nx + (m & 3)) * g.nf + f), c * W[m]);
     }
+  }
+  if (STAGE && gv && !stage) {  // not staged after all: FP64 scatter instead
+    st->ing = false;
+    scatter_point_f64(g.nrows, g.nx, g.nf, Q.w[0], Q.w[1], Q.w[2], Q.w[3], X.w[0], X.w[1], X.w[2], X.w[3], Q.k0,
+                      X.k0, cot + p * g.nf, gv);
   }
   if (gx) gx[p] = sx;
   if (gq) gq[p] = sq;

@@ -212,3 +212,27 @@ def test_sorted_batch_matches_oracle_and_small_batches(full, synth):
         err = np.abs(got - go)
         assert (err <= 1e-10 * gabs + 1e-300).all(), (err / np.maximum(gabs, 1e-300)).max()
     assert (np.abs(gv - cv) <= 1e-12 * gabs + 1e-300).all()
+
+
+def test_sorted_batch_keeps_each_knots_precision(full, synth):
+    """Float-float run sums are used only for weights and cotangents of
+    moderate size; a point with a weight or cotangent far from 1 (here whole
+    flavours scaled by 1e-30 and 1e30, and points within 1e-12 of a knot,
+    whose far weights are ~1e-24) scatters in FP64, so every knot's gradient
+    keeps its precision relative to its own terms."""
+    g, G, og = full
+    n = 20000
+    x, q2, cot = synth.adjoint_inputs(n, g.nflav, 35, 36)
+    cot[:, 0] *= 1e-30
+    cot[:, 1] *= 1e30
+    rng = np.random.default_rng(37)
+    near = rng.choice(n, 64, replace=False)
+    ks = rng.integers(1, len(g.x_knots) - 2, 64)
+    x[near] = g.x_knots[ks] * (1 + 1e-12 * rng.uniform(0.5, 2.0, 64))
+    q2[near] = np.exp(rng.uniform(np.log(g.q2_knots[0]), np.log(g.q2_knots[-1]), 64))
+    gx, gq, gv = run_vjp(G, x, q2, cot)
+    valid = np.isfinite(gx)
+    go, gabs = og.knot_grad(x[valid], q2[valid], cot[valid], with_abs=True)
+    err = np.abs(gv - go)
+    assert (err <= 1e-10 * gabs + 1e-300).all(), (err / np.maximum(gabs, 1e-300)).max()
+    assert np.abs(gv[..., 0]).max() < 1e-20 < np.abs(gv[..., 1]).max() * 1e-40
