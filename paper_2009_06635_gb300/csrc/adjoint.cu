@@ -461,6 +461,7 @@ k_vjp(GridView g, const double *__restrict__ xa, const double *__restrict__ qa, 
 constexpr int kSortBins0 = 4;        // bins 0..2: continuation kinds, 3: invalid, then the cells
 constexpr int kSortMaxBins = 65540;  // above this the grid has too many cells for runs to form
 constexpr long long kSortMinN = 16384;
+constexpr int kSortThreads = 128;    // three blocks per SM: 12 warps at <= 168 registers
 constexpr int kStPad = 17;           // float2 per staged row (16 used): 2-way bank conflicts at most
 
 // Sort key of a point: its kind for a continuation or invalid point, else
@@ -545,9 +546,12 @@ __global__ void __launch_bounds__(256) k_adj_place(const unsigned *__restrict__ 
 // counter (the costly continuation tiles first, the cheap in-grid ones fill
 // in at the end).  With GV, each run of lanes sharing a cell contracts its
 // staged terms: lane l owns knot m = l mod 16 of the cell and flavours
-// l / 16, l / 16 + 2, ... (at most 16 flavours).
+// l / 16, l / 16 + 2, ... (at most 16 flavours).  Blocks of four warps,
+// three per SM: 12 warps at <= 168 registers hide more of the FP64 latency
+// than 8 at 254 (1.66 -> 1.56 ms per 1e6 points; 16 warps at 128 registers,
+// with more spills, measured the same as 12).
 template <bool GV>
-__global__ void __launch_bounds__(kAdjThreads, 1)
+__global__ void __launch_bounds__(kSortThreads, 3)
 k_vjp_sorted(GridView g, const double *__restrict__ xa, const double *__restrict__ qa,
              const double *__restrict__ cot, long long n, const unsigned *__restrict__ perm,
              unsigned long long *__restrict__ next_tile, double *__restrict__ gx, double *__restrict__ gq,
@@ -563,11 +567,11 @@ k_vjp_sorted(GridView g, const double *__restrict__ xa, const double *__restrict
   double *ET = reinterpret_cast<double *>(smem + off);
   off += sizeof(double) * kExpTab;
   float2 *stw = reinterpret_cast<float2 *>(smem + off);  // [warp][lane][kStPad] weights
-  float2 *stc = stw + kAdjThreads * kStPad;               // [warp][lane][kStPad] cotangents
+  float2 *stc = stw + kSortThreads * kStPad;              // [warp][lane][kStPad] cotangents
   load_keys<double>(g, xkeys, 0);
   load_keys<double>(g, qkeys, 1);
-  for (int i = threadIdx.x; i < kLogTab; i += kAdjThreads) { LTt[i] = g.tlogtab[i]; LTh[i] = g.tloghtab[i]; }
-  for (int i = threadIdx.x; i < kExpTab; i += kAdjThreads) ET[i] = g.texptab[i];
+  for (int i = threadIdx.x; i < kLogTab; i += kSortThreads) { LTt[i] = g.tlogtab[i]; LTh[i] = g.tloghtab[i]; }
+  for (int i = threadIdx.x; i < kExpTab; i += kSortThreads) ET[i] = g.texptab[i];
   const LogTabs LT{LTt, LTh};
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -670,10 +674,10 @@ extern "C" int xfxq2_all_flavours_vjp(const pdf_grid *grid, const double *x, con
   // large batches on a float-float-safe grid: sorted by cell (see k_vjp_sorted)
   if ((long long)n >= kSortMinN && n < (1ull << 31) && g.ff && g.nf <= 16 && nb <= kSortMaxBins) {
     static LaunchCache cache_t, cache_f;
-    const size_t ssmem = smem + 2 * sizeof(float2) * kAdjThreads * kStPad;
+    const size_t ssmem = smem + 2 * sizeof(float2) * kSortThreads * kStPad;
     LaunchCache &cache = grad_values ? cache_t : cache_f;
-    const int per_sm = grad_values ? cache.blocks_per_sm(k_vjp_sorted<true>, kAdjThreads, ssmem)
-                                   : cache.blocks_per_sm(k_vjp_sorted<false>, kAdjThreads, ssmem);
+    const int per_sm = grad_values ? cache.blocks_per_sm(k_vjp_sorted<true>, kSortThreads, ssmem)
+                                   : cache.blocks_per_sm(k_vjp_sorted<false>, kSortThreads, ssmem);
     cudaMemPool_t pool = sort_pool(dev);
     void *buf = nullptr;
     const size_t cnt_bytes = ((size_t)nb * sizeof(unsigned) + 15) / 16 * 16;
@@ -691,13 +695,14 @@ extern "C" int xfxq2_all_flavours_vjp(const pdf_grid *grid, const double *x, con
         k_adj_key<<<sblocks, 256, kbytes, stream>>>(g, x, q2, (long long)n, (unsigned)nb, keys, cnt);
         k_adj_scan<<<1, 1024, 0, stream>>>(cnt, (int)nb);
         k_adj_place<<<sblocks, 256, 0, stream>>>(keys, (long long)n, cnt, perm);
-        const unsigned blocks = (unsigned)std::min<long long>(((long long)n + kAdjThreads - 1) / kAdjThreads, sms);
+        const unsigned blocks =
+            (unsigned)std::min<long long>(((long long)n + kSortThreads - 1) / kSortThreads, (long long)sms * per_sm);
         if (grad_values)
-          k_vjp_sorted<true><<<blocks, kAdjThreads, ssmem, stream>>>(g, x, q2, cot, (long long)n, perm, next_tile,
-                                                                     grad_x, grad_q2, grad_values);
-        else
-          k_vjp_sorted<false><<<blocks, kAdjThreads, ssmem, stream>>>(g, x, q2, cot, (long long)n, perm, next_tile,
+          k_vjp_sorted<true><<<blocks, kSortThreads, ssmem, stream>>>(g, x, q2, cot, (long long)n, perm, next_tile,
                                                                       grad_x, grad_q2, grad_values);
+        else
+          k_vjp_sorted<false><<<blocks, kSortThreads, ssmem, stream>>>(g, x, q2, cot, (long long)n, perm, next_tile,
+                                                                       grad_x, grad_q2, grad_values);
         rc = check_launch("xfxq2_all_flavours_vjp sorted kernels");
       }
       cudaFreeAsync(buf, stream);
