@@ -281,7 +281,14 @@ PDF_API int xfxq2_all_flavours_host_noalloc(const pdf_grid *grid, const double *
  * cot is [n][nflav] FP64.  All pointers are device memory; enqueued on
  * `stream`.  Invalid points get NaN gradients and add nothing to
  * grad_values.  A point exactly on the last x (top Q^2) knot gets the
- * one-sided derivative of the last cell. */
+ * one-sided derivative of the last cell.
+ * Batches of 16384 points or more (grids with at most 16 flavours and
+ * ~65K cells) are sorted by cell on the device first: the call then takes
+ * 8 B per point (plus 4 B per cell) of stream-ordered scratch from a memory
+ * pool the library keeps per device, and releases it on `stream`; if that
+ * memory is not available it runs the unsorted kernel instead.  Both
+ * paths agree to rounding (the sorted one sums in-grid knot terms per cell
+ * in float-float, to ~2^-46 of each knot's own terms). */
 PDF_API int xfxq2_all_flavours_vjp(const pdf_grid *grid, const double *x, const double *q2, size_t n,
                                    const double *cot, double *grad_x, double *grad_q2, double *grad_values,
                                    cudaStream_t stream);
