@@ -145,6 +145,32 @@ __device__ __noinline__ void scatter_point_f64(int nrows, int nx, int nf, double
   }
 }
 
+// Bernstein weights and their t-derivatives in float-float from the site's
+// position t and its complement s (computed apart, so whichever is small
+// keeps its precision): four conversions on the FP64 pipe, the rest on the
+// FMA pipe.  dB/dt = (-3 s^2, 3 s^2 - 6 t s, 6 t s - 3 t^2, 3 t^2).
+__device__ __forceinline__ ff2 ff_sub(ff2 a, ff2 b) {
+  const float s = __fsub_rn(a.h, b.h);
+  const float bb = __fsub_rn(s, a.h);
+  const float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(-b.h, bb));
+  const float l = __fadd_rn(e, __fsub_rn(a.l, b.l));
+  const float h = __fadd_rn(s, l);
+  return {h, __fsub_rn(l, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ void ff_bern_d(double t, double s, ff2 dpos, ff2 *B, ff2 *dB) {
+  const ff2 tf = ff_of(t), sf = ff_of(s), three = {3.f, 0.f}, six = {6.f, 0.f};
+  const ff2 t2 = ff_mul(tf, tf), s2 = ff_mul(sf, sf), ts = ff_mul(tf, sf);
+  B[0] = ff_mul(s2, sf);
+  B[1] = ff_mul(three, ff_mul(tf, s2));
+  B[2] = ff_mul(three, ff_mul(t2, sf));
+  B[3] = ff_mul(t2, tf);
+  const ff2 s23 = ff_mul(three, s2), t23 = ff_mul(three, t2), ts6 = ff_mul(six, ts);
+  dB[0] = ff_mul(ff2{-s23.h, -s23.l}, dpos);
+  dB[1] = ff_mul(ff_sub(s23, ts6), dpos);
+  dB[2] = ff_mul(ff_sub(ts6, t23), dpos);
+  dB[3] = ff_mul(t23, dpos);
+}
+
 // ---- in-grid points on a float-float-safe grid ------------------------------
 // An in-grid point: F_t dt/dx = sum_lk B_l(u) B'_k(t) dt/dx c_lk and F_u du/dQ^2
 // (likewise) for every flavour in float-float on the FMA pipe from the
@@ -153,19 +179,15 @@ __device__ __noinline__ void scatter_point_f64(int nrows, int nx, int nf, double
 // with weights w_a(t) w_b(u)): FP64 products and atomics per point, or
 // (STAGE) the weights and cotangents staged for the warp's contraction.
 template <bool STAGE>
-__device__ __forceinline__ void vjp_ingrid_ff(const GridView &g, const Site64 &X, const Site64 &Q, long long p,
+__device__ __forceinline__ void vjp_ingrid_ff(const GridView &g, const Site64 &X, const Site64 &Q, double t,
+                                              double ts, double u, double us, long long p,
                                               const double *__restrict__ cot, double *__restrict__ gx,
                                               double *__restrict__ gq, double *__restrict__ gv, Staged *st) {
   ff2 wt[16], wu[16];
   {
     ff2 xb[4], xd[4], qb[4], qd[4];
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-      xb[k] = ff_of(X.B[k]);
-      xd[k] = ff_of(X.dB[k] * X.dpos);
-      qb[k] = ff_of(Q.B[k]);
-      qd[k] = ff_of(Q.dB[k] * Q.dpos);
-    }
+    ff_bern_d(t, ts, ff_of(X.dpos), xb, xd);
+    ff_bern_d(u, us, ff_of(Q.dpos), qb, qd);
 #pragma unroll
     for (int m = 0; m < 16; m++) {
       wt[m] = ff_mul(qb[m >> 2], xd[m & 3]);
@@ -284,7 +306,7 @@ __device__ __forceinline__ void vjp_point(const GridView &g, const long long *xk
       make_site(Q[b], g.qW + 16 * qc, u, s, qc, row - 1, dpos);
     }
     if (cls == C_IN && g.ff) {
-      vjp_ingrid_ff<STAGE>(g, X[0], Q[0], p, cot, gx, gq, gv, st);
+      vjp_ingrid_ff<STAGE>(g, X[0], Q[0], ps.t0, ps.ts0, ps.u0, ps.us0, p, cot, gx, gq, gv, st);
       return;
     }
     const int nsx = lowx ? 2 : 1;
