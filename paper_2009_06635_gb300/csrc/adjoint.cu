@@ -75,6 +75,34 @@ __device__ __forceinline__ void patch_d(const double *b, const Site64 &X, const 
   }
 }
 
+// The same for a site whose Bernstein weights in x (xk) or in u (qk) are
+// (1, 0, 0, 0) -- a site on a knot, as the continuation rules' fixed sites
+// are: only the first control point of each row, or the first row, enters,
+// and the sums are exactly those of patch_d.  F_u only where the Q site
+// moves with Q^2 (need_u); a fixed site's F_u would be multiplied by 0.
+__device__ __forceinline__ void patch_site(const double *b, const Site64 &X, const Site64 &Q, bool xk, bool qk,
+                                           bool need_t, bool need_u, double &F, double &Ft, double &Fu) {
+  if (xk && !need_t) {
+    F = Ft = Fu = 0.0;
+#pragma unroll
+    for (int l = 0; l < 4; l++) {
+      const double v = __ldg(b + 4 * l);
+      F = fma(Q.B[l], v, F);
+      if (need_u) Fu = fma(Q.dB[l], v, Fu);
+    }
+    return;
+  }
+  if (qk && !need_u) {
+    const double2 *q = reinterpret_cast<const double2 *>(b);
+    const double2 v0 = __ldg(q), v1 = __ldg(q + 1);
+    F = X.B[0] * v0.x + X.B[1] * v0.y + X.B[2] * v1.x + X.B[3] * v1.y;
+    Ft = need_t ? X.dB[0] * v0.x + X.dB[1] * v0.y + X.dB[2] * v1.x + X.dB[3] * v1.y : 0.0;
+    Fu = 0.0;
+    return;
+  }
+  patch_d(b, X, Q, need_t, F, Ft, Fu);
+}
+
 // A continuation rule and its partial derivatives.  Both rules are of the
 // log form v = f0 exp(a ln(f1/f0) + b): the pair rule with a = p, b = 0 (and
 // v = f0 + (f1 - f0) p when f0 or f1 is not positive), the low-Q^2 rule with
@@ -319,6 +347,11 @@ __device__ __forceinline__ void vjp_point(const GridView &g, const long long *xk
       irho = ddiv(1.0, ps.pq);
       iL = g.iln101;
     }
+    // sites on a knot (weights (1, 0, 0, 0)): the x rule's x sites, the Q rule's Q sites but the
+    // low-Q^2 rule's second one
+    bool xk[2], qk[2];
+    for (int a = 0; a < nsx; a++) xk[a] = X[a].B[1] == 0.0 && X[a].B[2] == 0.0 && X[a].B[3] == 0.0;
+    for (int b = 0; b < nsq; b++) qk[b] = Q[b].B[1] == 0.0 && Q[b].B[2] == 0.0 && Q[b].B[3] == 0.0;
     double sx = 0.0, sq = 0.0;
     for (int f = 0; f < g.nf; f++) {
       const double c = cot[p * g.nf + f];
@@ -326,7 +359,8 @@ __device__ __forceinline__ void vjp_point(const GridView &g, const long long *xk
       for (int a = 0; a < nsx; a++)
         for (int b = 0; b < nsq; b++) {
           const double *blk = g.coef + (((size_t)Q[b].c * g.nx + X[a].c) * g.nf + f) * 16;
-          patch_d(blk, X[a], Q[b], !lowx, F[a][b], Ft[a][b], Fu[a][b]);  // x sites of the x rule are fixed
+          // x sites of the x rule are fixed (no F_t), Q sites of the Q rule too (no F_u)
+          patch_site(blk, X[a], Q[b], xk[a], qk[b], !lowx, realq, F[a][b], Ft[a][b], Fu[a][b]);
         }
       // the q rule on each x site (lam_q: dA/dF(a, 0), dA/dF(a, 1), dA/dpar), then the x rule
       double A[2], l0[2], l1[2], lpar[2];
