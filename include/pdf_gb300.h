@@ -282,7 +282,7 @@ PDF_API int xfxq2_all_flavours_host_noalloc(const pdf_grid *grid, const double *
  * `stream`.  Invalid points get NaN gradients and add nothing to
  * grad_values.  A point exactly on the last x (top Q^2) knot gets the
  * one-sided derivative of the last cell.
- * Batches of 16384 points or more (grids with at most 16 flavours and
+ * Batches of 2048 points or more (grids with at most 16 flavours and
  * ~65K cells) are sorted by cell on the device first: the call then takes
  * 8 B per point (plus 4 B per cell) of stream-ordered scratch from a memory
  * pool the library keeps per device, and releases it on `stream`; if that

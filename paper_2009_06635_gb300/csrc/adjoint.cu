@@ -10,7 +10,7 @@
 // w_a the tangent-augmented Hermite weight of knot a (the patch is linear in
 // the knot values: dF/df_ab = w_a(t) w_b(u)).  The x and Q^2 derivatives are
 // summed over flavours in registers, in a fixed order.  Small batches run
-// k_vjp (continuation points queued per warp by kind); batches of 16384
+// k_vjp (continuation points queued per warp by kind); batches of 2048
 // points or more are first sorted by cell and run k_vjp_sorted, which
 // contracts the knot-value terms of same-cell runs before its atomics.
 //
@@ -516,7 +516,7 @@ k_vjp(GridView g, const double *__restrict__ xa, const double *__restrict__ qa, 
 // work, and their atomics a stream of L2 reductions).
 constexpr int kSortBins0 = 4;        // bins 0..2: continuation kinds, 3: invalid, then the cells
 constexpr int kSortMaxBins = 65540;  // above this the grid has too many cells for runs to form
-constexpr long long kSortMinN = 16384;
+constexpr long long kSortMinN = 2048;
 constexpr int kSortThreads = 128;    // three blocks per SM: 12 warps at <= 168 registers
 constexpr int kStPad = 17;           // float2 per staged row (16 used): 2-way bank conflicts at most
 

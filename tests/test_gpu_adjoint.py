@@ -159,7 +159,7 @@ def test_full_size_batch_in_the_benchmark_configuration(full, synth):
 
 
 def test_sorted_batch_matches_oracle_and_small_batches(full, synth):
-    """Batches of 16384 points or more are sorted by cell, and the knot-value
+    """Batches of 2048 points or more are sorted by cell, and the knot-value
     terms of each warp's run of same-cell points are contracted in
     float-float before one atomic per knot and flavour; smaller batches
     scatter point by point.  Both are checked against the oracle's knot
@@ -185,7 +185,7 @@ def test_sorted_batch_matches_oracle_and_small_batches(full, synth):
     perm = rng.permutation(n)
     x, q2, cot = x[perm], q2[perm], cot[perm]
     gx, gq, gv = run_vjp(G, x, q2, cot)  # sorted
-    parts = [run_vjp(G, x[a:a + 6000], q2[a:a + 6000], cot[a:a + 6000]) for a in range(0, n, 6000)]
+    parts = [run_vjp(G, x[a:a + 1500], q2[a:a + 1500], cot[a:a + 1500]) for a in range(0, n, 1500)]
     cx = np.concatenate([p[0] for p in parts])
     cq = np.concatenate([p[1] for p in parts])
     cv = sum(p[2] for p in parts)
