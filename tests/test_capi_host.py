@@ -59,6 +59,31 @@ def test_null_arguments_are_rejected(lib):
     assert lib.pdf_grid_invalid_count(None, ctypes.byref(c)) == -1
 
 
+def test_null_arguments_of_the_growth_entries_are_rejected(lib):
+    """The adjoint, member sets, Monte Carlo integration, surrogate and LHAPDF
+    entries validate their handles before any CUDA call, and freeing NULL is
+    a no-op."""
+    h = ctypes.c_void_p(None)
+    assert lib.xfxq2_all_flavours_vjp(None, None, None, 10, None, None, None, None, None) == -1
+    assert b"vjp" in lib.pdf_last_error()
+    assert lib.xfxq2_all_members(None, None, None, 10, None, None) == -1
+    assert lib.pdf_mc_integrate(None, None, 0, 10, 10, None, None) == -1
+    assert lib.pdf_surrogate_create(None, None, None, 1024, ctypes.byref(h)) == -1
+    assert lib.pdf_surrogate_create_ex(None, None, None, 1024, 0, ctypes.byref(h)) == -1
+    assert lib.pdf_surrogate_eval(None, None, None, 10, None, None) == -1
+    assert lib.pdf_surrogate_train(None, None, None, None, 10, None, None, None) == -1
+    assert lib.pdf_surrogate_build_error_map(None, None, None, None, 10, 1e-3, None) == -1
+    nfb = ctypes.c_ulonglong()
+    assert lib.pdf_surrogate_eval_fallback(None, None, None, None, 10, None, ctypes.byref(nfb), None) == -1
+    n = ctypes.c_size_t()
+    assert lib.pdf_surrogate_nparams(None, ctypes.byref(n)) == -1
+    assert lib.pdf_surrogate_free(None) == 0
+    assert lib.pdf_lhapdf_read(None, None, ctypes.byref(h)) == -1
+    assert lib.pdf_load_lhapdf(None, 0, 1, ctypes.byref(h)) == -1
+    assert lib.pdf_lhapdf_free(None) == 0
+    assert h.value is None
+
+
 @pytest.mark.parametrize("case", ["x_not_increasing", "x_above_one", "x_zero", "nq_one", "boundary_gap",
                                   "q2_negative", "value_nan", "pid_repeat", "alphas_decreasing",
                                   "alphas_short_subgrid", "nx_one"])
