@@ -236,3 +236,30 @@ def test_sorted_batch_keeps_each_knots_precision(full, synth):
     err = np.abs(gv - go)
     assert (err <= 1e-10 * gabs + 1e-300).all(), (err / np.maximum(gabs, 1e-300)).max()
     assert np.abs(gv[..., 0]).max() < 1e-20 < np.abs(gv[..., 1]).max() * 1e-40
+
+
+def test_large_batch_on_a_grid_the_sort_does_not_take(synth, oracle_mod):
+    """More than 16 flavours: the contraction's lane layout does not fit, so
+    even a large batch runs the unsorted kernel (its per-warp queues fill);
+    its gradients against the oracle."""
+    full = synth.grid_full()
+    pids = list(full.pids) + [22, 23, 24, 25, 26]
+    params = synth.flavour_params(len(pids), 41)
+    qb = [q * q for q in (synth.Q_RANGE[0], *synth.Q_THRESHOLDS, synth.Q_RANGE[1])]
+    subs = [synth.geom_knots(qb[s], qb[s + 1], synth.SUBGRID_KNOTS[s]) for s in range(3)]
+    g = synth.make_grid(full.x_knots, subs, pids, params=params)
+    assert g.nflav == 18
+    G = P.pdf_load_grid(g)
+    og = oracle_mod.OracleGrid(g)
+    n = 8000
+    x, q2, cot = synth.adjoint_inputs(n, g.nflav, 45, 46)
+    gx, gq, gv = run_vjp(G, x, q2, cot)
+    dx, dq = og.dxfxq2(x, q2, "x"), og.dxfxq2(x, q2, "q2")
+    _, s, _ = og.xfxq2(x, q2)
+    sx = np.abs(cot * dx).sum(axis=1) + (np.abs(cot) * s).sum(axis=1) / (x * min_log_spacing(g.x_knots))
+    sq = np.abs(cot * dq).sum(axis=1) + (np.abs(cot) * s).sum(axis=1) / (q2 * min_log_spacing(g.q2_knots))
+    assert (np.abs(gx - (cot * dx).sum(axis=1)) <= 1e-10 * sx + 1e-280).all()
+    assert (np.abs(gq - (cot * dq).sum(axis=1)) <= 1e-10 * sq + 1e-280).all()
+    go, gabs = og.knot_grad(x, q2, cot, with_abs=True)
+    assert (np.abs(gv - go) <= 1e-10 * gabs + 1e-300).all()
+    G.free()
