@@ -149,8 +149,11 @@ class OracleGrid:
     def xfxq2(self, x, q2, cols=None, nthreads: int = 0):
         """-> (values, data_mass, marginal_flags), each [n][ncols].
 
-        data_mass is sum |w f| over the knots that entered (no cancellation):
-        the scale of a relative error where xf crosses zero.  marginal marks
+        data_mass is the first-order propagation of the knot values'
+        magnitudes through the same expression (sum over the knots that
+        entered of |f| times the magnitudes of the coefficients on every path;
+        >= |xf|, ~|xf| away from zero crossings): the scale of a relative
+        error where xf crosses zero.  marginal marks
         outputs whose extrapolation branch (a positivity test) lies within
         rounding of its threshold, so another FP64 implementation may take
         the other branch."""

@@ -56,10 +56,21 @@
  *   m  a running first-order rounding-error bound in units of the unit
  *      roundoff (|computed - exact| <~ m * 2^-53), used to flag branch
  *      decisions that rounding could flip;
- *   s  the data mass: the same computation with every knot value replaced by
- *      its magnitude and no cancellation (for an in-grid point,
- *      sum_ab |w_a(x) w_b(Q) f_ab|).  It is the scale of a relative error
- *      near zero crossings of xf, where |xf| itself is no scale.
+ *   s  the data mass: first-order propagation of the data's absolute size
+ *      through the same expression (a datum gives |f|; a + b and a - b give
+ *      s_a + s_b; a b gives |b| s_a + |a| s_b; a / b gives
+ *      (s_a + |a/b| s_b) / |b|; ln a gives s_a / |a|; e^a gives e^a s_a).
+ *      For an in-grid point it is sum_ab P_ab |f_ab|, P_ab the sum of the
+ *      magnitudes of the coefficients along every path from knot (a, b) to
+ *      the result, so s >= sum_ab |W_ab f_ab| >= |xf| with W_ab = d xf/d f_ab;
+ *      on a grid of constant value C, s = |C| R(t) R(u) with
+ *      R(t) = 1 + a0 t (1-t)^2 + a1 t^2 (1-t), a0 = 1 + d_i / d_(i-1) and
+ *      a1 = 1 + d_i / d_(i+1) for cell widths d (2 where the tangent is a
+ *      one-sided secant).  Through a log-linear continuation from knot
+ *      values it grows to |xf| (1 + 2|p|).
+ *      It is the scale of a relative error near zero crossings of xf, where
+ *      |xf| itself is no scale, and the size of the rounding any evaluation
+ *      order of the same formula can make.
  *
  * Build: gcc -O2 -fopenmp -ffp-contract=off -shared -fPIC (no FMA
  * contraction, so x86-64 and aarch64 hosts give identical bits).
