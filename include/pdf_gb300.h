@@ -184,6 +184,13 @@ PDF_API int xfxq2_all_flavours_alphas(const pdf_grid *grid, const double *x, con
 PDF_API int alphas_q2(const pdf_grid *grid, const double *q2, size_t n, double *out,
               cudaStream_t stream);
 
+/* alpha_s at n scales given as Q in GeV (not Q^2), FP64 [n]: the kernel
+ * squares each Q (one rounding) and continues as alphas_q2, so the result
+ * equals alphas_q2 at q2 = Q * Q bit for bit.  Q <= 0, NaN, +inf, or a Q
+ * whose square overflows, is invalid (NaN out, counter incremented).
+ * PDFFlow Sec. 2.1 / Fig. 1 (alphas_Q), Sec. 2.3. */
+PDF_API int alphas_q(const pdf_grid *grid, const double *q, size_t n, double *out, cudaStream_t stream);
+
 /* FP32 variants: float inputs and outputs, FP32 arithmetic and accumulation
  * on FP32-rounded patch coefficients; the knot search is exact for the float
  * inputs (the same cell an FP64 search picks) and ln x, ln Q^2 are taken
@@ -194,6 +201,7 @@ PDF_API int xfxq2_all_flavours_f32(const pdf_grid *grid, const float *x, const f
                            float *out, cudaStream_t stream);
 PDF_API int alphas_q2_f32(const pdf_grid *grid, const float *q2, size_t n, float *out,
                   cudaStream_t stream);
+PDF_API int alphas_q_f32(const pdf_grid *grid, const float *q, size_t n, float *out, cudaStream_t stream);
 /* FP32 all flavours and alpha_s in one pass (as xfxq2_all_flavours_alphas);
  * bit-identical to xfxq2_all_flavours_f32 and alphas_q2_f32. */
 PDF_API int xfxq2_all_flavours_alphas_f32(const pdf_grid *grid, const float *x, const float *q2, size_t n,
@@ -300,6 +308,15 @@ PDF_API int xfxq2_all_flavours_vjp(const pdf_grid *grid, const double *x, const 
  * the float-float contraction of the FP64 path in range.  Work on other
  * streams that reads the grid must be ordered after it by the caller. */
 PDF_API int pdf_grid_set_values(pdf_grid *grid, const double *values, cudaStream_t stream);
+
+/* Bound on the device scratch one call may take for a sorted path (the
+ * adjoint's, and the FP32 evaluation's for large batches): stream-ordered
+ * memory from a pool the library keeps per device.  A call whose scratch
+ * would exceed the bound runs its unsorted kernel, which needs none, with the
+ * same results to rounding.  Process-wide; default SIZE_MAX (no bound); 0
+ * keeps every call off the sorted paths.  Not part of the paper's method. */
+PDF_API int pdf_set_scratch_limit(size_t bytes);
+PDF_API int pdf_get_scratch_limit(size_t *bytes);
 
 /* Invalid-point counter: read (synchronous) and reset. */
 PDF_API int pdf_grid_invalid_count(const pdf_grid *grid, unsigned long long *count);

@@ -15,6 +15,9 @@ from pathlib import Path
 _PKG = Path(__file__).resolve().parent
 LIB_PATH = _PKG / "_lib" / "libpdfgb300.so"
 HEADERS = sorted((_PKG.parent / "include").glob("*.h"))
+# measurement and test hooks: a library of their own, not the C ABI above
+PROBE_LIB_PATH = _PKG / "_lib" / "libpdfgb300_probe.so"
+PROBE_HEADERS = sorted((_PKG / "probe").glob("*.h"))
 
 PDF_OK = 0
 ERRORS = {
@@ -58,7 +61,6 @@ SIGNATURES = {
     "xfxq2_all_flavours_alphas_f32": (I32, [P, P, P, SZ, P, P, P]),
     "pdf_mc_integrate": (I32, [P, P, ctypes.c_ulonglong, ctypes.c_ulonglong, SZ, P, P]),
     "pdf_load_lhapdf": (I32, [ctypes.c_char_p, I32, I32, ctypes.POINTER(P)]),
-    "pdf_probe_math": (I32, [P, I32, P, P, SZ, P, P]),
     "pdf_lhapdf_read": (I32, [ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(P)]),
     "pdf_lhapdf_desc": (I32, [P, ctypes.POINTER(GridDesc)]),
     "pdf_lhapdf_free": (I32, [P]),
@@ -66,6 +68,8 @@ SIGNATURES = {
     "xfxq2_f32": (I32, [P, I32, P, P, SZ, P, P]),
     "xfxq2_all_flavours_f32": (I32, [P, P, P, SZ, P, P]),
     "alphas_q2_f32": (I32, [P, P, SZ, P, P]),
+    "alphas_q": (I32, [P, P, SZ, P, P]),
+    "alphas_q_f32": (I32, [P, P, SZ, P, P]),
     "pdf_mc_event": (I32, [P, P, P, F64, SZ, P, P]),
     "pdf_mc_event_f32": (I32, [P, P, P, F32, SZ, P, P]),
     "xfxq2_all_flavours_host": (I32, [P, P, P, SZ, P, P]),
@@ -75,7 +79,8 @@ SIGNATURES = {
     "pdf_grid_invalid_count": (I32, [P, ctypes.POINTER(ctypes.c_ulonglong)]),
     "pdf_grid_reset_invalid_count": (I32, [P]),
     "pdf_last_error": (ctypes.c_char_p, []),
-    "pdf_probe_fma_rate": (I32, [I32, I32, ctypes.POINTER(ctypes.c_double)]),
+    "pdf_set_scratch_limit": (I32, [SZ]),
+    "pdf_get_scratch_limit": (I32, [ctypes.POINTER(SZ)]),
     "pdf_surrogate_create": (I32, [P, P, P, I32, ctypes.POINTER(P)]),
     "pdf_surrogate_create_ex": (I32, [P, P, P, I32, I32, ctypes.POINTER(P)]),
     "pdf_surrogate_free": (I32, [P]),
@@ -100,10 +105,17 @@ class TrainConfig(ctypes.Structure):
                 ("lr_min", ctypes.c_float), ("warmup", ctypes.c_int)]
 
 
-def header_functions() -> list[str]:
-    """Names of the functions the headers under include/ declare."""
+PROBE_SIGNATURES = {
+    "pdf_probe_fma_rate": (I32, [I32, I32, ctypes.POINTER(ctypes.c_double)]),
+    "pdf_probe_math": (I32, [P, I32, P, P, SZ, P, P]),
+    "pdf_probe_last_error": (ctypes.c_char_p, []),
+}
+
+
+def header_functions(headers=None) -> list[str]:
+    """Names of the functions the headers (default: those under include/) declare."""
     names = []
-    for h in HEADERS:
+    for h in HEADERS if headers is None else headers:
         names += re.findall(r"^PDF_API\s+(?:const\s+char\s*\*|int)\s*([A-Za-z_0-9]+)\s*\(", h.read_text(),
                             flags=re.M)
     return names
@@ -128,6 +140,33 @@ def load(build_if_missing: bool = True):
             fn.argtypes = args
         _lib = lib
         return lib
+
+
+_probe = None
+
+
+def load_probe():
+    """The measurement/test hooks library (built beside the evaluation library)."""
+    global _probe
+    with _lock:
+        if _probe is not None:
+            return _probe
+        if not PROBE_LIB_PATH.exists():
+            from . import build as _build
+
+            _build.build()
+        lib = ctypes.CDLL(str(PROBE_LIB_PATH), mode=os.RTLD_LOCAL if hasattr(os, "RTLD_LOCAL") else 0)
+        for name, (res, args) in PROBE_SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _probe = lib
+        return lib
+
+
+def check_probe(rc: int, what: str):
+    if rc != PDF_OK:
+        raise PdfError(rc, f"{what}: {load_probe().pdf_probe_last_error().decode()}")
 
 
 def last_error() -> str:

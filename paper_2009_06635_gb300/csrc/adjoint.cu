@@ -684,30 +684,6 @@ k_vjp_sorted(GridView g, const double *__restrict__ xa, const double *__restrict
   }
 }
 
-// Scratch of the sorted path, from a pool of the device's own (stream-ordered,
-// kept between calls up to 256 MB so a call does not map memory afresh).
-static cudaMemPool_t sort_pool(int dev) {
-  static std::mutex mu;
-  static cudaMemPool_t pools[64] = {};
-  if (dev < 0 || dev >= 64) return nullptr;
-  std::lock_guard<std::mutex> lock(mu);
-  if (!pools[dev]) {
-    cudaMemPoolProps props = {};
-    props.allocType = cudaMemAllocationTypePinned;
-    props.location.type = cudaMemLocationTypeDevice;
-    props.location.id = dev;
-    cudaMemPool_t p = nullptr;
-    if (cudaMemPoolCreate(&p, &props) != cudaSuccess) {
-      cudaGetLastError();
-      return nullptr;
-    }
-    unsigned long long keep = 256ull << 20;
-    cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
-    pools[dev] = p;
-  }
-  return pools[dev];
-}
-
 }  // namespace pdfgb
 
 using namespace pdfgb;
@@ -732,12 +708,12 @@ extern "C" int xfxq2_all_flavours_vjp(const pdf_grid *grid, const double *x, con
     static LaunchCache cache_t, cache_f;
     const size_t ssmem = smem + 2 * sizeof(float2) * kSortThreads * kStPad;
     LaunchCache &cache = grad_values ? cache_t : cache_f;
-    const int per_sm = grad_values ? cache.blocks_per_sm(k_vjp_sorted<true>, kSortThreads, ssmem)
-                                   : cache.blocks_per_sm(k_vjp_sorted<false>, kSortThreads, ssmem);
-    cudaMemPool_t pool = sort_pool(dev);
+    const int per_sm = grad_values ? cache.blocks_per_sm(k_vjp_sorted<true>, kSortThreads, ssmem, false)
+                                   : cache.blocks_per_sm(k_vjp_sorted<false>, kSortThreads, ssmem, false);
     void *buf = nullptr;
     const size_t cnt_bytes = ((size_t)nb * sizeof(unsigned) + 15) / 16 * 16;
     const size_t bytes = cnt_bytes + 16 + 2 * ((n * sizeof(unsigned) + 15) / 16 * 16);
+    cudaMemPool_t pool = bytes <= scratch_limit() ? sort_pool(dev) : nullptr;
     if (per_sm >= 1 && pool && cudaMallocFromPoolAsync(&buf, bytes, pool, stream) == cudaSuccess) {
       unsigned *cnt = static_cast<unsigned *>(buf);
       auto *next_tile = reinterpret_cast<unsigned long long *>(static_cast<char *>(buf) + cnt_bytes);

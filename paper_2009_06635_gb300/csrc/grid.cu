@@ -18,8 +18,10 @@
 //     knots are reproduced exactly;
 //   - fixed sites used by the continuation (1.01 Q2min, the top knots) and
 //     float thresholds for the exact FP32 search.
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -42,6 +44,33 @@ int check_launch(const char *what) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(PDF_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
   return PDF_OK;
+}
+
+std::atomic<size_t> g_scratch_limit{SIZE_MAX};
+size_t scratch_limit() { return g_scratch_limit.load(std::memory_order_relaxed); }
+
+// Stream-ordered scratch of the sorted paths, from a pool of the device's
+// own (kept between calls up to 256 MB, so a call does not map memory afresh).
+cudaMemPool_t sort_pool(int dev) {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  if (dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    if (cudaMemPoolCreate(&p, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    unsigned long long keep = 256ull << 20;
+    cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    pools[dev] = p;
+  }
+  return pools[dev];
 }
 
 // Knot weights of one cell in the cubic Bernstein basis
@@ -380,6 +409,16 @@ struct Arena {
 using namespace pdfgb;
 
 extern "C" const char *pdf_last_error(void) { return g_errbuf; }
+
+extern "C" int pdf_set_scratch_limit(size_t bytes) {
+  g_scratch_limit.store(bytes, std::memory_order_relaxed);
+  return PDF_OK;
+}
+extern "C" int pdf_get_scratch_limit(size_t *bytes) {
+  if (!bytes) return set_error(PDF_ERR_NULL, "pdf_get_scratch_limit: NULL output");
+  *bytes = scratch_limit();
+  return PDF_OK;
+}
 
 static int load_impl(const pdf_grid_desc *d, int nmem, const double *member_values, pdf_grid **out) {
   g_errbuf[0] = 0;

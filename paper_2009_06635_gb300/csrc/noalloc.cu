@@ -79,8 +79,9 @@ extern "C" int xfxq2_all_flavours_host_noalloc(const pdf_grid *g, const double *
   if (e == cudaSuccess) e = cudaMemcpyAsync(sq, q2, n * sizeof(double), cudaMemcpyHostToDevice, stream);
   if (e != cudaSuccess)
     return set_error(PDF_ERR_CUDA, "xfxq2_all_flavours_host_noalloc: copy in: %s", cudaGetErrorString(e));
-  rc = launch_all_f64(g, sx, sq, (long long)n, so, nullptr, stream);
-  if (rc == PDF_OK && alphas_out) rc = launch_alphas_f64(g, sq, (long long)n, sa, stream);
+  // all flavours and alpha_s in one pass (ln Q^2 taken once; the same bits
+  // as the two separate kernels)
+  rc = launch_all_f64(g, sx, sq, (long long)n, so, alphas_out ? sa : nullptr, stream);
   if (rc) return rc;
   e = cudaMemcpyAsync(out, so, n * nf * sizeof(double), cudaMemcpyDeviceToHost, stream);
   if (e == cudaSuccess && alphas_out)

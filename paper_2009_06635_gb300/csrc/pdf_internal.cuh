@@ -214,28 +214,43 @@ int check_launch(const char *what);
 // size (a small launch would otherwise pay for the attribute and occupancy
 // queries on every call).  The size attribute only grows, so concurrent
 // callers never lower it under one another's launch.  One device per process.
+// A failed attribute or occupancy query (e.g. more shared memory than the
+// device allows) counts as 0 blocks: callers with another kernel to fall back
+// on pass at_least_one = false and see the 0; the others get 1 and let the
+// launch report the error.
 struct LaunchCache {
   std::mutex mu;
   size_t attr = 0, sizes[16] = {};
   int occ[16] = {}, nc = 0;
   template <typename K>
-  int blocks_per_sm(K kern, int threads, size_t smem) {
+  int blocks_per_sm(K kern, int threads, size_t smem, bool at_least_one = true) {
     std::lock_guard<std::mutex> lock(mu);
     for (int i = 0; i < nc; i++)
-      if (sizes[i] == smem) return occ[i];
-    if (smem > attr) {
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      attr = smem;
-    }
+      if (sizes[i] == smem) return at_least_one && occ[i] < 1 ? 1 : occ[i];
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
-    if (per_sm < 1) per_sm = 1;
+    bool ok = true;
+    if (smem > attr) {
+      ok = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess;
+      if (ok) attr = smem;
+    }
+    if (ok) ok = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      per_sm = 0;
+    }
     const int slot = nc < 16 ? nc++ : 15;
     sizes[slot] = smem;
     occ[slot] = per_sm;
-    return per_sm;
+    return at_least_one && per_sm < 1 ? 1 : per_sm;
   }
 };
+
+// Process-wide bound on the stream-ordered device scratch one call may take
+// for a sorted path (pdf_set_scratch_limit; default: none).
+size_t scratch_limit();
+// The per-device memory pool the sorted paths take their scratch from (kept
+// between calls up to 256 MB), or nullptr.
+cudaMemPool_t sort_pool(int dev);
 
 // Evaluation layouts (see the kernels in xf64.cu and xfxq2.cu).
 enum { MODE_POINTS = 0, MODE_MC = 1, MODE_MEMBERS = 2 };
@@ -275,8 +290,7 @@ struct McGen;
 int launch_xf64(const pdf_grid *grid, int mode, const double *xa, const double *qa, const double *xb, double s,
                 long long n, int col0, int ncol, double *out, double *as_out, cudaStream_t st,
                 const McGen *gen = nullptr);
-// xfxq2.cu: all flavours (+ alpha_s when as_out is not null); alpha_s alone.
+// xfxq2.cu: all flavours (+ alpha_s when as_out is not null) in one pass.
 int launch_all_f64(const pdf_grid *g, const double *x, const double *q2, long long n, double *out,
                    double *as_out, cudaStream_t st);
-int launch_alphas_f64(const pdf_grid *g, const double *q2, long long n, double *out, cudaStream_t st);
 }  // namespace pdfgb

@@ -925,6 +925,10 @@ struct pdf_surrogate {
   int *tc_err;  // set by the inference kernel when a tensor-core wait ran out
   double *fb_x, *fb_q, *fb_out;
   size_t fb_cap;
+  // recorded after a fallback call's last use of fb_*: the next call's stream
+  // waits on it, so a call on another stream cannot overwrite them early
+  cudaEvent_t fb_done;
+  bool fb_pending;
   bool has_map;
   std::vector<void *> blocks;
   template <typename T>
@@ -1109,6 +1113,8 @@ static int create_body(pdf_surrogate *s, const pdf_grid *grid, const float *para
   for (int k = 0; k < 2 && !rc; k++)
     if (cudaEventCreateWithFlags(&s->tev[k], cudaEventDisableTiming) != cudaSuccess)
       rc = set_error(PDF_ERR_CUDA, "pdf_surrogate_create: training events");
+  if (!rc && cudaEventCreateWithFlags(&s->fb_done, cudaEventDisableTiming) != cudaSuccess)
+    rc = set_error(PDF_ERR_CUDA, "pdf_surrogate_create: fallback event");
   if (!rc) rc = s->alloc(&s->y, B * SOUT);
   if (!rc) rc = s->alloc(&s->t, B * SOUT);
   if (!rc) rc = s->alloc(&s->xfbuf, B * nf);
@@ -1167,6 +1173,10 @@ extern "C" int pdf_surrogate_free(pdf_surrogate *s) {
   }
   for (cudaEvent_t e : s->tev)
     if (e) cudaEventDestroy(e);
+  if (s->fb_done) {
+    cudaEventSynchronize(s->fb_done);
+    cudaEventDestroy(s->fb_done);
+  }
   for (void *p : {(void *)s->fb_idx, (void *)s->fb_x, (void *)s->fb_q, (void *)s->fb_out})
     if (p) cudaFree(p);
   for (void *p : s->blocks) cudaFree(p);
@@ -1390,6 +1400,10 @@ extern "C" int pdf_surrogate_eval_fallback(pdf_surrogate *s, const pdf_grid *gri
   if (n > 0xFFFFFFFFull) return set_error(PDF_ERR_ARG, "pdf_surrogate_eval_fallback: n too large");
   if (n == 0) { if (n_fallback) *n_fallback = 0; return PDF_OK; }
   std::lock_guard<std::mutex> lock(s->mu);
+  // the previous call (perhaps on another stream) may still read fb_* (its
+  // gather, fallback evaluation and scatter run after its count is known)
+  if (s->fb_pending && cudaStreamWaitEvent(st, s->fb_done, 0) != cudaSuccess)
+    return cuda_err(cudaGetLastError(), "pdf_surrogate_eval_fallback: ordering after the previous call");
   if (n > s->fb_cap) {
     for (void *p : {(void *)s->fb_idx, (void *)s->fb_x, (void *)s->fb_q, (void *)s->fb_out}) if (p) cudaFree(p);
     s->fb_idx = nullptr; s->fb_x = s->fb_q = s->fb_out = nullptr; s->fb_cap = 0;
@@ -1411,9 +1425,12 @@ extern "C" int pdf_surrogate_eval_fallback(pdf_surrogate *s, const pdf_grid *gri
   if (m > 0) {
     k_gather<<<(m + 255) / 256, 256, 0, st>>>(x, q2, s->fb_idx, m, s->fb_x, s->fb_q);
     rc = launch_all_f64(grid, s->fb_x, s->fb_q, (long long)m, s->fb_out, nullptr, st);
-    if (rc) return rc;
-    k_scatter<<<(unsigned)(((long long)m * s->nf + 255) / 256), 256, 0, st>>>(s->fb_out, s->fb_idx, m, s->nf, out);
+    if (!rc)
+      k_scatter<<<(unsigned)(((long long)m * s->nf + 255) / 256), 256, 0, st>>>(s->fb_out, s->fb_idx, m, s->nf,
+                                                                                out);
   }
+  s->fb_pending = cudaEventRecord(s->fb_done, st) == cudaSuccess;
+  if (rc) return rc;
   if (n_fallback) *n_fallback = m;
   return check_launch("pdf_surrogate_eval_fallback");
 }

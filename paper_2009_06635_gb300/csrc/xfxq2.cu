@@ -177,7 +177,9 @@ k_xf32(GridView g, const float *__restrict__ xa, const float *__restrict__ qa, c
   }
 }
 
-template <typename T>
+// SQ: the input is Q, squared here (Q <= 0 or NaN is invalid; a square that
+// overflows to infinity is invalid like Q^2 = inf).
+template <typename T, bool SQ>
 __global__ void __launch_bounds__(kThreads) k_alphas(GridView g, const T *__restrict__ qa,
                                                      long long n, T *__restrict__ out) {
   using K = typename Prec<T>::K;
@@ -190,6 +192,7 @@ __global__ void __launch_bounds__(kThreads) k_alphas(GridView g, const T *__rest
     long long i = base + threadIdx.x;
     bool present = i < n;
     T q2 = present ? qa[i] : T(1);
+    if (SQ) q2 = q2 > T(0) ? q2 * q2 : T(-1);
     bool bad = present && !((q2 > T(0)) && (q2 < T(INFINITY)));
     unsigned inv = __ballot_sync(0xffffffffu, bad);
     if ((threadIdx.x & 31) == 0 && inv) atomicAdd(g.invalid, (unsigned long long)__popc(inv));
@@ -244,7 +247,7 @@ static int launch_xf(const pdf_grid *grid, const T *xa, const T *qa, const T *xb
   else return launch_xf32<MODE>(grid, xa, qa, xb, s, n, col0, ncol, out, st);
 }
 
-template <typename T>
+template <typename T, bool SQ = false>
 static int launch_alphas(const pdf_grid *grid, const T *q2, long long n, T *out, cudaStream_t st) {
   const GridView &g = grid->v;
   using K = typename std::conditional<sizeof(T) == 8, long long, int>::type;
@@ -252,8 +255,8 @@ static int launch_alphas(const pdf_grid *grid, const T *q2, long long n, T *out,
   long long blocks = (n + kThreads - 1) / kThreads;
   long long cap = (long long)num_sms() * 8;
   if (blocks > cap) blocks = cap;
-  k_alphas<T><<<(unsigned)blocks, kThreads, smem, st>>>(g, q2, n, out);
-  return check_launch("alphas_q2 kernel");
+  k_alphas<T, SQ><<<(unsigned)blocks, kThreads, smem, st>>>(g, q2, n, out);
+  return check_launch(SQ ? "alphas_q kernel" : "alphas_q2 kernel");
 }
 
 static int check_common(const pdf_grid *g, const void *a, const void *b, const void *o, size_t n,
@@ -283,13 +286,14 @@ static int do_all(const pdf_grid *g, const T *x, const T *q2, size_t n, T *out, 
   return launch_xf<T, MODE_POINTS>(g, x, q2, nullptr, T(0), (long long)n, 0, g->v.nf, out, st);
 }
 
-template <typename T>
-static int do_alphas(const pdf_grid *g, const T *q2, size_t n, T *out, cudaStream_t st) {
-  int rc = check_common(g, q2, q2, out, n, "alphas_q2");
+template <typename T, bool SQ = false>
+static int do_alphas(const pdf_grid *g, const T *q, size_t n, T *out, cudaStream_t st) {
+  const char *what = SQ ? "alphas_q" : "alphas_q2";
+  int rc = check_common(g, q, q, out, n, what);
   if (rc) return rc;
-  if (g->v.na == 0) return set_error(PDF_ERR_NO_ALPHAS, "alphas_q2: grid has no alpha_s nodes");
+  if (g->v.na == 0) return set_error(PDF_ERR_NO_ALPHAS, "%s: grid has no alpha_s nodes", what);
   if (n == 0) return PDF_OK;
-  return launch_alphas<T>(g, q2, (long long)n, out, st);
+  return launch_alphas<T, SQ>(g, q, (long long)n, out, st);
 }
 
 template <typename T>
@@ -307,10 +311,6 @@ int launch_members_f64(const pdf_grid *g, const double *x, const double *q2, lon
   return launch_xf64(g, MODE_MEMBERS, x, q2, nullptr, 0.0, n, 0, g->v.nf, out, nullptr, st);
 }
 
-// Used by the host-memory path.
-int launch_alphas_f64(const pdf_grid *g, const double *q2, long long n, double *out, cudaStream_t st) {
-  return launch_alphas<double>(g, q2, n, out, st);
-}
 // All flavours, and alpha_s into as_out when not null, in one pass.
 int launch_all_f64(const pdf_grid *g, const double *x, const double *q2, long long n, double *out,
                    double *as_out, cudaStream_t st) {
@@ -360,6 +360,12 @@ extern "C" int alphas_q2(const pdf_grid *g, const double *q2, size_t n, double *
 }
 extern "C" int alphas_q2_f32(const pdf_grid *g, const float *q2, size_t n, float *out, cudaStream_t st) {
   return do_alphas<float>(g, q2, n, out, st);
+}
+extern "C" int alphas_q(const pdf_grid *g, const double *q, size_t n, double *out, cudaStream_t st) {
+  return do_alphas<double, true>(g, q, n, out, st);
+}
+extern "C" int alphas_q_f32(const pdf_grid *g, const float *q, size_t n, float *out, cudaStream_t st) {
+  return do_alphas<float, true>(g, q, n, out, st);
 }
 extern "C" int xfxq2_all_members(const pdf_grid *g, const double *x, const double *q2, size_t n, double *out,
                                  cudaStream_t st) {

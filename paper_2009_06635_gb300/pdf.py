@@ -3,6 +3,7 @@
     grid = pdf_load_grid(synthetic.grid_full())      # PDFFlow mkPDF (Sec. 2.1)
     out  = xfxq2_all_flavours(grid, x, q2)           # xfxQ2_allpid
     a    = alphas_q2(grid, q2)                       # alphas_Q2
+    a    = alphas_q(grid, q)                         # alphas_Q (Q in GeV)
 
 Tensors must be CUDA, contiguous, float64 (or float32 for the *_f32 paths);
 work is enqueued on torch's current stream of the tensors' device.  PyTorch
@@ -273,6 +274,20 @@ def alphas_q2(grid: Grid, q2: torch.Tensor, out=None) -> torch.Tensor:
     return out
 
 
+def alphas_q(grid: Grid, q: torch.Tensor, out=None) -> torch.Tensor:
+    """alpha_s at scales Q in GeV (squared by the kernel; FP64 or FP32 by the input dtype)."""
+    if q.dim() != 1:
+        raise ValueError("q must be 1-D")
+    out = _out(out, (q.shape[0],), q)
+    lib = _native.load()
+    f32 = q.dtype == torch.float32
+    dt = torch.float32 if f32 else torch.float64
+    fn = lib.alphas_q_f32 if f32 else lib.alphas_q
+    check(fn(grid.handle, _dev_ptr(q, dt, "q"), q.shape[0], _dev_ptr(out, dt, "out"),
+             _stream_handle(q.device)), "alphas_q")
+    return out
+
+
 def pdf_mc_event(grid: Grid, x1: torch.Tensor, x2: torch.Tensor, s: float, out=None) -> torch.Tensor:
     """Fused Monte Carlo event evaluation: [n][2 nflav + 1] with Q^2 = x1 x2 s."""
     _check_pair(x1, x2)
@@ -306,6 +321,18 @@ def xfxq2_all_flavours_host(grid: Grid, x, q2, out=None, alphas_out=None, with_a
                                           ctypes.c_void_p(qs.data_ptr()), xs.shape[0],
                                           ctypes.c_void_p(out.data_ptr()), aptr), "xfxq2_all_flavours_host")
     return out if alphas_out is None else (out, alphas_out)
+
+
+def set_scratch_limit(nbytes: int):
+    """Bound the device scratch one call may take for a sorted path (None: no bound)."""
+    lim = (1 << 64) - 1 if nbytes is None else int(nbytes)
+    check(_native.load().pdf_set_scratch_limit(lim), "pdf_set_scratch_limit")
+
+
+def scratch_limit() -> int:
+    v = ctypes.c_size_t()
+    check(_native.load().pdf_get_scratch_limit(ctypes.byref(v)), "pdf_get_scratch_limit")
+    return int(v.value)
 
 
 def pdf_grid_set_values(grid: Grid, values: torch.Tensor):

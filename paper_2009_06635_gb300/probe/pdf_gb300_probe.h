@@ -1,10 +1,13 @@
 /*
- * pdf_gb300_probe.h -- measurement helpers of the GB300 PDF library.
+ * pdf_gb300_probe.h -- measurement and test hooks, built as a library of
+ * their own (libpdfgb300_probe.so) beside the evaluation library; not part
+ * of its C ABI, and the paper has no counterpart.
  *
- * Not part of the evaluation path (the paper has no counterpart): they
- * measure the arithmetic ceilings that bound the evaluation kernels, so the
- * benchmark can state its roofline fractions against numbers taken on the
- * same GPU, next to the ceilings derived from unit counts and clocks.
+ * pdf_probe_fma_rate measures the arithmetic ceilings that bound the
+ * evaluation kernels, so a benchmark can state roofline fractions against
+ * numbers taken on the same GPU; pdf_probe_math runs the kernels' own
+ * elementary functions on given arguments, for tests against the C library.
+ * Errors are reported by return code and pdf_probe_last_error().
  */
 #ifndef PDF_GB300_PROBE_H
 #define PDF_GB300_PROBE_H
@@ -27,9 +30,13 @@ PDF_API int pdf_probe_fma_rate(int precision, int iters, double *flops_per_s);
  * (table-driven, Tang's method; within 2 ulp or 2e-17 absolute); fn 1:
  * out = e^a (within 2 ulp); fn 2: out = a / b (reciprocal approximation and
  * Newton steps, within 2 ulp; b may be NULL otherwise).  The tables are the
- * grid's.  Asynchronous on `stream`. */
+ * grid's (a handle of the evaluation library, loaded in the same process).
+ * Asynchronous on `stream`. */
 PDF_API int pdf_probe_math(const pdf_grid *grid, int fn, const double *a, const double *b, size_t n,
                            double *out, cudaStream_t stream);
+
+/* Description of the last probe error on the calling thread ("" if none). */
+PDF_API const char *pdf_probe_last_error(void);
 
 #ifdef __cplusplus
 }

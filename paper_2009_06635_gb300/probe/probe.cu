@@ -1,7 +1,33 @@
-// probe.cu -- FMA-rate microbenchmark (the ALU ceiling of the FP64 and FP32
-// evaluation kernels).  8 independent chains per thread hide the FMA latency.
+// probe.cu -- measurement and test hooks, linked into libpdfgb300_probe.so
+// (not the evaluation library): an FMA-rate microbenchmark (the ALU ceiling
+// of the FP64 and FP32 evaluation kernels; 8 independent chains per thread
+// hide the FMA latency) and the evaluation kernels' elementary functions on
+// given arguments.  It reads a grid handle's staged tables through the
+// evaluation library's internal layout, so both libraries are built from the
+// same headers.
+#include <cstdarg>
+#include <cstdio>
+
 #include "pdf_gb300_probe.h"
 #include "pdf_internal.cuh"
+
+namespace {
+thread_local char g_probe_err[256] = "";
+
+int probe_error(int code, const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_probe_err, sizeof g_probe_err, fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int probe_launch(const char *what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return probe_error(PDF_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+  return PDF_OK;
+}
+}  // namespace
 
 namespace pdfgb {
 
@@ -24,7 +50,7 @@ static int probe(int iters, double *out) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   T *sink = nullptr;
   cudaEvent_t e0, e1;
-  if (cudaMalloc(&sink, 256 * sizeof(T)) != cudaSuccess) return set_error(PDF_ERR_ALLOC, "probe: cudaMalloc");
+  if (cudaMalloc(&sink, 256 * sizeof(T)) != cudaSuccess) return probe_error(PDF_ERR_ALLOC, "probe: cudaMalloc");
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   const int blocks = sms * 8;
@@ -38,9 +64,9 @@ static int probe(int iters, double *out) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(sink);
-  if (e != cudaSuccess) return set_error(PDF_ERR_CUDA, "probe: %s", cudaGetErrorString(e));
+  if (e != cudaSuccess) return probe_error(PDF_ERR_CUDA, "probe: %s", cudaGetErrorString(e));
   *out = 2.0 * 8.0 * (double)iters * blocks * 256 / (ms * 1e-3);
-  return check_launch("probe");
+  return probe_launch("probe");
 }
 
 // The evaluation kernels' own elementary functions, elementwise (tang.cuh).
@@ -55,18 +81,20 @@ __global__ void k_math(GridView g, int fn, const double *a, const double *b, lon
 extern "C" int pdf_probe_math(const pdf_grid *grid, int fn, const double *a, const double *b, size_t n,
                               double *out, cudaStream_t stream) {
   using namespace pdfgb;
-  if (!grid || (n > 0 && (!a || !out || (fn == 2 && !b)))) return set_error(PDF_ERR_NULL, "pdf_probe_math: NULL argument");
-  if (fn < 0 || fn > 2) return set_error(PDF_ERR_ARG, "pdf_probe_math: fn must be 0, 1 or 2");
+  if (!grid || (n > 0 && (!a || !out || (fn == 2 && !b)))) return probe_error(PDF_ERR_NULL, "pdf_probe_math: NULL argument");
+  if (fn < 0 || fn > 2) return probe_error(PDF_ERR_ARG, "pdf_probe_math: fn must be 0, 1 or 2");
   if (n == 0) return PDF_OK;
   k_math<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(grid->v, fn, a, b, (long long)n, out);
-  return check_launch("pdf_probe_math");
+  return probe_launch("pdf_probe_math");
 }
 
 extern "C" int pdf_probe_fma_rate(int precision, int iters, double *flops_per_s) {
   using namespace pdfgb;
-  if (!flops_per_s) return set_error(PDF_ERR_NULL, "pdf_probe_fma_rate: NULL output");
-  if (iters < 1 || iters > (1 << 24)) return set_error(PDF_ERR_ARG, "pdf_probe_fma_rate: iters out of range");
+  if (!flops_per_s) return probe_error(PDF_ERR_NULL, "pdf_probe_fma_rate: NULL output");
+  if (iters < 1 || iters > (1 << 24)) return probe_error(PDF_ERR_ARG, "pdf_probe_fma_rate: iters out of range");
   if (precision == 64) return probe<double>(iters, flops_per_s);
   if (precision == 32) return probe<float>(iters, flops_per_s);
-  return set_error(PDF_ERR_ARG, "pdf_probe_fma_rate: precision must be 32 or 64");
+  return probe_error(PDF_ERR_ARG, "pdf_probe_fma_rate: precision must be 32 or 64");
 }
+
+extern "C" const char *pdf_probe_last_error(void) { return g_probe_err; }

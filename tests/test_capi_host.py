@@ -26,6 +26,35 @@ def test_library_exports_every_declared_function(lib):
     assert set(names) <= exported
 
 
+def test_probe_hooks_live_in_their_own_library(lib):
+    """The measurement/test hooks are a separate library: the evaluation
+    library exports none of them, the probe library exports what its header
+    declares."""
+    out = subprocess.run(["nm", "-D", "--defined-only", str(_native.LIB_PATH)], capture_output=True, text=True).stdout
+    assert not [l for l in out.splitlines() if "pdf_probe" in l]
+    probe = _native.load_probe()
+    names = _native.header_functions(_native.PROBE_HEADERS)
+    assert set(names) == set(_native.PROBE_SIGNATURES)
+    for n in names:
+        assert hasattr(probe, n), n
+    assert probe.pdf_probe_fma_rate(16, 10, None) == -1  # NULL output checked before any CUDA call
+    assert b"NULL" in probe.pdf_probe_last_error()
+
+
+def test_scratch_limit_round_trip(lib):
+    import paper_2009_06635_gb300 as P
+
+    before = P.scratch_limit()
+    try:
+        P.set_scratch_limit(12345)
+        assert P.scratch_limit() == 12345
+        P.set_scratch_limit(None)
+        assert P.scratch_limit() == (1 << 64) - 1
+    finally:
+        P.set_scratch_limit(before)
+    assert lib.pdf_get_scratch_limit(None) == -1
+
+
 def _desc(g, **over):
     arrs = dict(x=np.ascontiguousarray(g.x_knots), nq=np.ascontiguousarray(g.nq, dtype=np.int32),
                 q2=np.ascontiguousarray(g.q2_knots), pids=np.ascontiguousarray(g.pids, dtype=np.int32),
@@ -51,6 +80,9 @@ def test_null_arguments_are_rejected(lib):
     assert b"NULL" in lib.pdf_last_error()
     assert lib.xfxq2_all_flavours(None, None, None, 10, None, None) == -1
     assert lib.alphas_q2(None, None, 0, None, None) == -1
+    assert lib.alphas_q(None, None, 0, None, None) == -1
+    assert b"alphas_q" in lib.pdf_last_error()
+    assert lib.alphas_q_f32(None, None, 0, None, None) == -1
     assert lib.xfxq2(None, 21, None, None, 0, None, None) == -1
     assert lib.pdf_mc_event(None, None, None, 1.0, 0, None, None) == -1
     assert lib.xfxq2_all_flavours_host(None, None, None, 0, None, None) == -1
@@ -138,7 +170,7 @@ def test_malformed_descriptors_are_rejected(lib, case):
 def test_python_binding_names_match_the_c_abi():
     import paper_2009_06635_gb300 as P
 
-    for name in ("pdf_load_grid", "xfxq2", "xfxq2_all_flavours", "alphas_q2", "pdf_mc_event",
+    for name in ("pdf_load_grid", "xfxq2", "xfxq2_all_flavours", "alphas_q2", "alphas_q", "pdf_mc_event",
                  "xfxq2_all_flavours_host"):
         assert callable(getattr(P, name))
         assert name in _native.SIGNATURES

@@ -263,3 +263,29 @@ def test_large_batch_on_a_grid_the_sort_does_not_take(synth, oracle_mod):
     go, gabs = og.knot_grad(x, q2, cot, with_abs=True)
     assert (np.abs(gv - go) <= 1e-10 * gabs + 1e-300).all()
     G.free()
+
+
+def test_no_scratch_runs_the_unsorted_kernel(full, synth):
+    """With the scratch bound at 0 a batch above the sort threshold takes the
+    unsorted kernel (no scratch); its gradients against the oracle and
+    against the sorted path's."""
+    g, G, og = full
+    n = 6000
+    x, q2, cot = synth.adjoint_inputs(n, g.nflav, 55, 56)
+    sx_, sq_, sv_ = run_vjp(G, x, q2, cot)  # sorted
+    before = P.scratch_limit()
+    try:
+        P.set_scratch_limit(0)
+        gx, gq, gv = run_vjp(G, x, q2, cot)
+    finally:
+        P.set_scratch_limit(before)
+    dx, dq = og.dxfxq2(x, q2, "x"), og.dxfxq2(x, q2, "q2")
+    _, s, _ = og.xfxq2(x, q2)
+    sx = np.abs(cot * dx).sum(axis=1) + (np.abs(cot) * s).sum(axis=1) / (x * min_log_spacing(g.x_knots))
+    sq = np.abs(cot * dq).sum(axis=1) + (np.abs(cot) * s).sum(axis=1) / (q2 * min_log_spacing(g.q2_knots))
+    assert (np.abs(gx - (cot * dx).sum(axis=1)) <= 1e-10 * sx + 1e-280).all()
+    assert (np.abs(gq - (cot * dq).sum(axis=1)) <= 1e-10 * sq + 1e-280).all()
+    go, gabs = og.knot_grad(x, q2, cot, with_abs=True)
+    assert (np.abs(gv - go) <= 1e-10 * gabs + 1e-300).all()
+    assert (np.abs(gv - sv_) <= 1e-12 * gabs + 1e-300).all()
+    assert (np.abs(gx - sx_) <= 1e-13 * sx + 1e-280).all()

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 import torch
 
-from parity import RTOL_FP64, RTOL_FP32, assert_parity, special_points
+from parity import RTOL_FP64, assert_fp32, assert_parity, special_points
 
 pytestmark = pytest.mark.gpu
 
@@ -45,8 +45,9 @@ def check(synth, oracle_mod, g, n=20_000, seed=1, fp32=True):
     if fp32:
         x32, q32 = x.astype(np.float32), q2.astype(np.float32)
         o32 = P.xfxq2_all_flavours(G, dev(x32, torch.float32), dev(q32, torch.float32)).cpu().numpy()
-        v32, s32, fl32 = og.xfxq2(x32.astype(np.float64), q32.astype(np.float64))
-        assert_parity(o32, v32, s32, fl32, RTOL_FP32, "fp32")
+        xs, qs = x32.astype(np.float64), q32.astype(np.float64)
+        v32, s32, fl32 = og.xfxq2(xs, qs)
+        assert_fp32(g, xs, qs, o32, v32, s32, fl32, "fp32")
     return G
 
 

@@ -25,7 +25,7 @@ def run(G, fn, a, b=None):
     ad = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
     bd = torch.from_numpy(np.ascontiguousarray(b, dtype=np.float64)).cuda() if b is not None else None
     out = torch.empty_like(ad)
-    _native.check(_native.load().pdf_probe_math(G.handle, fn, ctypes.c_void_p(ad.data_ptr()),
+    _native.check_probe(_native.load_probe().pdf_probe_math(G.handle, fn, ctypes.c_void_p(ad.data_ptr()),
                                                 ctypes.c_void_p(bd.data_ptr() if bd is not None else 0), len(a),
                                                 ctypes.c_void_p(out.data_ptr()), None), "pdf_probe_math")
     torch.cuda.synchronize()

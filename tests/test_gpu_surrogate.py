@@ -177,6 +177,47 @@ def test_full_size_inference_sampled(setup, synth):
     assert np.quantile(dy, 0.99) < 2e-2 and dy.max() < 1e-1, (np.quantile(dy, 0.99), dy.max())
 
 
+def test_fallback_calls_on_two_streams_from_two_threads(setup, synth):
+    """Fallback calls share the surrogate's gather/scatter buffers, and each
+    call's gather, interpolation and scatter still run after it returns: a
+    call on another stream must wait for them.  Two threads, each with its own
+    non-blocking stream and a batch that falls back nearly everywhere (an
+    untrained network), must each get what the same call gives alone."""
+    import threading
+
+    g, G, Surrogate, params, freq, scale, bounds, og = setup
+    s = Surrogate(G, params, freq, max_batch=1024)
+    xv, qv = synth.ingrid_samples(g, 50_000, 25)
+    s.build_error_map(G, dev(xv), dev(qv), threshold=1e-3)
+    batches = [tuple(map(dev, synth.queries_full(n, 70 + k))) for k, n in enumerate((600_001, 400_003))]
+    alone = []
+    for xd, qd in batches:
+        out, nfb = s.eval_fallback(G, xd, qd)
+        torch.cuda.synchronize()
+        assert nfb > 0.9 * xd.shape[0]
+        alone.append(out.cpu())
+    res = [[None] * 4 for _ in batches]
+
+    def run(k):
+        torch.cuda.set_device(0)
+        st = torch.cuda.Stream()
+        xd, qd = batches[k]
+        with torch.cuda.stream(st):
+            for r in range(4):
+                res[k][r], _ = s.eval_fallback(G, xd, qd)
+        st.synchronize()
+
+    th = [threading.Thread(target=run, args=(k,)) for k in range(len(batches))]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    torch.cuda.synchronize()
+    for k in range(len(batches)):
+        for r in range(4):
+            assert torch.equal(res[k][r].cpu(), alone[k]), (k, r)
+
+
 def test_grid_with_other_flavours_is_refused(setup, synth):
     """The error map, training and the fallback write [n][nflav] rows of the
     surrogate's width: a grid with another flavour count is an argument
