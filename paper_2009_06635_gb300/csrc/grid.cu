@@ -26,6 +26,7 @@
 #include <cstring>
 #include <new>
 
+#include "ffmath.cuh"
 #include "pdf_internal.cuh"
 
 namespace pdfgb {
@@ -108,6 +109,8 @@ struct Stage {
   float2 *coefff;
   double2 *tlogtab;  // tang.cuh tables, filled on the host before staging
   double *tloghtab, *texptab;
+  float4 *fflog;     // ffmath.cuh tables, likewise
+  float2 *ffexp;
   int *ffbad;  // set when a control point is outside the float-float range
   int *row_qc, *qc_row;
   double *scal;  // scalar outputs, see k_scalars
@@ -129,6 +132,22 @@ void tang_tables(double *logtab, double *loghtab, double *exptab) {
     loghtab[j] = (double)logl((long double)F / 2.0L);
   }
   for (int k = 0; k < kExpTab; k++) exptab[k] = (double)exp2l((long double)k / 256.0L);
+}
+
+// Float-float tables of ffmath.cuh: c_j = 1/F_j rounded to float and -ln c_j
+// split into hi + lo (F_j = 1 + j/128), and 2^(k/64) split likewise.
+void ff_tables(float *logtab, float *exptab) {
+  auto split = [](long double v, float *o) {
+    o[0] = (float)v;
+    o[1] = (float)(v - (long double)o[0]);
+  };
+  for (int j = 0; j < kFFLogTab; j++) {
+    const float c = (float)(1.0L / (1.0L + j / 128.0L));
+    logtab[4 * j] = c;
+    split(-logl((long double)c), logtab + 4 * j + 1);
+    logtab[4 * j + 3] = 0.f;
+  }
+  for (int k = 0; k < kFFExpTab; k++) split(exp2l(k / 64.0L), exptab + 2 * k);
 }
 
 // FP32 cell table: both end knots rounded to float (k0f, k1f), their float
@@ -457,6 +476,7 @@ static int load_impl(const pdf_grid_desc *d, int nmem, const double *member_valu
     S.ffbad = A.take<int>(1);
     S.tlogtab = A.take<double2>(kLogTab); S.tloghtab = A.take<double>(kLogTab);
     S.texptab = A.take<double>(kExpTab);
+    S.fflog = A.take<float4>(kFFLogTab); S.ffexp = A.take<float2>(kFFExpTab);
     S.acell = A.take<double>(6 * (na > 0 ? na : 1));
     S.acell32 = A.take<float>(6 * (na > 0 ? na : 1));
     S.xthr32 = A.take<float>(nx); S.q2thr32 = A.take<float>(nrows); S.aq2thr32 = A.take<float>(na > 0 ? na : 1);
@@ -506,6 +526,10 @@ static int load_impl(const pdf_grid_desc *d, int nmem, const double *member_valu
     H2D(S.tlogtab, lt, sizeof lt);
     H2D(S.tloghtab, lh, sizeof lh);
     H2D(S.texptab, et, sizeof et);
+    float fl[4 * kFFLogTab], fe[2 * kFFExpTab];
+    ff_tables(fl, fe);
+    H2D(S.fflog, fl, sizeof fl);
+    H2D(S.ffexp, fe, sizeof fe);
   }
   if (e == cudaSuccess) e = cudaMemset(inv, 0, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(S.ffbad, 0, sizeof(int));
@@ -541,6 +565,7 @@ static int load_impl(const pdf_grid_desc *d, int nmem, const double *member_valu
   v.coef = S.coef; v.coef32 = S.coef32; v.xW = S.xW; v.qW = S.qW;
   v.coefff = S.coefff; v.ff = ffbad ? 0 : 1;
   v.tlogtab = S.tlogtab; v.tloghtab = S.tloghtab; v.texptab = S.texptab;
+  v.fflog = S.fflog; v.ffexp = S.ffexp;
   v.nmem = nmem;
   v.mstride = (size_t)(nqc + 1) * nx * nf * 16;
   v.nfp = nfp;
@@ -566,6 +591,11 @@ static int load_impl(const pdf_grid_desc *d, int nmem, const double *member_valu
   v.q2maxinv32 = (float)(1.0 / v.q2max); v.idq_top32 = (float)v.idq_top;
   v.q2min32 = (float)v.q2min; v.ln101_32 = (float)v.ln101;
   v.iln101 = 1.0 / v.ln101; v.iln101_32 = (float)(1.0 / v.ln101);
+  {
+    const long double il = 1.0L / logl(1.01L);
+    v.iln101_ffh = (float)il;
+    v.iln101_ffl = (float)(il - (long double)v.iln101_ffh);
+  }
   v.q101_u32 = (float)v.q101_u;
   v.invalid = inv;
   for (int f = 0; f < nf; f++) g->pids[f] = d->pids[f];

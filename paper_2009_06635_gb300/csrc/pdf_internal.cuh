@@ -118,6 +118,10 @@ struct GridView {
   // left the offsets of the fields above as they were
   double iln101;
   float iln101_32;
+  // float-float continuation (ffmath.cuh): its tables, and 1 / ln 1.01 as a pair
+  const float4 *fflog;  // [kFFLogTab]
+  const float2 *ffexp;  // [kFFExpTab]
+  float iln101_ffh, iln101_ffl;
 };
 
 // ---------------------------------------------------------------------------

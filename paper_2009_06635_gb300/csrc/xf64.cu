@@ -16,13 +16,18 @@
 // outputs, so stores coalesce): in-grid points contract the cell's 16
 // float-float control points with float-float Bernstein weights on the FP32
 // pipe (GB300 issues FP32 at 64x its FP64 rate; the result is good to about
-// 2^-46 of the data scale); exact knot hits and continuation sites use FP64.
-// The continuation classes share one copy of the pair rule, so lanes of
-// different classes reconverge before its logarithm and exponential.
+// 2^-46 of the data scale); exact knot hits use FP64.  Continuation points
+// evaluate their sites and rules in float-float too (ffmath.cuh: quotient,
+// logarithm and exponential on the FP32 pipe; FP64 only for the final sum and
+// for exponents beyond the float range), on grids whose control points are
+// in float-float range; other grids keep the FP64 rules.  The continuation
+// classes share one copy of the pair rule, so lanes of different classes
+// reconverge before its logarithm and exponential.
 #include <cmath>
 
 #include "mc.cuh"
 #include "ff.cuh"
+#include "ffmath.cuh"
 #include "sites.cuh"
 
 namespace pdfgb {
@@ -45,10 +50,13 @@ struct alignas(16) Rec64 {
   double W[32][18];
   double px[32], pq[32], lr[32];
 };
-// Continuation points waiting for a full tile (at most 31 + 32).
+// Continuation points waiting for a full tile, one queue per class (at most
+// 31 + 32 each), as point indices (MODE_MC: event index times 2 plus the side);
+// a drain reads the coordinates again.  Full tiles of one class run one code
+// path; only the leftovers at the end mix classes.
+constexpr int kFar = C_LOWX_LOWQ - C_LOWX + 1;  // continuation classes
 struct alignas(16) Queue64 {
-  double x[64], q2[64];
-  long long ob[64];
+  unsigned idx[kFar][64];
 };
 
 // sum_m w_m b_m with w (hi, lo) from the record and b (hi, lo) from the
@@ -124,13 +132,158 @@ __device__ __forceinline__ double site_t(const double *c, const Rec64 &R, int p,
   return fma(R.W[p][4 * a + 3], v1.y, f);
 }
 
+// ---- float-float continuation ------------------------------------------------
+// A continuation point's record row holds its Bernstein weights as float
+// pairs, W2[0..3] Bx0, [4..7] Bx1, [8..11] Bq0, [12..15] Bq1, and px, pq, lr
+// as float pairs in the same 8-byte slots.  Sites contract the float-float
+// control points (coefff: pair m2 of control points m = 2 m2, 2 m2 + 1 of a
+// flavour as one float4 {hi, lo, hi, lo}; control point m = 4 l + k).
+__device__ __forceinline__ ff2 ffv(const double &d) {
+  const float2 v = reinterpret_cast<const float2 &>(d);
+  return {v.x, v.y};
+}
+__device__ __forceinline__ ff2 ffw(const float2 &w) { return {w.x, w.y}; }
+__device__ __forceinline__ ff2 ff_norm(float sh, float sl) { return ff_two_sum(sh, sl); }
+// on an x knot (t = 0): sum_l Bq[l] b[l][0]
+__device__ __forceinline__ ff2 ffsite_u(const float4 *c, int nfp, const float2 *bq) {
+  float sh = 0.f, sl = 0.f;
+#pragma unroll
+  for (int l = 0; l < 4; l++) {
+    const float4 v = __ldg(c + (size_t)(2 * l) * nfp);
+    ff_acc(sh, sl, ffw(bq[l]), v.x, v.y);
+  }
+  return ff_norm(sh, sl);
+}
+// on a Q knot (u = 0): sum_k Bx[k] b[0][k]
+__device__ __forceinline__ ff2 ffsite_t(const float4 *c, int nfp, const float2 *bx) {
+  const float4 v0 = __ldg(c), v1 = __ldg(c + nfp);
+  float sh = 0.f, sl = 0.f;
+  ff_acc(sh, sl, ffw(bx[0]), v0.x, v0.y);
+  ff_acc(sh, sl, ffw(bx[1]), v0.z, v0.w);
+  ff_acc(sh, sl, ffw(bx[2]), v1.x, v1.y);
+  ff_acc(sh, sl, ffw(bx[3]), v1.z, v1.w);
+  return ff_norm(sh, sl);
+}
+// general: sum_l Bq[l] sum_k Bx[k] b[l][k]
+__device__ __forceinline__ ff2 ffsite_tu(const float4 *c, int nfp, const float2 *bx, const float2 *bq) {
+  float sh = 0.f, sl = 0.f;
+#pragma unroll
+  for (int l = 0; l < 4; l++) {
+    const ff2 r = ffsite_t(c + (size_t)(2 * l) * nfp, nfp, bx);
+    ff_acc(sh, sl, ffw(bq[l]), r.h, r.l);
+  }
+  return ff_norm(sh, sl);
+}
+__device__ __forceinline__ ff2 ffknot(const float4 *c) {
+  const float4 v = __ldg(c);
+  return {v.x, v.y};
+}
+
+// A rule's result: a float pair, or (out of the pairs' range) a double.
+struct FFRes {
+  ff2 v;
+  double d;
+  bool dbl;
+};
+__device__ __forceinline__ ff2 res_ff(const FFRes &r) { return r.dbl ? ff_of(r.d) : r.v; }
+__device__ __forceinline__ double res_d(const FFRes &r) { return r.dbl ? r.d : ff_to_d(r.v); }
+
+// The FP64 steps the float-pair rules fall back on (out of line: they are
+// rare, and inlined they would take registers from the common path).
+__device__ __noinline__ double pair_rule_fp64(double g0, double g1, double p) { return g0 * exp(p * log(g1 / g0)); }
+__device__ __noinline__ double lowq_rule_fp64(double f0, double f1, double rho, double lr, double iln101, bool pos) {
+  const double g = pos ? log(f1 / f0) * iln101 : 1.0;
+  return f0 * exp(((g * rho + 1.0) - rho) * lr);
+}
+
+// The pair rule: g0 (g1/g0)^p if both are > 0, else g0 + (g1 - g0) p.
+// Float pairs keep ~48 bits only while their low part is a normal float:
+// a quotient outside [2^-100, 2^100], an exponent beyond +-64 or a result
+// below 2^-100 in magnitude is taken again in FP64.
+constexpr float kFFLo = 0x1p-100f, kFFHi = 0x1p100f;
+__device__ __forceinline__ bool ff_ok(ff2 v) { return fabsf(v.h) >= kFFLo && fabsf(v.h) < kFFHi; }
+__device__ __forceinline__ FFRes ff_pair_rule(ff2 g0, ff2 g1, ff2 p, FFTabs FT) {
+  if (g0.h > 0.f && g1.h > 0.f) {
+    const ff2 r = ff_div(g1, g0);
+    if (ff_ok(r)) {
+      const ff2 y = ff_mul(p, ff_log(r, FT));
+      if (fabsf(y.h) < 64.f) {
+        const ff2 v = ff_mul(g0, ff_exp(y, FT));
+        if (ff_ok(v)) return {v, 0.0, false};
+      }
+    }
+    return {{0.f, 0.f}, pair_rule_fp64(ff_to_d(g0), ff_to_d(g1), ff_to_d(p)), true};
+  }
+  return {ff_add(g0, ff_mul(ff_sub(g1, g0), p)), 0.0, false};
+}
+// The low-Q^2 rule: gamma = ln(f1/f0) / ln 1.01 if both are > 0, else 1;
+// f0 rho^(gamma rho + 1 - rho) as f0 exp((gamma rho + 1 - rho) ln rho).
+__device__ __forceinline__ FFRes ff_lowq_rule(ff2 f0, ff2 f1, ff2 rho, ff2 lr, ff2 iln101, FFTabs FT) {
+  const bool pos = f0.h > 0.f && f1.h > 0.f;
+  ff2 gam = {1.f, 0.f};
+  bool fp64 = false;
+  if (pos) {
+    const ff2 r = ff_div(f1, f0);
+    if (ff_ok(r)) gam = ff_mul(ff_log(r, FT), iln101);
+    else fp64 = true;
+  }
+  if (!fp64) {
+    const ff2 ex = ff_sub(ff_add(ff_mul(gam, rho), ff2{1.f, 0.f}), rho);
+    const ff2 y = ff_mul(ex, lr);
+    if (fabsf(y.h) < 64.f) {
+      const ff2 v = ff_mul(f0, ff_exp(y, FT));
+      if (ff_ok(v) || f0.h == 0.f) return {v, 0.0, false};
+    }
+  }
+  return {{0.f, 0.f}, lowq_rule_fp64(ff_to_d(f0), ff_to_d(f1), ff_to_d(rho), ff_to_d(lr), ff_to_d(iln101), pos), true};
+}
+
+// A continuation item in float-float (the grid's control points are in range).
+__device__ __forceinline__ double eval_far_ff(const GridView &g, const Rec64 &R, int p, int col, int m,
+                                              FFTabs FT) {
+  const float4 *cb = reinterpret_cast<const float4 *>(g.coefff + (size_t)m * g.mstride_ff) + col;
+  const size_t cstride = (size_t)8 * g.nfp;  // float4 per cell
+  const int nfp = g.nfp;
+  auto C = [&](int a, int b) {
+    const int xc = a ? R.xc1[p] : R.xc0[p];
+    const int qc = b ? R.qc1[p] : R.qc0[p];
+    return cb + ((size_t)qc * g.nx + xc) * cstride;
+  };
+  const float2 *W2 = reinterpret_cast<const float2 *>(R.W[p]);
+  const ff2 il = ff2{g.iln101_ffh, g.iln101_ffl};
+  ff2 a, b, prm = ffv(R.px[p]);
+  switch (R.cls[p]) {
+    case C_LOWX:  // sites (x0, Q^2), (x1, Q^2): t = 0
+      a = ffsite_u(C(0, 0), nfp, W2 + 8);
+      b = ffsite_u(C(1, 0), nfp, W2 + 8);
+      break;
+    case C_HIGHQ:  // sites (x, Q2max), (x, knot below): u = 0
+      a = ffsite_t(C(0, 0), nfp, W2);
+      b = ffsite_t(C(0, 1), nfp, W2);
+      prm = ffv(R.pq[p]);
+      break;
+    case C_LOWQ:  // sites (x, Q2min): u = 0; (x, 1.01 Q2min): general
+      return res_d(ff_lowq_rule(ffsite_t(C(0, 0), nfp, W2), ffsite_tu(C(0, 1), nfp, W2, W2 + 12), ffv(R.pq[p]),
+                                ffv(R.lr[p]), il, FT));
+    case C_LOWX_HIGHQ:  // all four sites are knots
+      a = res_ff(ff_pair_rule(ffknot(C(0, 0)), ffknot(C(0, 1)), ffv(R.pq[p]), FT));
+      b = res_ff(ff_pair_rule(ffknot(C(1, 0)), ffknot(C(1, 1)), ffv(R.pq[p]), FT));
+      break;
+    default:  // C_LOWX_LOWQ
+      a = res_ff(ff_lowq_rule(ffknot(C(0, 0)), ffsite_u(C(0, 1), nfp, W2 + 12), ffv(R.pq[p]), ffv(R.lr[p]), il, FT));
+      b = res_ff(ff_lowq_rule(ffknot(C(1, 0)), ffsite_u(C(1, 1), nfp, W2 + 12), ffv(R.pq[p]), ffv(R.lr[p]), il, FT));
+      break;
+  }
+  return res_d(ff_pair_rule(a, b, prm, FT));
+}
+
 // One item: column col of the point in slot p, of member m.
 // RCP: the low-Q^2 rule multiplies by 1 / ln 1.01 (the Monte Carlo kernel,
 // where a fifth of the events take it; the other kernels keep the division,
 // which left their register allocation as measured fastest).
 template <bool RCP>
 __device__ __forceinline__ double eval_item64(const GridView &g, const Rec64 &R, int p, int col, int m,
-                                              LogTabs LT, const double *ET) {
+                                              LogTabs LT, const double *ET, FFTabs FT) {
   const double *cb = g.coef + (size_t)m * g.mstride + (size_t)col * 16;
   const size_t stride = (size_t)g.nf * 16;
   auto C = [&](int a, int b) {
@@ -145,6 +298,7 @@ __device__ __forceinline__ double eval_item64(const GridView &g, const Rec64 &R,
                     g.nfp, reinterpret_cast<const float2 *>(R.W[p]));
   if (cls == C_IN) return dot_w16(C(0, 0), R, p);
   if (cls == C_INVALID) return NAN;
+  if (g.ff) return eval_far_ff(g, R, p, col, m, FT);
   // continuation: the two values the final rule combines, then one shared rule
   double a, b, prm = R.px[p];
   bool lowq = false;
@@ -185,13 +339,39 @@ __device__ __forceinline__ double eval_item64(const GridView &g, const Rec64 &R,
   return pair_rule(a, b, prm, LT, ET);
 }
 
-// Bernstein weights of a point's sites into its record slot.
-__device__ __forceinline__ void store_point(Rec64 &R, int slot, const PointSites<double> &ps, long long ob) {
+// Bernstein weights of a point's sites into its record slot (float-float
+// for continuation points when ff is set).
+__device__ __forceinline__ void store_point(Rec64 &R, int slot, const PointSites<double> &ps, long long ob,
+                                            int ff) {
   R.cls[slot] = ps.cls;
   R.xc0[slot] = ps.xc0; R.xc1[slot] = ps.xc1; R.qc0[slot] = ps.qc0; R.qc1[slot] = ps.qc1;
   R.ob[slot] = ob;
   R.px[slot] = ps.px; R.pq[slot] = ps.pq; R.lr[slot] = ps.lr;
   if (ps.cls == C_INVALID) return;
+  if (ff && ps.cls >= C_LOWX && ps.cls <= C_LOWX_LOWQ) {
+    auto put = [](double &slot_, double v) {
+      const ff2 f = ff_of(v);
+      reinterpret_cast<float2 &>(slot_) = make_float2(f.h, f.l);
+    };
+    put(R.px[slot], ps.px);
+    put(R.pq[slot], ps.pq);
+    put(R.lr[slot], ps.lr);
+    ff2 B[4];
+    float2 *W2 = reinterpret_cast<float2 *>(R.W[slot]);
+    ff_bernstein(ps.t0, ps.ts0, B);
+#pragma unroll
+    for (int k = 0; k < 4; k++) W2[k] = make_float2(B[k].h, B[k].l);
+    ff_bernstein(ps.t1, 1.0 - ps.t1, B);
+#pragma unroll
+    for (int k = 0; k < 4; k++) W2[4 + k] = make_float2(B[k].h, B[k].l);
+    ff_bernstein(ps.u0, ps.us0, B);
+#pragma unroll
+    for (int k = 0; k < 4; k++) W2[8 + k] = make_float2(B[k].h, B[k].l);
+    ff_bernstein(ps.u1, 1.0 - ps.u1, B);
+#pragma unroll
+    for (int k = 0; k < 4; k++) W2[12 + k] = make_float2(B[k].h, B[k].l);
+    return;
+  }
   if (ps.cls == C_INF) {
     ff2 bx[4], bq[4];
     ff_bernstein(ps.t0, ps.ts0, bx);
@@ -231,12 +411,12 @@ __device__ __forceinline__ void store_point(Rec64 &R, int slot, const PointSites
 template <bool RCP>
 __device__ __forceinline__ void items64(const GridView &g, const Rec64 &R, int np, int nc, int cbase,
                                         int m, long long mo, double *__restrict__ out, LogTabs LT,
-                                        const double *ET, int lane) {
+                                        const double *ET, FFTabs FT, int lane) {
   const int nitems = np * nc;
   int p = lane / nc, c = lane - (lane / nc) * nc;
   const int dp = 32 / nc, dc = 32 - dp * nc;
   for (int k = lane; k < nitems; k += 32) {
-    out[mo + R.ob[p] + c] = eval_item64<RCP>(g, R, p, cbase + c, m, LT, ET);
+    out[mo + R.ob[p] + c] = eval_item64<RCP>(g, R, p, cbase + c, m, LT, ET, FT);
     c += dc;
     p += dp;
     if (c >= nc) { c -= nc; p++; }
@@ -287,8 +467,10 @@ k_xf64(GridView g, const double *__restrict__ xa, const double *__restrict__ qa,
   off += sizeof(double2) * kLogTab;
   double *LTh = reinterpret_cast<double *>(smem + off);
   off += keys_bytes(kLogTab, 8);
-  double *ET = reinterpret_cast<double *>(smem + off);
-  off += sizeof(double) * kExpTab;
+  float4 *FTl = reinterpret_cast<float4 *>(smem + off);
+  off += sizeof(float4) * kFFLogTab;
+  float2 *FTe = reinterpret_cast<float2 *>(smem + off);
+  off += sizeof(float2) * kFFExpTab;
   Rec64 *recs = reinterpret_cast<Rec64 *>(smem + off);
   off += kWarps * sizeof(Rec64);
   Queue64 *queues = reinterpret_cast<Queue64 *>(smem + off);
@@ -299,7 +481,10 @@ k_xf64(GridView g, const double *__restrict__ xa, const double *__restrict__ qa,
   if (want_as) load_keys<double>(g, akeys, 2);
   for (int i = threadIdx.x; i < kLogTab; i += kThreads) { LTt[i] = g.tlogtab[i]; LTh[i] = g.tloghtab[i]; }
   const LogTabs LT{LTt, LTh};
-  for (int i = threadIdx.x; i < kExpTab; i += kThreads) ET[i] = g.texptab[i];
+  for (int i = threadIdx.x; i < kFFLogTab; i += kThreads) FTl[i] = g.fflog[i];
+  for (int i = threadIdx.x; i < kFFExpTab; i += kThreads) FTe[i] = g.ffexp[i];
+  const FFTabs FT{FTl, FTe};
+  const double *ET = g.texptab;  // the FP64 exponential (grids outside float-float range) reads it from L2
   __syncthreads();
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -312,23 +497,59 @@ k_xf64(GridView g, const double *__restrict__ xa, const double *__restrict__ qa,
   const int nchunks = MODE == MODE_MEMBERS ? (g.nmem + mchunk - 1) / mchunk : 1;
   const long long nunits = ntiles * nchunks;
   const long long nwarps = (long long)gridDim.x * kWarps;
-  int nq = 0;  // queued continuation points (warp-uniform)
+  int nq[kFar] = {};  // queued continuation points per class (warp-uniform)
 
-  // a full (or final partial) tile of queued points, entries [base, base + cnt)
-  auto drain = [&](int base, int cnt) {
+  // the point behind a queue entry: coordinates and output offset
+  auto point_of = [&](unsigned id, double &x, double &q2, long long &ob) {
+    if (MODE != MODE_MC) {
+      x = xa[id];
+      q2 = qa[id];
+      ob = (long long)id * nc;
+    } else {
+      const unsigned long long e = id >> 1;
+      double x1, x2;
+      if (gen.on) mc_event(gen, e, x1, x2);
+      else { x1 = xa[e]; x2 = xb[e]; }
+      q2 = x1 * x2 * s;
+      x = (id & 1) ? x2 : x1;
+      ob = (long long)e * (2 * g.nf + 1) + (long long)(id & 1) * g.nf;
+    }
+  };
+  // a tile of queued points of class C_LOWX + c: lane i takes entry from + i
+  auto drain = [&](int c, int from, int cnt) {
     const bool present = lane < cnt;
     double x = 0.0, q2 = 0.0, lq;
     long long ob = 0;
-    if (present) { x = Q.x[base + lane]; q2 = Q.q2[base + lane]; ob = Q.ob[base + lane]; }
+    if (present) {
+      point_of(Q.idx[c][from + lane], x, q2, ob);
+    }
     PointSites<double> ps;
     ps.cls = -1;
     if (present) ps = sites(g, xkeys, qkeys, x, q2, LT, lq);
     int slot = 0;
     const int np = sort_slots<C_LOWX, C_HIGHQ, C_LOWQ, C_LOWX_HIGHQ, C_LOWX_LOWQ>(ps.cls, lane, slot);
-    if (present) store_point(R, slot, ps, ob);
+    if (present) store_point(R, slot, ps, ob, g.ff);
     __syncwarp();
-    items64<MODE == MODE_MC>(g, R, np, nc, cbase, 0, 0, out, LT, ET, lane);
+    items64<MODE == MODE_MC>(g, R, np, nc, cbase, 0, 0, out, LT, ET, FT, lane);
     __syncwarp();
+  };
+
+  // full tiles of one class; with last, also the partial ones (one call site
+  // of the drain code)
+  auto drain_ready = [&](bool last) {
+    while (true) {
+      int c0 = -1, from = 0, cnt = 0;
+#pragma unroll
+      for (int c = 0; c < kFar; c++)
+        if (c0 < 0 && (nq[c] >= 32 || (last && nq[c] > 0))) {
+          c0 = c;
+          cnt = nq[c] < 32 ? nq[c] : 32;
+          nq[c] -= cnt;
+          from = nq[c];
+        }
+      if (c0 < 0) break;
+      drain(c0, from, cnt);
+    }
   };
 
   for (long long unit = (long long)blockIdx.x * kWarps + warp; unit < nunits; unit += nwarps) {
@@ -377,38 +598,35 @@ k_xf64(GridView g, const double *__restrict__ xa, const double *__restrict__ qa,
 
     int key = ps.cls, slot = 0, np;
     if (kQueue) {
-      const bool far = is_far(ps.cls);
-      const unsigned fm = __ballot_sync(kFull, far);
-      if (far) {
-        const int at = nq + __popc(fm & ((1u << lane) - 1u));
-        Q.x[at] = x;
-        Q.q2[at] = q2;
-        Q.ob[at] = ob;
-        key = -1;
+      const unsigned id = MODE == MODE_MC ? (unsigned)(2 * (e0 + (lane >> 1)) + (lane & 1)) : (unsigned)(e0 + lane);
+#pragma unroll
+      for (int c = 0; c < kFar; c++) {
+        const unsigned fm = __ballot_sync(kFull, ps.cls == C_LOWX + c);
+        if (ps.cls == C_LOWX + c) {
+          Q.idx[c][nq[c] + __popc(fm & ((1u << lane) - 1u))] = id;
+          key = -1;
+        }
+        nq[c] += __popc(fm);
       }
-      nq += __popc(fm);
       np = sort_slots<C_INF, C_IN, C_INVALID>(key, lane, slot);
     } else {
       np = sort_slots<C_INF, C_IN, C_LOWX, C_HIGHQ, C_LOWQ, C_LOWX_HIGHQ, C_LOWX_LOWQ, C_INVALID>(key, lane, slot);
     }
-    if (key >= 0) store_point(R, slot, ps, ob);
+    if (key >= 0) store_point(R, slot, ps, ob, g.ff);
     __syncwarp();
 
     // ---- phase 2: items ----
     if (MODE == MODE_MEMBERS) {
       const int m1 = min(g.nmem, (chunk + 1) * mchunk);
       for (int m = chunk * mchunk; m < m1; m++)
-        items64<MODE == MODE_MC>(g, R, np, nc, cbase, m, (long long)m * n * nc, out, LT, ET, lane);
+        items64<MODE == MODE_MC>(g, R, np, nc, cbase, m, (long long)m * n * nc, out, LT, ET, FT, lane);
     } else {
-      items64<MODE == MODE_MC>(g, R, np, nc, cbase, 0, 0, out, LT, ET, lane);
+      items64<MODE == MODE_MC>(g, R, np, nc, cbase, 0, 0, out, LT, ET, FT, lane);
     }
     __syncwarp();
-    if (kQueue && nq >= 32) {
-      nq -= 32;
-      drain(nq, 32);
-    }
+    if (kQueue) drain_ready(false);
   }
-  if (kQueue && nq > 0) drain(0, nq);
+  if (kQueue) drain_ready(true);
 }
 
 static int num_sms() {
@@ -425,7 +643,8 @@ static int num_sms() {
 template <int MODE>
 static size_t xf64_smem(const GridView &g) {
   return keys_bytes(g.nx, 8) + keys_bytes(g.nrows, 8) + keys_bytes(g.na, 8) + sizeof(double2) * kLogTab +
-         keys_bytes(kLogTab, 8) + sizeof(double) * kExpTab + kWarps * (sizeof(Rec64) + (MODE == MODE_MEMBERS ? 0 : sizeof(Queue64)));
+         keys_bytes(kLogTab, 8) + sizeof(float4) * kFFLogTab + sizeof(float2) * kFFExpTab +
+         kWarps * (sizeof(Rec64) + (MODE == MODE_MEMBERS ? 0 : sizeof(Queue64)));
 }
 
 template <int MODE>

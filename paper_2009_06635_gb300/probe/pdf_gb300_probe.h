@@ -25,11 +25,15 @@ extern "C" {
  * Synchronous; returns PDF_OK or a PDF_ERR_* code. */
 PDF_API int pdf_probe_fma_rate(int precision, int iters, double *flops_per_s);
 
-/* The evaluation kernels' own FP64 elementary functions, elementwise on n
- * DEVICE values, for testing them against the C library: fn 0: out = ln a
+/* The evaluation kernels' own elementary functions, elementwise on n DEVICE
+ * values, for testing them against the C library: fn 0: out = ln a
  * (table-driven, Tang's method; within 2 ulp or 2e-17 absolute); fn 1:
  * out = e^a (within 2 ulp); fn 2: out = a / b (reciprocal approximation and
- * Newton steps, within 2 ulp; b may be NULL otherwise).  The tables are the
+ * Newton steps, within 2 ulp); fn 3, 4, 5: the float-float logarithm,
+ * exponential and quotient of the continuation rules, on a (and b) rounded to
+ * float pairs (ln a within 2e-14 + 2e-14 |ln a| absolute for a in [2^-100, 2^100];
+ * e^a within (1 + |a|) 1e-14 relative for |a| < 64; a / b within 4e-14
+ * relative).  b may be NULL unless fn is 2 or 5.  The tables are the
  * grid's (a handle of the evaluation library, loaded in the same process).
  * Asynchronous on `stream`. */
 PDF_API int pdf_probe_math(const pdf_grid *grid, int fn, const double *a, const double *b, size_t n,

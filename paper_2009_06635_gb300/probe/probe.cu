@@ -9,6 +9,7 @@
 #include <cstdio>
 
 #include "pdf_gb300_probe.h"
+#include "ffmath.cuh"
 #include "pdf_internal.cuh"
 
 namespace {
@@ -69,11 +70,20 @@ static int probe(int iters, double *out) {
   return probe_launch("probe");
 }
 
-// The evaluation kernels' own elementary functions, elementwise (tang.cuh).
+// The evaluation kernels' own elementary functions, elementwise (tang.cuh,
+// ffmath.cuh; the float-float ones take their argument rounded to a float pair).
 __global__ void k_math(GridView g, int fn, const double *a, const double *b, long long n, double *out) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  out[i] = fn == 0 ? tlog(a[i], LogTabs{g.tlogtab, g.tloghtab}) : fn == 1 ? texp(a[i], g.texptab) : ddiv(a[i], b[i]);
+  const FFTabs FT{g.fflog, g.ffexp};
+  switch (fn) {
+    case 0: out[i] = tlog(a[i], LogTabs{g.tlogtab, g.tloghtab}); break;
+    case 1: out[i] = texp(a[i], g.texptab); break;
+    case 2: out[i] = ddiv(a[i], b[i]); break;
+    case 3: out[i] = ff_to_d(ff_log(ff_of(a[i]), FT)); break;
+    case 4: out[i] = ff_to_d(ff_exp(ff_of(a[i]), FT)); break;
+    default: out[i] = ff_to_d(ff_div(ff_of(a[i]), ff_of(b[i]))); break;
+  }
 }
 
 }  // namespace pdfgb
@@ -81,8 +91,9 @@ __global__ void k_math(GridView g, int fn, const double *a, const double *b, lon
 extern "C" int pdf_probe_math(const pdf_grid *grid, int fn, const double *a, const double *b, size_t n,
                               double *out, cudaStream_t stream) {
   using namespace pdfgb;
-  if (!grid || (n > 0 && (!a || !out || (fn == 2 && !b)))) return probe_error(PDF_ERR_NULL, "pdf_probe_math: NULL argument");
-  if (fn < 0 || fn > 2) return probe_error(PDF_ERR_ARG, "pdf_probe_math: fn must be 0, 1 or 2");
+  if (!grid || (n > 0 && (!a || !out || ((fn == 2 || fn == 5) && !b))))
+    return probe_error(PDF_ERR_NULL, "pdf_probe_math: NULL argument");
+  if (fn < 0 || fn > 5) return probe_error(PDF_ERR_ARG, "pdf_probe_math: fn must be 0 .. 5");
   if (n == 0) return PDF_OK;
   k_math<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(grid->v, fn, a, b, (long long)n, out);
   return probe_launch("pdf_probe_math");

@@ -1,7 +1,8 @@
 """The FP64 evaluation kernels' own elementary functions (tang.cuh: Tang's
-table-driven logarithm and exponential, and the Newton division) against the
-C library's, which round within one ulp: over the ranges the kernels use,
-and at the special values they must get right."""
+table-driven logarithm and exponential, and the Newton division; ffmath.cuh:
+their float-float counterparts used by the continuation rules) against the C
+library's, which round within one ulp: over the ranges the kernels use, and
+at the special values they must get right."""
 import ctypes
 
 import numpy as np
@@ -78,3 +79,43 @@ def test_division(grid):
     assert np.all(ulps(got, want) <= 2.0), ulps(got, want).max()
     special = run(grid, 2, np.array([1.0, 1.0, 1.0, 0.0]), np.array([0.0, 5e-324, np.inf, 2.0]))
     assert np.isinf(special[0]) and special[1] == 1.0 / 5e-324 and special[2] == 0.0 and special[3] == 0.0
+
+
+def test_float_float_log(grid):
+    """ln r of the continuation rules (r a quotient of site values, which the
+    rules keep in [2^-100, 2^100], where the low part of a float pair is a
+    normal float): absolute error within 2e-14 + 2e-14 |ln r| (the table's and
+    the series' float-float roundings, ~2^-47, and three float-float additions
+    of terms as large as |ln r|, each within ~2^-48 of its result)."""
+    r = np.random.default_rng(4)
+    a = np.concatenate([np.exp(r.uniform(-69, 69, 200_000)), r.uniform(0.3, 3.0, 200_000),
+                        1 + r.uniform(-1e-4, 1e-4, 100_000), [1.0, 2.0, 0.5, 1.0 + 2.0**-30, 1.0 - 2.0**-30]])
+    a = a.astype(np.float32).astype(np.float64) * (1 + r.uniform(-2.0**-30, 2.0**-30, a.size))  # use the low part
+    got = run(grid, 3, a)
+    want = np.log(a)
+    err = np.abs(got - want)
+    bound = 2e-14 + 2e-14 * np.abs(want)
+    assert np.all(err <= bound), (err / bound).max()
+
+
+def test_float_float_exp(grid):
+    """e^y for the exponents the rules send here (|y| < 64: the result's low
+    part stays a normal float): relative error within (1 + |y|) 1e-14."""
+    r = np.random.default_rng(5)
+    y = np.concatenate([r.uniform(-63.9, 63.9, 300_000), r.uniform(-1e-3, 1e-3, 100_000), [0.0, 1e-20, -1e-20, 50.0]])
+    got = run(grid, 4, y)
+    want = np.exp(y)
+    rel = np.abs(got - want) / want
+    bound = (1 + np.abs(y)) * 1e-14
+    assert np.all(rel <= bound), (rel / bound).max()
+    assert got[-4] == 1.0
+
+
+def test_float_float_division(grid):
+    r = np.random.default_rng(6)
+    a = r.normal(0, 1, 300_000) * 10.0 ** r.integers(-15, 15, 300_000)
+    b = r.normal(0, 1, 300_000) * 10.0 ** r.integers(-15, 15, 300_000)
+    got = run(grid, 5, a, b)
+    want = a / b
+    rel = np.abs(got - want) / np.abs(want)
+    assert np.all(rel <= 4e-14), rel.max()
