@@ -442,6 +442,26 @@ __device__ __forceinline__ int sort_slots(int key, int lane, int &slot) {
 
 }  // namespace
 
+// Parts of a batch one launch evaluates.  Large batches take two launches:
+// PART_NEAR (in-grid and invalid points, alpha_s and the invalid count of
+// every point; points that need a rule are skipped) and PART_FAR (only the
+// points that need a rule: a range test on the bit patterns finds them, they
+// wait in the per-class queues and run class-pure tiles).  Each kernel keeps
+// a small loop: in one kernel the continuation code evicted the in-grid loop
+// from the instruction cache (19% of stalls) and raised its register need.
+enum { PART_ALL = 0, PART_NEAR = 1, PART_FAR = 2 };
+
+// Class of a point that needs a continuation rule (C_LOWX..C_LOWX_LOWQ), or
+// -1: the range tests of sites() on the raw bit patterns, nothing else.
+__device__ __forceinline__ int far_class(const GridView &g, double x, double q2) {
+  const long long kx = __double_as_longlong(x), kq = __double_as_longlong(q2);
+  if (!(kq > 0 && kq < 0x7FF0000000000000LL && kx > 0 && kx <= __double_as_longlong(g.xlast))) return -1;
+  const bool lowx = kx < __double_as_longlong(g.x0);
+  const bool lowq = kq < __double_as_longlong(g.q2min), highq = kq > __double_as_longlong(g.q2max);
+  if (!(lowx || lowq || highq)) return -1;
+  return lowx ? (highq ? C_LOWX_HIGHQ : lowq ? C_LOWX_LOWQ : C_LOWX) : (highq ? C_HIGHQ : C_LOWQ);
+}
+
 // MODE_POINTS:  points xa[n], qa[n]; out[n][ncol] for columns col0..col0+ncol-1;
 //               as_out[n] (alpha_s) when not null.
 // MODE_MC:      events xa[n] (x1), xb[n] (x2), Q^2 = x1 x2 s; out[n][2 nf + 1]
@@ -449,12 +469,12 @@ __device__ __forceinline__ int sort_slots(int key, int lane, int &slot) {
 //               are generated (mc.cuh) and xa, xb are not read.
 // MODE_MEMBERS: points xa[n], qa[n]; out[nmem][n][nf].  A warp's unit is
 //               (tile, chunk of mchunk members); phase 1 repeats per chunk.
-template <int MODE>
+template <int MODE, int PART>
 __global__ void __launch_bounds__(kThreads, 3)
 k_xf64(GridView g, const double *__restrict__ xa, const double *__restrict__ qa, const double *__restrict__ xb,
        double s, long long n, int col0, int ncol, int mchunk, double *__restrict__ out,
        double *__restrict__ as_out, McGen gen) {
-  constexpr bool kQueue = MODE != MODE_MEMBERS;
+  constexpr bool kQueue = MODE != MODE_MEMBERS && PART != PART_NEAR;
   extern __shared__ __align__(16) unsigned char smem[];
   size_t off = 0;
   long long *xkeys = reinterpret_cast<long long *>(smem + off);
@@ -475,7 +495,7 @@ k_xf64(GridView g, const double *__restrict__ xa, const double *__restrict__ qa,
   off += kWarps * sizeof(Rec64);
   Queue64 *queues = reinterpret_cast<Queue64 *>(smem + off);
 
-  const bool want_as = MODE == MODE_MC || (MODE == MODE_POINTS && as_out != nullptr);
+  const bool want_as = PART != PART_FAR && (MODE == MODE_MC || (MODE == MODE_POINTS && as_out != nullptr));
   load_keys<double>(g, xkeys, 0);
   load_keys<double>(g, qkeys, 1);
   if (want_as) load_keys<double>(g, akeys, 2);
@@ -578,6 +598,19 @@ k_xf64(GridView g, const double *__restrict__ xa, const double *__restrict__ qa,
       }
       ob = (e0 + e) * (long long)(2 * g.nf + 1) + (lane & 1) * g.nf;
     }
+    if constexpr (PART == PART_FAR) {  // queue the points that need a rule, nothing else
+      const int fc = present ? far_class(g, x, q2) : -1;
+      const unsigned id = MODE == MODE_MC ? (unsigned)(2 * (e0 + (lane >> 1)) + (lane & 1)) : (unsigned)(e0 + lane);
+#pragma unroll
+      for (int c = 0; c < kFar; c++) {
+        const unsigned fm = __ballot_sync(kFull, fc == C_LOWX + c);
+        if (fc == C_LOWX + c) Q.idx[c][nq[c] + __popc(fm & ((1u << lane) - 1u))] = id;
+        nq[c] += __popc(fm);
+      }
+      __syncwarp();
+      drain_ready(false);
+      continue;
+    }
     PointSites<double> ps;
     ps.cls = -1;
     if (present) ps = sites(g, xkeys, qkeys, x, q2, LT, lq);
@@ -597,7 +630,10 @@ k_xf64(GridView g, const double *__restrict__ xa, const double *__restrict__ qa,
     }
 
     int key = ps.cls, slot = 0, np;
-    if (kQueue) {
+    if (PART == PART_NEAR) {  // points that need a rule are the far launch's
+      if (is_far(ps.cls)) key = -1;
+      np = sort_slots<C_INF, C_IN, C_INVALID>(key, lane, slot);
+    } else if (kQueue) {
       const unsigned id = MODE == MODE_MC ? (unsigned)(2 * (e0 + (lane >> 1)) + (lane & 1)) : (unsigned)(e0 + lane);
 #pragma unroll
       for (int c = 0; c < kFar; c++) {
@@ -640,20 +676,30 @@ static int num_sms() {
   return sms;
 }
 
-template <int MODE>
+template <int MODE, int PART = PART_ALL>
 static size_t xf64_smem(const GridView &g) {
   return keys_bytes(g.nx, 8) + keys_bytes(g.nrows, 8) + keys_bytes(g.na, 8) + sizeof(double2) * kLogTab +
          keys_bytes(kLogTab, 8) + sizeof(float4) * kFFLogTab + sizeof(float2) * kFFExpTab +
-         kWarps * (sizeof(Rec64) + (MODE == MODE_MEMBERS ? 0 : sizeof(Queue64)));
+         kWarps * (sizeof(Rec64) + (MODE == MODE_MEMBERS || PART == PART_NEAR ? 0 : sizeof(Queue64)));
 }
 
-template <int MODE>
+// Batches of at least this many points take the two launches (near, far).
+constexpr long long kSplitMin = 1LL << 16;
+
+template <int MODE, int PART = PART_ALL>
 static int launch_mode(const pdf_grid *grid, const double *xa, const double *qa, const double *xb, double s,
                        long long n, int col0, int ncol, double *out, double *as_out, const McGen &gen,
                        cudaStream_t st) {
+  if constexpr (MODE != MODE_MEMBERS && PART == PART_ALL) {
+    if (n >= kSplitMin) {
+      const int rc = launch_mode<MODE, PART_NEAR>(grid, xa, qa, xb, s, n, col0, ncol, out, as_out, gen, st);
+      if (rc) return rc;
+      return launch_mode<MODE, PART_FAR>(grid, xa, qa, xb, s, n, col0, ncol, out, as_out, gen, st);
+    }
+  }
   const GridView &g = grid->v;
-  const size_t smem = xf64_smem<MODE>(g);
-  auto kern = k_xf64<MODE>;
+  const size_t smem = xf64_smem<MODE, PART>(g);
+  auto kern = k_xf64<MODE, PART>;
   static LaunchCache cache;
   const int per_sm = cache.blocks_per_sm(kern, kThreads, smem);
   const int per_tile = MODE == MODE_MC ? 16 : 32;

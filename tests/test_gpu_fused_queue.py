@@ -116,3 +116,36 @@ def test_all_points_continued(full):
         assert_parity(mc[:, side * nf:(side + 1) * nf], v, s, fl, RTOL_FP64, f"mc side {side}")
     a, sa = og.alphas(qq)
     assert_parity(mc[:, 2 * nf], a, sa, np.zeros(a.shape, bool), RTOL_FP64, "mc alphas")
+
+
+def test_two_launches_match_one_launch_bit_for_bit(full, synth):
+    """Batches of 65536 points or more run as two launches (in-grid and
+    invalid points; then the points that need a rule, in class-pure tiles);
+    smaller ones as one.  Every point is computed by the same arithmetic from
+    its own coordinates, so a large batch must equal its pieces run alone:
+    flavours, alpha_s, the invalid count, and the Monte Carlo layout."""
+    g, G, og = full
+    n = 300_007
+    x, q2 = interleaved(g, n, 77)
+    sx, sq = special_points(g)
+    at = np.random.default_rng(78).choice(n, len(sx), replace=False)
+    x[at], q2[at] = sx, sq
+    xd, qd = dev(x), dev(q2)
+    G.reset_invalid_count()
+    out, al = P.xfxq2_all_flavours_alphas(G, xd, qd)
+    torch.cuda.synchronize()
+    ninv = G.invalid_count()
+    G.reset_invalid_count()
+    parts = [P.xfxq2_all_flavours_alphas(G, xd[a:a + 40_000], qd[a:a + 40_000]) for a in range(0, n, 40_000)]
+    torch.cuda.synchronize()
+    assert G.invalid_count() == ninv > 0
+    assert np.array_equal(host(out), np.concatenate([host(p[0]) for p in parts]), equal_nan=True)
+    assert np.array_equal(host(al), np.concatenate([host(p[1]) for p in parts]), equal_nan=True)
+    r = np.random.default_rng(79)
+    x1 = np.exp(r.uniform(np.log(1e-10), 0.0, 150_001))
+    x2 = np.exp(r.uniform(np.log(1e-10), 0.0, 150_001))
+    s2 = 13000.0**2
+    mc = host(P.pdf_mc_event(G, dev(x1), dev(x2), s2))
+    mcp = np.concatenate([host(P.pdf_mc_event(G, dev(x1[a:a + 30_000]), dev(x2[a:a + 30_000]), s2))
+                          for a in range(0, len(x1), 30_000)])
+    assert np.array_equal(mc, mcp, equal_nan=True)
