@@ -91,7 +91,7 @@ def algorithmic_flops(counts, nflav):
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for name in ("xf64.cu", "ff.cuh", "tang.cuh", "sites.cuh", "pdf_internal.cuh", "grid.cu"):
+    for name in ("xf64.cu", "ff.cuh", "ffmath.cuh", "tang.cuh", "sites.cuh", "pdf_internal.cuh", "grid.cu"):
         h.update((ROOT / "paper_2009_06635_gb300" / "csrc" / name).read_bytes())
     return h.hexdigest()[:16]
 
@@ -109,6 +109,34 @@ def profiled_traffic(kernel, n_points):
     if not rec or rec.get("source_hash") != kernel_source_hash():
         return None
     return rec["dram_bytes_per_point"] * n_points
+
+
+def profiled_pipes(kernel):
+    """Per-point busy time of each SM unit for `kernel` (all its launches of
+    one call), from the committed ncu capture (profiles/pipes.json), or None
+    if the source changed since."""
+    f = ROOT / "profiles" / "pipes.json"
+    if not f.exists():
+        return None
+    try:
+        rec = json.loads(f.read_text()).get(kernel)
+    except Exception:
+        return None
+    if not rec or rec.get("source_hash") != kernel_source_hash():
+        return None
+    return rec
+
+
+def unit_bound(pipes, n, sm_mhz, alg_bytes, hbm_gbs):
+    """Seconds each unit needs for n points at its full rate: the capture's
+    busy time per point of every SM unit (its utilisation times the launch
+    duration, summed over the call's launches), scaled from the capture's SM
+    clock to this run's; HBM from the algorithmic bytes over the measured copy
+    bandwidth.  Returns {unit: seconds}."""
+    scale = pipes["sm_mhz"] / sm_mhz
+    t = {u: s * n * scale for u, s in pipes["per_point_busy_s"].items()}
+    t["hbm"] = alg_bytes / (hbm_gbs * 1e9)
+    return t
 
 
 class Clocks:
@@ -152,6 +180,95 @@ class Clocks:
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(rows),
                 "power_w_max": max((float(r[3]) for r in rows if r[3].replace(".", "").isdigit()), default=None)}
+
+
+def _cpulist(text):
+    cpus = set()
+    for part in text.strip().split(","):
+        if part:
+            a, _, b = part.partition("-")
+            cpus.update(range(int(a), int(b or a) + 1))
+    return cpus
+
+
+class near_gpu:
+    """Within the block the process runs on the CPUs of the GPU's NUMA node
+    (read from sysfs), so pages first touched there are that node's memory;
+    the previous affinity comes back on exit.  Records what it found."""
+
+    def __init__(self, local):
+        self.local = local
+        self.info = {"gpu_pci": None, "gpu_numa_node": None, "cpus_used": None}
+        self.saved = None
+
+    def __enter__(self):
+        import torch
+
+        try:
+            pr = torch.cuda.get_device_properties(self.local)
+            bdf = f"{pr.pci_domain_id:04x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0"
+            self.info["gpu_pci"] = bdf
+            node = int(Path(f"/sys/bus/pci/devices/{bdf}/numa_node").read_text())
+            self.info["gpu_numa_node"] = node
+            if node >= 0 and hasattr(os, "sched_setaffinity"):
+                cpus = _cpulist(Path(f"/sys/devices/system/node/node{node}/cpulist").read_text())
+                self.saved = os.sched_getaffinity(0)
+                use = self.saved & cpus
+                if use:
+                    os.sched_setaffinity(0, use)
+                    self.info["cpus_used"] = len(use)
+                else:
+                    self.saved = None
+        except Exception as e:  # no sysfs entry, no permission: run where we are
+            self.info["note"] = f"placement not applied: {type(e).__name__}"
+        return self.info
+
+    def __exit__(self, *exc):
+        if self.saved is not None:
+            os.sched_setaffinity(0, self.saved)
+        return False
+
+
+def buffer_nodes(tensor):
+    """NUMA nodes holding a host tensor's pages ({node: pages}), from /proc/self/numa_maps."""
+    addr = tensor.data_ptr()
+    try:
+        best = None
+        for line in Path("/proc/self/numa_maps").read_text().splitlines():
+            f = line.split()
+            start = int(f[0], 16)
+            if start <= addr and (best is None or start > best[0]):
+                best = (start, f)
+        if best is None:
+            return None
+        return {k[1:].split("=")[0]: int(k.split("=")[1]) for k in best[1] if k.startswith("N") and "=" in k}
+    except Exception:
+        return None
+
+
+def link_rates(dev, hbuf_out, hbuf_in, sync, reps=5):
+    """Host-link rates (GB/s) on the given pinned buffers: device to host into
+    hbuf_out, host to device from hbuf_in; best of `reps` timed copies each
+    after a warm copy, CUDA events on the current stream."""
+    import torch
+
+    res = {}
+    for name, dst, src in (("d2h_gbs", hbuf_out, torch.empty_like(hbuf_out, device=dev)),
+                           ("h2d_gbs", torch.empty_like(hbuf_in, device=dev), hbuf_in)):
+        dst.copy_(src, non_blocking=True)
+        sync()
+        best = None
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            dst.copy_(src, non_blocking=True)
+            b.record()
+            sync()
+            ms = a.elapsed_time(b)
+            best = ms if best is None else min(best, ms)
+        res[name] = src.numel() * src.element_size() / (best * 1e-3) / 1e9
+        del dst, src
+    return res
 
 
 def dist_setup():
@@ -478,7 +595,10 @@ def our_arm(args):
     g = S.grid_full()
     G = P.pdf_load_grid(g)
     n = args.points
-    x, q2 = S.queries_full(n, 3 + 1000 * rank)
+    if args.law == "bench":
+        x, q2 = S.queries_full(n, 3 + 1000 * rank)
+    else:  # one class of point (profiling runs of --only)
+        x, q2 = S.queries_class(g, args.law, n, 3 + 1000 * rank)
     counts = classify(g, x, q2)
     nf = g.nflav
     xd = torch.from_numpy(x).to(dev)
@@ -598,11 +718,16 @@ def our_arm(args):
     surrogate_asinh = None if args.no_surrogate else surrogate_leg(args, G, g, dev, world, sync, rank, nf,
                                                                    ms64 / (n * (nf + 1)), target="asinh")
 
-    # end to end through the C ABI with host buffers (pinned), copies timed
-    hx = torch.from_numpy(x).pin_memory()
-    hq = torch.from_numpy(q2).pin_memory()
-    hout = torch.empty((n, nf), dtype=torch.float64).pin_memory()
-    hal = torch.empty((n,), dtype=torch.float64).pin_memory()
+    # end to end through the C ABI with host buffers (pinned), copies timed;
+    # the buffers are first touched on the GPU's own NUMA node
+    with near_gpu(local) as numa:
+        hx = torch.from_numpy(x).pin_memory()
+        hq = torch.from_numpy(q2).pin_memory()
+        hout = torch.empty((n, nf), dtype=torch.float64).pin_memory()
+        hal = torch.empty((n,), dtype=torch.float64).pin_memory()
+        hout.fill_(0.0)
+        hal.fill_(0.0)
+    numa["buffer_nodes"] = {k: buffer_nodes(v) for k, v in (("x", hx), ("q2", hq), ("out", hout), ("alphas", hal))}
     e2e_steps = max(3, min(args.steps, 10))
     for _ in range(2):
         P.xfxq2_all_flavours_host(G, hx, hq, out=hout, alphas_out=hal)
@@ -611,31 +736,53 @@ def our_arm(args):
     for _ in range(e2e_steps):
         P.xfxq2_all_flavours_host(G, hx, hq, out=hout, alphas_out=hal)
     e2e_s = max_over_ranks(world, (time.perf_counter() - t0) / e2e_steps)
-    # the host link's device-to-host rate on the step's output (the e2e bound)
-    dsrc = torch.empty((n, nf), dtype=torch.float64, device=dev)
-    hout.copy_(dsrc, non_blocking=True)
-    sync()
-    la, lb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    la.record()
-    hout.copy_(dsrc, non_blocking=True)
-    lb.record()
-    sync()
-    link_d2h = 8 * n * nf / (la.elapsed_time(lb) * 1e-3) / 1e9
-    del dsrc
-    e2e_bound_s = 8 * n * (nf + 1) / (link_d2h * 1e9)
+    # the host link on the step's own buffers: best of 5 timed copies each way
+    # (after a warm copy), device to host into the output buffer, host to device
+    # from the input buffer
+    link = link_rates(dev, hout, hx, sync)
+    e2e_bound_s = max(8 * n * (nf + 1) / (link["d2h_gbs"] * 1e9), 16 * n / (link["h2d_gbs"] * 1e9))
 
     # ceilings measured on this GPU
     fp64_meas = ctypes.c_double(0.0)
     fp32_meas = ctypes.c_double(0.0)
-    _native.check(lib.pdf_probe_fma_rate(64, 4096, ctypes.byref(fp64_meas)), "probe fp64")
-    _native.check(lib.pdf_probe_fma_rate(32, 65536, ctypes.byref(fp32_meas)), "probe fp32")
+    probe = _native.load_probe()
+    _native.check_probe(probe.pdf_probe_fma_rate(64, 4096, ctypes.byref(fp64_meas)), "probe fp64")
+    _native.check_probe(probe.pdf_probe_fma_rate(32, 65536, ctypes.byref(fp32_meas)), "probe fp32")
     peaks = json.loads((ROOT / "MEASURED_PEAKS.json").read_text()) if (ROOT / "MEASURED_PEAKS.json").exists() else {}
     hbm = peaks.get("hbm_gbs", 6800.0)
 
     flops = algorithmic_flops(counts, nf)
     achieved = flops / (kern_ms * 1e-3)
-    traffic = profiled_traffic("k_xf64<points>", n)
+    traffic = profiled_traffic("k_xf64<points> near + far", n)
     bytes32 = n * (8 + 4 * nf)
+    alg_bytes = n * (16 + 8 * nf + 8)
+    sm_mhz = (clk or {}).get("sm_mhz") or SM_MHZ
+    pipes = profiled_pipes("k_xf64<points> near + far")
+    if pipes:
+        # the kernel's own ceiling: the unit it keeps busiest, at its full rate
+        ut = unit_bound(pipes, n, sm_mhz, alg_bytes, hbm)
+        binding = max(ut, key=ut.get)
+        t_bound = ut[binding]
+        roofline = {
+            "bound": "hbm" if binding == "hbm" else "alu", "binding_unit": binding,
+            "kernel": "xfxq2_all_flavours_alphas FP64 (k_xf64<points> near + far launches, all flavours + alpha_s)",
+            "achieved": achieved / 1e12, "peak": flops / t_bound / 1e12, "unit": "TFLOP/s",
+            "frac": t_bound / (kern_ms * 1e-3), "traffic": traffic,
+            "peak_source": ("per-unit model: each SM unit's busy time per point (ncu utilisation x launch "
+                            "duration, both launches of a call, profiles/pipes.json) x points, at the sampled SM "
+                            "clock; the peak is the algorithmic flop rate at which the busiest unit is saturated"),
+            "unit_ms": {k: v * 1e3 for k, v in ut.items()}, "sm_mhz_used": sm_mhz,
+            "kernel_ms": kern_ms, "algorithmic_flops_per_launch": flops,
+            "fp64_dfma_peak_tflops": FP64_PEAK / 1e12,
+            "fp64_dfma_frac_of_algorithmic_flops": achieved / FP64_PEAK,
+            "hbm_frac": alg_bytes / (kern_ms * 1e-3) / (hbm * 1e9)}
+    else:  # no capture of this source: the algorithmic bytes against HBM
+        roofline = {
+            "bound": "hbm", "kernel": "xfxq2_all_flavours_alphas FP64 (k_xf64<points>, all flavours + alpha_s)",
+            "achieved": alg_bytes / (kern_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+            "frac": alg_bytes / (kern_ms * 1e-3) / (hbm * 1e9), "traffic": traffic,
+            "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json); no per-unit capture of this source",
+            "kernel_ms": kern_ms, "algorithmic_flops_per_launch": flops}
     line = {
         "metric": METRIC,
         "value": value,
@@ -647,25 +794,20 @@ def our_arm(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64",
+        "dtype": "f64 (float-float in-grid contraction, FP64 logarithms, exponentials and rules)",
         "data": "synthetic: seeded LHAPDF-shaped grid and log-uniform queries (no real PDF set in the container)",
         "config": {"workload": WORKLOAD, "points_per_rank": n, "evals_per_step_per_rank": evals_step,
                    "class_counts": counts, "l2": "inputs + outputs 1.3 GB per step > 129 MB L2, no flush",
                    "parallelism": f"{world} independent replicas (weak scaling, no collective)"},
-        "roofline": {"bound": "alu", "kernel": "xfxq2_all_flavours_alphas FP64 (k_xf64<points>, all flavours + alpha_s)",
-                     "achieved": achieved / 1e12, "peak": FP64_PEAK / 1e12, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK, "traffic": traffic,
-                     "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
-                     "peak_measured_dfma": fp64_meas.value / 1e12,
-                     "kernel_ms": kern_ms, "algorithmic_flops_per_launch": flops,
-                     "hbm_frac": n * (16 + 8 * nf) / (kern_ms * 1e-3) / (hbm * 1e9)},
-        "gpu_launches": args.steps,  # one k_xf64 launch per step (all flavours + alpha_s fused)
+        "roofline": dict(roofline, peak_measured_dfma_tflops=fp64_meas.value / 1e12),
+        "gpu_launches": 2 * args.steps,  # per step: the near and the far k_xf64 launch (all flavours + alpha_s)
         "clocks": clk,
         "e2e": {"value": world * evals_step / e2e_s, "unit": "evals/s", "h2d_bytes_per_step": 16 * n,
                 "d2h_bytes_per_step": 8 * n * (nf + 1), "ms_per_step": e2e_s * 1e3,
                 "call": "xfxq2_all_flavours_host (pinned host buffers, alpha_s included)",
-                "host_link_d2h_gbs": link_d2h, "link_bound_ms": e2e_bound_s * 1e3,
-                "frac_of_link_bound": e2e_bound_s / e2e_s},
+                "host_link_d2h_gbs": link["d2h_gbs"], "host_link_h2d_gbs": link["h2d_gbs"],
+                "link_probe": "best of 5 timed copies each way on the step's own pinned buffers, after a warm copy",
+                "link_bound_ms": e2e_bound_s * 1e3, "frac_of_link_bound": e2e_bound_s / e2e_s, "numa": numa},
         "paths": {
             "fp32": {"value": world * evals_step / (ms32 * 1e-3), "ms_per_step": ms32, "kernel_ms": k32,
                      "roofline": {"bound": "hbm", "achieved": bytes32 / (k32 * 1e-3) / 1e9, "peak": hbm,
@@ -715,6 +857,9 @@ def main():
     ap.add_argument("--no-members", action="store_true")
     ap.add_argument("--only", choices=["fp64", "fp32", "surrogate", "adjoint"], default=None,
                     help="run only that path's step (a small case for profiling); prints its timing")
+    ap.add_argument("--law", default="bench", choices=["bench", "in", "lowx", "highq", "lowq", "lowx_highq",
+                                                       "lowx_lowq"],
+                    help="with --only fp64/fp32: the benchmark's query law, or points of one class only")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

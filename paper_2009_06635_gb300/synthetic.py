@@ -191,6 +191,32 @@ def queries_full(n: int = 10_000_000, seed: int = 3):
     return np.exp(lx), np.exp(2.0 * lqq)
 
 
+QUERY_CLASSES = ("in", "lowx", "highq", "lowq", "lowx_highq", "lowx_lowq")
+
+
+def queries_class(grid: Grid, cls: str, n: int, seed: int = 3):
+    """n queries of one class of point (for profiling one class at a time):
+    drawn from the queries_full law widened to Q in [0.1, 2e5] GeV, keeping
+    those whose x lies below, inside or above the grid's x range and Q^2
+    below, inside or above its Q^2 range as `cls` names ("in", "lowx",
+    "highq", "lowq", "lowx_highq", "lowx_lowq")."""
+    want_lowx = cls.startswith("lowx")
+    want_q = "highq" if cls.endswith("highq") else "lowq" if cls.endswith("lowq") else "in"
+    r = _rng(seed)
+    xs, qs, have = [], [], 0
+    while have < n:
+        m = max(4 * (n - have), 1024)
+        x = np.exp(r.uniform(np.log(1e-10), 0.0, m))
+        q2 = np.exp(2.0 * r.uniform(np.log(0.1), np.log(2e5), m))
+        lowx = x < grid.x_knots[0]
+        qcls = np.where(q2 > grid.q2_knots[-1], "highq", np.where(q2 < grid.q2_knots[0], "lowq", "in"))
+        keep = (lowx == want_lowx) & (qcls == want_q)
+        xs.append(x[keep])
+        qs.append(q2[keep])
+        have += int(keep.sum())
+    return np.concatenate(xs)[:n], np.concatenate(qs)[:n]
+
+
 SQRT_S = 13000.0  # GeV
 
 
