@@ -18,7 +18,17 @@
  *                      least c_f), ln E_f linear in ln x between x knots and
  *                      tabulated at 1025 equal steps of ln x over the grid
  *                      (the network then learns an O(1) function, smooth
- *                      through the zeros of xf_f).
+ *                      through the zeros of xf_f);
+ *   PDF_SURR_RESIDUAL  xf_f = B_f + 2^-10 E_f(x) y_f, trained on
+ *                      (xf_f - B_f) / (2^-10 E_f(x)) clipped to [-32, 32]
+ *                      (where the base misses by more than 3% of E_f the
+ *                      cell fails the error map anyway): the network corrects a
+ *                      base B_f, bilinear in the scaled coordinates on a
+ *                      uniform 257 x 257 table of the FP64 interpolator (FP32,
+ *                      built when the surrogate is made), whose own error is
+ *                      ~1e-3 of E_f; the network's BF16 error then acts on a
+ *                      term of that size.  Evaluation writes B_f, then adds
+ *                      the network's term.
  * Products run on the BF16 tensor cores (tcgen05) with FP32 accumulation;
  * BF16 weight copies are made from FP32 master weights.
  * The parameter vector is flat FP32: W1 [128][32], b1 [128], W2..W4
@@ -52,6 +62,7 @@ typedef struct {
 
 #define PDF_SURR_ASINH 0
 #define PDF_SURR_ENVELOPE 1
+#define PDF_SURR_RESIDUAL 2
 
 /* Make a surrogate for `grid` from HOST parameters (flat FP32, see above)
  * and HOST frequencies freq[16][2]; scratch for batches of up to max_batch
@@ -73,6 +84,19 @@ PDF_API int pdf_surrogate_set_params(pdf_surrogate *s, const float *params);
  * nparams FP32) its gradient.  Synchronous. */
 PDF_API int pdf_surrogate_loss_grad(pdf_surrogate *s, const double *x, const double *q2, const double *xf,
                                     size_t n, double *loss, float *grad);
+
+/* The intermediate values of the last pdf_surrogate_loss_grad pass, for
+ * checking each stage of the GPU computation on its own inputs: out (HOST,
+ * FP32) receives [n][cols] of
+ *   what 0: the bfloat16 activations h_layer (layer 0: the 32 features; 1..4
+ *           the SiLU outputs, 128 columns), as stored;
+ *   what 1: the FP32 pre-activations z_layer of the SiLU layers (0..3, 128);
+ *   what 2: the bfloat16 backward signals of layer `layer` (0..3: 128
+ *           columns, dL/dz; 4: the 16 padded output columns, dL/dy);
+ *   what 3: the FP32 outputs y (layer 0; 16 padded columns);
+ *   what 4: the FP32 targets (layer 0; 16 padded columns).
+ * PDF_ERR_ARG before any such pass or for another (what, layer).  Synchronous. */
+PDF_API int pdf_surrogate_trace(pdf_surrogate *s, int what, int layer, float *out);
 
 /* Train on the n points (x, q2), targets from the FP64 interpolator of
  * `grid`, batches taken in order.  *final_loss (HOST, may be NULL) is the

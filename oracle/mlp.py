@@ -14,7 +14,11 @@ all flavours:
   xf_f = c_f sinh(y_f)     (inverse of the training target y_f = asinh(xf_f / c_f)),
   or, with the envelope target, xf_f = E_f(x) y_f (target xf_f / E_f(x)), where
   E_f(x_i) = max over the Q knots of |xf_f(x_i, Q)| (at least c_f) and ln E_f is
-  linear in ln x between knots, tabulated at ENV_N + 1 equal steps of ln x.
+  linear in ln x between knots, tabulated at ENV_N + 1 equal steps of ln x;
+  or, with the residual target, xf_f = B_f(z) + RES_EPS E_f(x) y_f (target
+  (xf_f - B_f) / (RES_EPS E_f) clipped to [-RES_CLIP, RES_CLIP]), B_f bilinear
+  in (z0, z1) between the nodes of a uniform (BASE_N + 1)^2 table of the
+  interpolator's values rounded to float.
 silu(v) = v sigmoid(v) = v (1 + tanh(v/2)) / 2.
 Training loss: mean over batch and flavours of (y - target)^2.
 
@@ -29,6 +33,9 @@ import numpy as np
 WIDTH = 128
 NFEAT = 16  # frequencies; features = 2 * NFEAT
 ENV_N = 1024  # envelope table intervals
+BASE_N = 256  # base table intervals per axis (residual target)
+RES_EPS = 2.0**-10  # residual target scale
+RES_CLIP = 32.0  # residual targets clipped to [-RES_CLIP, RES_CLIP]
 
 
 def bf16(a):
@@ -89,7 +96,9 @@ def forward(params, x, q2, freq, bounds, nflav, bf=False):
     return y, cache
 
 
-def target(xf, scale, env=None):
+def target(xf, scale, env=None, base_vals=None):
+    if base_vals is not None:
+        return np.clip((np.asarray(xf) - base_vals) / (RES_EPS * env), -RES_CLIP, RES_CLIP)
     return np.asarray(xf) / env if env is not None else np.arcsinh(np.asarray(xf) / scale)
 
 
@@ -113,13 +122,14 @@ def envelope(table, x, bounds):
     return np.exp(a + (u - k) * (b - a)).T
 
 
-def loss_grad(params, x, q2, xf, scale, freq, bounds, nflav, bf=False, env=None):
-    """Mean-square loss on the targets (asinh, or xf / E with env = E [n][nflav])
-    and its gradient (flat, FP64)."""
+def loss_grad(params, x, q2, xf, scale, freq, bounds, nflav, bf=False, env=None, base_vals=None):
+    """Mean-square loss on the targets (asinh; xf / E with env = E [n][nflav];
+    or (xf - B) / (RES_EPS E) with base_vals = B as well) and its gradient
+    (flat, FP64)."""
     layers = unpack(params, nflav)
     r = bf16 if bf else (lambda t: t)
     y, c = forward(params, x, q2, freq, bounds, nflav, bf)
-    t = target(xf, scale, env)
+    t = target(xf, scale, env, base_vals)
     n = y.shape[0]
     diff = y - t
     loss = float(np.mean(diff * diff))
@@ -136,6 +146,38 @@ def loss_grad(params, x, q2, xf, scale, freq, bounds, nflav, bf=False, env=None)
     return loss, flat
 
 
-def predict(params, x, q2, scale, freq, bounds, nflav, bf=False, env=None):
+def predict(params, x, q2, scale, freq, bounds, nflav, bf=False, env=None, base_vals=None):
     y, _ = forward(params, x, q2, freq, bounds, nflav, bf)
+    if base_vals is not None:
+        return base_vals + RES_EPS * env * y
     return env * y if env is not None else scale * np.sinh(y)
+
+
+def base_nodes(bounds):
+    """(x, Q^2) of the base table's nodes, [BASE_N + 1][BASE_N + 1] (z0 outer)."""
+    i = np.arange(BASE_N + 1)
+    lx = bounds[0] + (bounds[1] - bounds[0]) * i / BASE_N
+    lq = bounds[2] + (bounds[3] - bounds[2]) * i / BASE_N
+    X, Q = np.meshgrid(np.exp(lx), np.exp(lq), indexing="ij")
+    return X, Q
+
+
+def base_table(values_at_nodes):
+    """The table from the interpolator's values at base_nodes ([nodes][nflav]
+    FP64): rounded to float, [BASE_N + 1][BASE_N + 1][nflav]."""
+    v = np.asarray(values_at_nodes, dtype=np.float64).astype(np.float32).astype(np.float64)
+    return v.reshape(BASE_N + 1, BASE_N + 1, -1)
+
+
+def base(table, x, q2, bounds):
+    """B_f for every point: bilinear between the table's nodes in (z0, z1), [n][nflav]."""
+    z0 = 2.0 * (np.log(x) - bounds[0]) / (bounds[1] - bounds[0]) - 1.0
+    z1 = 2.0 * (np.log(q2) - bounds[2]) / (bounds[3] - bounds[2]) - 1.0
+    u0 = np.clip((z0 + 1.0) * 0.5 * BASE_N, 0.0, BASE_N)
+    u1 = np.clip((z1 + 1.0) * 0.5 * BASE_N, 0.0, BASE_N)
+    i = np.minimum(np.floor(u0).astype(int), BASE_N - 1)
+    j = np.minimum(np.floor(u1).astype(int), BASE_N - 1)
+    a, b = (u0 - i)[:, None], (u1 - j)[:, None]
+    v00, v01 = table[i, j], table[i, j + 1]
+    v10, v11 = table[i + 1, j], table[i + 1, j + 1]
+    return (1 - a) * ((1 - b) * v00 + b * v01) + a * ((1 - b) * v10 + b * v11)

@@ -12,6 +12,12 @@
 //                             c_f = 1e-5 max|xf_f| (a signed logarithm);
 //   target PDF_SURR_ENVELOPE: xf_f = E_f(x) y_f, trained on y_f = xf_f / E_f(x), with
 //                             E_f the per-flavour envelope of |xf_f| over Q (see env_table)
+//   target PDF_SURR_RESIDUAL: xf_f = B_f(z) + eps E_f(x) y_f, trained on
+//                             y_f = (xf_f - B_f) / (eps E_f): the network corrects a
+//                             base B, bilinear in (z0, z1) on a uniform 257 x 257
+//                             table of the FP64 interpolator (FP32), eps = 2^-10 the
+//                             size of the base's relative error; BF16's ~1% error then
+//                             lands on a term ~1e-3 of xf
 // silu(v) = v (1 + tanh(v/2)) / 2 with the hardware tanh approximation.
 // Weights are FP32 masters (Adam) with BF16 copies for the products.
 //
@@ -43,6 +49,10 @@ constexpr int SIN = 32;   // features
 constexpr int SOUT = 16;  // outputs, padded
 constexpr int MAPN = 64;  // error-map tiles per axis
 constexpr int ENVN = 1024;  // envelope table intervals over [lx_lo, lx_hi]
+constexpr int BASEN = 256;  // base table intervals per axis of (z0, z1)
+constexpr float kResEps = 1.f / 1024.f;  // residual target scale
+constexpr float kResClip = 32.f;         // residual targets clipped to [-32, 32] (cells the base misses by more
+                                         // than 3% of E fail the error map whatever the network does)
 constexpr float kPi = 3.14159265358979f;
 
 struct SurrConst {
@@ -50,8 +60,10 @@ struct SurrConst {
   float lx_lo, inv_lx, lq_lo, inv_lq;  // z = 2 (l - lo) inv - 1
   float scale[SOUT];
   int nf;
-  int target;          // PDF_SURR_ASINH or PDF_SURR_ENVELOPE
+  int target;          // PDF_SURR_ASINH, PDF_SURR_ENVELOPE or PDF_SURR_RESIDUAL
   const float *envt;   // [ENVN + 1][SOUT] ln E_f at lx_lo + k (lx_hi - lx_lo) / ENVN, zero for f >= nf
+  const float *baset;  // residual target: [BASEN + 1][BASEN + 1][SOUT] xf at z0 = -1 + 2 i / BASEN (outer),
+                       // z1 = -1 + 2 j / BASEN (inner), zero for f >= nf
 };
 
 // parameter offsets in the flat FP32 vector
@@ -103,6 +115,20 @@ __device__ __forceinline__ float envelope(const SurrConst &c, float z0, int f) {
   const float *t = c.envt + k * SOUT + f;
   const float a = __ldg(t), b = __ldg(t + SOUT);
   return expf(a + (u - (float)k) * (b - a));
+}
+
+// B_f at scaled coordinates (z0, z1): bilinear on the base table (clamped to
+// the square), FP32
+__device__ __forceinline__ float base_at(const SurrConst &c, float z0, float z1, int f) {
+  const float u0 = fminf(fmaxf((z0 + 1.f) * (0.5f * BASEN), 0.f), (float)BASEN);
+  const float u1 = fminf(fmaxf((z1 + 1.f) * (0.5f * BASEN), 0.f), (float)BASEN);
+  const int i = min((int)u0, BASEN - 1), j = min((int)u1, BASEN - 1);
+  const float a = u0 - (float)i, b = u1 - (float)j;
+  const float *r0 = c.baset + ((size_t)i * (BASEN + 1) + j) * SOUT + f;
+  const float *r1 = r0 + (size_t)(BASEN + 1) * SOUT;
+  const float v00 = __ldg(r0), v01 = __ldg(r0 + SOUT), v10 = __ldg(r1), v11 = __ldg(r1 + SOUT);
+  const float lo = fmaf(b, v01 - v00, v00), hi = fmaf(b, v11 - v10, v10);
+  return fmaf(a, hi - lo, lo);
 }
 
 // feature k (0..31) of a point
@@ -247,7 +273,7 @@ __global__ void k_cast(CastArgs a) {
   a.w[i] = __float2bfloat16_rn(v);
 }
 
-// training targets as FP32 [n][16]: asinh(xf / c), or xf / E(x)
+// training targets as FP32 [n][16]: asinh(xf / c), xf / E(x), or (xf - B) / (eps E(x))
 __global__ void k_targets(SurrConst c, const double *x, const double *q2, const double *xf, int n, float *t) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n * SOUT) return;
@@ -258,9 +284,28 @@ __global__ void k_targets(SurrConst c, const double *x, const double *q2, const 
     float z0, z1;
     point_z(c, x[p], q2[p], z0, z1);
     t[i] = (float)(v / (double)envelope(c, z0, f));
+  } else if (c.target == PDF_SURR_RESIDUAL) {
+    float z0, z1;
+    point_z(c, x[p], q2[p], z0, z1);
+    const double r = (v - (double)base_at(c, z0, z1, f)) / ((double)kResEps * (double)envelope(c, z0, f));
+    t[i] = (float)fmin(fmax(r, -(double)kResClip), (double)kResClip);
   } else {
     t[i] = (float)asinh(v / (double)c.scale[f]);
   }
+}
+
+// The residual target's base B_f for n points, into outf [n][nf] (FP32) or
+// outd (FP64); the inference kernel then adds eps E_f y_f.
+__global__ void k_base(SurrConst c, const double *x, const double *q2, long long n, float *outf, double *outd) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * c.nf) return;
+  const long long p = i / c.nf;
+  const int f = (int)(i - p * c.nf);
+  float z0, z1;
+  point_z(c, x[p], q2[p], z0, z1);
+  const float b = base_at(c, z0, z1, f);
+  if (outf) outf[i] = b;
+  if (outd) outd[i] = (double)b;
 }
 
 // ---------------------------------------------------------------------------
@@ -546,7 +591,7 @@ k_infer(SurrConst c, const bf16 *__restrict__ wg, const float *__restrict__ para
     const float u = fminf(fmaxf((z0 + 1.f) * (0.5f * ENVN), 0.f), (float)ENVN);
     const int k = min((int)u, ENVN - 1);
     const float fr = u - (float)k;
-    if (c.target == PDF_SURR_ENVELOPE) {
+    if (c.target != PDF_SURR_ASINH) {
       const float *src = c.envt + (size_t)k * SOUT + 8 * half;
 #pragma unroll
       for (int j = 0; j < 2; j++) {
@@ -609,7 +654,7 @@ k_infer(SurrConst c, const bf16 *__restrict__ wg, const float *__restrict__ para
         float v[8];
         tmem_ld8(tD + lanes + 8 * half, v);
         float o[8];
-        if (c.target == PDF_SURR_ENVELOPE) {
+        if (c.target != PDF_SURR_ASINH) {
           cp_async_wait_all();
           const float *er = E + t * 2 * SOUT;
           const float4 a0 = *reinterpret_cast<const float4 *>(er + (((2 * half) ^ (t & 7)) << 2));
@@ -618,8 +663,9 @@ k_infer(SurrConst c, const bf16 *__restrict__ wg, const float *__restrict__ para
           const float4 b1 = *reinterpret_cast<const float4 *>(er + (((5 + 2 * half) ^ (t & 7)) << 2));
           const float ea[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
           const float eb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+          const float sc = c.target == PDF_SURR_RESIDUAL ? kResEps : 1.f;
 #pragma unroll
-          for (int i = 0; i < 8; i++) o[i] = expf(ea[i] + fr * (eb[i] - ea[i])) * v[i];
+          for (int i = 0; i < 8; i++) o[i] = sc * expf(ea[i] + fr * (eb[i] - ea[i])) * v[i];
         } else {
 #pragma unroll
           for (int i = 0; i < 8; i++) o[i] = sscale[8 * half + i] * sinhf(v[i]);
@@ -630,14 +676,22 @@ k_infer(SurrConst c, const bf16 *__restrict__ wg, const float *__restrict__ para
         asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(kGT));
         const long long rows = min(128LL, n - p0);
         const int cnt = (int)rows * nf;
+        const bool add = c.target == PDF_SURR_RESIDUAL;  // the base is already in the output
         if (outf) {
           float *dst = outf + p0 * nf;
           int i0 = 0;
           if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
-            for (int i = gt; i < cnt / 4; i += kGT) __stcs(reinterpret_cast<float4 *>(dst) + i, reinterpret_cast<const float4 *>(O)[i]);
+            for (int i = gt; i < cnt / 4; i += kGT) {
+              float4 w = reinterpret_cast<const float4 *>(O)[i];
+              if (add) {
+                const float4 b = __ldcs(reinterpret_cast<const float4 *>(dst) + i);
+                w = make_float4(b.x + w.x, b.y + w.y, b.z + w.z, b.w + w.w);
+              }
+              __stcs(reinterpret_cast<float4 *>(dst) + i, w);
+            }
             i0 = cnt & ~3;
           }
-          for (int i = i0 + gt; i < cnt; i += kGT) __stcs(dst + i, O[i]);
+          for (int i = i0 + gt; i < cnt; i += kGT) __stcs(dst + i, add ? __ldcs(dst + i) + O[i] : O[i]);
         }
         if (outd) {
           double *dst = outd + p0 * nf;
@@ -645,11 +699,16 @@ k_infer(SurrConst c, const bf16 *__restrict__ wg, const float *__restrict__ para
           if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
             for (int i = gt; i < cnt / 2; i += kGT) {
               const float2 w = reinterpret_cast<const float2 *>(O)[i];
-              __stcs(reinterpret_cast<double2 *>(dst) + i, make_double2((double)w.x, (double)w.y));
+              double2 d = make_double2((double)w.x, (double)w.y);
+              if (add) {
+                const double2 b = __ldcs(reinterpret_cast<const double2 *>(dst) + i);
+                d = make_double2(b.x + d.x, b.y + d.y);
+              }
+              __stcs(reinterpret_cast<double2 *>(dst) + i, d);
             }
             i0 = cnt & ~1;
           }
-          for (int i = i0 + gt; i < cnt; i += kGT) __stcs(dst + i, (double)O[i]);
+          for (int i = i0 + gt; i < cnt; i += kGT) __stcs(dst + i, add ? __ldcs(dst + i) + (double)O[i] : (double)O[i]);
         }
       }
     }
@@ -917,6 +976,7 @@ struct pdf_surrogate {
   cudaStream_t tstream; // training runs here (a capturable stream), ordered with the caller's by events
   cudaEvent_t tev[2];
   float *z[4], *y, *t;
+  int last_n;  // points of the last loss/gradient pass (pdf_surrogate_trace reads its buffers)
   double *xfbuf, *loss;
   long long step;
   // error map and fallback
@@ -1081,6 +1141,7 @@ static int create_body(pdf_surrogate *s, const pdf_grid *grid, const float *para
     }
   }
   s->c.target = target;
+  s->c.baset = nullptr;
   s->c.lx_lo = (float)lxlo; s->c.inv_lx = (float)(1.0 / (lxhi - lxlo));
   s->c.lq_lo = (float)lqlo; s->c.inv_lq = (float)(1.0 / (lqhi - lqlo));
   for (int j = 0; j < SNQ; j++) { s->c.freq[j][0] = freq[2 * j]; s->c.freq[j][1] = freq[2 * j + 1]; }
@@ -1135,6 +1196,42 @@ static int create_body(pdf_surrogate *s, const pdf_grid *grid, const float *para
   if (!rc) rc = cuda_err(cudaMemset(s->tc_err, 0, sizeof(int)), what);
   if (rc) return rc;
   s->c.envt = envt_d;
+  if (target == PDF_SURR_RESIDUAL) {
+    // base table: the FP64 interpolator at the (BASEN + 1)^2 nodes of (z0, z1), rounded to FP32
+    const size_t nn = (size_t)(BASEN + 1) * (BASEN + 1);
+    std::vector<double> bx(nn), bq(nn);
+    for (int i = 0; i <= BASEN; i++)
+      for (int j = 0; j <= BASEN; j++) {
+        bx[(size_t)i * (BASEN + 1) + j] = i == BASEN ? v.xlast : exp(lxlo + (lxhi - lxlo) * i / BASEN);
+        bq[(size_t)i * (BASEN + 1) + j] = j == BASEN ? v.q2max : exp(lqlo + (lqhi - lqlo) * j / BASEN);
+      }
+    bx[0] = v.x0;
+    double *dx = nullptr, *dq = nullptr, *dv = nullptr;
+    float *bt = nullptr;
+    rc = s->alloc(&bt, nn * SOUT);
+    if (!rc) rc = cuda_err(cudaMalloc(&dx, nn * sizeof(double)), what);
+    if (!rc) rc = cuda_err(cudaMalloc(&dq, nn * sizeof(double)), what);
+    if (!rc) rc = cuda_err(cudaMalloc(&dv, nn * nf * sizeof(double)), what);
+    for (size_t k = 0; k < nn; k++) {  // the nodes on the low edges are the knots themselves
+      if (k % (BASEN + 1) == 0) bq[k] = v.q2min;
+      if (k < (size_t)(BASEN + 1)) bx[k] = v.x0;
+    }
+    if (!rc) rc = cuda_err(cudaMemcpy(dx, bx.data(), nn * sizeof(double), cudaMemcpyHostToDevice), what);
+    if (!rc) rc = cuda_err(cudaMemcpy(dq, bq.data(), nn * sizeof(double), cudaMemcpyHostToDevice), what);
+    if (!rc) rc = launch_all_f64(grid, dx, dq, (long long)nn, dv, nullptr, 0);
+    std::vector<double> hv(rc ? 0 : nn * nf);
+    if (!rc) rc = cuda_err(cudaMemcpy(hv.data(), dv, nn * nf * sizeof(double), cudaMemcpyDeviceToHost), what);
+    if (dx) cudaFree(dx);
+    if (dq) cudaFree(dq);
+    if (dv) cudaFree(dv);
+    if (rc) return rc;
+    std::vector<float> ht(nn * SOUT, 0.f);
+    for (size_t k = 0; k < nn; k++)
+      for (int f = 0; f < nf; f++) ht[k * SOUT + f] = (float)hv[k * nf + f];
+    rc = cuda_err(cudaMemcpy(bt, ht.data(), ht.size() * sizeof(float), cudaMemcpyHostToDevice), what);
+    if (rc) return rc;
+    s->c.baset = bt;
+  }
   cast_weights(s, 0);
   return cuda_err(cudaDeviceSynchronize(), what);
 }
@@ -1143,7 +1240,7 @@ extern "C" int pdf_surrogate_create_ex(const pdf_grid *grid, const float *params
                                        int target, pdf_surrogate **out) {
   if (!grid || !params || !freq || !out) return set_error(PDF_ERR_NULL, "pdf_surrogate_create: NULL argument");
   *out = nullptr;
-  if (target != PDF_SURR_ASINH && target != PDF_SURR_ENVELOPE)
+  if (target != PDF_SURR_ASINH && target != PDF_SURR_ENVELOPE && target != PDF_SURR_RESIDUAL)
     return set_error(PDF_ERR_ARG, "pdf_surrogate_create: unknown target %d", target);
   if (grid->v.nf > SOUT) return set_error(PDF_ERR_ARG, "pdf_surrogate_create: at most %d flavours", SOUT);
   if (max_batch < 16 || max_batch > (1 << 22))
@@ -1218,12 +1315,53 @@ extern "C" int pdf_surrogate_loss_grad(pdf_surrogate *s, const double *x, const 
   int rc = features_targets(s, nullptr, x, q2, (int)n, xf, 0);
   if (!rc) rc = forward_backward(s, (int)n, 0);
   if (rc) return rc;
+  s->last_n = (int)n;
   double sum = 0.0;
   rc = cuda_err(cudaMemcpy(&sum, s->loss, sizeof(double), cudaMemcpyDeviceToHost), "pdf_surrogate_loss_grad");
   if (!rc) rc = cuda_err(cudaMemcpy(grad, s->grads, s->L.total * sizeof(float), cudaMemcpyDeviceToHost),
                          "pdf_surrogate_loss_grad");
   if (!rc) rc = check_tc(s, "pdf_surrogate_loss_grad");
   *loss = sum / ((double)n * s->nf);
+  return rc;
+}
+
+// bfloat16 [rows][cols] with row stride ld -> FP32 [rows][cols]
+__global__ void k_bf16_rows(const bf16 *a, int rows, int cols, int ld, float *out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows * cols) return;
+  out[i] = __bfloat162float(a[(size_t)(i / cols) * ld + i % cols]);
+}
+
+extern "C" int pdf_surrogate_trace(pdf_surrogate *s, int what, int layer, float *out) {
+  if (!s || !out) return set_error(PDF_ERR_NULL, "pdf_surrogate_trace: NULL argument");
+  std::lock_guard<std::mutex> lock(s->mu);
+  const int n = s->last_n;
+  if (n < 1) return set_error(PDF_ERR_ARG, "pdf_surrogate_trace: no loss/gradient pass yet");
+  // the pass may have run on any stream: wait for the device
+  if (int rc = cuda_err(cudaDeviceSynchronize(), "pdf_surrogate_trace")) return rc;
+  const int cols_h = layer == 0 ? SIN : SW, cols_g = layer == 4 ? SOUT : SW;
+  const float *src = nullptr;
+  const bf16 *srcb = nullptr;
+  int cols = 0, ld = 0;
+  if (what == 0 && layer >= 0 && layer <= 4) { srcb = s->h[layer]; cols = ld = cols_h; }
+  else if (what == 1 && layer >= 0 && layer <= 3) { src = s->z[layer]; cols = ld = SW; }
+  else if (what == 2 && layer >= 0 && layer <= 4) { srcb = s->g[layer]; cols = ld = cols_g; }
+  else if (what == 3 && layer == 0) { src = s->y; cols = ld = SOUT; }
+  else if (what == 4 && layer == 0) { src = s->t; cols = ld = SOUT; }
+  else return set_error(PDF_ERR_ARG, "pdf_surrogate_trace: no buffer (what %d, layer %d)", what, layer);
+  const size_t bytes = (size_t)n * cols * sizeof(float);
+  int rc = PDF_OK;
+  if (src) {
+    rc = cuda_err(cudaMemcpy(out, src, bytes, cudaMemcpyDeviceToHost), "pdf_surrogate_trace");
+  } else {
+    float *tmp = nullptr;
+    rc = cuda_err(cudaMalloc(&tmp, bytes), "pdf_surrogate_trace");
+    if (!rc) {
+      k_bf16_rows<<<(unsigned)(((size_t)n * cols + 255) / 256), 256>>>(srcb, n, cols, ld, tmp);
+      rc = cuda_err(cudaMemcpy(out, tmp, bytes, cudaMemcpyDeviceToHost), "pdf_surrogate_trace");
+      cudaFree(tmp);
+    }
+  }
   return rc;
 }
 
@@ -1236,6 +1374,7 @@ extern "C" int pdf_surrogate_train(pdf_surrogate *s, const pdf_grid *grid, const
   if (grid->v.nf != s->nf) return set_error(PDF_ERR_ARG, "pdf_surrogate_train: grid flavours differ");
   if (cfg->steps < 1) return set_error(PDF_ERR_ARG, "pdf_surrogate_train: steps must be >= 1");
   std::lock_guard<std::mutex> lock(s->mu);
+  s->last_n = 0;  // training reuses the buffers a trace would read
   const long long nb = (long long)(n / (size_t)B);  // whole batches per pass
   cudaStream_t ts = s->tstream;
   // one training step; everything that changes from step to step (the batch,
@@ -1312,6 +1451,10 @@ static int launch_infer(const pdf_surrogate *s, const double *x, const double *q
   long long tiles = ((long long)n + 127) / 128;
   long long blocks = (tiles + TG - 1) / TG;
   if (blocks > sms) blocks = sms;
+  if (s->c.target == PDF_SURR_RESIDUAL) {
+    const long long items = (long long)n * s->nf;
+    k_base<<<(unsigned)((items + 255) / 256), 256, 0, st>>>(s->c, x, q2, (long long)n, outf, outd);
+  }
   k_infer<<<(unsigned)blocks, kTcThreads, kTcSmem, st>>>(s->c, s->wbf, s->params, s->L, x, q2, (long long)n, outf,
                                                           outd, mask, nfb, idx, s->tc_err);
   return check_launch("surrogate inference");

@@ -18,7 +18,7 @@ from .pdf import Grid, _dev_ptr, _stream_handle
 
 
 class Surrogate:
-    TARGETS = {"asinh": 0, "envelope": 1}  # PDF_SURR_ASINH, PDF_SURR_ENVELOPE
+    TARGETS = {"asinh": 0, "envelope": 1, "residual": 2}  # PDF_SURR_ASINH, _ENVELOPE, _RESIDUAL
 
     def __init__(self, grid: Grid, params=None, freq=None, max_batch: int = 16384, seed: int = 9,
                  target: str = "asinh"):
@@ -80,6 +80,15 @@ class Surrogate:
             _dev_ptr(xf, torch.float64, "xf"), x.shape[0], ctypes.byref(loss), grad.ctypes.data),
             "pdf_surrogate_loss_grad")
         return loss.value, grad
+
+    def trace(self, what: str, layer: int = 0, n: int = None) -> np.ndarray:
+        """An intermediate of the last loss_grad pass: "h" (bfloat16 activations),
+        "z" (pre-activations), "g" (backward signals), "y" (outputs), "t" (targets)."""
+        code = {"h": 0, "z": 1, "g": 2, "y": 3, "t": 4}[what]
+        cols = {"h": 32 if layer == 0 else 128, "z": 128, "g": 16 if layer == 4 else 128, "y": 16, "t": 16}[what]
+        out = np.empty((n, cols), dtype=np.float32)
+        check(_native.load().pdf_surrogate_trace(self.handle, code, int(layer), out.ctypes.data), "pdf_surrogate_trace")
+        return out
 
     def train(self, grid: Grid, x: torch.Tensor, q2: torch.Tensor, batch: int = 8192, steps: int = 1000,
               lr: float = 2e-3, lr_min: float = 2e-5, warmup: int = 100) -> float:

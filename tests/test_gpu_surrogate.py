@@ -46,13 +46,12 @@ def test_loss_and_gradient_match_oracle(setup, synth):
     oloss, ograd = mlp.loss_grad(params.astype(np.float64), x, q2, xf, scale, freq.astype(np.float64), bounds,
                                  g.nflav, bf=True)
     assert abs(loss - oloss) <= 1e-3 * oloss, (loss, oloss)
-    layers_g = mlp.unpack(grad.astype(np.float64), g.nflav)
-    layers_o = mlp.unpack(ograd, g.nflav)
-    for li, ((gw, gb), (ow, ob)) in enumerate(zip(layers_g, layers_o)):
-        for a, b, name in ((gw, ow, "W"), (gb, ob, "b")):
-            rel = np.linalg.norm(a - b) / np.linalg.norm(b)
-            cos = float((a * b).sum() / (np.linalg.norm(a) * np.linalg.norm(b)))
-            assert rel < 2e-2 and cos > 0.9995, (li, name, rel, cos)
+    # every element of every stage, the gradient included, within the bound
+    # its own arithmetic gives, on the GPU's inputs of that stage
+    from surrogate_bounds import check_training_pass
+
+    worst = check_training_pass(s, params, x, q2, xf, scale, freq.astype(np.float64), bounds, g.nflav, grad)
+    print("training pass, largest ratio to the bound per stage:", {k: round(v, 3) for k, v in worst.items()})
 
 
 def test_fused_inference_matches_oracle(setup, synth):
@@ -62,9 +61,10 @@ def test_fused_inference_matches_oracle(setup, synth):
     s = Surrogate(G, params, freq, max_batch=1024)
     x, q2 = synth.ingrid_samples(g, 4001, 22)
     out = s.eval(dev(x), dev(q2)).cpu().numpy().astype(np.float64)
-    want = mlp.predict(params.astype(np.float64), x, q2, scale, freq.astype(np.float64), bounds, g.nflav, bf=True)
-    dy = np.abs(np.arcsinh(out / scale) - np.arcsinh(want / scale))
-    assert np.quantile(dy, 0.99) < 2e-2 and dy.max() < 1e-1, (np.quantile(dy, 0.99), dy.max())
+    from surrogate_bounds import check_inference
+
+    worst = check_inference(out, params, x, q2, scale, freq.astype(np.float64), bounds, g.nflav)
+    print(f"inference: worst element at {worst:.3f} of its bound")
 
 
 @pytest.mark.parametrize("target", ["asinh", "envelope"])
@@ -87,15 +87,11 @@ def test_fused_inference_with_biases_matches_oracle(setup, synth, target):
     s = Surrogate(G, p32, freq, max_batch=1024, target=target)
     x, q2 = synth.ingrid_samples(g, 4001, 23)
     out = s.eval(dev(x), dev(q2)).cpu().numpy().astype(np.float64)
-    if target == "envelope":
-        env = mlp.envelope(mlp.envelope_table(g.x_knots, g.values, bounds), x, bounds)
-        want = mlp.predict(p32.astype(np.float64), x, q2, scale, freq.astype(np.float64), bounds, g.nflav, bf=True,
-                           env=env)
-        dy = np.abs(out - want) / env
-    else:
-        want = mlp.predict(p32.astype(np.float64), x, q2, scale, freq.astype(np.float64), bounds, g.nflav, bf=True)
-        dy = np.abs(np.arcsinh(out / scale) - np.arcsinh(want / scale))
-    assert np.quantile(dy, 0.99) < 2e-2 and dy.max() < 1e-1, (np.quantile(dy, 0.99), dy.max())
+    from surrogate_bounds import check_inference
+
+    table = mlp.envelope_table(g.x_knots, g.values, bounds) if target == "envelope" else None
+    worst = check_inference(out, p32, x, q2, scale, freq.astype(np.float64), bounds, g.nflav, target, table)
+    print(f"inference with biases ({target}): worst element at {worst:.3f} of its bound")
 
 
 def test_training_error_map_and_fallback(setup, synth):
@@ -172,9 +168,9 @@ def test_full_size_inference_sampled(setup, synth):
     alone = s.eval(xd[ti], qd[ti]).cpu().numpy()
     assert np.array_equal(got, alone)
     k = idx[:2000]
-    want = mlp.predict(p32.astype(np.float64), x[k], q2[k], scale, freq.astype(np.float64), bounds, g.nflav, bf=True)
-    dy = np.abs(np.arcsinh(got[:2000].astype(np.float64) / scale) - np.arcsinh(want / scale))
-    assert np.quantile(dy, 0.99) < 2e-2 and dy.max() < 1e-1, (np.quantile(dy, 0.99), dy.max())
+    from surrogate_bounds import check_inference
+
+    check_inference(got[:2000], p32, x[k], q2[k], scale, freq.astype(np.float64), bounds, g.nflav)
 
 
 def test_fallback_calls_on_two_streams_from_two_threads(setup, synth):

@@ -50,19 +50,15 @@ def test_loss_gradient_and_inference_match_oracle(setup, synth):
     oloss, ograd = mlp.loss_grad(params.astype(np.float64), x, q2, xf, scale, freq.astype(np.float64), bounds,
                                  g.nflav, bf=True, env=env)
     assert abs(loss - oloss) <= 1e-3 * oloss, (loss, oloss)
-    for li, ((gw, gb), (ow, ob)) in enumerate(zip(mlp.unpack(grad.astype(np.float64), g.nflav),
-                                                  mlp.unpack(ograd, g.nflav))):
-        for a, b, name in ((gw, ow, "W"), (gb, ob, "b")):
-            rel = np.linalg.norm(a - b) / np.linalg.norm(b)
-            cos = float((a * b).sum() / (np.linalg.norm(a) * np.linalg.norm(b)))
-            assert rel < 2e-2 and cos > 0.9995, (li, name, rel, cos)
+    from surrogate_bounds import check_inference, check_training_pass
+
+    f64 = freq.astype(np.float64)
+    worst = check_training_pass(s, params, x, q2, xf, scale, f64, bounds, g.nflav, grad, "envelope", table)
+    print("training pass (envelope), largest ratio per stage:", {k: round(v, 3) for k, v in worst.items()})
     x, q2 = synth.ingrid_samples(g, 4001, 32)
-    out = s.eval(dev(x), dev(q2)).cpu().numpy().astype(np.float64)
-    env = mlp.envelope(table, x, bounds)
-    want = mlp.predict(params.astype(np.float64), x, q2, scale, freq.astype(np.float64), bounds, g.nflav, bf=True,
-                       env=env)
-    dy = np.abs(out - want) / env  # in units of the network output
-    assert np.quantile(dy, 0.99) < 2e-2 and dy.max() < 1e-1, (np.quantile(dy, 0.99), dy.max())
+    out = s.eval(dev(x), dev(q2)).cpu().numpy()
+    worst = check_inference(out, params, x, q2, scale, f64, bounds, g.nflav, "envelope", table)
+    print(f"inference (envelope): worst element at {worst:.3f} of its bound")
 
 
 def test_training_error_map_and_fallback(setup, synth):
