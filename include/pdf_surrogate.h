@@ -115,10 +115,21 @@ PDF_API int pdf_surrogate_eval(const pdf_surrogate *s, const double *x, const do
  * points, record per tile of a 64 x 64 partition of the scaled (ln x, ln Q^2)
  * square the largest error |s - v| / max(|v|, c_f) over points and
  * flavours, and accept a tile when it was sampled and its error is at most
- * `threshold`.  stats (HOST, may be NULL) receives [tiles accepted, tiles
- * sampled, largest error, median tile error].  Synchronous. */
+ * `threshold`.  With PDF_SURR_RESIDUAL the base alone (the network's term
+ * left out) is measured on the same points too, and a tile is served by the
+ * more accurate of the two among those within the threshold.  stats (HOST,
+ * may be NULL) receives [tiles accepted, tiles sampled, largest error,
+ * median tile error], a tile's error being that of the way it is served (of
+ * the better way where neither passes).  Synchronous. */
 PDF_API int pdf_surrogate_build_error_map(pdf_surrogate *s, const pdf_grid *grid, const double *x,
                                           const double *q2, size_t n, double threshold, double *stats);
+
+/* The last error map's tile states into HOST states[64 * 64], tile (tx, tq)
+ * at tq * 64 + tx, tx = floor((z0 + 1) 32), tq = floor((z1 + 1) 32) of the
+ * scaled coordinates (FP32): 0 the interpolator, 1 the network, 2 the
+ * residual target's base alone.  PDF_ERR_ARG before any error map.
+ * Synchronous. */
+PDF_API int pdf_surrogate_map(pdf_surrogate *s, unsigned char *states);
 
 /* x f for all flavours, out [n][nflav] FP64: the network on accepted tiles,
  * the FP64 interpolator everywhere else (rejected tiles, outside the grid,

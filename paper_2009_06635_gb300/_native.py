@@ -89,6 +89,7 @@ SIGNATURES = {
     "pdf_surrogate_set_params": (I32, [P, P]),
     "pdf_surrogate_loss_grad": (I32, [P, P, P, P, SZ, ctypes.POINTER(ctypes.c_double), P]),
     "pdf_surrogate_trace": (I32, [P, I32, I32, P]),
+    "pdf_surrogate_map": (I32, [P, P]),
     "pdf_surrogate_train": (I32, [P, P, P, P, SZ, P, ctypes.POINTER(ctypes.c_double), P]),
     "pdf_surrogate_eval": (I32, [P, P, P, SZ, P, P]),
     "pdf_surrogate_build_error_map": (I32, [P, P, P, P, SZ, F64, P]),

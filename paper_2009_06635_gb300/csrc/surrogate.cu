@@ -599,11 +599,14 @@ k_infer(SurrConst c, const bf16 *__restrict__ wg, const float *__restrict__ para
         cp_async16(e_row + (uint32_t)(((4 + 2 * half + j) ^ (t & 7)) * 16), src + SOUT + 4 * j);
       }
     }
+    bool base_only = false;  // a tile the map serves by the residual target's base alone
     if (mask) {  // fallback: outside the grid, or on a tile the map rejects
       const bool inside = z0 >= -1.f && z0 <= 1.f && z1 >= -1.f && z1 <= 1.f && x > 0.0 && q > 0.0;
       const int tx = min(MAPN - 1, max(0, (int)((z0 + 1.f) * 0.5f * MAPN)));
       const int tq = min(MAPN - 1, max(0, (int)((z1 + 1.f) * 0.5f * MAPN)));
-      const bool bad = in && !(inside && mask[tq * MAPN + tx]);
+      const unsigned char ms = inside ? mask[tq * MAPN + tx] : (unsigned char)0;
+      const bool bad = in && ms == 0;
+      base_only = ms == 2;
       if (half == 0) {  // one record per point
         const unsigned int bb = __ballot_sync(0xffffffffu, bad);
         unsigned int base = 0;
@@ -665,7 +668,7 @@ k_infer(SurrConst c, const bf16 *__restrict__ wg, const float *__restrict__ para
           const float eb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
           const float sc = c.target == PDF_SURR_RESIDUAL ? kResEps : 1.f;
 #pragma unroll
-          for (int i = 0; i < 8; i++) o[i] = sc * expf(ea[i] + fr * (eb[i] - ea[i])) * v[i];
+          for (int i = 0; i < 8; i++) o[i] = base_only ? 0.f : sc * expf(ea[i] + fr * (eb[i] - ea[i])) * v[i];
         } else {
 #pragma unroll
           for (int i = 0; i < 8; i++) o[i] = sscale[8 * half + i] * sinhf(v[i]);
@@ -927,14 +930,25 @@ __global__ void k_tile_err(SurrConst c, const double *xa, const double *qa, long
   }
   if (isnan(e)) e = 1e30f;
   atomicMax(tile_err_bits + tq * MAPN + tx, __float_as_uint(e));  // e >= 0: bits order like values
-  atomicAdd(tile_cnt + tq * MAPN + tx, 1u);
+  if (tile_cnt) atomicAdd(tile_cnt + tq * MAPN + tx, 1u);
 }
 
-__global__ void k_make_mask(const unsigned int *tile_err_bits, const unsigned int *tile_cnt, float thr,
-                            unsigned char *mask) {
+// tile states: 0 the interpolator, 1 the network, 2 the residual target's
+// base alone (its network term left out): the more accurate of 1 and 2 among
+// those within the threshold
+__global__ void k_make_mask(const unsigned int *tile_err_bits, const unsigned int *base_err_bits,
+                            const unsigned int *tile_cnt, float thr, unsigned char *mask) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= MAPN * MAPN) return;
-  mask[t] = (tile_cnt[t] > 0 && __uint_as_float(tile_err_bits[t]) <= thr) ? 1 : 0;
+  const float en = __uint_as_float(tile_err_bits[t]);
+  const float eb = base_err_bits ? __uint_as_float(base_err_bits[t]) : INFINITY;
+  unsigned char m = 0;
+  if (tile_cnt[t] > 0) {
+    if (en <= thr && en <= eb) m = 1;
+    else if (eb <= thr) m = 2;
+    else if (en <= thr) m = 1;
+  }
+  mask[t] = m;
 }
 
 __global__ void k_gather(const double *x, const double *q2, const unsigned int *idx, unsigned int m, double *gx,
@@ -981,7 +995,7 @@ struct pdf_surrogate {
   long long step;
   // error map and fallback
   unsigned char *mask;
-  unsigned int *tile_bits, *tile_cnt, *nfb, *fb_idx;
+  unsigned int *tile_bits, *base_bits, *tile_cnt, *nfb, *fb_idx;
   int *tc_err;  // set by the inference kernel when a tensor-core wait ran out
   double *fb_x, *fb_q, *fb_out;
   size_t fb_cap;
@@ -1182,6 +1196,7 @@ static int create_body(pdf_surrogate *s, const pdf_grid *grid, const float *para
   if (!rc) rc = s->alloc(&s->loss, 1);
   if (!rc) rc = s->alloc(&s->mask, MAPN * MAPN);
   if (!rc) rc = s->alloc(&s->tile_bits, MAPN * MAPN);
+  if (!rc) rc = s->alloc(&s->base_bits, MAPN * MAPN);
   if (!rc) rc = s->alloc(&s->tile_cnt, MAPN * MAPN);
   if (!rc) rc = s->alloc(&s->nfb, 1);
   if (!rc) rc = s->alloc(&s->tc_err, 1);
@@ -1471,40 +1486,55 @@ extern "C" int pdf_surrogate_eval(const pdf_surrogate *s, const double *x, const
 static int error_map_body(pdf_surrogate *s, const pdf_grid *grid, const double *x, const double *q2, size_t n,
                           double threshold, double *stats) {
   std::lock_guard<std::mutex> lock(s->mu);
+  const bool res = s->c.target == PDF_SURR_RESIDUAL;
   // host copies first, so that nothing below can throw while device scratch is held
-  std::vector<unsigned int> bits(MAPN * MAPN), cnt(MAPN * MAPN);
+  std::vector<unsigned int> bits(MAPN * MAPN), bbits(MAPN * MAPN), cnt(MAPN * MAPN);
   std::vector<unsigned char> m(MAPN * MAPN);
   std::vector<float> errs;
   errs.reserve(MAPN * MAPN);
-  float *sv = nullptr;
+  float *sv = nullptr, *bv = nullptr;
   double *iv = nullptr;
   int rc = cuda_err(cudaMalloc(&sv, n * s->nf * sizeof(float)), "error map");
   if (!rc) rc = cuda_err(cudaMalloc(&iv, n * s->nf * sizeof(double)), "error map");
+  if (!rc && res) rc = cuda_err(cudaMalloc(&bv, n * s->nf * sizeof(float)), "error map");
   if (!rc) rc = launch_infer(s, x, q2, n, sv, nullptr, nullptr, nullptr, nullptr, 0);
   if (!rc) rc = launch_all_f64(grid, x, q2, (long long)n, iv, nullptr, 0);
   if (!rc) {
     cudaMemset(s->tile_bits, 0, MAPN * MAPN * sizeof(unsigned int));
+    cudaMemset(s->base_bits, 0, MAPN * MAPN * sizeof(unsigned int));
     cudaMemset(s->tile_cnt, 0, MAPN * MAPN * sizeof(unsigned int));
-    k_tile_err<<<(unsigned)((n + 255) / 256), 256>>>(s->c, x, q2, (long long)n, sv, iv, s->tile_bits, s->tile_cnt);
-    k_make_mask<<<(MAPN * MAPN + 255) / 256, 256>>>(s->tile_bits, s->tile_cnt, (float)threshold, s->mask);
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    k_tile_err<<<blocks, 256>>>(s->c, x, q2, (long long)n, sv, iv, s->tile_bits, s->tile_cnt);
+    if (res) {  // the base alone on the same points (counts taken once)
+      const long long items = (long long)n * s->nf;
+      k_base<<<(unsigned)((items + 255) / 256), 256>>>(s->c, x, q2, (long long)n, bv, nullptr);
+      k_tile_err<<<blocks, 256>>>(s->c, x, q2, (long long)n, bv, iv, s->base_bits, nullptr);
+    }
+    k_make_mask<<<(MAPN * MAPN + 255) / 256, 256>>>(s->tile_bits, res ? s->base_bits : nullptr, s->tile_cnt,
+                                                    (float)threshold, s->mask);
     rc = check_launch("error map");
   }
   if (!rc) rc = cuda_err(cudaMemcpy(bits.data(), s->tile_bits, bits.size() * 4, cudaMemcpyDeviceToHost), "error map");
+  if (!rc) rc = cuda_err(cudaMemcpy(bbits.data(), s->base_bits, bbits.size() * 4, cudaMemcpyDeviceToHost), "error map");
   if (!rc) rc = cuda_err(cudaMemcpy(cnt.data(), s->tile_cnt, cnt.size() * 4, cudaMemcpyDeviceToHost), "error map");
   if (!rc) rc = cuda_err(cudaMemcpy(m.data(), s->mask, m.size(), cudaMemcpyDeviceToHost), "error map");
   cudaFree(sv);
   cudaFree(iv);
+  if (bv) cudaFree(bv);
   if (!rc) rc = check_tc(s, "pdf_surrogate_build_error_map");
   if (rc) return rc;
-  // stats: [tiles accepted, tiles with samples, largest error on sampled tiles, median tile error]
+  // stats: [tiles accepted, tiles with samples, largest error on sampled tiles, median tile error];
+  // a tile's error is that of the way it is served (of the better way, if neither passes)
   int ok = 0, sampled = 0;
   float worst = 0.f;
   for (size_t t = 0; t < bits.size(); t++) {
-    ok += m[t];
+    ok += m[t] != 0;
     if (cnt[t] > 0) {
       sampled++;
-      float e;
+      float e, eb;
       std::memcpy(&e, &bits[t], 4);
+      std::memcpy(&eb, &bbits[t], 4);
+      if (res && (m[t] == 2 || (m[t] == 0 && eb < e))) e = eb;
       worst = fmaxf(worst, e);
       errs.push_back(e);
     }
@@ -1531,6 +1561,13 @@ extern "C" int pdf_surrogate_build_error_map(pdf_surrogate *s, const pdf_grid *g
   if (grid->v.nf != s->nf) return set_error(PDF_ERR_ARG, "pdf_surrogate_build_error_map: grid flavours differ");
   return guarded("pdf_surrogate_build_error_map",
                  [&] { return error_map_body(s, grid, x, q2, n, threshold, stats); });
+}
+
+extern "C" int pdf_surrogate_map(pdf_surrogate *s, unsigned char *states) {
+  if (!s || !states) return set_error(PDF_ERR_NULL, "pdf_surrogate_map: NULL argument");
+  std::lock_guard<std::mutex> lock(s->mu);
+  if (!s->has_map) return set_error(PDF_ERR_ARG, "pdf_surrogate_map: build the error map first");
+  return cuda_err(cudaMemcpy(states, s->mask, MAPN * MAPN, cudaMemcpyDeviceToHost), "pdf_surrogate_map");
 }
 
 extern "C" int pdf_surrogate_eval_fallback(pdf_surrogate *s, const pdf_grid *grid, const double *x,

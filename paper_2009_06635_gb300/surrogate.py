@@ -112,8 +112,17 @@ class Surrogate:
         check(_native.load().pdf_surrogate_build_error_map(
             self.handle, grid.handle, _dev_ptr(x, torch.float64, "x"), _dev_ptr(q2, torch.float64, "q2"),
             x.shape[0], float(threshold), st.ctypes.data), "pdf_surrogate_build_error_map")
+        m = self.tile_map()
         return {"tiles_accepted": int(st[0]), "tiles_sampled": int(st[1]), "max_error": float(st[2]),
-                "median_tile_error": float(st[3]), "threshold": threshold}
+                "median_tile_error": float(st[3]), "threshold": threshold, "tiles_network": int((m == 1).sum()),
+                "tiles_base_only": int((m == 2).sum())}
+
+    def tile_map(self) -> np.ndarray:
+        """The last error map's tile states [64 (z1 tiles)][64 (z0 tiles)]: 0 the
+        interpolator, 1 the network, 2 the residual target's base alone."""
+        m = np.zeros(64 * 64, dtype=np.uint8)
+        check(_native.load().pdf_surrogate_map(self.handle, m.ctypes.data), "pdf_surrogate_map")
+        return m.reshape(64, 64)
 
     def eval_fallback(self, grid: Grid, x: torch.Tensor, q2: torch.Tensor, out=None):
         if out is None:

@@ -92,12 +92,27 @@ def test_loss_and_inference_match_oracle(setup, synth):
     print(f"inference (residual): worst element at {worst:.3f} of its bound")
 
 
+def gpu_tiles(x, q2, bounds):
+    """Error-map tile (tq, tx) of each point from FP32 coordinates computed as
+    the GPU does, and whether the point is clear of tile edges (so that an ulp
+    of difference in ln cannot move it to the neighbouring tile)."""
+    f = np.float32
+    lo0, lo1 = f(bounds[0]), f(bounds[2])
+    i0, i1 = f(1.0 / (bounds[1] - bounds[0])), f(1.0 / (bounds[3] - bounds[2]))
+    z0 = f(2) * (np.log(x.astype(f)) - lo0) * i0 - f(1)
+    z1 = f(2) * (np.log(q2.astype(f)) - lo1) * i1 - f(1)
+    u0, u1 = (z0.astype(np.float64) + 1) * 32, (z1.astype(np.float64) + 1) * 32
+    clear = (np.abs(u0 - np.round(u0)) > 1e-3) & (np.abs(u1 - np.round(u1)) > 1e-3)
+    return np.clip(u1.astype(int), 0, 63), np.clip(u0.astype(int), 0, 63), clear
+
+
 def test_training_reaches_the_threshold_and_serves_points(setup, synth):
     """Trained on interpolator samples, the network passes the 1e-3 error
-    threshold on part of the (z0, z1) square; evaluation with fallback then
-    serves those points from the network (base + correction) and the rest
-    from the interpolator, each within the threshold (checked on fresh points
-    with the map's tile resolution as margin)."""
+    threshold on part of the (z0, z1) square and the base alone on another
+    part; evaluation with fallback serves each tile the way its map state
+    says (network, base alone, or the interpolator), each served point within
+    the threshold (checked on fresh points, with the map's tile resolution as
+    margin), and base-alone tiles give exactly the base."""
     g, G, Surrogate, params, freq, scale, bounds, env_table, base_table, og = setup
     s = Surrogate(G, params, freq, max_batch=8192, target="residual")
     x, q2 = synth.ingrid_samples(g, 2_000_000, 7)
@@ -109,15 +124,29 @@ def test_training_reaches_the_threshold_and_serves_points(setup, synth):
     xv, qv = synth.ingrid_samples(g, 1_000_000, 23)
     stats = s.build_error_map(G, dev(xv), dev(qv), threshold=1e-3)
     print("residual target: error map", stats, "loss", l0, "->", final)
-    assert stats["tiles_accepted"] > 0.25 * 64 * 64, stats
+    assert stats["tiles_accepted"] == stats["tiles_network"] + stats["tiles_base_only"]
+    assert stats["tiles_network"] > 0 and stats["tiles_accepted"] > 0.25 * 64 * 64, stats
+    m = s.tile_map()
+    assert int((m != 0).sum()) == stats["tiles_accepted"]
     xt, qt = synth.ingrid_samples(g, 400_000, 24)
     out, nfb = s.eval_fallback(G, dev(xt), dev(qt))
     out = out.cpu().numpy()
     ref = P.xfxq2_all_flavours(G, dev(xt), dev(qt)).cpu().numpy()
     served = ~np.all(out == ref, axis=1)
     assert served.sum() == len(xt) - nfb > 0
+    tq, tx, clear = gpu_tiles(xt, qt, bounds)
+    state = m[tq, tx]
+    assert np.array_equal(served[clear], state[clear] != 0)
+    # base-alone tiles: exactly the base (a network of zeros adds nothing to it)
+    s0 = Surrogate(G, np.zeros_like(params), freq, max_batch=8192, target="residual")
+    b = s0.eval(dev(xt), dev(qt)).cpu().numpy().astype(np.float64)
+    k = clear & (state == 2)
+    assert np.array_equal(out[k], b[k])
+    k = clear & (state == 1)
+    assert k.sum() > 0 and not np.array_equal(out[k], b[k])
     err = np.max(np.abs(out - ref) / np.maximum(np.abs(ref), scale), axis=1)
-    print(f"served {served.mean():.3f} of the points; worst error on them {err[served].max():.2e}")
+    print(f"served {served.mean():.3f} of the points ({(state[clear] == 1).mean():.3f} by the network, "
+          f"{(state[clear] == 2).mean():.3f} by the base alone); worst error on them {err[served].max():.2e}")
     assert err[served].max() < 3e-3, err[served].max()
     assert np.quantile(err[served], 0.999) < 1e-3
 
@@ -161,6 +190,8 @@ def test_gain_over_the_interpolator_at_the_threshold(setup, synth):
     _, nfb0 = s0.eval_fallback(G, xd, qd)
     served0 = 1.0 - nfb0 / n
     print(f"residual surrogate with fallback: {t_sur:.3f} ms, interpolator alone {t_int:.3f} ms "
-          f"(gain {t_int / t_sur:.2f}x); served at 1e-3: {served:.3f} of {n} in-grid points with the network, "
-          f"{served0:.3f} with the base alone")
-    assert served > 0.25 and t_sur > 0 and t_int > 0
+          f"(gain {t_int / t_sur:.2f}x); served at 1e-3: {served:.3f} of {n} in-grid points with the network "
+          f"and its base, {served0:.3f} with the base alone")
+    # each tile takes the better of network and base, so the trained network
+    # serves at least what the base alone does (the same validation points)
+    assert served >= served0 and served > 0.25 and t_sur > 0 and t_int > 0
