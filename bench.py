@@ -652,7 +652,7 @@ def our_arm(args):
         from paper_2009_06635_gb300 import synthetic as S
         from paper_2009_06635_gb300.surrogate import Surrogate
 
-        s = Surrogate(G, max_batch=1024, target="envelope")
+        s = Surrogate(G, max_batch=1024, target=args.target)
         xi, qi = S.ingrid_samples(g, n, 8 + 1000 * rank)
         xid, qid = torch.from_numpy(xi).to(dev), torch.from_numpy(qi).to(dev)
         so = torch.empty((n, nf), dtype=torch.float32, device=dev)
@@ -874,6 +874,8 @@ def main():
     ap.add_argument("--no-members", action="store_true")
     ap.add_argument("--only", choices=["fp64", "fp32", "surrogate", "adjoint"], default=None,
                     help="run only that path's step (a small case for profiling); prints its timing")
+    ap.add_argument("--target", default="residual", choices=["residual", "envelope", "asinh"],
+                    help="with --only surrogate: the surrogate's target")
     ap.add_argument("--law", default="bench", choices=["bench", "in", "lowx", "highq", "lowq", "lowx_highq",
                                                        "lowx_lowq"],
                     help="with --only fp64/fp32: the benchmark's query law, or points of one class only")

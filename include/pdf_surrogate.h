@@ -27,8 +27,8 @@
  *                      uniform 257 x 257 table of the FP64 interpolator (FP32,
  *                      built when the surrogate is made), whose own error is
  *                      ~1e-3 of E_f; the network's BF16 error then acts on a
- *                      term of that size.  Evaluation writes B_f, then adds
- *                      the network's term.
+ *                      term of that size.  The inference kernel forms B_f
+ *                      from its four table nodes in its epilogue.
  * Products run on the BF16 tensor cores (tcgen05) with FP32 accumulation;
  * BF16 weight copies are made from FP32 master weights.
  * The parameter vector is flat FP32: W1 [128][32], b1 [128], W2..W4

@@ -294,8 +294,9 @@ __global__ void k_targets(SurrConst c, const double *x, const double *q2, const 
   }
 }
 
-// The residual target's base B_f for n points, into outf [n][nf] (FP32) or
-// outd (FP64); the inference kernel then adds eps E_f y_f.
+// The residual target's base B_f alone for n points, into outf [n][nf] (FP32)
+// or outd (FP64): the error map's measure of the base (the inference kernel
+// forms B_f itself, with the same arithmetic).
 __global__ void k_base(SurrConst c, const double *x, const double *q2, long long n, float *outf, double *outd) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n * c.nf) return;
@@ -654,6 +655,23 @@ k_infer(SurrConst c, const bf16 *__restrict__ wg, const float *__restrict__ para
         tmem_st16(tA + lanes + c0 / 2 + 16, r1);
         asm volatile("tcgen05.wait::st.sync.aligned;");
       } else {  // outputs of this half's eight flavours, staged as whole rows
+        // residual target: the base's four corners for this half's eight
+        // flavours (loads issued before the accumulator and envelope waits)
+        float4 bc[8];
+        float bu0 = 0.f, bu1 = 0.f;
+        if (c.target == PDF_SURR_RESIDUAL) {
+          const float u0 = fminf(fmaxf((z0 + 1.f) * (0.5f * BASEN), 0.f), (float)BASEN);
+          const float u1 = fminf(fmaxf((z1 + 1.f) * (0.5f * BASEN), 0.f), (float)BASEN);
+          const int bi = min((int)u0, BASEN - 1), bj = min((int)u1, BASEN - 1);
+          bu0 = u0 - (float)bi;
+          bu1 = u1 - (float)bj;
+          const float4 *r0 = reinterpret_cast<const float4 *>(c.baset + ((size_t)bi * (BASEN + 1) + bj) * SOUT + 8 * half);
+          const float4 *r1 = r0 + (BASEN + 1) * SOUT / 4;
+          bc[0] = __ldg(r0); bc[1] = __ldg(r0 + 1);                        // (i, j)
+          bc[2] = __ldg(r0 + SOUT / 4); bc[3] = __ldg(r0 + SOUT / 4 + 1);  // (i, j + 1)
+          bc[4] = __ldg(r1); bc[5] = __ldg(r1 + 1);                        // (i + 1, j)
+          bc[6] = __ldg(r1 + SOUT / 4); bc[7] = __ldg(r1 + SOUT / 4 + 1);  // (i + 1, j + 1)
+        }
         float v[8];
         tmem_ld8(tD + lanes + 8 * half, v);
         float o[8];
@@ -666,9 +684,22 @@ k_infer(SurrConst c, const bf16 *__restrict__ wg, const float *__restrict__ para
           const float4 b1 = *reinterpret_cast<const float4 *>(er + (((5 + 2 * half) ^ (t & 7)) << 2));
           const float ea[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
           const float eb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-          const float sc = c.target == PDF_SURR_RESIDUAL ? kResEps : 1.f;
+          if (c.target == PDF_SURR_RESIDUAL) {
+            // B + eps E y, B bilinear as base_at computes it (base alone: B)
+            const float v00[8] = {bc[0].x, bc[0].y, bc[0].z, bc[0].w, bc[1].x, bc[1].y, bc[1].z, bc[1].w};
+            const float v01[8] = {bc[2].x, bc[2].y, bc[2].z, bc[2].w, bc[3].x, bc[3].y, bc[3].z, bc[3].w};
+            const float v10[8] = {bc[4].x, bc[4].y, bc[4].z, bc[4].w, bc[5].x, bc[5].y, bc[5].z, bc[5].w};
+            const float v11[8] = {bc[6].x, bc[6].y, bc[6].z, bc[6].w, bc[7].x, bc[7].y, bc[7].z, bc[7].w};
 #pragma unroll
-          for (int i = 0; i < 8; i++) o[i] = base_only ? 0.f : sc * expf(ea[i] + fr * (eb[i] - ea[i])) * v[i];
+            for (int i = 0; i < 8; i++) {
+              const float lo = fmaf(bu1, v01[i] - v00[i], v00[i]), hi = fmaf(bu1, v11[i] - v10[i], v10[i]);
+              const float bv = fmaf(bu0, hi - lo, lo);
+              o[i] = base_only ? bv : bv + kResEps * expf(ea[i] + fr * (eb[i] - ea[i])) * v[i];
+            }
+          } else {
+#pragma unroll
+            for (int i = 0; i < 8; i++) o[i] = expf(ea[i] + fr * (eb[i] - ea[i])) * v[i];
+          }
         } else {
 #pragma unroll
           for (int i = 0; i < 8; i++) o[i] = sscale[8 * half + i] * sinhf(v[i]);
@@ -679,22 +710,15 @@ k_infer(SurrConst c, const bf16 *__restrict__ wg, const float *__restrict__ para
         asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(kGT));
         const long long rows = min(128LL, n - p0);
         const int cnt = (int)rows * nf;
-        const bool add = c.target == PDF_SURR_RESIDUAL;  // the base is already in the output
         if (outf) {
           float *dst = outf + p0 * nf;
           int i0 = 0;
           if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
-            for (int i = gt; i < cnt / 4; i += kGT) {
-              float4 w = reinterpret_cast<const float4 *>(O)[i];
-              if (add) {
-                const float4 b = __ldcs(reinterpret_cast<const float4 *>(dst) + i);
-                w = make_float4(b.x + w.x, b.y + w.y, b.z + w.z, b.w + w.w);
-              }
-              __stcs(reinterpret_cast<float4 *>(dst) + i, w);
-            }
+            for (int i = gt; i < cnt / 4; i += kGT)
+              __stcs(reinterpret_cast<float4 *>(dst) + i, reinterpret_cast<const float4 *>(O)[i]);
             i0 = cnt & ~3;
           }
-          for (int i = i0 + gt; i < cnt; i += kGT) __stcs(dst + i, add ? __ldcs(dst + i) + O[i] : O[i]);
+          for (int i = i0 + gt; i < cnt; i += kGT) __stcs(dst + i, O[i]);
         }
         if (outd) {
           double *dst = outd + p0 * nf;
@@ -702,16 +726,11 @@ k_infer(SurrConst c, const bf16 *__restrict__ wg, const float *__restrict__ para
           if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
             for (int i = gt; i < cnt / 2; i += kGT) {
               const float2 w = reinterpret_cast<const float2 *>(O)[i];
-              double2 d = make_double2((double)w.x, (double)w.y);
-              if (add) {
-                const double2 b = __ldcs(reinterpret_cast<const double2 *>(dst) + i);
-                d = make_double2(b.x + d.x, b.y + d.y);
-              }
-              __stcs(reinterpret_cast<double2 *>(dst) + i, d);
+              __stcs(reinterpret_cast<double2 *>(dst) + i, make_double2((double)w.x, (double)w.y));
             }
             i0 = cnt & ~1;
           }
-          for (int i = i0 + gt; i < cnt; i += kGT) __stcs(dst + i, add ? __ldcs(dst + i) + (double)O[i] : (double)O[i]);
+          for (int i = i0 + gt; i < cnt; i += kGT) __stcs(dst + i, (double)O[i]);
         }
       }
     }
@@ -1466,10 +1485,6 @@ static int launch_infer(const pdf_surrogate *s, const double *x, const double *q
   long long tiles = ((long long)n + 127) / 128;
   long long blocks = (tiles + TG - 1) / TG;
   if (blocks > sms) blocks = sms;
-  if (s->c.target == PDF_SURR_RESIDUAL) {
-    const long long items = (long long)n * s->nf;
-    k_base<<<(unsigned)((items + 255) / 256), 256, 0, st>>>(s->c, x, q2, (long long)n, outf, outd);
-  }
   k_infer<<<(unsigned)blocks, kTcThreads, kTcSmem, st>>>(s->c, s->wbf, s->params, s->L, x, q2, (long long)n, outf,
                                                           outd, mask, nfb, idx, s->tc_err);
   return check_launch("surrogate inference");
