@@ -399,6 +399,9 @@ def cpu_baseline_leg(g, x, q2, out_gpu, a_gpu, x32, q32, out32, target_s=10.0):
     # crossing of xf (|oracle| below 1e-3 of the data mass)
     far = ~fl & (np.abs(v) >= 1e-3 * s)
     eq1 = np.where(far, np.abs(out_gpu[idx] - v) / (np.abs(v) + 1e-16), 0.0)
+    xs, qs = x[idx], q2[idx]
+    ingrid = (xs >= g.x_knots[0]) & (q2[idx] >= g.q2_knots[0]) & (qs <= g.q2_knots[-1])
+    above = eq1 > 1e-12
     aerr = float((np.abs(a_gpu[idx] - av) / np.maximum(np.abs(av), asv)).max())
     # FP32 path against the oracle at the float inputs (a sub-sample)
     k = min(m, 200_000)
@@ -411,6 +414,11 @@ def cpu_baseline_leg(g, x, q2, out_gpu, a_gpu, x32, q32, out32, target_s=10.0):
              "fp64_eq1_max_per_flavour": [float(e) for e in eq1.max(axis=0)],
              "eq1": "|gpu - oracle| / (|oracle| + 1e-16), paper eq. (1), per flavour",
              "eq1_near_zero_excluded": int((~fl & ~far).sum()),
+             "eq1_max_in_grid": float(eq1[ingrid].max()) if ingrid.any() else 0.0,
+             "eq1_max_continued": float(eq1[~ingrid].max()) if (~ingrid).any() else 0.0,
+             "eq1_outputs_above_1e-12": int(above.sum()),
+             "eq1_above_1e-12_median_mass_over_value": float(np.median((s / np.maximum(np.abs(v), 1e-300))[above]))
+             if above.any() else None,
              "fp32_max_scaled_err_per_flavour": [float(e) for e in np.nanmax(err32, axis=0)],
              "scaled_err": "|gpu - oracle| / max(|oracle|, sum|w f|), on the sampled points",
              "marginal_excluded": int(fl.sum()), "sample_points": m})
@@ -552,16 +560,22 @@ def members_leg(args, dev, world, sync, rank):
     xd, qd = torch.from_numpy(x).to(dev), torch.from_numpy(q2).to(dev)
     rows = []
     for nrep in sorted(TABLE2):
-        G = P.pdf_load_grid(g0, member_values=vals[:nrep])
+        sync()
+        t0 = time.perf_counter()
+        G = P.pdf_load_grid(g0, member_values=vals[:nrep])  # host checks, copy, staging kernels (synchronous)
+        load_ms = (time.perf_counter() - t0) * 1e3
         out = torch.empty((nrep, len(x), g0.nflav), dtype=torch.float64, device=dev)
         ms = run_timed(lambda: P.xfxq2_all_members(G, xd, qd, out=out), max(5, args.steps // 5), 3, world, sync)
         evals = nrep * len(x) * g0.nflav
         rows.append({"n_rep": nrep, "evals": evals, "ms": ms, "evals_per_s": world * evals / (ms * 1e-3),
+                     "load_ms": load_ms,
                      "paper_gpu_s": TABLE2[nrep], "paper_gpu_evals_per_s": evals / TABLE2[nrep]})
         del G, out
     return {"rows": rows, "workload": "13 flavours x N_rep members x 2415 x points (log-spaced in [1e-9, 1)), "
             "Q = 1.65 GeV; members perturb the synthetic set's flavour parameters",
-            "paper_hardware": "PDFFlow v1.0 on TITAN V or RTX 2080 Ti (system P1); context, not the target"}
+            "paper_hardware": "PDFFlow v1.0 on TITAN V or RTX 2080 Ti (system P1); context, not the target",
+            "load_ms": "pdf_load_grid of the N_rep-member set (host validation, host-to-device copy, staging "
+                       "kernels), wall clock, once per set; ms is one evaluation call on the loaded set"}
 
 
 def mc_leg(G, world, sync, rank):
