@@ -75,7 +75,7 @@ def fp32_bound(g, x, q2):
     with np.errstate(divide="ignore", invalid="ignore"):
         lr = np.abs(np.log(np.asarray(q2, dtype=np.float64) / g.q2_knots[0]))
     lowq = (cls == 3) | (cls == 5)
-    units = FP32_IN + FP32_RULE * rules + np.where(lowq, FP32_LOWQ_LOG * np.nan_to_num(lr), 0.0)
+    units = FP32_IN + FP32_RULE * rules + FP32_LOWQ_LOG * np.where(lowq, lr, 0.0)
     return units * U32
 
 
