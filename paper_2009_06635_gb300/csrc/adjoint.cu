@@ -265,10 +265,11 @@ __device__ __forceinline__ void vjp_ingrid_ff(const GridView &g, const Site64 &X
 #pragma unroll
     for (int m2 = 0; m2 < 8; m2++) {
       const float4 b = __ldg(cb + (size_t)m2 * g.nfp + f);
-      ff_acc(th, tl, wt[2 * m2], b.x, b.y);
-      ff_acc(uh, ul, wu[2 * m2], b.x, b.y);
-      ff_acc(th, tl, wt[2 * m2 + 1], b.z, b.w);
-      ff_acc(uh, ul, wu[2 * m2 + 1], b.z, b.w);
+      // b = {hi_m, hi_m+1, lo_m, lo_m+1}, m = 2 m2
+      ff_acc(th, tl, wt[2 * m2], b.x, b.z);
+      ff_acc(uh, ul, wu[2 * m2], b.x, b.z);
+      ff_acc(th, tl, wt[2 * m2 + 1], b.y, b.w);
+      ff_acc(uh, ul, wu[2 * m2 + 1], b.y, b.w);
     }
     sx = fma(c, f2d(th) + f2d(tl), sx);
     sq = fma(c, f2d(uh) + f2d(ul), sq);

@@ -263,9 +263,11 @@ __global__ void k_coef(Stage S) {
   // the flavour stride nfp (a multiple of 8) makes each row block whole lines
   float *o32 = S.coef32 + (size_t)(gid / S.nf) * 16 * S.nfp + (size_t)f * 4;
   // float-float copy flavour-minor by pairs of control points,
-  // [cell][m / 2][flavour][m % 2]: one 16-byte load per pair and flavour, and
-  // the lanes of one load (consecutive flavours of a point) read consecutive bytes
-  float2 *off = S.coefff + (size_t)(gid / S.nf) * 16 * S.nfp + (size_t)f * 2;
+  // [cell][m / 2][flavour][4] = {hi_m, hi_m+1, lo_m, lo_m+1} (m even): one
+  // 16-byte load per pair and flavour, the lanes of one load (consecutive
+  // flavours of a point) read consecutive bytes, and the two high (low) parts
+  // land in one register pair for packed f32x2 arithmetic
+  float *off = reinterpret_cast<float *>(S.coefff + (size_t)(gid / S.nf) * 16 * S.nfp) + (size_t)f * 4;
   bool bad = false;
   for (int m = 0; m < 16; m++) {
     o[m] = c[m];
@@ -274,7 +276,8 @@ __global__ void k_coef(Stage S) {
     // while |c| stays well inside the float exponent range
     float hi = __double2float_rn(c[m]);
     float lo = __double2float_rn(c[m] - (double)hi);
-    off[(size_t)(m >> 1) * 2 * S.nfp + (m & 1)] = make_float2(hi, lo);
+    off[(size_t)(m >> 1) * 4 * S.nfp + (m & 1)] = hi;
+    off[(size_t)(m >> 1) * 4 * S.nfp + 2 + (m & 1)] = lo;
     double a = fabs(c[m]);
     if (a != 0.0 && (a < 1e-30 || a > 1e30)) bad = true;
   }

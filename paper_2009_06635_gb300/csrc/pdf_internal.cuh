@@ -15,10 +15,12 @@
 //          one load instruction over the flavours of a point reads
 //          consecutive rows of as few lines as possible.
 //   coefff the same control points as float-float pairs (hi, lo), laid out
-//          [nqc+1][nx][8][nfp][2] (pairs of control points m, m+1 of a
-//          flavour adjacent; flavour stride nfp as for coef32): one 16-byte
-//          load per pair, and one load instruction over the flavours of a
-//          point reads consecutive bytes of whole lines.
+//          [nqc+1][nx][8][nfp][4]: control points m, m+1 (m even) of a
+//          flavour as {hi_m, hi_m+1, lo_m, lo_m+1} (flavour stride nfp as for
+//          coef32): one 16-byte load per pair, one load instruction over the
+//          flavours of a point reads consecutive bytes of whole lines, and
+//          the two high (low) parts share a register pair for packed f32x2
+//          arithmetic.
 //   xk/q2k raw knots, searched as integer bit patterns (positive doubles
 //          order like their bits), so a cell choice never depends on a log.
 //   xcell  per x cell {ln x_i, 1/d, ln x_{i+1}, 0}, d = ln x_{i+1} - ln x_i;
@@ -77,7 +79,7 @@ struct GridView {
   double *vals;               // [nrows][nx][nf] device copy of the knot values
   const double *coef;         // [nqc + 1][nx][nf][16]
   const float *coef32;        // [nqc + 1][nx][4][nfp][4]: row l of every flavour, then the next row
-  const float2 *coefff;       // [nqc + 1][nx][8][nfp][2] float-float (hi, lo) copy of coef
+  const float2 *coefff;       // [nqc + 1][nx][8][nfp][4] float-float copy of coef (see above)
   int ff;                     // 1 if every control point is safe for float-float
   int nmem;                   // members (replicas) sharing the knots; member m's
   size_t mstride;             // control points start m * mstride elements further

@@ -101,9 +101,11 @@ __device__ __forceinline__ PointSites<double> sites(const GridView &g, const lon
 // 1 - t keeps its relative precision: where xf varies steeply (x -> 1, where
 // (1 - x)^b makes the value sensitive to t) the position is still good to a
 // float ulp.  No absolute logarithm of x is rounded to FP32.
+// c: the cell's 8-float row of the FP32 cell table (shared memory in the
+// evaluation kernel, which stages the table per block).
 __device__ __forceinline__ void cell_pos32(const float *c, float v, float &t, float &ts) {
-  const float4 a = __ldg(reinterpret_cast<const float4 *>(c));
-  const float4 b = __ldg(reinterpret_cast<const float4 *>(c) + 1);
+  const float4 a = *reinterpret_cast<const float4 *>(c);
+  const float4 b = *(reinterpret_cast<const float4 *>(c) + 1);
   if (v < b.w) {
     t = (log1pf((v - a.x) * a.y) + a.z) * a.w;
     ts = 1.f - t;
@@ -113,8 +115,11 @@ __device__ __forceinline__ void cell_pos32(const float *c, float v, float &t, fl
   }
 }
 
-__device__ __forceinline__ PointSites<float> sites(const GridView &g, const int *xkeys,
-                                                   const int *qkeys, float x, float q2) {
+// xcell, qcell, rowqc: the grid's xcell32, qcell32 and row_qc tables (or
+// copies of them in shared memory).
+__device__ __forceinline__ PointSites<float> sites(const GridView &g, const int *xkeys, const int *qkeys,
+                                                   const float *xcell, const float *qcell, const int *rowqc,
+                                                   float x, float q2) {
   PointSites<float> r;
   r.xc0 = r.xc1 = r.qc0 = r.qc1 = 0;
   r.t0 = r.t1 = r.u0 = r.u1 = r.px = r.pq = r.lr = 0.f;
@@ -125,15 +130,15 @@ __device__ __forceinline__ PointSites<float> sites(const GridView &g, const int 
   if (!lowx) {
     int i = search_cell(xkeys, g.nx, g.xstep, __float_as_int(x));
     r.xc0 = i;
-    cell_pos32(g.xcell32 + 8 * i, x, r.t0, r.ts0);
+    cell_pos32(xcell + 8 * i, x, r.t0, r.ts0);
   } else {
     r.xc1 = 1;
     r.px = logf(x * g.x0inv32) * g.idx0_32;
   }
   if (!lowq && !highq) {
     int j = search_cell(qkeys, g.nrows, g.qstep, __float_as_int(q2));
-    r.qc0 = g.row_qc[j];
-    cell_pos32(g.qcell32 + 8 * j, q2, r.u0, r.us0);
+    r.qc0 = rowqc[j];
+    cell_pos32(qcell + 8 * j, q2, r.u0, r.us0);
   } else if (highq) {
     r.qc0 = g.nqc;
     r.qc1 = g.top_qc;
@@ -161,12 +166,13 @@ __device__ __forceinline__ double alphas_eval(const GridView &g, const long long
   double u = (lq - c[0]) * c[1];
   return fma(fma(fma(c[5], u, c[4]), u, c[3]), u, c[2]);
 }
-__device__ __forceinline__ float alphas_eval(const GridView &g, const int *akeys, float q2) {
+// acell: the grid's acell32 table (or a copy in shared memory).
+__device__ __forceinline__ float alphas_eval(const GridView &g, const int *akeys, const float *acell, float q2) {
   if (!((q2 > 0.f) && (q2 < INFINITY))) return NAN;
   if (q2 < g.aq2lo_ru) return g.as_lo32;
   if (q2 > g.aq2hi_rd) return g.as_hi32;
   int j = search_cell(akeys, g.na, g.astep, __float_as_int(q2));
-  const float *c = g.acell32 + 6 * j;
+  const float *c = acell + 6 * j;
   float u = log1pf(fmaf(q2, c[0], -1.f)) * c[1];
   return fmaf(fmaf(fmaf(c[5], u, c[4]), u, c[3]), u, c[2]);
 }

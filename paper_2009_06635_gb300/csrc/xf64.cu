@@ -59,31 +59,37 @@ struct alignas(16) Queue64 {
   unsigned idx[kFar][64];
 };
 
-// sum_m w_m b_m with w (hi, lo) from the record and b (hi, lo) from the
-// float-float control points (c: the item's first pair; pairs of control
-// points nf float4 apart): exact products, TwoSum accumulation, the cross
-// terms and the rounding errors gathered in a second float.
-__device__ __forceinline__ double dot_ff16(const float4 *c, int nf, const float2 *w) {
-  float sh = 0.f, sl = 0.f;
+// sum_m w_m b_m with w from the record and b from the float-float control
+// points (c: the item's first pair of control points; pairs nf float4
+// apart), as two chains run side by side in packed f32x2 operations (GB300
+// issues one instruction for both halves): chain 0 takes the even control
+// points m = 2 m2, chain 1 the odd ones.  Both the record row and the control
+// points hold a pair as {hi_even, hi_odd, lo_even, lo_odd}, so the halves of
+// each operand sit in one register pair.  Each chain adds exact products by
+// TwoSum and gathers the cross terms and rounding errors in a second float;
+// the chains are merged by one more TwoSum at the end.
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ double dot_ff16(const float4 *c, int nf, const float4 *w) {
+  float2 sh = make_float2(0.f, 0.f), sl = make_float2(0.f, 0.f);
 #pragma unroll
   for (int m2 = 0; m2 < 8; m2++) {
-    const float4 ww = *reinterpret_cast<const float4 *>(w + 2 * m2);
+    const float4 ww = w[m2];
     const float4 bb = __ldg(c + (size_t)m2 * nf);
-#pragma unroll
-    for (int half = 0; half < 2; half++) {
-      const float bh = half ? bb.z : bb.x, bl = half ? bb.w : bb.y;
-      const float wh = half ? ww.z : ww.x, wl = half ? ww.w : ww.y;
-      const float ph = __fmul_rn(wh, bh);
-      float pe = __fmaf_rn(wh, bh, -ph);
-      pe = __fmaf_rn(wh, bl, __fmaf_rn(wl, bh, pe));
-      const float t = __fadd_rn(sh, ph);
-      const float bp = __fsub_rn(t, sh);
-      const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bp)), __fsub_rn(ph, bp));
-      sh = t;
-      sl = __fadd_rn(sl, __fadd_rn(err, pe));
-    }
+    const float2 wh = make_float2(ww.x, ww.y), wl = make_float2(ww.z, ww.w);
+    const float2 bh = make_float2(bb.x, bb.y), bl = make_float2(bb.z, bb.w);
+    const float2 ph = __fmul2_rn(wh, bh);
+    float2 pe = __ffma2_rn(wh, bh, neg2(ph));
+    pe = __ffma2_rn(wh, bl, __ffma2_rn(wl, bh, pe));
+    const float2 t = __fadd2_rn(sh, ph);
+    const float2 bp = __fadd2_rn(t, neg2(sh));
+    const float2 err = __fadd2_rn(__fadd2_rn(sh, neg2(__fadd2_rn(t, neg2(bp)))), __fadd2_rn(ph, neg2(bp)));
+    sh = t;
+    sl = __fadd2_rn(sl, __fadd2_rn(err, pe));
   }
-  return f2d(sh) + f2d(sl);
+  const float s = __fadd_rn(sh.x, sh.y);
+  const float bp = __fsub_rn(s, sh.x);
+  const float e = __fadd_rn(__fsub_rn(sh.x, __fsub_rn(s, bp)), __fsub_rn(sh.y, bp));
+  return f2d(s) + f2d(__fadd_rn(__fadd_rn(sl.x, sl.y), e));
 }
 
 // ---- FP64 site evaluation ---------------------------------------------------
@@ -137,7 +143,8 @@ __device__ __forceinline__ double site_t(const double *c, const Rec64 &R, int p,
 // pairs, W2[0..3] Bx0, [4..7] Bx1, [8..11] Bq0, [12..15] Bq1, and px, pq, lr
 // as float pairs in the same 8-byte slots.  Sites contract the float-float
 // control points (coefff: pair m2 of control points m = 2 m2, 2 m2 + 1 of a
-// flavour as one float4 {hi, lo, hi, lo}; control point m = 4 l + k).
+// flavour as one float4 {hi_m, hi_m+1, lo_m, lo_m+1} with m = 2 m2;
+// control point m = 4 l + k).
 __device__ __forceinline__ ff2 ffv(const double &d) {
   const float2 v = reinterpret_cast<const float2 &>(d);
   return {v.x, v.y};
@@ -149,8 +156,8 @@ __device__ __forceinline__ ff2 ffsite_u(const float4 *c, int nfp, const float2 *
   float sh = 0.f, sl = 0.f;
 #pragma unroll
   for (int l = 0; l < 4; l++) {
-    const float4 v = __ldg(c + (size_t)(2 * l) * nfp);
-    ff_acc(sh, sl, ffw(bq[l]), v.x, v.y);
+    const float4 v = __ldg(c + (size_t)(2 * l) * nfp);  // control point m = 4 l: the pair's even one
+    ff_acc(sh, sl, ffw(bq[l]), v.x, v.z);
   }
   return ff_norm(sh, sl);
 }
@@ -158,10 +165,10 @@ __device__ __forceinline__ ff2 ffsite_u(const float4 *c, int nfp, const float2 *
 __device__ __forceinline__ ff2 ffsite_t(const float4 *c, int nfp, const float2 *bx) {
   const float4 v0 = __ldg(c), v1 = __ldg(c + nfp);
   float sh = 0.f, sl = 0.f;
-  ff_acc(sh, sl, ffw(bx[0]), v0.x, v0.y);
-  ff_acc(sh, sl, ffw(bx[1]), v0.z, v0.w);
-  ff_acc(sh, sl, ffw(bx[2]), v1.x, v1.y);
-  ff_acc(sh, sl, ffw(bx[3]), v1.z, v1.w);
+  ff_acc(sh, sl, ffw(bx[0]), v0.x, v0.z);
+  ff_acc(sh, sl, ffw(bx[1]), v0.y, v0.w);
+  ff_acc(sh, sl, ffw(bx[2]), v1.x, v1.z);
+  ff_acc(sh, sl, ffw(bx[3]), v1.y, v1.w);
   return ff_norm(sh, sl);
 }
 // general: sum_l Bq[l] sum_k Bx[k] b[l][k]
@@ -176,7 +183,7 @@ __device__ __forceinline__ ff2 ffsite_tu(const float4 *c, int nfp, const float2 
 }
 __device__ __forceinline__ ff2 ffknot(const float4 *c) {
   const float4 v = __ldg(c);
-  return {v.x, v.y};
+  return {v.x, v.z};
 }
 
 // A rule's result: a float pair, or (out of the pairs' range) a double.
@@ -295,7 +302,7 @@ __device__ __forceinline__ double eval_item64(const GridView &g, const Rec64 &R,
   if (cls == C_INF)
     return dot_ff16(reinterpret_cast<const float4 *>(g.coefff + (size_t)m * g.mstride_ff +
                                                      ((size_t)R.qc0[p] * g.nx + R.xc0[p]) * 16 * g.nfp) + col,
-                    g.nfp, reinterpret_cast<const float2 *>(R.W[p]));
+                    g.nfp, reinterpret_cast<const float4 *>(R.W[p]));
   if (cls == C_IN) return dot_w16(C(0, 0), R, p);
   if (cls == C_INVALID) return NAN;
   if (g.ff) return eval_far_ff(g, R, p, col, m, FT);
@@ -376,12 +383,14 @@ __device__ __forceinline__ void store_point(Rec64 &R, int slot, const PointSites
     ff2 bx[4], bq[4];
     ff_bernstein(ps.t0, ps.ts0, bx);
     ff_bernstein(ps.u0, ps.us0, bq);
+    // pairs of products m = 2 m2, 2 m2 + 1 as {hi, hi, lo, lo} (dot_ff16)
+    float4 *row = reinterpret_cast<float4 *>(R.W[slot]);
 #pragma unroll
     for (int l = 0; l < 4; l++)
 #pragma unroll
-      for (int k = 0; k < 4; k++) {
-        const ff2 w = ff_mul(bx[k], bq[l]);
-        reinterpret_cast<float2 *>(R.W[slot])[l * 4 + k] = make_float2(w.h, w.l);
+      for (int k = 0; k < 4; k += 2) {
+        const ff2 w0 = ff_mul(bx[k], bq[l]), w1 = ff_mul(bx[k + 1], bq[l]);
+        row[(l * 4 + k) >> 1] = make_float4(w0.h, w1.h, w0.l, w1.l);
       }
     return;
   }

@@ -2,15 +2,20 @@
 // and the C entry points of both precisions (FP64 evaluation: xf64.cu).
 //
 // One warp owns a tile of 32 query points (16 events in the Monte Carlo
-// layout).  Phase 1 (lane = point): read x and Q^2 (coalesced), classify
-// against the grid edges with exact float thresholds, search the cells on the
-// raw bit patterns (knots in shared memory), record the Bernstein weights of
-// the patch sites (one slot-major row per point) and the continuation
-// parameters; points are ordered by class so that lanes of one instruction
-// take the same branch.  Phase 2 (lane = item (point, column), consecutive
-// items are consecutive outputs): one lane evaluates a whole item, four
-// float4 rows of the cell's control points against weights read as two
-// 16-byte shared loads, so one instruction covers 32 items.
+// layout).  Each block first copies the grid's knot keys and its FP32 cell
+// tables (x cells, Q cells, the row-to-cell map, alpha_s cells) into shared
+// memory, so the per-point table reads of phase 1 stay off the global path.
+// Phase 1 (lane = point): read x and Q^2 (coalesced), classify against the
+// grid edges with exact float thresholds, search the cells on the raw bit
+// patterns, record the Bernstein weights of the patch sites (one slot-major
+// row per point) and the continuation parameters; points are ordered by
+// class so that lanes of one instruction take the same branch.  Phase 2
+// (lane = item (point, column), consecutive items are consecutive outputs):
+// one lane evaluates a whole item, four float4 rows of the cell's control
+// points against weights read as two 16-byte shared loads, so one
+// instruction covers 32 items.  (A group of 16 lanes per point, so that one
+// load instruction reads whole row blocks of two points, measured 7% slower
+// at 1e7 points: fewer L1 wavefronts, more instructions.)
 #include <cmath>
 #include <type_traits>
 
@@ -95,6 +100,25 @@ __device__ __forceinline__ void store_point32(Rec32 &R, int slot, const PointSit
   row[3] = make_float4(bq1[0], bq1[1], bq1[2], bq1[3]);
 }
 
+// Byte offsets of the kernel's shared-memory regions (every region starts on
+// a 16-byte boundary).
+struct Smem32 {
+  size_t xkeys, qkeys, akeys, xcell, qcell, rowqc, acell, recs, total;
+};
+__host__ __device__ inline Smem32 smem32_layout(const GridView &g) {
+  Smem32 L;
+  L.xkeys = 0;
+  L.qkeys = L.xkeys + keys_bytes(g.nx, 4);
+  L.akeys = L.qkeys + keys_bytes(g.nrows, 4);
+  L.xcell = L.akeys + keys_bytes(g.na, 4);
+  L.qcell = L.xcell + (size_t)32 * g.nx;
+  L.rowqc = L.qcell + (size_t)32 * g.nrows;
+  L.acell = L.rowqc + keys_bytes(g.nrows, 4);
+  L.recs = L.acell + keys_bytes(6 * g.na, 4);
+  L.total = L.recs + kWarps * sizeof(Rec32);
+  return L;
+}
+
 // MODE_POINTS: points xa[n], qa[n]; out[n][ncol] for columns col0..col0+ncol-1;
 //              as_out[n] (alpha_s) when not null.
 // MODE_MC:     events xa[n] (x1), xb[n] (x2), Q^2 = x1 x2 s; out[n][2 nf + 1].
@@ -103,14 +127,26 @@ __global__ void __launch_bounds__(kThreads, 3)
 k_xf32(GridView g, const float *__restrict__ xa, const float *__restrict__ qa, const float *__restrict__ xb,
        float s, long long n, int col0, int ncol, float *__restrict__ out, float *__restrict__ as_out) {
   extern __shared__ __align__(16) unsigned char smem[];
-  int *xkeys = reinterpret_cast<int *>(smem);
-  int *qkeys = reinterpret_cast<int *>(smem + keys_bytes(g.nx, 4));
-  int *akeys = reinterpret_cast<int *>(smem + keys_bytes(g.nx, 4) + keys_bytes(g.nrows, 4));
-  size_t rec_off = keys_bytes(g.nx, 4) + keys_bytes(g.nrows, 4) + keys_bytes(g.na, 4);
-  Rec32 *recs = reinterpret_cast<Rec32 *>(smem + rec_off);
+  const Smem32 L = smem32_layout(g);
+  int *xkeys = reinterpret_cast<int *>(smem + L.xkeys);
+  int *qkeys = reinterpret_cast<int *>(smem + L.qkeys);
+  int *akeys = reinterpret_cast<int *>(smem + L.akeys);
+  float *xcell = reinterpret_cast<float *>(smem + L.xcell);
+  float *qcell = reinterpret_cast<float *>(smem + L.qcell);
+  int *rowqc = reinterpret_cast<int *>(smem + L.rowqc);
+  float *acell = reinterpret_cast<float *>(smem + L.acell);
+  Rec32 *recs = reinterpret_cast<Rec32 *>(smem + L.recs);
+  const bool want_as = MODE == MODE_MC || as_out;
   load_keys<float>(g, xkeys, 0);
   load_keys<float>(g, qkeys, 1);
-  if (MODE == MODE_MC || as_out) load_keys<float>(g, akeys, 2);
+  if (want_as) load_keys<float>(g, akeys, 2);
+  for (int i = threadIdx.x; i < 2 * g.nx; i += blockDim.x)
+    reinterpret_cast<float4 *>(xcell)[i] = __ldg(reinterpret_cast<const float4 *>(g.xcell32) + i);
+  for (int i = threadIdx.x; i < 2 * g.nrows; i += blockDim.x)
+    reinterpret_cast<float4 *>(qcell)[i] = __ldg(reinterpret_cast<const float4 *>(g.qcell32) + i);
+  for (int i = threadIdx.x; i < g.nrows; i += blockDim.x) rowqc[i] = __ldg(g.row_qc + i);
+  if (want_as)
+    for (int i = threadIdx.x; i < 6 * g.na; i += blockDim.x) acell[i] = __ldg(g.acell32 + i);
   __syncthreads();
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -121,7 +157,6 @@ k_xf32(GridView g, const float *__restrict__ xa, const float *__restrict__ qa, c
   const long long ntiles = (n + per_tile - 1) / per_tile;
   const long long nwarps = (long long)gridDim.x * kWarps;
   const unsigned lt = (1u << lane) - 1u;
-  const int dp = 32 / nc, dc = 32 - dp * nc;
 
   for (long long tile = (long long)blockIdx.x * kWarps + warp; tile < ntiles; tile += nwarps) {
     const long long e0 = tile * per_tile;
@@ -147,11 +182,11 @@ k_xf32(GridView g, const float *__restrict__ xa, const float *__restrict__ qa, c
     }
     PointSites<float> ps;
     ps.cls = -1;
-    if (present) ps = sites(g, xkeys, qkeys, x, q2);
+    if (present) ps = sites(g, xkeys, qkeys, xcell, qcell, rowqc, x, q2);
     unsigned inv = __ballot_sync(0xffffffffu, ps.cls == C_INVALID);
     if (lane == 0 && inv) atomicAdd(g.invalid, (unsigned long long)__popc(inv));
-    if (MODE == MODE_MC && present && (lane & 1) == 0) out[ob + 2 * g.nf] = alphas_eval(g, akeys, q2);
-    if (MODE == MODE_POINTS && present && as_out) as_out[e0 + lane] = alphas_eval(g, akeys, q2);
+    if (MODE == MODE_MC && present && (lane & 1) == 0) out[ob + 2 * g.nf] = alphas_eval(g, akeys, acell, q2);
+    if (MODE == MODE_POINTS && present && as_out) as_out[e0 + lane] = alphas_eval(g, akeys, acell, q2);
     // order the points by class (counting sort over the warp); in-grid points first
     int slot = 0, base = 0, nin = 0;
 #pragma unroll
@@ -166,6 +201,7 @@ k_xf32(GridView g, const float *__restrict__ xa, const float *__restrict__ qa, c
     __syncwarp();
 
     // ---- phase 2: items (point, column) ----
+    const int dp = 32 / nc, dc = 32 - dp * nc;
     int p = lane / nc, c = lane - (lane / nc) * nc;
     for (int k = lane; k < np * nc; k += 32) {
       out[R.ob[p] + c] = p < nin ? eval_in32(g, R, p, cbase + c) : eval_item32(g, R, p, cbase + c);
@@ -198,7 +234,7 @@ __global__ void __launch_bounds__(kThreads) k_alphas(GridView g, const T *__rest
     if ((threadIdx.x & 31) == 0 && inv) atomicAdd(g.invalid, (unsigned long long)__popc(inv));
     if (present) {
       if constexpr (sizeof(T) == 8) out[i] = alphas_eval(g, akeys, q2, bad ? 0.0 : tlog(q2, LogTabs{g.tlogtab, g.tloghtab}));
-      else out[i] = alphas_eval(g, akeys, q2);
+      else out[i] = alphas_eval(g, akeys, g.acell32, q2);
     }
   }
 }
@@ -217,16 +253,13 @@ static int num_sms() {
   return sms;
 }
 
-template <int MODE>
-static size_t xf32_smem(const GridView &g) {
-  return keys_bytes(g.nx, 4) + keys_bytes(g.nrows, 4) + keys_bytes(g.na, 4) + kWarps * sizeof(Rec32);
-}
+static size_t xf32_smem(const GridView &g) { return smem32_layout(g).total; }
 
 template <int MODE>
 static int launch_xf32(const pdf_grid *grid, const float *xa, const float *qa, const float *xb, float s,
                        long long n, int col0, int ncol, float *out, cudaStream_t st, float *as_out = nullptr) {
   const GridView &g = grid->v;
-  const size_t smem = xf32_smem<MODE>(g);
+  const size_t smem = xf32_smem(g);
   auto kern = k_xf32<MODE>;
   static LaunchCache cache;
   const int per_sm = cache.blocks_per_sm(kern, kThreads, smem);
