@@ -288,7 +288,9 @@ __device__ __forceinline__ double eval_far_ff(const GridView &g, const Rec64 &R,
 // RCP: the low-Q^2 rule multiplies by 1 / ln 1.01 (the Monte Carlo kernel,
 // where a fifth of the events take it; the other kernels keep the division,
 // which left their register allocation as measured fastest).
-template <bool RCP>
+// FAR: the continuation classes may occur (the near launch has none, and
+// leaves their code out).
+template <bool RCP, bool FAR>
 __device__ __forceinline__ double eval_item64(const GridView &g, const Rec64 &R, int p, int col, int m,
                                               LogTabs LT, const double *ET, FFTabs FT) {
   const double *cb = g.coef + (size_t)m * g.mstride + (size_t)col * 16;
@@ -305,6 +307,7 @@ __device__ __forceinline__ double eval_item64(const GridView &g, const Rec64 &R,
                     g.nfp, reinterpret_cast<const float4 *>(R.W[p]));
   if (cls == C_IN) return dot_w16(C(0, 0), R, p);
   if (cls == C_INVALID) return NAN;
+  if constexpr (!FAR) return NAN;
   if (g.ff) return eval_far_ff(g, R, p, col, m, FT);
   // continuation: the two values the final rule combines, then one shared rule
   double a, b, prm = R.px[p];
@@ -417,7 +420,7 @@ __device__ __forceinline__ void store_point(Rec64 &R, int slot, const PointSites
 }
 
 // Phase 2 over the first np slots: items (slot, column) in order, lane-strided.
-template <bool RCP>
+template <bool RCP, bool FAR = true>
 __device__ __forceinline__ void items64(const GridView &g, const Rec64 &R, int np, int nc, int cbase,
                                         int m, long long mo, double *__restrict__ out, LogTabs LT,
                                         const double *ET, FFTabs FT, int lane) {
@@ -425,7 +428,7 @@ __device__ __forceinline__ void items64(const GridView &g, const Rec64 &R, int n
   int p = lane / nc, c = lane - (lane / nc) * nc;
   const int dp = 32 / nc, dc = 32 - dp * nc;
   for (int k = lane; k < nitems; k += 32) {
-    out[mo + R.ob[p] + c] = eval_item64<RCP>(g, R, p, cbase + c, m, LT, ET, FT);
+    out[mo + R.ob[p] + c] = eval_item64<RCP, FAR>(g, R, p, cbase + c, m, LT, ET, FT);
     c += dc;
     p += dp;
     if (c >= nc) { c -= nc; p++; }
@@ -666,7 +669,7 @@ k_xf64(GridView g, const double *__restrict__ xa, const double *__restrict__ qa,
       for (int m = chunk * mchunk; m < m1; m++)
         items64<MODE == MODE_MC>(g, R, np, nc, cbase, m, (long long)m * n * nc, out, LT, ET, FT, lane);
     } else {
-      items64<MODE == MODE_MC>(g, R, np, nc, cbase, 0, 0, out, LT, ET, FT, lane);
+      items64<MODE == MODE_MC, PART != PART_NEAR>(g, R, np, nc, cbase, 0, 0, out, LT, ET, FT, lane);
     }
     __syncwarp();
     if (kQueue) drain_ready(false);
