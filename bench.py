@@ -89,9 +89,17 @@ def algorithmic_flops(counts, nflav):
     return sum(c * (FLOP_POINT + nflav * CLASS_EVAL_FLOPS[k]) for k, c in counts.items())
 
 
-def kernel_source_hash():
+# the sources each captured kernel is built from (a capture counts only while they are unchanged)
+KERNEL_SOURCES = {
+    "k_xf64<points> near + far": ("xf64.cu", "ff.cuh", "ffmath.cuh", "tang.cuh", "sites.cuh", "pdf_internal.cuh",
+                                  "grid.cu"),
+    "k_xf32<points>": ("xfxq2.cu", "sites.cuh", "pdf_internal.cuh", "grid.cu"),
+}
+
+
+def kernel_source_hash(kernel="k_xf64<points> near + far"):
     h = hashlib.sha256()
-    for name in ("xf64.cu", "ff.cuh", "ffmath.cuh", "tang.cuh", "sites.cuh", "pdf_internal.cuh", "grid.cu"):
+    for name in KERNEL_SOURCES[kernel]:
         h.update((ROOT / "paper_2009_06635_gb300" / "csrc" / name).read_bytes())
     return h.hexdigest()[:16]
 
@@ -106,7 +114,7 @@ def profiled_traffic(kernel, n_points):
         rec = json.loads(f.read_text()).get(kernel)
     except Exception:
         return None
-    if not rec or rec.get("source_hash") != kernel_source_hash():
+    if not rec or rec.get("source_hash") != kernel_source_hash(kernel):
         return None
     return rec["dram_bytes_per_point"] * n_points
 
@@ -122,7 +130,7 @@ def profiled_pipes(kernel):
         rec = json.loads(f.read_text()).get(kernel)
     except Exception:
         return None
-    if not rec or rec.get("source_hash") != kernel_source_hash():
+    if not rec or rec.get("source_hash") != kernel_source_hash(kernel):
         return None
     return rec
 
@@ -785,7 +793,7 @@ def our_arm(args):
     flops = algorithmic_flops(counts, nf)
     achieved = flops / (kern_ms * 1e-3)
     traffic = profiled_traffic("k_xf64<points> near + far", n)
-    bytes32 = n * (8 + 4 * nf)
+    bytes32 = n * (8 + 4 * nf + 4)  # x, Q^2 in; the flavours and alpha_s out
     alg_bytes = n * (16 + 8 * nf + 8)
     sm_mhz = (clk or {}).get("sm_mhz") or SM_MHZ
     pipes = profiled_pipes("k_xf64<points> near + far")
@@ -814,6 +822,22 @@ def our_arm(args):
             "frac": alg_bytes / (kern_ms * 1e-3) / (hbm * 1e9), "traffic": traffic,
             "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json); no per-unit capture of this source",
             "kernel_ms": kern_ms, "algorithmic_flops_per_launch": flops}
+    # FP32: its algorithmic bytes against HBM, and (with a capture of this
+    # source) the same per-unit model as the FP64 call
+    roofline32 = {"bound": "hbm", "achieved": bytes32 / (k32 * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                  "frac": bytes32 / (k32 * 1e-3) / 1e9 / hbm,
+                  "traffic": profiled_traffic("k_xf32<points>", n),
+                  "fp32_fma_peak_derived_tflops": FP32_PEAK / 1e12,
+                  "fp32_fma_peak_measured_tflops": fp32_meas.value / 1e12}
+    pipes32 = profiled_pipes("k_xf32<points>")
+    if pipes32:
+        ut32 = unit_bound(pipes32, n, sm_mhz, bytes32, hbm)
+        b32 = max(ut32, key=ut32.get)
+        roofline32["per_unit"] = {
+            "binding_unit": b32, "frac": ut32[b32] / (k32 * 1e-3),
+            "unit_ms": {k: v * 1e3 for k, v in ut32.items()},
+            "source": "each SM unit's busy time per point from the committed capture (profiles/pipes.json), "
+                      "x points, at the sampled SM clock; frac = the busiest unit's time over the kernel's"}
     line = {
         "metric": METRIC,
         "value": value,
@@ -841,10 +865,7 @@ def our_arm(args):
                 "link_bound_ms": e2e_bound_s * 1e3, "frac_of_link_bound": e2e_bound_s / e2e_s, "numa": numa},
         "paths": {
             "fp32": {"value": world * evals_step / (ms32 * 1e-3), "ms_per_step": ms32, "kernel_ms": k32,
-                     "roofline": {"bound": "hbm", "achieved": bytes32 / (k32 * 1e-3) / 1e9, "peak": hbm,
-                                  "unit": "GB/s", "frac": bytes32 / (k32 * 1e-3) / 1e9 / hbm,
-                                  "fp32_fma_peak_derived_tflops": FP32_PEAK / 1e12,
-                                  "fp32_fma_peak_measured_tflops": fp32_meas.value / 1e12}},
+                     "roofline": roofline32},
             "single_pid_fp64": {"value": world * n / (ms_pid * 1e-3), "ms_per_step": ms_pid},
             "alphas_fp64": {"value": world * n / (ms_as * 1e-3), "ms_per_step": ms_as},
             "mc_event_fp64": {"value": world * MC_EVENTS * (2 * nf + 1) / (ms_mc * 1e-3), "ms_per_step": ms_mc,
