@@ -584,97 +584,102 @@ k_xf64(GridView g, const double *__restrict__ xa, const double *__restrict__ qa,
     }
   };
 
-  for (long long unit = (long long)blockIdx.x * kWarps + warp; unit < nunits; unit += nwarps) {
-    const long long tile = unit / nchunks;
-    const int chunk = (int)(unit - tile * nchunks);
-    const long long e0 = tile * per_tile;
-    const int ne = (int)(n - e0 < per_tile ? n - e0 : per_tile);
+  // one call site of the queue drain (it is inlined once): the loop runs one
+  // more, empty round to drain the queues at the end
+  for (long long unit = (long long)blockIdx.x * kWarps + warp;; unit += nwarps) {
+    const bool more = unit < nunits;  // warp-uniform
+    if (more) {
+      const long long tile = unit / nchunks;
+      const int chunk = (int)(unit - tile * nchunks);
+      const long long e0 = tile * per_tile;
+      const int ne = (int)(n - e0 < per_tile ? n - e0 : per_tile);
 
-    // ---- phase 1: lane = point ----
-    bool present;
-    double x = 0.0, q2 = 0.0, lq = 0.0;
-    long long ob;
-    if (MODE != MODE_MC) {
-      present = lane < ne;
-      if (present) { x = xa[e0 + lane]; q2 = qa[e0 + lane]; }
-      ob = (e0 + lane) * (long long)nc;
-    } else {
-      const int e = lane >> 1;
-      present = e < ne;
-      if (present) {
-        double x1, x2;
-        if (gen.on) mc_event(gen, (unsigned long long)(e0 + e), x1, x2);
-        else { x1 = xa[e0 + e]; x2 = xb[e0 + e]; }
-        q2 = x1 * x2 * s;
-        x = (lane & 1) ? x2 : x1;
-      }
-      ob = (e0 + e) * (long long)(2 * g.nf + 1) + (lane & 1) * g.nf;
-    }
-    if constexpr (PART == PART_FAR) {  // queue the points that need a rule, nothing else
-      const int fc = present ? far_class(g, x, q2) : -1;
-      const unsigned id = MODE == MODE_MC ? (unsigned)(2 * (e0 + (lane >> 1)) + (lane & 1)) : (unsigned)(e0 + lane);
-#pragma unroll
-      for (int c = 0; c < kFar; c++) {
-        const unsigned fm = __ballot_sync(kFull, fc == C_LOWX + c);
-        if (fc == C_LOWX + c) Q.idx[c][nq[c] + __popc(fm & ((1u << lane) - 1u))] = id;
-        nq[c] += __popc(fm);
-      }
-      __syncwarp();
-      drain_ready(false);
-      continue;
-    }
-    PointSites<double> ps;
-    ps.cls = -1;
-    if (present) ps = sites(g, xkeys, qkeys, x, q2, LT, lq);
-    // in-grid points contract in float-float, except exact knot hits
-    // (t = u = 0), which keep FP64 so that knot values come back bit-exact
-    if (ps.cls == C_IN && g.ff &&
-        !((__double_as_longlong(ps.t0) << 1) == 0 && (__double_as_longlong(ps.u0) << 1) == 0))
-      ps.cls = C_INF;
-    if (MODE != MODE_MEMBERS || chunk == 0) {
-      const unsigned inv = __ballot_sync(kFull, ps.cls == C_INVALID);
-      if (lane == 0 && inv) atomicAdd(g.invalid, (unsigned long long)__popc(inv));
-    }
-    if (MODE == MODE_MC) {
-      if (present && (lane & 1) == 0) out[ob + 2 * g.nf] = alphas_eval(g, akeys, q2, lq);
-    } else if (MODE == MODE_POINTS) {
-      if (present && as_out) as_out[e0 + lane] = alphas_eval(g, akeys, q2, lq);
-    }
-
-    int key = ps.cls, slot = 0, np;
-    if (PART == PART_NEAR) {  // points that need a rule are the far launch's
-      if (is_far(ps.cls)) key = -1;
-      np = sort_slots<C_INF, C_IN, C_INVALID>(key, lane, slot);
-    } else if (kQueue) {
-      const unsigned id = MODE == MODE_MC ? (unsigned)(2 * (e0 + (lane >> 1)) + (lane & 1)) : (unsigned)(e0 + lane);
-#pragma unroll
-      for (int c = 0; c < kFar; c++) {
-        const unsigned fm = __ballot_sync(kFull, ps.cls == C_LOWX + c);
-        if (ps.cls == C_LOWX + c) {
-          Q.idx[c][nq[c] + __popc(fm & ((1u << lane) - 1u))] = id;
-          key = -1;
+      // ---- phase 1: lane = point ----
+      bool present;
+      double x = 0.0, q2 = 0.0, lq = 0.0;
+      long long ob;
+      if (MODE != MODE_MC) {
+        present = lane < ne;
+        if (present) { x = xa[e0 + lane]; q2 = qa[e0 + lane]; }
+        ob = (e0 + lane) * (long long)nc;
+      } else {
+        const int e = lane >> 1;
+        present = e < ne;
+        if (present) {
+          double x1, x2;
+          if (gen.on) mc_event(gen, (unsigned long long)(e0 + e), x1, x2);
+          else { x1 = xa[e0 + e]; x2 = xb[e0 + e]; }
+          q2 = x1 * x2 * s;
+          x = (lane & 1) ? x2 : x1;
         }
-        nq[c] += __popc(fm);
+        ob = (e0 + e) * (long long)(2 * g.nf + 1) + (lane & 1) * g.nf;
       }
-      np = sort_slots<C_INF, C_IN, C_INVALID>(key, lane, slot);
-    } else {
-      np = sort_slots<C_INF, C_IN, C_LOWX, C_HIGHQ, C_LOWQ, C_LOWX_HIGHQ, C_LOWX_LOWQ, C_INVALID>(key, lane, slot);
-    }
-    if (key >= 0) store_point(R, slot, ps, ob, g.ff);
-    __syncwarp();
+      if constexpr (PART == PART_FAR) {  // queue the points that need a rule, nothing else
+        const int fc = present ? far_class(g, x, q2) : -1;
+        const unsigned id = MODE == MODE_MC ? (unsigned)(2 * (e0 + (lane >> 1)) + (lane & 1)) : (unsigned)(e0 + lane);
+#pragma unroll
+        for (int c = 0; c < kFar; c++) {
+          const unsigned fm = __ballot_sync(kFull, fc == C_LOWX + c);
+          if (fc == C_LOWX + c) Q.idx[c][nq[c] + __popc(fm & ((1u << lane) - 1u))] = id;
+          nq[c] += __popc(fm);
+        }
+        __syncwarp();
+      }
+      if constexpr (PART != PART_FAR) {
+        PointSites<double> ps;
+        ps.cls = -1;
+        if (present) ps = sites(g, xkeys, qkeys, x, q2, LT, lq);
+        // in-grid points contract in float-float, except exact knot hits
+        // (t = u = 0), which keep FP64 so that knot values come back bit-exact
+        if (ps.cls == C_IN && g.ff &&
+            !((__double_as_longlong(ps.t0) << 1) == 0 && (__double_as_longlong(ps.u0) << 1) == 0))
+          ps.cls = C_INF;
+        if (MODE != MODE_MEMBERS || chunk == 0) {
+          const unsigned inv = __ballot_sync(kFull, ps.cls == C_INVALID);
+          if (lane == 0 && inv) atomicAdd(g.invalid, (unsigned long long)__popc(inv));
+        }
+        if (MODE == MODE_MC) {
+          if (present && (lane & 1) == 0) out[ob + 2 * g.nf] = alphas_eval(g, akeys, q2, lq);
+        } else if (MODE == MODE_POINTS) {
+          if (present && as_out) as_out[e0 + lane] = alphas_eval(g, akeys, q2, lq);
+        }
 
-    // ---- phase 2: items ----
-    if (MODE == MODE_MEMBERS) {
-      const int m1 = min(g.nmem, (chunk + 1) * mchunk);
-      for (int m = chunk * mchunk; m < m1; m++)
-        items64<MODE == MODE_MC>(g, R, np, nc, cbase, m, (long long)m * n * nc, out, LT, ET, FT, lane);
-    } else {
-      items64<MODE == MODE_MC, PART != PART_NEAR>(g, R, np, nc, cbase, 0, 0, out, LT, ET, FT, lane);
+        int key = ps.cls, slot = 0, np;
+        if (PART == PART_NEAR) {  // points that need a rule are the far launch's
+          if (is_far(ps.cls)) key = -1;
+          np = sort_slots<C_INF, C_IN, C_INVALID>(key, lane, slot);
+        } else if (kQueue) {
+          const unsigned id = MODE == MODE_MC ? (unsigned)(2 * (e0 + (lane >> 1)) + (lane & 1)) : (unsigned)(e0 + lane);
+#pragma unroll
+          for (int c = 0; c < kFar; c++) {
+            const unsigned fm = __ballot_sync(kFull, ps.cls == C_LOWX + c);
+            if (ps.cls == C_LOWX + c) {
+              Q.idx[c][nq[c] + __popc(fm & ((1u << lane) - 1u))] = id;
+              key = -1;
+            }
+            nq[c] += __popc(fm);
+          }
+          np = sort_slots<C_INF, C_IN, C_INVALID>(key, lane, slot);
+        } else {
+          np = sort_slots<C_INF, C_IN, C_LOWX, C_HIGHQ, C_LOWQ, C_LOWX_HIGHQ, C_LOWX_LOWQ, C_INVALID>(key, lane, slot);
+        }
+        if (key >= 0) store_point(R, slot, ps, ob, g.ff);
+        __syncwarp();
+
+        // ---- phase 2: items ----
+        if (MODE == MODE_MEMBERS) {
+          const int m1 = min(g.nmem, (chunk + 1) * mchunk);
+          for (int m = chunk * mchunk; m < m1; m++)
+            items64<MODE == MODE_MC>(g, R, np, nc, cbase, m, (long long)m * n * nc, out, LT, ET, FT, lane);
+        } else {
+          items64<MODE == MODE_MC, PART != PART_NEAR>(g, R, np, nc, cbase, 0, 0, out, LT, ET, FT, lane);
+        }
+        __syncwarp();
+      }
     }
-    __syncwarp();
-    if (kQueue) drain_ready(false);
+    if (kQueue) drain_ready(!more);
+    if (!more) break;
   }
-  if (kQueue) drain_ready(true);
 }
 
 static int num_sms() {
