@@ -177,14 +177,7 @@ __device__ __noinline__ void scatter_point_f64(int nrows, int nx, int nf, double
 // position t and its complement s (computed apart, so whichever is small
 // keeps its precision): four conversions on the FP64 pipe, the rest on the
 // FMA pipe.  dB/dt = (-3 s^2, 3 s^2 - 6 t s, 6 t s - 3 t^2, 3 t^2).
-__device__ __forceinline__ ff2 ff_sub(ff2 a, ff2 b) {
-  const float s = __fsub_rn(a.h, b.h);
-  const float bb = __fsub_rn(s, a.h);
-  const float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(-b.h, bb));
-  const float l = __fadd_rn(e, __fsub_rn(a.l, b.l));
-  const float h = __fadd_rn(s, l);
-  return {h, __fsub_rn(l, __fsub_rn(h, s))};
-}
+// (ff_sub: ffmath.cuh)
 __device__ __forceinline__ void ff_bern_d(double t, double s, ff2 dpos, ff2 *B, ff2 *dB) {
   const ff2 tf = ff_of(t), sf = ff_of(s), three = {3.f, 0.f}, six = {6.f, 0.f};
   const ff2 t2 = ff_mul(tf, tf), s2 = ff_mul(sf, sf), ts = ff_mul(tf, sf);

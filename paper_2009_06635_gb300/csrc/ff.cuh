@@ -13,9 +13,20 @@ namespace pdfgb {
 struct ff2 {
   float h, l;
 };
+// Exact float -> double on the integer pipe for normal floats and zeros (the
+// FP64 pipe's conversion costs as much as an FMA on GB300); subnormals,
+// infinities and NaN take the hardware conversion.
+__device__ __forceinline__ double f2d(float f) {
+  const unsigned b = __float_as_uint(f), a = b & 0x7FFFFFFFu;
+  if (a - 0x00800000u < 0x7F000000u)  // biased exponent in [1, 254]
+    return __hiloint2double((int)(((a >> 3) + 0x38000000u) | (b & 0x80000000u)), (int)(b << 29));
+  if (a == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
+  return (double)f;
+}
+// a double as hi + lo (the hi part back to double on the integer pipe)
 __device__ __forceinline__ ff2 ff_of(double a) {
   float h = __double2float_rn(a);
-  return {h, __double2float_rn(a - (double)h)};
+  return {h, __double2float_rn(a - f2d(h))};
 }
 __device__ __forceinline__ ff2 ff_mul(ff2 a, ff2 b) {
   float p = __fmul_rn(a.h, b.h);
@@ -31,16 +42,6 @@ __device__ __forceinline__ void ff_bernstein(double t, double s, ff2 *B) {
   B[1] = ff_mul(three, ff_mul(tf, s2));
   B[2] = ff_mul(three, ff_mul(t2, sf));
   B[3] = ff_mul(t2, tf);
-}
-// Exact float -> double on the integer pipe for normal floats and zeros (the
-// FP64 pipe's conversion costs as much as an FMA on GB300); subnormals,
-// infinities and NaN take the hardware conversion.
-__device__ __forceinline__ double f2d(float f) {
-  const unsigned b = __float_as_uint(f), a = b & 0x7FFFFFFFu;
-  if (a - 0x00800000u < 0x7F000000u)  // biased exponent in [1, 254]
-    return __hiloint2double((int)(((a >> 3) + 0x38000000u) | (b & 0x80000000u)), (int)(b << 29));
-  if (a == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
-  return (double)f;
 }
 // s += w b, s an unnormalised pair (sum, gathered rounding errors): exact
 // product, TwoSum of the high parts, the cross terms and errors in s_l

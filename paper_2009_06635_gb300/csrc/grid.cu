@@ -20,6 +20,7 @@
 //     float thresholds for the exact FP32 search.
 #include <atomic>
 #include <cmath>
+#include <vector>
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
@@ -111,6 +112,8 @@ struct Stage {
   double *tloghtab, *texptab;
   float4 *fflog;     // ffmath.cuh tables, likewise
   float2 *ffexp;
+  float4 *xposff, *qposff, *aposff, *lnfff;  // ffpos.cuh tables, likewise
+  float2 *lnfff2;
   int *ffbad;  // set when a control point is outside the float-float range
   int *row_qc, *qc_row;
   double *scal;  // scalar outputs, see k_scalars
@@ -148,6 +151,39 @@ void ff_tables(float *logtab, float *exptab) {
     logtab[4 * j + 3] = 0.f;
   }
   for (int k = 0; k < kFFExpTab; k++) split(exp2l(k / 64.0L), exptab + 2 * k);
+}
+
+// ffpos.cuh tables.  A knot a starting a cell that ends at b (b = a: no
+// cell): {ln m hi, lo, 1/ln(b/a) hi, lo}, with a = 2^e m and m taken in
+// [sqrt(1/2), sqrt(2)) by the device's test on the bits (ff_sig_high).
+static float4 pos_entry(double a, double b) {
+  long long bits;
+  std::memcpy(&bits, &a, sizeof bits);
+  const bool high = ((bits >> 32) & 0xFFFFF) >= 0x6A09E;
+  int e2 = 0;
+  long double m = 2.0L * frexpl((long double)a, &e2);  // [1, 2)
+  if (high) m /= 2.0L;                                 // [sqrt(1/2), 1)
+  const long double lm = logl(m);
+  const long double id = b > a ? 1.0L / logl((long double)b / (long double)a) : 0.0L;
+  float4 r;
+  r.x = (float)lm;
+  r.y = (float)(lm - (long double)r.x);
+  r.z = (float)id;
+  r.w = (float)(id - (long double)r.z);
+  return r;
+}
+// {1/F_j hi, lo, ln F_j hi, lo} and ln(F_j / 2) {hi, lo} for F_j = 1 + j/256,
+// j = 0..256 (tang.cuh's steps)
+static void ln_f_table(float4 *o, float2 *o2) {
+  for (int j = 0; j < kLogTab; j++) {
+    const long double F = 1.0L + j / 256.0L, iF = 1.0L / F, lF = logl(F), lF2 = logl(F / 2.0L);
+    o[j].x = (float)iF;
+    o[j].y = (float)(iF - (long double)o[j].x);
+    o[j].z = (float)lF;
+    o[j].w = (float)(lF - (long double)o[j].z);
+    o2[j].x = (float)lF2;
+    o2[j].y = (float)(lF2 - (long double)o2[j].x);
+  }
 }
 
 // FP32 cell table: both end knots rounded to float (k0f, k1f), their float
@@ -480,6 +516,9 @@ static int load_impl(const pdf_grid_desc *d, int nmem, const double *member_valu
     S.tlogtab = A.take<double2>(kLogTab); S.tloghtab = A.take<double>(kLogTab);
     S.texptab = A.take<double>(kExpTab);
     S.fflog = A.take<float4>(kFFLogTab); S.ffexp = A.take<float2>(kFFExpTab);
+    S.xposff = A.take<float4>(nx); S.qposff = A.take<float4>(nrows);
+    S.aposff = A.take<float4>(na > 0 ? na : 1); S.lnfff = A.take<float4>(kLogTab);
+    S.lnfff2 = A.take<float2>(kLogTab);
     S.acell = A.take<double>(6 * (na > 0 ? na : 1));
     S.acell32 = A.take<float>(6 * (na > 0 ? na : 1));
     S.xthr32 = A.take<float>(nx); S.q2thr32 = A.take<float>(nrows); S.aq2thr32 = A.take<float>(na > 0 ? na : 1);
@@ -534,6 +573,32 @@ static int load_impl(const pdf_grid_desc *d, int nmem, const double *member_valu
     H2D(S.fflog, fl, sizeof fl);
     H2D(S.ffexp, fe, sizeof fe);
   }
+  int ffpos = 1;
+  {
+    std::vector<float4> xp(nx), qp(nrows), ap(na > 0 ? na : 1), lf(kLogTab);
+    std::vector<float2> lf2(kLogTab);
+    // a knot's row for each knot list; starts[k]: knot k starts a cell
+    auto fill = [&](const double *k, int n, const std::vector<char> &starts, std::vector<float4> &o) {
+      for (int i = 0; i < n; i++) {
+        if (!(std::fpclassify(k[i]) == FP_NORMAL)) ffpos = 0;
+        const bool st = starts[i] && i + 1 < n && k[i + 1] > k[i];
+        if (st && std::abs(std::ilogb(k[i + 1]) - std::ilogb(k[i])) >= 100) ffpos = 0;
+        o[i] = pos_entry(k[i], st ? k[i + 1] : k[i]);
+      }
+    };
+    std::vector<char> xs(nx, 1), qs(nrows, 0), as(na > 0 ? na : 1, 1);
+    for (int s = 0; s < nsub; s++)
+      for (int r = first[s]; r < first[s] + d->nq[s] - 1; r++) qs[r] = 1;
+    fill(d->x_knots, nx, xs, xp);
+    fill(d->q2_knots, nrows, qs, qp);
+    if (na > 0) fill(d->as_q2, na, as, ap);
+    ln_f_table(lf.data(), lf2.data());
+    H2D(S.xposff, xp.data(), sizeof(float4) * nx);
+    H2D(S.qposff, qp.data(), sizeof(float4) * nrows);
+    if (na > 0) H2D(S.aposff, ap.data(), sizeof(float4) * na);
+    H2D(S.lnfff, lf.data(), sizeof(float4) * kLogTab);
+    H2D(S.lnfff2, lf2.data(), sizeof(float2) * kLogTab);
+  }
   if (e == cudaSuccess) e = cudaMemset(inv, 0, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(S.ffbad, 0, sizeof(int));
   if (e != cudaSuccess) {
@@ -569,6 +634,8 @@ static int load_impl(const pdf_grid_desc *d, int nmem, const double *member_valu
   v.coefff = S.coefff; v.ff = ffbad ? 0 : 1;
   v.tlogtab = S.tlogtab; v.tloghtab = S.tloghtab; v.texptab = S.texptab;
   v.fflog = S.fflog; v.ffexp = S.ffexp;
+  v.xposff = S.xposff; v.qposff = S.qposff; v.aposff = S.aposff; v.lnfff = S.lnfff; v.lnfff2 = S.lnfff2;
+  v.ffpos = ffpos;
   v.nmem = nmem;
   v.mstride = (size_t)(nqc + 1) * nx * nf * 16;
   v.nfp = nfp;

@@ -124,6 +124,15 @@ struct GridView {
   const float4 *fflog;  // [kFFLogTab]
   const float2 *ffexp;  // [kFFExpTab]
   float iln101_ffh, iln101_ffl;
+  // Float-float positions of in-grid points (ffpos.cuh): per x knot, Q row
+  // and alpha_s node {ln m hi, lo, 1/d hi, lo} (m the knot's binary
+  // significand in [1, 2), d the ln-width of the cell it starts, 0 where it
+  // starts none), and per step F_j = 1 + j/256 {1/F_j hi, lo, ln F_j hi, lo}.
+  // ffpos = 1 when every knot is a normal double and no cell spans 2^100 or
+  // more (the exponent difference stays exact in floats).
+  const float4 *xposff, *qposff, *aposff, *lnfff;
+  int ffpos;
+  const float2 *lnfff2;  // ln(F_j / 2) as a float pair (the high-significand steps)
 };
 
 // ---------------------------------------------------------------------------

@@ -5,6 +5,7 @@
 #include <cmath>
 
 #include "pdf_internal.cuh"
+#include "ffpos.cuh"
 
 namespace pdfgb {
 
@@ -110,7 +111,11 @@ __device__ __forceinline__ void cell_pos32(const float *c, float v, float &t, fl
     t = (log1pf((v - a.x) * a.y) + a.z) * a.w;
     ts = 1.f - t;
   } else {
-    ts = -(log1pf((v - b.x) * b.y) + b.z) * a.w;
+    // ln(v / k1) <= 0; far below k1 (a cell wider than a factor 4) the
+    // complement 1 + z of z = (v - k1)/k1 is no longer precise, and the
+    // quotient itself is taken instead
+    const float z = (v - b.x) * b.y;
+    ts = -((z > -0.5f ? log1pf(z) : logf(v * b.y)) + b.z) * a.w;
     t = 1.f - ts;
   }
 }
@@ -177,6 +182,19 @@ __device__ __forceinline__ float alphas_eval(const GridView &g, const int *akeys
   return fmaf(fmaf(fmaf(c[5], u, c[4]), u, c[3]), u, c[2]);
 }
 
+// alpha_s (Sec. 2.3) with the node position from ffpos.cuh: constant
+// outside, the cubic in FP64 from the position.
+__device__ __forceinline__ double alphas_ff(const GridView &g, const long long *akeys, const float4 *LF,
+                                            const float2 *LF2, double q2) {
+  const long long kq = __double_as_longlong(q2);
+  if (!(kq > 0 && kq < 0x7FF0000000000000LL)) return NAN;
+  if (kq < __double_as_longlong(g.aq2lo)) return g.as_lo;
+  if (kq > __double_as_longlong(g.aq2hi)) return g.as_hi;
+  const int k = search_cell(akeys, g.na, g.astep, kq);
+  const double u = ff_to_d(ff_cell_pos(kq, akeys[k], g.aposff[k], LF, LF2));
+  const double *c = g.acell + 6 * k;
+  return fma(fma(fma(c[5], u, c[4]), u, c[3]), u, c[2]);
+}
 template <typename T>
 __device__ __forceinline__ void load_keys(const GridView &g, typename Prec<T>::K *keys, int which);
 

@@ -349,6 +349,76 @@ __device__ __forceinline__ double eval_item64(const GridView &g, const Rec64 &R,
   return pair_rule(a, b, prm, LT, ET);
 }
 
+// ---- near launch on float-float grids: positions without FP64 -------------
+// An in-grid point's cell positions t, u (and 1 - t, 1 - u) as float pairs
+// (ffpos.cuh); points of the other classes are only classified here.
+struct NearFF {
+  int cls, xc0, qc0;
+  ff2 t, ts, u, us;
+};
+__device__ __forceinline__ NearFF near_sites_ff(const GridView &g, const long long *xkeys,
+                                                const long long *qkeys, const float4 *LF, const float2 *LF2,
+                                                double x, double q2) {
+  NearFF r;
+  r.xc0 = r.qc0 = 0;
+  r.t = r.u = ff2{0.f, 0.f};
+  r.ts = r.us = ff2{1.f, 0.f};
+  const long long kx = __double_as_longlong(x), kq = __double_as_longlong(q2);
+  if (!(kq > 0 && kq < 0x7FF0000000000000LL && kx > 0 && kx <= __double_as_longlong(g.xlast))) {
+    r.cls = C_INVALID;
+    return r;
+  }
+  const bool lowx = kx < __double_as_longlong(g.x0);
+  const bool lowq = kq < __double_as_longlong(g.q2min), highq = kq > __double_as_longlong(g.q2max);
+  if (lowx || lowq || highq) {
+    r.cls = lowx ? (highq ? C_LOWX_HIGHQ : lowq ? C_LOWX_LOWQ : C_LOWX) : (highq ? C_HIGHQ : C_LOWQ);
+    return r;
+  }
+  const int i = search_cell(xkeys, g.nx, g.xstep, kx);
+  const int j = search_cell(qkeys, g.nrows, g.qstep, kq);
+  r.xc0 = i;
+  r.qc0 = g.row_qc[j];
+  // (an exact hit on the last knot, or the top row, is the knot case: no next knot is read)
+  const bool xk1 = kx != xkeys[i], qk1 = kq != qkeys[j];
+  ff_cell_pos2(kx, xkeys[i], xk1 ? xkeys[i + 1] : 0, g.xposff[i], xk1 ? g.xposff[i + 1] : make_float4(0.f, 0.f, 0.f, 0.f),
+               LF, LF2, r.t, r.ts);
+  ff_cell_pos2(kq, qkeys[j], qk1 ? qkeys[j + 1] : 0, g.qposff[j], qk1 ? g.qposff[j + 1] : make_float4(0.f, 0.f, 0.f, 0.f),
+               LF, LF2, r.u, r.us);
+  // an exact knot hit (t = u = 0) keeps the FP64 contraction, so knot values come back exactly
+  r.cls = (r.t.h == 0.f && r.u.h == 0.f) ? C_IN : C_INF;
+  return r;
+}
+// Bernstein basis from a float-pair position and its complement.
+__device__ __forceinline__ void ff_bernstein2(ff2 tf, ff2 sf, ff2 *B) {
+  const ff2 three = {3.f, 0.f};
+  const ff2 t2 = ff_mul(tf, tf), s2 = ff_mul(sf, sf);
+  B[0] = ff_mul(s2, sf);
+  B[1] = ff_mul(three, ff_mul(tf, s2));
+  B[2] = ff_mul(three, ff_mul(t2, sf));
+  B[3] = ff_mul(t2, tf);
+}
+__device__ __forceinline__ void store_point_ff(Rec64 &R, int slot, const NearFF &ps, long long ob) {
+  R.cls[slot] = ps.cls;
+  R.xc0[slot] = ps.xc0; R.xc1[slot] = 0; R.qc0[slot] = ps.qc0; R.qc1[slot] = 0;
+  R.ob[slot] = ob;
+  if (ps.cls == C_INF) {
+    ff2 bx[4], bq[4];
+    ff_bernstein2(ps.t, ps.ts, bx);
+    ff_bernstein2(ps.u, ps.us, bq);
+    float4 *row = reinterpret_cast<float4 *>(R.W[slot]);
+#pragma unroll
+    for (int l = 0; l < 4; l++)
+#pragma unroll
+      for (int k = 0; k < 4; k += 2) {
+        const ff2 w0 = ff_mul(bx[k], bq[l]), w1 = ff_mul(bx[k + 1], bq[l]);
+        row[(l * 4 + k) >> 1] = make_float4(w0.h, w1.h, w0.l, w1.l);
+      }
+  } else if (ps.cls == C_IN) {  // an exact knot: the weight of control point 0 alone
+#pragma unroll
+    for (int m = 0; m < 16; m++) R.W[slot][m] = m == 0 ? 1.0 : 0.0;
+  }
+}
+
 // Bernstein weights of a point's sites into its record slot (float-float
 // for continuation points when ff is set).
 __device__ __forceinline__ void store_point(Rec64 &R, int slot, const PointSites<double> &ps, long long ob,
@@ -481,8 +551,11 @@ __device__ __forceinline__ int far_class(const GridView &g, double x, double q2)
 //               are generated (mc.cuh) and xa, xb are not read.
 // MODE_MEMBERS: points xa[n], qa[n]; out[nmem][n][nf].  A warp's unit is
 //               (tile, chunk of mchunk members); phase 1 repeats per chunk.
+// One launch for everything (small batches) holds both the float-float
+// positions and the continuation code: two blocks per SM give it the
+// registers to do so without spilling.
 template <int MODE, int PART>
-__global__ void __launch_bounds__(kThreads, 3)
+__global__ void __launch_bounds__(kThreads, PART == PART_ALL && MODE != MODE_MEMBERS ? 2 : 3)
 k_xf64(GridView g, const double *__restrict__ xa, const double *__restrict__ qa, const double *__restrict__ xb,
        double s, long long n, int col0, int ncol, int mchunk, double *__restrict__ out,
        double *__restrict__ as_out, McGen gen) {
@@ -513,6 +586,13 @@ k_xf64(GridView g, const double *__restrict__ xa, const double *__restrict__ qa,
   if (want_as) load_keys<double>(g, akeys, 2);
   for (int i = threadIdx.x; i < kLogTab; i += kThreads) { LTt[i] = g.tlogtab[i]; LTh[i] = g.tloghtab[i]; }
   const LogTabs LT{LTt, LTh};
+  // float-float positions (ffpos.cuh) of in-grid points and alpha_s: their
+  // steps table after the queues (not in the far launch, which has neither)
+  float4 *LF = reinterpret_cast<float4 *>(smem + off + (kQueue ? kWarps * sizeof(Queue64) : 0));
+  float2 *LF2 = reinterpret_cast<float2 *>(LF + kLogTab);
+  if (PART != PART_FAR && g.ffpos)
+    for (int i = threadIdx.x; i < kLogTab; i += kThreads) { LF[i] = g.lnfff[i]; LF2[i] = g.lnfff2[i]; }
+  const bool ffp = g.ff && g.ffpos;  // in-grid positions in float-float
   for (int i = threadIdx.x; i < kFFLogTab; i += kThreads) FTl[i] = g.fflog[i];
   for (int i = threadIdx.x; i < kFFExpTab; i += kThreads) FTe[i] = g.ffexp[i];
   const FFTabs FT{FTl, FTe};
@@ -628,20 +708,32 @@ k_xf64(GridView g, const double *__restrict__ xa, const double *__restrict__ qa,
       if constexpr (PART != PART_FAR) {
         PointSites<double> ps;
         ps.cls = -1;
-        if (present) ps = sites(g, xkeys, qkeys, x, q2, LT, lq);
-        // in-grid points contract in float-float, except exact knot hits
-        // (t = u = 0), which keep FP64 so that knot values come back bit-exact
-        if (ps.cls == C_IN && g.ff &&
-            !((__double_as_longlong(ps.t0) << 1) == 0 && (__double_as_longlong(ps.u0) << 1) == 0))
-          ps.cls = C_INF;
+        NearFF nf;
+        nf.cls = -1;
+        if (ffp) {  // warp-uniform
+          // classification and in-grid positions without the FP64 logarithm;
+          // continuation points keep the FP64 sites of their rules (the near
+          // launch leaves them to the far one)
+          if (present) nf = near_sites_ff(g, xkeys, qkeys, LF, LF2, x, q2);
+          ps.cls = nf.cls;
+          if (PART != PART_NEAR && is_far(nf.cls)) ps = sites(g, xkeys, qkeys, x, q2, LT, lq);
+        } else {
+          if (present) ps = sites(g, xkeys, qkeys, x, q2, LT, lq);
+          // in-grid points contract in float-float, except exact knot hits
+          // (t = u = 0), which keep FP64 so that knot values come back bit-exact
+          if (ps.cls == C_IN && g.ff &&
+              !((__double_as_longlong(ps.t0) << 1) == 0 && (__double_as_longlong(ps.u0) << 1) == 0))
+            ps.cls = C_INF;
+        }
         if (MODE != MODE_MEMBERS || chunk == 0) {
           const unsigned inv = __ballot_sync(kFull, ps.cls == C_INVALID);
           if (lane == 0 && inv) atomicAdd(g.invalid, (unsigned long long)__popc(inv));
         }
         if (MODE == MODE_MC) {
-          if (present && (lane & 1) == 0) out[ob + 2 * g.nf] = alphas_eval(g, akeys, q2, lq);
+          if (present && (lane & 1) == 0)
+            out[ob + 2 * g.nf] = g.ffpos ? alphas_ff(g, akeys, LF, LF2, q2) : alphas_eval(g, akeys, q2, lq);
         } else if (MODE == MODE_POINTS) {
-          if (present && as_out) as_out[e0 + lane] = alphas_eval(g, akeys, q2, lq);
+          if (present && as_out) as_out[e0 + lane] = g.ffpos ? alphas_ff(g, akeys, LF, LF2, q2) : alphas_eval(g, akeys, q2, lq);
         }
 
         int key = ps.cls, slot = 0, np;
@@ -663,7 +755,10 @@ k_xf64(GridView g, const double *__restrict__ xa, const double *__restrict__ qa,
         } else {
           np = sort_slots<C_INF, C_IN, C_LOWX, C_HIGHQ, C_LOWQ, C_LOWX_HIGHQ, C_LOWX_LOWQ, C_INVALID>(key, lane, slot);
         }
-        if (key >= 0) store_point(R, slot, ps, ob, g.ff);
+        if (key >= 0) {
+          if (ffp && !is_far(ps.cls)) store_point_ff(R, slot, nf, ob);
+          else store_point(R, slot, ps, ob, g.ff);
+        }
         __syncwarp();
 
         // ---- phase 2: items ----
@@ -697,7 +792,8 @@ template <int MODE, int PART = PART_ALL>
 static size_t xf64_smem(const GridView &g) {
   return keys_bytes(g.nx, 8) + keys_bytes(g.nrows, 8) + keys_bytes(g.na, 8) + sizeof(double2) * kLogTab +
          keys_bytes(kLogTab, 8) + sizeof(float4) * kFFLogTab + sizeof(float2) * kFFExpTab +
-         kWarps * (sizeof(Rec64) + (MODE == MODE_MEMBERS || PART == PART_NEAR ? 0 : sizeof(Queue64)));
+         kWarps * (sizeof(Rec64) + (MODE == MODE_MEMBERS || PART == PART_NEAR ? 0 : sizeof(Queue64))) +
+         (PART == PART_FAR ? 0 : (sizeof(float4) + sizeof(float2)) * kLogTab);
 }
 
 // Batches of at least this many points take the two launches (near, far).

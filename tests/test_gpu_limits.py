@@ -81,3 +81,14 @@ def test_smallest_grid_and_a_two_knot_subgrid(synth, oracle_mod):
                                                       np.geomspace(9.0, 1e5, 10)], pids,
                         params=synth.flavour_params(3, 34))
     check(synth, oracle_mod, g, n=5_000, seed=6)
+
+
+def test_a_cell_wider_than_2_to_the_100_takes_the_fp64_positions(synth, oracle_mod):
+    """In-grid positions are taken in float-float from the knots' binary
+    exponents and significands, which needs the exponent difference across a
+    cell exact in floats; a grid with a cell spanning 2^100 or more (here Q^2
+    from 10 to 1e33) takes the FP64 logarithm for them instead, and must give
+    the same parity."""
+    pids = [-1, 21, 1]
+    g = synth.make_grid(np.geomspace(1e-5, 1.0, 20), [[1.0, 10.0, 1e33]], pids, params=synth.flavour_params(3, 35))
+    check(synth, oracle_mod, g, n=5_000, seed=7)
