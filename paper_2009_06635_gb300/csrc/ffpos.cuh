@@ -77,9 +77,11 @@ __device__ __forceinline__ ff2 ff_ln_ratio(const FFLnSig &a, long long bk, float
 }
 
 // The position of v in the cell [v_k, v_k1] of ln-width d: t = ln(v/v_k)/d
-// and ts = ln(v_k1/v)/d, each from its own end, the larger then taken as one
-// minus the smaller (so the small one keeps its relative precision, as next
-// to x = 1 where the data vanish); t = 0, ts = 1 exactly on the knot.
+// and ts = 1 - t.  The logarithm is taken against the nearer knot (the
+// positive doubles' bit patterns are nearly linear in log2, so their mean
+// splits the cell near its geometric middle) and the other position is one
+// minus that one, so the small position keeps its relative precision (as
+// next to x = 1, where the data vanish); t = 0, ts = 1 exactly on the knot.
 // kt = {ln m_k hi, lo, 1/d hi, lo}, kt1 the next knot's entry.
 __device__ __forceinline__ void ff_cell_pos2(long long bv, long long bk, long long bk1, float4 kt, float4 kt1,
                                              const float4 *LF, const float2 *LF2, ff2 &t, ff2 &ts) {
@@ -88,12 +90,13 @@ __device__ __forceinline__ void ff_cell_pos2(long long bv, long long bk, long lo
     ts = ff2{1.f, 0.f};
     return;
   }
+  const bool right = bv > (bk >> 1) + (bk1 >> 1);
   const FFLnSig a = ff_ln_sig(bv, LF, LF2);
-  const ff2 id = ff2{kt.z, kt.w};
-  t = ff_mul(ff_ln_ratio(a, bk, kt.x, kt.y), id);
-  ts = ff_mul(ff_ln_ratio(a, bk1, kt1.x, kt1.y), ff2{-id.h, -id.l});
-  if (t.h <= ts.h) ts = ff_sub(ff2{1.f, 0.f}, t);
-  else t = ff_sub(ff2{1.f, 0.f}, ts);
+  const ff2 L = ff_ln_ratio(a, right ? bk1 : bk, right ? kt1.x : kt.x, right ? kt1.y : kt.y);
+  const ff2 p = ff_mul(L, right ? ff2{-kt.z, -kt.w} : ff2{kt.z, kt.w});  // the position from the nearer end
+  const ff2 q = ff_sub(ff2{1.f, 0.f}, p);
+  t = right ? q : p;
+  ts = right ? p : q;
 }
 // The left-end position alone (t = 0 on the knot).
 __device__ __forceinline__ ff2 ff_cell_pos(long long bv, long long bk, float4 kt, const float4 *LF,
