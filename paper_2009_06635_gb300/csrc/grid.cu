@@ -573,7 +573,11 @@ static int load_impl(const pdf_grid_desc *d, int nmem, const double *member_valu
     H2D(S.fflog, fl, sizeof fl);
     H2D(S.ffexp, fe, sizeof fe);
   }
-  int ffpos = 1;
+  // Member sets keep the FP64 logarithm for positions: their kernel repeats
+  // the per-point work for every chunk of members with about two units per
+  // warp, so the warps run it in step and its longer float-float dependency
+  // chain is not hidden (400 members x 2415 points: 0.234 against 0.193 ms).
+  int ffpos = nmem > 1 ? 0 : 1;
   {
     std::vector<float4> xp(nx), qp(nrows), ap(na > 0 ? na : 1), lf(kLogTab);
     std::vector<float2> lf2(kLogTab);
@@ -667,6 +671,11 @@ static int load_impl(const pdf_grid_desc *d, int nmem, const double *member_valu
     v.iln101_ffl = (float)(il - (long double)v.iln101_ffh);
   }
   v.q101_u32 = (float)v.q101_u;
+  {
+    auto split = [](double a, float &h, float &l) { h = (float)a; l = (float)(a - (double)h); };
+    split(v.q101_u, v.q101ff[0], v.q101ff[1]);
+    split(1.0 - v.q101_u, v.q101ff[2], v.q101ff[3]);
+  }
   v.invalid = inv;
   for (int f = 0; f < nf; f++) g->pids[f] = d->pids[f];
   *out = g;

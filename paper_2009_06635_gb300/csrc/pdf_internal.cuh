@@ -128,11 +128,13 @@ struct GridView {
   // and alpha_s node {ln m hi, lo, 1/d hi, lo} (m the knot's binary
   // significand in [1, 2), d the ln-width of the cell it starts, 0 where it
   // starts none), and per step F_j = 1 + j/256 {1/F_j hi, lo, ln F_j hi, lo}.
-  // ffpos = 1 when every knot is a normal double and no cell spans 2^100 or
-  // more (the exponent difference stays exact in floats).
+  // ffpos = 1 when every knot is a normal double, no cell spans 2^100 or
+  // more (the exponent difference stays exact in floats) and the set has one
+  // member (see load_impl in grid.cu).
   const float4 *xposff, *qposff, *aposff, *lnfff;
   int ffpos;
   const float2 *lnfff2;  // ln(F_j / 2) as a float pair (the high-significand steps)
+  float q101ff[4];        // the 1.01 Q2min site's position u and 1 - u as float pairs
 };
 
 // ---------------------------------------------------------------------------

@@ -419,6 +419,92 @@ __device__ __forceinline__ void store_point_ff(Rec64 &R, int slot, const NearFF 
   }
 }
 
+// ---- continued points on float-float grids: sites without FP64 -------------
+// The sites and rule parameters of a point outside the grid (as sites() and
+// store_point give them) from ffpos.cuh: the in-grid coordinate's position,
+// p_x = ln(x/x0)/d0 below x0, p_q = -ln(Q^2/Q2max)/d_top above Q2max, and
+// below Q2min rho = Q^2/Q2min (one FP64 product) with ln rho.  The other
+// sites sit on knots (t = 0) except the low-Q^2 one at 1.01 Q2min.
+struct FarFF {
+  int cls, xc0, xc1, qc0, qc1;
+  bool q101;  // the second Q site is 1.01 Q2min (else a knot)
+  ff2 t0, ts0, u0, us0, px, pq, lr;
+};
+__device__ __forceinline__ FarFF far_sites_ff(const GridView &g, const long long *xkeys, const long long *qkeys,
+                                              const float4 *LF, const float2 *LF2, double x, double q2) {
+  FarFF r;
+  r.xc0 = r.xc1 = r.qc0 = r.qc1 = 0;
+  r.q101 = false;
+  r.t0 = r.u0 = r.px = r.pq = r.lr = ff2{0.f, 0.f};
+  r.ts0 = r.us0 = ff2{1.f, 0.f};
+  const long long kx = __double_as_longlong(x), kq = __double_as_longlong(q2);
+  if (!(kq > 0 && kq < 0x7FF0000000000000LL && kx > 0 && kx <= __double_as_longlong(g.xlast))) {
+    r.cls = C_INVALID;
+    return r;
+  }
+  const bool lowx = kx < __double_as_longlong(g.x0);
+  const bool lowq = kq < __double_as_longlong(g.q2min), highq = kq > __double_as_longlong(g.q2max);
+  if (!lowx) {
+    const int i = search_cell(xkeys, g.nx, g.xstep, kx);
+    r.xc0 = i;
+    const bool k1 = kx != xkeys[i];
+    ff_cell_pos2(kx, xkeys[i], k1 ? xkeys[i + 1] : 0, g.xposff[i], k1 ? g.xposff[i + 1] : make_float4(0.f, 0.f, 0.f, 0.f),
+                 LF, LF2, r.t0, r.ts0);
+  } else {
+    r.xc1 = 1;
+    const float4 k0 = g.xposff[0];
+    r.px = ff_mul(ff_ln_ratio(ff_ln_sig(kx, LF, LF2), xkeys[0], k0.x, k0.y), ff2{k0.z, k0.w});
+  }
+  if (!lowq && !highq) {
+    const int j = search_cell(qkeys, g.nrows, g.qstep, kq);
+    r.qc0 = g.row_qc[j];
+    const bool k1 = kq != qkeys[j];
+    ff_cell_pos2(kq, qkeys[j], k1 ? qkeys[j + 1] : 0, g.qposff[j], k1 ? g.qposff[j + 1] : make_float4(0.f, 0.f, 0.f, 0.f),
+                 LF, LF2, r.u0, r.us0);
+  } else if (highq) {
+    r.qc0 = g.nqc;
+    r.qc1 = g.top_qc;
+    const float4 kt = g.qposff[g.nrows - 1], kc = g.qposff[g.nrows - 2];  // Q2max; its cell's width
+    r.pq = ff_mul(ff_ln_ratio(ff_ln_sig(kq, LF, LF2), qkeys[g.nrows - 1], kt.x, kt.y), ff2{-kc.z, -kc.w});
+  } else {
+    r.qc1 = g.q101_qc;
+    r.q101 = true;
+    r.pq = ff_of(q2 * g.inv_q2min);
+    const float4 k0 = g.qposff[0];
+    r.lr = ff_ln_ratio(ff_ln_sig(kq, LF, LF2), qkeys[0], k0.x, k0.y);
+  }
+  r.cls = lowx ? (highq ? C_LOWX_HIGHQ : lowq ? C_LOWX_LOWQ : C_LOWX) : (highq ? C_HIGHQ : lowq ? C_LOWQ : C_IN);
+  return r;
+}
+__device__ __forceinline__ void store_point_far_ff(Rec64 &R, int slot, const FarFF &ps, long long ob,
+                                                   const GridView &g) {
+  R.cls[slot] = ps.cls;
+  R.xc0[slot] = ps.xc0; R.xc1[slot] = ps.xc1; R.qc0[slot] = ps.qc0; R.qc1[slot] = ps.qc1;
+  R.ob[slot] = ob;
+  if (ps.cls == C_INVALID) return;
+  reinterpret_cast<float2 &>(R.px[slot]) = make_float2(ps.px.h, ps.px.l);
+  reinterpret_cast<float2 &>(R.pq[slot]) = make_float2(ps.pq.h, ps.pq.l);
+  reinterpret_cast<float2 &>(R.lr[slot]) = make_float2(ps.lr.h, ps.lr.l);
+  float2 *W2 = reinterpret_cast<float2 *>(R.W[slot]);
+  ff2 B[4];
+  ff_bernstein2(ps.t0, ps.ts0, B);
+#pragma unroll
+  for (int k = 0; k < 4; k++) W2[k] = make_float2(B[k].h, B[k].l);
+#pragma unroll
+  for (int k = 0; k < 4; k++) W2[4 + k] = make_float2(k == 0 ? 1.f : 0.f, 0.f);  // on a knot: t = 0
+  ff_bernstein2(ps.u0, ps.us0, B);
+#pragma unroll
+  for (int k = 0; k < 4; k++) W2[8 + k] = make_float2(B[k].h, B[k].l);
+  if (ps.q101) {
+    ff_bernstein2(ff2{g.q101ff[0], g.q101ff[1]}, ff2{g.q101ff[2], g.q101ff[3]}, B);
+#pragma unroll
+    for (int k = 0; k < 4; k++) W2[12 + k] = make_float2(B[k].h, B[k].l);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; k++) W2[12 + k] = make_float2(k == 0 ? 1.f : 0.f, 0.f);
+  }
+}
+
 // Bernstein weights of a point's sites into its record slot (float-float
 // for continuation points when ff is set).
 __device__ __forceinline__ void store_point(Rec64 &R, int slot, const PointSites<double> &ps, long long ob,
@@ -555,7 +641,7 @@ __device__ __forceinline__ int far_class(const GridView &g, double x, double q2)
 // positions and the continuation code: two blocks per SM give it the
 // registers to do so without spilling.
 template <int MODE, int PART>
-__global__ void __launch_bounds__(kThreads, PART == PART_ALL && MODE != MODE_MEMBERS ? 2 : 3)
+__global__ void __launch_bounds__(kThreads, (PART == PART_ALL && MODE != MODE_MEMBERS) || PART == PART_FAR ? 2 : 3)
 k_xf64(GridView g, const double *__restrict__ xa, const double *__restrict__ qa, const double *__restrict__ xb,
        double s, long long n, int col0, int ncol, int mchunk, double *__restrict__ out,
        double *__restrict__ as_out, McGen gen) {
@@ -586,13 +672,16 @@ k_xf64(GridView g, const double *__restrict__ xa, const double *__restrict__ qa,
   if (want_as) load_keys<double>(g, akeys, 2);
   for (int i = threadIdx.x; i < kLogTab; i += kThreads) { LTt[i] = g.tlogtab[i]; LTh[i] = g.tloghtab[i]; }
   const LogTabs LT{LTt, LTh};
-  // float-float positions (ffpos.cuh) of in-grid points and alpha_s: their
-  // steps table after the queues (not in the far launch, which has neither)
+  // float-float positions (ffpos.cuh) of in-grid points, continued points'
+  // sites and alpha_s: their steps table after the queues
   float4 *LF = reinterpret_cast<float4 *>(smem + off + (kQueue ? kWarps * sizeof(Queue64) : 0));
   float2 *LF2 = reinterpret_cast<float2 *>(LF + kLogTab);
-  if (PART != PART_FAR && g.ffpos)
+  if (g.ffpos)
     for (int i = threadIdx.x; i < kLogTab; i += kThreads) { LF[i] = g.lnfff[i]; LF2[i] = g.lnfff2[i]; }
-  const bool ffp = g.ff && g.ffpos;  // in-grid positions in float-float
+  // positions and continuation sites in float-float (member sets keep the
+  // FP64 logarithm: their grids have ffpos = 0, and the kernel is smaller
+  // without the other path)
+  const bool ffp = MODE != MODE_MEMBERS && g.ff && g.ffpos;
   for (int i = threadIdx.x; i < kFFLogTab; i += kThreads) FTl[i] = g.fflog[i];
   for (int i = threadIdx.x; i < kFFExpTab; i += kThreads) FTe[i] = g.ffexp[i];
   const FFTabs FT{FTl, FTe};
@@ -635,12 +724,20 @@ k_xf64(GridView g, const double *__restrict__ xa, const double *__restrict__ qa,
     if (present) {
       point_of(Q.idx[c][from + lane], x, q2, ob);
     }
-    PointSites<double> ps;
-    ps.cls = -1;
-    if (present) ps = sites(g, xkeys, qkeys, x, q2, LT, lq);
-    int slot = 0;
-    const int np = sort_slots<C_LOWX, C_HIGHQ, C_LOWQ, C_LOWX_HIGHQ, C_LOWX_LOWQ>(ps.cls, lane, slot);
-    if (present) store_point(R, slot, ps, ob, g.ff);
+    int slot = 0, np;
+    if (ffp) {  // warp-uniform: sites and rule parameters without the FP64 logarithm
+      FarFF fs;
+      fs.cls = -1;
+      if (present) fs = far_sites_ff(g, xkeys, qkeys, LF, LF2, x, q2);
+      np = sort_slots<C_LOWX, C_HIGHQ, C_LOWQ, C_LOWX_HIGHQ, C_LOWX_LOWQ>(fs.cls, lane, slot);
+      if (present) store_point_far_ff(R, slot, fs, ob, g);
+    } else {
+      PointSites<double> ps;
+      ps.cls = -1;
+      if (present) ps = sites(g, xkeys, qkeys, x, q2, LT, lq);
+      np = sort_slots<C_LOWX, C_HIGHQ, C_LOWQ, C_LOWX_HIGHQ, C_LOWX_LOWQ>(ps.cls, lane, slot);
+      if (present) store_point(R, slot, ps, ob, g.ff);
+    }
     __syncwarp();
     items64<MODE == MODE_MC>(g, R, np, nc, cbase, 0, 0, out, LT, ET, FT, lane);
     __syncwarp();
@@ -716,7 +813,7 @@ k_xf64(GridView g, const double *__restrict__ xa, const double *__restrict__ qa,
           // launch leaves them to the far one)
           if (present) nf = near_sites_ff(g, xkeys, qkeys, LF, LF2, x, q2);
           ps.cls = nf.cls;
-          if (PART != PART_NEAR && is_far(nf.cls)) ps = sites(g, xkeys, qkeys, x, q2, LT, lq);
+          if (PART != PART_NEAR && !kQueue && is_far(nf.cls)) ps = sites(g, xkeys, qkeys, x, q2, LT, lq);
         } else {
           if (present) ps = sites(g, xkeys, qkeys, x, q2, LT, lq);
           // in-grid points contract in float-float, except exact knot hits
@@ -793,7 +890,7 @@ static size_t xf64_smem(const GridView &g) {
   return keys_bytes(g.nx, 8) + keys_bytes(g.nrows, 8) + keys_bytes(g.na, 8) + sizeof(double2) * kLogTab +
          keys_bytes(kLogTab, 8) + sizeof(float4) * kFFLogTab + sizeof(float2) * kFFExpTab +
          kWarps * (sizeof(Rec64) + (MODE == MODE_MEMBERS || PART == PART_NEAR ? 0 : sizeof(Queue64))) +
-         (PART == PART_FAR ? 0 : (sizeof(float4) + sizeof(float2)) * kLogTab);
+         (sizeof(float4) + sizeof(float2)) * kLogTab;
 }
 
 // Batches of at least this many points take the two launches (near, far).

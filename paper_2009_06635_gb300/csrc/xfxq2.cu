@@ -345,6 +345,9 @@ static int do_mc(const pdf_grid *g, const T *x1, const T *x2, T s, size_t n, T *
 
 int launch_members_f64(const pdf_grid *g, const double *x, const double *q2, long long n, double *out,
                        cudaStream_t st) {
+  // one member: the layout [1][n][nf] is the points layout, and the points
+  // kernel gives the bits xfxq2_all_flavours gives
+  if (g->v.nmem == 1) return launch_xf64(g, MODE_POINTS, x, q2, nullptr, 0.0, n, 0, g->v.nf, out, nullptr, st);
   return launch_xf64(g, MODE_MEMBERS, x, q2, nullptr, 0.0, n, 0, g->v.nf, out, nullptr, st);
 }
 
