@@ -849,7 +849,7 @@ def our_arm(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64 (in-grid positions and contraction in float-float; continuation rules in float-float on FP64 sites; FP64 results)",
+        "dtype": "f64 (positions, contraction and continuation rules in float-float; FP64 results)",
         "data": "synthetic: seeded LHAPDF-shaped grid and log-uniform queries (no real PDF set in the container)",
         "config": {"workload": WORKLOAD, "points_per_rank": n, "evals_per_step_per_rank": evals_step,
                    "class_counts": counts, "l2": "inputs + outputs 1.3 GB per step > 129 MB L2, no flush",
