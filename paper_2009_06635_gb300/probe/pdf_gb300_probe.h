@@ -33,7 +33,10 @@ PDF_API int pdf_probe_fma_rate(int precision, int iters, double *flops_per_s);
  * exponential and quotient of the continuation rules, on a (and b) rounded to
  * float pairs (ln a within 2e-14 + 2e-14 |ln a| absolute for a in [2^-100, 2^100];
  * e^a within (1 + |a|) 1e-14 relative for |a| < 64; a / b within 4e-14
- * relative).  b may be NULL unless fn is 2 or 5.  The tables are the
+ * relative); fn 6, 7: the position t of x = a in its x cell and 1 - t, as
+ * the evaluation kernels take it in float-float (ffpos.cuh; NaN for a
+ * outside [x0, x_last]; PDF_ERR_ARG on a grid that keeps the FP64
+ * positions).  b may be NULL unless fn is 2 or 5.  The tables are the
  * grid's (a handle of the evaluation library, loaded in the same process).
  * Asynchronous on `stream`. */
 PDF_API int pdf_probe_math(const pdf_grid *grid, int fn, const double *a, const double *b, size_t n,

@@ -10,6 +10,7 @@
 
 #include "pdf_gb300_probe.h"
 #include "ffmath.cuh"
+#include "ffpos.cuh"
 #include "pdf_internal.cuh"
 
 namespace {
@@ -82,7 +83,22 @@ __global__ void k_math(GridView g, int fn, const double *a, const double *b, lon
     case 2: out[i] = ddiv(a[i], b[i]); break;
     case 3: out[i] = ff_to_d(ff_log(ff_of(a[i]), FT)); break;
     case 4: out[i] = ff_to_d(ff_exp(ff_of(a[i]), FT)); break;
-    default: out[i] = ff_to_d(ff_div(ff_of(a[i]), ff_of(b[i]))); break;
+    case 5: out[i] = ff_to_d(ff_div(ff_of(a[i]), ff_of(b[i]))); break;
+    default: {  // 6, 7: t and 1 - t of x = a[i] in its x cell (ffpos.cuh), a[i] in [x0, x_last]
+      const long long *xk = reinterpret_cast<const long long *>(g.xk);
+      const long long kx = __double_as_longlong(a[i]);
+      if (!(kx >= xk[0] && kx <= xk[g.nx - 1])) {  // outside the knots (or not a positive number)
+        out[i] = NAN;
+        break;
+      }
+      const int c = search_cell(xk, g.nx, g.xstep, kx);
+      const bool k1 = kx != xk[c];
+      ff2 t, ts;
+      ff_cell_pos2(kx, xk[c], k1 ? xk[c + 1] : 0, g.xposff[c], k1 ? g.xposff[c + 1] : make_float4(0.f, 0.f, 0.f, 0.f),
+                   g.lnfff, g.lnfff2, t, ts);
+      out[i] = ff_to_d(fn == 6 ? t : ts);
+      break;
+    }
   }
 }
 
@@ -93,7 +109,8 @@ extern "C" int pdf_probe_math(const pdf_grid *grid, int fn, const double *a, con
   using namespace pdfgb;
   if (!grid || (n > 0 && (!a || !out || ((fn == 2 || fn == 5) && !b))))
     return probe_error(PDF_ERR_NULL, "pdf_probe_math: NULL argument");
-  if (fn < 0 || fn > 5) return probe_error(PDF_ERR_ARG, "pdf_probe_math: fn must be 0 .. 5");
+  if (fn < 0 || fn > 7) return probe_error(PDF_ERR_ARG, "pdf_probe_math: fn must be 0 .. 7");
+  if (fn >= 6 && !grid->v.ffpos) return probe_error(PDF_ERR_ARG, "pdf_probe_math: the grid takes no float-float positions");
   if (n == 0) return PDF_OK;
   k_math<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(grid->v, fn, a, b, (long long)n, out);
   return probe_launch("pdf_probe_math");

@@ -119,3 +119,40 @@ def test_float_float_division(grid):
     want = a / b
     rel = np.abs(got - want) / np.abs(want)
     assert np.all(rel <= 4e-14), rel.max()
+
+
+def test_float_float_cell_positions(synth):
+    """The evaluation kernels' in-grid positions t = ln(x/x_i) / ln(x_(i+1)/x_i)
+    and 1 - t, taken in float-float from the bit patterns (ffpos.cuh), against
+    40-digit decimal logarithms: within 5e-14 absolute everywhere (the FP64
+    path's own rounding is ~2e-14), exactly 0 and 1 on the knots, and within
+    1e-13 relative for the small 1 - t next to x = 1, where the data vanish."""
+    from decimal import Decimal, getcontext
+
+    getcontext().prec = 40
+    g = synth.grid_full()
+    G = P.pdf_load_grid(g)
+    xk = g.x_knots
+    r = np.random.default_rng(8)
+    i = r.integers(0, len(xk) - 1, 3000)
+    x = np.exp(r.uniform(np.log(xk[i]), np.log(xk[i + 1])))
+    near = np.concatenate([xk[1:-1, None] * (1 + 10.0 ** -np.arange(1, 14))[None, :],
+                           xk[2:, None] * (1 - 10.0 ** -np.arange(1, 14))[None, :]]).ravel()[::7]
+    top = 1.0 - 10.0 ** -np.arange(1, 14)
+    x = np.concatenate([x, near, top, xk])
+    t, ts = run(G, 6, x), run(G, 7, x)
+    cell = np.searchsorted(xk, x, side="right") - 1
+    for k in range(x.size):
+        c = cell[k]
+        if c == len(xk) - 1:  # the last knot itself
+            assert t[k] == 0.0 and ts[k] == 1.0
+            continue
+        lo, hi = Decimal(float(xk[c])).ln(), Decimal(float(xk[c + 1])).ln()
+        et = (Decimal(float(x[k])).ln() - lo) / (hi - lo)
+        assert abs(Decimal(float(t[k])) - et) <= Decimal("5e-14"), (x[k], float(t[k]), float(et))
+        assert abs(Decimal(float(ts[k])) - (1 - et)) <= Decimal("5e-14"), (x[k], float(ts[k]), float(1 - et))
+        if x[k] == xk[c]:
+            assert t[k] == 0.0 and ts[k] == 1.0
+    for k in range(x.size - len(xk) - len(top), x.size - len(xk)):  # next to x = 1
+        ets = 1 - (Decimal(float(x[k])).ln() - Decimal(float(xk[-2])).ln()) / (-Decimal(float(xk[-2])).ln())
+        assert abs(Decimal(float(ts[k])) - ets) <= Decimal("1e-13") * ets, (x[k], float(ts[k]), float(ets))

@@ -33,3 +33,21 @@ def test_members_match_oracle_member_by_member(synth, oracle_mod):
     # the single-member calls evaluate member 0, bit for bit
     one = P.xfxq2_all_flavours(G, dev(x), dev(q2)).cpu().numpy()
     assert np.array_equal(one, out[0], equal_nan=True)
+
+
+def test_one_member_set_takes_the_points_kernel(synth, oracle_mod):
+    """A set of one member evaluated as a member set gives the bits of the
+    all-flavour call on the same grid (it runs the points kernel), and the
+    oracle's values."""
+    torch.cuda.set_device(0)
+    g0, vals = synth.grid_members(1)
+    G = P.pdf_load_grid(g0, member_values=vals)
+    assert G.nmem == 1
+    x, q2 = synth.queries_full(30_011, 34)
+    out = P.xfxq2_all_members(G, dev(x), dev(q2)).cpu().numpy()
+    assert out.shape == (1, len(x), g0.nflav)
+    one = P.xfxq2_all_flavours(G, dev(x), dev(q2)).cpu().numpy()
+    assert np.array_equal(one, out[0], equal_nan=True)
+    og = oracle_mod.OracleGrid(x_knots=g0.x_knots, nq=g0.nq, q2_knots=g0.q2_knots, values=vals[0])
+    v, s, fl = og.xfxq2(x, q2)
+    assert_parity(out[0], v, s, fl, RTOL_FP64, "one member")
