@@ -141,6 +141,7 @@ extern "C" int pdf_mc_integrate(const pdf_grid *cg, const pdf_mc_config *cfg, un
   gen.lxmax = log(v.xlast);
   gen.xmax = v.xlast;
   gen.on = 1;
+  gen.et = v.texptab;
   const double L = gen.lxmax - gen.lxmin;
   cudaError_t e = cudaMemsetAsync(g->mc_acc, 0, 3 * sizeof(double), st);
   for (unsigned long long off = 0; off < n_events && e == cudaSuccess && rc == PDF_OK; off += chunk) {
