@@ -299,7 +299,8 @@ __device__ __forceinline__ void vjp_point(const GridView &g, const long long *xk
                                           double *__restrict__ gv, Staged *st) {
     const double x = xa[p], q2 = qa[p];
     double lq;
-    PointSites<double> ps = sites(g, xkeys, qkeys, x, q2, LT, lq);
+    PointSites<double> ps = g.ffpos ? sites_ffpos(g, xkeys, qkeys, g.lnfff, g.lnfff2, x, q2, LT, lq)
+                                    : sites(g, xkeys, qkeys, x, q2, LT, lq);
     if (ps.cls == C_INVALID) {
       if (gx) gx[p] = NAN;
       if (gq) gq[p] = NAN;

@@ -93,6 +93,40 @@ __device__ __forceinline__ PointSites<double> sites(const GridView &g, const lon
   return r;
 }
 
+// The same for a grid with float-float positions (ffpos.cuh): an in-grid
+// point's t, 1 - t, u, 1 - u from the bit patterns (no FP64 logarithm),
+// rounded to doubles; any other point as sites() gives it.  lq is left 0 for
+// in-grid points (their callers take alpha_s elsewhere).
+__device__ __forceinline__ PointSites<double> sites_ffpos(const GridView &g, const long long *xkeys,
+                                                          const long long *qkeys, const float4 *LF,
+                                                          const float2 *LF2, double x, double q2, LogTabs LT,
+                                                          double &lq) {
+  const long long kx = __double_as_longlong(x), kq = __double_as_longlong(q2);
+  const bool ingrid = kq >= __double_as_longlong(g.q2min) && kq <= __double_as_longlong(g.q2max) &&
+                      kx >= __double_as_longlong(g.x0) && kx <= __double_as_longlong(g.xlast);
+  if (!ingrid) return sites(g, xkeys, qkeys, x, q2, LT, lq);
+  PointSites<double> r;
+  lq = 0.0;
+  r.cls = C_IN;
+  r.xc1 = r.qc1 = 0;
+  r.t1 = r.u1 = r.px = r.pq = r.lr = 0.0;
+  const int i = search_cell(xkeys, g.nx, g.xstep, kx);
+  const int j = search_cell(qkeys, g.nrows, g.qstep, kq);
+  r.xc0 = i;
+  r.qc0 = g.row_qc[j];
+  ff2 t, ts, u, us;
+  const bool xk1 = kx != xkeys[i], qk1 = kq != qkeys[j];
+  ff_cell_pos2(kx, xkeys[i], xk1 ? xkeys[i + 1] : 0, g.xposff[i], xk1 ? g.xposff[i + 1] : make_float4(0.f, 0.f, 0.f, 0.f),
+               LF, LF2, t, ts);
+  ff_cell_pos2(kq, qkeys[j], qk1 ? qkeys[j + 1] : 0, g.qposff[j], qk1 ? g.qposff[j + 1] : make_float4(0.f, 0.f, 0.f, 0.f),
+               LF, LF2, u, us);
+  r.t0 = ff_to_d(t);
+  r.ts0 = ff_to_d(ts);
+  r.u0 = ff_to_d(u);
+  r.us0 = ff_to_d(us);
+  return r;
+}
+
 // ---- FP32 classification and sites -----------------------------------------
 // The comparisons against rounded-up/down float thresholds decide exactly as
 // FP64 comparisons of the float input against the FP64 knots would.  ln x
