@@ -20,6 +20,7 @@ import argparse
 import tempfile
 import ctypes
 import hashlib
+import re
 import json
 import math
 import os
@@ -89,18 +90,32 @@ def algorithmic_flops(counts, nflav):
     return sum(c * (FLOP_POINT + nflav * CLASS_EVAL_FLOPS[k]) for k, c in counts.items())
 
 
-# the sources each captured kernel is built from (a capture counts only while they are unchanged)
+# the translation units each captured kernel is built from, with everything
+# they include from the package (a capture counts only while all are unchanged)
 KERNEL_SOURCES = {
-    "k_xf64<points> near + far": ("xf64.cu", "ff.cuh", "ffmath.cuh", "tang.cuh", "sites.cuh", "pdf_internal.cuh",
-                                  "grid.cu"),
-    "k_xf32<points>": ("xfxq2.cu", "sites.cuh", "pdf_internal.cuh", "grid.cu"),
+    "k_xf64<points> near + far": ("xf64.cu", "grid.cu"),
+    "k_xf32<points>": ("xfxq2.cu", "grid.cu"),
 }
+_INCLUDE_RE = re.compile(r'^\s*#\s*include\s+"([^"]+)"', re.M)
+
+
+def kernel_source_files(kernel):
+    dirs = (ROOT / "paper_2009_06635_gb300" / "csrc", ROOT / "include")
+    seen, todo = [], list(KERNEL_SOURCES[kernel])
+    while todo:
+        name = todo.pop(0)
+        path = next((d / name for d in dirs if (d / name).exists()), None)
+        if path is None or path in seen:
+            continue
+        seen.append(path)
+        todo.extend(_INCLUDE_RE.findall(path.read_text()))
+    return seen
 
 
 def kernel_source_hash(kernel="k_xf64<points> near + far"):
     h = hashlib.sha256()
-    for name in KERNEL_SOURCES[kernel]:
-        h.update((ROOT / "paper_2009_06635_gb300" / "csrc" / name).read_bytes())
+    for path in kernel_source_files(kernel):
+        h.update(path.read_bytes())
     return h.hexdigest()[:16]
 
 
@@ -661,6 +676,8 @@ def our_arm(args):
 
     if args.only == "adjoint":  # the adjoint alone on --points points of the same law
         ax, aq, acot = S.adjoint_inputs(n, nf, 5 + 1000 * rank, 6 + 1000 * rank)
+        if args.law != "bench":  # points of one class, same cotangents
+            ax, aq = S.queries_class(g, args.law, n, 5 + 1000 * rank)
         axd, aqd, acd = torch.from_numpy(ax).to(dev), torch.from_numpy(aq).to(dev), torch.from_numpy(acot).to(dev)
         agx, agq = torch.empty_like(axd), torch.empty_like(aqd)
         agv = torch.zeros((G.nrows, G.nx, nf), dtype=torch.float64, device=dev)
@@ -913,7 +930,7 @@ def main():
                     help="with --only surrogate: the surrogate's target")
     ap.add_argument("--law", default="bench", choices=["bench", "in", "lowx", "highq", "lowq", "lowx_highq",
                                                        "lowx_lowq"],
-                    help="with --only fp64/fp32: the benchmark's query law, or points of one class only")
+                    help="with --only fp64/fp32/adjoint: the benchmark's query law, or points of one class only")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

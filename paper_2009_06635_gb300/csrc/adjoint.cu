@@ -347,6 +347,20 @@ __device__ __forceinline__ void vjp_point(const GridView &g, const long long *xk
     bool xk[2], qk[2];
     for (int a = 0; a < nsx; a++) xk[a] = X[a].B[1] == 0.0 && X[a].B[2] == 0.0 && X[a].B[3] == 0.0;
     for (int b = 0; b < nsq; b++) qk[b] = Q[b].B[1] == 0.0 && Q[b].B[2] == 0.0 && Q[b].B[3] == 0.0;
+    // the sorted kernel's warps of points that take both rules: when all 32
+    // lanes have the same class and sites (hence the same knots), each knot
+    // term is summed over the warp and added by one lane (k0 + 1 of each
+    // site in 14 bits)
+    bool wsum = false;
+    if (STAGE && gv && lowx && !realq && g.nx < 16383 && g.nrows < 16383) {
+      const unsigned long long key =
+          (unsigned long long)cls | (unsigned long long)(X[0].k0 + 1) << 4 |
+          (unsigned long long)(lowx ? X[1].k0 + 1 : 0) << 18 | (unsigned long long)(Q[0].k0 + 1) << 32 |
+          (unsigned long long)(realq ? 0 : Q[1].k0 + 1) << 46;
+      int same = 0;
+      if (__activemask() == 0xffffffffu) __match_all_sync(0xffffffffu, key, &same);
+      wsum = same != 0;
+    }
     double sx = 0.0, sq = 0.0;
     for (int f = 0; f < g.nf; f++) {
       const double c = cot[p * g.nf + f];
@@ -392,7 +406,28 @@ __device__ __forceinline__ void vjp_point(const GridView &g, const long long *xk
         for (int b = 0; b < nsq; b++) {
           dx = fma(lam[a][b] * Ft[a][b], X[a].dpos, dx);
           dq = fma(lam[a][b] * Fu[a][b], Q[b].dpos, dq);
-          if (gv) {
+          if (STAGE && wsum) {
+            // the same knots in every lane: a term that is zero in every lane is skipped
+            const double m = c * lam[a][b];
+            for (int bb = 0; bb < 4; bb++) {
+              const int row = Q[b].k0 + bb;
+              const double wq = Q[b].w[bb];
+              if (!__any_sync(0xffffffffu, (__double_as_longlong(m * wq) << 1) != 0) || row < 0 || row >= g.nrows)
+                continue;
+              const double mq = m * wq;
+              for (int aa = 0; aa < 4; aa++) {
+                const int col = X[a].k0 + aa;
+                const double wx = X[a].w[aa];
+                if (!__any_sync(0xffffffffu, (__double_as_longlong(wx) << 1) != 0) || col < 0 || col >= g.nx)
+                  continue;
+                double v = mq * wx;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if ((threadIdx.x & 31) == 0 && (__double_as_longlong(v) << 1) != 0)
+                  atomicAdd(gv + ((size_t)row * g.nx + col) * g.nf + f, v);
+              }
+            }
+          } else if (gv) {
             // zero tests on bit patterns (the FP64 pipe is the busy unit);
             // c lam w_b folded once per row, then times each w_a
             const double m = c * lam[a][b];
@@ -499,25 +534,36 @@ k_vjp(GridView g, const double *__restrict__ xa, const double *__restrict__ qa, 
 }
 
 // ---- large batches: points sorted by cell ------------------------------------
-// A counting sort puts the continuation points first (by kind: x rule, Q rule,
-// both; then invalid points) and the in-grid points after them, cell by cell.
-// A warp then takes 32 consecutive sorted points: continuation warps are of
-// one kind (as with the queues above), and in-grid warps hold runs of points
-// that share a cell, hence the same 16 knots.  Their knot-value gradient is
-// contracted over the run in float-float on the FMA pipe,
+// A counting sort puts the continuation points first, by kind (below), then
+// the invalid points, then the in-grid points cell by cell.  A warp then
+// takes 32 consecutive sorted points: continuation warps are of one kind (as
+// with the queues above), and in-grid warps hold runs of points that share a
+// cell, hence the same 16 knots.  Their knot-value gradient is contracted over the run in
+// float-float on the FMA pipe,
 //   dL/df_(ab, f) += sum_p c_pf w_b(u_p) w_a(t_p),
 // and added with one FP64 atomic per knot and flavour per run instead of one
 // per point (the per-point products were a third of an in-grid point's FP64
 // work, and their atomics a stream of L2 reductions).
-constexpr int kSortBins0 = 4;        // bins 0..2: continuation kinds, 3: invalid, then the cells
+//
+// Continuation bins: the x rule alone (bin 0), a Q rule alone (bin 1), both
+// rules below (bin 2) and above the Q^2 range (bin 3).  Points that take both
+// rules all add to the same few knots (x0, x1 in the bottom or top rows), so
+// a warp of them sums each knot term before one atomic (without that, every
+// such point's atomics went to the same addresses, one after another: 20 to
+// 44 ms per 1e6 of them, against 5 to 8 ms).  The other continuation points
+// spread their atomics over the rows or columns of their cells; summing
+// theirs in the warp (sorted by cell) costs more FP64 additions than the
+// waits it saves.
+constexpr int kSortCont = 4;  // continuation bins; the invalid bin follows, then the cells
 constexpr int kSortMaxBins = 65540;  // above this the grid has too many cells for runs to form
 constexpr long long kSortMinN = 2048;
 constexpr int kSortThreads = 128;    // three blocks per SM: 12 warps at <= 168 registers
 constexpr int kStPad = 17;           // float2 per staged row (16 used): 2-way bank conflicts at most
 
-// Sort key of a point: its kind for a continuation or invalid point, else
-// kSortBins0 + (Q cell) nx + (x cell), from integer range tests and searches
-// on the raw bit patterns (no logarithm); counts per key in cnt.
+// Sort key of a point: its continuation bin, the invalid bin, or for an
+// in-grid point (bins after those) its cell, (Q cell) nx + (x cell), from
+// integer range tests and searches on the raw bit patterns (no logarithm);
+// counts per key in cnt.
 __global__ void __launch_bounds__(256) k_adj_key(GridView g, const double *__restrict__ xa,
                                                  const double *__restrict__ qa, long long n, unsigned nb,
                                                  unsigned *__restrict__ keys, unsigned *__restrict__ cnt) {
@@ -530,6 +576,7 @@ __global__ void __launch_bounds__(256) k_adj_key(GridView g, const double *__res
   const int lane = threadIdx.x & 31;
   const long long kxlast = __double_as_longlong(g.xlast), kx0 = __double_as_longlong(g.x0);
   const long long kqmin = __double_as_longlong(g.q2min), kqmax = __double_as_longlong(g.q2max);
+  const unsigned cont = (unsigned)kSortCont;  // the invalid bin; in-grid bins follow
   // whole warps iterate together (blockDim is a multiple of 32) for the match
   for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += (long long)gridDim.x * blockDim.x) {
     const long long p = base + threadIdx.x;
@@ -539,14 +586,15 @@ __global__ void __launch_bounds__(256) k_adj_key(GridView g, const double *__res
       const bool valid = kq > 0 && kq < 0x7FF0000000000000LL && kx > 0 && kx <= kxlast;
       const bool fx = kx < kx0, fq = kq < kqmin || kq > kqmax;
       if (!valid) {
-        key = 3u;
+        key = cont;
       } else if (fx || fq) {
-        key = fx ? (fq ? 2u : 0u) : 1u;
+        key = fx ? (fq ? (kq > kqmax ? 3u : 2u) : 0u) : 1u;
       } else {
         const int i = search_cell(xkeys, g.nx, g.xstep, kx);
         const int j = search_cell(qkeys, g.nrows, g.qstep, kq);
-        key = min(kSortBins0 + (unsigned)max(g.row_qc[j], 0) * (unsigned)g.nx + (unsigned)i, nb - 1u);
+        key = cont + 1u + (unsigned)max(g.row_qc[j], 0) * (unsigned)g.nx + (unsigned)i;
       }
+      key = min(key, nb - 1u);
       keys[p] = key;
     }
     const unsigned peers = __match_any_sync(0xffffffffu, key);
@@ -696,7 +744,7 @@ extern "C" int xfxq2_all_flavours_vjp(const pdf_grid *grid, const double *x, con
   if (sms < 1) sms = 1;
   const size_t kbytes = keys_bytes(g.nx, 8) + keys_bytes(g.nrows, 8);
   const size_t smem = kbytes + (sizeof(double2) + sizeof(double)) * kLogTab + sizeof(double) * kExpTab;
-  const long long nb = kSortBins0 + (long long)(g.nqc + 1) * g.nx;
+  const long long nb = kSortCont + 1 + (long long)(g.nqc + 1) * g.nx;
 
   // large batches on a float-float-safe grid: sorted by cell (see k_vjp_sorted)
   if ((long long)n >= kSortMinN && n < (1ull << 31) && g.ff && g.nf <= 16 && nb <= kSortMaxBins) {

@@ -214,6 +214,34 @@ def test_sorted_batch_matches_oracle_and_small_batches(full, synth):
     assert (np.abs(gv - cv) <= 1e-12 * gabs + 1e-300).all()
 
 
+@pytest.mark.parametrize("cls", ["lowx", "highq", "lowq", "lowx_highq", "lowx_lowq"])
+def test_sorted_continuation_warps_sum_their_knot_terms(full, synth, cls):
+    """Continuation points are sorted by kind; those that take both rules
+    (all on the same few knots) by side too, and a warp of 32 of them that
+    share their sites sums each knot term over the warp before one atomic.
+    Batches of one class against the oracle's knot gradient and against
+    small (unsorted) batches."""
+    g, G, og = full
+    n = 6000
+    x, q2 = synth.queries_class(g, cls, n, 41)
+    cot = np.random.default_rng(42).standard_normal((n, g.nflav))
+    gx, gq, gv = run_vjp(G, x, q2, cot)  # sorted
+    parts = [run_vjp(G, x[a:a + 1500], q2[a:a + 1500], cot[a:a + 1500]) for a in range(0, n, 1500)]
+    cx = np.concatenate([p[0] for p in parts])
+    cq = np.concatenate([p[1] for p in parts])
+    cv = sum(p[2] for p in parts)
+    assert np.isfinite(gx).all() and np.isfinite(gq).all()
+    go, gabs = og.knot_grad(x, q2, cot, with_abs=True)
+    assert np.abs(gabs).max() > 0
+    for got in (gv, cv):
+        err = np.abs(got - go)
+        assert (err <= 1e-10 * gabs + 1e-300).all(), (err / np.maximum(gabs, 1e-300)).max()
+    assert (np.abs(gv - cv) <= 1e-12 * gabs + 1e-300).all()
+    # the per-point gradients do not depend on the order the points run in
+    assert (np.abs(gx - cx) <= 1e-13 * np.abs(cx) + 1e-300).all()
+    assert (np.abs(gq - cq) <= 1e-13 * np.abs(cq) + 1e-300).all()
+
+
 def test_sorted_batch_keeps_each_knots_precision(full, synth):
     """Float-float run sums are used only for weights and cotangents of
     moderate size; a point with a weight or cotangent far from 1 (here whole
