@@ -293,7 +293,10 @@ PDF_API int xfxq2_all_flavours_host_noalloc(const pdf_grid *grid, const double *
  * Batches of 2048 points or more (grids with at most 16 flavours and
  * ~65K cells) are sorted by cell on the device first: the call then takes
  * 8 B per point (plus 4 B per cell) of stream-ordered scratch from a memory
- * pool the library keeps per device, and releases it on `stream`; if that
+ * pool the library keeps per device, and with grad_values up to 16 zeroed
+ * copies of grad_values (64 MB at most, fewer where the scratch limit
+ * requires) that take the continuation points' knot terms and are added
+ * into grad_values at the end; it releases the scratch on `stream`.  If that
  * memory is not available it runs the unsorted kernel instead.  Both
  * paths agree to rounding (the sorted one sums in-grid knot terms per cell
  * in float-float, to ~2^-46 of each knot's own terms). */

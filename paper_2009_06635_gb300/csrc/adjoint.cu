@@ -144,6 +144,62 @@ __device__ __forceinline__ RuleD rule_d(double f0, double f1, double p, bool low
   return R;
 }
 
+__device__ __noinline__ RuleD rule_d_fp64(double f0, double f1, double p, bool lowq, double rho, double lr,
+                                          double irho, double iL, LogTabs LT, const double *ET) {
+  return rule_d(f0, f1, p, lowq, rho, lr, irho, iL, LT, ET);
+}
+
+// The same rule in float-float on the FMA pipe (ffmath.cuh), for positive
+// f0, f1 on a float-float-safe grid: the FP64 pipe keeps only the
+// conversions in and out.  A rule's point constants as float pairs, once per
+// point: a, b and 1 - a of the log form, and dv/dpar = v (k1 ln r + k2) --
+// the pair rule k1 = 1, k2 = 0; the low-Q^2 rule k1 = (lr + 1) / ln1.01,
+// k2 = (1 - rho) / rho - lr.  Anything outside the pairs' range (a quotient,
+// exponent or result beyond 2^+-100, |exponent| >= 64), and f0 or f1 not
+// positive, takes the FP64 rule.
+struct RuleFF {
+  ff2 a, b, oma, k1, k2;
+  double p, rho, lr, irho, iL;
+  bool lowq;
+};
+__device__ __forceinline__ RuleFF rule_ff_consts(double p, bool lowq, double rho, double lr, double irho,
+                                                 double iL) {
+  RuleFF c;
+  c.p = p; c.rho = rho; c.lr = lr; c.irho = irho; c.iL = iL; c.lowq = lowq;
+  // (explicit roundings: both kernels that inline this get the same constants)
+  const double a = lowq ? __dmul_rn(__dmul_rn(rho, lr), iL) : p;
+  c.a = ff_of(a);
+  c.b = ff_of(lowq ? __dmul_rn(__dsub_rn(1.0, rho), lr) : 0.0);
+  c.oma = ff_of(__dsub_rn(1.0, a));
+  c.k1 = lowq ? ff_of(__dmul_rn(__dadd_rn(lr, 1.0), iL)) : ff2{1.f, 0.f};
+  c.k2 = ff_of(lowq ? __dsub_rn(__dmul_rn(__dsub_rn(1.0, rho), irho), lr) : 0.0);
+  return c;
+}
+__device__ __forceinline__ bool ff_fine(ff2 v) { return v.h == 0.f || (fabsf(v.h) >= 0x1p-100f && fabsf(v.h) < 0x1p100f); }
+__device__ __forceinline__ RuleD rule_d_ff(double f0, double f1, const RuleFF &c, FFTabs FT, LogTabs LT,
+                                           const double *ET) {
+  if (__double_as_longlong(f0) > 0 && __double_as_longlong(f1) > 0) {
+    const ff2 F0 = ff_of(f0), F1 = ff_of(f1);
+    if (ff_fine(F0) && ff_fine(F1)) {
+      const ff2 r = ff_div(F1, F0);
+      if (ff_fine(r)) {
+        const ff2 lnr = ff_log(r, FT);
+        const ff2 y = ff_add(ff_mul(c.a, lnr), c.b);
+        if (fabsf(y.h) < 64.f) {
+          const ff2 e = ff_exp(y, FT);
+          const ff2 v = ff_mul(F0, e);
+          const ff2 d0 = ff_mul(e, c.oma);
+          const ff2 d1 = ff_div(ff_mul(e, c.a), r);
+          const ff2 dp = ff_mul(v, ff_add(ff_mul(c.k1, lnr), c.k2));
+          if (ff_fine(v) && ff_fine(d0) && ff_fine(d1) && ff_fine(dp))
+            return {ff_to_d(v), ff_to_d(d0), ff_to_d(d1), ff_to_d(dp)};
+        }
+      }
+    }
+  }
+  return rule_d_fp64(f0, f1, c.p, c.lowq, c.rho, c.lr, c.irho, c.iL, LT, ET);
+}
+
 // Where an in-grid point leaves its knot-weight terms for the warp's
 // contraction (k_vjp_sorted): its 16 weights w_b(u) w_a(t) and its nf
 // cotangents as float-float pairs, its cell and the cell's first knot.
@@ -151,6 +207,7 @@ struct Staged {
   float2 *w, *c;
   int cell, xk0, qk0;
   bool ing;
+  double *gvc;  // where a continuation point's knot terms go (one of the private copies, or gv)
 };
 
 // FP64 knot scatter of one in-grid point, out of line: the staged path
@@ -344,6 +401,13 @@ __device__ __forceinline__ void vjp_point(const GridView &g, const long long *xk
     }
     // sites on a knot (weights (1, 0, 0, 0)): the x rule's x sites, the Q rule's Q sites but the
     // low-Q^2 rule's second one
+    // the rules' point constants in float pairs (float-float-safe grids)
+    const FFTabs FT{g.fflog, g.ffexp};
+    RuleFF cq, cx;
+    if (g.ff) {
+      if (!realq) cq = rule_ff_consts(ps.pq, lowq, ps.pq, ps.lr, irho, iL);
+      if (lowx) cx = rule_ff_consts(ps.px, false, 0.0, 0.0, 0.0, 0.0);
+    }
     bool xk[2], qk[2];
     for (int a = 0; a < nsx; a++) xk[a] = X[a].B[1] == 0.0 && X[a].B[2] == 0.0 && X[a].B[3] == 0.0;
     for (int b = 0; b < nsq; b++) qk[b] = Q[b].B[1] == 0.0 && Q[b].B[2] == 0.0 && Q[b].B[3] == 0.0;
@@ -351,6 +415,7 @@ __device__ __forceinline__ void vjp_point(const GridView &g, const long long *xk
     // lanes have the same class and sites (hence the same knots), each knot
     // term is summed over the warp and added by one lane (k0 + 1 of each
     // site in 14 bits)
+    double *const gvc = STAGE && st ? st->gvc : gv;
     bool wsum = false;
     if (STAGE && gv && lowx && !realq && g.nx < 16383 && g.nrows < 16383) {
       const unsigned long long key =
@@ -375,7 +440,8 @@ __device__ __forceinline__ void vjp_point(const GridView &g, const long long *xk
       double A[2], l0[2], l1[2], lpar[2];
       for (int a = 0; a < nsx; a++) {
         if (!realq) {
-          const RuleD R = rule_d(F[a][0], F[a][1], ps.pq, lowq, ps.pq, ps.lr, irho, iL, LT, ET);
+          const RuleD R = g.ff ? rule_d_ff(F[a][0], F[a][1], cq, FT, LT, ET)
+                               : rule_d(F[a][0], F[a][1], ps.pq, lowq, ps.pq, ps.lr, irho, iL, LT, ET);
           A[a] = R.v; l0[a] = R.d0; l1[a] = R.d1; lpar[a] = R.dpar;
         } else {
           A[a] = F[a][0]; l0[a] = 1.0; l1[a] = 0.0; lpar[a] = 0.0;
@@ -383,7 +449,8 @@ __device__ __forceinline__ void vjp_point(const GridView &g, const long long *xk
       }
       double o0 = 1.0, o1 = 0.0, dvpx = 0.0;
       if (lowx) {
-        const RuleD R = rule_d(A[0], A[1], ps.px, false, 0.0, 0.0, 0.0, 0.0, LT, ET);
+        const RuleD R = g.ff ? rule_d_ff(A[0], A[1], cx, FT, LT, ET)
+                             : rule_d(A[0], A[1], ps.px, false, 0.0, 0.0, 0.0, 0.0, LT, ET);
         o0 = R.d0; o1 = R.d1; dvpx = R.dpar;
       }
       double lam[2][2];
@@ -424,7 +491,7 @@ __device__ __forceinline__ void vjp_point(const GridView &g, const long long *xk
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
                 if ((threadIdx.x & 31) == 0 && (__double_as_longlong(v) << 1) != 0)
-                  atomicAdd(gv + ((size_t)row * g.nx + col) * g.nf + f, v);
+                  atomicAdd(gvc + ((size_t)row * g.nx + col) * g.nf + f, v);
               }
             }
           } else if (gv) {
@@ -441,7 +508,7 @@ __device__ __forceinline__ void vjp_point(const GridView &g, const long long *xk
                 const int col = X[a].k0 + aa;
                 const double wx = X[a].w[aa];
                 if ((__double_as_longlong(wx) << 1) == 0 || col < 0 || col >= g.nx) continue;
-                atomicAdd(gv + ((size_t)row * g.nx + col) * g.nf + f, mq * wx);
+                atomicAdd(gvc + ((size_t)row * g.nx + col) * g.nf + f, mq * wx);
               }
             }
           }
@@ -559,6 +626,8 @@ constexpr int kSortMaxBins = 65540;  // above this the grid has too many cells f
 constexpr long long kSortMinN = 2048;
 constexpr int kSortThreads = 128;    // three blocks per SM: 12 warps at <= 168 registers
 constexpr int kStPad = 17;           // float2 per staged row (16 used): 2-way bank conflicts at most
+constexpr int kAdjCopies = 16;       // private knot-gradient copies for continuation points (at most)
+constexpr size_t kAdjCopyBytes = 64u << 20;
 
 // Sort key of a point: its continuation bin, the invalid bin, or for an
 // in-grid point (bins after those) its cell, (Q cell) nx + (x cell), from
@@ -654,7 +723,7 @@ __global__ void __launch_bounds__(kSortThreads, 3)
 k_vjp_sorted(GridView g, const double *__restrict__ xa, const double *__restrict__ qa,
              const double *__restrict__ cot, long long n, const unsigned *__restrict__ perm,
              unsigned long long *__restrict__ next_tile, double *__restrict__ gx, double *__restrict__ gq,
-             double *__restrict__ gv) {
+             double *__restrict__ gv, double *__restrict__ gvp, int ncopy, long long pstride) {
   extern __shared__ __align__(16) unsigned char smem[];
   long long *xkeys = reinterpret_cast<long long *>(smem);
   long long *qkeys = reinterpret_cast<long long *>(smem + keys_bytes(g.nx, 8));
@@ -683,7 +752,7 @@ k_vjp_sorted(GridView g, const double *__restrict__ xa, const double *__restrict
     const long long tile = (long long)__shfl_sync(0xffffffffu, t, 0);
     if (tile >= ntiles) break;
     const long long pos = tile * 32 + lane;
-    Staged st{wrow, crow, -1, 0, 0, false};
+    Staged st{wrow, crow, -1, 0, 0, false, ncopy > 0 ? gvp + (tile % ncopy) * pstride : gv};
     if (pos < n) vjp_point<GV>(g, xkeys, qkeys, LT, ET, (long long)perm[pos], xa, qa, cot, gx, gq, gv, &st);
     if (GV) {
       __syncwarp();
@@ -727,6 +796,18 @@ k_vjp_sorted(GridView g, const double *__restrict__ xa, const double *__restrict
   }
 }
 
+// gv[i] += sum over the private copies of their element i (copies zeroed
+// before the sorted kernel; continuation points' knot terms went there).
+__global__ void __launch_bounds__(256) k_adj_fold(double *__restrict__ gv, const double *__restrict__ gvp,
+                                                  int ncopy, long long pstride) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < pstride;
+       i += (long long)gridDim.x * blockDim.x) {
+    double sum = 0.0;
+    for (int k = 0; k < ncopy; k++) sum += gvp[k * pstride + i];
+    if ((__double_as_longlong(sum) << 1) != 0) gv[i] += sum;
+  }
+}
+
 }  // namespace pdfgb
 
 using namespace pdfgb;
@@ -755,15 +836,30 @@ extern "C" int xfxq2_all_flavours_vjp(const pdf_grid *grid, const double *x, con
                                    : cache.blocks_per_sm(k_vjp_sorted<false>, kSortThreads, ssmem, false);
     void *buf = nullptr;
     const size_t cnt_bytes = ((size_t)nb * sizeof(unsigned) + 15) / 16 * 16;
-    const size_t bytes = cnt_bytes + 16 + 2 * ((n * sizeof(unsigned) + 15) / 16 * 16);
+    const size_t sort_bytes = cnt_bytes + 16 + 2 * ((n * sizeof(unsigned) + 15) / 16 * 16);
+    // private copies of the knot gradient for the continuation points' atomics
+    // (they add to the few knots next to the grid's edges, and spreading them
+    // over copies spreads the queues on those addresses)
+    const long long pstride = (long long)g.nrows * g.nx * g.nf;
+    int ncopy = 0;
+    if (grad_values && pstride > 0) {
+      ncopy = kAdjCopies;
+      while (ncopy > 1 && ((size_t)ncopy * pstride * sizeof(double) > kAdjCopyBytes ||
+                           sort_bytes + (size_t)ncopy * pstride * sizeof(double) > scratch_limit()))
+        ncopy >>= 1;
+      if (ncopy < 2) ncopy = 0;
+    }
+    const size_t copy_bytes = (size_t)ncopy * pstride * sizeof(double);
+    const size_t bytes = sort_bytes + copy_bytes;
     cudaMemPool_t pool = bytes <= scratch_limit() ? sort_pool(dev) : nullptr;
     if (per_sm >= 1 && pool && cudaMallocFromPoolAsync(&buf, bytes, pool, stream) == cudaSuccess) {
       unsigned *cnt = static_cast<unsigned *>(buf);
       auto *next_tile = reinterpret_cast<unsigned long long *>(static_cast<char *>(buf) + cnt_bytes);
-      unsigned *keys = reinterpret_cast<unsigned *>(static_cast<char *>(buf) + cnt_bytes + 16);
+      double *gvp = reinterpret_cast<double *>(static_cast<char *>(buf) + cnt_bytes + 16);
+      unsigned *keys = reinterpret_cast<unsigned *>(static_cast<char *>(buf) + cnt_bytes + 16 + copy_bytes);
       unsigned *perm = keys + (n * sizeof(unsigned) + 15) / 16 * 4;
       int rc = PDF_OK;
-      if (cudaMemsetAsync(buf, 0, cnt_bytes + 16, stream) != cudaSuccess)
+      if (cudaMemsetAsync(buf, 0, cnt_bytes + 16 + copy_bytes, stream) != cudaSuccess)
         rc = set_error(PDF_ERR_CUDA, "xfxq2_all_flavours_vjp: scratch");
       const unsigned sblocks = (unsigned)std::min<long long>(((long long)n + 255) / 256, 8LL * sms);
       if (!rc) {
@@ -772,12 +868,17 @@ extern "C" int xfxq2_all_flavours_vjp(const pdf_grid *grid, const double *x, con
         k_adj_place<<<sblocks, 256, 0, stream>>>(keys, (long long)n, cnt, perm);
         const unsigned blocks =
             (unsigned)std::min<long long>(((long long)n + kSortThreads - 1) / kSortThreads, (long long)sms * per_sm);
-        if (grad_values)
+        if (grad_values) {
           k_vjp_sorted<true><<<blocks, kSortThreads, ssmem, stream>>>(g, x, q2, cot, (long long)n, perm, next_tile,
-                                                                      grad_x, grad_q2, grad_values);
-        else
+                                                                      grad_x, grad_q2, grad_values, gvp, ncopy,
+                                                                      pstride);
+          if (ncopy > 0)
+            k_adj_fold<<<(unsigned)std::min<long long>((pstride + 255) / 256, 4LL * sms), 256, 0, stream>>>(
+                grad_values, gvp, ncopy, pstride);
+        } else {
           k_vjp_sorted<false><<<blocks, kSortThreads, ssmem, stream>>>(g, x, q2, cot, (long long)n, perm, next_tile,
-                                                                       grad_x, grad_q2, grad_values);
+                                                                       grad_x, grad_q2, grad_values, nullptr, 0, 0);
+        }
         rc = check_launch("xfxq2_all_flavours_vjp sorted kernels");
       }
       cudaFreeAsync(buf, stream);

@@ -237,9 +237,17 @@ def test_sorted_continuation_warps_sum_their_knot_terms(full, synth, cls):
         err = np.abs(got - go)
         assert (err <= 1e-10 * gabs + 1e-300).all(), (err / np.maximum(gabs, 1e-300)).max()
     assert (np.abs(gv - cv) <= 1e-12 * gabs + 1e-300).all()
-    # the per-point gradients do not depend on the order the points run in
-    assert (np.abs(gx - cx) <= 1e-13 * np.abs(cx) + 1e-300).all()
-    assert (np.abs(gq - cq) <= 1e-13 * np.abs(cq) + 1e-300).all()
+    # the per-point gradients: the oracle's, and the same whatever order the
+    # points run in (scales as in the tests above)
+    dx, dq = og.dxfxq2(x, q2, "x"), og.dxfxq2(x, q2, "q2")
+    _, s, _ = og.xfxq2(x, q2)
+    sx = np.abs(cot * dx).sum(axis=1) + (np.abs(cot) * s).sum(axis=1) / (x * min_log_spacing(g.x_knots))
+    sq = np.abs(cot * dq).sum(axis=1) + (np.abs(cot) * s).sum(axis=1) / (q2 * min_log_spacing(g.q2_knots))
+    for ax, aq in ((gx, gq), (cx, cq)):
+        assert (np.abs(ax - (cot * dx).sum(axis=1)) <= 1e-10 * sx).all()
+        assert (np.abs(aq - (cot * dq).sum(axis=1)) <= 1e-10 * sq).all()
+    assert (np.abs(gx - cx) <= 1e-13 * sx).all()
+    assert (np.abs(gq - cq) <= 1e-13 * sq).all()
 
 
 def test_sorted_batch_keeps_each_knots_precision(full, synth):
