@@ -654,10 +654,6 @@ k_xf64(GridView g, const double *__restrict__ xa, const double *__restrict__ qa,
   off += keys_bytes(g.nrows, 8);
   long long *akeys = reinterpret_cast<long long *>(smem + off);
   off += keys_bytes(g.na, 8);
-  double2 *LTt = reinterpret_cast<double2 *>(smem + off);
-  off += sizeof(double2) * kLogTab;
-  double *LTh = reinterpret_cast<double *>(smem + off);
-  off += keys_bytes(kLogTab, 8);
   float4 *FTl = reinterpret_cast<float4 *>(smem + off);
   off += sizeof(float4) * kFFLogTab;
   float2 *FTe = reinterpret_cast<float2 *>(smem + off);
@@ -670,18 +666,23 @@ k_xf64(GridView g, const double *__restrict__ xa, const double *__restrict__ qa,
   load_keys<double>(g, xkeys, 0);
   load_keys<double>(g, qkeys, 1);
   if (want_as) load_keys<double>(g, akeys, 2);
-  for (int i = threadIdx.x; i < kLogTab; i += kThreads) { LTt[i] = g.tlogtab[i]; LTh[i] = g.tloghtab[i]; }
-  const LogTabs LT{LTt, LTh};
-  // float-float positions (ffpos.cuh) of in-grid points, continued points'
-  // sites and alpha_s: their steps table after the queues
-  float4 *LF = reinterpret_cast<float4 *>(smem + off + (kQueue ? kWarps * sizeof(Queue64) : 0));
-  float2 *LF2 = reinterpret_cast<float2 *>(LF + kLogTab);
-  if (g.ffpos)
-    for (int i = threadIdx.x; i < kLogTab; i += kThreads) { LF[i] = g.lnfff[i]; LF2[i] = g.lnfff2[i]; }
   // positions and continuation sites in float-float (member sets keep the
   // FP64 logarithm: their grids have ffpos = 0, and the kernel is smaller
   // without the other path)
   const bool ffp = MODE != MODE_MEMBERS && g.ff && g.ffpos;
+  // float-float positions (ffpos.cuh) of in-grid points, continued points'
+  // sites and alpha_s: their steps table after the queues; then the FP64
+  // logarithm's tables, which only a grid without float-float positions
+  // reads (none reserved otherwise: xf64_smem)
+  float4 *LF = reinterpret_cast<float4 *>(smem + off + (kQueue ? kWarps * sizeof(Queue64) : 0));
+  float2 *LF2 = reinterpret_cast<float2 *>(LF + kLogTab);
+  if (g.ffpos)
+    for (int i = threadIdx.x; i < kLogTab; i += kThreads) { LF[i] = g.lnfff[i]; LF2[i] = g.lnfff2[i]; }
+  double2 *LTt = reinterpret_cast<double2 *>(reinterpret_cast<unsigned char *>(LF2) + keys_bytes(kLogTab, 8));
+  double *LTh = reinterpret_cast<double *>(LTt + kLogTab);
+  if (!ffp)
+    for (int i = threadIdx.x; i < kLogTab; i += kThreads) { LTt[i] = g.tlogtab[i]; LTh[i] = g.tloghtab[i]; }
+  const LogTabs LT{LTt, LTh};
   for (int i = threadIdx.x; i < kFFLogTab; i += kThreads) FTl[i] = g.fflog[i];
   for (int i = threadIdx.x; i < kFFExpTab; i += kThreads) FTe[i] = g.ffexp[i];
   const FFTabs FT{FTl, FTe};
@@ -887,10 +888,12 @@ static int num_sms() {
 
 template <int MODE, int PART = PART_ALL>
 static size_t xf64_smem(const GridView &g) {
-  return keys_bytes(g.nx, 8) + keys_bytes(g.nrows, 8) + keys_bytes(g.na, 8) + sizeof(double2) * kLogTab +
-         keys_bytes(kLogTab, 8) + sizeof(float4) * kFFLogTab + sizeof(float2) * kFFExpTab +
+  const bool ffp = MODE != MODE_MEMBERS && g.ff && g.ffpos;  // as in the kernel: no FP64 log tables then
+  return keys_bytes(g.nx, 8) + keys_bytes(g.nrows, 8) + keys_bytes(g.na, 8) + sizeof(float4) * kFFLogTab +
+         sizeof(float2) * kFFExpTab +
          kWarps * (sizeof(Rec64) + (MODE == MODE_MEMBERS || PART == PART_NEAR ? 0 : sizeof(Queue64))) +
-         (sizeof(float4) + sizeof(float2)) * kLogTab;
+         sizeof(float4) * kLogTab + keys_bytes(kLogTab, 8) +
+         (ffp ? 0 : sizeof(double2) * kLogTab + keys_bytes(kLogTab, 8));
 }
 
 // Batches of at least this many points take the two launches (near, far).
