@@ -325,3 +325,27 @@ def test_no_scratch_runs_the_unsorted_kernel(full, synth):
     assert (np.abs(gv - go) <= 1e-10 * gabs + 1e-300).all()
     assert (np.abs(gv - sv_) <= 1e-12 * gabs + 1e-300).all()
     assert (np.abs(gx - sx_) <= 1e-13 * sx + 1e-280).all()
+
+
+def test_sorted_batch_without_private_copies(full, synth):
+    """A scratch bound that leaves room for the sort (~8 B per point) but not
+    for two copies of the knot gradient keeps the sorted kernel and sends
+    the continuation points' knot terms to grad_values directly: the same
+    gradients as with the copies, and the oracle's."""
+    g, G, og = full
+    n = 6000
+    x, q2 = synth.queries_class(g, "lowx", n, 61)
+    cot = np.random.default_rng(62).standard_normal((n, g.nflav))
+    _, _, with_copies = run_vjp(G, x, q2, cot)
+    copy_bytes = 8 * G.nrows * G.nx * G.nflav
+    before = P.scratch_limit()
+    try:
+        P.set_scratch_limit(copy_bytes)  # the sort's ~0.1 MB fits, two copies do not
+        gx, gq, gv = run_vjp(G, x, q2, cot)
+    finally:
+        P.set_scratch_limit(before)
+    go, gabs = og.knot_grad(x, q2, cot, with_abs=True)
+    for got in (gv, with_copies):
+        assert (np.abs(got - go) <= 1e-10 * gabs + 1e-300).all()
+    assert (np.abs(gv - with_copies) <= 1e-12 * gabs + 1e-300).all()
+    assert np.isfinite(gx).all() and np.isfinite(gq).all()
