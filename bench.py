@@ -601,11 +601,28 @@ def members_leg(args, dev, world, sync, rank):
                        "kernels), wall clock, once per set; ms is one evaluation call on the loaded set"}
 
 
-def mc_leg(G, world, sync, rank):
+def mc_cut_pass_fraction(x_min, x_max, s, shat_min):
+    """Share of events with x1 x2 s >= shat_min for x1, x2 log-uniform in
+    [x_min, x_max]: ln x1 + ln x2 has the triangular density of two uniform
+    variables on [lo, hi]."""
+    lo, hi = math.log(x_min), math.log(x_max)
+    span = hi - lo
+    a = math.log(shat_min / s) if shat_min > 0 else -math.inf
+    if a <= 2 * lo:
+        return 1.0
+    if a >= 2 * hi:
+        return 0.0
+    if a <= lo + hi:
+        return 1.0 - (a - 2 * lo) ** 2 / (2 * span * span)
+    return (2 * hi - a) ** 2 / (2 * span * span)
+
+
+def mc_leg(G, world, sync, rank, x_max=1.0):
     """Monte Carlo integration (the event workload at full size): 1e8 events per rank in 100
     chunks of 1e6, device RNG, fused PDF + alpha_s load, weights summed on the
     device; the three sums are added over ranks (the integration's one
-    exchange step)."""
+    exchange step).  Events below the s-hat cut are integrated with weight
+    zero and not evaluated; evals_per_s counts the evaluations made."""
     import paper_2009_06635_gb300 as P
 
     n, chunk = MC_INTEGRATE_EVENTS, MC_EVENTS
@@ -622,8 +639,10 @@ def mc_leg(G, world, sync, rank):
     sync()
     s = max_over_ranks(world, time.perf_counter() - t0)
     tot = P.McResult(allreduce_mc_sums([r.sum_w, r.sum_w2, r.sum_abs]), world * n)
+    passed = mc_cut_pass_fraction(cfg["x_min"], x_max, cfg["sqrt_s"] ** 2, cfg["shat_min"])
     return {"events": world * n, "chunk": chunk, "s": s, "events_per_s": world * n / s,
-            "evals_per_s": world * n * (2 * 13 + 1) / s, "estimate": tot.estimate, "std_error": tot.std_error,
+            "evaluated_fraction": passed, "evals_per_s": world * n * passed * (2 * 13 + 1) / s,
+            "estimate": tot.estimate, "std_error": tot.std_error,
             "config": dict(cfg, observable="toy LO: L^2/s-hat [sum_q e_q^2 (q qbar + qbar q) + alpha_s^2 g g]")}
 
 
@@ -766,7 +785,7 @@ def our_arm(args):
 
     ms_adj = run_timed(step_adj, args.steps, 2, world, sync)
 
-    mc_int = mc_leg(G, world, sync, rank)
+    mc_int = mc_leg(G, world, sync, rank, x_max=float(g.x_knots[-1]))
     small = small_grid_leg(dev, sync)
     members = None if args.no_members else members_leg(args, dev, world, sync, rank)
     surrogate = None if args.no_surrogate else surrogate_leg(args, G, g, dev, world, sync, rank, nf,

@@ -219,7 +219,8 @@ PDF_API int pdf_mc_event_f32(const pdf_grid *grid, const float *x1, const float 
 /* Monte Carlo integration driven by the PDF load (PDFFlow Sec. 4.1; the
  * VegasFlow use of Sec. 5): events are generated on the device, their
  * flavours and alpha_s evaluated by the fused event kernel, and their weights
- * summed on the device in a fixed order, chunk by chunk.
+ * summed on the device in a fixed order, chunk by chunk.  Events below the
+ * s-hat cut (weight zero) are counted but their PDFs are not evaluated.
  *   Event i (global index): u1 = U(z_{2i}), u2 = U(z_{2i+1}), z_k the k-th
  *   output of SplitMix64 seeded with `seed` (Steele, Lea, Flood, OOPSLA 2014:
  *   state seed + (k+1) * 0x9E3779B97F4A7C15 through its 64-bit finaliser),
@@ -236,7 +237,7 @@ PDF_API int pdf_mc_event_f32(const pdf_grid *grid, const float *x1, const float 
  * [first_event, first_event + n_events).  chunk: events per launch (>= 1).
  * Requires alpha_s and pids 1..5, -1..-5, 21 (PDF_ERR_NO_ALPHAS, PDF_ERR_PID);
  * 0 < x_min < last x knot, sqrt_s > 0, shat_min >= 0 (PDF_ERR_ARG).  The
- * device scratch (chunk x (2 nflav + 1) doubles) belongs to the grid and is
+ * device scratch (chunk x (2 nflav + 2) doubles) belongs to the grid and is
  * reused: calls on one grid must not overlap.  Returns when sums are on the
  * host; the result is bit-reproducible for given (seed, events, chunk). */
 typedef struct {

@@ -2,8 +2,11 @@
 // of PDFFlow Sec. 4.1 (the VegasFlow use of Sec. 5).
 //
 // Per chunk of events, three launches on the caller's stream:
-//   1. k_xf64<MODE_MC> generates the events (mc.cuh) and writes, per event,
-//      all flavours at x1 and at x2 and alpha_s at Q^2 = x1 x2 s;
+//   1. k_xf64<MODE_MC> generates the events (mc.cuh), writes each event's
+//      s-hat = Q^2 = x1 x2 s, and for the events that pass the s-hat cut
+//      all flavours at x1 and at x2 and alpha_s at Q^2 (an event below the
+//      cut has weight zero whatever its PDFs: it is not evaluated, and when
+//      no evaluated event can leave the grid the far launch is left out);
 //   2. k_mc_weights turns each row into the event weight and reduces
 //      (w, w^2, |w|) per block, in a fixed order;
 //   3. k_mc_reduce adds the block sums, in a fixed order, to the running sums.
@@ -40,16 +43,14 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
 //   w = L^2 / s-hat * [sum_q e_q^2 (xf_q(x1) xf_qbar(x2) + xf_qbar(x1) xf_q(x2))
 //                      + alpha_s^2 xf_g(x1) xf_g(x2)],  s-hat >= s-hat_min, else 0.
 __global__ void __launch_bounds__(kMcThreads)
-k_mc_weights(const double *__restrict__ ev, long long n, McGen gen, double s, double shat_min, double lfac2,
-             McCols c, double *__restrict__ part) {
+k_mc_weights(const double *__restrict__ ev, const double *__restrict__ shats, long long n, double shat_min,
+             double lfac2, McCols c, double *__restrict__ part) {
   __shared__ double sh[kMcThreads / 32];
   const double e2[5] = {1.0 / 9.0, 4.0 / 9.0, 1.0 / 9.0, 4.0 / 9.0, 1.0 / 9.0};
   const int per = 2 * c.nf + 1;
   double sw = 0.0, sw2 = 0.0, sa = 0.0;
   for (long long i = (long long)blockIdx.x * kMcThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kMcThreads) {
-    double x1, x2;
-    mc_event(gen, (unsigned long long)i, x1, x2);
-    const double shat = x1 * x2 * s;
+    const double shat = shats[i];  // x1 x2 s, as the event kernel took it
     double w = 0.0;
     if (shat >= shat_min) {
       const double *r1 = ev + i * per, *r2 = r1 + c.nf;
@@ -86,8 +87,8 @@ int ensure_mc(pdf_grid *g, size_t cap) {
   if (g->mc_buf && g->mc_cap >= cap) return PDF_OK;
   if (g->mc_buf) { cudaFree(g->mc_buf); g->mc_buf = nullptr; }
   if (g->mc_part) { cudaFree(g->mc_part); g->mc_part = nullptr; }
-  const size_t per = 2 * (size_t)g->v.nf + 1;
-  cudaError_t e = cudaMalloc(&g->mc_buf, cap * per * sizeof(double));
+  const size_t per = 2 * (size_t)g->v.nf + 1;  // a row per event, then the events' s-hat
+  cudaError_t e = cudaMalloc(&g->mc_buf, cap * (per + 1) * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&g->mc_part, (3 * (size_t)kMcBlocks + 3) * sizeof(double));
   if (e != cudaSuccess) {
     if (g->mc_buf) cudaFree(g->mc_buf);
@@ -142,6 +143,22 @@ extern "C" int pdf_mc_integrate(const pdf_grid *cg, const pdf_mc_config *cfg, un
   gen.xmax = v.xlast;
   gen.on = 1;
   gen.et = v.texptab;
+  // events that fail the s-hat cut get weight zero whatever their PDFs, and
+  // k_mc_weights reads the rows of the others only: the event kernel skips
+  // them (the same product x1 x2 s decides in both kernels)
+  gen.cut = 1;
+  gen.shat_min = cfg->shat_min;
+  // With x in [x_min, x_max] (x_max capped, the lower end within a few ulp of
+  // x_min) and Q^2 = x1 x2 s in [shat_min, fl(fl(x_max x_max) s)] (rounding is
+  // monotonic) every evaluated event lies inside the grid when x_min clears
+  // its first x knot and that Q^2 range lies in [Q2min, Q2max]: the far launch
+  // would find nothing to do.
+  gen.near_only = cfg->x_min * (1.0 - 1e-9) >= v.x0 && (v.xlast * v.xlast) * s <= v.q2max &&
+                  cfg->shat_min >= v.q2min;
+  // the event kernel leaves each event's s-hat after the rows: the weights
+  // need no second generation of the events
+  double *shats = g->mc_buf + cap * (2 * (size_t)v.nf + 1);
+  gen.shat_out = shats;
   const double L = gen.lxmax - gen.lxmin;
   cudaError_t e = cudaMemsetAsync(g->mc_acc, 0, 3 * sizeof(double), st);
   for (unsigned long long off = 0; off < n_events && e == cudaSuccess && rc == PDF_OK; off += chunk) {
@@ -149,7 +166,7 @@ extern "C" int pdf_mc_integrate(const pdf_grid *cg, const pdf_mc_config *cfg, un
     gen.first = first_event + off;
     rc = launch_xf64(g, MODE_MC, nullptr, nullptr, nullptr, s, (long long)m, 0, 0, g->mc_buf, nullptr, st, &gen);
     if (rc) break;
-    k_mc_weights<<<kMcBlocks, kMcThreads, 0, st>>>(g->mc_buf, (long long)m, gen, s, cfg->shat_min, L * L, c,
+    k_mc_weights<<<kMcBlocks, kMcThreads, 0, st>>>(g->mc_buf, shats, (long long)m, cfg->shat_min, L * L, c,
                                                     g->mc_part);
     k_mc_reduce<<<1, kMcThreads, 0, st>>>(g->mc_part, kMcBlocks, g->mc_acc);
     rc = check_launch("pdf_mc_integrate kernels");

@@ -26,6 +26,10 @@ struct McGen {
   double xmax;               // x_max (exp may round ln x_max's image above it)
   int on;                    // 1: generate x1, x2; 0: read them
   const double *et;          // tang.cuh's table 2^(k/256) (the grid's texptab)
+  int cut;                   // 1: events with x1 x2 s below shat_min are not evaluated
+  double shat_min;           // (their weight is zero: the integration never reads their rows)
+  int near_only;             // 1: no evaluated event can need a continuation rule (no far launch)
+  double *shat_out;          // non-null: x1 x2 s of every event of the launch, cut or not
 };
 
 __host__ __device__ inline unsigned long long splitmix64(unsigned long long seed, unsigned long long k) {

@@ -789,6 +789,8 @@ k_xf64(GridView g, const double *__restrict__ xa, const double *__restrict__ qa,
           else { x1 = xa[e0 + e]; x2 = xb[e0 + e]; }
           q2 = x1 * x2 * s;
           x = (lane & 1) ? x2 : x1;
+          if (PART != PART_FAR && gen.shat_out && (lane & 1) == 0) gen.shat_out[e0 + e] = q2;
+          if (gen.cut && !(q2 >= gen.shat_min)) present = false;  // zero weight: not evaluated
         }
         ob = (e0 + e) * (long long)(2 * g.nf + 1) + (lane & 1) * g.nf;
       }
@@ -907,6 +909,7 @@ static int launch_mode(const pdf_grid *grid, const double *xa, const double *qa,
     if (n >= kSplitMin) {
       const int rc = launch_mode<MODE, PART_NEAR>(grid, xa, qa, xb, s, n, col0, ncol, out, as_out, gen, st);
       if (rc) return rc;
+      if (MODE == MODE_MC && gen.near_only) return PDF_OK;  // no event of the launch needs a rule
       return launch_mode<MODE, PART_FAR>(grid, xa, qa, xb, s, n, col0, ncol, out, as_out, gen, st);
     }
   }

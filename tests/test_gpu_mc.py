@@ -44,6 +44,34 @@ def test_sums_match_the_oracle_over_the_same_events(full):
     assert r.n == n and np.isfinite(r.std_error) and r.std_error > 0
 
 
+@pytest.mark.parametrize("kw", [{}, dict(sqrt_s=2e5, x_min=1e-10, shat_min=0.5)],
+                         ids=["inside_the_grid", "continued_events"])
+def test_two_launch_chunks_match_the_oracle(full, kw):
+    """Chunks of 65536 events or more take the near and far launches; events
+    below the s-hat cut are not evaluated, and where no evaluated event can
+    leave the grid (the standard configuration: x_min above the first x
+    knot, x_max^2 s below Q2max, shat_min above Q2min) the far launch is left
+    out.  The other configuration has evaluated events below x0, above
+    Q2max and below Q2min."""
+    from oracle import mc
+    g, G, og = full
+    c = dict(CFG, **kw)
+    first, n = 777, 70_001
+    r = run(G, n, first=first, chunk=n, **kw)
+    w = mc.weights(og, g.pids, c["sqrt_s"], c["x_min"], c["shat_min"], c["seed"], first, n, g.x_knots[-1])
+    sw, sw2, sa = mc.sums(w)
+    assert np.count_nonzero(w) > 0.3 * n
+    assert abs(r.sum_w - sw) <= 1e-12 * sa, (r.sum_w, sw)
+    assert abs(r.sum_abs - sa) <= 1e-12 * sa
+    assert abs(r.sum_w2 - sw2) <= 1e-12 * sw2
+    if kw:  # the events do leave the grid
+        x1, x2 = mc.events(c["seed"], first, n, c["x_min"], g.x_knots[-1])
+        q2 = x1 * x2 * c["sqrt_s"] ** 2
+        kept = q2 >= c["shat_min"]
+        assert (kept & (np.minimum(x1, x2) < g.x_knots[0])).any()
+        assert (kept & (q2 > g.q2_knots[-1])).any() and (kept & (q2 < g.q2_knots[0])).any()
+
+
 def test_reproducible_and_chunking_changes_only_rounding(full):
     g, G, og = full
     n = 300_007
