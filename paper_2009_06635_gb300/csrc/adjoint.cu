@@ -41,6 +41,20 @@ __device__ __forceinline__ bool ff_safe(double v, int lim) {
   const int e = (int)((b >> 52) & 0x7FF) - 1023;
   return (b << 1) == 0 || (e >= -lim && e < lim);
 }
+// A double with ff_safe(v, 50) as a float pair, on the integer and FMA pipes
+// (ff_of takes three FP64-pipe operations): the high float is the top 24
+// significant bits (truncated), the low one the other 29 fraction bits as an
+// integer rounded to a float and scaled by 2^(e - 52), so hi + lo is v to
+// within 2^-47 of v.
+__device__ __forceinline__ ff2 ff_split50(double v) {
+  const long long b = __double_as_longlong(v);
+  if ((b << 1) == 0) return {0.f, 0.f};
+  const unsigned top = (unsigned)((unsigned long long)b >> 32), sign = top & 0x80000000u;
+  const int e = (int)((top >> 20) & 0x7FF) - 1023;  // |e| < 50
+  const float h = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | (unsigned)((b >> 29) & 0x7FFFFF));
+  const float scale = __uint_as_float(sign | ((unsigned)(e - 52 + 127) << 23));
+  return {h, __fmul_rn(__int2float_rn((int)(b & 0x1FFFFFFF)), scale)};
+}
 
 __device__ __forceinline__ void bern_d(double t, double s, double *B, double *dB) {
   double t2 = t * t, s2 = s * s;
@@ -253,9 +267,10 @@ __device__ __forceinline__ void ff_bern_d(double t, double s, ff2 dpos, ff2 *B, 
 // An in-grid point: F_t dt/dx = sum_lk B_l(u) B'_k(t) dt/dx c_lk and F_u du/dQ^2
 // (likewise) for every flavour in float-float on the FMA pipe from the
 // float-float control points (good to ~2^-46 of sum |w c|); the coordinate
-// sums in FP64.  The knot scatter (the patch is linear in the knot values
-// with weights w_a(t) w_b(u)): FP64 products and atomics per point, or
-// (STAGE) the weights and cotangents staged for the warp's contraction.
+// sums in float-float with the knot gradient (else FP64).  The knot scatter
+// (the patch is linear in the knot values with weights w_a(t) w_b(u)): FP64
+// products and atomics per point, or (STAGE) the weights and cotangents
+// staged for the warp's contraction.
 template <bool STAGE>
 __device__ __forceinline__ void vjp_ingrid_ff(const GridView &g, const Site64 &X, const Site64 &Q, double t,
                                               double ts, double u, double us, long long p,
@@ -308,7 +323,11 @@ __device__ __forceinline__ void vjp_ingrid_ff(const GridView &g, const Site64 &X
   }
   const float4 *cb = reinterpret_cast<const float4 *>(g.coefff + ((size_t)Q.c * g.nx + X.c) * 16 * g.nfp);
   const long long k0 = ((long long)Q.k0 * g.nx + X.k0) * g.nf;  // knot (Q.k0, X.k0); the used ones are >= 0
+  // the coordinate sums sum_f c_f F_t,f and sum_f c_f F_u,f: with the knot
+  // gradient, in float-float for the flavours whose cotangent is of moderate
+  // size (its float pair is needed for the staging anyway), else in FP64
   double sx = 0.0, sq = 0.0;
+  ff2 sxf = {0.f, 0.f}, sqf = {0.f, 0.f};
   for (int f = 0; f < g.nf; f++) {
     const double c = cot[p * g.nf + f];
     float th = 0.f, tl = 0.f, uh = 0.f, ul = 0.f;
@@ -321,12 +340,18 @@ __device__ __forceinline__ void vjp_ingrid_ff(const GridView &g, const Site64 &X
       ff_acc(th, tl, wt[2 * m2 + 1], b.y, b.w);
       ff_acc(uh, ul, wu[2 * m2 + 1], b.y, b.w);
     }
-    sx = fma(c, f2d(th) + f2d(tl), sx);
-    sq = fma(c, f2d(uh) + f2d(ul), sq);
+    const bool cmod = gv && ff_safe(c, 50);
+    const ff2 cf = cmod ? ff_split50(c) : ff2{0.f, 0.f};
+    if (cmod) {
+      sxf = ff_add(sxf, ff_mul(cf, ff_two_sum(th, tl)));
+      sqf = ff_add(sqf, ff_mul(cf, ff_two_sum(uh, ul)));
+    } else {
+      sx = fma(c, f2d(th) + f2d(tl), sx);
+      sq = fma(c, f2d(uh) + f2d(ul), sq);
+    }
     if (STAGE) {
       if (stage) {
-        stage = ff_safe(c, 50);
-        const ff2 cf = ff_of(c);
+        stage = cmod;
         st->c[f] = make_float2(cf.h, cf.l);
       }
     } else if (gv && (__double_as_longlong(c) << 1) != 0) {
@@ -341,6 +366,8 @@ __device__ __forceinline__ void vjp_ingrid_ff(const GridView &g, const Site64 &X
     scatter_point_f64(g.nrows, g.nx, g.nf, Q.w[0], Q.w[1], Q.w[2], Q.w[3], X.w[0], X.w[1], X.w[2], X.w[3], Q.k0,
                       X.k0, cot + p * g.nf, gv);
   }
+  sx += ff_to_d(sxf);
+  sq += ff_to_d(sqf);
   if (gx) gx[p] = sx;
   if (gq) gq[p] = sq;
 }
