@@ -263,6 +263,42 @@ __device__ __forceinline__ void ff_bern_d(double t, double s, ff2 dpos, ff2 *B, 
   dB[3] = ff_mul(t23, dpos);
 }
 
+// The knot weights w_a = sum_k W[a][k] B_k of a proper cell (the Hermite
+// weights of the cell tables, grid.cu: W[1][0] = W[2][3] = 1, and besides
+// those only W[0][1], W[1][1], W[1][2], W[2][1], W[2][2], W[3][2] nonzero)
+// in float-float from the float-float Bernstein basis B.  false if an entry
+// is outside 2^+-50 (then the caller takes the FP64 weights).
+__device__ __forceinline__ bool ff_knot_weights(const double *Wc, const ff2 *B, ff2 *w) {
+  const double e01 = Wc[1], e11 = Wc[5], e12 = Wc[6], e21 = Wc[9], e22 = Wc[10], e32 = Wc[14];
+  if (!(ff_safe(e01, 50) && ff_safe(e11, 50) && ff_safe(e12, 50) && ff_safe(e21, 50) && ff_safe(e22, 50) &&
+        ff_safe(e32, 50)))
+    return false;
+  w[0] = ff_mul(ff_split50(e01), B[1]);
+  w[1] = ff_add(ff_add(B[0], ff_mul(ff_split50(e11), B[1])), ff_mul(ff_split50(e12), B[2]));
+  w[2] = ff_add(ff_add(ff_mul(ff_split50(e21), B[1]), ff_mul(ff_split50(e22), B[2])), B[3]);
+  w[3] = ff_mul(ff_split50(e32), B[2]);
+  return true;
+}
+// FP64 knot weights of both sites and their float pairs (out of line: the
+// rare case of a cell table entry outside the pairs' range).
+__device__ __noinline__ void site_weights_f64(const double *Wx, const double *Wq, double t, double ts, double u,
+                                              double us, double *xw, double *qw, ff2 *wxf, ff2 *wqf) {
+  Site64 Xf, Qf;
+  make_site(Xf, Wx, t, ts, 0, 0, 0.0);
+  make_site(Qf, Wq, u, us, 0, 0, 0.0);
+  for (int k = 0; k < 4; k++) {
+    xw[k] = Xf.w[k];
+    qw[k] = Qf.w[k];
+    wxf[k] = ff_of(xw[k]);
+    wqf[k] = ff_of(qw[k]);
+  }
+}
+// 0, or 2^-lim <= |v| < 2^lim, for a float pair
+__device__ __forceinline__ bool ff_safe_pair(ff2 v, int lim) {
+  const float a = fabsf(v.h);
+  return a == 0.f || (a >= __uint_as_float((unsigned)(127 - lim) << 23) && a < __uint_as_float((unsigned)(127 + lim) << 23));
+}
+
 // ---- in-grid points on a float-float-safe grid ------------------------------
 // An in-grid point: F_t dt/dx = sum_lk B_l(u) B'_k(t) dt/dx c_lk and F_u du/dQ^2
 // (likewise) for every flavour in float-float on the FMA pipe from the
@@ -277,6 +313,11 @@ __device__ __forceinline__ void vjp_ingrid_ff(const GridView &g, const Site64 &X
                                               const double *__restrict__ cot, double *__restrict__ gx,
                                               double *__restrict__ gq, double *__restrict__ gv, Staged *st) {
   ff2 wt[16], wu[16];
+  // the knot weights in float-float (the sorted kernel with the knot
+  // gradient: from the Bernstein basis below; FP64 site weights, X.w and
+  // Q.w, only where a cell table entry is out of range)
+  ff2 wxf[4], wqf[4];
+  bool wff = false;
   {
     ff2 xb[4], xd[4], qb[4], qd[4];
     ff_bern_d(t, ts, ff_of(X.dpos), xb, xd);
@@ -286,7 +327,11 @@ __device__ __forceinline__ void vjp_ingrid_ff(const GridView &g, const Site64 &X
       wt[m] = ff_mul(qb[m >> 2], xd[m & 3]);
       wu[m] = ff_mul(qd[m >> 2], xb[m & 3]);
     }
+    if (STAGE && gv)
+      wff = ff_knot_weights(g.xW + 16 * X.c, xb, wxf) && ff_knot_weights(g.qW + 16 * Q.c, qb, wqf);
   }
+  double xw64[4], qw64[4];  // FP64 knot weights (a table entry out of the pairs' range)
+  if (STAGE && gv && !wff) site_weights_f64(g.xW + 16 * X.c, g.qW + 16 * Q.c, t, ts, u, us, xw64, qw64, wxf, wqf);
   // staged only when every weight and cotangent is 0 or of moderate size, so
   // that each knot's float-float sum keeps its precision relative to that
   // knot's own terms; otherwise this point scatters in FP64
@@ -295,7 +340,7 @@ __device__ __forceinline__ void vjp_ingrid_ff(const GridView &g, const Site64 &X
   if (STAGE && gv) {
     stage = true;
 #pragma unroll
-    for (int k = 0; k < 4; k++) stage = stage && ff_safe(Q.w[k], 25) && ff_safe(X.w[k], 25);
+    for (int k = 0; k < 4; k++) stage = stage && ff_safe_pair(wqf[k], 25) && ff_safe_pair(wxf[k], 25);
   }
   double W[16];  // knot weights w_b(u) w_a(t), 0 where the knot is outside the grid
   if (!STAGE) {
@@ -305,15 +350,9 @@ __device__ __forceinline__ void vjp_ingrid_ff(const GridView &g, const Site64 &X
       W[m] = (row >= 0 && row < g.nrows && col >= 0 && col < g.nx) ? Q.w[m >> 2] * X.w[m & 3] : 0.0;
     }
   } else if (stage) {
-    ff2 wq[4], wx[4];
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-      wq[k] = ff_of(Q.w[k]);
-      wx[k] = ff_of(X.w[k]);
-    }
 #pragma unroll
     for (int m = 0; m < 16; m++) {
-      const ff2 w = ff_mul(wq[m >> 2], wx[m & 3]);
+      const ff2 w = ff_mul(wqf[m >> 2], wxf[m & 3]);
       st->w[m] = make_float2(w.h, w.l);
     }
     st->cell = Q.c * g.nx + X.c;
@@ -363,8 +402,13 @@ __device__ __forceinline__ void vjp_ingrid_ff(const GridView &g, const Site64 &X
   }
   if (STAGE && gv && !stage) {  // not staged after all: FP64 scatter instead
     st->ing = false;
-    scatter_point_f64(g.nrows, g.nx, g.nf, Q.w[0], Q.w[1], Q.w[2], Q.w[3], X.w[0], X.w[1], X.w[2], X.w[3], Q.k0,
-                      X.k0, cot + p * g.nf, gv);
+    if (wff)
+      scatter_point_f64(g.nrows, g.nx, g.nf, ff_to_d(wqf[0]), ff_to_d(wqf[1]), ff_to_d(wqf[2]), ff_to_d(wqf[3]),
+                        ff_to_d(wxf[0]), ff_to_d(wxf[1]), ff_to_d(wxf[2]), ff_to_d(wxf[3]), Q.k0, X.k0,
+                        cot + p * g.nf, gv);
+    else
+      scatter_point_f64(g.nrows, g.nx, g.nf, qw64[0], qw64[1], qw64[2], qw64[3], xw64[0], xw64[1], xw64[2],
+                        xw64[3], Q.k0, X.k0, cot + p * g.nf, gv);
   }
   sx += ff_to_d(sxf);
   sq += ff_to_d(sqf);
@@ -398,6 +442,21 @@ __device__ __forceinline__ void vjp_point(const GridView &g, const long long *xk
     if (!lowx && ps.xc0 == g.nx - 1) { ps.xc0 = g.nx - 2; ps.t0 = 1.0; ps.ts0 = 0.0; }
     if (realq && ps.qc0 == g.nqc) { ps.qc0 = g.top_qc; ps.u0 = 1.0; ps.us0 = 0.0; }
     const double ix = ddiv(1.0, x), iq = ddiv(1.0, q2);
+    if (STAGE && cls == C_IN && g.ff) {
+      // the sorted kernel's in-grid point: its sites' cells, first knots and
+      // d(position)/d(coordinate); the Bernstein and knot weights are taken
+      // in float-float by vjp_ingrid_ff
+      Site64 Xs, Qs;
+      Xs.c = ps.xc0;
+      Xs.k0 = ps.xc0 - 1;
+      Xs.dpos = g.xcell[4 * ps.xc0 + 1] * ix;
+      const int row = g.qc_row[ps.qc0];
+      Qs.c = ps.qc0;
+      Qs.k0 = row - 1;
+      Qs.dpos = g.qcell[4 * row + 1] * iq;
+      vjp_ingrid_ff<STAGE>(g, Xs, Qs, ps.t0, ps.ts0, ps.u0, ps.us0, p, cot, gx, gq, gv, st);
+      return;
+    }
     Site64 X[2], Q[2];
     for (int a = 0; a < (lowx ? 2 : 1); a++) {
       int xc = a ? ps.xc1 : ps.xc0;
