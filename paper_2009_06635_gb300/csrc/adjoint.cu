@@ -56,6 +56,10 @@ __device__ __forceinline__ ff2 ff_split50(double v) {
   return {h, __fmul_rn(__int2float_rn((int)(b & 0x1FFFFFFF)), scale)};
 }
 
+// A double as a float pair: split on the integer pipe within 2^+-50, else
+// by FP64 conversions.
+__device__ __forceinline__ ff2 ff_pair(double v) { return ff_safe(v, 50) ? ff_split50(v) : ff_of(v); }
+
 __device__ __forceinline__ void bern_d(double t, double s, double *B, double *dB) {
   double t2 = t * t, s2 = s * s;
   B[0] = s2 * s; B[1] = 3.0 * t * s2; B[2] = 3.0 * t2 * s; B[3] = t2 * t;
@@ -250,7 +254,7 @@ __device__ __noinline__ void scatter_point_f64(int nrows, int nx, int nf, double
 // FMA pipe.  dB/dt = (-3 s^2, 3 s^2 - 6 t s, 6 t s - 3 t^2, 3 t^2).
 // (ff_sub: ffmath.cuh)
 __device__ __forceinline__ void ff_bern_d(double t, double s, ff2 dpos, ff2 *B, ff2 *dB) {
-  const ff2 tf = ff_of(t), sf = ff_of(s), three = {3.f, 0.f}, six = {6.f, 0.f};
+  const ff2 tf = ff_pair(t), sf = ff_pair(s), three = {3.f, 0.f}, six = {6.f, 0.f};
   const ff2 t2 = ff_mul(tf, tf), s2 = ff_mul(sf, sf), ts = ff_mul(tf, sf);
   B[0] = ff_mul(s2, sf);
   B[1] = ff_mul(three, ff_mul(tf, s2));
@@ -308,8 +312,8 @@ __device__ __forceinline__ bool ff_safe_pair(ff2 v, int lim) {
 // products and atomics per point, or (STAGE) the weights and cotangents
 // staged for the warp's contraction.
 template <bool STAGE>
-__device__ __forceinline__ void vjp_ingrid_ff(const GridView &g, const Site64 &X, const Site64 &Q, double t,
-                                              double ts, double u, double us, long long p,
+__device__ __forceinline__ void vjp_ingrid_ff(const GridView &g, const Site64 &X, const Site64 &Q, ff2 dposx,
+                                              ff2 dposq, double t, double ts, double u, double us, long long p,
                                               const double *__restrict__ cot, double *__restrict__ gx,
                                               double *__restrict__ gq, double *__restrict__ gv, Staged *st) {
   ff2 wt[16], wu[16];
@@ -320,8 +324,8 @@ __device__ __forceinline__ void vjp_ingrid_ff(const GridView &g, const Site64 &X
   bool wff = false;
   {
     ff2 xb[4], xd[4], qb[4], qd[4];
-    ff_bern_d(t, ts, ff_of(X.dpos), xb, xd);
-    ff_bern_d(u, us, ff_of(Q.dpos), qb, qd);
+    ff_bern_d(t, ts, dposx, xb, xd);
+    ff_bern_d(u, us, dposq, qb, qd);
 #pragma unroll
     for (int m = 0; m < 16; m++) {
       wt[m] = ff_mul(qb[m >> 2], xd[m & 3]);
@@ -441,22 +445,30 @@ __device__ __forceinline__ void vjp_point(const GridView &g, const long long *xk
     // a query on the last knot: derivative of the last proper cell at t = 1
     if (!lowx && ps.xc0 == g.nx - 1) { ps.xc0 = g.nx - 2; ps.t0 = 1.0; ps.ts0 = 0.0; }
     if (realq && ps.qc0 == g.nqc) { ps.qc0 = g.top_qc; ps.u0 = 1.0; ps.us0 = 0.0; }
-    const double ix = ddiv(1.0, x), iq = ddiv(1.0, q2);
     if (STAGE && cls == C_IN && g.ff) {
-      // the sorted kernel's in-grid point: its sites' cells, first knots and
-      // d(position)/d(coordinate); the Bernstein and knot weights are taken
-      // in float-float by vjp_ingrid_ff
+      // the sorted kernel's in-grid point: its sites' cells and first knots,
+      // and d(position)/d(coordinate) = (1 / cell width) / coordinate as float
+      // pairs; the Bernstein and knot weights are taken in float-float by
+      // vjp_ingrid_ff
       Site64 Xs, Qs;
       Xs.c = ps.xc0;
       Xs.k0 = ps.xc0 - 1;
-      Xs.dpos = g.xcell[4 * ps.xc0 + 1] * ix;
       const int row = g.qc_row[ps.qc0];
       Qs.c = ps.qc0;
       Qs.k0 = row - 1;
-      Qs.dpos = g.qcell[4 * row + 1] * iq;
-      vjp_ingrid_ff<STAGE>(g, Xs, Qs, ps.t0, ps.ts0, ps.u0, ps.us0, p, cot, gx, gq, gv, st);
+      const double idx = g.xcell[4 * ps.xc0 + 1], idq = g.qcell[4 * row + 1];
+      ff2 dpx, dpq;
+      if (ff_safe(x, 50) && ff_safe(q2, 50) && ff_safe(idx, 50) && ff_safe(idq, 50)) {
+        dpx = ff_div(ff_split50(idx), ff_split50(x));
+        dpq = ff_div(ff_split50(idq), ff_split50(q2));
+      } else {
+        dpx = ff_of(idx * ddiv(1.0, x));
+        dpq = ff_of(idq * ddiv(1.0, q2));
+      }
+      vjp_ingrid_ff<STAGE>(g, Xs, Qs, dpx, dpq, ps.t0, ps.ts0, ps.u0, ps.us0, p, cot, gx, gq, gv, st);
       return;
     }
+    const double ix = ddiv(1.0, x), iq = ddiv(1.0, q2);
     Site64 X[2], Q[2];
     for (int a = 0; a < (lowx ? 2 : 1); a++) {
       int xc = a ? ps.xc1 : ps.xc0;
@@ -472,7 +484,8 @@ __device__ __forceinline__ void vjp_point(const GridView &g, const long long *xk
       make_site(Q[b], g.qW + 16 * qc, u, s, qc, row - 1, dpos);
     }
     if (cls == C_IN && g.ff) {
-      vjp_ingrid_ff<STAGE>(g, X[0], Q[0], ps.t0, ps.ts0, ps.u0, ps.us0, p, cot, gx, gq, gv, st);
+      vjp_ingrid_ff<STAGE>(g, X[0], Q[0], ff_of(X[0].dpos), ff_of(Q[0].dpos), ps.t0, ps.ts0, ps.u0, ps.us0, p, cot,
+                           gx, gq, gv, st);
       return;
     }
     const int nsx = lowx ? 2 : 1;
