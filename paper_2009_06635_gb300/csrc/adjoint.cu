@@ -852,7 +852,7 @@ k_vjp_sorted(GridView g, const double *__restrict__ xa, const double *__restrict
     if (tile >= ntiles) break;
     const long long pos = tile * 32 + lane;
     Staged st{wrow, crow, -1, 0, 0, false, ncopy > 0 ? gvp + (tile % ncopy) * pstride : gv};
-    if (pos < n) vjp_point<GV>(g, xkeys, qkeys, LT, ET, (long long)perm[pos], xa, qa, cot, gx, gq, gv, &st);
+    if (pos < n) vjp_point<true>(g, xkeys, qkeys, LT, ET, (long long)perm[pos], xa, qa, cot, gx, gq, gv, &st);
     if (GV) {
       __syncwarp();
       const int m = lane & 15, fh = lane >> 4;
