@@ -395,7 +395,9 @@ __device__ __forceinline__ void vjp_ingrid_ff(const GridView &g, const Site64 &X
     if (STAGE) {
       if (stage) {
         stage = cmod;
-        st->c[f] = make_float2(cf.h, cf.l);
+        float *cp = reinterpret_cast<float *>(st->c) + 4 * (f >> 1) + (f & 1);  // pair f / 2: {hi, hi, lo, lo}
+        cp[0] = cf.h;
+        cp[2] = cf.l;
       }
     } else if (gv && (__double_as_longlong(c) << 1) != 0) {
 #pragma unroll
@@ -414,6 +416,12 @@ __device__ __forceinline__ void vjp_ingrid_ff(const GridView &g, const Site64 &X
       scatter_point_f64(g.nrows, g.nx, g.nf, qw64[0], qw64[1], qw64[2], qw64[3], xw64[0], xw64[1], xw64[2],
                         xw64[3], Q.k0, X.k0, cot + p * g.nf, gv);
   }
+  if (STAGE && stage)  // the pairs' unused flavours (up to 16) contract as zeros
+    for (int f = g.nf; f < 16; f++) {
+      float *cp = reinterpret_cast<float *>(st->c) + 4 * (f >> 1) + (f & 1);
+      cp[0] = 0.f;
+      cp[2] = 0.f;
+    }
   sx += ff_to_d(sxf);
   sq += ff_to_d(sqf);
   if (gx) gx[p] = sx;
@@ -724,7 +732,8 @@ constexpr int kSortCont = 4;  // continuation bins; the invalid bin follows, the
 constexpr int kSortMaxBins = 65540;  // above this the grid has too many cells for runs to form
 constexpr long long kSortMinN = 2048;
 constexpr int kSortThreads = 128;    // three blocks per SM: 12 warps at <= 168 registers
-constexpr int kStPad = 17;           // float2 per staged row (16 used): 2-way bank conflicts at most
+constexpr int kStPad = 17;           // float2 per staged weight row (16 used): 2-way bank conflicts at most
+constexpr int kStPadC = 18;          // float2 per staged cotangent row: 8 flavour pairs {hi, hi, lo, lo}, 16-byte rows
 constexpr int kAdjCopies = 16;       // private knot-gradient copies for continuation points (at most)
 constexpr size_t kAdjCopyBytes = 64u << 20;
 
@@ -833,8 +842,9 @@ k_vjp_sorted(GridView g, const double *__restrict__ xa, const double *__restrict
   off += sizeof(double) * kLogTab;
   double *ET = reinterpret_cast<double *>(smem + off);
   off += sizeof(double) * kExpTab;
+  off = (off + 15) & ~(size_t)15;
   float2 *stw = reinterpret_cast<float2 *>(smem + off);  // [warp][lane][kStPad] weights
-  float2 *stc = stw + kSortThreads * kStPad;              // [warp][lane][kStPad] cotangents
+  float2 *stc = stw + kSortThreads * kStPad;              // [warp][lane][kStPadC] cotangent pairs
   load_keys<double>(g, xkeys, 0);
   load_keys<double>(g, qkeys, 1);
   for (int i = threadIdx.x; i < kLogTab; i += kSortThreads) { LTt[i] = g.tlogtab[i]; LTh[i] = g.tloghtab[i]; }
@@ -842,8 +852,8 @@ k_vjp_sorted(GridView g, const double *__restrict__ xa, const double *__restrict
   const LogTabs LT{LTt, LTh};
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float2 *wrow = stw + (size_t)threadIdx.x * kStPad, *crow = stc + (size_t)threadIdx.x * kStPad;
-  const float2 *wwarp = stw + (size_t)warp * 32 * kStPad, *cwarp = stc + (size_t)warp * 32 * kStPad;
+  float2 *wrow = stw + (size_t)threadIdx.x * kStPad, *crow = stc + (size_t)threadIdx.x * kStPadC;
+  const float2 *wwarp = stw + (size_t)warp * 32 * kStPad, *cwarp = stc + (size_t)warp * 32 * kStPadC;
   const long long ntiles = (n + 31) / 32;
   while (true) {
     unsigned long long t = 0;
@@ -855,6 +865,9 @@ k_vjp_sorted(GridView g, const double *__restrict__ xa, const double *__restrict
     if (pos < n) vjp_point<true>(g, xkeys, qkeys, LT, ET, (long long)perm[pos], xa, qa, cot, gx, gq, gv, &st);
     if (GV) {
       __syncwarp();
+      // lane: knot m, flavours 8 fh .. 8 fh + 7 as four pairs, each pair's
+      // sum in one packed (f32x2) float-float chain -- the steps of ff_acc
+      // per half
       const int m = lane & 15, fh = lane >> 4;
       unsigned todo = __ballot_sync(0xffffffffu, st.ing);
       while (todo) {  // one run of lanes sharing a cell at a time
@@ -864,29 +877,36 @@ k_vjp_sorted(GridView g, const double *__restrict__ xa, const double *__restrict
         const int qk0 = __shfl_sync(0xffffffffu, st.qk0, leader);
         const unsigned run = __ballot_sync(0xffffffffu, st.ing && st.cell == cell);
         todo &= ~run;
-        float ah[8], al[8];
+        float2 sh[4], sl[4];
 #pragma unroll
-        for (int j = 0; j < 8; j++) ah[j] = al[j] = 0.f;
+        for (int k = 0; k < 4; k++) sh[k] = sl[k] = make_float2(0.f, 0.f);
         for (unsigned r = run; r; r &= r - 1) {
           const int q = __ffs(r) - 1;
           const float2 w = wwarp[q * kStPad + m];
-          const ff2 wf{w.x, w.y};
+          const float2 wh = make_float2(w.x, w.x), wl = make_float2(w.y, w.y);
+          const float4 *cq = reinterpret_cast<const float4 *>(cwarp + q * kStPadC) + 4 * fh;
 #pragma unroll
-          for (int j = 0; j < 8; j++) {
-            const int f = fh + 2 * j;
-            if (f < g.nf) {
-              const float2 c = cwarp[q * kStPad + f];
-              ff_acc(ah[j], al[j], wf, c.x, c.y);
-            }
+          for (int k = 0; k < 4; k++) {
+            const float4 cc = cq[k];
+            const float2 ch = make_float2(cc.x, cc.y), cl = make_float2(cc.z, cc.w);
+            const float2 ph = __fmul2_rn(wh, ch);
+            float2 pe = __ffma2_rn(wh, ch, neg2(ph));
+            pe = __ffma2_rn(wh, cl, __ffma2_rn(wl, ch, pe));
+            const float2 t = __fadd2_rn(sh[k], ph);
+            const float2 bp = __fadd2_rn(t, neg2(sh[k]));
+            const float2 err = __fadd2_rn(__fadd2_rn(sh[k], neg2(__fadd2_rn(t, neg2(bp)))), __fadd2_rn(ph, neg2(bp)));
+            sh[k] = t;
+            sl[k] = __fadd2_rn(sl[k], __fadd2_rn(err, pe));
           }
         }
         const int row = qk0 + (m >> 2), col = xk0 + (m & 3);
         if (row >= 0 && row < g.nrows && col >= 0 && col < g.nx) {
           double *dst = gv + ((size_t)row * g.nx + col) * g.nf;
 #pragma unroll
-          for (int j = 0; j < 8; j++) {
-            const int f = fh + 2 * j;
-            if (f < g.nf) atomicAdd(dst + f, f2d(ah[j]) + f2d(al[j]));
+          for (int k = 0; k < 4; k++) {
+            const int f = 8 * fh + 2 * k;
+            if (f < g.nf) atomicAdd(dst + f, f2d(sh[k].x) + f2d(sl[k].x));
+            if (f + 1 < g.nf) atomicAdd(dst + f + 1, f2d(sh[k].y) + f2d(sl[k].y));
           }
         }
       }
@@ -929,7 +949,7 @@ extern "C" int xfxq2_all_flavours_vjp(const pdf_grid *grid, const double *x, con
   // large batches on a float-float-safe grid: sorted by cell (see k_vjp_sorted)
   if ((long long)n >= kSortMinN && n < (1ull << 31) && g.ff && g.nf <= 16 && nb <= kSortMaxBins) {
     static LaunchCache cache_t, cache_f;
-    const size_t ssmem = smem + 2 * sizeof(float2) * kSortThreads * kStPad;
+    const size_t ssmem = ((smem + 15) & ~(size_t)15) + sizeof(float2) * kSortThreads * (kStPad + kStPadC);
     LaunchCache &cache = grad_values ? cache_t : cache_f;
     const int per_sm = grad_values ? cache.blocks_per_sm(k_vjp_sorted<true>, kSortThreads, ssmem, false)
                                    : cache.blocks_per_sm(k_vjp_sorted<false>, kSortThreads, ssmem, false);

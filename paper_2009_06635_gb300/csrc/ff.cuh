@@ -43,6 +43,8 @@ __device__ __forceinline__ void ff_bernstein(double t, double s, ff2 *B) {
   B[2] = ff_mul(three, ff_mul(t2, sf));
   B[3] = ff_mul(t2, tf);
 }
+// -a of a packed pair (operands of the f32x2 intrinsics __fadd2_rn, __ffma2_rn)
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 // s += w b, s an unnormalised pair (sum, gathered rounding errors): exact
 // product, TwoSum of the high parts, the cross terms and errors in s_l
 __device__ __forceinline__ void ff_acc(float &sh, float &sl, ff2 w, float bh, float bl) {

@@ -68,7 +68,6 @@ struct alignas(16) Queue64 {
 // each operand sit in one register pair.  Each chain adds exact products by
 // TwoSum and gathers the cross terms and rounding errors in a second float;
 // the chains are merged by one more TwoSum at the end.
-__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 __device__ __forceinline__ double dot_ff16(const float4 *c, int nf, const float4 *w) {
   float2 sh = make_float2(0.f, 0.f), sl = make_float2(0.f, 0.f);
 #pragma unroll
