@@ -216,17 +216,37 @@ __device__ __forceinline__ float alphas_eval(const GridView &g, const int *akeys
   return fmaf(fmaf(fmaf(c[5], u, c[4]), u, c[3]), u, c[2]);
 }
 
+// The per-knot tables a point's float-float positions read -- {ln m, 1/d}
+// pairs of the x knots, Q rows and alpha_s nodes, the row -> Q cell map and
+// the alpha_s cells -- from global memory, or from copies in shared memory
+// (the FP64 evaluation kernels: a warp's scattered reads of a few-KB table
+// then take a few shared-memory wavefronts instead of one L1 wavefront per
+// cache line touched).
+struct PosTabs {
+  const float4 *xpos, *qpos, *apos;
+  const double *acell;
+  const int *row_qc;
+};
+__device__ __forceinline__ PosTabs pos_tabs(const GridView &g) {
+  return {g.xposff, g.qposff, g.aposff, g.acell, g.row_qc};
+}
+// Bytes of the shared-memory copies, in the order xpos, qpos, apos (float4),
+// acell (6 doubles per node), row_qc (ints, rounded up to 16 bytes).
+__host__ __device__ inline size_t pos_tabs_bytes(int nx, int nrows, int na) {
+  return 16 * (size_t)(nx + nrows + na) + 48 * (size_t)na + (((size_t)nrows * 4 + 15) / 16) * 16;
+}
+
 // alpha_s (Sec. 2.3) with the node position from ffpos.cuh: constant
 // outside, the cubic in FP64 from the position.
 __device__ __forceinline__ double alphas_ff(const GridView &g, const long long *akeys, const float4 *LF,
-                                            const float2 *LF2, double q2) {
+                                            const float2 *LF2, double q2, const PosTabs &T) {
   const long long kq = __double_as_longlong(q2);
   if (!(kq > 0 && kq < 0x7FF0000000000000LL)) return NAN;
   if (kq < __double_as_longlong(g.aq2lo)) return g.as_lo;
   if (kq > __double_as_longlong(g.aq2hi)) return g.as_hi;
   const int k = search_cell(akeys, g.na, g.astep, kq);
-  const double u = ff_to_d(ff_cell_pos(kq, akeys[k], g.aposff[k], LF, LF2));
-  const double *c = g.acell + 6 * k;
+  const double u = ff_to_d(ff_cell_pos(kq, akeys[k], T.apos[k], LF, LF2));
+  const double *c = T.acell + 6 * k;
   return fma(fma(fma(c[5], u, c[4]), u, c[3]), u, c[2]);
 }
 template <typename T>

@@ -357,7 +357,7 @@ struct NearFF {
 };
 __device__ __forceinline__ NearFF near_sites_ff(const GridView &g, const long long *xkeys,
                                                 const long long *qkeys, const float4 *LF, const float2 *LF2,
-                                                double x, double q2) {
+                                                double x, double q2, const PosTabs &T) {
   NearFF r;
   r.xc0 = r.qc0 = 0;
   r.t = r.u = ff2{0.f, 0.f};
@@ -376,12 +376,12 @@ __device__ __forceinline__ NearFF near_sites_ff(const GridView &g, const long lo
   const int i = search_cell(xkeys, g.nx, g.xstep, kx);
   const int j = search_cell(qkeys, g.nrows, g.qstep, kq);
   r.xc0 = i;
-  r.qc0 = g.row_qc[j];
+  r.qc0 = T.row_qc[j];
   // (an exact hit on the last knot, or the top row, is the knot case: no next knot is read)
   const bool xk1 = kx != xkeys[i], qk1 = kq != qkeys[j];
-  ff_cell_pos2(kx, xkeys[i], xk1 ? xkeys[i + 1] : 0, g.xposff[i], xk1 ? g.xposff[i + 1] : make_float4(0.f, 0.f, 0.f, 0.f),
+  ff_cell_pos2(kx, xkeys[i], xk1 ? xkeys[i + 1] : 0, T.xpos[i], xk1 ? T.xpos[i + 1] : make_float4(0.f, 0.f, 0.f, 0.f),
                LF, LF2, r.t, r.ts);
-  ff_cell_pos2(kq, qkeys[j], qk1 ? qkeys[j + 1] : 0, g.qposff[j], qk1 ? g.qposff[j + 1] : make_float4(0.f, 0.f, 0.f, 0.f),
+  ff_cell_pos2(kq, qkeys[j], qk1 ? qkeys[j + 1] : 0, T.qpos[j], qk1 ? T.qpos[j + 1] : make_float4(0.f, 0.f, 0.f, 0.f),
                LF, LF2, r.u, r.us);
   // an exact knot hit (t = u = 0) keeps the FP64 contraction, so knot values come back exactly
   r.cls = (r.t.h == 0.f && r.u.h == 0.f) ? C_IN : C_INF;
@@ -430,7 +430,8 @@ struct FarFF {
   ff2 t0, ts0, u0, us0, px, pq, lr;
 };
 __device__ __forceinline__ FarFF far_sites_ff(const GridView &g, const long long *xkeys, const long long *qkeys,
-                                              const float4 *LF, const float2 *LF2, double x, double q2) {
+                                              const float4 *LF, const float2 *LF2, double x, double q2,
+                                              const PosTabs &T) {
   FarFF r;
   r.xc0 = r.xc1 = r.qc0 = r.qc1 = 0;
   r.q101 = false;
@@ -447,29 +448,29 @@ __device__ __forceinline__ FarFF far_sites_ff(const GridView &g, const long long
     const int i = search_cell(xkeys, g.nx, g.xstep, kx);
     r.xc0 = i;
     const bool k1 = kx != xkeys[i];
-    ff_cell_pos2(kx, xkeys[i], k1 ? xkeys[i + 1] : 0, g.xposff[i], k1 ? g.xposff[i + 1] : make_float4(0.f, 0.f, 0.f, 0.f),
+    ff_cell_pos2(kx, xkeys[i], k1 ? xkeys[i + 1] : 0, T.xpos[i], k1 ? T.xpos[i + 1] : make_float4(0.f, 0.f, 0.f, 0.f),
                  LF, LF2, r.t0, r.ts0);
   } else {
     r.xc1 = 1;
-    const float4 k0 = g.xposff[0];
+    const float4 k0 = T.xpos[0];
     r.px = ff_mul(ff_ln_ratio(ff_ln_sig(kx, LF, LF2), xkeys[0], k0.x, k0.y), ff2{k0.z, k0.w});
   }
   if (!lowq && !highq) {
     const int j = search_cell(qkeys, g.nrows, g.qstep, kq);
-    r.qc0 = g.row_qc[j];
+    r.qc0 = T.row_qc[j];
     const bool k1 = kq != qkeys[j];
-    ff_cell_pos2(kq, qkeys[j], k1 ? qkeys[j + 1] : 0, g.qposff[j], k1 ? g.qposff[j + 1] : make_float4(0.f, 0.f, 0.f, 0.f),
+    ff_cell_pos2(kq, qkeys[j], k1 ? qkeys[j + 1] : 0, T.qpos[j], k1 ? T.qpos[j + 1] : make_float4(0.f, 0.f, 0.f, 0.f),
                  LF, LF2, r.u0, r.us0);
   } else if (highq) {
     r.qc0 = g.nqc;
     r.qc1 = g.top_qc;
-    const float4 kt = g.qposff[g.nrows - 1], kc = g.qposff[g.nrows - 2];  // Q2max; its cell's width
+    const float4 kt = T.qpos[g.nrows - 1], kc = T.qpos[g.nrows - 2];  // Q2max; its cell's width
     r.pq = ff_mul(ff_ln_ratio(ff_ln_sig(kq, LF, LF2), qkeys[g.nrows - 1], kt.x, kt.y), ff2{-kc.z, -kc.w});
   } else {
     r.qc1 = g.q101_qc;
     r.q101 = true;
     r.pq = ff_of(q2 * g.inv_q2min);
-    const float4 k0 = g.qposff[0];
+    const float4 k0 = T.qpos[0];
     r.lr = ff_ln_ratio(ff_ln_sig(kq, LF, LF2), qkeys[0], k0.x, k0.y);
   }
   r.cls = lowx ? (highq ? C_LOWX_HIGHQ : lowq ? C_LOWX_LOWQ : C_LOWX) : (highq ? C_HIGHQ : lowq ? C_LOWQ : C_IN);
@@ -677,7 +678,25 @@ k_xf64(GridView g, const double *__restrict__ xa, const double *__restrict__ qa,
   float2 *LF2 = reinterpret_cast<float2 *>(LF + kLogTab);
   if (g.ffpos)
     for (int i = threadIdx.x; i < kLogTab; i += kThreads) { LF[i] = g.lnfff[i]; LF2[i] = g.lnfff2[i]; }
-  double2 *LTt = reinterpret_cast<double2 *>(reinterpret_cast<unsigned char *>(LF2) + keys_bytes(kLogTab, 8));
+  // the per-knot position tables and cell maps (PosTabs) on grids with
+  // float-float positions (member sets read them from global memory)
+  const bool stp = MODE != MODE_MEMBERS && g.ffpos;
+  unsigned char *tab = reinterpret_cast<unsigned char *>(LF2) + keys_bytes(kLogTab, 8);
+  PosTabs PT = pos_tabs(g);
+  if (stp) {
+    float4 *xp = reinterpret_cast<float4 *>(tab), *qp = xp + g.nx, *ap = qp + g.nrows;
+    double *ac = reinterpret_cast<double *>(ap + g.na);
+    int *rq = reinterpret_cast<int *>(ac + 6 * g.na);
+    for (int i = threadIdx.x; i < g.nx; i += kThreads) xp[i] = g.xposff[i];
+    for (int i = threadIdx.x; i < g.nrows; i += kThreads) { qp[i] = g.qposff[i]; rq[i] = g.row_qc[i]; }
+    if (want_as) {
+      for (int i = threadIdx.x; i < g.na; i += kThreads) ap[i] = g.aposff[i];
+      for (int i = threadIdx.x; i < 6 * g.na; i += kThreads) ac[i] = g.acell[i];
+    }
+    PT = PosTabs{xp, qp, ap, ac, rq};
+    tab += pos_tabs_bytes(g.nx, g.nrows, g.na);
+  }
+  double2 *LTt = reinterpret_cast<double2 *>(tab);
   double *LTh = reinterpret_cast<double *>(LTt + kLogTab);
   if (!ffp)
     for (int i = threadIdx.x; i < kLogTab; i += kThreads) { LTt[i] = g.tlogtab[i]; LTh[i] = g.tloghtab[i]; }
@@ -728,7 +747,7 @@ k_xf64(GridView g, const double *__restrict__ xa, const double *__restrict__ qa,
     if (ffp) {  // warp-uniform: sites and rule parameters without the FP64 logarithm
       FarFF fs;
       fs.cls = -1;
-      if (present) fs = far_sites_ff(g, xkeys, qkeys, LF, LF2, x, q2);
+      if (present) fs = far_sites_ff(g, xkeys, qkeys, LF, LF2, x, q2, PT);
       np = sort_slots<C_LOWX, C_HIGHQ, C_LOWQ, C_LOWX_HIGHQ, C_LOWX_LOWQ>(fs.cls, lane, slot);
       if (present) store_point_far_ff(R, slot, fs, ob, g);
     } else {
@@ -813,7 +832,7 @@ k_xf64(GridView g, const double *__restrict__ xa, const double *__restrict__ qa,
           // classification and in-grid positions without the FP64 logarithm;
           // continuation points keep the FP64 sites of their rules (the near
           // launch leaves them to the far one)
-          if (present) nf = near_sites_ff(g, xkeys, qkeys, LF, LF2, x, q2);
+          if (present) nf = near_sites_ff(g, xkeys, qkeys, LF, LF2, x, q2, PT);
           ps.cls = nf.cls;
           if (PART != PART_NEAR && !kQueue && is_far(nf.cls)) ps = sites(g, xkeys, qkeys, x, q2, LT, lq);
         } else {
@@ -830,9 +849,9 @@ k_xf64(GridView g, const double *__restrict__ xa, const double *__restrict__ qa,
         }
         if (MODE == MODE_MC) {
           if (present && (lane & 1) == 0)
-            out[ob + 2 * g.nf] = g.ffpos ? alphas_ff(g, akeys, LF, LF2, q2) : alphas_eval(g, akeys, q2, lq);
+            out[ob + 2 * g.nf] = g.ffpos ? alphas_ff(g, akeys, LF, LF2, q2, PT) : alphas_eval(g, akeys, q2, lq);
         } else if (MODE == MODE_POINTS) {
-          if (present && as_out) as_out[e0 + lane] = g.ffpos ? alphas_ff(g, akeys, LF, LF2, q2) : alphas_eval(g, akeys, q2, lq);
+          if (present && as_out) as_out[e0 + lane] = g.ffpos ? alphas_ff(g, akeys, LF, LF2, q2, PT) : alphas_eval(g, akeys, q2, lq);
         }
 
         int key = ps.cls, slot = 0, np;
@@ -889,11 +908,13 @@ static int num_sms() {
 
 template <int MODE, int PART = PART_ALL>
 static size_t xf64_smem(const GridView &g) {
-  const bool ffp = MODE != MODE_MEMBERS && g.ff && g.ffpos;  // as in the kernel: no FP64 log tables then
+  // as in the kernel: no FP64 log tables with float-float positions and
+  // contraction; the position tables staged with float-float positions
+  const bool ffp = MODE != MODE_MEMBERS && g.ff && g.ffpos, stp = MODE != MODE_MEMBERS && g.ffpos;
   return keys_bytes(g.nx, 8) + keys_bytes(g.nrows, 8) + keys_bytes(g.na, 8) + sizeof(float4) * kFFLogTab +
          sizeof(float2) * kFFExpTab +
          kWarps * (sizeof(Rec64) + (MODE == MODE_MEMBERS || PART == PART_NEAR ? 0 : sizeof(Queue64))) +
-         sizeof(float4) * kLogTab + keys_bytes(kLogTab, 8) +
+         sizeof(float4) * kLogTab + keys_bytes(kLogTab, 8) + (stp ? pos_tabs_bytes(g.nx, g.nrows, g.na) : 0) +
          (ffp ? 0 : sizeof(double2) * kLogTab + keys_bytes(kLogTab, 8));
 }
 

@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(kThreads) k_alphas(GridView g, const T *__rest
       // FP64: the node position as the evaluation kernels take it (float-float
       // from the knots' exponents and significands, or the FP64 logarithm)
       if constexpr (sizeof(T) == 8)
-        out[i] = g.ffpos ? alphas_ff(g, akeys, g.lnfff, g.lnfff2, q2)
+        out[i] = g.ffpos ? alphas_ff(g, akeys, g.lnfff, g.lnfff2, q2, pos_tabs(g))
                          : alphas_eval(g, akeys, q2, bad ? 0.0 : tlog(q2, LogTabs{g.tlogtab, g.tloghtab}));
       else out[i] = alphas_eval(g, akeys, g.acell32, q2);
     }
