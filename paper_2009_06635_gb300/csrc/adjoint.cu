@@ -318,8 +318,9 @@ __device__ __forceinline__ void vjp_ingrid_ff(const GridView &g, const Site64 &X
                                               double *__restrict__ gq, double *__restrict__ gv, Staged *st) {
   ff2 wt[16], wu[16];
   // the knot weights in float-float (the sorted kernel with the knot
-  // gradient: from the Bernstein basis below; FP64 site weights, X.w and
-  // Q.w, only where a cell table entry is out of range)
+  // gradient: from the Bernstein basis below; FP64 weights, out of line in
+  // site_weights_f64, only where a cell table entry is out of range; the
+  // sorted kernel's sites carry no FP64 weights, the per-point kernel's do)
   ff2 wxf[4], wqf[4];
   bool wff = false;
   {
