@@ -61,6 +61,19 @@ def test_largest_knot_counts(synth, oracle_mod):
     check(synth, oracle_mod, g, n=20_000, seed=2)
 
 
+def test_largest_knot_counts_in_two_launches(synth, oracle_mod):
+    """The same grid (2048 x knots, 1024 Q rows and alpha_s nodes: the most
+    shared memory the staged knot and position tables take) with a batch
+    above the two-launch threshold (near and far launches)."""
+    xk = np.geomspace(1e-9, 1.0, 2048)
+    bounds = np.geomspace(1.0, 1e10, 5)
+    subs = [np.geomspace(bounds[k], bounds[k + 1], 256) for k in range(4)]
+    pids = list(range(-7, 0)) + [21] + list(range(1, 9))
+    g = synth.make_grid(xk, subs, pids, params=synth.flavour_params(len(pids), 31))
+    assert len(g.as_q2) == 1024
+    check(synth, oracle_mod, g, n=70_000, seed=3, fp32=False)
+
+
 def test_most_flavours(synth, oracle_mod):
     xk = np.geomspace(1e-7, 1.0, 40)
     subs = [np.geomspace(2.0, 20.0, 8), np.geomspace(20.0, 1e6, 12)]
