@@ -36,7 +36,10 @@ PDF_API int pdf_probe_fma_rate(int precision, int iters, double *flops_per_s);
  * relative); fn 6, 7: the position t of x = a in its x cell and 1 - t, as
  * the evaluation kernels take it in float-float (ffpos.cuh; NaN for a
  * outside [x0, x_last]; PDF_ERR_ARG on a grid that keeps the FP64
- * positions).  b may be NULL unless fn is 2 or 5.  The tables are the
+ * positions); fn 8, 9: the adjoint's split of a double into a float pair on
+ * the integer pipe (ffsplit.cuh), hi + lo and hi alone (hi the top 24
+ * significant bits of a, hi + lo within 2^-48 |a|; NaN for a outside 0 and
+ * 2^-50 <= |a| < 2^50).  b may be NULL unless fn is 2 or 5.  The tables are the
  * grid's (a handle of the evaluation library, loaded in the same process).
  * Asynchronous on `stream`. */
 PDF_API int pdf_probe_math(const pdf_grid *grid, int fn, const double *a, const double *b, size_t n,

@@ -11,6 +11,7 @@
 #include "pdf_gb300_probe.h"
 #include "ffmath.cuh"
 #include "ffpos.cuh"
+#include "ffsplit.cuh"
 #include "pdf_internal.cuh"
 
 namespace {
@@ -84,6 +85,16 @@ __global__ void k_math(GridView g, int fn, const double *a, const double *b, lon
     case 3: out[i] = ff_to_d(ff_log(ff_of(a[i]), FT)); break;
     case 4: out[i] = ff_to_d(ff_exp(ff_of(a[i]), FT)); break;
     case 5: out[i] = ff_to_d(ff_div(ff_of(a[i]), ff_of(b[i]))); break;
+    case 8:  // the integer split of a (ffsplit.cuh): hi + lo, NaN outside its range
+    case 9: {  // hi alone
+      if (!ff_safe(a[i], 50)) {
+        out[i] = NAN;
+        break;
+      }
+      const ff2 v = ff_split50(a[i]);
+      out[i] = fn == 8 ? ff_to_d(v) : f2d(v.h);
+      break;
+    }
     default: {  // 6, 7: t and 1 - t of x = a[i] in its x cell (ffpos.cuh), a[i] in [x0, x_last]
       const long long *xk = reinterpret_cast<const long long *>(g.xk);
       const long long kx = __double_as_longlong(a[i]);
@@ -109,8 +120,9 @@ extern "C" int pdf_probe_math(const pdf_grid *grid, int fn, const double *a, con
   using namespace pdfgb;
   if (!grid || (n > 0 && (!a || !out || ((fn == 2 || fn == 5) && !b))))
     return probe_error(PDF_ERR_NULL, "pdf_probe_math: NULL argument");
-  if (fn < 0 || fn > 7) return probe_error(PDF_ERR_ARG, "pdf_probe_math: fn must be 0 .. 7");
-  if (fn >= 6 && !grid->v.ffpos) return probe_error(PDF_ERR_ARG, "pdf_probe_math: the grid takes no float-float positions");
+  if (fn < 0 || fn > 9) return probe_error(PDF_ERR_ARG, "pdf_probe_math: fn must be 0 .. 9");
+  if ((fn == 6 || fn == 7) && !grid->v.ffpos)
+    return probe_error(PDF_ERR_ARG, "pdf_probe_math: the grid takes no float-float positions");
   if (n == 0) return PDF_OK;
   k_math<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(grid->v, fn, a, b, (long long)n, out);
   return probe_launch("pdf_probe_math");

@@ -156,3 +156,23 @@ def test_float_float_cell_positions(synth):
     for k in range(x.size - len(xk) - len(top), x.size - len(xk)):  # next to x = 1
         ets = 1 - (Decimal(float(x[k])).ln() - Decimal(float(xk[-2])).ln()) / (-Decimal(float(xk[-2])).ln())
         assert abs(Decimal(float(ts[k])) - ets) <= Decimal("1e-13") * ets, (x[k], float(ts[k]), float(ets))
+
+
+def test_integer_split_to_float_pairs(grid):
+    """The adjoint's split of a double into a float pair without FP64
+    conversions (ffsplit.cuh): hi is the double's top 24 significant bits
+    (truncated, so |hi| <= |a|), hi + lo is a to within 2^-48 |a| with lo of
+    a's sign, zeros split to zeros, and values outside 2^+-50 are refused."""
+    r = np.random.default_rng(11)
+    mag = np.exp2(r.uniform(-50, 50, 200_000))
+    a = np.concatenate([mag * r.choice([-1.0, 1.0], mag.size), [0.0, -0.0, 1.0, -1.0, 2.0 ** -50,
+                        np.nextafter(2.0 ** 50, 0), 1 + 2.0 ** -52, 1 - 2.0 ** -53, 3.0 ** 30]])
+    hi = run(grid, 9, a)
+    top = (a.view(np.int64) & ~np.int64((1 << 29) - 1)).view(np.float64)  # the top 24 significant bits
+    assert np.array_equal(hi, top)
+    both = run(grid, 8, a)
+    assert (np.abs(both - a) <= 2.0 ** -48 * np.abs(a)).all()
+    assert (np.abs(both) >= np.abs(hi)).all()  # lo has a's sign
+    assert np.array_equal(run(grid, 8, np.array([0.0])), [0.0])
+    out = run(grid, 8, np.array([2.0 ** 50, 2.0 ** -51, -2.0 ** 60, np.inf, np.nan]))
+    assert np.isnan(out).all()
